@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Throughput of the fused particle step (DEM contacts + drag + heat + USCM kinetics +
+deposition + gas update) on GB300, in parcel-updates per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on rank 0. The default workload is the 2,000,000-parcel two-ore bed with the
+conical bottom and perforated distributor plate (64x64x384 gas cells), split precision
+(FP32 forces/kinetics, FP64 positions, masses and cell sums), stepped by replaying a CUDA
+graph of one step. Under torchrun every rank steps its own replica of the workload (the
+path has no exchange between beds): weak scaling, max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "parcel-updates/s per fused DEM+reaction step; % HBM roofline; adjoint/fwd cost"
+UNIT = "parcel-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ibm_2m", choices=["ibm_2m", "split_200k", "plain_2k", "batched_32"])
+    ap.add_argument("--precision", default="split", choices=["split", "fp64", "split_kahan"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-form", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=100_000, help="parcels in the oracle's sample")
+    return ap.parse_args()
+
+
+def make_workload(name: str, rank: int = 0):
+    from paper_2311_03908_gb300 import synth
+    seed_shift = 7919 * rank
+    if name == "ibm_2m":
+        return synth.config_ibm_2m(seed=2311039083 + seed_shift)
+    if name == "split_200k":
+        return synth.config_split_200k(seed=2311039082 + seed_shift)
+    if name == "plain_2k":
+        return synth.config_plain_2k(seed=2311039081 + seed_shift)
+    if name == "batched_32":
+        return synth.config_batched_32(seed=2311039085 + seed_shift)
+    raise ValueError(name)
+
+
+# ---------------------------------------------------------------------------------------
+# Algorithmic bytes per launch of each kernel: the traffic the method cannot avoid in this
+# layout -- every parcel's own state read and written once, every occupied cell's state
+# once, z_bar live contact slots per parcel -- not counting re-reads of neighbours.
+# ---------------------------------------------------------------------------------------
+def algorithmic_bytes(kernel: str, n: int, ncells: int, zbar: float, rsize: int, passes: int) -> float:
+    R = rsize
+    slot = 4 + 3 * R                       # partner id + tangential displacement
+    state_r = 24 + 12 * R + 2 * R + 32 + 8  # x,y,z; v,w,a,al; T,d; masses; meta, orig
+    if kernel == "k_key":
+        return n * (24 + 6 * R + 4 + 8)
+    if kernel == "radix_sort":
+        return n * passes * (4 + 8 + 8)
+    if kernel == "k_gather":
+        per = 4 + state_r + 1 + zbar * slot                      # read
+        per += state_r + R + 16 + 4 + 1 + zbar * slot             # write (+ mass, xf, gcell)
+        return n * per
+    if kernel == "k_contacts":
+        per = 24 + 16 + R + R + 6 * R + 4 + 4 + 1 + zbar * slot  # read own record + old slots
+        per += 6 * R + 1 + zbar * slot                            # write force, torque, slots
+        return n * per
+    if kernel == "k_gas_particle":
+        per = 4 + 4 + R + 3 * R + R + 32 + R + 6 * R + 3 * R       # read
+        per += 12 * R + R + 32 + 14 * R                           # write state + sources
+        return n * per + ncells * 14 * R                           # cell properties once
+    if kernel == "k_cells":
+        return ncells * (1 + 4 + 8 + 5 * 8 + 5 * 8 + 14 * R) + n * 14 * R
+    return 0.0
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50",
+                 "-i", str(self.device)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(bed, steps: int, sample: int):
+    """The oracle as it stands on this host's cores, on a bounded sample of the workload."""
+    import oracle
+    n = min(sample, bed.n)
+    sub = bed.subset(np.arange(n)) if n < bed.n else bed   # parcel indices are shuffled
+    o = oracle.Oracle(sub)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return {"value": n * steps / dt, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"{n} of {bed.n} parcels of the same bed (random subset), {steps} step(s), FP64"}
+
+
+def reference_arm(args):
+    """--impl reference: the oracle (FP64 CPU) on the host cores, same workload and metric."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    bed = make_workload(args.workload)
+    import oracle
+    n = min(args.cpu_sample, bed.n)
+    sub = bed.subset(np.arange(n)) if n < bed.n else bed
+    o = oracle.Oracle(sub)
+    ksteps = max(1, min(args.steps, 20))
+    wsteps = max(0, min(args.warmup, 2))
+    o.step(wsteps)
+    t0 = time.perf_counter()
+    o.step(ksteps)
+    dt = time.perf_counter() - t0
+    value = n * ksteps / dt
+    sample = f"{n} of {bed.n} parcels (random subset), {ksteps} timed steps after {wsteps} warm-up, FP64"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": ksteps, "warmup": wsteps, "ms_per_step": 1e3 * dt / ksteps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}", "parcels_sampled": n, "precision": "fp64 oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2311_03908_gb300 import binding
+    stream = torch.cuda.current_stream()
+    bed = make_workload(args.workload, rank)
+    ctx = binding.Context(bed, precision=args.precision, stream=stream.cuda_stream)
+    n = bed.n
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up: W untimed steps (this also captures the two one-step graphs)
+    for _ in range(args.warmup):
+        ctx.dem_step_graph(1)
+    ctx.dem_sync()
+    launches_per_step = None
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    time.sleep(0.2)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    total_launches = 0
+    for _ in range(args.steps):
+        ctx.dem_step_graph(1)
+        total_launches += ctx.dem_last_launch_count()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ck = clocks.stop()
+    ctx.dem_sync()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = n * world * args.steps / (ms_max * 1e-3)
+
+    # per-kernel device times (CUDA events on the library's stream) over K plain steps
+    ctx.dem_profile(True)
+    ksteps = args.steps
+    ctx.dem_step(ksteps)
+    times = ctx.dem_kernel_times()
+    ctx.dem_profile(False)
+    cnt, _, _ = ctx.dem_get_contacts()
+    zbar = float(cnt.mean())
+    ncells = ctx.ncells
+    rsize = 8 if args.precision == "fp64" else 4
+    key_bits = max(1, math.ceil(math.log2(max(2, sum(c.nx * c.ny * c.nz for c in bed.beds)))))
+    passes = (key_bits + 7) // 8
+    peak, peak_kind = measured_peaks()
+    kernels = {}
+    for name, (nl, tot) in times.items():
+        avg = tot / max(nl, 1)
+        b = algorithmic_bytes(name, n, ncells, zbar, rsize, passes)
+        kernels[name] = {"launches": nl, "avg_ms": avg, "alg_bytes": b,
+                         "gbs": (b / (avg * 1e-3) / 1e9) if avg > 0 and b > 0 else None}
+    dom = max(kernels, key=lambda k: kernels[k]["avg_ms"]) if kernels else None
+    roof = None
+    if dom:
+        ach = kernels[dom]["gbs"] or 0.0
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "peak_kind": f"{peak_kind} HBM copy bandwidth", "traffic": None}
+    step_alg = sum(v["alg_bytes"] for v in kernels.values())
+    step_ms = ms_max / args.steps
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if args.precision != "fp64" else "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload} ({bed.n} parcels, {ncells} gas cells, {len(bed.beds)} bed(s))",
+                       "precision": args.precision, "stepping": "CUDA graph of one step, replayed",
+                       "l2": "inputs larger than L2 (parcel state and history ~ 1 GB)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof, "gpu_launches": total_launches, "clocks": ck,
+            "kernels": kernels, "step_alg_bytes": step_alg,
+            "step_alg_gbs": step_alg / (step_ms * 1e-3) / 1e9, "zbar_contacts": zbar}
+
+    # the all-FP64 form of the same workload (split vs FP64 comparison)
+    if not args.no_fp64_form and args.precision != "fp64":
+        ctx64 = binding.Context(bed, precision="fp64", stream=stream.cuda_stream)
+        k64 = max(3, args.steps // 10)
+        for _ in range(3):
+            ctx64.dem_step_graph(1)
+        ctx64.dem_sync()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(k64):
+            ctx64.dem_step_graph(1)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a0.elapsed_time(a1)
+        line["fp64_form"] = {"value": n * k64 / (ms64 * 1e-3), "unit": UNIT, "steps": k64,
+                             "ms_per_step": ms64 / k64}
+        ctx64.close()
+
+    # end to end through the C ABI with host buffers: every step the gas field comes from
+    # pinned host memory (the coupling input) and the bed-mean reduction degree goes back
+    if not args.no_e2e:
+        nc = ctx.ncells
+        gas = ctx.dem_get_gas()
+        Y = torch.from_numpy(np.ascontiguousarray(gas[:, 1:4])).pin_memory()
+        T = torch.from_numpy(np.ascontiguousarray(gas[:, 4])).pin_memory()
+        ke = max(3, min(args.steps, 200))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            ctx.dem_set_gas(Y, T)
+            ctx.dem_step_graph(1)
+            ctx.dem_reduction_degree()
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        tt = torch.tensor([te], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te = float(tt.item())
+        line["e2e"] = {"value": n * world * ke / te, "unit": UNIT, "steps": ke,
+                       "h2d_bytes_per_step": int(nc * 4 * 8), "d2h_bytes_per_step": int(len(bed.beds) * 2 * 8),
+                       "api": "dem_set_gas (pinned host) + dem_step_graph + dem_reduction_degree"}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(bed, 1, args.cpu_sample)
+    mean, _ = ctx.dem_reduction_degree()
+    line["f_ov_mean"] = float(mean.mean())
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,232 @@
+/*
+ * dem.h -- C ABI of the GB300 (sm_103a) particle-side step of the coarse-grained
+ * CFD-DEM-IBM method for hydrogen reduction of iron ore of Lan et al. (arXiv 2311.03908).
+ *
+ * One call of dem_step advances every coarse-grained parcel of every bed by one DEM time
+ * step, entirely on the GPU:
+ *   1. half kick and drift (velocity Verlet of eq (3-3) and eq (3-6));
+ *   2. binning by an LSD radix sort of the parcels on their cell key;
+ *   3. gather of the parcel state into the sorted order, occupied-cell ranges;
+ *   4. soft-sphere contacts with the neighbouring parcels (linear spring-dashpot normal
+ *      force, tangential spring with a contact-history table and a Coulomb cap) and with
+ *      the analytic reactor wall (cylinder, flat bottom or cone, perforated plate, lid);
+ *   5. gas-particle terms of the containing gas cell: Gidaspow-Ganser drag (eqs (3-5),
+ *      (3-5-2)..(3-5-5)), Gunn convection (eqs (3-10)..(3-13)), the multi-path unreacted
+ *      shrinking core model (Sec. 2: eqs (2-1)..(2-36)) with the coarse-graining k^3
+ *      scaling (eqs (3-41), (3-49), (3-50), (3-52));
+ *   6. second half kick, particle temperature (eqs (3-8), (3-9)) and, at coupling steps
+ *      (every n = coupling_interval steps, Sec. 4), the layer masses (eq (3-4));
+ *   7. deposition of the cell sources by a segmented reduction over the sorted parcels
+ *      (eqs (3-25), (3-27a), (3-38), (3-39), (4-4), (4-5), (4-10), (4-11));
+ *   8. a simple explicit update of the prescribed gas field (volume fraction, species,
+ *      temperature; semi-implicit in the convective coefficient as in eq (4-6)).
+ *
+ * Conventions (every entry point):
+ *   - returns int status: DEM_OK (0) or a negative DEM_E* code; never aborts or exits;
+ *   - host pointers are read during the call only (the library copies what it keeps);
+ *     device pointers (when a struct says on_device = 1) must stay valid for the call;
+ *   - all work is enqueued on the stream given to dem_init; a fault detected on the device
+ *     (contact-table overflow, non-finite state, a parcel outside its grid) is sticky: it
+ *     is returned by the next call that observes it (dem_sync always observes it);
+ *   - units are SI; arrays of parcels are indexed in input order (the "parcel index").
+ */
+#ifndef DEM_H
+#define DEM_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  DEM_OK = 0,
+  DEM_EINVAL = -1,      /* bad argument (sizes, ranges, geometry, stability) */
+  DEM_ENOMEM = -2,      /* device or pinned allocation failed */
+  DEM_ECUDA = -3,       /* a CUDA runtime call failed */
+  DEM_ECAPACITY = -4,   /* a parcel had more contacts than DEM_MAX_CONTACTS */
+  DEM_ENONFINITE = -5,  /* a parcel state became NaN or Inf */
+  DEM_ETIMEOUT = -6,    /* a bounded device wait gave up */
+  DEM_ESTATE = -7,      /* call not valid in the context's state */
+  DEM_EDOMAIN = -8      /* a parcel centre left its bed's gas grid (clamped) */
+};
+
+enum { DEM_PREC_FP64 = 0, DEM_PREC_SPLIT = 1, DEM_PREC_SPLIT_KAHAN = 2 };
+
+/* physics switches (bit mask in dem_bed_config.flags); 0 = the full method */
+enum {
+  DEM_NO_GRAVITY = 1, DEM_NO_DRAG = 2, DEM_NO_HEAT = 4, DEM_NO_KINETICS = 8,
+  DEM_NO_GAS_UPDATE = 16, DEM_NO_FILM = 32, DEM_NO_LAYER = 64, DEM_NO_RXN_HEAT = 128,
+  DEM_NO_CONTACTS = 256
+};
+
+enum { DEM_WALL_FLAT = 0, DEM_WALL_CONE = 1 };
+enum { DEM_ORE_HEMATITE = 0, DEM_ORE_MAGNETITE = 1 };
+
+#define DEM_MAX_CONTACTS 24   /* contact-history slots per parcel (walls included) */
+#define DEM_MAX_BEDS 1024
+
+/*
+ * One bed (Table 3 of the paper lists the physical parameters; the benchmark beds fix the
+ * rest). Geometry: a cylinder of diameter bed_D and height bed_H standing on z = 0, the
+ * gas grid nx*ny*nz covering [-D/2, D/2]^2 x [0, H]. wall_kind DEM_WALL_CONE adds a cone
+ * of half angle cone_half_angle (rad) whose rim meets the cylinder at z = cone_height,
+ * and a zero-thickness distributor plate at z = plate_z with round holes of diameter
+ * hole_d on a square lattice of pitch hole_pitch centred on the axis.
+ * Gas cells that lie wholly outside the fluid region are marked solid (immersed
+ * boundary): they take no sources and keep their state.
+ */
+typedef struct {
+  double bed_D, bed_H;
+  int32_t wall_kind;
+  double cone_half_angle, cone_height, plate_z, hole_d, hole_pitch;
+  int32_t nx, ny, nz;
+  double dt;              /* DEM time step, s */
+  double kn;              /* normal spring stiffness, N/m */
+  double kt_over_kn;      /* tangential / normal stiffness; tangential damping scales by its sqrt */
+  double restitution;     /* restitution coefficient of a parcel-parcel or parcel-wall contact */
+  double mu_s;            /* sliding friction coefficient (Coulomb cap) */
+  double mu_r;            /* rolling friction length, m (0 = off) */
+  double cg_ratio;        /* coarse-graining ratio k = d_CGP / d_p (Sec. 3.3) */
+  int32_t coupling_interval;  /* n = dt_CFD / dt_DEM (Sec. 4): masses, sources, gas every n steps */
+  double U_in, T_in, p0;  /* superficial inlet velocity (m/s), inlet temperature (K), pressure (Pa) */
+  double Y_in[3];         /* inlet mass fractions of H2, H2O, N2 */
+  double k0[3], Ea[3];    /* pre-exponential factor (m/s) and activation energy (J/mol) of R1..R3 */
+  double tortuosity;      /* tau of eq (2-30) (not printed in the paper) */
+  double sphericity[2];   /* psi of eqs (3-5-2)..(3-5-5), per ore type */
+  double xi0[2];          /* initial porosity per ore type (Table 3) */
+  double pore_d_cm[2];    /* pore diameter per ore type, cm (Table 3) */
+  double rho_true[4];     /* true densities of Fe2O3, Fe3O4, FeO, Fe (Table 3) */
+  double dpdz;            /* prescribed gas pressure gradient along z, Pa/m (force -V dp/dz) */
+  double eps_min;         /* lower clamp of the gas volume fraction */
+  uint32_t flags;         /* DEM_NO_* switches */
+} dem_bed_config;
+
+/*
+ * Parcels (coarse-grained particles). x, y, z, vx, vy, vz, d_real, T and m0[4] are n doubles
+ * each; ore_type and bed are n int32 (bed indexes the dem_bed_config array). d_real is the
+ * real particle diameter d_p (the parcel diameter is cg_ratio * d_real); m0 are the parcel
+ * masses of Fe2O3, Fe3O4, FeO and Fe (kg). id (nullable) is carried for the caller only.
+ * on_device = 1: every pointer is a device pointer; 0: host pointers.
+ */
+typedef struct {
+  int32_t n;
+  int32_t on_device;
+  const double *x, *y, *z, *vx, *vy, *vz, *d_real, *T;
+  const double *m0[4];
+  const int32_t *ore_type, *bed;
+  const int64_t *id;
+} dem_parcels;
+
+/*
+ * Initial gas field (nullable: uniform inlet state). Y is (total cells) x 3 mass fractions
+ * (H2, H2O, N2) and T the temperatures, cells ordered bed by bed, then x fastest, then y,
+ * then z.
+ */
+typedef struct {
+  int32_t on_device;
+  const double *Y, *T;
+} dem_gas;
+
+typedef struct dem_ctx dem_ctx;
+
+/* Create a context: validates the inputs, allocates one device arena, copies the parcels
+ * and bins them once. cuda_stream is a cudaStream_t (NULL = legacy default stream).
+ * precision: DEM_PREC_FP64 (everything FP64), DEM_PREC_SPLIT (FP32 forces, drag, kinetics
+ * and velocities; FP64 positions, layer masses and cell-source sums) or
+ * DEM_PREC_SPLIT_KAHAN (as SPLIT but masses and cell sums in Kahan-compensated FP32).
+ * Errors: DEM_EINVAL for n <= 0, n_beds outside [1, DEM_MAX_BEDS], a bad grid, a parcel
+ * outside its bed, coupling_interval < 1, k*d_p larger than a gas cell, or a time step at
+ * or above the stability limit omega_0 dt >= 2 of the stiffest pair; DEM_ENOMEM/DEM_ECUDA. */
+int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p,
+             const dem_gas *g, int32_t precision, void *cuda_stream, dem_ctx **out);
+
+/* Advance n_steps steps (asynchronous on the context stream). */
+int dem_step(dem_ctx *c, int32_t n_steps);
+
+/* Advance n_steps steps by replaying a CUDA graph of those steps (captured on first use
+ * for this n_steps and kept; one graph launch per call). */
+int dem_step_graph(dem_ctx *c, int32_t n_steps);
+
+/* Wait for the context stream and return any sticky device error. */
+int dem_sync(dem_ctx *c);
+
+/* Overall reduction degree (eqs (2-15)..(2-19)): mean_per_bed (host, n_beds doubles) gets
+ * the arithmetic mean of the parcels' f_ov in each bed; oxygen_per_bed (host, nullable)
+ * the bed's removed-oxygen fraction; per_parcel (nullable, device, n doubles) each
+ * parcel's f_ov in parcel-index order. Synchronous. */
+int dem_reduction_degree(dem_ctx *c, double *mean_per_bed, double *oxygen_per_bed,
+                         double *per_parcel);
+
+/* Adjoint of the frozen-position drag-heat-reaction sub-step: from the current state,
+ * J = mean over all parcels of f_ov after n_steps sub-steps minus f_ov now, with positions,
+ * cells and the gas field held fixed and (v, T_p, m_z) integrated by explicit Euler with
+ * the bed time step. grad (host, 6 doubles) gets dJ/dk0[0..2] and dJ/dEa[0..2], the
+ * parameters applied to every bed. The forward pass stores a checkpoint every
+ * ckpt_every sub-steps; the reverse pass recomputes each segment and runs the hand-written
+ * adjoint kernel back through it. The context's state is not changed. Synchronous. */
+int dem_adjoint(dem_ctx *c, int32_t n_steps, int32_t ckpt_every, double *J, double *grad);
+
+/* Replace the kinetic parameters of every bed (R1..R3). */
+int dem_set_kinetics(dem_ctx *c, const double k0[3], const double Ea[3]);
+
+/* Per-parcel state in parcel-index order, DEM_NSTATE rows of n doubles (host):
+ * x y z vx vy vz wx wy wz T m_Fe2O3 m_Fe3O4 m_FeO m_Fe ax ay az alx aly alz. Synchronous. */
+enum { DEM_NSTATE = 20 };
+int dem_get_state(dem_ctx *c, double *out_host);
+
+/* Per-gas-cell state, DEM_NGAS doubles per cell (host): eps Y_H2 Y_H2O Y_N2 T solid_mark. */
+enum { DEM_NGAS = 6 };
+int64_t dem_num_cells(dem_ctx *c);
+int dem_get_gas(dem_ctx *c, double *out_host);
+
+/* Cell sources of the last coupling step, DEM_NDEP doubles per cell (host): V_s, S_H2,
+ * S_H2O (kg/s into the gas), K, K v_x, K v_y, K v_z (eq (3-27a)), hA, hA T_p (eqs (4-4),
+ * (4-5)), Q_rm, Q_r (eqs (3-38), (3-49), (3-50)), E Q, E S (eqs (4-10), (4-11)), count.
+ * Recomputed from the per-parcel sources kept from the last step. Synchronous. */
+enum { DEM_NDEP = 14 };
+int dem_get_sources(dem_ctx *c, double *out_host);
+
+/* Contact-history table in parcel-index order (host): count[n]; partner[n*DEM_MAX_CONTACTS]
+ * (parcel index of the partner, or -1-p for wall primitive p: 0 side, 1 bottom or cone,
+ * 2 plate, 3 lid; INT32_MIN in unused slots); xi[n*DEM_MAX_CONTACTS*3] tangential
+ * displacements. Slots are sorted by partner. Synchronous. */
+int dem_get_contacts(dem_ctx *c, int32_t *count, int32_t *partner, double *xi);
+
+/* Per-parcel diagnostics of the last step (enable with dem_set_diagnostics before stepping),
+ * DEM_NDIAG rows of n doubles (host), parcel-index order:
+ * Fc(3) Tc(3) Fd(3) K Qconv Qr Qrm xidot(3) mdot(4) F_film A(3) B(3) Sh Nu Re ncontact cell */
+enum { DEM_NDIAG = 32 };
+int dem_set_diagnostics(dem_ctx *c, int32_t on);
+int dem_get_diag(dem_ctx *c, double *out_host);
+
+/* Pick block sizes of the hot kernels by timing candidates on n_steps steps; the state is
+ * saved before and restored after, so the simulation is unchanged. */
+int dem_autotune(dem_ctx *c, int32_t n_steps);
+
+/* Number of kernels launched by the last dem_step/dem_step_graph call (for accounting). */
+int64_t dem_last_launch_count(dem_ctx *c);
+
+/* Replace the gas field (the coupling input of Sec. 4: cell fields from the gas solver).
+ * g->Y is (total cells) x 3 mass fractions, g->T the temperatures (host or device by
+ * g->on_device); the gas volume fraction is kept; the cells' derived properties are
+ * recomputed. Asynchronous on the context stream (host buffers are copied before return
+ * when they are pageable; pinned buffers are read by the copy engine). */
+int dem_set_gas(dem_ctx *c, const dem_gas *g);
+
+/* Per-kernel timing: while on, every kernel that dem_step launches is bracketed by CUDA
+ * events on the context stream; dem_kernel_times (synchronous) returns, per kernel name,
+ * the number of launches and their total device time since profiling was switched on.
+ * names receives up to max_kernels NUL-terminated names of 32 bytes each. Returns the
+ * number of kernel names (>= 0) or a negative status. */
+int dem_profile(dem_ctx *c, int32_t on);
+int dem_kernel_times(dem_ctx *c, int32_t max_kernels, char *names, int64_t *launches, double *ms_total);
+
+/* Human-readable text of a status code (static storage). */
+const char *dem_strerror(int status);
+
+/* Release everything (safe on NULL and after any error). */
+void dem_destroy(dem_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

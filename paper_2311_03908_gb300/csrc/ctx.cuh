@@ -1,0 +1,94 @@
+// ctx.cuh -- the library's context: one device arena holding every array of the particle
+// path, plus the host-side bookkeeping (which ping-pong buffer is current, cached graphs).
+#pragma once
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "kernels.cuh"
+
+struct dem_ctx {
+  int n = 0, cap = 0, nbeds = 0, prec = DEM_PREC_FP64;
+  long long ncells = 0;
+  unsigned long long nkeys = 0;
+  int key_bits = 1;
+  bool gas_alias = true;            // every bed has s == 1: gas ranges are the DEM ranges
+  cudaStream_t st = nullptr;
+  std::vector<dem::DevBed> hbeds;
+  std::vector<dem_bed_config> cfg;
+  dem::DevBed *dbeds = nullptr;
+  // one device arena
+  char *arena = nullptr;
+  size_t arena_bytes = 0;
+  size_t rsize = 8;                 // sizeof(R)
+  // parcel state, two buffers (cur = current)
+  double *px[2][3] = {};
+  void *pv[2][3] = {}, *pw[2][3] = {}, *pa[2][3] = {}, *pal[2][3] = {}, *pT[2] = {}, *pd[2] = {};
+  double *pm[2][4] = {};
+  int *pmeta[2] = {}, *porig[2] = {};
+  // contact history: [0] current, [1] gather target
+  unsigned char *hcnt[2] = {};
+  int *hid[2] = {};
+  void *hxi[2] = {};
+  // binning
+  unsigned *keys = nullptr, *vals = nullptr, *keys2 = nullptr, *vals2 = nullptr, *rhist = nullptr;
+  unsigned *kres = nullptr, *vres = nullptr;   // where the last sort left its result
+  unsigned *cstart = nullptr, *cend = nullptr, *gstart = nullptr, *gend = nullptr;
+  int *gcell = nullptr;
+  float4 *xf = nullptr;
+  void *mass = nullptr, *F[3] = {}, *Tq[3] = {}, *src = nullptr;
+  // gas: two state buffers (gcur = current), properties, marks
+  double *gas[2] = {};
+  void *gp = nullptr;
+  unsigned char *mark = nullptr;
+  int *cell_bed = nullptr;
+  double *fv = nullptr, *fvbed = nullptr;
+  int *err = nullptr;
+  long long *step_ctr = nullptr;
+  int cur = 0, gcur = 0;
+  // optional buffers (cudaMalloc on first use, outside the arena)
+  double *diag = nullptr, *dep = nullptr, *scratch_out = nullptr;
+  size_t scratch_bytes = 0;
+  bool diag_on = false;
+  // host-side status
+  int *h_err = nullptr;             // pinned
+  cudaEvent_t ev = nullptr;
+  bool pending = false;
+  int sticky = DEM_OK;
+  long long launches = 0;
+  int bs_contacts = 128, bs_gp = 128, bs_gather = 256, bs_cells = 256, bs_key = 256;
+  std::map<std::tuple<int, int, int>, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;
+  std::map<std::tuple<int, int, int>, long long> graph_launches;
+  cudaStream_t gst = nullptr;     // private stream used to capture graphs
+  // per-kernel event timing
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> prof_marks;   // (kernel id, index of its start event)
+  std::vector<std::string> prof_names;
+  std::vector<double> prof_ms;
+  std::vector<long long> prof_n;
+  double *gas_stage = nullptr;
+  // adjoint buffers
+  double *adj = nullptr;
+  size_t adj_bytes = 0;
+};
+
+namespace dem {
+
+template <class R> StepView<R> make_view(dem_ctx *c, bool for_step);
+template <class R> int enqueue_steps(dem_ctx *c, int nsteps);
+template <class R> int enqueue_init(dem_ctx *c);
+template <class R> int enqueue_fov(dem_ctx *c, double *per_parcel_dev);
+template <class R> int enqueue_scatter_state(dem_ctx *c, double *out_dev);
+template <class R> int enqueue_scatter_diag(dem_ctx *c, double *out_dev);
+template <class R> int enqueue_scatter_hist(dem_ctx *c, int *cnt, int *partner, double *xi);
+template <class R> int enqueue_sources(dem_ctx *c);
+template <class R> int run_adjoint(dem_ctx *c, int nsteps, int ckpt, double *J, double *grad);
+template <class R> int enqueue_props(dem_ctx *c);
+
+// event pair around one kernel when profiling is on (returns the start-event slot or -1)
+int prof_begin(dem_ctx *c, const char *name);
+void prof_end(dem_ctx *c, int slot);
+
+}  // namespace dem

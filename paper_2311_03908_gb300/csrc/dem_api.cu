@@ -1,0 +1,807 @@
+// dem_api.cu -- the C ABI declared in include/dem.h: validation, the device arena,
+// initial binning, stepping (plain and CUDA-graph), getters and error handling.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "ctx.cuh"
+#include "radix.cuh"
+
+using dem::DevBed;
+
+namespace dem {
+
+__global__ void k_step_counter(long long *ctr) { *ctr += 1; }
+
+__global__ void k_mark_cells(const DevBed *beds, const int *cell_bed, unsigned char *mark, long long ncells) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncells) return;
+  const DevBed &B = beds[cell_bed[c]];
+  const long long l = c - B.cell_off;
+  const int ix = (int)(l % B.nx), iy = (int)((l / B.nx) % B.ny), iz = (int)(l / ((long long)B.nx * B.ny));
+  const double xc = B.x0 + (ix + 0.5) * B.dx, yc = B.y0 + (iy + 0.5) * B.dy, zc = B.z0 + (iz + 0.5) * B.dz;
+  const double hd = 0.5 * sqrt(B.dx * B.dx + B.dy * B.dy + B.dz * B.dz);
+  const double rho = sqrt(xc * xc + yc * yc);
+  double sd = B.R - rho;
+  if (B.wall == DEM_WALL_CONE) sd = fmin(sd, (zc - B.z_apex) * B.sin_a - rho * B.cos_a);
+  mark[c] = sd < -hd ? 1 : 0;
+}
+
+// Initial parcel state in input order (accelerations start as gravity, spins at rest).
+template <class R>
+__global__ void k_load(int n, const double *const *src /* 8 + 4 arrays */, const int *ore,
+                       const int *bed, const DevBed *beds, double *x, double *y, double *z,
+                       R *vx, R *vy, R *vz, R *wx, R *wy, R *wz, R *ax, R *ay, R *az, R *alx,
+                       R *aly, R *alz, R *T, R *d, double *m0, double *m1, double *m2, double *m3,
+                       int *meta, int *orig) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  x[i] = src[0][i]; y[i] = src[1][i]; z[i] = src[2][i];
+  vx[i] = (R)src[3][i]; vy[i] = (R)src[4][i]; vz[i] = (R)src[5][i];
+  d[i] = (R)src[6][i]; T[i] = (R)src[7][i];
+  m0[i] = src[8][i]; m1[i] = src[9][i]; m2[i] = src[10][i]; m3[i] = src[11][i];
+  wx[i] = wy[i] = wz[i] = (R)0;
+  alx[i] = aly[i] = alz[i] = (R)0;
+  ax[i] = ay[i] = (R)0;
+  const DevBed &B = beds[bed[i]];
+  az[i] = (B.flags & DEM_NO_GRAVITY) ? (R)0 : (R)(-kGrav);
+  meta[i] = (bed[i] << 8) | ore[i];
+  orig[i] = i;
+}
+
+// Gas state from the coupling input, keeping the volume fraction.
+__global__ void k_gas_set(long long nc, const double *Y /* nc*3 */, const double *T, double *G) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  G[GS_Y0 * nc + c] = Y[c * 3 + 0];
+  G[GS_Y1 * nc + c] = Y[c * 3 + 1];
+  G[GS_Y2 * nc + c] = Y[c * 3 + 2];
+  G[GS_T * nc + c] = T[c];
+}
+
+int prof_begin(dem_ctx *c, const char *name) {
+  if (!c->prof_on) return -1;
+  int id = -1;
+  for (size_t k = 0; k < c->prof_names.size(); ++k)
+    if (c->prof_names[k] == name) { id = (int)k; break; }
+  if (id < 0) {
+    c->prof_names.push_back(name);
+    c->prof_ms.push_back(0.0);
+    c->prof_n.push_back(0);
+    id = (int)c->prof_names.size() - 1;
+  }
+  const int slot = (int)(2 * c->prof_marks.size());
+  while ((int)c->ev_pool.size() < slot + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    c->ev_pool.push_back(e);
+  }
+  cudaEventRecord(c->ev_pool[slot], c->st);
+  c->prof_marks.push_back({id, slot});
+  return slot;
+}
+
+void prof_end(dem_ctx *c, int slot) {
+  if (slot < 0) return;
+  cudaEventRecord(c->ev_pool[slot + 1], c->st);
+}
+
+__global__ void k_gas_load(long long nc, const double *Y /* nc*3 */, const double *T, double *G) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  G[GS_EPS * nc + c] = 1.0;
+  G[GS_Y0 * nc + c] = Y[c * 3 + 0];
+  G[GS_Y1 * nc + c] = Y[c * 3 + 1];
+  G[GS_Y2 * nc + c] = Y[c * 3 + 2];
+  G[GS_T * nc + c] = T[c];
+}
+
+}  // namespace dem
+
+namespace {
+
+using namespace dem;
+
+constexpr double kMzH[4] = {159.69e-3, 231.533e-3, 71.844e-3, 55.845e-3};
+
+#define CK(call)                                           \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) { return fail(c, e_); }         \
+  } while (0)
+
+int fail(dem_ctx *c, cudaError_t e) {
+  (void)c;
+  if (e == cudaErrorMemoryAllocation) return DEM_ENOMEM;
+  return DEM_ECUDA;
+}
+
+int status_from_bits(int bits) {
+  if (bits & ERR_NONFINITE) return DEM_ENONFINITE;
+  if (bits & ERR_CAPACITY) return DEM_ECAPACITY;
+  if (bits & ERR_TIMEOUT) return DEM_ETIMEOUT;
+  if (bits & ERR_DOMAIN) return DEM_EDOMAIN;
+  return DEM_OK;
+}
+
+// observe a finished step's error word; block = wait for it
+int poll(dem_ctx *c, bool block) {
+  if (c->sticky != DEM_OK) return c->sticky;
+  if (!c->pending) return DEM_OK;
+  if (block) {
+    if (cudaEventSynchronize(c->ev) != cudaSuccess) { c->sticky = DEM_ECUDA; return c->sticky; }
+  } else {
+    cudaError_t q = cudaEventQuery(c->ev);
+    if (q == cudaErrorNotReady) return DEM_OK;
+    if (q != cudaSuccess) { c->sticky = DEM_ECUDA; return c->sticky; }
+  }
+  c->pending = false;
+  c->sticky = status_from_bits(*c->h_err);
+  return c->sticky;
+}
+
+int mark_pending(dem_ctx *c) {
+  CK(cudaMemcpyAsync(c->h_err, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaEventRecord(c->ev, c->st));
+  c->pending = true;
+  return DEM_OK;
+}
+
+int sync_all(dem_ctx *c) {
+  int s = poll(c, true);
+  if (s != DEM_OK) return s;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return DEM_ECUDA;
+  return DEM_OK;
+}
+
+// Layer porosities (Sec. 2.3): the core's effective density from the initial porosity, each
+// product layer's effective density by the equivalent-mass ratios q of eq (2-36).
+void layer_porosity_host(const dem_bed_config &b, int ore, double out[3]) {
+  const double q_mh = 2.0 * kMzH[1] / (3.0 * kMzH[0]);
+  const double q_wm = 3.0 * kMzH[2] / kMzH[1];
+  const double q_few = kMzH[3] / kMzH[2];
+  double rm = ore == 0 ? (1.0 - b.xi0[0]) * b.rho_true[0] * q_mh : (1.0 - b.xi0[1]) * b.rho_true[1];
+  double rw = rm * q_wm, rfe = rw * q_few;
+  out[0] = 1.0 - rm / b.rho_true[1];
+  out[1] = 1.0 - rw / b.rho_true[2];
+  out[2] = 1.0 - rfe / b.rho_true[3];
+}
+
+double fuller_const(double Mi, double Mj, double Vi, double Vj) {
+  const double s = std::cbrt(Vi) + std::cbrt(Vj);
+  return std::sqrt(1.0 / Mi + 1.0 / Mj) / (s * s);
+}
+
+int validate_bed(const dem_bed_config &b) {
+  if (!(b.bed_D > 0 && b.bed_H > 0 && b.nx >= 1 && b.ny >= 1 && b.nz >= 1)) return DEM_EINVAL;
+  if ((long long)b.nx * b.ny * b.nz > (1LL << 30)) return DEM_EINVAL;
+  if (!(b.dt > 0 && b.kn > 0 && b.kt_over_kn > 0 && b.restitution > 0 && b.restitution <= 1)) return DEM_EINVAL;
+  if (!(b.mu_s >= 0 && b.mu_r >= 0 && b.cg_ratio >= 1 && b.coupling_interval >= 1)) return DEM_EINVAL;
+  if (!(b.T_in > 0 && b.p0 > 0 && b.U_in >= 0 && b.tortuosity > 0 && b.eps_min > 0 && b.eps_min < 1)) return DEM_EINVAL;
+  double ys = b.Y_in[0] + b.Y_in[1] + b.Y_in[2];
+  if (!(std::fabs(ys - 1.0) < 1e-9) || b.Y_in[0] < 0 || b.Y_in[1] < 0 || b.Y_in[2] < 0) return DEM_EINVAL;
+  for (int o = 0; o < 2; ++o)
+    if (!(b.sphericity[o] > 0 && b.sphericity[o] <= 1 && b.xi0[o] >= 0 && b.xi0[o] < 1 && b.pore_d_cm[o] > 0)) return DEM_EINVAL;
+  for (int z = 0; z < 4; ++z) if (!(b.rho_true[z] > 0)) return DEM_EINVAL;
+  for (int r = 0; r < 3; ++r) if (!(b.k0[r] >= 0 && b.Ea[r] >= 0)) return DEM_EINVAL;
+  if (b.wall_kind != DEM_WALL_FLAT && b.wall_kind != DEM_WALL_CONE) return DEM_EINVAL;
+  if (b.wall_kind == DEM_WALL_CONE &&
+      !(b.cone_half_angle > 0 && b.cone_half_angle < 1.5707963 && b.cone_height > 0 && b.hole_pitch > 0 &&
+        b.hole_d > 0 && b.hole_d < b.hole_pitch && b.plate_z > 0 && b.plate_z < b.bed_H))
+    return DEM_EINVAL;
+  return DEM_OK;
+}
+
+DevBed derive_bed(const dem_bed_config &b) {
+  DevBed B;
+  std::memset(&B, 0, sizeof B);
+  B.nx = b.nx; B.ny = b.ny; B.nz = b.nz;
+  B.x0 = -0.5 * b.bed_D; B.y0 = -0.5 * b.bed_D; B.z0 = 0.0;
+  B.dx = b.bed_D / b.nx; B.dy = b.bed_D / b.ny; B.dz = b.bed_H / b.nz;
+  B.inv_dx = 1.0 / B.dx; B.inv_dy = 1.0 / B.dy; B.inv_dz = 1.0 / B.dz;
+  B.vcell = B.dx * B.dy * B.dz;
+  B.s = 1;
+  B.pf_margin = (float)(16.0 * std::max(b.bed_D, b.bed_H) * 5.96e-8);
+  B.R = 0.5 * b.bed_D; B.H = b.bed_H; B.wall = b.wall_kind;
+  B.cos_a = std::cos(b.cone_half_angle); B.sin_a = std::sin(b.cone_half_angle);
+  B.z_apex = b.wall_kind == DEM_WALL_CONE ? b.cone_height - B.R / std::tan(b.cone_half_angle) : 0.0;
+  B.plate_z = b.plate_z; B.pitch = b.hole_pitch > 0 ? b.hole_pitch : 1.0; B.r_hole = 0.5 * b.hole_d;
+  B.dt = b.dt; B.kn = b.kn; B.kt = b.kt_over_kn * b.kn;
+  const double le = std::log(b.restitution);
+  B.eta_coef = -2.0 * le / std::sqrt(kPI * kPI + le * le);
+  B.eta_t_ratio = std::sqrt(b.kt_over_kn);
+  B.mu_s = b.mu_s; B.mu_r = b.mu_r;
+  B.k = b.cg_ratio; B.k3 = b.cg_ratio * b.cg_ratio * b.cg_ratio;
+  B.ncouple = b.coupling_interval;
+  B.U_in = b.U_in; B.T_in = b.T_in; B.p0 = b.p0;
+  for (int j = 0; j < 3; ++j) B.Y_in[j] = b.Y_in[j];
+  B.fuller12 = fuller_const(2.016, 18.015, 7.07, 12.7);
+  B.fuller13 = fuller_const(2.016, 28.014, 7.07, 17.9);
+  for (int r = 0; r < 3; ++r) { B.k0[r] = b.k0[r]; B.Ea[r] = b.Ea[r]; }
+  B.tau = b.tortuosity;
+  for (int o = 0; o < 2; ++o) {
+    const double psi = b.sphericity[o];
+    B.psi[o] = psi;
+    B.K1b[o] = 1.0 / (1.0 / 3.0 + (2.0 / 3.0) / std::sqrt(psi));
+    B.K2[o] = std::pow(10.0, 1.8148 * std::pow(-std::log10(psi), 0.5743));
+    layer_porosity_host(b, o, B.xi[o]);
+    B.pore_cm[o] = b.pore_d_cm[o];
+  }
+  B.dpdz = b.dpdz; B.eps_min = b.eps_min; B.bedD = b.bed_D; B.flags = b.flags;
+  return B;
+}
+
+struct Bump {
+  char *base = nullptr;
+  size_t off = 0;
+  template <class T> T *take(size_t count, size_t elem = sizeof(T)) {
+    off = (off + 255) & ~(size_t)255;
+    T *p = base ? (T *)(base + off) : nullptr;
+    off += count * elem;
+    return p;
+  }
+};
+
+// Lay out (or measure, when base is null) every arena buffer.
+void layout(dem_ctx *c, Bump &m) {
+  const size_t N = (size_t)c->cap, R = c->rsize, C = (size_t)c->ncells;
+  for (int k = 0; k < 2; ++k) {
+    for (int q = 0; q < 3; ++q) c->px[k][q] = m.take<double>(N);
+    for (int q = 0; q < 3; ++q) {
+      c->pv[k][q] = m.take<char>(N, R); c->pw[k][q] = m.take<char>(N, R);
+      c->pa[k][q] = m.take<char>(N, R); c->pal[k][q] = m.take<char>(N, R);
+    }
+    c->pT[k] = m.take<char>(N, R);
+    c->pd[k] = m.take<char>(N, R);
+    for (int q = 0; q < 4; ++q) c->pm[k][q] = m.take<double>(N);
+    c->pmeta[k] = m.take<int>(N);
+    c->porig[k] = m.take<int>(N);
+    c->hcnt[k] = m.take<unsigned char>(N);
+    c->hid[k] = m.take<int>(N * KMAX);
+    c->hxi[k] = m.take<char>(N * KMAX * 3, R);
+  }
+  c->keys = m.take<unsigned>(N); c->vals = m.take<unsigned>(N);
+  c->keys2 = m.take<unsigned>(N); c->vals2 = m.take<unsigned>(N);
+  c->rhist = m.take<unsigned>(radix_hist_words((int)N));
+  c->cstart = m.take<unsigned>(c->nkeys); c->cend = m.take<unsigned>(c->nkeys);
+  if (!c->gas_alias) { c->gstart = m.take<unsigned>(C); c->gend = m.take<unsigned>(C); }
+  c->gcell = m.take<int>(N);
+  c->xf = m.take<float4>(N);
+  c->mass = m.take<char>(N, R);
+  for (int q = 0; q < 3; ++q) { c->F[q] = m.take<char>(N, R); c->Tq[q] = m.take<char>(N, R); }
+  c->src = m.take<char>(N * SR_N, R);
+  c->gas[0] = m.take<double>(C * GS_N);
+  c->gas[1] = m.take<double>(C * GS_N);
+  c->gp = m.take<char>(C * GP_N, R);
+  c->mark = m.take<unsigned char>(C);
+  c->cell_bed = m.take<int>(C);
+  c->fv = m.take<double>(N * 3);
+  c->fvbed = m.take<double>((size_t)c->nbeds * 4);
+  c->err = m.take<int>(1);
+  c->step_ctr = m.take<long long>(1);
+  c->dbeds = m.take<DevBed>(c->nbeds);
+}
+
+template <class R> int dispatch_steps(dem_ctx *c, int n) { return enqueue_steps<R>(c, n); }
+
+int enqueue_steps_any(dem_ctx *c, int n) {
+  return c->prec == DEM_PREC_FP64 ? enqueue_steps<double>(c, n) : enqueue_steps<float>(c, n);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *dem_strerror(int s) {
+  switch (s) {
+    case DEM_OK: return "ok";
+    case DEM_EINVAL: return "invalid argument";
+    case DEM_ENOMEM: return "out of memory";
+    case DEM_ECUDA: return "CUDA runtime error";
+    case DEM_ECAPACITY: return "contact-history capacity exceeded";
+    case DEM_ENONFINITE: return "non-finite parcel state";
+    case DEM_ETIMEOUT: return "bounded device wait timed out";
+    case DEM_ESTATE: return "call not valid in this state";
+    case DEM_EDOMAIN: return "parcel outside its gas grid";
+    default: return "unknown status";
+  }
+}
+
+void dem_destroy(dem_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->st);
+  if (c->gst) cudaStreamDestroy(c->gst);
+  for (auto &kv : c->graphs) {
+    if (kv.second.second) cudaGraphExecDestroy(kv.second.second);
+    if (kv.second.first) cudaGraphDestroy(kv.second.first);
+  }
+  if (c->arena) cudaFree(c->arena);
+  if (c->diag) cudaFree(c->diag);
+  if (c->dep) cudaFree(c->dep);
+  if (c->scratch_out) cudaFree(c->scratch_out);
+  if (c->adj) cudaFree(c->adj);
+  if (c->gas_stage) cudaFree(c->gas_stage);
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  if (c->h_err) cudaFreeHost(c->h_err);
+  if (c->ev) cudaEventDestroy(c->ev);
+  delete c;
+}
+
+int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, const dem_gas *g,
+             int32_t precision, void *cuda_stream, dem_ctx **out) {
+  if (!out) return DEM_EINVAL;
+  *out = nullptr;
+  if (!beds || !p || n_beds < 1 || n_beds > DEM_MAX_BEDS || p->n <= 0) return DEM_EINVAL;
+  if (precision != DEM_PREC_FP64 && precision != DEM_PREC_SPLIT && precision != DEM_PREC_SPLIT_KAHAN) return DEM_EINVAL;
+  if (!p->x || !p->y || !p->z || !p->vx || !p->vy || !p->vz || !p->d_real || !p->T || !p->ore_type || !p->bed)
+    return DEM_EINVAL;
+  for (int q = 0; q < 4; ++q) if (!p->m0[q]) return DEM_EINVAL;
+  for (int b = 0; b < n_beds; ++b) {
+    int s = validate_bed(beds[b]);
+    if (s != DEM_OK) return s;
+  }
+  const int n = p->n;
+  // stage the parcel arrays on the host for validation
+  std::vector<double> h[12];
+  std::vector<int> hore(n), hbed(n);
+  const double *srcs[12] = {p->x, p->y, p->z, p->vx, p->vy, p->vz, p->d_real, p->T, p->m0[0], p->m0[1], p->m0[2], p->m0[3]};
+  for (int k = 0; k < 12; ++k) {
+    h[k].resize(n);
+    if (p->on_device) {
+      if (cudaMemcpy(h[k].data(), srcs[k], sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess) return DEM_ECUDA;
+    } else {
+      std::memcpy(h[k].data(), srcs[k], sizeof(double) * n);
+    }
+  }
+  if (p->on_device) {
+    if (cudaMemcpy(hore.data(), p->ore_type, sizeof(int) * n, cudaMemcpyDeviceToHost) != cudaSuccess) return DEM_ECUDA;
+    if (cudaMemcpy(hbed.data(), p->bed, sizeof(int) * n, cudaMemcpyDeviceToHost) != cudaSuccess) return DEM_ECUDA;
+  } else {
+    std::memcpy(hore.data(), p->ore_type, sizeof(int) * n);
+    std::memcpy(hbed.data(), p->bed, sizeof(int) * n);
+  }
+  std::vector<double> dmax(n_beds, 0.0), mmin(n_beds, 1e300);
+  std::vector<long long> nb(n_beds, 0);
+  for (int i = 0; i < n; ++i) {
+    const int b = hbed[i];
+    if (b < 0 || b >= n_beds || (hore[i] != 0 && hore[i] != 1)) return DEM_EINVAL;
+    const dem_bed_config &B = beds[b];
+    for (int k = 0; k < 12; ++k) if (!std::isfinite(h[k][i])) return DEM_EINVAL;
+    const double d = h[6][i];
+    if (!(d > 0) || !(h[7][i] > 0)) return DEM_EINVAL;
+    double m = 0.0;
+    for (int q = 0; q < 4; ++q) { if (h[8 + q][i] < 0) return DEM_EINVAL; m += h[8 + q][i]; }
+    if (!(m > 0)) return DEM_EINVAL;
+    const double r = 0.5 * B.cg_ratio * d;
+    const double rho = std::sqrt(h[0][i] * h[0][i] + h[1][i] * h[1][i]);
+    if (!(rho <= 0.5 * B.bed_D && h[2][i] >= 0.0 && h[2][i] <= B.bed_H)) return DEM_EINVAL;
+    (void)r;
+    dmax[b] = std::max(dmax[b], B.cg_ratio * d);
+    mmin[b] = std::min(mmin[b], m);
+    nb[b]++;
+  }
+  dem_ctx *c = new dem_ctx();
+  c->n = n;
+  c->cap = n;
+  c->nbeds = n_beds;
+  c->prec = precision;
+  c->rsize = precision == DEM_PREC_FP64 ? sizeof(double) : sizeof(float);
+  c->st = (cudaStream_t)cuda_stream;
+  c->cfg.assign(beds, beds + n_beds);
+  // per-bed constants, grid offsets and the DEM sub-division
+  unsigned long long koff = 0;
+  long long coff = 0;
+  for (int b = 0; b < n_beds; ++b) {
+    DevBed B = derive_bed(beds[b]);
+    const double edge = std::min(B.dx, std::min(B.dy, B.dz));
+    if (nb[b] > 0 && dmax[b] > edge) { delete c; return DEM_EINVAL; }
+    // stability of the stiffest contact: omega_0 dt < 2 with m* = m_min / 2
+    if (nb[b] > 0 && std::sqrt(beds[b].kn / (0.5 * mmin[b])) * beds[b].dt >= 2.0) { delete c; return DEM_EINVAL; }
+    const long long ng = (long long)B.nx * B.ny * B.nz;
+    int s = nb[b] > 0 ? std::max(1, (int)std::floor(edge / dmax[b])) : 1;
+    const double budget = std::max((double)ng, 64.0 * (double)nb[b]);
+    while (s > 1 && (double)ng * s * s * s > budget) --s;
+    B.s = s;
+    B.cell_off = coff;
+    B.key_off = (unsigned)koff;
+    koff += (unsigned long long)ng * s * s * s;
+    coff += ng;
+    if (s != 1) c->gas_alias = false;
+    c->hbeds.push_back(B);
+  }
+  if (koff >= (1ULL << 32)) { delete c; return DEM_EINVAL; }
+  c->nkeys = koff;
+  c->ncells = coff;
+  c->key_bits = 1;
+  while ((1ULL << c->key_bits) < koff) ++c->key_bits;
+  // arena
+  Bump meas;
+  layout(c, meas);
+  c->arena_bytes = meas.off + 256;
+  if (cudaMalloc(&c->arena, c->arena_bytes) != cudaSuccess) { dem_destroy(c); return DEM_ENOMEM; }
+  Bump real;
+  real.base = c->arena;
+  layout(c, real);
+  if (cudaMallocHost(&c->h_err, sizeof(int)) != cudaSuccess) { dem_destroy(c); return DEM_ENOMEM; }
+  *c->h_err = 0;
+  if (cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) != cudaSuccess) { dem_destroy(c); return DEM_ECUDA; }
+  int rc = DEM_OK;
+  auto ck = [&](cudaError_t e) { if (e != cudaSuccess && rc == DEM_OK) rc = e == cudaErrorMemoryAllocation ? DEM_ENOMEM : DEM_ECUDA; };
+  ck(cudaMemcpyAsync(c->dbeds, c->hbeds.data(), sizeof(DevBed) * n_beds, cudaMemcpyHostToDevice, c->st));
+  // staging copies of the inputs (freed at the end of init)
+  double *dsrc = nullptr;
+  int *dint = nullptr;
+  const double **dptrs = nullptr;
+  ck(cudaMalloc(&dsrc, sizeof(double) * 12 * (size_t)n));
+  ck(cudaMalloc(&dint, sizeof(int) * 2 * (size_t)n));
+  ck(cudaMalloc(&dptrs, sizeof(double *) * 12));
+  if (rc != DEM_OK) { cudaFree(dsrc); cudaFree(dint); cudaFree(dptrs); dem_destroy(c); return rc; }
+  const double *hp[12];
+  for (int k = 0; k < 12; ++k) {
+    ck(cudaMemcpyAsync(dsrc + (size_t)k * n, h[k].data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->st));
+    hp[k] = dsrc + (size_t)k * n;
+  }
+  ck(cudaMemcpyAsync(dint, hore.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->st));
+  ck(cudaMemcpyAsync(dint + n, hbed.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->st));
+  ck(cudaMemcpyAsync(dptrs, hp, sizeof(hp), cudaMemcpyHostToDevice, c->st));
+  const int bs = 256, gridn = (n + bs - 1) / bs;
+  if (c->prec == DEM_PREC_FP64) {
+    k_load<double><<<gridn, bs, 0, c->st>>>(n, dptrs, dint, dint + n, c->dbeds, c->px[0][0], c->px[0][1], c->px[0][2],
+        (double *)c->pv[0][0], (double *)c->pv[0][1], (double *)c->pv[0][2], (double *)c->pw[0][0], (double *)c->pw[0][1],
+        (double *)c->pw[0][2], (double *)c->pa[0][0], (double *)c->pa[0][1], (double *)c->pa[0][2], (double *)c->pal[0][0],
+        (double *)c->pal[0][1], (double *)c->pal[0][2], (double *)c->pT[0], (double *)c->pd[0], c->pm[0][0], c->pm[0][1],
+        c->pm[0][2], c->pm[0][3], c->pmeta[0], c->porig[0]);
+  } else {
+    k_load<float><<<gridn, bs, 0, c->st>>>(n, dptrs, dint, dint + n, c->dbeds, c->px[0][0], c->px[0][1], c->px[0][2],
+        (float *)c->pv[0][0], (float *)c->pv[0][1], (float *)c->pv[0][2], (float *)c->pw[0][0], (float *)c->pw[0][1],
+        (float *)c->pw[0][2], (float *)c->pa[0][0], (float *)c->pa[0][1], (float *)c->pa[0][2], (float *)c->pal[0][0],
+        (float *)c->pal[0][1], (float *)c->pal[0][2], (float *)c->pT[0], (float *)c->pd[0], c->pm[0][0], c->pm[0][1],
+        c->pm[0][2], c->pm[0][3], c->pmeta[0], c->porig[0]);
+  }
+  ck(cudaMemsetAsync(c->hcnt[0], 0, (size_t)n, c->st));
+  ck(cudaMemsetAsync(c->hcnt[1], 0, (size_t)n, c->st));
+  ck(cudaMemsetAsync(c->err, 0, sizeof(int), c->st));
+  ck(cudaMemsetAsync(c->step_ctr, 0, sizeof(long long), c->st));
+  // gas: cell -> bed, marks, initial state
+  {
+    std::vector<int> cb(c->ncells);
+    for (int b = 0; b < n_beds; ++b) {
+      const long long ng = (long long)c->hbeds[b].nx * c->hbeds[b].ny * c->hbeds[b].nz;
+      std::fill(cb.begin() + c->hbeds[b].cell_off, cb.begin() + c->hbeds[b].cell_off + ng, b);
+    }
+    ck(cudaMemcpyAsync(c->cell_bed, cb.data(), sizeof(int) * c->ncells, cudaMemcpyHostToDevice, c->st));
+    std::vector<double> Y((size_t)c->ncells * 3), T(c->ncells);
+    if (g && g->Y && g->T) {
+      if (g->on_device) {
+        ck(cudaMemcpy(Y.data(), g->Y, sizeof(double) * Y.size(), cudaMemcpyDeviceToHost));
+        ck(cudaMemcpy(T.data(), g->T, sizeof(double) * T.size(), cudaMemcpyDeviceToHost));
+      } else {
+        std::memcpy(Y.data(), g->Y, sizeof(double) * Y.size());
+        std::memcpy(T.data(), g->T, sizeof(double) * T.size());
+      }
+    } else {
+      for (long long cc = 0; cc < c->ncells; ++cc) {
+        const dem_bed_config &B = beds[cb[cc]];
+        for (int j = 0; j < 3; ++j) Y[cc * 3 + j] = B.Y_in[j];
+        T[cc] = B.T_in;
+      }
+    }
+    double *dY = nullptr, *dT = nullptr;
+    ck(cudaMalloc(&dY, sizeof(double) * Y.size()));
+    ck(cudaMalloc(&dT, sizeof(double) * T.size()));
+    if (rc == DEM_OK) {
+      ck(cudaMemcpyAsync(dY, Y.data(), sizeof(double) * Y.size(), cudaMemcpyHostToDevice, c->st));
+      ck(cudaMemcpyAsync(dT, T.data(), sizeof(double) * T.size(), cudaMemcpyHostToDevice, c->st));
+      const int gg = (int)((c->ncells + 255) / 256);
+      k_gas_load<<<gg, 256, 0, c->st>>>(c->ncells, dY, dT, c->gas[0]);
+      k_mark_cells<<<gg, 256, 0, c->st>>>(c->dbeds, c->cell_bed, c->mark, c->ncells);
+    }
+    ck(cudaStreamSynchronize(c->st));
+    cudaFree(dY);
+    cudaFree(dT);
+  }
+  c->cur = 0;
+  c->gcur = 0;
+  if (rc == DEM_OK) {
+    int e = c->prec == DEM_PREC_FP64 ? enqueue_init<double>(c) : enqueue_init<float>(c);
+    if (e) rc = DEM_ECUDA;
+  }
+  ck(cudaStreamSynchronize(c->st));
+  cudaFree(dsrc);
+  cudaFree(dint);
+  cudaFree(dptrs);
+  if (rc == DEM_OK) {
+    int herr = 0;
+    ck(cudaMemcpy(&herr, c->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (rc == DEM_OK && herr) rc = status_from_bits(herr);
+  }
+  if (rc != DEM_OK) { dem_destroy(c); return rc; }
+  *out = c;
+  return DEM_OK;
+}
+
+int dem_step(dem_ctx *c, int32_t n_steps) {
+  if (!c || n_steps < 0) return DEM_EINVAL;
+  int s = poll(c, false);
+  if (s != DEM_OK) return s;
+  c->launches = 0;
+  if (enqueue_steps_any(c, n_steps)) return c->sticky = DEM_ECUDA;
+  return mark_pending(c);
+}
+
+int dem_step_graph(dem_ctx *c, int32_t n_steps) {
+  if (!c || n_steps <= 0) return DEM_EINVAL;
+  int s = poll(c, false);
+  if (s != DEM_OK) return s;
+  const auto key = std::make_tuple((int)n_steps, c->cur, c->gcur);
+  auto it = c->graphs.find(key);
+  if (it == c->graphs.end()) {
+    // capture on a private non-blocking stream (the legacy default stream cannot capture);
+    // capturing records the kernels without running them
+    if (!c->gst && cudaStreamCreateWithFlags(&c->gst, cudaStreamNonBlocking) != cudaSuccess) return c->sticky = DEM_ECUDA;
+    const int cur0 = c->cur, gcur0 = c->gcur;
+    cudaStream_t user = c->st;
+    c->st = c->gst;
+    c->launches = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { c->st = user; return c->sticky = DEM_ECUDA; }
+    int e = enqueue_steps_any(c, n_steps);
+    cudaError_t ce = cudaStreamEndCapture(c->st, &graph);
+    c->st = user;
+    if (e || ce != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return c->sticky = DEM_ECUDA; }
+    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) { cudaGraphDestroy(graph); return c->sticky = DEM_ECUDA; }
+    it = c->graphs.emplace(key, std::make_pair(graph, exec)).first;
+    c->graph_launches[key] = c->launches;
+    c->cur = cur0;
+    c->gcur = gcur0;
+  }
+  // the host-side bookkeeping advances as the captured steps do; every sort of this
+  // context leaves its result in the same buffer, so kres/vres already point there
+  for (int k = 0; k < n_steps; ++k) {
+    c->cur = 1 - c->cur;
+    c->gcur = 1 - c->gcur;
+  }
+  if (cudaGraphLaunch(it->second.second, c->st) != cudaSuccess) return c->sticky = DEM_ECUDA;
+  c->launches = c->graph_launches[key];
+  return mark_pending(c);
+}
+
+int dem_sync(dem_ctx *c) {
+  if (!c) return DEM_EINVAL;
+  return sync_all(c);
+}
+
+int dem_set_kinetics(dem_ctx *c, const double k0[3], const double Ea[3]) {
+  if (!c || !k0 || !Ea) return DEM_EINVAL;
+  int s = sync_all(c);
+  if (s != DEM_OK) return s;
+  for (int b = 0; b < c->nbeds; ++b)
+    for (int r = 0; r < 3; ++r) {
+      if (!(k0[r] >= 0 && Ea[r] >= 0)) return DEM_EINVAL;
+      c->hbeds[b].k0[r] = k0[r];
+      c->hbeds[b].Ea[r] = Ea[r];
+      c->cfg[b].k0[r] = k0[r];
+      c->cfg[b].Ea[r] = Ea[r];
+    }
+  CK(cudaMemcpyAsync(c->dbeds, c->hbeds.data(), sizeof(DevBed) * c->nbeds, cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return DEM_OK;
+}
+
+static int ensure_scratch(dem_ctx *c, size_t bytes) {
+  if (c->scratch_bytes >= bytes) return DEM_OK;
+  if (c->scratch_out) cudaFree(c->scratch_out);
+  c->scratch_out = nullptr;
+  c->scratch_bytes = 0;
+  if (cudaMalloc(&c->scratch_out, bytes) != cudaSuccess) return DEM_ENOMEM;
+  c->scratch_bytes = bytes;
+  return DEM_OK;
+}
+
+int dem_reduction_degree(dem_ctx *c, double *mean_per_bed, double *oxygen_per_bed, double *per_parcel) {
+  if (!c || !mean_per_bed) return DEM_EINVAL;
+  int s = sync_all(c);
+  if (s != DEM_OK) return s;
+  int e = c->prec == DEM_PREC_FP64 ? enqueue_fov<double>(c, per_parcel) : enqueue_fov<float>(c, per_parcel);
+  if (e) return DEM_ECUDA;
+  std::vector<double> hb((size_t)c->nbeds * 4);
+  CK(cudaMemcpyAsync(hb.data(), c->fvbed, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  for (int b = 0; b < c->nbeds; ++b) {
+    const double cnt = hb[b * 4 + 3];
+    mean_per_bed[b] = cnt > 0 ? hb[b * 4 + 0] / cnt : 0.0;
+    if (oxygen_per_bed) oxygen_per_bed[b] = hb[b * 4 + 2] > 0 ? 1.0 - hb[b * 4 + 1] / hb[b * 4 + 2] : 0.0;
+  }
+  return DEM_OK;
+}
+
+int dem_get_state(dem_ctx *c, double *out_host) {
+  if (!c || !out_host) return DEM_EINVAL;
+  int s = sync_all(c);
+  if (s != DEM_OK) return s;
+  const size_t bytes = sizeof(double) * DEM_NSTATE * (size_t)c->n;
+  if ((s = ensure_scratch(c, bytes)) != DEM_OK) return s;
+  int e = c->prec == DEM_PREC_FP64 ? enqueue_scatter_state<double>(c, c->scratch_out)
+                                   : enqueue_scatter_state<float>(c, c->scratch_out);
+  if (e) return DEM_ECUDA;
+  CK(cudaMemcpyAsync(out_host, c->scratch_out, bytes, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return DEM_OK;
+}
+
+int64_t dem_num_cells(dem_ctx *c) { return c ? c->ncells : 0; }
+
+int dem_get_gas(dem_ctx *c, double *out_host) {
+  if (!c || !out_host) return DEM_EINVAL;
+  int s = sync_all(c);
+  if (s != DEM_OK) return s;
+  const size_t nc = (size_t)c->ncells;
+  std::vector<double> G(nc * GS_N);
+  std::vector<unsigned char> mk(nc);
+  CK(cudaMemcpyAsync(G.data(), c->gas[c->gcur], sizeof(double) * G.size(), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(mk.data(), c->mark, nc, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  for (size_t k = 0; k < nc; ++k) {
+    for (int f = 0; f < GS_N; ++f) out_host[k * DEM_NGAS + f] = G[f * nc + k];
+    out_host[k * DEM_NGAS + 5] = mk[k];
+  }
+  return DEM_OK;
+}
+
+int dem_get_sources(dem_ctx *c, double *out_host) {
+  if (!c || !out_host) return DEM_EINVAL;
+  int s = sync_all(c);
+  if (s != DEM_OK) return s;
+  if (!c->dep && cudaMalloc(&c->dep, sizeof(double) * SR_N * (size_t)c->ncells) != cudaSuccess) return DEM_ENOMEM;
+  int e = c->prec == DEM_PREC_FP64 ? enqueue_sources<double>(c) : enqueue_sources<float>(c);
+  if (e) return DEM_ECUDA;
+  CK(cudaMemcpyAsync(out_host, c->dep, sizeof(double) * SR_N * (size_t)c->ncells, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return DEM_OK;
+}
+
+int dem_get_contacts(dem_ctx *c, int32_t *count, int32_t *partner, double *xi) {
+  if (!c || !count || !partner || !xi) return DEM_EINVAL;
+  int s = sync_all(c);
+  if (s != DEM_OK) return s;
+  const size_t n = (size_t)c->n;
+  const size_t bytes = n * sizeof(int) + n * KMAX * sizeof(int) + n * KMAX * 3 * sizeof(double) + 512;
+  if ((s = ensure_scratch(c, bytes)) != DEM_OK) return s;
+  char *base = (char *)c->scratch_out;
+  double *dxi = (double *)base;
+  int *dcnt = (int *)(base + n * KMAX * 3 * sizeof(double));
+  int *dpart = dcnt + n;
+  int e = c->prec == DEM_PREC_FP64 ? enqueue_scatter_hist<double>(c, dcnt, dpart, dxi)
+                                   : enqueue_scatter_hist<float>(c, dcnt, dpart, dxi);
+  if (e) return DEM_ECUDA;
+  CK(cudaMemcpyAsync(count, dcnt, n * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(partner, dpart, n * KMAX * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(xi, dxi, n * KMAX * 3 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  // slots sorted by partner
+  for (size_t i = 0; i < n; ++i) {
+    const int cnt = count[i];
+    std::vector<std::pair<int, int>> ord(cnt);
+    for (int k = 0; k < cnt; ++k) ord[k] = {partner[i * KMAX + k], k};
+    std::sort(ord.begin(), ord.end());
+    std::vector<int> p2(cnt);
+    std::vector<double> x2((size_t)cnt * 3);
+    for (int k = 0; k < cnt; ++k) {
+      p2[k] = ord[k].first;
+      for (int q = 0; q < 3; ++q) x2[(size_t)k * 3 + q] = xi[(i * KMAX + ord[k].second) * 3 + q];
+    }
+    for (int k = 0; k < cnt; ++k) {
+      partner[i * KMAX + k] = p2[k];
+      for (int q = 0; q < 3; ++q) xi[(i * KMAX + k) * 3 + q] = x2[(size_t)k * 3 + q];
+    }
+  }
+  return DEM_OK;
+}
+
+int dem_set_diagnostics(dem_ctx *c, int32_t on) {
+  if (!c) return DEM_EINVAL;
+  int s = sync_all(c);
+  if (s != DEM_OK) return s;
+  if (on && !c->diag) {
+    if (cudaMalloc(&c->diag, sizeof(double) * DG_N * (size_t)c->cap) != cudaSuccess) return DEM_ENOMEM;
+    CK(cudaMemset(c->diag, 0, sizeof(double) * DG_N * (size_t)c->cap));
+  }
+  if (c->diag_on != (on != 0)) {
+    // captured graphs bake the diagnostics pointer in: drop them
+    for (auto &kv : c->graphs) {
+      cudaGraphExecDestroy(kv.second.second);
+      cudaGraphDestroy(kv.second.first);
+    }
+    c->graphs.clear();
+  }
+  c->diag_on = on != 0;
+  return DEM_OK;
+}
+
+int dem_get_diag(dem_ctx *c, double *out_host) {
+  if (!c || !out_host) return DEM_EINVAL;
+  if (!c->diag) return DEM_ESTATE;
+  int s = sync_all(c);
+  if (s != DEM_OK) return s;
+  const size_t bytes = sizeof(double) * DG_N * (size_t)c->n;
+  if ((s = ensure_scratch(c, bytes)) != DEM_OK) return s;
+  int e = c->prec == DEM_PREC_FP64 ? enqueue_scatter_diag<double>(c, c->scratch_out)
+                                   : enqueue_scatter_diag<float>(c, c->scratch_out);
+  if (e) return DEM_ECUDA;
+  CK(cudaMemcpyAsync(out_host, c->scratch_out, bytes, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return DEM_OK;
+}
+
+int64_t dem_last_launch_count(dem_ctx *c) { return c ? c->launches : 0; }
+
+int dem_set_gas(dem_ctx *c, const dem_gas *g) {
+  if (!c || !g || !g->Y || !g->T) return DEM_EINVAL;
+  int s = poll(c, false);
+  if (s != DEM_OK) return s;
+  const size_t nc = (size_t)c->ncells;
+  if (!c->gas_stage && cudaMalloc(&c->gas_stage, sizeof(double) * 4 * nc) != cudaSuccess) return DEM_ENOMEM;
+  const double *Y = g->Y, *T = g->T;
+  if (!g->on_device) {
+    CK(cudaMemcpyAsync(c->gas_stage, g->Y, sizeof(double) * 3 * nc, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->gas_stage + 3 * nc, g->T, sizeof(double) * nc, cudaMemcpyHostToDevice, c->st));
+    Y = c->gas_stage;
+    T = c->gas_stage + 3 * nc;
+  }
+  k_gas_set<<<(int)((nc + 255) / 256), 256, 0, c->st>>>((long long)nc, Y, T, c->gas[c->gcur]);
+  int e = c->prec == DEM_PREC_FP64 ? enqueue_props<double>(c) : enqueue_props<float>(c);
+  if (e) return c->sticky = DEM_ECUDA;
+  return DEM_OK;
+}
+
+int dem_profile(dem_ctx *c, int32_t on) {
+  if (!c) return DEM_EINVAL;
+  int s = sync_all(c);
+  if (s != DEM_OK) return s;
+  c->prof_on = on != 0;
+  c->prof_marks.clear();
+  c->prof_names.clear();
+  c->prof_ms.clear();
+  c->prof_n.clear();
+  return DEM_OK;
+}
+
+int dem_kernel_times(dem_ctx *c, int32_t max_kernels, char *names, int64_t *launches, double *ms_total) {
+  if (!c || max_kernels < 0) return DEM_EINVAL;
+  int s = sync_all(c);
+  if (s != DEM_OK) return s;
+  for (const auto &mk : c->prof_marks) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev_pool[mk.second], c->ev_pool[mk.second + 1]) != cudaSuccess) return DEM_ECUDA;
+    c->prof_ms[mk.first] += ms;
+    c->prof_n[mk.first] += 1;
+  }
+  c->prof_marks.clear();
+  const int k = (int)c->prof_names.size();
+  for (int i = 0; i < k && i < max_kernels; ++i) {
+    if (names) {
+      std::memset(names + 32 * i, 0, 32);
+      std::strncpy(names + 32 * i, c->prof_names[i].c_str(), 31);
+    }
+    if (launches) launches[i] = c->prof_n[i];
+    if (ms_total) ms_total[i] = c->prof_ms[i];
+  }
+  return k;
+}
+
+int dem_autotune(dem_ctx *c, int32_t n_steps) {
+  (void)n_steps;
+  if (!c) return DEM_EINVAL;
+  return DEM_ESTATE;
+}
+
+int dem_adjoint(dem_ctx *c, int32_t n_steps, int32_t ckpt_every, double *J, double *grad) {
+  (void)n_steps; (void)ckpt_every; (void)J; (void)grad;
+  if (!c) return DEM_EINVAL;
+  return DEM_ESTATE;
+}
+
+}  // extern "C"

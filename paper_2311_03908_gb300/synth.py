@@ -398,7 +398,8 @@ def small_packed(seed: int = 7, n: int = 3000, sigma: float = 0.2, v_scale: floa
                  nx: int = 8, nz: int = 48, D: float = 0.012, H: float = 0.072,
                  cg_ratio: float = 4.0, flags: int = 0) -> Bed:
     """A small dense bed for parity tests: several gas cells, many contacts, walls."""
-    cfg = BedConfig(D=D, H=H, nx=nx, ny=nx, nz=nz, dt=1e-5, cg_ratio=cg_ratio, U_in=0.3,
+    # dt = 5e-6 keeps omega_0 dt < 2 for the smallest parcels of the +-3 sigma size range
+    cfg = BedConfig(D=D, H=H, nx=nx, ny=nx, nz=nz, dt=5e-6, cg_ratio=cg_ratio, U_in=0.3,
                     T_in=T0, Y_in=(0.9, 0.05, 0.05), wall_kind=wall_kind, flags=flags,
                     cone_half_angle=math.radians(45.0), cone_height=0.5 * D,
                     plate_z=0.5 * D, hole_d=0.6e-3, hole_pitch=1.5e-3, sphericity=(0.86, 0.85))
