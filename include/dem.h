@@ -220,6 +220,28 @@ int dem_set_gas(dem_ctx *c, const dem_gas *g);
 int dem_profile(dem_ctx *c, int32_t on);
 int dem_kernel_times(dem_ctx *c, int32_t max_kernels, char *names, int64_t *launches, double *ms_total);
 
+/* Reduction degree of parcel arrays the caller owns, without allocating anything.
+ * The paper has no counterpart: this serves callers that cannot call cudaMalloc -- code
+ * whose device memory is all handed out by another framework's allocator, or a
+ * latency-critical loop that cannot take cudaMalloc's implicit device-wide
+ * synchronisation -- and that keep their parcels in their own device arrays.
+ * Inputs (device, n each): the parcel masses of Fe2O3, Fe3O4, FeO, Fe (kg) and the ore type
+ * (0 hematite, 1 magnetite). Output (device, 2 doubles): out[0] the arithmetic mean of the
+ * parcels' f_ov (eqs (2-15)..(2-19), as dem_reduction_degree), out[1] the removed-oxygen
+ * fraction. Asynchronous on cuda_stream (NULL = legacy default stream).
+ * Scratch: a file-scope __device__ array of 4096 x 3 doubles (96 KiB) that every GPU loading
+ * the library holds until the process exits; n is limited to DEM_NOALLOC_MAX_PARCELS and a
+ * larger n returns DEM_EINVAL before any work is enqueued. No cudaMalloc, cudaFree or
+ * allocating library routine is called. The first call on a device (with that device
+ * current) looks up the array's device address with cudaGetSymbolAddress; make that first
+ * call before any stream capture. Every call shares the array and overwrites the rows it
+ * reads, so the array keeps the last call's partial sums; calls that overlap on the GPU
+ * (other streams, other threads) race on it and must be ordered by the caller. */
+#define DEM_NOALLOC_MAX_PARCELS 8388608
+int dem_reduction_degree_noalloc(const double *m_fe2o3, const double *m_fe3o4, const double *m_feo,
+                                 const double *m_fe, const int32_t *ore_type, int32_t n,
+                                 double *out, void *cuda_stream);
+
 /* Human-readable text of a status code (static storage). */
 const char *dem_strerror(int status);
 

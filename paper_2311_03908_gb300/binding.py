@@ -19,6 +19,7 @@ DEM_OK, DEM_EINVAL, DEM_ENOMEM, DEM_ECUDA, DEM_ECAPACITY, DEM_ENONFINITE, DEM_ET
 DEM_PREC_FP64, DEM_PREC_SPLIT, DEM_PREC_SPLIT_KAHAN = 0, 1, 2
 DEM_MAX_CONTACTS = 24
 DEM_NSTATE, DEM_NGAS, DEM_NDEP, DEM_NDIAG = 20, 6, 14, 32
+DEM_NOALLOC_MAX_PARCELS = 8388608
 PRECISIONS = {"fp64": DEM_PREC_FP64, "split": DEM_PREC_SPLIT, "split_kahan": DEM_PREC_SPLIT_KAHAN}
 
 STATE_ROWS = ["x", "y", "z", "vx", "vy", "vz", "wx", "wy", "wz", "T", "m_h", "m_m", "m_w", "m_fe",
@@ -94,6 +95,7 @@ def lib() -> C.CDLL:
         "dem_set_gas": (C.c_int, [vp, C.POINTER(DemGas)]),
         "dem_profile": (C.c_int, [vp, C.c_int32]),
         "dem_kernel_times": (C.c_int, [vp, C.c_int32, C.c_char_p, C.POINTER(C.c_int64), dp]),
+        "dem_reduction_degree_noalloc": (C.c_int, [vp, vp, vp, vp, vp, C.c_int32, vp, vp]),
         "dem_strerror": (C.c_char_p, [C.c_int]),
         "dem_destroy": (None, [vp]),
     }
