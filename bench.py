@@ -43,18 +43,21 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=100_000, help="parcels in the oracle's sample")
+    ap.add_argument("--parcels", type=int, default=0, help="override the workload's parcel count "
+                    "(smaller cases for profiler captures; same geometry and packing)")
     return ap.parse_args()
 
 
-def make_workload(name: str, rank: int = 0):
+def make_workload(name: str, rank: int = 0, parcels: int = 0):
     from paper_2311_03908_gb300 import synth
     seed_shift = 7919 * rank
+    kw = {"n": parcels} if parcels else {}
     if name == "ibm_2m":
-        return synth.config_ibm_2m(seed=2311039083 + seed_shift)
+        return synth.config_ibm_2m(seed=2311039083 + seed_shift, **kw)
     if name == "split_200k":
-        return synth.config_split_200k(seed=2311039082 + seed_shift)
+        return synth.config_split_200k(seed=2311039082 + seed_shift, **kw)
     if name == "plain_2k":
-        return synth.config_plain_2k(seed=2311039081 + seed_shift)
+        return synth.config_plain_2k(seed=2311039081 + seed_shift, **kw)
     if name == "batched_32":
         return synth.config_batched_32(seed=2311039085 + seed_shift)
     raise ValueError(name)
@@ -171,7 +174,7 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    bed = make_workload(args.workload)
+    bed = make_workload(args.workload, 0, args.parcels)
     import oracle
     n = min(args.cpu_sample, bed.n)
     sub = bed.subset(np.arange(n)) if n < bed.n else bed
@@ -210,7 +213,7 @@ def main():
     torch.cuda.set_device(local)
     from paper_2311_03908_gb300 import binding
     stream = torch.cuda.current_stream()
-    bed = make_workload(args.workload, rank)
+    bed = make_workload(args.workload, rank, args.parcels)
     ctx = binding.Context(bed, precision=args.precision, stream=stream.cuda_stream)
     n = bed.n
 

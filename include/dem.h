@@ -162,7 +162,11 @@ int dem_reduction_degree(dem_ctx *c, double *mean_per_bed, double *oxygen_per_be
  * the bed time step. grad (host, 6 doubles) gets dJ/dk0[0..2] and dJ/dEa[0..2], the
  * parameters applied to every bed. The forward pass stores a checkpoint every
  * ckpt_every sub-steps; the reverse pass recomputes each segment and runs the hand-written
- * adjoint kernel back through it. The context's state is not changed. Synchronous. */
+ * adjoint kernel back through it. The context's state is not changed. Synchronous.
+ * grad may be NULL: then only the forward sweep runs and only J is written. The sub-step
+ * is evaluated in FP64 whatever the context's precision. Errors: DEM_EINVAL for n_steps < 0
+ * or ckpt_every < 1; DEM_ENOMEM when the checkpoint and segment buffers (8 doubles per
+ * parcel per checkpoint and per sub-step of a segment) cannot be allocated. */
 int dem_adjoint(dem_ctx *c, int32_t n_steps, int32_t ckpt_every, double *J, double *grad);
 
 /* Replace the kinetic parameters of every bed (R1..R3). */

@@ -224,12 +224,15 @@ class Context:
                "dem_reduction_degree")
         return mean, oxy
 
-    def dem_adjoint(self, nsteps, ckpt_every=100):
+    def dem_adjoint(self, nsteps, ckpt_every=100, want_grad=True):
+        """(J, grad) of the frozen-position drag-heat-reaction map; grad is None when
+        want_grad is False (forward sweep only)."""
         J = np.zeros(1)
         g = np.zeros(6)
-        _check(lib().dem_adjoint(self.h, int(nsteps), int(ckpt_every), J.ctypes.data_as(C.POINTER(C.c_double)),
-                                 g.ctypes.data_as(C.POINTER(C.c_double))), "dem_adjoint")
-        return float(J[0]), g
+        gp = g.ctypes.data_as(C.POINTER(C.c_double)) if want_grad else None
+        _check(lib().dem_adjoint(self.h, int(nsteps), int(ckpt_every), J.ctypes.data_as(C.POINTER(C.c_double)), gp),
+               "dem_adjoint")
+        return float(J[0]), (g if want_grad else None)
 
     def dem_set_kinetics(self, k0, Ea):
         a = np.ascontiguousarray(k0, dtype=np.float64)

@@ -118,44 +118,51 @@ struct CellProps {
   double rho, mu, lam, cp, x, Dm, sc13, pr13, epow, D[2], uz, eps, T;
 };
 
-__device__ inline CellProps gas_cell_props(const DevBed &B, double eps, const double Y[3], double T) {
+// Computed in the form's arithmetic type P (double in the FP64 form, float in the split
+// form: GB300's FP64 rate is a small fraction of its FP32 rate); the gas state itself and
+// the cell sums stay FP64.
+template <class P>
+__device__ inline CellProps gas_cell_props(const DevBed &B, double eps_d, const double Yd[3], double Td) {
   CellProps o;
-  const double p = B.p0;
-  double inv = Y[0] / cMj[0] + Y[1] / cMj[1] + Y[2] / cMj[2];
-  double Mg = 1.0 / inv;
-  double xp0 = Y[0] * Mg / cMj[0], xp1 = Y[1] * Mg / cMj[1], xp2 = Y[2] * Mg / cMj[2];
-  double den = xp0 + xp1;
-  o.x = den > 0.0 ? xp0 / den : 0.0;
-  o.rho = Mg * p / (kRgas * T);
-  double mu = 0.0, lam = 0.0, cp = 0.0;
+  const P p = (P)B.p0, T = (P)Td, eps = (P)eps_d;
+  const P Y[3] = {(P)Yd[0], (P)Yd[1], (P)Yd[2]};
+  const P inv = Y[0] / (P)cMj[0] + Y[1] / (P)cMj[1] + Y[2] / (P)cMj[2];
+  const P Mg = (P)1 / inv;
+  const P xp0 = Y[0] * Mg / (P)cMj[0], xp1 = Y[1] * Mg / (P)cMj[1], xp2 = Y[2] * Mg / (P)cMj[2];
+  const P den = xp0 + xp1;
+  const P x = den > (P)0 ? xp0 / den : (P)0;
+  const P rho = Mg * p / ((P)kRgas * T);
+  P mu = 0, lam = 0, cp = 0;
+#pragma unroll
   for (int j = 0; j < 3; ++j) {
-    mu += Y[j] * (cVisc[j][0] + T * (cVisc[j][1] + T * cVisc[j][2]));
-    lam += Y[j] * (cCond[j][0] + T * (cCond[j][1] + T * (cCond[j][2] + T * (cCond[j][3] + T * cCond[j][4]))));
-    cp += Y[j] * cp_over_R<double>(j, T) * kRgas / cMj[j];
+    mu += Y[j] * ((P)cVisc[j][0] + T * ((P)cVisc[j][1] + T * (P)cVisc[j][2]));
+    lam += Y[j] * ((P)cCond[j][0] + T * ((P)cCond[j][1] + T * ((P)cCond[j][2] + T * ((P)cCond[j][3] + T * (P)cCond[j][4]))));
+    cp += Y[j] * cp_over_R<P>(j, T) * (P)(kRgas / cMj[j]);
   }
-  o.mu = mu;
-  o.lam = lam;
-  o.cp = cp;
-  // Fuller binary coefficients D(H2,H2O), D(H2,N2) and Wilke's rule for H2
-  double tf = exp(1.75 * log(T)) * (101325.0 / p) * 1e-7;
-  double D12 = tf * B.fuller12, D13 = tf * B.fuller13;
-  double rest = 1.0 - xp0;
-  o.Dm = rest < 1e-12 ? D12 : rest / (xp1 / D12 + xp2 / D13);
-  o.sc13 = cbrt(mu / (o.rho * o.Dm));
+  // Fuller binary coefficients D(H2,H2O), D(H2,N2) (T^1.75 = T sqrt(T) sqrt(sqrt(T))) and
+  // Wilke's rule for H2
+  const P sT = sqrt(T);
+  const P tf = T * sT * sqrt(sT) * ((P)101325 / p) * (P)1e-7;
+  const P D12 = tf * (P)B.fuller12, D13 = tf * (P)B.fuller13;
+  const P rest = (P)1 - xp0;
+  const P Dm = rest < (P)1e-12 ? D12 : rest / (xp1 / D12 + xp2 / D13);
+  o.rho = rho; o.mu = mu; o.lam = lam; o.cp = cp; o.x = x; o.Dm = Dm;
+  o.sc13 = cbrt(mu / (rho * Dm));
   o.pr13 = cbrt(cp * mu / lam);
-  o.epow = exp(-2.65 * log(eps));
+  o.epow = exp((P)-2.65 * log(eps));
   // pore diffusion per ore: molecular, Knudsen, or Bosanquet by lambda / d_a (Sec. 2.3)
-  double mfp = o.x > 0.0 ? 1.013 / (p * o.x) : 1e300;
-  double sq = sqrt(T / (cMj[0] * 1e3));
+  const P mfp = x > (P)0 ? (P)1.013 / (p * x) : (P)3e38;
+  const P sq = sqrt(T / (P)(cMj[0] * 1e3));
+#pragma unroll
   for (int ore = 0; ore < 2; ++ore) {
-    double da = B.pore_cm[ore];
-    double DK = 0.97 * (0.5 * da) * sq;
-    double ratio = mfp / da;
-    o.D[ore] = ratio <= 0.01 ? o.Dm : (ratio >= 10.0 ? DK : 1.0 / (1.0 / o.Dm + 1.0 / DK));
+    const P da = (P)B.pore_cm[ore];
+    const P DK = (P)0.97 * ((P)0.5 * da) * sq;
+    const P ratio = mfp / da;
+    o.D[ore] = ratio <= (P)0.01 ? Dm : (ratio >= (P)10 ? DK : (P)1 / ((P)1 / Dm + (P)1 / DK));
   }
-  o.uz = B.U_in / eps;
-  o.eps = eps;
-  o.T = T;
+  o.uz = (P)B.U_in / eps;
+  o.eps = eps_d;
+  o.T = Td;
   return o;
 }
 

@@ -799,9 +799,11 @@ int dem_autotune(dem_ctx *c, int32_t n_steps) {
 }
 
 int dem_adjoint(dem_ctx *c, int32_t n_steps, int32_t ckpt_every, double *J, double *grad) {
-  (void)n_steps; (void)ckpt_every; (void)J; (void)grad;
-  if (!c) return DEM_EINVAL;
-  return DEM_ESTATE;
+  if (!c || !J || n_steps < 0 || ckpt_every < 1) return DEM_EINVAL;
+  int s = sync_all(c);
+  if (s != DEM_OK) return s;
+  return c->prec == DEM_PREC_FP64 ? run_adjoint<double>(c, n_steps, ckpt_every, J, grad)
+                                  : run_adjoint<float>(c, n_steps, ckpt_every, J, grad);
 }
 
 }  // extern "C"

@@ -516,7 +516,7 @@ __global__ void k_cells(StepView<R> V, int mode /* 0 step, 1 eps init, 2 props o
   Gn[GS_EPS * nc + c] = eps;
   Gn[GS_Y0 * nc + c] = Y[0]; Gn[GS_Y1 * nc + c] = Y[1]; Gn[GS_Y2 * nc + c] = Y[2];
   Gn[GS_T * nc + c] = T;
-  const CellProps p = gas_cell_props(B, eps, Y, T);
+  const CellProps p = gas_cell_props<R>(B, eps, Y, T);
   store_props(V, (int)c, p);
 }
 

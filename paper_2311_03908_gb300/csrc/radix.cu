@@ -2,7 +2,7 @@
 // the binning step of the particle path (parcels sorted on their DEM-cell key).
 //
 // Each pass sorts on one 8-bit digit, stably, in three kernels: per-tile digit histograms,
-// one exclusive scan over (digit, tile), and a scatter in which every tile ranks its keys
+// an exclusive scan of each digit's row over the tiles (one block per digit), and a scatter in which every tile ranks its keys
 // with warp-level match masks (__match_any_sync) and per-warp digit counts in shared
 // memory, so equal digits keep their input order.
 #include <cuda_runtime.h>
@@ -31,17 +31,20 @@ __global__ void __launch_bounds__(RS_THREADS) rs_hist(const unsigned *keys, int 
   hist[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-// exclusive scan of hist[0..total) (digit-major, then tile) by one block of 1024 threads
-__global__ void __launch_bounds__(1024) rs_scan(unsigned *hist, int total) {
-  __shared__ unsigned part[1024];
-  const int per = (total + 1023) / 1024;
+// Exclusive scan of each digit's row hist[d][0..ntiles) (one block per digit, in place);
+// the row totals go to tot[d]. The scatter adds the digits' exclusive offsets itself.
+constexpr int RS_SCAN_THREADS = 512;
+__global__ void __launch_bounds__(RS_SCAN_THREADS) rs_scan_rows(unsigned *hist, int ntiles, unsigned *tot) {
+  __shared__ unsigned part[RS_SCAN_THREADS];
+  unsigned *row = hist + (size_t)blockIdx.x * ntiles;
+  const int per = (ntiles + RS_SCAN_THREADS - 1) / RS_SCAN_THREADS;
   const int b = threadIdx.x * per;
-  const int e = min(b + per, total);
+  const int e = min(b + per, ntiles);
   unsigned s = 0;
-  for (int t = b; t < e; ++t) s += hist[t];
+  for (int t = b; t < e; ++t) s += row[t];
   part[threadIdx.x] = s;
   __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
+  for (int off = 1; off < RS_SCAN_THREADS; off <<= 1) {
     const unsigned v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0u;
     __syncthreads();
     part[threadIdx.x] += v;
@@ -49,21 +52,33 @@ __global__ void __launch_bounds__(1024) rs_scan(unsigned *hist, int total) {
   }
   unsigned run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
   for (int t = b; t < e; ++t) {
-    const unsigned v = hist[t];
-    hist[t] = run;
+    const unsigned v = row[t];
+    row[t] = run;
     run += v;
   }
+  if (threadIdx.x == RS_SCAN_THREADS - 1) tot[blockIdx.x] = part[RS_SCAN_THREADS - 1];
 }
 
 __global__ void __launch_bounds__(RS_THREADS) rs_scatter(const unsigned *kin, const unsigned *vin,
                                                         unsigned *kout, unsigned *vout, int n,
-                                                        int shift, const unsigned *hist, int ntiles) {
+                                                        int shift, const unsigned *hist, int ntiles,
+                                                        const unsigned *tot) {
   __shared__ unsigned run[256];
   __shared__ unsigned gbase[256];
   __shared__ unsigned wc[RS_WARPS][257];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // exclusive offset of this digit: scan of the 256 digit totals (Hillis-Steele in run[])
+  run[tid] = tot[tid];
+  __syncthreads();
+  for (int off = 1; off < 256; off <<= 1) {
+    const unsigned v = tid >= off ? run[tid - off] : 0u;
+    __syncthreads();
+    run[tid] += v;
+    __syncthreads();
+  }
+  gbase[tid] = hist[tid * ntiles + blockIdx.x] + (run[tid] - tot[tid]);
+  __syncthreads();
   run[tid] = 0;
-  gbase[tid] = hist[tid * ntiles + blockIdx.x];
   const unsigned lt = (1u << lane) - 1u;
   const int base = blockIdx.x * RS_TILE;
   for (int it = 0; it < RS_ITEMS; ++it) {
@@ -98,7 +113,7 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter(const unsigned *kin, co
   }
 }
 
-size_t radix_hist_words(int n) { return (size_t)256 * (size_t)((n + RS_TILE - 1) / RS_TILE); }
+size_t radix_hist_words(int n) { return (size_t)256 * (size_t)((n + RS_TILE - 1) / RS_TILE) + 256; }
 
 int radix_sort_pairs(unsigned *k, unsigned *v, unsigned *k2, unsigned *v2, unsigned *hist, int n,
                      int bits, cudaStream_t st, unsigned **kres, unsigned **vres, long long *launches) {
@@ -107,9 +122,10 @@ int radix_sort_pairs(unsigned *k, unsigned *v, unsigned *k2, unsigned *v2, unsig
   unsigned *ka = k, *va = v, *kb = k2, *vb = v2;
   for (int p = 0; p < passes; ++p) {
     const int shift = 8 * p;
+    unsigned *tot = hist + (size_t)256 * ntiles;
     rs_hist<<<ntiles, RS_THREADS, 0, st>>>(ka, n, shift, hist, ntiles);
-    rs_scan<<<1, 1024, 0, st>>>(hist, 256 * ntiles);
-    rs_scatter<<<ntiles, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, shift, hist, ntiles);
+    rs_scan_rows<<<256, RS_SCAN_THREADS, 0, st>>>(hist, ntiles, tot);
+    rs_scatter<<<ntiles, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, shift, hist, ntiles, tot);
     if (launches) *launches += 3;
     unsigned *t = ka; ka = kb; kb = t;
     t = va; va = vb; vb = t;

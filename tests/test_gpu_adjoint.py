@@ -1,0 +1,69 @@
+"""Hand-written adjoint (through the C ABI and torch.autograd) against the FP64 oracle's
+dual-number gradient and central finite differences of the same map, on the GPU."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2311_03908_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no GPU", allow_module_level=True)
+
+from paper_2311_03908_gb300 import binding  # noqa: E402
+from paper_2311_03908_gb300.autograd import reduction_degree  # noqa: E402
+
+
+def _ctx(bed, prec="fp64"):
+    return binding.Context(bed, precision=prec, stream=torch.cuda.current_stream().cuda_stream)
+
+
+def test_adjoint_gradient_matches_dual_numbers_and_central_differences():
+    bed = synth.config_adjoint_64k(n=1500)
+    ctx = _ctx(bed)
+    J, g = ctx.dem_adjoint(300, 40)
+    ref = oracle.Oracle(bed)
+    Jd, gd = ref.adjoint(300, mode=2)
+    Jf, gf = ref.adjoint(300, mode=1, rel=1e-6)
+    assert J > 0
+    assert abs(J - Jd) < 1e-9 * abs(Jd)
+    assert np.all(np.abs(g - gd) <= 1e-4 * np.abs(gd)), (g, gd)
+    assert np.all(np.abs(g - gf) <= 1e-4 * np.abs(gf)), (g, gf)
+    # the checkpoint interval changes the recomputation, not the result
+    J2, g2 = ctx.dem_adjoint(300, 7)
+    assert J2 == J and np.allclose(g2, g, rtol=1e-12, atol=0)
+    J3, g3 = ctx.dem_adjoint(300, 300)
+    assert np.allclose(g3, g, rtol=1e-12, atol=0)
+    # forward sweep only
+    J4, none = ctx.dem_adjoint(300, 40, want_grad=False)
+    assert none is None and J4 == J
+    ctx.close()
+
+
+def test_adjoint_split_context_and_magnetite_fit():
+    bed = synth.config_adjoint_64k(n=800)
+    for c in bed.beds:
+        c.k0, c.Ea = synth.MAGNETITE_FIT
+    ctx = _ctx(bed, "split")
+    J, g = ctx.dem_adjoint(150, 50)
+    ref = oracle.Oracle(bed)
+    Jd, gd = ref.adjoint(150, mode=2)
+    # the split context stores v and T in FP32; the sub-step itself runs in FP64
+    assert abs(J - Jd) < 1e-5 * abs(Jd)
+    assert np.all(np.abs(g - gd) <= 1e-3 * np.abs(gd)), (g, gd)
+    ctx.close()
+
+
+def test_autograd_function_returns_the_adjoint_gradient():
+    bed = synth.config_adjoint_64k(n=600)
+    ctx = _ctx(bed)
+    k0, Ea = synth.TAKENAKA
+    params = torch.tensor(list(k0) + list(Ea), dtype=torch.float64, requires_grad=True)
+    J = reduction_degree(params, ctx, nsteps=100, ckpt_every=25)
+    J.backward()
+    Jr, gr = ctx.dem_adjoint(100, 25)
+    assert float(J.detach()) == Jr
+    assert np.allclose(params.grad.numpy(), gr, rtol=1e-13, atol=0)
+    ctx.close()
