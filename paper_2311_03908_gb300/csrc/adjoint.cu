@@ -43,14 +43,9 @@ struct Fwd {          // intermediates of one forward sub-step
 
 __device__ inline double cz_mass(int s, double T, double M) { return cp_over_R<double>(s, T) * kRgas / M; }
 
-// derivative of the molar heat capacity polynomial / R (eq (3-23)) w.r.t. T
-__device__ inline double dcp_over_R(int s, double T) {
-  const int r = T <= cNasaT[s] ? 0 : 1;
-  const double *a = cNasa[s][r];
-  return a[1] + T * (2.0 * a[2] + T * (3.0 * a[3] + T * 4.0 * a[4]));
-}
 
 __device__ void fwd(const Par &P, const double s[8], const double th[6], Fwd &F, double sn[8]) {
+  const Tab<double> &td = tab<double>();
   const unsigned fl = P.flags;
   const double v[3] = {s[0], s[1], s[2]};
   const double T = s[3];
@@ -78,7 +73,7 @@ __device__ void fwd(const Par &P, const double s[8], const double th[6], Fwd &F,
   F.hA = (fl & DEM_NO_HEAT) ? 0.0 : P.k3 * kPI * P.d * P.lam * F.Nu;
   F.Qc = F.hA * (P.Tg - T);
   // kinetics (the same arithmetic as uscm<double>)
-  for (int z = 0; z < 4; ++z) F.n[z] = m[z] * P.inv_k3 / cMz[z];
+  for (int z = 0; z < 4; ++z) F.n[z] = m[z] * P.inv_k3 / td.Mz[z];
   F.nfe = 2.0 * F.n[0] + 3.0 * F.n[1] + F.n[2] + F.n[3];
   for (int r = 0; r < 3; ++r) { F.xid[r] = 0.0; F.J[r] = 0.0; F.g[r] = 0.0; F.act[r] = F.fin[r] = F.hasB[r] = false; F.lim[r] = 2; }
   for (int z = 0; z < 4; ++z) F.mdot[z] = 0.0;
@@ -94,7 +89,7 @@ __device__ void fwd(const Par &P, const double s[8], const double th[6], Fwd &F,
     F.om[2] = (2.0 * F.n[0] + 3.0 * F.n[1] + F.n[2]) * inv_nfe;
     const bool kin = !(fl & DEM_NO_KINETICS);
     for (int r = 0; r < 3; ++r) {
-      F.K[r] = exp(cKa[r] * F.invT + cKb[r]);
+      F.K[r] = exp(td.Ka[r] * F.invT + td.Kb[r]);
       F.xeq[r] = 1.0 / (F.K[r] + 1.0);
       F.kr[r] = th[r] * exp(-(th[3 + r] / kRgas) * F.invT);
       F.c3[r] = cbrt(F.om[r]);
@@ -139,20 +134,20 @@ __device__ void fwd(const Par &P, const double s[8], const double th[6], Fwd &F,
       F.lim[r] = !(xr > 0.0) ? 2 : (x0 < cap ? 0 : 1);
     }
     const double k3 = P.k3;
-    F.mdot[0] = -3.0 * F.xid[0] * cMz[0] * k3;
-    F.mdot[1] = (2.0 * F.xid[0] - F.xid[1]) * cMz[1] * k3;
-    F.mdot[2] = (3.0 * F.xid[1] - F.xid[2]) * cMz[2] * k3;
-    F.mdot[3] = F.xid[2] * cMz[3] * k3;
+    F.mdot[0] = -3.0 * F.xid[0] * td.Mz[0] * k3;
+    F.mdot[1] = (2.0 * F.xid[0] - F.xid[1]) * td.Mz[1] * k3;
+    F.mdot[2] = (3.0 * F.xid[1] - F.xid[2]) * td.Mz[2] * k3;
+    F.mdot[3] = F.xid[2] * td.Mz[3] * k3;
     F.tot = F.xid[0] + F.xid[1] + F.xid[2];
     if (!(fl & DEM_NO_RXN_HEAT)) {
       double q = 0.0;
-      for (int z = 0; z < 4; ++z) q += h_over_R<double>(3 + z, T) * kRgas * F.mdot[z] / cMz[z];
+      for (int z = 0; z < 4; ++z) q += h_over_R<double>(3 + z, T) * kRgas * F.mdot[z] / td.Mz[z];
       F.Qx = -q + F.tot * k3 * kRgas * (h_over_R<double>(0, T) - h_over_R<double>(1, T));
     }
   }
   // temperature
   F.C = 0.0;
-  for (int z = 0; z < 4; ++z) F.C += m[z] * cz_mass(3 + z, T, cMz[z]);
+  for (int z = 0; z < 4; ++z) F.C += m[z] * cz_mass(3 + z, T, td.Mz[z]);
   sn[3] = T + P.dt * (F.Qc + F.Qx) / F.C;
   // masses
   for (int z = 0; z < 4; ++z) {
@@ -166,6 +161,7 @@ __device__ void fwd(const Par &P, const double s[8], const double th[6], Fwd &F,
 // and add this step's contribution to the parameter gradient g (k0[3], Ea[3]).
 __device__ void bwd(const Par &P, const double s[8], const double th[6], const Fwd &F, const double ln[8],
                     double l[8], double g[6]) {
+  const Tab<double> &td = tab<double>();
   const unsigned fl = P.flags;
   const double T = s[3];
   const double *m = s + 4;
@@ -181,8 +177,8 @@ __device__ void bwd(const Par &P, const double s[8], const double th[6], const F
   const double lC = -ln[3] * P.dt * (F.Qc + F.Qx) / (F.C * F.C);
   double dC = 0.0;
   for (int z = 0; z < 4; ++z) {
-    lm[z] += lC * cz_mass(3 + z, T, cMz[z]);
-    dC += m[z] * dcp_over_R(3 + z, T) * kRgas / cMz[z];
+    lm[z] += lC * cz_mass(3 + z, T, td.Mz[z]);
+    dC += m[z] * dcp_over_R<double>(3 + z, T) * kRgas / td.Mz[z];
   }
   lT += lC * dC;
   // v' = v + dt Kp sv / mp
@@ -207,17 +203,17 @@ __device__ void bwd(const Par &P, const double s[8], const double th[6], const F
       // Qx = -sum_z R h_z mdot_z / M_z + tot k3 R (h_H2 - h_H2O)
       double dQ = 0.0;
       for (int z = 0; z < 4; ++z) {
-        lmdot[z] += -lQ * h_over_R<double>(3 + z, T) * kRgas / cMz[z];
-        dQ += -cp_over_R<double>(3 + z, T) * kRgas * F.mdot[z] / cMz[z];
+        lmdot[z] += -lQ * h_over_R<double>(3 + z, T) * kRgas / td.Mz[z];
+        dQ += -cp_over_R<double>(3 + z, T) * kRgas * F.mdot[z] / td.Mz[z];
       }
       ltot = lQ * k3 * kRgas * (h_over_R<double>(0, T) - h_over_R<double>(1, T));
       dQ += F.tot * k3 * kRgas * (cp_over_R<double>(0, T) - cp_over_R<double>(1, T));
       lT += lQ * dQ;
     }
     double lx[3];
-    lx[0] = k3 * (-3.0 * cMz[0] * lmdot[0] + 2.0 * cMz[1] * lmdot[1]) + ltot;
-    lx[1] = k3 * (-cMz[1] * lmdot[1] + 3.0 * cMz[2] * lmdot[2]) + ltot;
-    lx[2] = k3 * (-cMz[2] * lmdot[2] + cMz[3] * lmdot[3]) + ltot;
+    lx[0] = k3 * (-3.0 * td.Mz[0] * lmdot[0] + 2.0 * td.Mz[1] * lmdot[1]) + ltot;
+    lx[1] = k3 * (-td.Mz[1] * lmdot[1] + 3.0 * td.Mz[2] * lmdot[2]) + ltot;
+    lx[2] = k3 * (-td.Mz[2] * lmdot[2] + td.Mz[3] * lmdot[3]) + ltot;
     double lJ[3] = {0, 0, 0}, lc = 0.0;
     for (int r = 0; r < 3; ++r) {
       if (F.lim[r] == 0) { lc += lx[r] * F.J[r]; lJ[r] = lx[r] * F.c; }
@@ -264,7 +260,7 @@ __device__ void bwd(const Par &P, const double s[8], const double th[6], const F
         linvT += lkr * (-F.kr[r] * th[3 + r] / kRgas);
       }
       lK[r] += lxeq[r] * (-1.0 / ((F.K[r] + 1.0) * (F.K[r] + 1.0)));
-      linvT += lK[r] * F.K[r] * cKa[r];
+      linvT += lK[r] * F.K[r] * td.Ka[r];
     }
     // c3 = cbrt(om); om = u / nfe
     double lom[3];
@@ -273,7 +269,7 @@ __device__ void bwd(const Par &P, const double s[8], const double th[6], const F
     const double dnfe[4] = {2, 3, 1, 1};
     for (int r = 0; r < 3; ++r)
       for (int z = 0; z < 4; ++z) ln_[z] += lom[r] * (du[r][z] - F.om[r] * dnfe[z]) / F.nfe;
-    for (int z = 0; z < 4; ++z) lm[z] += ln_[z] * P.inv_k3 / cMz[z];
+    for (int z = 0; z < 4; ++z) lm[z] += ln_[z] * P.inv_k3 / td.Mz[z];
   }
   lT += -linvT * F.invT * F.invT;
   // drag: Kp = bo Vp; bo(slip) with Re = cRe slip; Nu and Sh contributions arrive via lRe
@@ -300,7 +296,8 @@ __device__ void bwd(const Par &P, const double s[8], const double th[6], const F
 }
 
 __device__ double fov(const double *m, int ore) {
-  const double n0 = m[0] / cMz[0], n1 = m[1] / cMz[1], n2 = m[2] / cMz[2], n3 = m[3] / cMz[3];
+  const Tab<double> &td = tab<double>();
+  const double n0 = m[0] / td.Mz[0], n1 = m[1] / td.Mz[1], n2 = m[2] / td.Mz[2], n3 = m[3] / td.Mz[3];
   const double nfe = 2.0 * n0 + 3.0 * n1 + n2 + n3;
   if (!(nfe > 0.0)) return 0.0;
   const double fh = (3.0 * n1 + n2 + n3) / nfe, fm = (n2 + n3) / nfe, fw = n3 / nfe;
@@ -308,8 +305,9 @@ __device__ double fov(const double *m, int ore) {
 }
 
 __device__ void dfov_dm(const double *m, int ore, double out[4]) {
+  const Tab<double> &td = tab<double>();
   double n[4];
-  for (int z = 0; z < 4; ++z) n[z] = m[z] / cMz[z];
+  for (int z = 0; z < 4; ++z) n[z] = m[z] / td.Mz[z];
   const double nfe = 2.0 * n[0] + 3.0 * n[1] + n[2] + n[3];
   for (int z = 0; z < 4; ++z) out[z] = 0.0;
   if (!(nfe > 0.0)) return;
@@ -320,28 +318,28 @@ __device__ void dfov_dm(const double *m, int ore, double out[4]) {
   for (int z = 0; z < 4; ++z) {
     double s = 0.0;
     for (int k = 0; k < 3; ++k) s += w[k] * du[k][z];
-    out[z] = (s - f * dnfe[z]) / nfe / cMz[z];
+    out[z] = (s - f * dnfe[z]) / nfe / td.Mz[z];
   }
 }
 
-template <class R>
-__device__ void load_par(const StepView<R> &V, int i, Par &P, double s[8]) {
+template <class Pp>
+__device__ void load_par(const StepView<Pp> &V, const BedP<double> *bpd, int i, Par &P, double s[8]) {
   const int meta = V.A.meta[i];
-  const DevBed &B = V.beds[meta >> 8];
+  const BedP<double> &B = bpd[meta >> 8];
   P.ore = meta & 255;
   P.flags = B.flags;
   P.d = (double)V.A.d[i];
   P.k3 = B.k3;
-  P.inv_k3 = 1.0 / B.k3;
+  P.inv_k3 = B.inv_k3;
   const double dc = B.k * P.d;
   P.Vp = kPI / 6.0 * dc * dc * dc;
   P.dt = B.dt;
   P.p0 = B.p0;
   const size_t nc = (size_t)V.ncells;
-  const int c = V.gcell[i];
+  const unsigned c = V.keys[i];
   const double *G = V.gas;
   const double Y[3] = {G[GS_Y0 * nc + c], G[GS_Y1 * nc + c], G[GS_Y2 * nc + c]};
-  const CellProps cp = gas_cell_props<double>(B, G[GS_EPS * nc + c], Y, G[GS_T * nc + c]);
+  const CellProps<double> cp = gas_cell_props<double>(B, G[GS_EPS * nc + c], Y, G[GS_T * nc + c]);
   P.rho = cp.rho; P.mu = cp.mu; P.lam = cp.lam; P.eps = cp.eps; P.Tg = cp.T; P.x = cp.x; P.Dm = cp.Dm;
   P.sc13 = cp.sc13; P.pr13 = cp.pr13; P.epow = cp.epow; P.D = cp.D[P.ore]; P.uz = cp.uz;
   P.cRe = P.rho * P.eps * P.d / P.mu;
@@ -349,30 +347,30 @@ __device__ void load_par(const StepView<R> &V, int i, Par &P, double s[8]) {
   P.ergun = P.eps < 0.8;
   P.aE = 150.0 * ep * P.mu / (P.eps * P.d * P.d * psi * psi);
   P.bE = 1.75 * P.eps * P.rho / (P.d * psi * ep);
-  P.K1 = B.K1b[P.ore] - 2.25 * P.d / B.bedD;
+  P.K1 = B.K1b[P.ore] - B.wall_K1 * P.d;
   P.K2 = B.K2[P.ore];
   P.cW = 0.75 * P.eps * P.rho / P.d * P.epow;
   P.wlim = 0.75 * (24.0 / P.K1) * P.mu / (P.d * P.d) * P.epow;
   P.a1g = 7.0 - 10.0 * P.eps + 5.0 * P.eps * P.eps;
   P.a2g = 1.33 - 2.4 * P.eps + 1.2 * P.eps * P.eps;
   const double rp = 0.5 * P.d;
-  for (int l = 0; l < 3; ++l) P.cB[l] = rp / (P.D * B.xi[P.ore][l] / B.tau);
+  for (int l = 0; l < 3; ++l) P.cB[l] = rp / (P.D * B.xi[P.ore][l] * B.inv_tau);
   for (int q = 0; q < 3; ++q) s[q] = (double)V.A.v[q][i];
   s[3] = (double)V.A.T[i];
-  for (int z = 0; z < 4; ++z) s[4 + z] = V.A.m[z][i];
+  for (int z = 0; z < 4; ++z) s[4 + z] = mass_d<Pp>(V.A.m[z], i);
 }
 
 // grad == false: forward sweep only (J). partial: [grid][7] = J sum, then 6 gradient sums.
-template <class R>
-__global__ void __launch_bounds__(128) k_adjoint(StepView<R> V, int nsteps, int ckpt, Params6 th6,
-                                                 double *cks, double *seg, bool grad, double *partial) {
+template <class Pp>
+__global__ void __launch_bounds__(128) k_adjoint(StepView<Pp> V, const BedP<double> *bpd, int nsteps, int ckpt,
+                                                 Params6 th6, double *cks, double *seg, bool grad, double *partial) {
   __shared__ double sh[7][128];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
   if (i < V.n) {
     Par P;
     double s[8], sn[8];
-    load_par(V, i, P, s);
+    load_par(V, bpd, i, P, s);
     const double *th = th6.v;
     const int ore = P.ore;
     const double f0 = fov(s + 4, ore);
@@ -419,7 +417,7 @@ __global__ void __launch_bounds__(128) k_adjoint(StepView<R> V, int nsteps, int 
 
 }  // namespace
 
-template <class R>
+template <class Pp>
 int run_adjoint(dem_ctx *c, int nsteps, int ckpt, double *J, double *grad) {
   const bool want_grad = grad != nullptr;
   const int n = c->n;
@@ -436,10 +434,10 @@ int run_adjoint(dem_ctx *c, int nsteps, int ckpt, double *J, double *grad) {
   double *cks = c->adj;
   double *seg = cks + (want_grad ? (size_t)nseg * 8 * n : 0);
   double *partial = seg + (want_grad ? (size_t)ckpt * 8 * n : 0);
-  StepView<R> V = make_view<R>(c, false);
+  StepView<Pp> V = make_view<Pp>(c, false);
   Params6 th;
-  for (int r = 0; r < 3; ++r) { th.v[r] = c->hbeds[0].k0[r]; th.v[3 + r] = c->hbeds[0].Ea[r]; }
-  k_adjoint<R><<<grid, bs, 0, c->st>>>(V, nsteps, ckpt, th, cks, seg, want_grad, partial);
+  for (int r = 0; r < 3; ++r) { th.v[r] = c->cfg[0].k0[r]; th.v[3 + r] = c->cfg[0].Ea[r]; }
+  k_adjoint<Pp><<<grid, bs, 0, c->st>>>(V, c->dbp_d, nsteps, ckpt, th, cks, seg, want_grad, partial);
   if (cudaPeekAtLastError() != cudaSuccess) return DEM_ECUDA;
   std::vector<double> h((size_t)grid * 7);
   if (cudaMemcpyAsync(h.data(), partial, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
@@ -454,7 +452,8 @@ int run_adjoint(dem_ctx *c, int nsteps, int ckpt, double *J, double *grad) {
   return DEM_OK;
 }
 
-template int run_adjoint<double>(dem_ctx *, int, int, double *, double *);
-template int run_adjoint<float>(dem_ctx *, int, int, double *, double *);
+template int run_adjoint<PrecF64>(dem_ctx *, int, int, double *, double *);
+template int run_adjoint<PrecSplit>(dem_ctx *, int, int, double *, double *);
+template int run_adjoint<PrecKahan>(dem_ctx *, int, int, double *, double *);
 
 }  // namespace dem

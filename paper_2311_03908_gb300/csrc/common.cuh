@@ -1,8 +1,12 @@
 // common.cuh -- device-side constants, per-bed parameters and the physics of one parcel.
 //
-// Everything here is templated on R, the arithmetic type of forces, drag, heat and
-// kinetics: double for the all-FP64 form, float for the split form. Positions, layer
-// masses and cell-source sums are always double.
+// The arithmetic of forces, drag, heat and kinetics follows a precision policy P:
+//   PrecF64   -- everything in FP64 (the all-FP64 form);
+//   PrecSplit -- FP32 physics; FP64 positions, layer masses and cell-source sums;
+//   PrecKahan -- as PrecSplit, but masses and cell sums as Kahan-compensated FP32 pairs.
+// GB300 issues only a few FP64 operations per SM per clock, so in the FP32 forms every
+// constant and table is prepared in FP32 on the host and the device code avoids FP64
+// except where a result accumulates (positions, masses, cell sums, the gas state).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -15,6 +19,10 @@ constexpr int KMAX = DEM_MAX_CONTACTS;
 constexpr double kPI = 3.14159265358979323846;
 constexpr double kRgas = 8.314;  // gas constant of Sec. 2.1
 constexpr double kGrav = 9.81;
+
+struct PrecF64 { using R = double; static constexpr bool kahan = false; static constexpr bool exact = true; };
+struct PrecSplit { using R = float; static constexpr bool kahan = false; static constexpr bool exact = false; };
+struct PrecKahan { using R = float; static constexpr bool kahan = true; static constexpr bool exact = false; };
 
 enum : int { ERR_CAPACITY = 1, ERR_NONFINITE = 2, ERR_DOMAIN = 4, ERR_TIMEOUT = 8 };
 
@@ -38,43 +46,57 @@ enum : int {
 };
 static_assert((int)DG_N == (int)DEM_NDIAG, "diag rows");
 
-// Bed parameters as the kernels need them (derived once on the host at dem_init).
+// Geometry of a bed in FP64 (positions, grid, walls, gas state). The gas cells are also
+// the cell list of the contact search (init checks that no parcel is wider than a cell).
 struct DevBed {
-  // gas grid: cell of a point = floor((x - x0) * inv_dx), clamped
-  double x0, y0, z0, dx, dy, dz, inv_dx, inv_dy, inv_dz, vcell;
-  int nx, ny, nz, s;            // s = DEM sub-cells per gas-cell edge
-  long long cell_off;           // first global gas cell of this bed
-  unsigned key_off;             // first global DEM-cell key of this bed
-  float pf_margin;              // FP32 prefilter margin of the pair test, m
-  // walls
-  double R, H, cos_a, sin_a, z_apex, plate_z, pitch, r_hole;
+  double x0, y0, z0, dx, dy, dz, inv_dx, inv_dy, inv_dz, vcell, inv_vcell;
+  int nx, ny, nz;
+  long long cell_off;           // first global gas cell (and sort key) of this bed
+  double R_bed, H, cos_a, sin_a, z_apex, plate_z, pitch, inv_pitch, r_hole;
   int wall;
-  // contact law
-  double dt, kn, kt, eta_coef, eta_t_ratio, mu_s, mu_r;
-  double k, k3;
+  double dt, k;
   int ncouple;
-  // gas
-  double U_in, T_in, p0, Y_in[3];
-  double fuller12, fuller13;    // T- and p-free parts of eq (2-26)
-  // kinetics
-  double k0[3], Ea[3], tau;
-  double psi[2], K1b[2], K2[2]; // Ganser constants per ore (K1 without the wall term)
-  double xi[2][3];              // product-layer porosity per ore: m, w, Fe (eqs (2-31)..(2-36))
-  double pore_cm[2];
-  double dpdz, eps_min, bedD;
+  double U_in, T_in, p0, Y_in[3], eps_min;
   unsigned flags;
 };
 
+// Physics parameters of a bed in the form's arithmetic type R (prepared on the host).
+template <class R> struct BedP {
+  R k, k3, inv_k3, dt, half_dt, kn, kt, eta_coef, eta_t_ratio, mu_s, mu_r;
+  R x0, y0, z0, dx, dy, dz, inv_dx, inv_dy, inv_dz;   // grid (cell-local coordinates)
+  R R_bed, H, cos_a, sin_a, z_apex, plate_z, pitch, inv_pitch, r_hole;   // walls
+  R U_in, p0, T_in, Y_in[3], eps_min, inv_vcell;
+  R k0[3], Ea_R[3], inv_tau;
+  R psi[2], K1b[2], K2[2], wall_K1;   // Ganser constants; wall_K1 = 2.25 / D
+  R xi[2][3];                   // product-layer porosity per ore: m, w, Fe (eqs (2-31)..(2-36))
+  R pore_cm[2], DKc[2];         // pore diameter (cm) and 0.97 r_a of eq (2-28)
+  R fuller12, fuller13, mfp_c;  // eq (2-26) without T and p; 1.013 / p of Sec. 2.3
+  R rate_c;                     // pi p0 / R_g (molar-rate prefactor of eq (2-1) without d^2 / T)
+  R dpdz, grav, dtg;
+  R pf_margin;                  // prefilter margin of the exact (FP64) pair test, m
+  unsigned flags;
+  int ncouple, wall;
+};
+
+// Constant tables in the form's arithmetic type.
+template <class R> struct Tab {
+  R Mz[4], Mj[3], Ka[3], Kb[3], RMz[4], RMj[3];   // molar masses, Table 2, R_g / M
+  R nasaT[7];
+  R h[7][2][6];                 // Table C1: a1, a2/2, a3/3, a4/4, a5/5, a6 (enthalpy / R)
+  R cp[7][2][5];                // Table C1: a1..a5 (heat capacity / R)
+  R dcp[7][2][4];               // derivative of the heat-capacity polynomial
+  R visc[3][3], cond[3][5];     // Tables C2, C3
+};
+
 // Molar masses (kg/mol): solids Fe2O3, Fe3O4, FeO, Fe; gases H2, H2O, N2.
-__device__ __constant__ static const double cMz[4] = {159.69e-3, 231.533e-3, 71.844e-3, 55.845e-3};
-__device__ __constant__ static const double cMj[3] = {2.016e-3, 18.015e-3, 28.014e-3};
-// Table 2 equilibrium constants K = exp(a / T + b)
-__device__ __constant__ static const double cKa[3] = {1433.4, -7393.9, -2023.8};
-__device__ __constant__ static const double cKb[3] = {9.08, 7.56, 1.24};
+constexpr double kMz[4] = {159.69e-3, 231.533e-3, 71.844e-3, 55.845e-3};
+constexpr double kMj[3] = {2.016e-3, 18.015e-3, 28.014e-3};
+constexpr double kKa[3] = {1433.4, -7393.9, -2023.8};   // Table 2: K_eq = exp(a / T + b)
+constexpr double kKb[3] = {9.08, 7.56, 1.24};
 // Table C1, two ranges per species (H2, H2O, N2, Fe2O3, Fe3O4, FeO, Fe); the Fe ranges
 // 1000-1184 K are represented by the 298-1000 K range (see the design notes)
-__device__ __constant__ static const double cNasaT[7] = {1000.0, 1000.0, 1000.0, 960.0, 850.0, 1000.0, 1184.0};
-__device__ __constant__ static const double cNasa[7][2][6] = {
+constexpr double kNasaT[7] = {1000.0, 1000.0, 1000.0, 960.0, 850.0, 1000.0, 1184.0};
+constexpr double kNasa[7][2][6] = {
   {{2.3443, 7.98e-3, -1.95e-5, 2.02e-8, -7.38e-12, -9.179e2}, {2.9328, 8.27e-4, -1.46e-7, 1.54e-11, -6.89e-16, -8.131e2}},
   {{4.1986, -2.04e-3, 6.52e-6, -5.49e-9, 1.77e-12, -3.03e4}, {2.677, 2.97e-3, -7.74e-7, 9.44e-11, -4.27e-15, -2.989e4}},
   {{3.531, -1.24e-4, -5.03e-7, 2.44e-9, -1.41e-12, -1.047e3}, {2.9526, 1.40e-3, -4.93e-7, 7.86e-11, -4.61e-15, -9.239e2}},
@@ -83,86 +105,111 @@ __device__ __constant__ static const double cNasa[7][2][6] = {
   {{5.3195, 2.21e-3, 1.07e-6, -2.79e-9, 1.33e-12, -3.441e4}, {5.8316, 1.43e-3, -9.32e-8, -6.6e-12, -2.25e-14, -3.457e4}},
   {{2.4134, -1.58e-3, 2.15e-5, -3.8e-8, 2.20e-11, -774.38}, {61.011, -0.161, 1.68e-4, -7.75e-8, 1.33e-11, -1.65e4}},
 };
-// Table C2 viscosity, Table C3 conductivity
-__device__ __constant__ static const double cVisc[3][3] = {
-  {2.85e-6, 2.16e-8, -3.78e-12}, {-4.44e-6, 4.52e-8, -3.20e-12}, {7.86e-6, 3.87e-8, -5.11e-12}};
-__device__ __constant__ static const double cCond[3][5] = {
-  {3.07e-3, 8.09e-4, -8.52e-7, 7.2e-10, -2.21e-13},
-  {6.84e-3, 6.25e-6, 1.31e-7, -5.99e-11, 1.12e-14},
-  {2.51e-3, 8.92e-5, -4.00e-8, 1.62e-11, -2.61e-15}};
+constexpr double kVisc[3][3] = {{2.85e-6, 2.16e-8, -3.78e-12}, {-4.44e-6, 4.52e-8, -3.20e-12}, {7.86e-6, 3.87e-8, -5.11e-12}};
+constexpr double kCond[3][5] = {{3.07e-3, 8.09e-4, -8.52e-7, 7.2e-10, -2.21e-13},
+                                {6.84e-3, 6.25e-6, 1.31e-7, -5.99e-11, 1.12e-14},
+                                {2.51e-3, 8.92e-5, -4.00e-8, 1.62e-11, -2.61e-15}};
+
+template <class R> constexpr Tab<R> make_tab() {
+  Tab<R> t{};
+  for (int z = 0; z < 4; ++z) { t.Mz[z] = (R)kMz[z]; t.RMz[z] = (R)(kRgas / kMz[z]); }
+  for (int j = 0; j < 3; ++j) { t.Mj[j] = (R)kMj[j]; t.RMj[j] = (R)(kRgas / kMj[j]); }
+  for (int r = 0; r < 3; ++r) { t.Ka[r] = (R)kKa[r]; t.Kb[r] = (R)kKb[r]; }
+  for (int s = 0; s < 7; ++s) {
+    t.nasaT[s] = (R)kNasaT[s];
+    for (int g = 0; g < 2; ++g) {
+      const double *a = kNasa[s][g];
+      t.h[s][g][0] = (R)a[0];
+      t.h[s][g][1] = (R)(a[1] / 2.0);
+      t.h[s][g][2] = (R)(a[2] / 3.0);
+      t.h[s][g][3] = (R)(a[3] / 4.0);
+      t.h[s][g][4] = (R)(a[4] / 5.0);
+      t.h[s][g][5] = (R)a[5];
+      for (int k = 0; k < 5; ++k) t.cp[s][g][k] = (R)a[k];
+      for (int k = 0; k < 4; ++k) t.dcp[s][g][k] = (R)((k + 1) * a[k + 1]);
+    }
+  }
+  for (int j = 0; j < 3; ++j) {
+    for (int k = 0; k < 3; ++k) t.visc[j][k] = (R)kVisc[j][k];
+    for (int k = 0; k < 5; ++k) t.cond[j][k] = (R)kCond[j][k];
+  }
+  return t;
+}
+
+static __constant__ Tab<float> cTabF = make_tab<float>();
+static __constant__ Tab<double> cTabD = make_tab<double>();
+template <class R> __device__ __forceinline__ const Tab<R> &tab();
+template <> __device__ __forceinline__ const Tab<float> &tab<float>() { return cTabF; }
+template <> __device__ __forceinline__ const Tab<double> &tab<double>() { return cTabD; }
 
 // ---------------------------------------------------------------------------------------
 // Thermochemistry (eqs (3-22), (3-23)): molar enthalpy / R and molar heat capacity / R.
 // Species index s: 0 H2, 1 H2O, 2 N2, 3 Fe2O3, 4 Fe3O4, 5 FeO, 6 Fe.
 // ---------------------------------------------------------------------------------------
-template <class R>
-__device__ __forceinline__ R h_over_R(int s, R T) {
-  const int r = (double)T <= cNasaT[s] ? 0 : 1;
-  const double *a = cNasa[s][r];
-  const R c1 = (R)a[0], c2 = (R)(a[1] * 0.5), c3 = (R)(a[2] * (1.0 / 3.0)), c4 = (R)(a[3] * 0.25),
-          c5 = (R)(a[4] * 0.2);
-  return T * (c1 + T * (c2 + T * (c3 + T * (c4 + T * c5)))) + (R)a[5];
+template <class R> __device__ __forceinline__ R h_over_R(int s, R T) {
+  const Tab<R> &t = tab<R>();
+  const R *a = t.h[s][T <= t.nasaT[s] ? 0 : 1];
+  return T * (a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])))) + a[5];
 }
-template <class R>
-__device__ __forceinline__ R cp_over_R(int s, R T) {
-  const int r = (double)T <= cNasaT[s] ? 0 : 1;
-  const double *a = cNasa[s][r];
-  return (R)a[0] + T * ((R)a[1] + T * ((R)a[2] + T * ((R)a[3] + T * (R)a[4])));
+template <class R> __device__ __forceinline__ R cp_over_R(int s, R T) {
+  const Tab<R> &t = tab<R>();
+  const R *a = t.cp[s][T <= t.nasaT[s] ? 0 : 1];
+  return a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
+}
+template <class R> __device__ __forceinline__ R dcp_over_R(int s, R T) {
+  const Tab<R> &t = tab<R>();
+  const R *a = t.dcp[s][T <= t.nasaT[s] ? 0 : 1];
+  return a[0] + T * (a[1] + T * (a[2] + T * a[3]));
 }
 
 // ---------------------------------------------------------------------------------------
-// Gas-cell properties (eqs (2-1-1), (2-1-2), (2-26)..(2-29), (3-53)..(3-59)) computed once
-// per cell in double and stored in R: the parcel kernels then read finished numbers.
+// Gas-cell properties (eqs (2-1-1), (2-1-2), (2-26)..(2-29), (3-53)..(3-59)), once per cell.
 // ---------------------------------------------------------------------------------------
-struct CellProps {
-  double rho, mu, lam, cp, x, Dm, sc13, pr13, epow, D[2], uz, eps, T;
+template <class R> struct CellProps {
+  R rho, mu, lam, cp, x, Dm, sc13, pr13, epow, D[2], uz, eps, T;
 };
 
-// Computed in the form's arithmetic type P (double in the FP64 form, float in the split
-// form: GB300's FP64 rate is a small fraction of its FP32 rate); the gas state itself and
-// the cell sums stay FP64.
-template <class P>
-__device__ inline CellProps gas_cell_props(const DevBed &B, double eps_d, const double Yd[3], double Td) {
-  CellProps o;
-  const P p = (P)B.p0, T = (P)Td, eps = (P)eps_d;
-  const P Y[3] = {(P)Yd[0], (P)Yd[1], (P)Yd[2]};
-  const P inv = Y[0] / (P)cMj[0] + Y[1] / (P)cMj[1] + Y[2] / (P)cMj[2];
-  const P Mg = (P)1 / inv;
-  const P xp0 = Y[0] * Mg / (P)cMj[0], xp1 = Y[1] * Mg / (P)cMj[1], xp2 = Y[2] * Mg / (P)cMj[2];
-  const P den = xp0 + xp1;
-  const P x = den > (P)0 ? xp0 / den : (P)0;
-  const P rho = Mg * p / ((P)kRgas * T);
-  P mu = 0, lam = 0, cp = 0;
+template <class R>
+__device__ inline CellProps<R> gas_cell_props(const BedP<R> &B, R eps, const R Y[3], R T) {
+  const Tab<R> &t = tab<R>();
+  CellProps<R> o;
+  const R p = B.p0;
+  const R inv = Y[0] / t.Mj[0] + Y[1] / t.Mj[1] + Y[2] / t.Mj[2];
+  const R Mg = (R)1 / inv;
+  const R xp0 = Y[0] * Mg / t.Mj[0], xp1 = Y[1] * Mg / t.Mj[1], xp2 = Y[2] * Mg / t.Mj[2];
+  const R den = xp0 + xp1;
+  o.x = den > (R)0 ? xp0 / den : (R)0;
+  o.rho = Mg * p / ((R)kRgas * T);
+  R mu = 0, lam = 0, cp = 0;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    mu += Y[j] * ((P)cVisc[j][0] + T * ((P)cVisc[j][1] + T * (P)cVisc[j][2]));
-    lam += Y[j] * ((P)cCond[j][0] + T * ((P)cCond[j][1] + T * ((P)cCond[j][2] + T * ((P)cCond[j][3] + T * (P)cCond[j][4]))));
-    cp += Y[j] * cp_over_R<P>(j, T) * (P)(kRgas / cMj[j]);
+    mu += Y[j] * (t.visc[j][0] + T * (t.visc[j][1] + T * t.visc[j][2]));
+    lam += Y[j] * (t.cond[j][0] + T * (t.cond[j][1] + T * (t.cond[j][2] + T * (t.cond[j][3] + T * t.cond[j][4]))));
+    cp += Y[j] * cp_over_R<R>(j, T) * t.RMj[j];
   }
+  o.mu = mu; o.lam = lam; o.cp = cp;
   // Fuller binary coefficients D(H2,H2O), D(H2,N2) (T^1.75 = T sqrt(T) sqrt(sqrt(T))) and
-  // Wilke's rule for H2
-  const P sT = sqrt(T);
-  const P tf = T * sT * sqrt(sT) * ((P)101325 / p) * (P)1e-7;
-  const P D12 = tf * (P)B.fuller12, D13 = tf * (P)B.fuller13;
-  const P rest = (P)1 - xp0;
-  const P Dm = rest < (P)1e-12 ? D12 : rest / (xp1 / D12 + xp2 / D13);
-  o.rho = rho; o.mu = mu; o.lam = lam; o.cp = cp; o.x = x; o.Dm = Dm;
-  o.sc13 = cbrt(mu / (rho * Dm));
+  // Wilke's rule for H2 (its 0/0 limit in pure H2 is the binary coefficient)
+  const R sT = sqrt(T);
+  const R tf = T * sT * sqrt(sT) * ((R)101325 / p) * (R)1e-7;
+  const R D12 = tf * B.fuller12, D13 = tf * B.fuller13;
+  const R rest = (R)1 - xp0;
+  o.Dm = rest < (R)1e-12 ? D12 : rest / (xp1 / D12 + xp2 / D13);
+  o.sc13 = cbrt(mu / (o.rho * o.Dm));
   o.pr13 = cbrt(cp * mu / lam);
-  o.epow = exp((P)-2.65 * log(eps));
+  o.epow = exp((R)-2.65 * log(eps));
   // pore diffusion per ore: molecular, Knudsen, or Bosanquet by lambda / d_a (Sec. 2.3)
-  const P mfp = x > (P)0 ? (P)1.013 / (p * x) : (P)3e38;
-  const P sq = sqrt(T / (P)(cMj[0] * 1e3));
+  const R mfp = o.x > (R)0 ? B.mfp_c / o.x : (R)3e38;
+  const R sq = sqrt(T / (t.Mj[0] * (R)1e3));
 #pragma unroll
   for (int ore = 0; ore < 2; ++ore) {
-    const P da = (P)B.pore_cm[ore];
-    const P DK = (P)0.97 * ((P)0.5 * da) * sq;
-    const P ratio = mfp / da;
-    o.D[ore] = ratio <= (P)0.01 ? Dm : (ratio >= (P)10 ? DK : (P)1 / ((P)1 / Dm + (P)1 / DK));
+    const R DK = B.DKc[ore] * sq;
+    const R ratio = mfp / B.pore_cm[ore];
+    o.D[ore] = ratio <= (R)0.01 ? o.Dm : (ratio >= (R)10 ? DK : (R)1 / ((R)1 / o.Dm + (R)1 / DK));
   }
-  o.uz = (P)B.U_in / eps;
-  o.eps = eps_d;
-  o.T = Td;
+  o.uz = B.U_in / eps;
+  o.eps = eps;
+  o.T = T;
   return o;
 }
 
@@ -186,13 +233,13 @@ template <class R> __device__ __forceinline__ R gunn(R eps, R re02, R re07, R c1
 // Gidaspow-Ganser drag coefficient divided by the solid fraction (eqs (3-5-2)..(3-5-5)):
 // F_d = (beta / eps_p) V_p (u_g - v_p), the form of eq (3-5) with eps_p cancelled.
 template <class R>
-__device__ __forceinline__ R beta_over_epsp(const DevBed &B, int ore, R d, const Gas<R> &g, R slip, R Re) {
+__device__ __forceinline__ R beta_over_epsp(const BedP<R> &B, int ore, R d, const Gas<R> &g, R slip, R Re) {
   const R eps = g.eps, ep = (R)1 - eps;
-  const R psi = (R)B.psi[ore];
+  const R psi = B.psi[ore];
   if (eps < (R)0.8)
     return (R)150 * ep * g.mu / (eps * d * d * psi * psi) + (R)1.75 * eps * g.rho * slip / (d * psi * ep);
-  const R K1 = (R)B.K1b[ore] - (R)2.25 * d / (R)B.bedD;
-  const R K2 = (R)B.K2[ore];
+  const R K1 = B.K1b[ore] - B.wall_K1 * d;
+  const R K2 = B.K2[ore];
   if (Re > (R)0) {
     const R RK = Re * (K1 * K2);
     const R CD = (R)24 / (Re * K1) * ((R)1 + (R)0.1118 * pos_pow(RK, (R)0.6567)) +
@@ -213,18 +260,18 @@ template <class R> struct KinOut {
 };
 
 template <class R>
-__device__ __forceinline__ void uscm(const DevBed &Bd, const double m[4], R Tp, R d, int ore,
+__device__ __forceinline__ void uscm(const BedP<R> &Bd, const R m[4], R Tp, R d, int ore,
                                      const Gas<R> &g, R re02, R re07, R dtm, KinOut<R> &o) {
+  const Tab<R> &t = tab<R>();
   const unsigned fl = Bd.flags;
 #pragma unroll
   for (int r = 0; r < 3; ++r) { o.xidot[r] = 0; o.A[r] = 0; o.B[r] = 0; }
 #pragma unroll
   for (int z = 0; z < 4; ++z) o.mdot[z] = 0;
   o.sH2 = o.sH2O = o.Qr = o.Qrm = o.EQ = o.ES = o.F = o.Sh = 0;
-  const R inv_k3 = (R)(1.0 / Bd.k3);
   R n[4];
 #pragma unroll
-  for (int z = 0; z < 4; ++z) n[z] = (R)m[z] * inv_k3 / (R)cMz[z];
+  for (int z = 0; z < 4; ++z) n[z] = m[z] * Bd.inv_k3 / t.Mz[z];
   const R nfe = (R)2 * n[0] + (R)3 * n[1] + n[2] + n[3];
   if (!(nfe > (R)0)) return;
   const R inv_nfe = (R)1 / nfe;
@@ -239,31 +286,29 @@ __device__ __forceinline__ void uscm(const DevBed &Bd, const double m[4], R Tp, 
   const bool kin = !(fl & DEM_NO_KINETICS);
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    const R K = exp((R)cKa[r] * invT + (R)cKb[r]);                 // Table 2
-    xeq[r] = (R)1 / (K + (R)1);                                       // eq (2-1-3)
-    const R kr = (R)Bd.k0[r] * exp(-(R)(Bd.Ea[r] / kRgas) * invT);    // eq (2-13)
+    const R K = exp(t.Ka[r] * invT + t.Kb[r]);                 // Table 2
+    xeq[r] = (R)1 / (K + (R)1);                                  // eq (2-1-3)
+    const R kr = Bd.k0[r] * exp(-Bd.Ea_R[r] * invT);             // eq (2-13)
     c3[r] = cbrt(om[r]);
-    act[r] = kin && n[r] > (R)0 && g.x > xeq[r] && Bd.k0[r] > 0.0;
+    act[r] = kin && n[r] > (R)0 && g.x > xeq[r] && Bd.k0[r] > (R)0;
     // 1/A of eq (2-12): k_r (1-f)^(2/3) (1 + K)/K
     gk[r] = act[r] ? kr * c3[r] * c3[r] * ((R)1 + (R)1 / K) : (R)0;
   }
   // product-layer resistances, eq (2-14), with D_eff of eq (2-30)
-  const R D = g.D;
-  const R rp = (R)0.5 * d;
+  const R rp_tau = (R)0.5 * d / (g.D * Bd.inv_tau);
   R Bm = 0, Bw = 0, BFe = 0;
   if (!(fl & DEM_NO_LAYER)) {
-    const R inv_tau = (R)(1.0 / Bd.tau);
-    if (act[0]) Bm = rp / (D * (R)Bd.xi[ore][0] * inv_tau) * ((R)1 / c3[0] - (R)1 / c3[1]);
-    if ((act[0] || act[1]) && om[1] > (R)0) Bw = rp / (D * (R)Bd.xi[ore][1] * inv_tau) * ((R)1 / c3[1] - (R)1 / c3[2]);
-    if (om[2] > (R)0) BFe = rp / (D * (R)Bd.xi[ore][2] * inv_tau) * ((R)1 / c3[2] - (R)1);
+    if (act[0]) Bm = rp_tau / Bd.xi[ore][0] * ((R)1 / c3[0] - (R)1 / c3[1]);
+    if ((act[0] || act[1]) && om[1] > (R)0) Bw = rp_tau / Bd.xi[ore][1] * ((R)1 / c3[1] - (R)1 / c3[2]);
+    if (om[2] > (R)0) BFe = rp_tau / Bd.xi[ore][2] * ((R)1 / c3[2] - (R)1);
   }
   // gas film, eqs (2-20)..(2-24)
   o.Sh = gunn(g.eps, re02, re07, g.sc13);
   const R F = (fl & DEM_NO_FILM) ? (R)0 : d / (o.Sh * g.Dm);
-  // closed-form network; a reaction whose flux is negative is dropped and the rest re-solved
-  const R S = F + BFe, BwS = Bw + S;
 #pragma unroll
   for (int r = 0; r < 3; ++r) o.A[r] = gk[r] > (R)0 ? (R)1 / gk[r] : (R)0;
+  // closed-form network; a reaction whose flux is negative is dropped and the rest re-solved
+  const R S = F + BFe, BwS = Bw + S;
   R J[3] = {0, 0, 0}, vsum[3] = {0, 0, 0};
   for (int it = 0; it < 3; ++it) {
     const R g1 = gk[0], g2 = gk[1], g3 = gk[2];
@@ -290,31 +335,30 @@ __device__ __forceinline__ void uscm(const DevBed &Bd, const double m[4], R Tp, 
     if (!neg) break;
   }
   // molar rates per real particle (eq (2-1), eta = 1), limited by the reactant present
-  const R c = (R)kPI * d * d * (R)Bd.p0 * invT * (R)(1.0 / kRgas);
+  const R c = Bd.rate_c * d * d * invT;
   const R inv_dtm = (R)1 / dtm;
-  const R nu[3] = {3, 1, 1};
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     R x = gk[r] > (R)0 ? c * J[r] : (R)0;
-    const R cap = n[r] / nu[r] * inv_dtm;
+    const R cap = n[r] / (r == 0 ? (R)3 : (R)1) * inv_dtm;
     x = x < cap ? x : cap;
     o.xidot[r] = x > (R)0 ? x : (R)0;
   }
-  const R k3 = (R)Bd.k3;
-  o.mdot[0] = -(R)3 * o.xidot[0] * (R)cMz[0] * k3;
-  o.mdot[1] = ((R)2 * o.xidot[0] - o.xidot[1]) * (R)cMz[1] * k3;
-  o.mdot[2] = ((R)3 * o.xidot[1] - o.xidot[2]) * (R)cMz[2] * k3;
-  o.mdot[3] = o.xidot[2] * (R)cMz[3] * k3;
+  const R k3 = Bd.k3;
+  o.mdot[0] = -(R)3 * o.xidot[0] * t.Mz[0] * k3;
+  o.mdot[1] = ((R)2 * o.xidot[0] - o.xidot[1]) * t.Mz[1] * k3;
+  o.mdot[2] = ((R)3 * o.xidot[1] - o.xidot[2]) * t.Mz[2] * k3;
+  o.mdot[3] = o.xidot[2] * t.Mz[3] * k3;
   const R tot = o.xidot[0] + o.xidot[1] + o.xidot[2];
-  o.sH2 = -tot * (R)cMj[0] * k3;
-  o.sH2O = tot * (R)cMj[1] * k3;
+  o.sH2 = -tot * t.Mj[0] * k3;
+  o.sH2O = tot * t.Mj[1] * k3;
   if (!(fl & DEM_NO_RXN_HEAT)) {
     // eqs (3-19), (3-21) at T_p, with H in J/kg = R h / M
     R qr = 0;
 #pragma unroll
-    for (int z = 0; z < 4; ++z) qr += h_over_R(3 + z, Tp) * (R)(kRgas / cMz[z]) * o.mdot[z];
+    for (int z = 0; z < 4; ++z) qr += h_over_R<R>(3 + z, Tp) * t.RMz[z] * o.mdot[z];
     o.Qr = -qr;
-    o.Qrm = -(h_over_R(0, Tp) * (R)(kRgas / cMj[0]) * o.sH2 + h_over_R(1, Tp) * (R)(kRgas / cMj[1]) * o.sH2O);
+    o.Qrm = -(h_over_R<R>(0, Tp) * t.RMj[0] * o.sH2 + h_over_R<R>(1, Tp) * t.RMj[1] * o.sH2O);
   }
   const R E = k3 * (R)kPI * d * d * invT;
   o.EQ = E * (vsum[0] + vsum[1] + vsum[2]);
@@ -330,12 +374,12 @@ __device__ __forceinline__ void uscm(const DevBed &Bd, const double m[4], R Tp, 
 // velocity of the parcel relative to the partner.
 // ---------------------------------------------------------------------------------------
 template <class R>
-__device__ __forceinline__ void contact_force(const DevBed &B, R mstar, R ri, const R n[3], R delta,
+__device__ __forceinline__ void contact_force(const BedP<R> &B, R mstar, R ri, const R n[3], R delta,
                                               const R vrel[3], const R xo[3], const R w[3],
                                               R F[3], R Tq[3], R xn[3]) {
-  const R kn = (R)B.kn, kt = (R)B.kt;
-  const R eta_n = (R)B.eta_coef * sqrt(mstar * kn);
-  const R eta_t = eta_n * (R)B.eta_t_ratio;
+  const R kn = B.kn, kt = B.kt;
+  const R eta_n = B.eta_coef * sqrt(mstar * kn);
+  const R eta_t = eta_n * B.eta_t_ratio;
   const R vn = vrel[0] * n[0] + vrel[1] * n[1] + vrel[2] * n[2];
   R vt[3];
 #pragma unroll
@@ -352,7 +396,7 @@ __device__ __forceinline__ void contact_force(const DevBed &B, R mstar, R ri, co
 #pragma unroll
     for (int q = 0; q < 3; ++q) xr[q] *= sc;
   }
-  const R dt = (R)B.dt;
+  const R dt = B.dt;
   R ft[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
@@ -360,7 +404,7 @@ __device__ __forceinline__ void contact_force(const DevBed &B, R mstar, R ri, co
     ft[q] = -kt * xn[q] - eta_t * vt[q];
   }
   const R ftm = sqrt(ft[0] * ft[0] + ft[1] * ft[1] + ft[2] * ft[2]);
-  const R cap = (R)B.mu_s * fabs(fn);
+  const R cap = B.mu_s * fabs(fn);
   if (ftm > cap) {
     const R sc = cap / ftm;
 #pragma unroll
@@ -374,10 +418,10 @@ __device__ __forceinline__ void contact_force(const DevBed &B, R mstar, R ri, co
   Tq[0] = ri * (n[1] * ft[2] - n[2] * ft[1]);
   Tq[1] = ri * (n[2] * ft[0] - n[0] * ft[2]);
   Tq[2] = ri * (n[0] * ft[1] - n[1] * ft[0]);
-  if (B.mu_r > 0.0) {
+  if (B.mu_r > (R)0) {
     const R wm = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
     if (wm > (R)0) {
-      const R c = (R)B.mu_r * fabs(fn) / wm;
+      const R c = B.mu_r * fabs(fn) / wm;
 #pragma unroll
       for (int q = 0; q < 3; ++q) Tq[q] -= c * w[q];
     }
@@ -385,48 +429,87 @@ __device__ __forceinline__ void contact_force(const DevBed &B, R mstar, R ri, co
 }
 
 // Distances from a parcel centre to the four wall primitives (side, bottom or cone,
-// plate, lid) and unit normals pointing from the wall to the centre; 1e300 = absent.
-__device__ inline void wall_primitives(const DevBed &B, double x, double y, double z,
-                                       double dist[4], double nw[4][3]) {
+// plate, lid) and unit normals pointing from the wall to the centre; 1e30 = absent.
+// T is double for the overlap of a touching wall and float for the pre-screen.
+template <class T, class G>
+__device__ __forceinline__ void wall_primitives(const G &B, T x, T y, T z, T dist[4], T nw[4][3]) {
 #pragma unroll
-  for (int p = 0; p < 4; ++p) { dist[p] = 1e300; nw[p][0] = nw[p][1] = nw[p][2] = 0.0; }
-  const double rho = sqrt(x * x + y * y);
-  if (rho > 0.0) {
-    dist[0] = B.R - rho;
+  for (int p = 0; p < 4; ++p) { dist[p] = (T)1e30; nw[p][0] = nw[p][1] = nw[p][2] = (T)0; }
+  const T rho = sqrt(x * x + y * y);
+  if (rho > (T)0) {
+    dist[0] = (T)B.R_bed - rho;
     nw[0][0] = -x / rho;
     nw[0][1] = -y / rho;
   }
   if (B.wall == DEM_WALL_FLAT) {
     dist[1] = z;
-    nw[1][2] = 1.0;
+    nw[1][2] = (T)1;
   } else {
-    if (z < B.plate_z) {   // the cone acts below the distributor plate
-      dist[1] = (z - B.z_apex) * B.sin_a - rho * B.cos_a;
-      if (rho > 0.0) { nw[1][0] = -B.cos_a * x / rho; nw[1][1] = -B.cos_a * y / rho; }
-      else nw[1][0] = -B.cos_a;
-      nw[1][2] = B.sin_a;
+    if (z < (T)B.plate_z) {   // the cone acts below the distributor plate
+      dist[1] = (z - (T)B.z_apex) * (T)B.sin_a - rho * (T)B.cos_a;
+      if (rho > (T)0) { nw[1][0] = -(T)B.cos_a * x / rho; nw[1][1] = -(T)B.cos_a * y / rho; }
+      else nw[1][0] = -(T)B.cos_a;
+      nw[1][2] = (T)B.sin_a;
     }
-    const double hx = floor(x / B.pitch + 0.5) * B.pitch;
-    const double hy = floor(y / B.pitch + 0.5) * B.pitch;
-    const double ex = x - hx, ey = y - hy, ez = z - B.plate_z;
-    const double q = sqrt(ex * ex + ey * ey);
-    if (q >= B.r_hole) {
+    const T hx = floor(x * (T)B.inv_pitch + (T)0.5) * (T)B.pitch;
+    const T hy = floor(y * (T)B.inv_pitch + (T)0.5) * (T)B.pitch;
+    const T ex = x - hx, ey = y - hy, ez = z - (T)B.plate_z;
+    const T q = sqrt(ex * ex + ey * ey);
+    if (q >= (T)B.r_hole) {
       dist[2] = fabs(ez);
-      nw[2][2] = ez >= 0.0 ? 1.0 : -1.0;
+      nw[2][2] = ez >= (T)0 ? (T)1 : (T)-1;
     } else {
-      double ux = 1.0, uy = 0.0;
-      if (q > 0.0) { ux = ex / q; uy = ey / q; }
-      const double rx = -(B.r_hole - q) * ux, ry = -(B.r_hole - q) * uy;
-      const double dd = sqrt(rx * rx + ry * ry + ez * ez);
+      T ux = (T)1, uy = (T)0;
+      if (q > (T)0) { ux = ex / q; uy = ey / q; }
+      const T rx = -((T)B.r_hole - q) * ux, ry = -((T)B.r_hole - q) * uy;
+      const T dd = sqrt(rx * rx + ry * ry + ez * ez);
       dist[2] = dd;
-      if (dd > 0.0) { nw[2][0] = rx / dd; nw[2][1] = ry / dd; nw[2][2] = ez / dd; }
-      else nw[2][2] = 1.0;
+      if (dd > (T)0) { nw[2][0] = rx / dd; nw[2][1] = ry / dd; nw[2][2] = ez / dd; }
+      else nw[2][2] = (T)1;
     }
   }
-  dist[3] = B.H - z;
-  nw[3][2] = -1.0;
+  dist[3] = (T)B.H - z;
+  nw[3][2] = (T)-1;
 }
 
 __device__ __forceinline__ void set_error(int *err, int bit) { atomicOr(err, bit); }
+
+// ---------------------------------------------------------------------------------------
+// Layer masses: FP64 values (FP64 and split forms) or Kahan pairs (value, compensation) of
+// FP32 stored in the same 8-byte slot (split-Kahan form).
+// ---------------------------------------------------------------------------------------
+template <class P> __device__ __forceinline__ typename P::R mass_r(const double *m, int i) {
+  if constexpr (P::kahan) {
+    const float2 v = reinterpret_cast<const float2 *>(m)[i];
+    return v.x + v.y;
+  } else {
+    return (typename P::R)m[i];
+  }
+}
+template <class P> __device__ __forceinline__ double mass_d(const double *m, int i) {
+  if constexpr (P::kahan) {
+    const float2 v = reinterpret_cast<const float2 *>(m)[i];
+    return (double)v.x + (double)v.y;
+  } else {
+    return m[i];
+  }
+}
+// m += inc, not below zero (Kahan-compensated in the split-Kahan form)
+template <class P> __device__ __forceinline__ void mass_add(double *m, int i, typename P::R inc) {
+  if constexpr (P::kahan) {
+    // value = hi + lo; lo carries what the FP32 sum hi could not hold (compensated summation,
+    // Kahan 1965, with the compensation stored with the opposite sign)
+    float2 v = reinterpret_cast<float2 *>(m)[i];
+    const float y = inc + v.y;
+    const float t = v.x + y;
+    v.y = y - (t - v.x);
+    v.x = t;
+    if (v.x + v.y < 0.0f) { v.x = 0.0f; v.y = 0.0f; }
+    reinterpret_cast<float2 *>(m)[i] = v;
+  } else {
+    const double mn = m[i] + (double)inc;
+    m[i] = mn > 0.0 ? mn : 0.0;
+  }
+}
 
 }  // namespace dem

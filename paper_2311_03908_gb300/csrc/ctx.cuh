@@ -11,13 +11,15 @@
 struct dem_ctx {
   int n = 0, cap = 0, nbeds = 0, prec = DEM_PREC_FP64;
   long long ncells = 0;
-  unsigned long long nkeys = 0;
   int key_bits = 1;
-  bool gas_alias = true;            // every bed has s == 1: gas ranges are the DEM ranges
   cudaStream_t st = nullptr;
   std::vector<dem::DevBed> hbeds;
+  std::vector<dem::BedP<double>> hbp_d;
+  std::vector<dem::BedP<float>> hbp_f;
   std::vector<dem_bed_config> cfg;
   dem::DevBed *dbeds = nullptr;
+  dem::BedP<double> *dbp_d = nullptr;
+  dem::BedP<float> *dbp_f = nullptr;
   // one device arena
   char *arena = nullptr;
   size_t arena_bytes = 0;
@@ -34,9 +36,8 @@ struct dem_ctx {
   // binning
   unsigned *keys = nullptr, *vals = nullptr, *keys2 = nullptr, *vals2 = nullptr, *rhist = nullptr;
   unsigned *kres = nullptr, *vres = nullptr;   // where the last sort left its result
-  unsigned *cstart = nullptr, *cend = nullptr, *gstart = nullptr, *gend = nullptr;
-  int *gcell = nullptr;
-  float4 *xf = nullptr;
+  unsigned *cstart = nullptr, *cend = nullptr;
+  float4 *xl = nullptr;
   void *mass = nullptr, *F[3] = {}, *Tq[3] = {}, *src = nullptr;
   // gas: two state buffers (gcur = current), properties, marks
   double *gas[2] = {};
@@ -76,19 +77,25 @@ struct dem_ctx {
 
 namespace dem {
 
-template <class R> StepView<R> make_view(dem_ctx *c, bool for_step);
-template <class R> int enqueue_steps(dem_ctx *c, int nsteps);
-template <class R> int enqueue_init(dem_ctx *c);
-template <class R> int enqueue_fov(dem_ctx *c, double *per_parcel_dev);
-template <class R> int enqueue_scatter_state(dem_ctx *c, double *out_dev);
-template <class R> int enqueue_scatter_diag(dem_ctx *c, double *out_dev);
-template <class R> int enqueue_scatter_hist(dem_ctx *c, int *cnt, int *partner, double *xi);
-template <class R> int enqueue_sources(dem_ctx *c);
-template <class R> int run_adjoint(dem_ctx *c, int nsteps, int ckpt, double *J, double *grad);
-template <class R> int enqueue_props(dem_ctx *c);
+template <class P> StepView<P> make_view(dem_ctx *c, bool for_step);
+template <class P> int enqueue_steps(dem_ctx *c, int nsteps);
+template <class P> int enqueue_init(dem_ctx *c);
+template <class P> int enqueue_fov(dem_ctx *c, double *per_parcel_dev);
+template <class P> int enqueue_scatter_state(dem_ctx *c, double *out_dev);
+template <class P> int enqueue_scatter_diag(dem_ctx *c, double *out_dev);
+template <class P> int enqueue_scatter_hist(dem_ctx *c, int *cnt, int *partner, double *xi);
+template <class P> int enqueue_sources(dem_ctx *c);
+template <class P> int enqueue_props(dem_ctx *c);
+template <class P> int run_adjoint(dem_ctx *c, int nsteps, int ckpt, double *J, double *grad);
 
 // event pair around one kernel when profiling is on (returns the start-event slot or -1)
 int prof_begin(dem_ctx *c, const char *name);
 void prof_end(dem_ctx *c, int slot);
+
+// call FN<P>(args...) with the context's precision policy P
+#define DEM_DISPATCH(c, FN, ...)                                                         \
+  ((c)->prec == DEM_PREC_FP64 ? FN<::dem::PrecF64>(__VA_ARGS__)                         \
+                              : (c)->prec == DEM_PREC_SPLIT ? FN<::dem::PrecSplit>(__VA_ARGS__) \
+                                                            : FN<::dem::PrecKahan>(__VA_ARGS__))
 
 }  // namespace dem

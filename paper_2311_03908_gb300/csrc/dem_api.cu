@@ -24,29 +24,38 @@ __global__ void k_mark_cells(const DevBed *beds, const int *cell_bed, unsigned c
   const double xc = B.x0 + (ix + 0.5) * B.dx, yc = B.y0 + (iy + 0.5) * B.dy, zc = B.z0 + (iz + 0.5) * B.dz;
   const double hd = 0.5 * sqrt(B.dx * B.dx + B.dy * B.dy + B.dz * B.dz);
   const double rho = sqrt(xc * xc + yc * yc);
-  double sd = B.R - rho;
+  double sd = B.R_bed - rho;
   if (B.wall == DEM_WALL_CONE) sd = fmin(sd, (zc - B.z_apex) * B.sin_a - rho * B.cos_a);
   mark[c] = sd < -hd ? 1 : 0;
 }
 
 // Initial parcel state in input order (accelerations start as gravity, spins at rest).
-template <class R>
+template <class P>
 __global__ void k_load(int n, const double *const *src /* 8 + 4 arrays */, const int *ore,
                        const int *bed, const DevBed *beds, double *x, double *y, double *z,
-                       R *vx, R *vy, R *vz, R *wx, R *wy, R *wz, R *ax, R *ay, R *az, R *alx,
-                       R *aly, R *alz, R *T, R *d, double *m0, double *m1, double *m2, double *m3,
-                       int *meta, int *orig) {
+                       typename P::R *const *rv /* v3 w3 a3 al3 T d */, double *const *m, int *meta, int *orig) {
+  using R = typename P::R;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   x[i] = src[0][i]; y[i] = src[1][i]; z[i] = src[2][i];
-  vx[i] = (R)src[3][i]; vy[i] = (R)src[4][i]; vz[i] = (R)src[5][i];
-  d[i] = (R)src[6][i]; T[i] = (R)src[7][i];
-  m0[i] = src[8][i]; m1[i] = src[9][i]; m2[i] = src[10][i]; m3[i] = src[11][i];
-  wx[i] = wy[i] = wz[i] = (R)0;
-  alx[i] = aly[i] = alz[i] = (R)0;
-  ax[i] = ay[i] = (R)0;
+  for (int q = 0; q < 3; ++q) {
+    rv[q][i] = (R)src[3 + q][i];
+    rv[3 + q][i] = (R)0;
+    rv[6 + q][i] = (R)0;
+    rv[9 + q][i] = (R)0;
+  }
   const DevBed &B = beds[bed[i]];
-  az[i] = (B.flags & DEM_NO_GRAVITY) ? (R)0 : (R)(-kGrav);
+  rv[8][i] = (B.flags & DEM_NO_GRAVITY) ? (R)0 : (R)(-kGrav);
+  rv[12][i] = (R)src[7][i];
+  rv[13][i] = (R)src[6][i];
+  for (int q = 0; q < 4; ++q) {
+    if constexpr (P::kahan) {
+      const float hi = (float)src[8 + q][i];
+      reinterpret_cast<float2 *>(m[q])[i] = make_float2(hi, (float)(src[8 + q][i] - (double)hi));
+    } else {
+      m[q][i] = src[8 + q][i];
+    }
+  }
   meta[i] = (bed[i] << 8) | ore[i];
   orig[i] = i;
 }
@@ -104,7 +113,7 @@ namespace {
 
 using namespace dem;
 
-constexpr double kMzH[4] = {159.69e-3, 231.533e-3, 71.844e-3, 55.845e-3};
+const double kMzH[4] = {159.69e-3, 231.533e-3, 71.844e-3, 55.845e-3};
 
 #define CK(call)                                           \
   do {                                                     \
@@ -202,35 +211,68 @@ DevBed derive_bed(const dem_bed_config &b) {
   B.dx = b.bed_D / b.nx; B.dy = b.bed_D / b.ny; B.dz = b.bed_H / b.nz;
   B.inv_dx = 1.0 / B.dx; B.inv_dy = 1.0 / B.dy; B.inv_dz = 1.0 / B.dz;
   B.vcell = B.dx * B.dy * B.dz;
-  B.s = 1;
-  B.pf_margin = (float)(16.0 * std::max(b.bed_D, b.bed_H) * 5.96e-8);
-  B.R = 0.5 * b.bed_D; B.H = b.bed_H; B.wall = b.wall_kind;
+  B.inv_vcell = 1.0 / B.vcell;
+  B.R_bed = 0.5 * b.bed_D; B.H = b.bed_H; B.wall = b.wall_kind;
   B.cos_a = std::cos(b.cone_half_angle); B.sin_a = std::sin(b.cone_half_angle);
-  B.z_apex = b.wall_kind == DEM_WALL_CONE ? b.cone_height - B.R / std::tan(b.cone_half_angle) : 0.0;
-  B.plate_z = b.plate_z; B.pitch = b.hole_pitch > 0 ? b.hole_pitch : 1.0; B.r_hole = 0.5 * b.hole_d;
-  B.dt = b.dt; B.kn = b.kn; B.kt = b.kt_over_kn * b.kn;
-  const double le = std::log(b.restitution);
-  B.eta_coef = -2.0 * le / std::sqrt(kPI * kPI + le * le);
-  B.eta_t_ratio = std::sqrt(b.kt_over_kn);
-  B.mu_s = b.mu_s; B.mu_r = b.mu_r;
-  B.k = b.cg_ratio; B.k3 = b.cg_ratio * b.cg_ratio * b.cg_ratio;
+  B.z_apex = b.wall_kind == DEM_WALL_CONE ? b.cone_height - B.R_bed / std::tan(b.cone_half_angle) : 0.0;
+  B.plate_z = b.plate_z; B.pitch = b.hole_pitch > 0 ? b.hole_pitch : 1.0; B.inv_pitch = 1.0 / B.pitch;
+  B.r_hole = 0.5 * b.hole_d;
+  B.dt = b.dt; B.k = b.cg_ratio;
   B.ncouple = b.coupling_interval;
   B.U_in = b.U_in; B.T_in = b.T_in; B.p0 = b.p0;
   for (int j = 0; j < 3; ++j) B.Y_in[j] = b.Y_in[j];
-  B.fuller12 = fuller_const(2.016, 18.015, 7.07, 12.7);
-  B.fuller13 = fuller_const(2.016, 28.014, 7.07, 17.9);
-  for (int r = 0; r < 3; ++r) { B.k0[r] = b.k0[r]; B.Ea[r] = b.Ea[r]; }
-  B.tau = b.tortuosity;
+  B.eps_min = b.eps_min;
+  B.flags = b.flags;
+  return B;
+}
+
+// Physics parameters of a bed, computed in FP64 and stored in the form's type.
+template <class R>
+BedP<R> derive_params(const dem_bed_config &b, const DevBed &G) {
+  BedP<R> P;
+  std::memset(&P, 0, sizeof P);
+  P.k = (R)b.cg_ratio; P.k3 = (R)(b.cg_ratio * b.cg_ratio * b.cg_ratio);
+  P.inv_k3 = (R)(1.0 / (b.cg_ratio * b.cg_ratio * b.cg_ratio));
+  P.dt = (R)b.dt; P.half_dt = (R)(0.5 * b.dt);
+  P.kn = (R)b.kn; P.kt = (R)(b.kt_over_kn * b.kn);
+  const double le = std::log(b.restitution);
+  P.eta_coef = (R)(-2.0 * le / std::sqrt(kPI * kPI + le * le));
+  P.eta_t_ratio = (R)std::sqrt(b.kt_over_kn);
+  P.mu_s = (R)b.mu_s; P.mu_r = (R)b.mu_r;
+  P.x0 = (R)G.x0; P.y0 = (R)G.y0; P.z0 = (R)G.z0;
+  P.dx = (R)G.dx; P.dy = (R)G.dy; P.dz = (R)G.dz;
+  P.inv_dx = (R)G.inv_dx; P.inv_dy = (R)G.inv_dy; P.inv_dz = (R)G.inv_dz;
+  P.R_bed = (R)G.R_bed; P.H = (R)G.H; P.cos_a = (R)G.cos_a; P.sin_a = (R)G.sin_a; P.z_apex = (R)G.z_apex;
+  P.plate_z = (R)G.plate_z; P.pitch = (R)G.pitch; P.inv_pitch = (R)G.inv_pitch; P.r_hole = (R)G.r_hole;
+  P.U_in = (R)b.U_in; P.p0 = (R)b.p0; P.T_in = (R)b.T_in;
+  for (int j = 0; j < 3; ++j) P.Y_in[j] = (R)b.Y_in[j];
+  P.eps_min = (R)b.eps_min; P.inv_vcell = (R)G.inv_vcell;
+  for (int r = 0; r < 3; ++r) { P.k0[r] = (R)b.k0[r]; P.Ea_R[r] = (R)(b.Ea[r] / kRgas); }
+  P.inv_tau = (R)(1.0 / b.tortuosity);
   for (int o = 0; o < 2; ++o) {
     const double psi = b.sphericity[o];
-    B.psi[o] = psi;
-    B.K1b[o] = 1.0 / (1.0 / 3.0 + (2.0 / 3.0) / std::sqrt(psi));
-    B.K2[o] = std::pow(10.0, 1.8148 * std::pow(-std::log10(psi), 0.5743));
-    layer_porosity_host(b, o, B.xi[o]);
-    B.pore_cm[o] = b.pore_d_cm[o];
+    P.psi[o] = (R)psi;
+    P.K1b[o] = (R)(1.0 / (1.0 / 3.0 + (2.0 / 3.0) / std::sqrt(psi)));
+    P.K2[o] = (R)std::pow(10.0, 1.8148 * std::pow(-std::log10(psi), 0.5743));
+    double xi[3];
+    layer_porosity_host(b, o, xi);
+    for (int l = 0; l < 3; ++l) P.xi[o][l] = (R)xi[l];
+    P.pore_cm[o] = (R)b.pore_d_cm[o];
+    P.DKc[o] = (R)(0.97 * 0.5 * b.pore_d_cm[o]);
   }
-  B.dpdz = b.dpdz; B.eps_min = b.eps_min; B.bedD = b.bed_D; B.flags = b.flags;
-  return B;
+  P.wall_K1 = (R)(2.25 / b.bed_D);
+  P.fuller12 = (R)fuller_const(2.016, 18.015, 7.07, 12.7);
+  P.fuller13 = (R)fuller_const(2.016, 28.014, 7.07, 17.9);
+  P.mfp_c = (R)(1.013 / b.p0);
+  P.rate_c = (R)(kPI * b.p0 / kRgas);
+  P.dpdz = (R)b.dpdz;
+  P.grav = (b.flags & DEM_NO_GRAVITY) ? (R)0 : (R)(-kGrav);
+  P.dtg = (R)(b.coupling_interval * b.dt);
+  P.pf_margin = (R)1e-8;
+  P.flags = b.flags;
+  P.ncouple = b.coupling_interval;
+  P.wall = b.wall_kind;
+  return P;
 }
 
 struct Bump {
@@ -265,10 +307,8 @@ void layout(dem_ctx *c, Bump &m) {
   c->keys = m.take<unsigned>(N); c->vals = m.take<unsigned>(N);
   c->keys2 = m.take<unsigned>(N); c->vals2 = m.take<unsigned>(N);
   c->rhist = m.take<unsigned>(radix_hist_words((int)N));
-  c->cstart = m.take<unsigned>(c->nkeys); c->cend = m.take<unsigned>(c->nkeys);
-  if (!c->gas_alias) { c->gstart = m.take<unsigned>(C); c->gend = m.take<unsigned>(C); }
-  c->gcell = m.take<int>(N);
-  c->xf = m.take<float4>(N);
+  c->cstart = m.take<unsigned>(C); c->cend = m.take<unsigned>(C);
+  c->xl = m.take<float4>(N);
   c->mass = m.take<char>(N, R);
   for (int q = 0; q < 3; ++q) { c->F[q] = m.take<char>(N, R); c->Tq[q] = m.take<char>(N, R); }
   c->src = m.take<char>(N * SR_N, R);
@@ -282,13 +322,11 @@ void layout(dem_ctx *c, Bump &m) {
   c->err = m.take<int>(1);
   c->step_ctr = m.take<long long>(1);
   c->dbeds = m.take<DevBed>(c->nbeds);
+  c->dbp_d = m.take<BedP<double>>(c->nbeds);
+  c->dbp_f = m.take<BedP<float>>(c->nbeds);
 }
 
-template <class R> int dispatch_steps(dem_ctx *c, int n) { return enqueue_steps<R>(c, n); }
-
-int enqueue_steps_any(dem_ctx *c, int n) {
-  return c->prec == DEM_PREC_FP64 ? enqueue_steps<double>(c, n) : enqueue_steps<float>(c, n);
-}
+int enqueue_steps_any(dem_ctx *c, int n) { return DEM_DISPATCH(c, enqueue_steps, c, n); }
 
 }  // namespace
 
@@ -390,8 +428,8 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
   c->rsize = precision == DEM_PREC_FP64 ? sizeof(double) : sizeof(float);
   c->st = (cudaStream_t)cuda_stream;
   c->cfg.assign(beds, beds + n_beds);
-  // per-bed constants, grid offsets and the DEM sub-division
-  unsigned long long koff = 0;
+  // per-bed constants and grid offsets; the gas cells are the cell list of the contact
+  // search, so no parcel may be wider than a cell edge
   long long coff = 0;
   for (int b = 0; b < n_beds; ++b) {
     DevBed B = derive_bed(beds[b]);
@@ -399,23 +437,16 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
     if (nb[b] > 0 && dmax[b] > edge) { delete c; return DEM_EINVAL; }
     // stability of the stiffest contact: omega_0 dt < 2 with m* = m_min / 2
     if (nb[b] > 0 && std::sqrt(beds[b].kn / (0.5 * mmin[b])) * beds[b].dt >= 2.0) { delete c; return DEM_EINVAL; }
-    const long long ng = (long long)B.nx * B.ny * B.nz;
-    int s = nb[b] > 0 ? std::max(1, (int)std::floor(edge / dmax[b])) : 1;
-    const double budget = std::max((double)ng, 64.0 * (double)nb[b]);
-    while (s > 1 && (double)ng * s * s * s > budget) --s;
-    B.s = s;
     B.cell_off = coff;
-    B.key_off = (unsigned)koff;
-    koff += (unsigned long long)ng * s * s * s;
-    coff += ng;
-    if (s != 1) c->gas_alias = false;
+    coff += (long long)B.nx * B.ny * B.nz;
     c->hbeds.push_back(B);
+    c->hbp_d.push_back(derive_params<double>(beds[b], B));
+    c->hbp_f.push_back(derive_params<float>(beds[b], B));
   }
-  if (koff >= (1ULL << 32)) { delete c; return DEM_EINVAL; }
-  c->nkeys = koff;
+  if (coff >= (1LL << 31)) { delete c; return DEM_EINVAL; }
   c->ncells = coff;
   c->key_bits = 1;
-  while ((1ULL << c->key_bits) < koff) ++c->key_bits;
+  while ((1LL << c->key_bits) < coff) ++c->key_bits;
   // arena
   Bump meas;
   layout(c, meas);
@@ -430,6 +461,8 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
   int rc = DEM_OK;
   auto ck = [&](cudaError_t e) { if (e != cudaSuccess && rc == DEM_OK) rc = e == cudaErrorMemoryAllocation ? DEM_ENOMEM : DEM_ECUDA; };
   ck(cudaMemcpyAsync(c->dbeds, c->hbeds.data(), sizeof(DevBed) * n_beds, cudaMemcpyHostToDevice, c->st));
+  ck(cudaMemcpyAsync(c->dbp_d, c->hbp_d.data(), sizeof(BedP<double>) * n_beds, cudaMemcpyHostToDevice, c->st));
+  ck(cudaMemcpyAsync(c->dbp_f, c->hbp_f.data(), sizeof(BedP<float>) * n_beds, cudaMemcpyHostToDevice, c->st));
   // staging copies of the inputs (freed at the end of init)
   double *dsrc = nullptr;
   int *dint = nullptr;
@@ -447,18 +480,24 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
   ck(cudaMemcpyAsync(dint + n, hbed.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->st));
   ck(cudaMemcpyAsync(dptrs, hp, sizeof(hp), cudaMemcpyHostToDevice, c->st));
   const int bs = 256, gridn = (n + bs - 1) / bs;
-  if (c->prec == DEM_PREC_FP64) {
-    k_load<double><<<gridn, bs, 0, c->st>>>(n, dptrs, dint, dint + n, c->dbeds, c->px[0][0], c->px[0][1], c->px[0][2],
-        (double *)c->pv[0][0], (double *)c->pv[0][1], (double *)c->pv[0][2], (double *)c->pw[0][0], (double *)c->pw[0][1],
-        (double *)c->pw[0][2], (double *)c->pa[0][0], (double *)c->pa[0][1], (double *)c->pa[0][2], (double *)c->pal[0][0],
-        (double *)c->pal[0][1], (double *)c->pal[0][2], (double *)c->pT[0], (double *)c->pd[0], c->pm[0][0], c->pm[0][1],
-        c->pm[0][2], c->pm[0][3], c->pmeta[0], c->porig[0]);
-  } else {
-    k_load<float><<<gridn, bs, 0, c->st>>>(n, dptrs, dint, dint + n, c->dbeds, c->px[0][0], c->px[0][1], c->px[0][2],
-        (float *)c->pv[0][0], (float *)c->pv[0][1], (float *)c->pv[0][2], (float *)c->pw[0][0], (float *)c->pw[0][1],
-        (float *)c->pw[0][2], (float *)c->pa[0][0], (float *)c->pa[0][1], (float *)c->pa[0][2], (float *)c->pal[0][0],
-        (float *)c->pal[0][1], (float *)c->pal[0][2], (float *)c->pT[0], (float *)c->pd[0], c->pm[0][0], c->pm[0][1],
-        c->pm[0][2], c->pm[0][3], c->pmeta[0], c->porig[0]);
+  void **drv = nullptr;   // 14 state-row pointers and 4 mass pointers for k_load
+  ck(cudaMalloc(&drv, sizeof(void *) * 18));
+  {
+    void *hrv[18] = {c->pv[0][0], c->pv[0][1], c->pv[0][2], c->pw[0][0], c->pw[0][1], c->pw[0][2],
+                     c->pa[0][0], c->pa[0][1], c->pa[0][2], c->pal[0][0], c->pal[0][1], c->pal[0][2],
+                     c->pT[0], c->pd[0], c->pm[0][0], c->pm[0][1], c->pm[0][2], c->pm[0][3]};
+    ck(cudaMemcpyAsync(drv, hrv, sizeof(hrv), cudaMemcpyHostToDevice, c->st));
+  }
+  if (rc == DEM_OK) {
+    if (c->prec == DEM_PREC_FP64)
+      k_load<PrecF64><<<gridn, bs, 0, c->st>>>(n, dptrs, dint, dint + n, c->dbeds, c->px[0][0], c->px[0][1], c->px[0][2],
+                                               (double *const *)drv, (double *const *)(drv + 14), c->pmeta[0], c->porig[0]);
+    else if (c->prec == DEM_PREC_SPLIT)
+      k_load<PrecSplit><<<gridn, bs, 0, c->st>>>(n, dptrs, dint, dint + n, c->dbeds, c->px[0][0], c->px[0][1], c->px[0][2],
+                                                 (float *const *)drv, (double *const *)(drv + 14), c->pmeta[0], c->porig[0]);
+    else
+      k_load<PrecKahan><<<gridn, bs, 0, c->st>>>(n, dptrs, dint, dint + n, c->dbeds, c->px[0][0], c->px[0][1], c->px[0][2],
+                                                 (float *const *)drv, (double *const *)(drv + 14), c->pmeta[0], c->porig[0]);
   }
   ck(cudaMemsetAsync(c->hcnt[0], 0, (size_t)n, c->st));
   ck(cudaMemsetAsync(c->hcnt[1], 0, (size_t)n, c->st));
@@ -505,13 +544,14 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
   c->cur = 0;
   c->gcur = 0;
   if (rc == DEM_OK) {
-    int e = c->prec == DEM_PREC_FP64 ? enqueue_init<double>(c) : enqueue_init<float>(c);
+    int e = DEM_DISPATCH(c, enqueue_init, c);
     if (e) rc = DEM_ECUDA;
   }
   ck(cudaStreamSynchronize(c->st));
   cudaFree(dsrc);
   cudaFree(dint);
   cudaFree(dptrs);
+  cudaFree(drv);
   if (rc == DEM_OK) {
     int herr = 0;
     ck(cudaMemcpy(&herr, c->err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -581,12 +621,15 @@ int dem_set_kinetics(dem_ctx *c, const double k0[3], const double Ea[3]) {
   for (int b = 0; b < c->nbeds; ++b)
     for (int r = 0; r < 3; ++r) {
       if (!(k0[r] >= 0 && Ea[r] >= 0)) return DEM_EINVAL;
-      c->hbeds[b].k0[r] = k0[r];
-      c->hbeds[b].Ea[r] = Ea[r];
+      c->hbp_d[b].k0[r] = k0[r];
+      c->hbp_d[b].Ea_R[r] = Ea[r] / kRgas;
+      c->hbp_f[b].k0[r] = (float)k0[r];
+      c->hbp_f[b].Ea_R[r] = (float)(Ea[r] / kRgas);
       c->cfg[b].k0[r] = k0[r];
       c->cfg[b].Ea[r] = Ea[r];
     }
-  CK(cudaMemcpyAsync(c->dbeds, c->hbeds.data(), sizeof(DevBed) * c->nbeds, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->dbp_d, c->hbp_d.data(), sizeof(BedP<double>) * c->nbeds, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->dbp_f, c->hbp_f.data(), sizeof(BedP<float>) * c->nbeds, cudaMemcpyHostToDevice, c->st));
   CK(cudaStreamSynchronize(c->st));
   return DEM_OK;
 }
@@ -605,7 +648,7 @@ int dem_reduction_degree(dem_ctx *c, double *mean_per_bed, double *oxygen_per_be
   if (!c || !mean_per_bed) return DEM_EINVAL;
   int s = sync_all(c);
   if (s != DEM_OK) return s;
-  int e = c->prec == DEM_PREC_FP64 ? enqueue_fov<double>(c, per_parcel) : enqueue_fov<float>(c, per_parcel);
+  int e = DEM_DISPATCH(c, enqueue_fov, c, per_parcel);
   if (e) return DEM_ECUDA;
   std::vector<double> hb((size_t)c->nbeds * 4);
   CK(cudaMemcpyAsync(hb.data(), c->fvbed, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, c->st));
@@ -624,8 +667,7 @@ int dem_get_state(dem_ctx *c, double *out_host) {
   if (s != DEM_OK) return s;
   const size_t bytes = sizeof(double) * DEM_NSTATE * (size_t)c->n;
   if ((s = ensure_scratch(c, bytes)) != DEM_OK) return s;
-  int e = c->prec == DEM_PREC_FP64 ? enqueue_scatter_state<double>(c, c->scratch_out)
-                                   : enqueue_scatter_state<float>(c, c->scratch_out);
+  int e = DEM_DISPATCH(c, enqueue_scatter_state, c, c->scratch_out);
   if (e) return DEM_ECUDA;
   CK(cudaMemcpyAsync(out_host, c->scratch_out, bytes, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
@@ -656,7 +698,7 @@ int dem_get_sources(dem_ctx *c, double *out_host) {
   int s = sync_all(c);
   if (s != DEM_OK) return s;
   if (!c->dep && cudaMalloc(&c->dep, sizeof(double) * SR_N * (size_t)c->ncells) != cudaSuccess) return DEM_ENOMEM;
-  int e = c->prec == DEM_PREC_FP64 ? enqueue_sources<double>(c) : enqueue_sources<float>(c);
+  int e = DEM_DISPATCH(c, enqueue_sources, c);
   if (e) return DEM_ECUDA;
   CK(cudaMemcpyAsync(out_host, c->dep, sizeof(double) * SR_N * (size_t)c->ncells, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
@@ -674,8 +716,7 @@ int dem_get_contacts(dem_ctx *c, int32_t *count, int32_t *partner, double *xi) {
   double *dxi = (double *)base;
   int *dcnt = (int *)(base + n * KMAX * 3 * sizeof(double));
   int *dpart = dcnt + n;
-  int e = c->prec == DEM_PREC_FP64 ? enqueue_scatter_hist<double>(c, dcnt, dpart, dxi)
-                                   : enqueue_scatter_hist<float>(c, dcnt, dpart, dxi);
+  int e = DEM_DISPATCH(c, enqueue_scatter_hist, c, dcnt, dpart, dxi);
   if (e) return DEM_ECUDA;
   CK(cudaMemcpyAsync(count, dcnt, n * sizeof(int), cudaMemcpyDeviceToHost, c->st));
   CK(cudaMemcpyAsync(partner, dpart, n * KMAX * sizeof(int), cudaMemcpyDeviceToHost, c->st));
@@ -728,8 +769,7 @@ int dem_get_diag(dem_ctx *c, double *out_host) {
   if (s != DEM_OK) return s;
   const size_t bytes = sizeof(double) * DG_N * (size_t)c->n;
   if ((s = ensure_scratch(c, bytes)) != DEM_OK) return s;
-  int e = c->prec == DEM_PREC_FP64 ? enqueue_scatter_diag<double>(c, c->scratch_out)
-                                   : enqueue_scatter_diag<float>(c, c->scratch_out);
+  int e = DEM_DISPATCH(c, enqueue_scatter_diag, c, c->scratch_out);
   if (e) return DEM_ECUDA;
   CK(cudaMemcpyAsync(out_host, c->scratch_out, bytes, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
@@ -752,7 +792,7 @@ int dem_set_gas(dem_ctx *c, const dem_gas *g) {
     T = c->gas_stage + 3 * nc;
   }
   k_gas_set<<<(int)((nc + 255) / 256), 256, 0, c->st>>>((long long)nc, Y, T, c->gas[c->gcur]);
-  int e = c->prec == DEM_PREC_FP64 ? enqueue_props<double>(c) : enqueue_props<float>(c);
+  int e = DEM_DISPATCH(c, enqueue_props, c);
   if (e) return c->sticky = DEM_ECUDA;
   return DEM_OK;
 }
@@ -802,8 +842,7 @@ int dem_adjoint(dem_ctx *c, int32_t n_steps, int32_t ckpt_every, double *J, doub
   if (!c || !J || n_steps < 0 || ckpt_every < 1) return DEM_EINVAL;
   int s = sync_all(c);
   if (s != DEM_OK) return s;
-  return c->prec == DEM_PREC_FP64 ? run_adjoint<double>(c, n_steps, ckpt_every, J, grad)
-                                  : run_adjoint<float>(c, n_steps, ckpt_every, J, grad);
+  return DEM_DISPATCH(c, run_adjoint, c, n_steps, ckpt_every, J, grad);
 }
 
 }  // extern "C"

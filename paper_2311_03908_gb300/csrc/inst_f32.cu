@@ -2,5 +2,5 @@
 // layer masses and cell sums.
 #include "launch.cuh"
 namespace dem {
-DEM_INSTANTIATE(float)
+DEM_INSTANTIATE(PrecSplit)
 }

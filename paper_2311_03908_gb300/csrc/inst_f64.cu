@@ -1,5 +1,5 @@
 // inst_f64.cu -- the all-FP64 form of the per-step kernels.
 #include "launch.cuh"
 namespace dem {
-DEM_INSTANTIATE(double)
+DEM_INSTANTIATE(PrecF64)
 }

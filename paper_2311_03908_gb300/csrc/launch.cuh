@@ -8,26 +8,28 @@ namespace dem {
 
 inline int grid_for(long long n, int bs) { return (int)((n + bs - 1) / bs); }
 
-template <class R>
-StepView<R> make_view(dem_ctx *c, bool for_step) {
-  StepView<R> V;
+template <class P>
+StepView<P> make_view(dem_ctx *c, bool for_step) {
+  using R = typename P::R;
+  StepView<P> V;
   V.n = c->n;
   V.cap = c->cap;
   V.nbeds = c->nbeds;
   V.ncells = c->ncells;
   V.beds = c->dbeds;
+  if constexpr (sizeof(R) == 8) V.bp = c->dbp_d; else V.bp = c->dbp_f;
   const int a = c->cur, b = for_step ? 1 - c->cur : c->cur;
-  auto fill = [&](PState<R> &P, int k) {
-    P.x = c->px[k][0]; P.y = c->px[k][1]; P.z = c->px[k][2];
+  auto fill = [&](PState<R> &Pp, int k) {
+    Pp.x = c->px[k][0]; Pp.y = c->px[k][1]; Pp.z = c->px[k][2];
     for (int q = 0; q < 3; ++q) {
-      P.v[q] = (R *)c->pv[k][q]; P.w[q] = (R *)c->pw[k][q];
-      P.a[q] = (R *)c->pa[k][q]; P.al[q] = (R *)c->pal[k][q];
+      Pp.v[q] = (R *)c->pv[k][q]; Pp.w[q] = (R *)c->pw[k][q];
+      Pp.a[q] = (R *)c->pa[k][q]; Pp.al[q] = (R *)c->pal[k][q];
     }
-    P.T = (R *)c->pT[k];
-    P.d = (R *)c->pd[k];
-    for (int q = 0; q < 4; ++q) P.m[q] = c->pm[k][q];
-    P.meta = c->pmeta[k];
-    P.orig = c->porig[k];
+    Pp.T = (R *)c->pT[k];
+    Pp.d = (R *)c->pd[k];
+    for (int q = 0; q < 4; ++q) Pp.m[q] = c->pm[k][q];
+    Pp.meta = c->pmeta[k];
+    Pp.orig = c->porig[k];
   };
   fill(V.A, a);
   fill(V.B, b);
@@ -36,10 +38,7 @@ StepView<R> make_view(dem_ctx *c, bool for_step) {
   V.keys = c->kres ? c->kres : c->keys;
   V.vals = c->vres ? c->vres : c->vals;
   V.cstart = c->cstart; V.cend = c->cend;
-  V.gstart = c->gas_alias ? c->cstart : c->gstart;
-  V.gend = c->gas_alias ? c->cend : c->gend;
-  V.gcell = c->gcell;
-  V.xf = c->xf;
+  V.xl = c->xl;
   V.mass = (R *)c->mass;
   for (int q = 0; q < 3; ++q) { V.F[q] = (R *)c->F[q]; V.Tq[q] = (R *)c->Tq[q]; }
   V.src = (R *)c->src;
@@ -56,14 +55,14 @@ StepView<R> make_view(dem_ctx *c, bool for_step) {
 }
 
 // binning: keys of the (drifted) positions, radix sort, gather into the sorted order
-template <class R>
+template <class P>
 int enqueue_binning(dem_ctx *c, int drift) {
   cudaStream_t st = c->st;
-  StepView<R> V = make_view<R>(c, true);
+  StepView<P> V = make_view<P>(c, true);
   V.keys = c->keys;
   V.vals = c->vals;
   int ps = prof_begin(c, "k_key");
-  k_key<R><<<grid_for(c->n, c->bs_key), c->bs_key, 0, st>>>(V, drift);
+  k_key<P><<<grid_for(c->n, c->bs_key), c->bs_key, 0, st>>>(V, drift);
   prof_end(c, ps);
   ++c->launches;
   unsigned *kr = nullptr, *vr = nullptr;
@@ -76,38 +75,30 @@ int enqueue_binning(dem_ctx *c, int drift) {
   c->vres = vr;
   V.keys = kr;
   V.vals = vr;
-  cudaMemsetAsync(c->cstart, 0, sizeof(unsigned) * c->nkeys, st);
-  cudaMemsetAsync(c->cend, 0, sizeof(unsigned) * c->nkeys, st);
-  if (!c->gas_alias) {
-    cudaMemsetAsync(c->gstart, 0, sizeof(unsigned) * c->ncells, st);
-    cudaMemsetAsync(c->gend, 0, sizeof(unsigned) * c->ncells, st);
-  }
+  cudaMemsetAsync(c->cstart, 0, sizeof(unsigned) * c->ncells, st);
+  cudaMemsetAsync(c->cend, 0, sizeof(unsigned) * c->ncells, st);
   ps = prof_begin(c, "k_gather");
-  k_gather<R><<<grid_for(c->n, c->bs_gather), c->bs_gather, 0, st>>>(V, drift);
+  k_gather<P><<<grid_for(c->n, c->bs_gather), c->bs_gather, 0, st>>>(V, drift);
   prof_end(c, ps);
   ++c->launches;
-  if (!c->gas_alias) {
-    k_gas_ranges<R><<<grid_for(c->n, 256), 256, 0, st>>>(V);
-    ++c->launches;
-  }
   return (int)cudaPeekAtLastError();
 }
 
-template <class R>
+template <class P>
 int enqueue_steps(dem_ctx *c, int nsteps) {
   cudaStream_t st = c->st;
   for (int s = 0; s < nsteps; ++s) {
-    int e = enqueue_binning<R>(c, 1);
+    int e = enqueue_binning<P>(c, 1);
     if (e) return e;
-    StepView<R> V = make_view<R>(c, true);
+    StepView<P> V = make_view<P>(c, true);
     int ps = prof_begin(c, "k_contacts");
-    k_contacts<R><<<grid_for(c->n, c->bs_contacts), c->bs_contacts, 0, st>>>(V);
+    k_contacts<P><<<grid_for(c->n, c->bs_contacts), c->bs_contacts, 0, st>>>(V);
     prof_end(c, ps);
     ps = prof_begin(c, "k_gas_particle");
-    k_gas_particle<R><<<grid_for(c->n, c->bs_gp), c->bs_gp, 0, st>>>(V);
+    k_gas_particle<P><<<grid_for(c->n, c->bs_gp), c->bs_gp, 0, st>>>(V);
     prof_end(c, ps);
     ps = prof_begin(c, "k_cells");
-    k_cells<R><<<grid_for(c->ncells, c->bs_cells), c->bs_cells, 0, st>>>(V, 0);
+    k_cells<P><<<grid_for(c->ncells, c->bs_cells), c->bs_cells, 0, st>>>(V, 0);
     prof_end(c, ps);
     k_step_counter<<<1, 1, 0, st>>>(c->step_ctr);
     c->launches += 4;
@@ -119,76 +110,76 @@ int enqueue_steps(dem_ctx *c, int nsteps) {
   return 0;
 }
 
-template <class R>
+template <class P>
 int enqueue_init(dem_ctx *c) {
   cudaStream_t st = c->st;
-  int e = enqueue_binning<R>(c, 0);
+  int e = enqueue_binning<P>(c, 0);
   if (e) return e;
-  StepView<R> V = make_view<R>(c, true);
-  k_volume<R><<<grid_for(c->n, 256), 256, 0, st>>>(V);
-  k_cells<R><<<grid_for(c->ncells, 256), 256, 0, st>>>(V, 1);
+  StepView<P> V = make_view<P>(c, true);
+  k_volume<P><<<grid_for(c->n, 256), 256, 0, st>>>(V);
+  k_cells<P><<<grid_for(c->ncells, 256), 256, 0, st>>>(V, 1);
   c->cur = 1 - c->cur;
   c->gcur = 1 - c->gcur;
   return (int)cudaPeekAtLastError();
 }
 
-template <class R>
+template <class P>
 int enqueue_fov(dem_ctx *c, double *per_parcel_dev) {
-  StepView<R> V = make_view<R>(c, false);
-  k_fov_parcel<R><<<grid_for(c->n, 256), 256, 0, c->st>>>(V, per_parcel_dev, c->fv);
-  k_fov_bed<R><<<c->nbeds, 256, 0, c->st>>>(V, c->fv, c->fvbed);
+  StepView<P> V = make_view<P>(c, false);
+  k_fov_parcel<P><<<grid_for(c->n, 256), 256, 0, c->st>>>(V, per_parcel_dev, c->fv);
+  k_fov_bed<P><<<c->nbeds, 256, 0, c->st>>>(V, c->fv, c->fvbed);
   return (int)cudaPeekAtLastError();
 }
 
-template <class R>
+template <class P>
 int enqueue_scatter_state(dem_ctx *c, double *out_dev) {
-  StepView<R> V = make_view<R>(c, false);
-  k_scatter_state<R><<<grid_for(c->n, 256), 256, 0, c->st>>>(V, out_dev);
+  StepView<P> V = make_view<P>(c, false);
+  k_scatter_state<P><<<grid_for(c->n, 256), 256, 0, c->st>>>(V, out_dev);
   return (int)cudaPeekAtLastError();
 }
 
-template <class R>
+template <class P>
 int enqueue_scatter_diag(dem_ctx *c, double *out_dev) {
-  StepView<R> V = make_view<R>(c, false);
+  StepView<P> V = make_view<P>(c, false);
   V.diag = c->diag;
-  k_scatter_diag<R><<<grid_for(c->n, 256), 256, 0, c->st>>>(V, out_dev);
+  k_scatter_diag<P><<<grid_for(c->n, 256), 256, 0, c->st>>>(V, out_dev);
   return (int)cudaPeekAtLastError();
 }
 
-template <class R>
+template <class P>
 int enqueue_scatter_hist(dem_ctx *c, int *cnt, int *partner, double *xi) {
-  StepView<R> V = make_view<R>(c, false);
-  k_scatter_hist<R><<<grid_for(c->n, 256), 256, 0, c->st>>>(V, cnt, partner, xi);
+  StepView<P> V = make_view<P>(c, false);
+  k_scatter_hist<P><<<grid_for(c->n, 256), 256, 0, c->st>>>(V, cnt, partner, xi);
   return (int)cudaPeekAtLastError();
 }
 
-template <class R>
+template <class P>
 int enqueue_sources(dem_ctx *c) {
-  StepView<R> V = make_view<R>(c, false);
+  StepView<P> V = make_view<P>(c, false);
   V.dep = c->dep;
-  k_sources<R><<<grid_for(c->ncells, 256), 256, 0, c->st>>>(V);
+  k_sources<P><<<grid_for(c->ncells, 256), 256, 0, c->st>>>(V);
   return (int)cudaPeekAtLastError();
 }
 
-template <class R>
+template <class P>
 int enqueue_props(dem_ctx *c) {
-  StepView<R> V = make_view<R>(c, false);
+  StepView<P> V = make_view<P>(c, false);
   V.gas = c->gas[c->gcur];
   V.gas_new = c->gas[1 - c->gcur];
-  k_cells<R><<<grid_for(c->ncells, 256), 256, 0, c->st>>>(V, 2);
+  k_cells<P><<<grid_for(c->ncells, 256), 256, 0, c->st>>>(V, 2);
   c->gcur = 1 - c->gcur;
   return (int)cudaPeekAtLastError();
 }
 
-#define DEM_INSTANTIATE(R)                                                             \
-  template StepView<R> make_view<R>(dem_ctx *, bool);                                   \
-  template int enqueue_steps<R>(dem_ctx *, int);                                        \
-  template int enqueue_init<R>(dem_ctx *);                                              \
-  template int enqueue_fov<R>(dem_ctx *, double *);                                     \
-  template int enqueue_scatter_state<R>(dem_ctx *, double *);                           \
-  template int enqueue_scatter_diag<R>(dem_ctx *, double *);                            \
-  template int enqueue_scatter_hist<R>(dem_ctx *, int *, int *, double *);              \
-  template int enqueue_sources<R>(dem_ctx *);                                           \
-  template int enqueue_props<R>(dem_ctx *);
+#define DEM_INSTANTIATE(P)                                                             \
+  template StepView<P> make_view<P>(dem_ctx *, bool);                                   \
+  template int enqueue_steps<P>(dem_ctx *, int);                                        \
+  template int enqueue_init<P>(dem_ctx *);                                              \
+  template int enqueue_fov<P>(dem_ctx *, double *);                                     \
+  template int enqueue_scatter_state<P>(dem_ctx *, double *);                           \
+  template int enqueue_scatter_diag<P>(dem_ctx *, double *);                            \
+  template int enqueue_scatter_hist<P>(dem_ctx *, int *, int *, double *);              \
+  template int enqueue_sources<P>(dem_ctx *);                                           \
+  template int enqueue_props<P>(dem_ctx *);
 
 }  // namespace dem

@@ -119,9 +119,10 @@ def test_packed_bed_fp64_multistep(wall):
     ctx.close()
 
 
-def test_split_form_against_oracle():
+@pytest.mark.parametrize("prec", ["split", "split_kahan"])
+def test_split_form_against_oracle(prec):
     bed = synth.small_packed(seed=10, n=3000, v_scale=0.3, T0=1073.0)
-    ctx = _ctx(bed, prec="split", diag=True)
+    ctx = _ctx(bed, prec=prec, diag=True)
     ref = oracle.Oracle(bed)
     ctx.dem_step(20)
     ref.step(20)
