@@ -338,8 +338,8 @@ __device__ void load_par(const StepView<Pp> &V, const BedP<double> *bpd, int i, 
   const size_t nc = (size_t)V.ncells;
   const unsigned c = V.keys[i];
   const double *G = V.gas;
-  const double Y[3] = {G[GS_Y0 * nc + c], G[GS_Y1 * nc + c], G[GS_Y2 * nc + c]};
-  const CellProps<double> cp = gas_cell_props<double>(B, G[GS_EPS * nc + c], Y, G[GS_T * nc + c]);
+  const double Y[3] = {gas_d<Pp>(G, GS_Y0 * nc + c), gas_d<Pp>(G, GS_Y1 * nc + c), gas_d<Pp>(G, GS_Y2 * nc + c)};
+  const CellProps<double> cp = gas_cell_props<double>(B, gas_d<Pp>(G, GS_EPS * nc + c), Y, gas_d<Pp>(G, GS_T * nc + c));
   P.rho = cp.rho; P.mu = cp.mu; P.lam = cp.lam; P.eps = cp.eps; P.Tg = cp.T; P.x = cp.x; P.Dm = cp.Dm;
   P.sc13 = cp.sc13; P.pr13 = cp.pr13; P.epow = cp.epow; P.D = cp.D[P.ore]; P.uz = cp.uz;
   P.cRe = P.rho * P.eps * P.d / P.mu;

@@ -16,6 +16,9 @@
 namespace dem {
 
 constexpr int KMAX = DEM_MAX_CONTACTS;
+// candidate list of the pair search (per thread, shared memory): live contacts plus the few
+// extra candidates of the exact form's FP32 prefilter
+constexpr int KLIST = KMAX + 8;
 constexpr double kPI = 3.14159265358979323846;
 constexpr double kRgas = 8.314;  // gas constant of Sec. 2.1
 constexpr double kGrav = 9.81;
@@ -52,6 +55,7 @@ struct DevBed {
   double x0, y0, z0, dx, dy, dz, inv_dx, inv_dy, inv_dz, vcell, inv_vcell;
   int nx, ny, nz;
   long long cell_off;           // first global gas cell (and sort key) of this bed
+  int corner_off;               // first entry of this bed in the cell-corner table
   double R_bed, H, cos_a, sin_a, z_apex, plate_z, pitch, inv_pitch, r_hole;
   int wall;
   double dt, k;
@@ -74,6 +78,7 @@ template <class R> struct BedP {
   R rate_c;                     // pi p0 / R_g (molar-rate prefactor of eq (2-1) without d^2 / T)
   R dpdz, grav, dtg;
   R pf_margin;                  // prefilter margin of the exact (FP64) pair test, m
+  R reach_max;                  // largest parcel radius of the bed (CGP), m
   unsigned flags;
   int ncouple, wall;
 };
@@ -510,6 +515,43 @@ template <class P> __device__ __forceinline__ void mass_add(double *m, int i, ty
     const double mn = m[i] + (double)inc;
     m[i] = mn > 0.0 ? mn : 0.0;
   }
+}
+
+// ---------------------------------------------------------------------------------------
+// Gas state words: FP64 values in the FP64 form; in the FP32 forms a (value, compensation)
+// pair of FP32 in the same 8-byte slot, so that the explicit update accumulates small
+// increments without FP64 arithmetic (compensated summation).
+// ---------------------------------------------------------------------------------------
+template <class P> __device__ __forceinline__ typename P::R gas_r(const double *G, size_t k) {
+  if constexpr (P::exact) {
+    return G[k];
+  } else {
+    const float2 v = reinterpret_cast<const float2 *>(G)[k];
+    return v.x + v.y;
+  }
+}
+template <class P> __device__ __forceinline__ double gas_d(const double *G, size_t k) {
+  if constexpr (P::exact) {
+    return G[k];
+  } else {
+    const float2 v = reinterpret_cast<const float2 *>(G)[k];
+    return (double)v.x + (double)v.y;
+  }
+}
+// a value given in FP64 (inputs)
+__device__ __forceinline__ void gas_put(double *G, size_t k, double v, bool pairs) {
+  if (!pairs) {
+    G[k] = v;
+  } else {
+    const float hi = (float)v;
+    reinterpret_cast<float2 *>(G)[k] = make_float2(hi, (float)(v - (double)hi));
+  }
+}
+// (hi, lo) + inc, compensated
+__device__ __forceinline__ float2 pair_add(float2 v, float inc) {
+  const float y = inc + v.y;
+  const float t = v.x + y;
+  return make_float2(t, y - (t - v.x));
 }
 
 }  // namespace dem

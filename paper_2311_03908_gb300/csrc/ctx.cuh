@@ -37,7 +37,10 @@ struct dem_ctx {
   unsigned *keys = nullptr, *vals = nullptr, *keys2 = nullptr, *vals2 = nullptr, *rhist = nullptr;
   unsigned *kres = nullptr, *vres = nullptr;   // where the last sort left its result
   unsigned *cstart = nullptr, *cend = nullptr;
-  float4 *xl = nullptr;
+  float4 *xl = nullptr;             // cell-local position and radius, sorted order
+  float4 *xlk = nullptr;            // the same, written by the key kernel (pre-sort order)
+  double *corner = nullptr;         // cell-corner coordinates: per bed x0+i dx, y0+j dy, z0+k dz
+  std::vector<double> hcorner;
   void *mass = nullptr, *F[3] = {}, *Tq[3] = {}, *src = nullptr;
   // gas: two state buffers (gcur = current), properties, marks
   double *gas[2] = {};

@@ -61,13 +61,13 @@ __global__ void k_load(int n, const double *const *src /* 8 + 4 arrays */, const
 }
 
 // Gas state from the coupling input, keeping the volume fraction.
-__global__ void k_gas_set(long long nc, const double *Y /* nc*3 */, const double *T, double *G) {
+__global__ void k_gas_set(long long nc, const double *Y /* nc*3 */, const double *T, double *G, bool pairs) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc) return;
-  G[GS_Y0 * nc + c] = Y[c * 3 + 0];
-  G[GS_Y1 * nc + c] = Y[c * 3 + 1];
-  G[GS_Y2 * nc + c] = Y[c * 3 + 2];
-  G[GS_T * nc + c] = T[c];
+  gas_put(G, GS_Y0 * nc + c, Y[c * 3 + 0], pairs);
+  gas_put(G, GS_Y1 * nc + c, Y[c * 3 + 1], pairs);
+  gas_put(G, GS_Y2 * nc + c, Y[c * 3 + 2], pairs);
+  gas_put(G, GS_T * nc + c, T[c], pairs);
 }
 
 int prof_begin(dem_ctx *c, const char *name) {
@@ -97,14 +97,14 @@ void prof_end(dem_ctx *c, int slot) {
   cudaEventRecord(c->ev_pool[slot + 1], c->st);
 }
 
-__global__ void k_gas_load(long long nc, const double *Y /* nc*3 */, const double *T, double *G) {
+__global__ void k_gas_load(long long nc, const double *Y /* nc*3 */, const double *T, double *G, bool pairs) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc) return;
-  G[GS_EPS * nc + c] = 1.0;
-  G[GS_Y0 * nc + c] = Y[c * 3 + 0];
-  G[GS_Y1 * nc + c] = Y[c * 3 + 1];
-  G[GS_Y2 * nc + c] = Y[c * 3 + 2];
-  G[GS_T * nc + c] = T[c];
+  gas_put(G, GS_EPS * nc + c, 1.0, pairs);
+  gas_put(G, GS_Y0 * nc + c, Y[c * 3 + 0], pairs);
+  gas_put(G, GS_Y1 * nc + c, Y[c * 3 + 1], pairs);
+  gas_put(G, GS_Y2 * nc + c, Y[c * 3 + 2], pairs);
+  gas_put(G, GS_T * nc + c, T[c], pairs);
 }
 
 }  // namespace dem
@@ -229,7 +229,7 @@ DevBed derive_bed(const dem_bed_config &b) {
 // Physics parameters of a bed, computed in FP64 and stored in the form's type.
 template <class R>
 BedP<R> derive_params(const dem_bed_config &b, const DevBed &G) {
-  BedP<R> P;
+  BedP<R> P{};
   std::memset(&P, 0, sizeof P);
   P.k = (R)b.cg_ratio; P.k3 = (R)(b.cg_ratio * b.cg_ratio * b.cg_ratio);
   P.inv_k3 = (R)(1.0 / (b.cg_ratio * b.cg_ratio * b.cg_ratio));
@@ -309,6 +309,8 @@ void layout(dem_ctx *c, Bump &m) {
   c->rhist = m.take<unsigned>(radix_hist_words((int)N));
   c->cstart = m.take<unsigned>(C); c->cend = m.take<unsigned>(C);
   c->xl = m.take<float4>(N);
+  c->xlk = m.take<float4>(N);
+  c->corner = m.take<double>(c->hcorner.size());
   c->mass = m.take<char>(N, R);
   for (int q = 0; q < 3; ++q) { c->F[q] = m.take<char>(N, R); c->Tq[q] = m.take<char>(N, R); }
   c->src = m.take<char>(N * SR_N, R);
@@ -439,9 +441,15 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
     if (nb[b] > 0 && std::sqrt(beds[b].kn / (0.5 * mmin[b])) * beds[b].dt >= 2.0) { delete c; return DEM_EINVAL; }
     B.cell_off = coff;
     coff += (long long)B.nx * B.ny * B.nz;
+    B.corner_off = (int)c->hcorner.size();
+    for (int q = 0; q < B.nx; ++q) c->hcorner.push_back(B.x0 + q * B.dx);
+    for (int q = 0; q < B.ny; ++q) c->hcorner.push_back(B.y0 + q * B.dy);
+    for (int q = 0; q < B.nz; ++q) c->hcorner.push_back(B.z0 + q * B.dz);
     c->hbeds.push_back(B);
     c->hbp_d.push_back(derive_params<double>(beds[b], B));
     c->hbp_f.push_back(derive_params<float>(beds[b], B));
+    c->hbp_d.back().reach_max = 0.5 * dmax[b];
+    c->hbp_f.back().reach_max = (float)(0.5 * dmax[b]);
   }
   if (coff >= (1LL << 31)) { delete c; return DEM_EINVAL; }
   c->ncells = coff;
@@ -463,6 +471,7 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
   ck(cudaMemcpyAsync(c->dbeds, c->hbeds.data(), sizeof(DevBed) * n_beds, cudaMemcpyHostToDevice, c->st));
   ck(cudaMemcpyAsync(c->dbp_d, c->hbp_d.data(), sizeof(BedP<double>) * n_beds, cudaMemcpyHostToDevice, c->st));
   ck(cudaMemcpyAsync(c->dbp_f, c->hbp_f.data(), sizeof(BedP<float>) * n_beds, cudaMemcpyHostToDevice, c->st));
+  ck(cudaMemcpyAsync(c->corner, c->hcorner.data(), sizeof(double) * c->hcorner.size(), cudaMemcpyHostToDevice, c->st));
   // staging copies of the inputs (freed at the end of init)
   double *dsrc = nullptr;
   int *dint = nullptr;
@@ -534,7 +543,7 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
       ck(cudaMemcpyAsync(dY, Y.data(), sizeof(double) * Y.size(), cudaMemcpyHostToDevice, c->st));
       ck(cudaMemcpyAsync(dT, T.data(), sizeof(double) * T.size(), cudaMemcpyHostToDevice, c->st));
       const int gg = (int)((c->ncells + 255) / 256);
-      k_gas_load<<<gg, 256, 0, c->st>>>(c->ncells, dY, dT, c->gas[0]);
+      k_gas_load<<<gg, 256, 0, c->st>>>(c->ncells, dY, dT, c->gas[0], c->prec != DEM_PREC_FP64);
       k_mark_cells<<<gg, 256, 0, c->st>>>(c->dbeds, c->cell_bed, c->mark, c->ncells);
     }
     ck(cudaStreamSynchronize(c->st));
@@ -687,7 +696,15 @@ int dem_get_gas(dem_ctx *c, double *out_host) {
   CK(cudaMemcpyAsync(mk.data(), c->mark, nc, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
   for (size_t k = 0; k < nc; ++k) {
-    for (int f = 0; f < GS_N; ++f) out_host[k * DEM_NGAS + f] = G[f * nc + k];
+    for (int f = 0; f < GS_N; ++f) {
+      double v = G[f * nc + k];
+      if (c->prec != DEM_PREC_FP64) {   // FP32 forms: (value, compensation) pair of FP32
+        float p[2];
+        std::memcpy(p, &v, sizeof p);
+        v = (double)p[0] + (double)p[1];
+      }
+      out_host[k * DEM_NGAS + f] = v;
+    }
     out_host[k * DEM_NGAS + 5] = mk[k];
   }
   return DEM_OK;
@@ -791,7 +808,7 @@ int dem_set_gas(dem_ctx *c, const dem_gas *g) {
     Y = c->gas_stage;
     T = c->gas_stage + 3 * nc;
   }
-  k_gas_set<<<(int)((nc + 255) / 256), 256, 0, c->st>>>((long long)nc, Y, T, c->gas[c->gcur]);
+  k_gas_set<<<(int)((nc + 255) / 256), 256, 0, c->st>>>((long long)nc, Y, T, c->gas[c->gcur], c->prec != DEM_PREC_FP64);
   int e = DEM_DISPATCH(c, enqueue_props, c);
   if (e) return c->sticky = DEM_ECUDA;
   return DEM_OK;

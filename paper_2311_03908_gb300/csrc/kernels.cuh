@@ -34,6 +34,9 @@ template <class P> struct StepView {
   unsigned *keys, *vals;        // sorted keys (global gas cell) and the permutation
   unsigned *cstart, *cend;      // parcel range of every gas cell (empty: 0, 0)
   float4 *xl;                   // FP32 position relative to the own cell's corner, radius
+  float4 *xlk;                  // the same in pre-sort order (written by k_key)
+  const double *corner;         // cell-corner coordinates (see DevBed::corner_off)
+  const unsigned *kprev;        // keys of the state before the step (its order)
   R *mass;                      // parcel mass (new order)
   R *F[3], *Tq[3];              // contact force and torque
   R *src;                       // [SR_N][cap] per-parcel cell sources
@@ -52,48 +55,46 @@ __device__ __forceinline__ bool coupled_step(int ncouple, const long long *ctr) 
 }
 
 // ---------------------------------------------------------------------------------------
-// half kick and drift of velocity Verlet (kick-drift-kick). The key kernel and the gather
-// kernel both call this, so the new positions they see are the same bits.
+// Velocity Verlet (kick-drift-kick). The first half kick is evaluated by the key kernel
+// (for the drift) and again by the gather kernel with the same expression, so both see the
+// same bits; the drift is applied once, by the key kernel, to the FP64 positions.
 // ---------------------------------------------------------------------------------------
 template <class R>
-__device__ __forceinline__ void kick_drift(R half_dt, R dt, double dt_d, double &x, R &v, R a) {
-  if constexpr (sizeof(R) == 8) {
-    const double vh = __dadd_rn((double)v, __dmul_rn((double)a, 0.5 * dt_d));
-    x = __dadd_rn(x, __dmul_rn(vh, dt_d));
-    v = (R)vh;
-  } else {
-    v = v + a * half_dt;
-    x = x + (double)(v * dt);
-  }
+__device__ __forceinline__ R half_kick(R half_dt, double dt_d, R v, R a) {
+  if constexpr (sizeof(R) == 8) return __dadd_rn(v, __dmul_rn(a, 0.5 * dt_d));
+  else return v + a * half_dt;
 }
 
-// Gas cell of a point: floor((x - x0) * (1/dx)) clamped, in FP64. The FP32 forms first try
-// FP32 and fall back to FP64 only within 1e-3 of a cell face, so both agree.
+// Gas cell of a point: floor((x - x0) * (1/dx)) clamped, in FP64.
 __device__ __forceinline__ int cell_coord_d(double x, double x0, double inv, int n, bool &out) {
   const double f = floor((x - x0) * inv);
   if (!(f >= 0.0 && f < (double)n)) out = true;
   return (int)fmin(fmax(f, 0.0), (double)(n - 1));
 }
-template <class P>
-__device__ __forceinline__ int cell_coord(double x, double x0, double inv, float x0f, float invf, int n, bool &out) {
-  if constexpr (!P::exact) {
-    const float u = ((float)x - x0f) * invf;
-    const float fl = floorf(u);
-    if (u - fl > 1e-3f && u - fl < 1.0f - 1e-3f && fl >= 0.0f && fl < (float)n) return (int)fl;
-  }
-  return cell_coord_d(x, x0, inv, n, out);
-}
 
-template <class P>
-__device__ __forceinline__ unsigned point_key(const DevBed &B, const BedP<typename P::R> &bp, double x,
-                                              double y, double z, bool &out) {
+static __device__ __noinline__ unsigned point_key_d(const DevBed &B, double x, double y, double z, bool &out) {
   out = false;
-  const int ix = cell_coord<P>(x, B.x0, B.inv_dx, (float)bp.x0, (float)bp.inv_dx, B.nx, out);
-  const int iy = cell_coord<P>(y, B.y0, B.inv_dy, (float)bp.y0, (float)bp.inv_dy, B.ny, out);
-  const int iz = cell_coord<P>(z, B.z0, B.inv_dz, (float)bp.z0, (float)bp.inv_dz, B.nz, out);
+  const int ix = cell_coord_d(x, B.x0, B.inv_dx, B.nx, out);
+  const int iy = cell_coord_d(y, B.y0, B.inv_dy, B.ny, out);
+  const int iz = cell_coord_d(z, B.z0, B.inv_dz, B.nz, out);
   return (unsigned)(B.cell_off + ((long long)iz * B.ny + iy) * B.nx + ix);
 }
 
+// cell coordinates of a key within its bed (32-bit arithmetic: keys are below 2^31)
+__device__ __forceinline__ void key_cell(const DevBed &B, unsigned key, int &ix, int &iy, int &iz) {
+  const unsigned l = key - (unsigned)B.cell_off;
+  const unsigned nx = (unsigned)B.nx, ny = (unsigned)B.ny;
+  const unsigned row = l / nx;
+  ix = (int)(l - row * nx);
+  iz = (int)(row / ny);
+  iy = (int)(row - (unsigned)iz * ny);
+}
+
+// Half kick + drift (written back to the FP64 positions), the sort key, and the FP32
+// cell-local coordinates. The FP32 forms take the key from the previous cell when the
+// parcel stays more than 1e-3 of an edge inside it (the local coordinates then decide
+// it exactly, their error being ~1e-10 m); otherwise, and always in the FP64 form, the key
+// is the FP64 definition.
 template <class P>
 __global__ void k_key(StepView<P> V, int drift) {
   using R = typename P::R;
@@ -103,20 +104,48 @@ __global__ void k_key(StepView<P> V, int drift) {
   const DevBed &B = V.beds[b];
   const BedP<R> &bp = V.bp[b];
   double x = V.A.x[i], y = V.A.y[i], z = V.A.z[i];
+  bool fast = false;
+  unsigned key = 0;
   if (drift) {
-    R vx = V.A.v[0][i], vy = V.A.v[1][i], vz = V.A.v[2][i];
-    kick_drift<R>(bp.half_dt, bp.dt, B.dt, x, vx, V.A.a[0][i]);
-    kick_drift<R>(bp.half_dt, bp.dt, B.dt, y, vy, V.A.a[1][i]);
-    kick_drift<R>(bp.half_dt, bp.dt, B.dt, z, vz, V.A.a[2][i]);
+    R disp[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const R vh = half_kick<R>(bp.half_dt, B.dt, V.A.v[q][i], V.A.a[q][i]);
+      if constexpr (sizeof(R) == 8) disp[q] = __dmul_rn(vh, B.dt);
+      else disp[q] = vh * bp.dt;
+    }
+    if constexpr (sizeof(R) == 8) {
+      x = __dadd_rn(x, disp[0]); y = __dadd_rn(y, disp[1]); z = __dadd_rn(z, disp[2]);
+    } else {
+      x = x + (double)disp[0]; y = y + (double)disp[1]; z = z + (double)disp[2];
+    }
+    V.A.x[i] = x; V.A.y[i] = y; V.A.z[i] = z;
+    if constexpr (!P::exact) {
+      const float4 o = V.xl[i];
+      const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
+      const float ux = o.x + (float)disp[0], uy = o.y + (float)disp[1], uz = o.z + (float)disp[2];
+      fast = ux > 1e-3f * hx && ux < 0.999f * hx && uy > 1e-3f * hy && uy < 0.999f * hy &&
+             uz > 1e-3f * hz && uz < 0.999f * hz;
+      if (fast) key = V.kprev[i];
+    }
   }
-  bool out;
-  V.keys[i] = point_key<P>(B, bp, x, y, z, out);
+  if (!fast) {
+    bool out;
+    key = point_key_d(B, x, y, z, out);
+    if (out) set_error(V.err, ERR_DOMAIN);
+  }
+  int ix, iy, iz;
+  key_cell(B, key, ix, iy, iz);
+  const float r = (float)(bp.k * V.A.d[i]) * 0.5f;
+  const double *cn = V.corner + B.corner_off;
+  V.xlk[i] = make_float4((float)(x - cn[ix]), (float)(y - cn[B.nx + iy]), (float)(z - cn[B.nx + B.ny + iz]), r);
+  V.keys[i] = key;
   V.vals[i] = (unsigned)i;
-  if (out) set_error(V.err, ERR_DOMAIN);
 }
 
-// Gather the state into the sorted order, applying the half kick and drift; record the
-// cell ranges by boundary detection on the sorted keys; copy the history slots.
+// Gather the state into the sorted order (positions already drifted by k_key; the half
+// kicks applied here); record the cell ranges by boundary detection on the sorted keys;
+// copy the history slots.
 template <class P>
 __global__ void k_gather(StepView<P> V, int drift) {
   using R = typename P::R;
@@ -126,26 +155,19 @@ __global__ void k_gather(StepView<P> V, int drift) {
   const int meta = V.A.meta[j];
   const DevBed &B = V.beds[meta >> 8];
   const BedP<R> &bp = V.bp[meta >> 8];
-  double x = V.A.x[j], y = V.A.y[j], z = V.A.z[j];
-  R v[3] = {V.A.v[0][j], V.A.v[1][j], V.A.v[2][j]};
-  R w[3] = {V.A.w[0][j], V.A.w[1][j], V.A.w[2][j]};
-  R a[3] = {V.A.a[0][j], V.A.a[1][j], V.A.a[2][j]};
-  R al[3] = {V.A.al[0][j], V.A.al[1][j], V.A.al[2][j]};
-  if (drift) {
-    kick_drift<R>(bp.half_dt, bp.dt, B.dt, x, v[0], a[0]);
-    kick_drift<R>(bp.half_dt, bp.dt, B.dt, y, v[1], a[1]);
-    kick_drift<R>(bp.half_dt, bp.dt, B.dt, z, v[2], a[2]);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) w[q] = w[q] + al[q] * bp.half_dt;
-  }
-  V.B.x[i] = x; V.B.y[i] = y; V.B.z[i] = z;
+  V.B.x[i] = V.A.x[j]; V.B.y[i] = V.A.y[j]; V.B.z[i] = V.A.z[j];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    V.B.v[q][i] = v[q]; V.B.w[q][i] = w[q]; V.B.a[q][i] = a[q]; V.B.al[q][i] = al[q];
+    R v = V.A.v[q][j], w = V.A.w[q][j];
+    const R a = V.A.a[q][j], al = V.A.al[q][j];
+    if (drift) {
+      v = half_kick<R>(bp.half_dt, B.dt, v, a);
+      w = w + al * bp.half_dt;
+    }
+    V.B.v[q][i] = v; V.B.w[q][i] = w; V.B.a[q][i] = a; V.B.al[q][i] = al;
   }
   V.B.T[i] = V.A.T[j];
-  const R d = V.A.d[j];
-  V.B.d[i] = d;
+  V.B.d[i] = V.A.d[j];
   R msum = 0;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -156,14 +178,9 @@ __global__ void k_gather(StepView<P> V, int drift) {
   V.B.meta[i] = meta;
   V.B.orig[i] = V.A.orig[j];
   V.mass[i] = msum;
-  // position relative to the own cell's corner (FP64 difference, then FP32)
-  const unsigned k = V.keys[i];
-  const long long l = (long long)k - B.cell_off;
-  const int ix = (int)(l % B.nx), iy = (int)((l / B.nx) % B.ny), iz = (int)(l / ((long long)B.nx * B.ny));
-  const float r = (float)(bp.k * d) * 0.5f;
-  V.xl[i] = make_float4((float)(x - (B.x0 + ix * B.dx)), (float)(y - (B.y0 + iy * B.dy)),
-                        (float)(z - (B.z0 + iz * B.dz)), r);
+  V.xl[i] = V.xlk[j];
   // occupied ranges
+  const unsigned k = V.keys[i];
   if (i == 0 || V.keys[i - 1] != k) V.cstart[k] = (unsigned)i;
   if (i == V.n - 1 || V.keys[i + 1] != k) V.cend[k] = (unsigned)(i + 1);
   // history slots travel with the parcel
@@ -210,11 +227,21 @@ __device__ __forceinline__ void add_contact(const StepView<P> &V, int i, int cin
   }
 }
 
+// Phase A (search): for each of the 9 neighbour rows (dy, dz) the cells X-1..X+1 hold one
+// contiguous run of sorted parcels; rows and end cells that lie farther than r_i + r_max from
+// the parcel are skipped. Every candidate is tested on the FP32 cell-local coordinates and the
+// hits go to a per-thread list in shared memory (index + cell offset code).
+// Phase B (forces): the list is processed with the lanes of a warp together, so the few hits
+// of a parcel do not serialise the warp the way a force evaluation inside the search loop does.
+// Pairs are visited in the same order as a plain 27-cell loop (dz, dy, dx, then index).
 template <class P>
 __global__ void k_contacts(StepView<P> V) {
   using R = typename P::R;
+  extern __shared__ int s_list[];   // [KLIST][blockDim.x] indices, then [KLIST][blockDim.x] codes
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V.n) return;
+  const int nt = blockDim.x, tid = threadIdx.x;
+  unsigned char *s_code = reinterpret_cast<unsigned char *>(s_list + KLIST * nt);
   const int meta = V.B.meta[i];
   const int b = meta >> 8;
   const DevBed &B = V.beds[b];
@@ -224,74 +251,92 @@ __global__ void k_contacts(StepView<P> V) {
   const int cin = V.Hn.cnt[i];
   if (!(bp.flags & DEM_NO_CONTACTS)) {
     const float4 me = V.xl[i];
+    int X, Y, Z;
+    key_cell(B, V.keys[i], X, Y, Z);
+    const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
+    const float pm = (float)bp.pf_margin;
+    // reach: no partner centre lies farther than r_i + r_max (with a margin far above the
+    // ~1e-10 m resolution of the local coordinates)
+    const float reach = (me.w + (float)bp.reach_max) * 1.0001f + pm + 1e-9f;
+    const int xlo = (X > 0 && me.x < reach) ? -1 : 0, xhi = (X < B.nx - 1 && hx - me.x < reach) ? 1 : 0;
+    const int ylo = (Y > 0 && me.y < reach) ? -1 : 0, yhi = (Y < B.ny - 1 && hy - me.y < reach) ? 1 : 0;
+    const int zlo = (Z > 0 && me.z < reach) ? -1 : 0, zhi = (Z < B.nz - 1 && hz - me.z < reach) ? 1 : 0;
+    int nh = 0;
+    for (int dz = zlo; dz <= zhi; ++dz) {
+      const float gz = dz < 0 ? me.z : (dz > 0 ? hz - me.z : 0.0f);   // distance to the row
+      for (int dy = ylo; dy <= yhi; ++dy) {
+        const float gy = dy < 0 ? me.y : (dy > 0 ? hy - me.y : 0.0f);
+        if (gy * gy + gz * gz >= reach * reach) continue;
+        const unsigned krow = (unsigned)(B.cell_off + ((long long)(Z + dz) * B.ny + (Y + dy)) * B.nx + X);
+        const float oy = dy * hy - me.y, oz = dz * hz - me.z;
+        for (int dx = xlo; dx <= xhi; ++dx) {
+          const unsigned k2 = krow + dx;
+          const unsigned jb = __ldg(V.cstart + k2), je = __ldg(V.cend + k2);
+          const float ox = dx * hx - me.x;
+          const unsigned char code = (unsigned char)((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
+          for (unsigned jj = jb; jj < je; ++jj) {
+            const float4 o = __ldg(V.xl + jj);
+            const float ex = o.x + ox, ey = o.y + oy, ez = o.z + oz;   // x_j - x_i
+            const float d2f = ex * ex + ey * ey + ez * ez;
+            const float rsf = me.w + o.w;
+            const float lim = P::exact ? rsf + pm : rsf;
+            if (d2f < lim * lim && (int)jj != i) {
+              if (nh < KLIST) {
+                s_list[nh * nt + tid] = (int)jj;
+                s_code[nh * nt + tid] = code;
+              }
+              ++nh;
+            }
+          }
+        }
+      }
+    }
+    if (nh > KLIST) { set_error(V.err, ERR_CAPACITY); nh = KLIST; }
+    // phase B
     const R di = V.B.d[i];
     const R mi = V.mass[i];
     const R vi[3] = {V.B.v[0][i], V.B.v[1][i], V.B.v[2][i]};
     const R wi[3] = {V.B.w[0][i], V.B.w[1][i], V.B.w[2][i]};
-    const unsigned key = V.keys[i];
-    const long long l = (long long)key - B.cell_off;
-    const int X = (int)(l % B.nx), Y = (int)((l / B.nx) % B.ny), Z = (int)(l / ((long long)B.nx * B.ny));
-    const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
-    const float pm = (float)bp.pf_margin;
     double xi_d = 0, yi_d = 0, zi_d = 0, ri_d = 0;
     if constexpr (P::exact) {
       xi_d = V.B.x[i]; yi_d = V.B.y[i]; zi_d = V.B.z[i];
       ri_d = __dmul_rn(0.5, __dmul_rn(B.k, (double)di));
     }
     const R ri = P::exact ? (R)ri_d : (R)me.w;
-    for (int dz = -1; dz <= 1; ++dz) {
-      const int Z2 = Z + dz;
-      if (Z2 < 0 || Z2 >= B.nz) continue;
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int Y2 = Y + dy;
-        if (Y2 < 0 || Y2 >= B.ny) continue;
-        const unsigned krow = (unsigned)(B.cell_off + ((long long)Z2 * B.ny + Y2) * B.nx);
-        const float oy = dy * hy - me.y, oz = dz * hz - me.z;
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int X2 = X + dx;
-          if (X2 < 0 || X2 >= B.nx) continue;
-          const unsigned k2 = krow + (unsigned)X2;
-          const unsigned jb = V.cstart[k2], je = V.cend[k2];
-          const float ox = dx * hx - me.x;
-          for (unsigned jj = jb; jj < je; ++jj) {
-            const int j = (int)jj;
-            if (j == i) continue;
-            const float4 o = V.xl[j];
-            const float ex = o.x + ox, ey = o.y + oy, ez = o.z + oz;   // x_j - x_i
-            const float d2f = ex * ex + ey * ey + ez * ez;
-            const float rsf = me.w + o.w;
-            R nrm[3], delta;
-            double rj_d = 0;
-            if constexpr (P::exact) {
-              const float rp = rsf + pm;
-              if (d2f >= rp * rp) continue;
-              const double dxd = V.B.x[j] - xi_d, dyd = V.B.y[j] - yi_d, dzd = V.B.z[j] - zi_d;
-              rj_d = __dmul_rn(0.5, __dmul_rn(B.k, (double)V.B.d[j]));
-              const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dxd, dxd), __dmul_rn(dyd, dyd)), __dmul_rn(dzd, dzd));
-              const double rs = __dadd_rn(ri_d, rj_d);
-              if (!(d2 < __dmul_rn(rs, rs))) continue;
-              const double dd = sqrt(d2);
-              nrm[0] = (R)(dxd / dd); nrm[1] = (R)(dyd / dd); nrm[2] = (R)(dzd / dd);
-              delta = (R)(rs - dd);
-            } else {
-              if (!(d2f < rsf * rsf)) continue;
-              const float df = sqrtf(d2f);
-              const float inv = 1.0f / df;
-              nrm[0] = (R)(ex * inv); nrm[1] = (R)(ey * inv); nrm[2] = (R)(ez * inv);
-              delta = (R)((rsf * rsf - d2f) / (rsf + df));
-            }
-            const R rj = P::exact ? (R)rj_d : (R)o.w;
-            const R mj = V.mass[j];
-            const R mstar = mi * mj / (mi + mj);
-            const R ws[3] = {ri * wi[0] + rj * V.B.w[0][j], ri * wi[1] + rj * V.B.w[1][j], ri * wi[2] + rj * V.B.w[2][j]};
-            R vrel[3];
-            vrel[0] = (vi[0] - V.B.v[0][j]) + (ws[1] * nrm[2] - ws[2] * nrm[1]);
-            vrel[1] = (vi[1] - V.B.v[1][j]) + (ws[2] * nrm[0] - ws[0] * nrm[2]);
-            vrel[2] = (vi[2] - V.B.v[2][j]) + (ws[0] * nrm[1] - ws[1] * nrm[0]);
-            add_contact<P>(V, i, cin, V.B.orig[j], bp, mstar, ri, nrm, delta, vrel, wi, Fi, Ti, cout);
-          }
-        }
+    for (int h = 0; h < nh; ++h) {
+      const int j = s_list[h * nt + tid];
+      const int code = s_code[h * nt + tid];
+      R nrm[3], delta;
+      double rj_d = 0;
+      if constexpr (P::exact) {
+        const double dxd = V.B.x[j] - xi_d, dyd = V.B.y[j] - yi_d, dzd = V.B.z[j] - zi_d;
+        rj_d = __dmul_rn(0.5, __dmul_rn(B.k, (double)V.B.d[j]));
+        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dxd, dxd), __dmul_rn(dyd, dyd)), __dmul_rn(dzd, dzd));
+        const double rs = __dadd_rn(ri_d, rj_d);
+        if (!(d2 < __dmul_rn(rs, rs))) continue;
+        const double dd = sqrt(d2);
+        nrm[0] = (R)(dxd / dd); nrm[1] = (R)(dyd / dd); nrm[2] = (R)(dzd / dd);
+        delta = (R)(rs - dd);
+      } else {
+        const int cdx = code % 3 - 1, cdy = (code / 3) % 3 - 1, cdz = code / 9 - 1;
+        const float4 o = __ldg(V.xl + j);
+        const float ex = o.x + (cdx * hx - me.x), ey = o.y + (cdy * hy - me.y), ez = o.z + (cdz * hz - me.z);
+        const float d2f = ex * ex + ey * ey + ez * ez;
+        const float rsf = me.w + o.w;
+        const float df = sqrtf(d2f);
+        const float inv = 1.0f / df;
+        nrm[0] = (R)(ex * inv); nrm[1] = (R)(ey * inv); nrm[2] = (R)(ez * inv);
+        delta = (R)((rsf * rsf - d2f) / (rsf + df));
       }
+      const R rj = P::exact ? (R)rj_d : (R)__ldg(&V.xl[j].w);
+      const R mj = V.mass[j];
+      const R mstar = mi * mj / (mi + mj);
+      const R ws[3] = {ri * wi[0] + rj * V.B.w[0][j], ri * wi[1] + rj * V.B.w[1][j], ri * wi[2] + rj * V.B.w[2][j]};
+      R vrel[3];
+      vrel[0] = (vi[0] - V.B.v[0][j]) + (ws[1] * nrm[2] - ws[2] * nrm[1]);
+      vrel[1] = (vi[1] - V.B.v[1][j]) + (ws[2] * nrm[0] - ws[0] * nrm[2]);
+      vrel[2] = (vi[2] - V.B.v[2][j]) + (ws[0] * nrm[1] - ws[1] * nrm[0]);
+      add_contact<P>(V, i, cin, V.B.orig[j], bp, mstar, ri, nrm, delta, vrel, wi, Fi, Ti, cout);
     }
     // walls: FP32 pre-screen on the absolute position rebuilt from the cell corner
     const float xa = (float)bp.x0 + X * hx + me.x, ya = (float)bp.y0 + Y * hy + me.y, za = (float)bp.z0 + Z * hz + me.z;
@@ -324,6 +369,9 @@ __global__ void k_contacts(StepView<P> V) {
   for (int q = 0; q < 3; ++q) { V.F[q][i] = Fi[q]; V.Tq[q][i] = Ti[q]; }
   if (V.diag) V.diag[(size_t)DG_NCONTACT * V.cap + i] = (double)cout;
 }
+
+// dynamic shared memory of k_contacts for a block of nt threads
+inline size_t contacts_smem(int nt) { return (size_t)KLIST * nt * (sizeof(int) + 1); }
 
 // ---------------------------------------------------------------------------------------
 // Gas-particle terms, kinetics, second half kick, temperature and mass update; writes the
@@ -455,31 +503,33 @@ __device__ __forceinline__ void store_props(StepView<P> &V, long long c, const C
   V.gp[GP_EPS * nc + c] = p.eps; V.gp[GP_TG * nc + c] = p.T;
 }
 
-// sums of the per-parcel sources of [jb, je): FP64 or Kahan-compensated FP32
+// sums of the per-parcel sources of [jb, je): FP64 in the FP64 form, compensated FP32
+// (Kahan) in the FP32 forms
 template <class P> struct CellSum {
-  double s[SR_N];
-  __device__ __forceinline__ void run(const typename P::R *src, size_t cp, unsigned jb, unsigned je) {
-    if constexpr (P::kahan) {
-      float v[SR_N], cc[SR_N];
+  using S = typename P::R;
+  S s[SR_N];
+  __device__ __forceinline__ void run(const S *src, size_t cp, unsigned jb, unsigned je) {
+    if constexpr (!P::exact) {
+      float cc[SR_N];
 #pragma unroll
-      for (int f = 0; f < SR_N; ++f) { v[f] = 0.f; cc[f] = 0.f; }
+      for (int f = 0; f < SR_N; ++f) { s[f] = 0.f; cc[f] = 0.f; }
       for (unsigned j = jb; j < je; ++j) {
 #pragma unroll
         for (int f = 0; f < SR_N; ++f) {
           const float y = src[f * cp + j] - cc[f];
-          const float t = v[f] + y;
-          cc[f] = (t - v[f]) - y;
-          v[f] = t;
+          const float t = s[f] + y;
+          cc[f] = (t - s[f]) - y;
+          s[f] = t;
         }
       }
 #pragma unroll
-      for (int f = 0; f < SR_N; ++f) s[f] = (double)v[f] - (double)cc[f];
+      for (int f = 0; f < SR_N; ++f) s[f] -= cc[f];
     } else {
 #pragma unroll
       for (int f = 0; f < SR_N; ++f) s[f] = 0.0;
       for (unsigned j = jb; j < je; ++j) {
 #pragma unroll
-        for (int f = 0; f < SR_N; ++f) s[f] += (double)src[f * cp + j];
+        for (int f = 0; f < SR_N; ++f) s[f] += src[f * cp + j];
       }
     }
   }
@@ -496,105 +546,122 @@ __global__ void k_cells(StepView<P> V, int mode /* 0 step, 1 eps init, 2 props o
   const size_t nc = (size_t)V.ncells;
   const double *G = V.gas;
   double *Gn = V.gas_new;
-  double eps = G[GS_EPS * nc + c], Y[3] = {G[GS_Y0 * nc + c], G[GS_Y1 * nc + c], G[GS_Y2 * nc + c]};
-  double T = G[GS_T * nc + c];
   const bool solid = V.mark[c] != 0;
-  if (mode != 2) {
-    const unsigned jb = V.cstart[c], je = V.cend[c];
-    const size_t cp = (size_t)V.cap;
+  const size_t cp = (size_t)V.cap;
+  const long long layer = (long long)B.nx * B.ny;
+  const bool update = mode == 0 && !solid && coupled_step(bp.ncouple, V.step_ctr) && !(bp.flags & DEM_NO_GAS_UPDATE);
+  if constexpr (P::exact) {
+    // the all-FP64 form: the oracle's expressions
+    double eps = G[GS_EPS * nc + c], Y[3] = {G[GS_Y0 * nc + c], G[GS_Y1 * nc + c], G[GS_Y2 * nc + c]};
+    double T = G[GS_T * nc + c];
     if (mode == 1) {
       double vs = 0.0;
-      for (unsigned j = jb; j < je; ++j) vs += (double)V.src[SR_VS * cp + j];
+      for (unsigned j = V.cstart[c]; j < V.cend[c]; ++j) vs += (double)V.src[SR_VS * cp + j];
       eps = solid ? B.eps_min : fmax(1.0 - vs / B.vcell, B.eps_min);
-    } else if (!solid && coupled_step(bp.ncouple, V.step_ctr) && !(bp.flags & DEM_NO_GAS_UPDATE)) {
+    } else if (update) {
       CellSum<P> S;
-      S.run(V.src, cp, jb, je);
-      const long long lc = c - B.cell_off;
-      const long long layer = (long long)B.nx * B.ny;
-      const bool up = lc >= layer && !V.mark[c - layer];
-      if constexpr (sizeof(R) == 8) {
-        // the all-FP64 form: the oracle's expressions
-        const double dtg = B.ncouple * B.dt;
-        const double rho = (double)V.gp[GP_RHO * nc + c], cpg = (double)V.gp[GP_CP * nc + c];
-        const double uz = B.U_in / eps;
-        double Yup[3] = {B.Y_in[0], B.Y_in[1], B.Y_in[2]}, Tup = B.T_in;
-        if (up) {
-          Yup[0] = G[GS_Y0 * nc + c - layer]; Yup[1] = G[GS_Y1 * nc + c - layer]; Yup[2] = G[GS_Y2 * nc + c - layer];
-          Tup = G[GS_T * nc + c - layer];
-        }
-        const double Sj[3] = {S.s[SR_SH2], S.s[SR_SH2O], 0.0};
-        const double Snet = Sj[0] + Sj[1];
-        const double mg = eps * rho * B.vcell;
-        double Yn[3], ys = 0.0;
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          const double y = Y[j] + dtg * (-uz * (Y[j] - Yup[j]) / B.dz + (Sj[j] - Y[j] * Snet) / mg);
-          Yn[j] = fmax(y, 0.0);
-          ys += Yn[j];
-        }
-#pragma unroll
-        for (int j = 0; j < 3; ++j) Yn[j] = ys > 0.0 ? Yn[j] / ys : Y[j];
-        const double capc = eps * rho * cpg;
-        const double H0 = S.s[SR_HA] / B.vcell, H1 = S.s[SR_HAT] / B.vcell;
-        const double Mrm = -S.s[SR_QRM] / B.vcell;
-        const Tab<double> &td = tab<double>();
-        const double Mr = -(h_over_R<double>(0, T) * td.RMj[0] * Sj[0] + h_over_R<double>(1, T) * td.RMj[1] * Sj[1]) / B.vcell;
-        const double rhs = T + dtg * (-uz * (T - Tup) / B.dz + (H1 + Mr + Mrm) / capc);
-        T = rhs / (1.0 + dtg * H0 / capc);
-        eps = fmax(1.0 - S.s[SR_VS] / B.vcell, B.eps_min);
-#pragma unroll
-        for (int j = 0; j < 3; ++j) Y[j] = Yn[j];
-      } else {
-        // FP32 forms: increments in FP32, accumulated into the FP64 state
-        const Tab<R> &t = tab<R>();
-        const R dtg = bp.dtg;
-        const R rho = V.gp[GP_RHO * nc + c], cpg = V.gp[GP_CP * nc + c];
-        const R eps_r = V.gp[GP_EPS * nc + c], T_r = V.gp[GP_TG * nc + c];
-        const R uz = bp.U_in / eps_r;
-        const R Yr[3] = {(R)Y[0], (R)Y[1], (R)Y[2]};
-        R Yup[3] = {bp.Y_in[0], bp.Y_in[1], bp.Y_in[2]}, Tup = bp.T_in;
-        if (up) {
-          Yup[0] = (R)G[GS_Y0 * nc + c - layer]; Yup[1] = (R)G[GS_Y1 * nc + c - layer];
-          Yup[2] = (R)G[GS_Y2 * nc + c - layer];
-          Tup = (R)G[GS_T * nc + c - layer];   // the old state: props are rewritten in place
-        }
-        const R Sj[3] = {(R)S.s[SR_SH2], (R)S.s[SR_SH2O], (R)0};
-        const R Snet = Sj[0] + Sj[1];
-        const R inv_mg = bp.inv_vcell / (eps_r * rho);
-        bool clamp = false;
-        double Yn[3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          const R dy = dtg * (-uz * (Yr[j] - Yup[j]) * bp.inv_dz + (Sj[j] - Yr[j] * Snet) * inv_mg);
-          Yn[j] = Y[j] + (double)dy;
-          if (Yn[j] < 0.0) { Yn[j] = 0.0; clamp = true; }
-        }
-        if (clamp) {
-          const double ys = Yn[0] + Yn[1] + Yn[2];
-#pragma unroll
-          for (int j = 0; j < 3; ++j) Yn[j] = ys > 0.0 ? Yn[j] / ys : Y[j];
-        }
-        const R capc = eps_r * rho * cpg;
-        const R H0 = (R)S.s[SR_HA] * bp.inv_vcell, H1 = (R)S.s[SR_HAT] * bp.inv_vcell;
-        const R Mrm = -(R)S.s[SR_QRM] * bp.inv_vcell;
-        const R Mr = -(h_over_R<R>(0, T_r) * t.RMj[0] * Sj[0] + h_over_R<R>(1, T_r) * t.RMj[1] * Sj[1]) * bp.inv_vcell;
-        // T' - T of the semi-implicit update (eq (4-6)), H1 - H0 T formed before dividing
-        const R num = dtg * (-uz * (T_r - Tup) * bp.inv_dz + (H1 - H0 * T_r + Mr + Mrm) / capc);
-        const R den = (R)1 + dtg * H0 / capc;
-        T = T + (double)(num / den);
-        const R epsn = (R)1 - (R)S.s[SR_VS] * bp.inv_vcell;
-        eps = (double)(epsn > bp.eps_min ? epsn : bp.eps_min);
-#pragma unroll
-        for (int j = 0; j < 3; ++j) Y[j] = Yn[j];
+      S.run(V.src, cp, V.cstart[c], V.cend[c]);
+      const bool up = c - B.cell_off >= layer && !V.mark[c - layer];
+      const double dtg = B.ncouple * B.dt;
+      const double rho = (double)V.gp[GP_RHO * nc + c], cpg = (double)V.gp[GP_CP * nc + c];
+      const double uz = B.U_in / eps;
+      double Yup[3] = {B.Y_in[0], B.Y_in[1], B.Y_in[2]}, Tup = B.T_in;
+      if (up) {
+        Yup[0] = G[GS_Y0 * nc + c - layer]; Yup[1] = G[GS_Y1 * nc + c - layer]; Yup[2] = G[GS_Y2 * nc + c - layer];
+        Tup = G[GS_T * nc + c - layer];
       }
+      const double Sj[3] = {S.s[SR_SH2], S.s[SR_SH2O], 0.0};
+      const double Snet = Sj[0] + Sj[1];
+      const double mg = eps * rho * B.vcell;
+      double Yn[3], ys = 0.0;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const double y = Y[j] + dtg * (-uz * (Y[j] - Yup[j]) / B.dz + (Sj[j] - Y[j] * Snet) / mg);
+        Yn[j] = fmax(y, 0.0);
+        ys += Yn[j];
+      }
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Yn[j] = ys > 0.0 ? Yn[j] / ys : Y[j];
+      const double capc = eps * rho * cpg;
+      const double H0 = S.s[SR_HA] / B.vcell, H1 = S.s[SR_HAT] / B.vcell;
+      const double Mrm = -S.s[SR_QRM] / B.vcell;
+      const Tab<double> &td = tab<double>();
+      const double Mr = -(h_over_R<double>(0, T) * td.RMj[0] * Sj[0] + h_over_R<double>(1, T) * td.RMj[1] * Sj[1]) / B.vcell;
+      const double rhs = T + dtg * (-uz * (T - Tup) / B.dz + (H1 + Mr + Mrm) / capc);
+      T = rhs / (1.0 + dtg * H0 / capc);
+      eps = fmax(1.0 - S.s[SR_VS] / B.vcell, B.eps_min);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Y[j] = Yn[j];
     }
+    Gn[GS_EPS * nc + c] = eps;
+    Gn[GS_Y0 * nc + c] = Y[0]; Gn[GS_Y1 * nc + c] = Y[1]; Gn[GS_Y2 * nc + c] = Y[2];
+    Gn[GS_T * nc + c] = T;
+    const CellProps<double> p = gas_cell_props<double>(bp, eps, Y, T);
+    store_props(V, c, p);
+  } else {
+    // FP32 forms: FP32 increments added to compensated FP32 pairs; no FP64 arithmetic
+    const float2 *G2 = reinterpret_cast<const float2 *>(G);
+    float2 *Gn2 = reinterpret_cast<float2 *>(Gn);
+    float2 eps2 = G2[GS_EPS * nc + c], T2 = G2[GS_T * nc + c];
+    float2 Y2[3] = {G2[GS_Y0 * nc + c], G2[GS_Y1 * nc + c], G2[GS_Y2 * nc + c]};
+    if (mode == 1) {
+      float vs = 0.f, cc = 0.f;
+      for (unsigned j = V.cstart[c]; j < V.cend[c]; ++j) {
+        const float y = V.src[SR_VS * cp + j] - cc, t = vs + y;
+        cc = (t - vs) - y;
+        vs = t;
+      }
+      const float e = (float)1 - (vs - cc) * bp.inv_vcell;
+      eps2 = make_float2(solid ? bp.eps_min : (e > bp.eps_min ? e : bp.eps_min), 0.f);
+    } else if (update) {
+      CellSum<P> S;
+      S.run(V.src, cp, V.cstart[c], V.cend[c]);
+      const bool up = c - B.cell_off >= layer && !V.mark[c - layer];
+      const Tab<R> &t = tab<R>();
+      const R dtg = bp.dtg;
+      const R rho = V.gp[GP_RHO * nc + c], cpg = V.gp[GP_CP * nc + c];
+      const R eps_r = eps2.x + eps2.y, T_r = T2.x + T2.y;
+      const R uz = bp.U_in / eps_r;
+      const R Yr[3] = {Y2[0].x + Y2[0].y, Y2[1].x + Y2[1].y, Y2[2].x + Y2[2].y};
+      R Yup[3] = {bp.Y_in[0], bp.Y_in[1], bp.Y_in[2]}, Tup = bp.T_in;
+      if (up) {   // the old state of the cell below
+        Yup[0] = gas_r<P>(G, GS_Y0 * nc + c - layer); Yup[1] = gas_r<P>(G, GS_Y1 * nc + c - layer);
+        Yup[2] = gas_r<P>(G, GS_Y2 * nc + c - layer);
+        Tup = gas_r<P>(G, GS_T * nc + c - layer);
+      }
+      const R Sj[3] = {S.s[SR_SH2], S.s[SR_SH2O], (R)0};
+      const R Snet = Sj[0] + Sj[1];
+      const R inv_mg = bp.inv_vcell / (eps_r * rho);
+      bool clamp = false;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const R dy = dtg * (-uz * (Yr[j] - Yup[j]) * bp.inv_dz + (Sj[j] - Yr[j] * Snet) * inv_mg);
+        Y2[j] = pair_add(Y2[j], dy);
+        if (Y2[j].x + Y2[j].y < 0.f) { Y2[j] = make_float2(0.f, 0.f); clamp = true; }
+      }
+      if (clamp) {
+        const float ys = (Y2[0].x + Y2[0].y) + (Y2[1].x + Y2[1].y) + (Y2[2].x + Y2[2].y);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Y2[j] = make_float2(ys > 0.f ? (Y2[j].x + Y2[j].y) / ys : Yr[j], 0.f);
+      }
+      const R capc = eps_r * rho * cpg;
+      const R H0 = S.s[SR_HA] * bp.inv_vcell, H1 = S.s[SR_HAT] * bp.inv_vcell;
+      const R Mrm = -S.s[SR_QRM] * bp.inv_vcell;
+      const R Mr = -(h_over_R<R>(0, T_r) * t.RMj[0] * Sj[0] + h_over_R<R>(1, T_r) * t.RMj[1] * Sj[1]) * bp.inv_vcell;
+      // T' - T of the semi-implicit update (eq (4-6)), H1 - H0 T formed before dividing
+      const R num = dtg * (-uz * (T_r - Tup) * bp.inv_dz + (H1 - H0 * T_r + Mr + Mrm) / capc);
+      const R den = (R)1 + dtg * H0 / capc;
+      T2 = pair_add(T2, num / den);
+      const R epsn = (R)1 - S.s[SR_VS] * bp.inv_vcell;
+      eps2 = make_float2(epsn > bp.eps_min ? epsn : bp.eps_min, 0.f);
+    }
+    Gn2[GS_EPS * nc + c] = eps2;
+    Gn2[GS_Y0 * nc + c] = Y2[0]; Gn2[GS_Y1 * nc + c] = Y2[1]; Gn2[GS_Y2 * nc + c] = Y2[2];
+    Gn2[GS_T * nc + c] = T2;
+    const R Yr[3] = {Y2[0].x + Y2[0].y, Y2[1].x + Y2[1].y, Y2[2].x + Y2[2].y};
+    const CellProps<R> p = gas_cell_props<R>(bp, eps2.x + eps2.y, Yr, T2.x + T2.y);
+    store_props(V, c, p);
   }
-  Gn[GS_EPS * nc + c] = eps;
-  Gn[GS_Y0 * nc + c] = Y[0]; Gn[GS_Y1 * nc + c] = Y[1]; Gn[GS_Y2 * nc + c] = Y[2];
-  Gn[GS_T * nc + c] = T;
-  const R Yr[3] = {(R)Y[0], (R)Y[1], (R)Y[2]};
-  const CellProps<R> p = gas_cell_props<R>(bp, (R)eps, Yr, (R)T);
-  store_props(V, c, p);
 }
 
 // Cell sums of the last step's per-parcel sources (dem_get_sources).
@@ -606,7 +673,7 @@ __global__ void k_sources(StepView<P> V) {
   CellSum<P> S;
   S.run(V.src, cp, V.cstart[c], V.cend[c]);
   const bool solid = V.mark[c] != 0;
-  for (int f = 0; f < SR_N; ++f) V.dep[(size_t)c * SR_N + f] = solid ? 0.0 : S.s[f];
+  for (int f = 0; f < SR_N; ++f) V.dep[(size_t)c * SR_N + f] = solid ? 0.0 : (double)S.s[f];
 }
 
 // Initial per-parcel volume for the initial gas volume fraction.

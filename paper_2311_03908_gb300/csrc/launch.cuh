@@ -39,6 +39,9 @@ StepView<P> make_view(dem_ctx *c, bool for_step) {
   V.vals = c->vres ? c->vres : c->vals;
   V.cstart = c->cstart; V.cend = c->cend;
   V.xl = c->xl;
+  V.xlk = c->xlk;
+  V.corner = c->corner;
+  V.kprev = c->kres ? c->kres : c->keys;
   V.mass = (R *)c->mass;
   for (int q = 0; q < 3; ++q) { V.F[q] = (R *)c->F[q]; V.Tq[q] = (R *)c->Tq[q]; }
   V.src = (R *)c->src;
@@ -92,7 +95,7 @@ int enqueue_steps(dem_ctx *c, int nsteps) {
     if (e) return e;
     StepView<P> V = make_view<P>(c, true);
     int ps = prof_begin(c, "k_contacts");
-    k_contacts<P><<<grid_for(c->n, c->bs_contacts), c->bs_contacts, 0, st>>>(V);
+    k_contacts<P><<<grid_for(c->n, c->bs_contacts), c->bs_contacts, contacts_smem(c->bs_contacts), st>>>(V);
     prof_end(c, ps);
     ps = prof_begin(c, "k_gas_particle");
     k_gas_particle<P><<<grid_for(c->n, c->bs_gp), c->bs_gp, 0, st>>>(V);
