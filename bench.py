@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=100_000, help="parcels in the oracle's sample")
     ap.add_argument("--parcels", type=int, default=0, help="override the workload's parcel count "
                     "(smaller cases for profiler captures; same geometry and packing)")
+    ap.add_argument("--autotune", type=int, default=30, help="steps per autotuner candidate before the "
+                    "warm-up (0: keep the default launch configuration)")
     return ap.parse_args()
 
 
@@ -65,31 +67,30 @@ def make_workload(name: str, rank: int = 0, parcels: int = 0):
 
 # ---------------------------------------------------------------------------------------
 # Algorithmic bytes per launch of each kernel: the traffic the method cannot avoid in this
-# layout -- every parcel's own state read and written once, every occupied cell's state
-# once, z_bar live contact slots per parcel -- not counting re-reads of neighbours.
+# layout -- every parcel's own record read and written once, every cell's state once, the
+# live contact slots (z_bar per parcel) and neighbour-list entries (L per parcel) once -- not
+# counting the re-reads of neighbours' records, which the caches serve.
 # ---------------------------------------------------------------------------------------
-def algorithmic_bytes(kernel: str, n: int, ncells: int, zbar: float, rsize: int, passes: int) -> float:
+def algorithmic_bytes(kernel: str, n: int, ncells: int, zbar: float, L: float, rsize: int, passes: int) -> float:
     R = rsize
-    slot = 4 + 3 * R                       # partner id + tangential displacement
-    state_r = 24 + 12 * R + 2 * R + 32 + 8  # x,y,z; v,w,a,al; T,d; masses; meta, orig
+    slot = 4 + 3 * R                                  # partner id + tangential displacement
+    state = 24 + 12 * R + 2 * R + 32 + 4 * 3 + 12     # x; v,w,a,al; T,d; masses; meta,orig,bidx; dsp
     if kernel == "k_key":
-        return n * (24 + 6 * R + 4 + 8)
+        return n * ((4 + 24 + 6 * R + 12 + 16 + 4 + R) + (24 + 12 + 16 + 8))
     if kernel == "radix_sort":
-        return n * passes * (4 + 8 + 8)
+        return n * passes * (8 + 8)
     if kernel == "k_gather":
-        per = 4 + state_r + 1 + zbar * slot                      # read
-        per += state_r + R + 16 + 4 + 1 + zbar * slot             # write (+ mass, xf, gcell)
-        return n * per
-    if kernel == "k_contacts":
-        per = 24 + 16 + R + R + 6 * R + 4 + 4 + 1 + zbar * slot  # read own record + old slots
-        per += 6 * R + 1 + zbar * slot                            # write force, torque, slots
-        return n * per
+        return n * ((8 + state + 16 + 1 + zbar * slot) + (state + R + 16 + 4 + 1 + zbar * slot))
+    if kernel == "k_pair_search":
+        return n * ((4 + 16 + 4 + 4 + 1 + 4 * L) + (1 + 5 * zbar))
+    if kernel == "k_pair_forces":
+        return n * ((4 + 1 + 1 + 16 + 4 + 2 * R + 6 * R + 5 * zbar + zbar * slot) + (1 + zbar * slot + 6 * R))
+    if kernel == "k_contacts_cell":
+        return n * ((4 + 16 + 4 + 1 + 2 * R + 6 * R + zbar * slot) + (1 + zbar * slot + 6 * R))
     if kernel == "k_gas_particle":
-        per = 4 + 4 + R + 3 * R + R + 32 + R + 6 * R + 3 * R       # read
-        per += 12 * R + R + 32 + 14 * R                           # write state + sources
-        return n * per + ncells * 14 * R                           # cell properties once
+        return n * ((4 + 4 + R + 3 * R + R + 32 + R + 6 * R + 3 * R) + (12 * R + R + 32 + 14 * R)) + ncells * 13 * R
     if kernel == "k_cells":
-        return ncells * (1 + 4 + 8 + 5 * 8 + 5 * 8 + 14 * R) + n * 14 * R
+        return ncells * ((4 + 1 + 8 + 5 * 8 + 2 * R) + (5 * 8 + 14 * R)) + n * 14 * R
     return 0.0
 
 
@@ -216,6 +217,7 @@ def main():
     bed = make_workload(args.workload, rank, args.parcels)
     ctx = binding.Context(bed, precision=args.precision, stream=stream.cuda_stream)
     n = bed.n
+    tuning = ctx.dem_autotune(args.autotune) if args.autotune > 0 else ctx.dem_get_tuning()
 
     def barrier():
         torch.cuda.synchronize()
@@ -227,6 +229,7 @@ def main():
     for _ in range(args.warmup):
         ctx.dem_step_graph(1)
     ctx.dem_sync()
+    c_pre = ctx.dem_get_counters()
     launches_per_step = None
     clocks = ClockSampler(local)
     barrier()
@@ -244,6 +247,7 @@ def main():
     ms = e0.elapsed_time(e1)
     ck = clocks.stop()
     ctx.dem_sync()
+    c_post = ctx.dem_get_counters()
     t = torch.tensor([ms], dtype=torch.float64, device="cuda")
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -259,6 +263,8 @@ def main():
     cnt, _, _ = ctx.dem_get_contacts()
     zbar = float(cnt.mean())
     ncells = ctx.ncells
+    steps_done, builds, entries = ctx.dem_get_counters()
+    L = entries / n
     rsize = 8 if args.precision == "fp64" else 4
     key_bits = max(1, math.ceil(math.log2(max(2, sum(c.nx * c.ny * c.nz for c in bed.beds)))))
     passes = (key_bits + 7) // 8
@@ -266,7 +272,7 @@ def main():
     kernels = {}
     for name, (nl, tot) in times.items():
         avg = tot / max(nl, 1)
-        b = algorithmic_bytes(name, n, ncells, zbar, rsize, passes)
+        b = algorithmic_bytes(name, n, ncells, zbar, L, rsize, passes)
         kernels[name] = {"launches": nl, "avg_ms": avg, "alg_bytes": b,
                          "gbs": (b / (avg * 1e-3) / 1e9) if avg > 0 and b > 0 else None}
     dom = max(kernels, key=lambda k: kernels[k]["avg_ms"]) if kernels else None
@@ -287,7 +293,10 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "gpu_launches": total_launches, "clocks": ck,
             "kernels": kernels, "step_alg_bytes": step_alg,
-            "step_alg_gbs": step_alg / (step_ms * 1e-3) / 1e9, "zbar_contacts": zbar}
+            "step_alg_gbs": step_alg / (step_ms * 1e-3) / 1e9, "zbar_contacts": zbar,
+            "neighbour_lists": {"mean_length": L, "builds_in_timed_steps": c_post[1] - c_pre[1], "builds_total": builds,
+                                "steps_total": steps_done},
+            "tuning": tuning}
 
     # the all-FP64 form of the same workload (split vs FP64 comparison)
     if not args.no_fp64_form and args.precision != "fp64":

@@ -202,9 +202,30 @@ enum { DEM_NDIAG = 32 };
 int dem_set_diagnostics(dem_ctx *c, int32_t on);
 int dem_get_diag(dem_ctx *c, double *out_host);
 
-/* Pick block sizes of the hot kernels by timing candidates on n_steps steps; the state is
- * saved before and restored after, so the simulation is unchanged. */
+/* Launch configuration of the step kernels (no counterpart in the paper: it only changes how
+ * the same step is computed), DEM_NTUNE int32 values:
+ *   [0] contact kernels: 0 = one thread per parcel (neighbour-list search + force kernel),
+ *       1 = one warp per occupied cell (cell-list search every step, fused forces);
+ *   [1]..[6] block sizes of the key, gather, pair-search, pair-force, gas-particle and
+ *       gas-cell kernels (multiples of 32 in [32, 1024], and no larger than the kernel's
+ *       register use allows: the FP64 form's larger kernels stop below 512);
+ *   [7] neighbour-list skin in thousandths of the bed's largest parcel diameter (1..1000).
+ * dem_set_tuning validates every value (DEM_EINVAL, nothing changed), drops captured graphs
+ * and makes the next step rebuild the neighbour lists; results can then differ from an
+ * untuned run in the last bits (order of the force sums), never in the pair sets. */
+enum { DEM_NTUNE = 8 };
+int dem_get_tuning(dem_ctx *c, int32_t *out);
+int dem_set_tuning(dem_ctx *c, const int32_t *in);
+
+/* Pick the tuning above by timing candidates, each over n_steps steps started from the same
+ * saved state (contact kernel, block sizes, skin). The state is restored afterwards and the
+ * chosen tuning applied (as dem_set_tuning). Needs a temporary device copy of the context's
+ * arena (DEM_ENOMEM if it cannot be allocated); clears the dem_profile record. Synchronous. */
 int dem_autotune(dem_ctx *c, int32_t n_steps);
+
+/* Counters since dem_init (3 values, host): steps taken, neighbour-list builds, and the total
+ * number of list entries at the last build (their mean length is that over n). Synchronous. */
+int dem_get_counters(dem_ctx *c, int64_t *out);
 
 /* Number of kernels launched by the last dem_step/dem_step_graph call (for accounting). */
 int64_t dem_last_launch_count(dem_ctx *c);

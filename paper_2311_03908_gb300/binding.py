@@ -21,6 +21,9 @@ DEM_MAX_CONTACTS = 24
 DEM_NSTATE, DEM_NGAS, DEM_NDEP, DEM_NDIAG = 20, 6, 14, 32
 DEM_NOALLOC_MAX_PARCELS = 8388608
 PRECISIONS = {"fp64": DEM_PREC_FP64, "split": DEM_PREC_SPLIT, "split_kahan": DEM_PREC_SPLIT_KAHAN}
+DEM_NTUNE = 8
+TUNING_KEYS = ("contact_kernel", "bs_key", "bs_gather", "bs_search", "bs_forces", "bs_gas_particle", "bs_cells",
+               "skin_permille")
 
 STATE_ROWS = ["x", "y", "z", "vx", "vy", "vz", "wx", "wy", "wz", "T", "m_h", "m_m", "m_w", "m_fe",
               "ax", "ay", "az", "alx", "aly", "alz"]
@@ -91,6 +94,9 @@ def lib() -> C.CDLL:
         "dem_set_diagnostics": (C.c_int, [vp, C.c_int32]),
         "dem_get_diag": (C.c_int, [vp, dp]),
         "dem_autotune": (C.c_int, [vp, C.c_int32]),
+        "dem_get_tuning": (C.c_int, [vp, C.POINTER(C.c_int32)]),
+        "dem_set_tuning": (C.c_int, [vp, C.POINTER(C.c_int32)]),
+        "dem_get_counters": (C.c_int, [vp, C.POINTER(C.c_int64)]),
         "dem_last_launch_count": (C.c_int64, [vp]),
         "dem_set_gas": (C.c_int, [vp, C.POINTER(DemGas)]),
         "dem_profile": (C.c_int, [vp, C.c_int32]),
@@ -272,8 +278,31 @@ class Context:
         _check(lib().dem_get_diag(self.h, out.ctypes.data_as(C.POINTER(C.c_double))), "dem_get_diag")
         return out
 
-    def dem_autotune(self, nsteps=3):
+    def dem_autotune(self, nsteps=30):
         _check(lib().dem_autotune(self.h, int(nsteps)), "dem_autotune")
+        return self.dem_get_tuning()
+
+    def dem_get_tuning(self):
+        """Launch configuration: dict with the DEM_NTUNE values by name."""
+        t = (C.c_int32 * DEM_NTUNE)()
+        _check(lib().dem_get_tuning(self.h, t), "dem_get_tuning")
+        return dict(zip(TUNING_KEYS, [int(v) for v in t]))
+
+    def dem_set_tuning(self, **kw):
+        """Change named entries of the launch configuration (see TUNING_KEYS)."""
+        cur = self.dem_get_tuning()
+        for k, v in kw.items():
+            if k not in cur:
+                raise KeyError(k)
+            cur[k] = int(v)
+        t = (C.c_int32 * DEM_NTUNE)(*[cur[k] for k in TUNING_KEYS])
+        _check(lib().dem_set_tuning(self.h, t), "dem_set_tuning")
+
+    def dem_get_counters(self):
+        """(steps taken, neighbour-list builds, list entries at the last build) since dem_init."""
+        v = (C.c_int64 * 3)()
+        _check(lib().dem_get_counters(self.h, v), "dem_get_counters")
+        return int(v[0]), int(v[1]), int(v[2])
 
     def dem_set_gas(self, Y, T):
         """Y: (cells, 3) mass fractions, T: (cells,) temperatures; numpy (host, ideally pinned)

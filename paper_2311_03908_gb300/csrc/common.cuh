@@ -56,6 +56,8 @@ struct DevBed {
   int nx, ny, nz;
   long long cell_off;           // first global gas cell (and sort key) of this bed
   int corner_off;               // first entry of this bed in the cell-corner table
+  float inv_nx_f, inv_nxy_f;    // 1/nx, 1/(nx ny): cell offsets from key differences
+  int fast_offsets;             // nx, ny >= 5: offsets in [-2, 2] decode by rounding
   double R_bed, H, cos_a, sin_a, z_apex, plate_z, pitch, inv_pitch, r_hole;
   int wall;
   double dt, k;
@@ -79,6 +81,7 @@ template <class R> struct BedP {
   R dpdz, grav, dtg;
   R pf_margin;                  // prefilter margin of the exact (FP64) pair test, m
   R reach_max;                  // largest parcel radius of the bed (CGP), m
+  R skin, half_skin2;           // neighbour-list skin (m) and (skin / 2)^2
   unsigned flags;
   int ncouple, wall;
 };
@@ -151,6 +154,27 @@ template <> __device__ __forceinline__ const Tab<double> &tab<double>() { return
 // Thermochemistry (eqs (3-22), (3-23)): molar enthalpy / R and molar heat capacity / R.
 // Species index s: 0 H2, 1 H2O, 2 N2, 3 Fe2O3, 4 Fe3O4, 5 FeO, 6 Fe.
 // ---------------------------------------------------------------------------------------
+// Elementary functions in the form's arithmetic type. The FP64 form uses the libm
+// functions and IEEE division; the FP32 forms use the hardware approximations (__expf,
+// __logf, reciprocal-based division: errors of a few ulp, or ~1e-6 relative for exp of
+// arguments up to ~20), far inside those forms' 1e-4 tolerance against the FP64 oracle.
+template <class R> __device__ __forceinline__ R fexp(R x) {
+  if constexpr (sizeof(R) == 8) return exp(x); else return __expf(x);
+}
+template <class R> __device__ __forceinline__ R flog(R x) {
+  if constexpr (sizeof(R) == 8) return log(x); else return __logf(x);
+}
+// cube root of x >= 0 (FP32: exp(log(x) / 3))
+template <class R> __device__ __forceinline__ R fcbrt(R x) {
+  if constexpr (sizeof(R) == 8) return cbrt(x); else return __expf(__logf(x) * (1.0f / 3.0f));
+}
+template <class R> __device__ __forceinline__ R fdiv(R a, R b) {
+  if constexpr (sizeof(R) == 8) return a / b; else return __fdividef(a, b);
+}
+template <class R> __device__ __forceinline__ R frcp(R x) {
+  if constexpr (sizeof(R) == 8) return 1.0 / x; else return __fdividef(1.0f, x);
+}
+
 template <class R> __device__ __forceinline__ R h_over_R(int s, R T) {
   const Tab<R> &t = tab<R>();
   const R *a = t.h[s][T <= t.nasaT[s] ? 0 : 1];
@@ -179,12 +203,12 @@ __device__ inline CellProps<R> gas_cell_props(const BedP<R> &B, R eps, const R Y
   const Tab<R> &t = tab<R>();
   CellProps<R> o;
   const R p = B.p0;
-  const R inv = Y[0] / t.Mj[0] + Y[1] / t.Mj[1] + Y[2] / t.Mj[2];
-  const R Mg = (R)1 / inv;
-  const R xp0 = Y[0] * Mg / t.Mj[0], xp1 = Y[1] * Mg / t.Mj[1], xp2 = Y[2] * Mg / t.Mj[2];
+  const R inv = fdiv<R>(Y[0], t.Mj[0]) + fdiv<R>(Y[1], t.Mj[1]) + fdiv<R>(Y[2], t.Mj[2]);
+  const R Mg = frcp<R>(inv);
+  const R xp0 = fdiv<R>(Y[0] * Mg, t.Mj[0]), xp1 = fdiv<R>(Y[1] * Mg, t.Mj[1]), xp2 = fdiv<R>(Y[2] * Mg, t.Mj[2]);
   const R den = xp0 + xp1;
-  o.x = den > (R)0 ? xp0 / den : (R)0;
-  o.rho = Mg * p / ((R)kRgas * T);
+  o.x = den > (R)0 ? fdiv<R>(xp0, den) : (R)0;
+  o.rho = fdiv<R>(Mg * p, (R)kRgas * T);
   R mu = 0, lam = 0, cp = 0;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
@@ -199,10 +223,10 @@ __device__ inline CellProps<R> gas_cell_props(const BedP<R> &B, R eps, const R Y
   const R tf = T * sT * sqrt(sT) * ((R)101325 / p) * (R)1e-7;
   const R D12 = tf * B.fuller12, D13 = tf * B.fuller13;
   const R rest = (R)1 - xp0;
-  o.Dm = rest < (R)1e-12 ? D12 : rest / (xp1 / D12 + xp2 / D13);
-  o.sc13 = cbrt(mu / (o.rho * o.Dm));
-  o.pr13 = cbrt(cp * mu / lam);
-  o.epow = exp((R)-2.65 * log(eps));
+  o.Dm = rest < (R)1e-12 ? D12 : fdiv<R>(rest, fdiv<R>(xp1, D12) + fdiv<R>(xp2, D13));
+  o.sc13 = fcbrt<R>(fdiv<R>(mu, o.rho * o.Dm));
+  o.pr13 = fcbrt<R>(fdiv<R>(cp * mu, lam));
+  o.epow = fexp<R>((R)-2.65 * flog<R>(eps));
   // pore diffusion per ore: molecular, Knudsen, or Bosanquet by lambda / d_a (Sec. 2.3)
   const R mfp = o.x > (R)0 ? B.mfp_c / o.x : (R)3e38;
   const R sq = sqrt(T / (t.Mj[0] * (R)1e3));
@@ -210,9 +234,9 @@ __device__ inline CellProps<R> gas_cell_props(const BedP<R> &B, R eps, const R Y
   for (int ore = 0; ore < 2; ++ore) {
     const R DK = B.DKc[ore] * sq;
     const R ratio = mfp / B.pore_cm[ore];
-    o.D[ore] = ratio <= (R)0.01 ? o.Dm : (ratio >= (R)10 ? DK : (R)1 / ((R)1 / o.Dm + (R)1 / DK));
+    o.D[ore] = ratio <= (R)0.01 ? o.Dm : (ratio >= (R)10 ? DK : frcp<R>(frcp<R>(o.Dm) + frcp<R>(DK)));
   }
-  o.uz = B.U_in / eps;
+  o.uz = fdiv<R>(B.U_in, eps);
   o.eps = eps;
   o.T = T;
   return o;
@@ -226,7 +250,7 @@ template <class R> struct Gas {   // a cell's properties in the parcel's arithme
 };
 
 template <class R> __device__ __forceinline__ R pos_pow(R x, R e) {   // x^e for x >= 0
-  return x > (R)0 ? exp(e * log(x)) : (R)0;
+  return x > (R)0 ? fexp<R>(e * flog<R>(x)) : (R)0;
 }
 
 // Gunn correlation (eqs (2-22), (3-12)); c13 is Sc^(1/3) or Pr^(1/3), re02 = Re^0.2
@@ -242,16 +266,16 @@ __device__ __forceinline__ R beta_over_epsp(const BedP<R> &B, int ore, R d, cons
   const R eps = g.eps, ep = (R)1 - eps;
   const R psi = B.psi[ore];
   if (eps < (R)0.8)
-    return (R)150 * ep * g.mu / (eps * d * d * psi * psi) + (R)1.75 * eps * g.rho * slip / (d * psi * ep);
+    return fdiv<R>((R)150 * ep * g.mu, eps * d * d * psi * psi) + fdiv<R>((R)1.75 * eps * g.rho * slip, d * psi * ep);
   const R K1 = B.K1b[ore] - B.wall_K1 * d;
   const R K2 = B.K2[ore];
   if (Re > (R)0) {
     const R RK = Re * (K1 * K2);
-    const R CD = (R)24 / (Re * K1) * ((R)1 + (R)0.1118 * pos_pow(RK, (R)0.6567)) +
-                 (R)0.4305 * K2 / ((R)1 + (R)3305 / RK);
-    return (R)0.75 * CD * eps * g.rho * slip / d * g.epow;
+    const R CD = fdiv<R>((R)24, Re * K1) * ((R)1 + (R)0.1118 * pos_pow(RK, (R)0.6567)) +
+                 fdiv<R>((R)0.4305 * K2, (R)1 + fdiv<R>((R)3305, RK));
+    return fdiv<R>((R)0.75 * CD * eps * g.rho * slip, d) * g.epow;
   }
-  return (R)0.75 * ((R)24 / K1) * g.mu / (d * d) * g.epow;
+  return (R)0.75 * fdiv<R>((R)24 * g.mu, K1 * d * d) * g.epow;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -276,42 +300,43 @@ __device__ __forceinline__ void uscm(const BedP<R> &Bd, const R m[4], R Tp, R d,
   o.sH2 = o.sH2O = o.Qr = o.Qrm = o.EQ = o.ES = o.F = o.Sh = 0;
   R n[4];
 #pragma unroll
-  for (int z = 0; z < 4; ++z) n[z] = m[z] * Bd.inv_k3 / t.Mz[z];
+  for (int z = 0; z < 4; ++z) n[z] = fdiv<R>(m[z] * Bd.inv_k3, t.Mz[z]);
   const R nfe = (R)2 * n[0] + (R)3 * n[1] + n[2] + n[3];
   if (!(nfe > (R)0)) return;
-  const R inv_nfe = (R)1 / nfe;
+  const R inv_nfe = frcp<R>(nfe);
   // 1 - f of eqs (2-15)..(2-17), written as the iron fractions still behind each front
   R om[3];
   om[0] = (R)2 * n[0] * inv_nfe;
   om[1] = ((R)2 * n[0] + (R)3 * n[1]) * inv_nfe;
   om[2] = ((R)2 * n[0] + (R)3 * n[1] + n[2]) * inv_nfe;
-  const R invT = (R)1 / Tp;
+  const R invT = frcp<R>(Tp);
   R xeq[3], gk[3], c3[3];
   bool act[3];
   const bool kin = !(fl & DEM_NO_KINETICS);
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    const R K = exp(t.Ka[r] * invT + t.Kb[r]);                 // Table 2
-    xeq[r] = (R)1 / (K + (R)1);                                  // eq (2-1-3)
-    const R kr = Bd.k0[r] * exp(-Bd.Ea_R[r] * invT);             // eq (2-13)
-    c3[r] = cbrt(om[r]);
+    const R K = fexp<R>(t.Ka[r] * invT + t.Kb[r]);             // Table 2
+    xeq[r] = frcp<R>(K + (R)1);                                  // eq (2-1-3)
+    const R kr = Bd.k0[r] * fexp<R>(-Bd.Ea_R[r] * invT);         // eq (2-13)
+    c3[r] = fcbrt<R>(om[r]);
     act[r] = kin && n[r] > (R)0 && g.x > xeq[r] && Bd.k0[r] > (R)0;
     // 1/A of eq (2-12): k_r (1-f)^(2/3) (1 + K)/K
-    gk[r] = act[r] ? kr * c3[r] * c3[r] * ((R)1 + (R)1 / K) : (R)0;
+    gk[r] = act[r] ? kr * c3[r] * c3[r] * ((R)1 + frcp<R>(K)) : (R)0;
   }
   // product-layer resistances, eq (2-14), with D_eff of eq (2-30)
-  const R rp_tau = (R)0.5 * d / (g.D * Bd.inv_tau);
+  const R rp_tau = fdiv<R>((R)0.5 * d, g.D * Bd.inv_tau);
   R Bm = 0, Bw = 0, BFe = 0;
   if (!(fl & DEM_NO_LAYER)) {
-    if (act[0]) Bm = rp_tau / Bd.xi[ore][0] * ((R)1 / c3[0] - (R)1 / c3[1]);
-    if ((act[0] || act[1]) && om[1] > (R)0) Bw = rp_tau / Bd.xi[ore][1] * ((R)1 / c3[1] - (R)1 / c3[2]);
-    if (om[2] > (R)0) BFe = rp_tau / Bd.xi[ore][2] * ((R)1 / c3[2] - (R)1);
+    const R ic0 = frcp<R>(c3[0]), ic1 = frcp<R>(c3[1]), ic2 = frcp<R>(c3[2]);
+    if (act[0]) Bm = fdiv<R>(rp_tau, Bd.xi[ore][0]) * (ic0 - ic1);
+    if ((act[0] || act[1]) && om[1] > (R)0) Bw = fdiv<R>(rp_tau, Bd.xi[ore][1]) * (ic1 - ic2);
+    if (om[2] > (R)0) BFe = fdiv<R>(rp_tau, Bd.xi[ore][2]) * (ic2 - (R)1);
   }
   // gas film, eqs (2-20)..(2-24)
   o.Sh = gunn(g.eps, re02, re07, g.sc13);
-  const R F = (fl & DEM_NO_FILM) ? (R)0 : d / (o.Sh * g.Dm);
+  const R F = (fl & DEM_NO_FILM) ? (R)0 : fdiv<R>(d, o.Sh * g.Dm);
 #pragma unroll
-  for (int r = 0; r < 3; ++r) o.A[r] = gk[r] > (R)0 ? (R)1 / gk[r] : (R)0;
+  for (int r = 0; r < 3; ++r) o.A[r] = gk[r] > (R)0 ? frcp<R>(gk[r]) : (R)0;
   // closed-form network; a reaction whose flux is negative is dropped and the rest re-solved
   const R S = F + BFe, BwS = Bw + S;
   R J[3] = {0, 0, 0}, vsum[3] = {0, 0, 0};
@@ -319,7 +344,7 @@ __device__ __forceinline__ void uscm(const BedP<R> &Bd, const R m[4], R Tp, R d,
     const R g1 = gk[0], g2 = gk[1], g3 = gk[2];
     const R a1 = (R)1 + Bm * g1;
     const R W = a1 * ((R)1 + BwS * g2 + S * g3 * ((R)1 + Bw * g2)) + g1 * (BwS + Bw * S * g3);
-    const R iW = (R)1 / W;
+    const R iW = frcp<R>(W);
     const R v11 = g1 * (((R)1 + BwS * g2) + S * g3 * ((R)1 + Bw * g2)) * iW;
     const R v12 = -g1 * g2 * (BwS + Bw * S * g3) * iW;
     const R v13 = -S * g1 * g3 * iW;
@@ -341,11 +366,11 @@ __device__ __forceinline__ void uscm(const BedP<R> &Bd, const R m[4], R Tp, R d,
   }
   // molar rates per real particle (eq (2-1), eta = 1), limited by the reactant present
   const R c = Bd.rate_c * d * d * invT;
-  const R inv_dtm = (R)1 / dtm;
+  const R inv_dtm = frcp<R>(dtm);
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     R x = gk[r] > (R)0 ? c * J[r] : (R)0;
-    const R cap = n[r] / (r == 0 ? (R)3 : (R)1) * inv_dtm;
+    const R cap = fdiv<R>(n[r], r == 0 ? (R)3 : (R)1) * inv_dtm;
     x = x < cap ? x : cap;
     o.xidot[r] = x > (R)0 ? x : (R)0;
   }

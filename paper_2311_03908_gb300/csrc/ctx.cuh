@@ -28,7 +28,8 @@ struct dem_ctx {
   double *px[2][3] = {};
   void *pv[2][3] = {}, *pw[2][3] = {}, *pa[2][3] = {}, *pal[2][3] = {}, *pT[2] = {}, *pd[2] = {};
   double *pm[2][4] = {};
-  int *pmeta[2] = {}, *porig[2] = {};
+  int *pmeta[2] = {}, *porig[2] = {}, *pbidx[2] = {};
+  float *pdsp[2][3] = {};
   // contact history: [0] current, [1] gather target
   unsigned char *hcnt[2] = {};
   int *hid[2] = {};
@@ -39,6 +40,11 @@ struct dem_ctx {
   unsigned *cstart = nullptr, *cend = nullptr;
   float4 *xl = nullptr;             // cell-local position and radius, sorted order
   float4 *xlk = nullptr;            // the same, written by the key kernel (pre-sort order)
+  int *plist = nullptr;             // pair-search hit lists [KLIST][cap]
+  unsigned char *pcode = nullptr, *pcnt = nullptr;
+  int *nl = nullptr, *curpos = nullptr, *rebuild = nullptr;   // neighbour lists
+  unsigned char *nlc = nullptr;
+  double skin_frac = 0.1;         // neighbour-list skin as a fraction of the largest diameter
   double *corner = nullptr;         // cell-corner coordinates: per bed x0+i dx, y0+j dy, z0+k dz
   std::vector<double> hcorner;
   void *mass = nullptr, *F[3] = {}, *Tq[3] = {}, *src = nullptr;
@@ -62,6 +68,8 @@ struct dem_ctx {
   int sticky = DEM_OK;
   long long launches = 0;
   int bs_contacts = 128, bs_gp = 128, bs_gather = 256, bs_cells = 256, bs_key = 256;
+  int contact_mode = 0;            // 0: one thread per parcel (search + forces), 1: one warp per occupied cell
+  int bs_search = 256;
   std::map<std::tuple<int, int, int>, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;
   std::map<std::tuple<int, int, int>, long long> graph_launches;
   cudaStream_t gst = nullptr;     // private stream used to capture graphs
@@ -80,6 +88,7 @@ struct dem_ctx {
 
 namespace dem {
 
+template <class P> int kernel_limits(int *lim);
 template <class P> StepView<P> make_view(dem_ctx *c, bool for_step);
 template <class P> int enqueue_steps(dem_ctx *c, int nsteps);
 template <class P> int enqueue_init(dem_ctx *c);

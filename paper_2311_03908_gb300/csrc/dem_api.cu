@@ -13,7 +13,15 @@ using dem::DevBed;
 
 namespace dem {
 
-__global__ void k_step_counter(long long *ctr) { *ctr += 1; }
+__global__ void k_step_counter(long long *ctr, int *rebuild, int lists) {
+  ctr[0] += 1;
+  if (lists && *rebuild) {   // neighbour-list builds, and the list entries of the last one
+    ctr[1] += 1;
+    ctr[2] = ctr[3];
+    ctr[3] = 0;
+  }
+  *rebuild = 0;   // the lists built this step (if any) are current
+}
 
 __global__ void k_mark_cells(const DevBed *beds, const int *cell_bed, unsigned char *mark, long long ncells) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -286,6 +294,11 @@ struct Bump {
   }
 };
 
+template <class R> void set_skin(BedP<R> &P, double skin) {
+  P.skin = (R)skin;
+  P.half_skin2 = (R)(0.49 * 0.49 * skin * skin);   // 2% below half the skin: FP32 displacements
+}
+
 // Lay out (or measure, when base is null) every arena buffer.
 void layout(dem_ctx *c, Bump &m) {
   const size_t N = (size_t)c->cap, R = c->rsize, C = (size_t)c->ncells;
@@ -300,6 +313,8 @@ void layout(dem_ctx *c, Bump &m) {
     for (int q = 0; q < 4; ++q) c->pm[k][q] = m.take<double>(N);
     c->pmeta[k] = m.take<int>(N);
     c->porig[k] = m.take<int>(N);
+    c->pbidx[k] = m.take<int>(N);
+    for (int q = 0; q < 3; ++q) c->pdsp[k][q] = m.take<float>(N);
     c->hcnt[k] = m.take<unsigned char>(N);
     c->hid[k] = m.take<int>(N * KMAX);
     c->hxi[k] = m.take<char>(N * KMAX * 3, R);
@@ -310,6 +325,13 @@ void layout(dem_ctx *c, Bump &m) {
   c->cstart = m.take<unsigned>(C); c->cend = m.take<unsigned>(C);
   c->xl = m.take<float4>(N);
   c->xlk = m.take<float4>(N);
+  c->plist = m.take<int>(N * KLIST);
+  c->pcode = m.take<unsigned char>(N * KLIST);
+  c->pcnt = m.take<unsigned char>(N);
+  c->nl = m.take<int>(N * KNL);
+  c->nlc = m.take<unsigned char>(N);
+  c->curpos = m.take<int>(N);
+  c->rebuild = m.take<int>(1);
   c->corner = m.take<double>(c->hcorner.size());
   c->mass = m.take<char>(N, R);
   for (int q = 0; q < 3; ++q) { c->F[q] = m.take<char>(N, R); c->Tq[q] = m.take<char>(N, R); }
@@ -322,13 +344,55 @@ void layout(dem_ctx *c, Bump &m) {
   c->fv = m.take<double>(N * 3);
   c->fvbed = m.take<double>((size_t)c->nbeds * 4);
   c->err = m.take<int>(1);
-  c->step_ctr = m.take<long long>(1);
+  c->step_ctr = m.take<long long>(4);
   c->dbeds = m.take<DevBed>(c->nbeds);
   c->dbp_d = m.take<BedP<double>>(c->nbeds);
   c->dbp_f = m.take<BedP<float>>(c->nbeds);
 }
 
 int enqueue_steps_any(dem_ctx *c, int n) { return DEM_DISPATCH(c, enqueue_steps, c, n); }
+
+// captured graphs bake launch shapes and pointers in
+void drop_graphs(dem_ctx *c) {
+  for (auto &kv : c->graphs) {
+    cudaGraphExecDestroy(kv.second.second);
+    cudaGraphDestroy(kv.second.first);
+  }
+  c->graphs.clear();
+  c->graph_launches.clear();
+}
+
+void get_tuning(const dem_ctx *c, int32_t *t) {
+  t[0] = c->contact_mode;
+  t[1] = c->bs_key; t[2] = c->bs_gather; t[3] = c->bs_search; t[4] = c->bs_contacts;
+  t[5] = c->bs_gp; t[6] = c->bs_cells;
+  t[7] = (int32_t)std::lround(c->skin_frac * 1000.0);
+}
+
+int apply_tuning(dem_ctx *c, const int32_t *t) {
+  if (t[0] != 0 && t[0] != 1) return DEM_EINVAL;
+  int lim[6];
+  if (DEM_DISPATCH(c, kernel_limits, lim) != 0) return DEM_ECUDA;
+  for (int k = 1; k <= 6; ++k)
+    if (t[k] < 32 || t[k] > 1024 || t[k] % 32 != 0 || t[k] > lim[k - 1]) return DEM_EINVAL;
+  if (t[7] < 1 || t[7] > 1000) return DEM_EINVAL;
+  c->contact_mode = t[0];
+  c->bs_key = t[1]; c->bs_gather = t[2]; c->bs_search = t[3]; c->bs_contacts = t[4];
+  c->bs_gp = t[5]; c->bs_cells = t[6];
+  c->skin_frac = t[7] / 1000.0;
+  for (int b = 0; b < c->nbeds; ++b) {
+    const double dmax = 2.0 * c->hbp_d[b].reach_max;
+    set_skin(c->hbp_d[b], c->skin_frac * dmax);
+    set_skin(c->hbp_f[b], c->skin_frac * dmax);
+  }
+  drop_graphs(c);
+  if (cudaMemcpyAsync(c->dbp_d, c->hbp_d.data(), sizeof(BedP<double>) * c->nbeds, cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
+      cudaMemcpyAsync(c->dbp_f, c->hbp_f.data(), sizeof(BedP<float>) * c->nbeds, cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
+      cudaMemsetAsync(c->rebuild, 1, sizeof(int), c->st) != cudaSuccess ||
+      cudaStreamSynchronize(c->st) != cudaSuccess)
+    return DEM_ECUDA;
+  return DEM_OK;
+}
 
 }  // namespace
 
@@ -442,6 +506,9 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
     B.cell_off = coff;
     coff += (long long)B.nx * B.ny * B.nz;
     B.corner_off = (int)c->hcorner.size();
+    B.inv_nx_f = 1.0f / (float)B.nx;
+    B.inv_nxy_f = 1.0f / (float)((long long)B.nx * B.ny);
+    B.fast_offsets = (B.nx >= 5 && B.ny >= 5 && (long long)B.nx * B.ny < (1 << 22)) ? 1 : 0;
     for (int q = 0; q < B.nx; ++q) c->hcorner.push_back(B.x0 + q * B.dx);
     for (int q = 0; q < B.ny; ++q) c->hcorner.push_back(B.y0 + q * B.dy);
     for (int q = 0; q < B.nz; ++q) c->hcorner.push_back(B.z0 + q * B.dz);
@@ -450,6 +517,8 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
     c->hbp_f.push_back(derive_params<float>(beds[b], B));
     c->hbp_d.back().reach_max = 0.5 * dmax[b];
     c->hbp_f.back().reach_max = (float)(0.5 * dmax[b]);
+    set_skin(c->hbp_d.back(), c->skin_frac * dmax[b]);
+    set_skin(c->hbp_f.back(), c->skin_frac * dmax[b]);
   }
   if (coff >= (1LL << 31)) { delete c; return DEM_EINVAL; }
   c->ncells = coff;
@@ -511,7 +580,15 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
   ck(cudaMemsetAsync(c->hcnt[0], 0, (size_t)n, c->st));
   ck(cudaMemsetAsync(c->hcnt[1], 0, (size_t)n, c->st));
   ck(cudaMemsetAsync(c->err, 0, sizeof(int), c->st));
-  ck(cudaMemsetAsync(c->step_ctr, 0, sizeof(long long), c->st));
+  ck(cudaMemsetAsync(c->step_ctr, 0, 4 * sizeof(long long), c->st));
+  // neighbour lists: none yet (the first step builds them); no displacement
+  ck(cudaMemsetAsync(c->rebuild, 1, sizeof(int), c->st));
+  for (int k = 0; k < 2; ++k) {
+    ck(cudaMemsetAsync(c->pbidx[k], 0, sizeof(int) * (size_t)n, c->st));
+    for (int q = 0; q < 3; ++q) ck(cudaMemsetAsync(c->pdsp[k][q], 0, sizeof(float) * (size_t)n, c->st));
+  }
+  ck(cudaMemsetAsync(c->nlc, 0, (size_t)n, c->st));
+  ck(cudaMemsetAsync(c->curpos, 0, sizeof(int) * (size_t)n, c->st));
   // gas: cell -> bed, marks, initial state
   {
     std::vector<int> cb(c->ncells);
@@ -768,12 +845,7 @@ int dem_set_diagnostics(dem_ctx *c, int32_t on) {
     CK(cudaMemset(c->diag, 0, sizeof(double) * DG_N * (size_t)c->cap));
   }
   if (c->diag_on != (on != 0)) {
-    // captured graphs bake the diagnostics pointer in: drop them
-    for (auto &kv : c->graphs) {
-      cudaGraphExecDestroy(kv.second.second);
-      cudaGraphDestroy(kv.second.first);
-    }
-    c->graphs.clear();
+    drop_graphs(c);   // captured graphs bake the diagnostics pointer in
   }
   c->diag_on = on != 0;
   return DEM_OK;
@@ -849,10 +921,126 @@ int dem_kernel_times(dem_ctx *c, int32_t max_kernels, char *names, int64_t *laun
   return k;
 }
 
+int dem_get_tuning(dem_ctx *c, int32_t *out) {
+  if (!c || !out) return DEM_EINVAL;
+  get_tuning(c, out);
+  return DEM_OK;
+}
+
+int dem_set_tuning(dem_ctx *c, const int32_t *in) {
+  if (!c || !in) return DEM_EINVAL;
+  int s = sync_all(c);
+  if (s != DEM_OK) return s;
+  return apply_tuning(c, in);
+}
+
+int dem_get_counters(dem_ctx *c, int64_t *out) {
+  if (!c || !out) return DEM_EINVAL;
+  int s = sync_all(c);
+  if (s != DEM_OK) return s;
+  long long v[3];
+  CK(cudaMemcpyAsync(v, c->step_ctr, sizeof v, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  for (int k = 0; k < 3; ++k) out[k] = v[k];
+  return DEM_OK;
+}
+
 int dem_autotune(dem_ctx *c, int32_t n_steps) {
-  (void)n_steps;
-  if (!c) return DEM_EINVAL;
-  return DEM_ESTATE;
+  if (!c || n_steps < 1) return DEM_EINVAL;
+  int s = sync_all(c);
+  if (s != DEM_OK) return s;
+  void *snap = nullptr;
+  if (cudaMalloc(&snap, c->arena_bytes) != cudaSuccess) return DEM_ENOMEM;
+  CK(cudaMemcpyAsync(snap, c->arena, c->arena_bytes, cudaMemcpyDeviceToDevice, c->st));
+  const int cur0 = c->cur, gcur0 = c->gcur;
+  unsigned *kres0 = c->kres, *vres0 = c->vres;
+  const bool prof0 = c->prof_on;
+  int32_t best[DEM_NTUNE];
+  get_tuning(c, best);
+  int rc = DEM_OK;
+  auto restore = [&]() {
+    cudaMemcpyAsync(c->arena, snap, c->arena_bytes, cudaMemcpyDeviceToDevice, c->st);
+    c->cur = cur0; c->gcur = gcur0; c->kres = kres0; c->vres = vres0;
+  };
+  // one candidate: per-kernel mean times (ms) and the total, or a negative total on error
+  auto trial = [&](const int32_t *t, std::map<std::string, double> &per) -> double {
+    restore();
+    if (apply_tuning(c, t) != DEM_OK) return -1.0;
+    c->prof_on = true;
+    c->prof_marks.clear(); c->prof_names.clear(); c->prof_ms.clear(); c->prof_n.clear();
+    if (enqueue_steps_any(c, n_steps) != 0) { c->prof_on = false; return -1.0; }
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) { c->prof_on = false; return -1.0; }
+    c->prof_on = false;
+    for (const auto &mk : c->prof_marks) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, c->ev_pool[mk.second], c->ev_pool[mk.second + 1]);
+      c->prof_ms[mk.first] += ms;
+      c->prof_n[mk.first] += 1;
+    }
+    double tot = 0.0;
+    per.clear();
+    for (size_t k = 0; k < c->prof_names.size(); ++k) {
+      per[c->prof_names[k]] = c->prof_ms[k] / (double)std::max<long long>(1, c->prof_n[k]);
+      tot += c->prof_ms[k];
+    }
+    return tot;
+  };
+  // 1) block sizes, every per-thread kernel at once, each kernel keeping its fastest
+  const char *kname[6] = {"k_key", "k_gather", "k_pair_search", "k_pair_forces", "k_gas_particle", "k_cells"};
+  double bt[6];
+  for (int k = 0; k < 6; ++k) bt[k] = 1e300;
+  int32_t tb[DEM_NTUNE];
+  std::memcpy(tb, best, sizeof tb);
+  tb[0] = 0;
+  int lim[6];
+  if (DEM_DISPATCH(c, kernel_limits, lim) != 0) rc = DEM_ECUDA;
+  for (int bs : {64, 128, 256, 512}) {
+    if (rc != DEM_OK) break;
+    int32_t t[DEM_NTUNE];
+    std::memcpy(t, tb, sizeof t);
+    for (int k = 1; k <= 6; ++k) t[k] = std::min(bs, lim[k - 1] / 32 * 32);
+    std::map<std::string, double> per;
+    if (trial(t, per) < 0) { rc = DEM_ECUDA; break; }
+    for (int k = 0; k < 6; ++k) {
+      auto it = per.find(kname[k]);
+      if (it != per.end() && it->second < bt[k]) { bt[k] = it->second; best[1 + k] = t[1 + k]; }
+    }
+  }
+  // 2) skin of the neighbour lists (whole-step time: rebuilds against list length)
+  double best_tot = 1e300;
+  if (rc == DEM_OK) {
+    const int32_t skin0 = best[7];
+    for (int sk : {25, 50, 100, 200}) {
+      int32_t t[DEM_NTUNE];
+      std::memcpy(t, best, sizeof t);
+      t[0] = 0;
+      t[7] = sk;
+      std::map<std::string, double> per;
+      const double tot = trial(t, per);
+      if (tot < 0) { rc = DEM_ECUDA; break; }
+      if (tot < best_tot) { best_tot = tot; best[7] = sk; }
+    }
+    if (rc != DEM_OK) best[7] = skin0;
+  }
+  // 3) the warp-per-cell contact kernel against the best per-thread configuration
+  best[0] = 0;
+  if (rc == DEM_OK) {
+    int32_t t[DEM_NTUNE];
+    std::memcpy(t, best, sizeof t);
+    t[0] = 1;
+    std::map<std::string, double> per;
+    const double tot = trial(t, per);
+    if (tot < 0) rc = DEM_ECUDA;
+    else if (tot < best_tot) best[0] = 1;
+  }
+  restore();
+  if (rc == DEM_OK) rc = apply_tuning(c, best);
+  cudaStreamSynchronize(c->st);
+  cudaFree(snap);
+  c->prof_marks.clear(); c->prof_names.clear(); c->prof_ms.clear(); c->prof_n.clear();
+  c->prof_on = prof0;
+  if (rc != DEM_OK) c->sticky = rc;
+  return rc;
 }
 
 int dem_adjoint(dem_ctx *c, int32_t n_steps, int32_t ckpt_every, double *J, double *grad) {

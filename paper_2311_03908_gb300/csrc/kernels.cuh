@@ -13,9 +13,15 @@ template <class R> struct PState {
   double *m[4];  // FP64 masses, or (value, compensation) FP32 pairs in the split-Kahan form
   int *meta;     // bed << 8 | ore
   int *orig;     // parcel index (input order)
+  int *bidx;     // position of the parcel when the neighbour lists were last built
+  float *dsp[3]; // displacement since that build (FP32)
 };
 
 // Contact-history table: count per parcel, then KMAX slots of partner index and 3-vector.
+// Verlet neighbour lists: slots per parcel, and the count that marks an overflowed list
+constexpr int KNL = 32;
+constexpr int NL_OVERFLOW = 255;
+
 template <class R> struct Hist {
   unsigned char *cnt;
   int *id;     // [KMAX][cap]
@@ -35,6 +41,13 @@ template <class P> struct StepView {
   unsigned *cstart, *cend;      // parcel range of every gas cell (empty: 0, 0)
   float4 *xl;                   // FP32 position relative to the own cell's corner, radius
   float4 *xlk;                  // the same in pre-sort order (written by k_key)
+  int *plist;                   // [KLIST][cap] candidate partners found by k_pair_search
+  unsigned char *pcode;         // [KLIST][cap] their cell offset codes
+  unsigned char *pcnt;          // number of listed candidates per parcel
+  int *nl;                      // [KNL][cap] neighbour lists (build positions), by build position
+  unsigned char *nlc;           // list lengths by build position (NL_OVERFLOW: none)
+  int *cur;                     // current sorted position of each build position
+  int *rebuild;                 // device flag: rebuild the neighbour lists this step
   const double *corner;         // cell-corner coordinates (see DevBed::corner_off)
   const unsigned *kprev;        // keys of the state before the step (its order)
   R *mass;                      // parcel mass (new order)
@@ -48,6 +61,7 @@ template <class P> struct StepView {
   double *dep;                  // [ncells][SR_N] or null (written by k_sources)
   int *err;
   const long long *step_ctr;    // steps completed so far (device)
+  unsigned long long *list_acc; // list entries of the build in progress
 };
 
 __device__ __forceinline__ bool coupled_step(int ncouple, const long long *ctr) {
@@ -120,6 +134,15 @@ __global__ void k_key(StepView<P> V, int drift) {
       x = x + (double)disp[0]; y = y + (double)disp[1]; z = z + (double)disp[2];
     }
     V.A.x[i] = x; V.A.y[i] = y; V.A.z[i] = z;
+    // displacement since the neighbour lists were built; past half the skin they are rebuilt
+    float s2 = 0.f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float dq = V.A.dsp[q][i] + (float)disp[q];
+      V.A.dsp[q][i] = dq;
+      s2 += dq * dq;
+    }
+    if (s2 > (float)bp.half_skin2) atomicOr(V.rebuild, 1);
     if constexpr (!P::exact) {
       const float4 o = V.xl[i];
       const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
@@ -177,6 +200,11 @@ __global__ void k_gather(StepView<P> V, int drift) {
   }
   V.B.meta[i] = meta;
   V.B.orig[i] = V.A.orig[j];
+  const int bi = V.A.bidx[j];
+  V.B.bidx[i] = bi;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) V.B.dsp[q][i] = V.A.dsp[q][j];
+  if (!*V.rebuild) V.cur[bi] = i;
   V.mass[i] = msum;
   V.xl[i] = V.xlk[j];
   // occupied ranges
@@ -227,21 +255,190 @@ __device__ __forceinline__ void add_contact(const StepView<P> &V, int i, int cin
   }
 }
 
-// Phase A (search): for each of the 9 neighbour rows (dy, dz) the cells X-1..X+1 hold one
-// contiguous run of sorted parcels; rows and end cells that lie farther than r_i + r_max from
-// the parcel are skipped. Every candidate is tested on the FP32 cell-local coordinates and the
-// hits go to a per-thread list in shared memory (index + cell offset code).
-// Phase B (forces): the list is processed with the lanes of a warp together, so the few hits
-// of a parcel do not serialise the warp the way a force evaluation inside the search loop does.
-// Pairs are visited in the same order as a plain 27-cell loop (dz, dy, dx, then index).
+// ---------------------------------------------------------------------------------------
+// Contacts, one thread per parcel, in two kernels.
+// k_pair_search: for each of the 9 neighbour rows (dy, dz) the cells X-1..X+1 hold one
+// contiguous run of sorted parcels; rows and end cells farther than r_i + r_max from the
+// parcel are skipped. Every candidate is tested on the FP32 cell-local coordinates (the
+// exact form with a small margin) and the hits are written, in visiting order, to a
+// per-parcel list (sorted index + cell offset code). Few registers, so many warps hide the
+// load latency of the pair loop.
+// k_pair_forces: the contact law for the listed pairs (the FP64 form first re-tests each
+// pair on the FP64 positions with the oracle's expression, so its pair sets are bit-exact),
+// then the walls; pairs are visited in the order of a plain 27-cell loop (dz, dy, dx, index).
+// ---------------------------------------------------------------------------------------
+// cell offsets (dx, dy, dz) of the cell with key k2 relative to the cell with key k1
+__device__ __forceinline__ void key_offset(const DevBed &B, unsigned k1, unsigned k2, int &dx, int &dy, int &dz) {
+  if (B.fast_offsets) {
+    // k2 - k1 = dz nx ny + dy nx + dx with |dx|, |dy|, |dz| <= 2 and nx, ny >= 5, so rounding
+    // recovers each term with a margin of 0.05 in units of the divisor
+    const int dk = (int)(k2 - k1);
+    const int nxy = B.nx * B.ny;
+    dz = __float2int_rn((float)dk * B.inv_nxy_f);
+    const int r = dk - dz * nxy;
+    dy = __float2int_rn((float)r * B.inv_nx_f);
+    dx = r - dy * B.nx;
+  } else {
+    int x1, y1, z1, x2, y2, z2;
+    key_cell(B, k1, x1, y1, z1);
+    key_cell(B, k2, x2, y2, z2);
+    dx = x2 - x1; dy = y2 - y1; dz = z2 - z1;
+  }
+}
+
 template <class P>
-__global__ void k_contacts(StepView<P> V) {
-  using R = typename P::R;
-  extern __shared__ int s_list[];   // [KLIST][blockDim.x] indices, then [KLIST][blockDim.x] codes
+__global__ void k_pair_search(StepView<P> V) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V.n) return;
-  const int nt = blockDim.x, tid = threadIdx.x;
-  unsigned char *s_code = reinterpret_cast<unsigned char *>(s_list + KLIST * nt);
+  const int b = V.B.meta[i] >> 8;
+  const DevBed &B = V.beds[b];
+  const BedP<typename P::R> &bp = V.bp[b];
+  const size_t cap = (size_t)V.cap;
+  const bool rebuild = *V.rebuild != 0;
+  // between rebuilds the parcels with a list are k_pair_list's
+  if (!rebuild && V.nlc[V.B.bidx[i]] != NL_OVERFLOW) return;
+  int nh = 0, nn = 0;
+  if (!(bp.flags & DEM_NO_CONTACTS)) {
+    const float4 me = V.xl[i];
+    const unsigned key = V.keys[i];
+    const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
+    const float pm = P::exact ? (float)bp.pf_margin : 0.f;
+    {
+      // cell-list path (list rebuild, or a parcel whose list overflowed)
+      const float skin = rebuild ? (float)bp.skin : 0.f;
+      int X, Y, Z;
+      key_cell(B, key, X, Y, Z);
+      // no partner centre lies farther than r_i + r_max (+ skin); the margin is far above
+      // the ~1e-10 m resolution of the local coordinates
+      const float reach = (me.w + (float)bp.reach_max + skin) * 1.0001f + pm + 1e-9f;
+      const int xlo = (X > 0 && me.x < reach) ? -1 : 0, xhi = (X < B.nx - 1 && hx - me.x < reach) ? 1 : 0;
+      const int ylo = (Y > 0 && me.y < reach) ? -1 : 0, yhi = (Y < B.ny - 1 && hy - me.y < reach) ? 1 : 0;
+      const int zlo = (Z > 0 && me.z < reach) ? -1 : 0, zhi = (Z < B.nz - 1 && hz - me.z < reach) ? 1 : 0;
+      for (int dz = zlo; dz <= zhi; ++dz) {
+        const float gz = dz < 0 ? me.z : (dz > 0 ? hz - me.z : 0.0f);   // distance to the row
+        for (int dy = ylo; dy <= yhi; ++dy) {
+          const float gy = dy < 0 ? me.y : (dy > 0 ? hy - me.y : 0.0f);
+          if (gy * gy + gz * gz >= reach * reach) continue;
+          const unsigned krow = key + (unsigned)(dy * B.nx) + (unsigned)(dz * B.nx * B.ny);
+          const float oy = dy * hy - me.y, oz = dz * hz - me.z;
+          for (int dx = xlo; dx <= xhi; ++dx) {
+            const unsigned jb = __ldg(V.cstart + krow + dx), je = __ldg(V.cend + krow + dx);
+            const float ox = dx * hx - me.x;
+            const unsigned char code = (unsigned char)((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
+#define DEM_PAIR_TEST(o, jj)                                                          \
+  do {                                                                                \
+    const float ex = (o).x + ox, ey = (o).y + oy, ez = (o).z + oz; /* x_j - x_i */   \
+    const float d2 = ex * ex + ey * ey + ez * ez;                                     \
+    const float rs = me.w + (o).w;                                                    \
+    const float lim = rs + pm, liml = rs + skin;                                      \
+    if (rebuild && d2 < liml * liml && (int)(jj) != i) {                              \
+      if (nn < KNL) V.nl[nn * cap + i] = (int)(jj);                                   \
+      ++nn;                                                                           \
+    }                                                                                 \
+    if (d2 < lim * lim && (int)(jj) != i) {                                           \
+      if (nh < KLIST) {                                                               \
+        V.plist[nh * cap + i] = (int)(jj);                                            \
+        V.pcode[nh * cap + i] = code;                                                 \
+      }                                                                               \
+      ++nh;                                                                           \
+    }                                                                                 \
+  } while (0)
+            unsigned jj = jb;
+            for (; jj + 4 <= je; jj += 4) {
+              const float4 o0 = __ldg(V.xl + jj), o1 = __ldg(V.xl + jj + 1);
+              const float4 o2 = __ldg(V.xl + jj + 2), o3 = __ldg(V.xl + jj + 3);
+              DEM_PAIR_TEST(o0, jj);
+              DEM_PAIR_TEST(o1, jj + 1);
+              DEM_PAIR_TEST(o2, jj + 2);
+              DEM_PAIR_TEST(o3, jj + 3);
+            }
+            for (; jj < je; ++jj) {
+              const float4 o0 = __ldg(V.xl + jj);
+              DEM_PAIR_TEST(o0, jj);
+            }
+#undef DEM_PAIR_TEST
+          }
+        }
+      }
+    }
+  }
+  if (rebuild) {
+    // this step's positions become the build positions
+    V.nlc[i] = (unsigned char)(nn > KNL ? NL_OVERFLOW : nn);
+    const unsigned am = __activemask();   // one atomic per group of lanes running together
+    const unsigned tot = __reduce_add_sync(am, (unsigned)min(nn, KNL));
+    if ((threadIdx.x & 31) == __ffs(am) - 1) atomicAdd(V.list_acc, (unsigned long long)tot);
+    V.B.bidx[i] = i;
+    V.cur[i] = i;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) V.B.dsp[q][i] = 0.f;
+  }
+  if (nh > KLIST) { set_error(V.err, ERR_CAPACITY); nh = KLIST; }
+  V.pcnt[i] = (unsigned char)nh;
+}
+
+// Between rebuilds: test the partners listed at the last build. Four list entries are
+// resolved at a time (entry -> current position -> key and local position) so that several
+// of these dependent loads are in flight per thread.
+template <class P>
+__global__ void k_pair_list(StepView<P> V) {
+  if (*V.rebuild) return;   // k_pair_search rebuilds the lists this step
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V.n) return;
+  const int bi = V.B.bidx[i];
+  const int listed = V.nlc[bi];
+  if (listed == NL_OVERFLOW) return;   // k_pair_search handles it
+  const size_t cap = (size_t)V.cap;
+  int nh = 0;
+  if (listed > 0) {
+    const int b = V.B.meta[i] >> 8;
+    const DevBed &B = V.beds[b];
+    const BedP<typename P::R> &bp = V.bp[b];
+    const float4 me = V.xl[i];
+    const unsigned key = V.keys[i];
+    const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
+    const float pm = P::exact ? (float)bp.pf_margin : 0.f;
+    for (int k0 = 0; k0 < listed; k0 += 4) {
+      int j[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) j[u] = k0 + u < listed ? V.nl[(k0 + u) * cap + bi] : -1;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) j[u] = j[u] >= 0 ? V.cur[j[u]] : -1;
+      unsigned kj[4];
+      float4 o[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        kj[u] = j[u] >= 0 ? V.keys[j[u]] : key;
+        o[u] = j[u] >= 0 ? __ldg(V.xl + j[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (j[u] < 0) continue;
+        int dx, dy, dz;
+        key_offset(B, key, kj[u], dx, dy, dz);
+        if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) continue;   // cannot touch
+        const float ex = o[u].x + (dx * hx - me.x), ey = o[u].y + (dy * hy - me.y), ez = o[u].z + (dz * hz - me.z);
+        const float d2 = ex * ex + ey * ey + ez * ez;
+        const float lim = me.w + o[u].w + pm;
+        if (d2 < lim * lim) {
+          if (nh < KLIST) {
+            V.plist[nh * cap + i] = j[u];
+            V.pcode[nh * cap + i] = (unsigned char)((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
+          }
+          ++nh;
+        }
+      }
+    }
+  }
+  if (nh > KLIST) { set_error(V.err, ERR_CAPACITY); nh = KLIST; }
+  V.pcnt[i] = (unsigned char)nh;
+}
+
+template <class P>
+__global__ void k_pair_forces(StepView<P> V) {
+  using R = typename P::R;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V.n) return;
   const int meta = V.B.meta[i];
   const int b = meta >> 8;
   const DevBed &B = V.beds[b];
@@ -249,50 +446,20 @@ __global__ void k_contacts(StepView<P> V) {
   R Fi[3] = {0, 0, 0}, Ti[3] = {0, 0, 0};
   int cout = 0;
   const int cin = V.Hn.cnt[i];
-  if (!(bp.flags & DEM_NO_CONTACTS)) {
-    const float4 me = V.xl[i];
-    int X, Y, Z;
-    key_cell(B, V.keys[i], X, Y, Z);
-    const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
-    const float pm = (float)bp.pf_margin;
-    // reach: no partner centre lies farther than r_i + r_max (with a margin far above the
-    // ~1e-10 m resolution of the local coordinates)
-    const float reach = (me.w + (float)bp.reach_max) * 1.0001f + pm + 1e-9f;
-    const int xlo = (X > 0 && me.x < reach) ? -1 : 0, xhi = (X < B.nx - 1 && hx - me.x < reach) ? 1 : 0;
-    const int ylo = (Y > 0 && me.y < reach) ? -1 : 0, yhi = (Y < B.ny - 1 && hy - me.y < reach) ? 1 : 0;
-    const int zlo = (Z > 0 && me.z < reach) ? -1 : 0, zhi = (Z < B.nz - 1 && hz - me.z < reach) ? 1 : 0;
-    int nh = 0;
-    for (int dz = zlo; dz <= zhi; ++dz) {
-      const float gz = dz < 0 ? me.z : (dz > 0 ? hz - me.z : 0.0f);   // distance to the row
-      for (int dy = ylo; dy <= yhi; ++dy) {
-        const float gy = dy < 0 ? me.y : (dy > 0 ? hy - me.y : 0.0f);
-        if (gy * gy + gz * gz >= reach * reach) continue;
-        const unsigned krow = (unsigned)(B.cell_off + ((long long)(Z + dz) * B.ny + (Y + dy)) * B.nx + X);
-        const float oy = dy * hy - me.y, oz = dz * hz - me.z;
-        for (int dx = xlo; dx <= xhi; ++dx) {
-          const unsigned k2 = krow + dx;
-          const unsigned jb = __ldg(V.cstart + k2), je = __ldg(V.cend + k2);
-          const float ox = dx * hx - me.x;
-          const unsigned char code = (unsigned char)((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
-          for (unsigned jj = jb; jj < je; ++jj) {
-            const float4 o = __ldg(V.xl + jj);
-            const float ex = o.x + ox, ey = o.y + oy, ez = o.z + oz;   // x_j - x_i
-            const float d2f = ex * ex + ey * ey + ez * ez;
-            const float rsf = me.w + o.w;
-            const float lim = P::exact ? rsf + pm : rsf;
-            if (d2f < lim * lim && (int)jj != i) {
-              if (nh < KLIST) {
-                s_list[nh * nt + tid] = (int)jj;
-                s_code[nh * nt + tid] = code;
-              }
-              ++nh;
-            }
-          }
-        }
-      }
-    }
-    if (nh > KLIST) { set_error(V.err, ERR_CAPACITY); nh = KLIST; }
-    // phase B
+  const float4 me = V.xl[i];
+  const int nh = V.pcnt[i];
+  // walls: FP32 pre-screen on the absolute position rebuilt from the cell corner
+  int X, Y, Z;
+  key_cell(B, V.keys[i], X, Y, Z);
+  const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
+  const float xa = (float)bp.x0 + X * hx + me.x, ya = (float)bp.y0 + Y * hy + me.y, za = (float)bp.z0 + Z * hz + me.z;
+  float distf[4], nwf[4][3];
+  wall_primitives<float>(bp, xa, ya, za, distf, nwf);
+  bool near = false;
+#pragma unroll
+  for (int p = 0; p < 4; ++p) near |= distf[p] < me.w + 1e-6f;
+  // the parcel's own state is read only when it has a partner or a wall within reach
+  if (!(bp.flags & DEM_NO_CONTACTS) && (nh > 0 || near)) {
     const R di = V.B.d[i];
     const R mi = V.mass[i];
     const R vi[3] = {V.B.v[0][i], V.B.v[1][i], V.B.v[2][i]};
@@ -303,9 +470,9 @@ __global__ void k_contacts(StepView<P> V) {
       ri_d = __dmul_rn(0.5, __dmul_rn(B.k, (double)di));
     }
     const R ri = P::exact ? (R)ri_d : (R)me.w;
+    const size_t cap = (size_t)V.cap;
     for (int h = 0; h < nh; ++h) {
-      const int j = s_list[h * nt + tid];
-      const int code = s_code[h * nt + tid];
+      const int j = V.plist[h * cap + i];
       R nrm[3], delta;
       double rj_d = 0;
       if constexpr (P::exact) {
@@ -318,6 +485,7 @@ __global__ void k_contacts(StepView<P> V) {
         nrm[0] = (R)(dxd / dd); nrm[1] = (R)(dyd / dd); nrm[2] = (R)(dzd / dd);
         delta = (R)(rs - dd);
       } else {
+        const int code = V.pcode[h * cap + i];
         const int cdx = code % 3 - 1, cdy = (code / 3) % 3 - 1, cdz = code / 9 - 1;
         const float4 o = __ldg(V.xl + j);
         const float ex = o.x + (cdx * hx - me.x), ey = o.y + (cdy * hy - me.y), ez = o.z + (cdz * hz - me.z);
@@ -338,13 +506,6 @@ __global__ void k_contacts(StepView<P> V) {
       vrel[2] = (vi[2] - V.B.v[2][j]) + (ws[0] * nrm[1] - ws[1] * nrm[0]);
       add_contact<P>(V, i, cin, V.B.orig[j], bp, mstar, ri, nrm, delta, vrel, wi, Fi, Ti, cout);
     }
-    // walls: FP32 pre-screen on the absolute position rebuilt from the cell corner
-    const float xa = (float)bp.x0 + X * hx + me.x, ya = (float)bp.y0 + Y * hy + me.y, za = (float)bp.z0 + Z * hz + me.z;
-    float distf[4], nwf[4][3];
-    wall_primitives<float>(bp, xa, ya, za, distf, nwf);
-    bool near = false;
-#pragma unroll
-    for (int p = 0; p < 4; ++p) near |= distf[p] < me.w + 1e-6f;
     if (near) {
       const double xd = V.B.x[i], yd = V.B.y[i], zd = V.B.z[i];
       const double rid = __dmul_rn(0.5, __dmul_rn(B.k, (double)di));
@@ -370,8 +531,328 @@ __global__ void k_contacts(StepView<P> V) {
   if (V.diag) V.diag[(size_t)DG_NCONTACT * V.cap + i] = (double)cout;
 }
 
-// dynamic shared memory of k_contacts for a block of nt threads
-inline size_t contacts_smem(int nt) { return (size_t)KLIST * nt * (sizeof(int) + 1); }
+
+// ---------------------------------------------------------------------------------------
+// Contacts, one warp per occupied cell. Warp w takes the cells whose first parcel lies in
+// sorted positions [32w, 32w+32). For a cell (up to 32 own parcels at a time):
+//  * the 27 neighbouring cells form 9 contiguous runs of sorted parcels (rows dz, dy);
+//    lanes read 32 candidates at a time, keep those within reach of the own cell's box
+//    (r_j + the largest own radius) and compact them in order with a ballot;
+//  * each round tests 32 compacted candidates against one own parcel, one per lane, and
+//    appends the hits of that parcel in candidate order;
+//  * hits are then evaluated flattened over the lanes (32 pairs at a time) and each own
+//    parcel's lane accumulates its own results in order, so force sums and history slots
+//    come out in the same order as a sequential 27-cell loop (dz, dy, dx, then index).
+// ---------------------------------------------------------------------------------------
+constexpr int CW_WARPS = 4;   // warps per block of k_contacts_cell
+
+template <class R> struct CellWarpSmem {
+  int list[32][KLIST];          // hits per own parcel: sorted index of the partner
+  unsigned char code[32][KLIST];
+  float4 own[32];               // own parcels: cell-local position, radius
+  float4 cbuf[64];              // compacted candidates, relative to the own cell's corner
+  int cj[64];
+  unsigned char cc[64];
+  int nh[32];                   // hits per own parcel (may exceed KLIST: capacity error)
+  int rb[9], pre[10];           // row starts and exclusive prefix of row lengths
+  unsigned kc[9];               // key of the row's centre cell
+  int hex[33];                  // exclusive prefix of the (capped) hit counts
+  R res[10][32];                // evaluated pairs: F, T, xi, accepted
+  int rid[32];
+};
+
+template <class P>
+__global__ void __launch_bounds__(CW_WARPS * 32) k_contacts_cell(StepView<P> V) {
+  using R = typename P::R;
+  __shared__ CellWarpSmem<R> sm_all[CW_WARPS];
+  CellWarpSmem<R> &S = sm_all[threadIdx.x >> 5];
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int i0 = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
+  if (i0 >= V.n) return;   // whole warp
+  const int iv = i0 + lane;
+  const bool valid = iv < V.n;
+  const unsigned key_i = valid ? V.keys[iv] : 0u;
+  const bool head = valid && (iv == 0 || V.keys[iv - 1] != key_i);
+  unsigned hm = __ballot_sync(FULL, head);
+  while (hm) {
+    const int h = __ffs(hm) - 1;
+    hm &= hm - 1;
+    const int s = i0 + h;
+    const unsigned key = __shfl_sync(FULL, key_i, h);
+    const int e = (int)V.cend[key];
+    const int b = V.B.meta[s] >> 8;
+    const DevBed &B = V.beds[b];
+    const BedP<R> &bp = V.bp[b];
+    const bool no_contacts = (bp.flags & DEM_NO_CONTACTS) != 0;
+    int X, Y, Z;
+    key_cell(B, key, X, Y, Z);
+    const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
+    const float pm = (float)bp.pf_margin;
+    for (int g0 = s; g0 < e; g0 += 32) {
+      const int nq = min(32, e - g0);
+      // own parcels
+      float ow_r = 0.f;
+      if (lane < nq) {
+        const float4 o = V.xl[g0 + lane];
+        S.own[lane] = o;
+        ow_r = o.w;
+      }
+      S.nh[lane] = 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ow_r = fmaxf(ow_r, __shfl_xor_sync(FULL, ow_r, o));
+      // rows of the 27-cell block
+      int len = 0;
+      if (lane < 9 && !no_contacts) {
+        const int dz = lane / 3 - 1, dy = lane % 3 - 1;
+        const int Y2 = Y + dy, Z2 = Z + dz;
+        unsigned jb = 0xffffffffu, je = 0;
+        if (Y2 >= 0 && Y2 < B.ny && Z2 >= 0 && Z2 < B.nz) {
+          const unsigned kcen = key + (unsigned)(dy * B.nx) + (unsigned)(dz * B.nx * B.ny);
+          S.kc[lane] = kcen;
+          for (int dx = -1; dx <= 1; ++dx) {
+            if (X + dx < 0 || X + dx >= B.nx) continue;
+            const unsigned a = V.cstart[kcen + dx], z = V.cend[kcen + dx];
+            if (z > a) { jb = min(jb, a); je = max(je, z); }
+          }
+        }
+        if (je > 0) { S.rb[lane] = (int)jb; len = (int)(je - jb); }
+      }
+      int incl = len;
+#pragma unroll
+      for (int o = 1; o < 16; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+      }
+      if (lane < 9) S.pre[lane] = incl - len;
+      const int C = __shfl_sync(FULL, incl, 8);
+      if (lane == 9) S.pre[9] = C;
+      __syncwarp();
+      const float reach_own = ow_r * 1.0001f + pm + 1e-9f;
+      int nb = 0;
+      for (int t0 = 0; t0 < C; t0 += 32) {
+        const int t = t0 + lane;
+        bool rel = false;
+        float4 cpos = make_float4(0.f, 0.f, 0.f, 0.f);
+        int j = 0;
+        unsigned char code = 0;
+        if (t < C) {
+          int r = 0;
+#pragma unroll
+          for (int q = 1; q < 9; ++q) r += (t >= S.pre[q]) ? 1 : 0;
+          j = S.rb[r] + (t - S.pre[r]);
+          const float4 o = __ldg(V.xl + j);
+          const int dz = r / 3 - 1, dy = r % 3 - 1;
+          const int dx = (int)(V.keys[j] - S.kc[r]);
+          cpos = make_float4(o.x + dx * hx, o.y + dy * hy, o.z + dz * hz, o.w);
+          code = (unsigned char)((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
+          // distance from the candidate to the own cell's box
+          const float gx = fmaxf(fmaxf(-cpos.x, cpos.x - hx), 0.f);
+          const float gy = fmaxf(fmaxf(-cpos.y, cpos.y - hy), 0.f);
+          const float gz = fmaxf(fmaxf(-cpos.z, cpos.z - hz), 0.f);
+          const float rr = o.w * 1.0001f + reach_own;
+          rel = gx * gx + gy * gy + gz * gz < rr * rr;
+        }
+        const unsigned m = __ballot_sync(FULL, rel);
+        if (rel) {
+          const int p = nb + __popc(m & lt);
+          S.cbuf[p] = cpos;
+          S.cj[p] = j;
+          S.cc[p] = code;
+        }
+        nb += __popc(m);
+        __syncwarp();
+        const bool last = t0 + 32 >= C;
+        while (nb >= 32 || (last && nb > 0)) {
+          const int mcnt = min(nb, 32);
+          const bool has = lane < mcnt;
+          const float4 c = S.cbuf[lane];
+          const int cjl = S.cj[lane];
+          const unsigned char ccl = S.cc[lane];
+          for (int q = 0; q < nq; ++q) {
+            const float4 ow = S.own[q];
+            const float ex = c.x - ow.x, ey = c.y - ow.y, ez = c.z - ow.z;
+            const float d2 = ex * ex + ey * ey + ez * ez;
+            const float rs = c.w + ow.w;
+            const float lim = P::exact ? rs + pm : rs;
+            const bool hit = has && d2 < lim * lim && cjl != g0 + q;
+            const unsigned hb = __ballot_sync(FULL, hit);
+            if (hb) {
+              const int base = S.nh[q];
+              if (hit) {
+                const int p = base + __popc(hb & lt);
+                if (p < KLIST) { S.list[q][p] = cjl; S.code[q][p] = ccl; }
+              }
+              __syncwarp();
+              if (lane == 0) S.nh[q] = base + __popc(hb);
+              __syncwarp();
+            }
+          }
+          // move the rest of the buffer to its front
+          __syncwarp();
+          if (nb > 32 && lane < nb - 32) {
+            const float4 c2 = S.cbuf[32 + lane];
+            const int j2 = S.cj[32 + lane];
+            const unsigned char k2 = S.cc[32 + lane];
+            // source [32, nb) and target [0, nb - 32) do not overlap
+            S.cbuf[lane] = c2; S.cj[lane] = j2; S.cc[lane] = k2;
+          }
+          nb -= mcnt;
+          __syncwarp();
+        }
+      }
+      // ---- phase B: evaluate the hits, flattened over the lanes ----
+      int nhq = lane < nq ? S.nh[lane] : 0;
+      if (nhq > KLIST) { set_error(V.err, ERR_CAPACITY); nhq = KLIST; }
+      int hin = nhq;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, hin, o);
+        if (lane >= o) hin += t;
+      }
+      S.hex[lane] = hin - nhq;
+      const int Htot = __shfl_sync(FULL, hin, 31);
+      if (lane == 0) S.hex[32] = Htot;
+      __syncwarp();
+      // own parcel of this lane (consumer)
+      const int p = g0 + lane;
+      R Fi[3] = {0, 0, 0}, Ti[3] = {0, 0, 0};
+      int cout = 0;
+      for (int e0 = 0; e0 < Htot; e0 += 32) {
+        const int ee = e0 + lane;
+        if (ee < Htot) {
+          int q = 0;
+          while (S.hex[q + 1] <= ee) ++q;
+          const int k = ee - S.hex[q];
+          const int j = S.list[q][k];
+          const int code = S.code[q][k];
+          const int ip = g0 + q;   // own parcel of the pair
+          const R di = V.B.d[ip];
+          const R mi = V.mass[ip];
+          const R vi[3] = {V.B.v[0][ip], V.B.v[1][ip], V.B.v[2][ip]};
+          const R wi[3] = {V.B.w[0][ip], V.B.w[1][ip], V.B.w[2][ip]};
+          const float4 me = S.own[q];
+          R nrm[3], delta;
+          bool ok = true;
+          R ri, rj;
+          if constexpr (P::exact) {
+            const double xi_d = V.B.x[ip], yi_d = V.B.y[ip], zi_d = V.B.z[ip];
+            const double ri_d = __dmul_rn(0.5, __dmul_rn(B.k, (double)di));
+            const double dxd = V.B.x[j] - xi_d, dyd = V.B.y[j] - yi_d, dzd = V.B.z[j] - zi_d;
+            const double rj_d = __dmul_rn(0.5, __dmul_rn(B.k, (double)V.B.d[j]));
+            const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dxd, dxd), __dmul_rn(dyd, dyd)), __dmul_rn(dzd, dzd));
+            const double rs = __dadd_rn(ri_d, rj_d);
+            ok = d2 < __dmul_rn(rs, rs);
+            const double dd = sqrt(d2);
+            nrm[0] = (R)(dxd / dd); nrm[1] = (R)(dyd / dd); nrm[2] = (R)(dzd / dd);
+            delta = (R)(rs - dd);
+            ri = (R)ri_d; rj = (R)rj_d;
+          } else {
+            const int cdx = code % 3 - 1, cdy = (code / 3) % 3 - 1, cdz = code / 9 - 1;
+            const float4 o = __ldg(V.xl + j);
+            const float ex = o.x + (cdx * hx - me.x), ey = o.y + (cdy * hy - me.y), ez = o.z + (cdz * hz - me.z);
+            const float d2f = ex * ex + ey * ey + ez * ez;
+            const float rsf = me.w + o.w;
+            const float df = sqrtf(d2f);
+            const float inv = 1.0f / df;
+            nrm[0] = (R)(ex * inv); nrm[1] = (R)(ey * inv); nrm[2] = (R)(ez * inv);
+            delta = (R)((rsf * rsf - d2f) / (rsf + df));
+            ri = (R)me.w; rj = (R)o.w;
+          }
+          const int pid = V.B.orig[j];
+          R Fc[3] = {0, 0, 0}, Tc[3] = {0, 0, 0}, xn[3] = {0, 0, 0};
+          if (ok) {
+            const R mj = V.mass[j];
+            const R mstar = mi * mj / (mi + mj);
+            const R ws[3] = {ri * wi[0] + rj * V.B.w[0][j], ri * wi[1] + rj * V.B.w[1][j], ri * wi[2] + rj * V.B.w[2][j]};
+            R vrel[3];
+            vrel[0] = (vi[0] - V.B.v[0][j]) + (ws[1] * nrm[2] - ws[2] * nrm[1]);
+            vrel[1] = (vi[1] - V.B.v[1][j]) + (ws[2] * nrm[0] - ws[0] * nrm[2]);
+            vrel[2] = (vi[2] - V.B.v[2][j]) + (ws[0] * nrm[1] - ws[1] * nrm[0]);
+            R xo[3] = {0, 0, 0};
+            const int cin = V.Hn.cnt[ip];
+            for (int sl = 0; sl < cin; ++sl)
+              if (V.Hn.id[(size_t)sl * V.cap + ip] == pid) {
+#pragma unroll
+                for (int qq = 0; qq < 3; ++qq) xo[qq] = V.Hn.xi[(size_t)(sl * 3 + qq) * V.cap + ip];
+                break;
+              }
+            contact_force<R>(bp, mstar, ri, nrm, delta, vrel, xo, wi, Fc, Tc, xn);
+          }
+#pragma unroll
+          for (int qq = 0; qq < 3; ++qq) {
+            S.res[qq][lane] = Fc[qq];
+            S.res[3 + qq][lane] = Tc[qq];
+            S.res[6 + qq][lane] = xn[qq];
+          }
+          S.res[9][lane] = ok ? (R)1 : (R)0;
+          S.rid[lane] = pid;
+        }
+        __syncwarp();
+        if (lane < nq) {
+          const int a0 = max(S.hex[lane], e0), a1 = min(S.hex[lane + 1], e0 + 32);
+          for (int a = a0; a < a1; ++a) {
+            const int slot = a - e0;
+            if (S.res[9][slot] == (R)0) continue;
+#pragma unroll
+            for (int qq = 0; qq < 3; ++qq) { Fi[qq] += S.res[qq][slot]; Ti[qq] += S.res[3 + qq][slot]; }
+            if (cout < KMAX) {
+              V.H.id[(size_t)cout * V.cap + p] = S.rid[slot];
+#pragma unroll
+              for (int qq = 0; qq < 3; ++qq) V.H.xi[(size_t)(cout * 3 + qq) * V.cap + p] = S.res[6 + qq][slot];
+              ++cout;
+            } else {
+              set_error(V.err, ERR_CAPACITY);
+            }
+          }
+        }
+        __syncwarp();
+      }
+      // walls and outputs, one lane per own parcel
+      if (lane < nq) {
+        const int cin = V.Hn.cnt[p];
+        if (!no_contacts) {
+          const float4 me = S.own[lane];
+          const R di = V.B.d[p];
+          const R mi = V.mass[p];
+          const R vi[3] = {V.B.v[0][p], V.B.v[1][p], V.B.v[2][p]};
+          const R wi[3] = {V.B.w[0][p], V.B.w[1][p], V.B.w[2][p]};
+          const double rid = __dmul_rn(0.5, __dmul_rn(B.k, (double)di));
+          const R ri = P::exact ? (R)rid : (R)me.w;
+          const float xa = (float)bp.x0 + X * hx + me.x, ya = (float)bp.y0 + Y * hy + me.y, za = (float)bp.z0 + Z * hz + me.z;
+          float distf[4], nwf[4][3];
+          wall_primitives<float>(bp, xa, ya, za, distf, nwf);
+          bool near = false;
+#pragma unroll
+          for (int pp = 0; pp < 4; ++pp) near |= distf[pp] < me.w + 1e-6f;
+          if (near) {
+            const double xd = V.B.x[p], yd = V.B.y[p], zd = V.B.z[p];
+            double dist[4], nw[4][3];
+            wall_primitives<double>(B, xd, yd, zd, dist, nw);
+            for (int pp = 0; pp < 4; ++pp) {
+              const double gap = rid - dist[pp];
+              if (!(gap > 0.0)) continue;
+              const R nrm[3] = {(R)-nw[pp][0], (R)-nw[pp][1], (R)-nw[pp][2]};
+              const R delta = (R)gap;
+              const R wr[3] = {ri * wi[0], ri * wi[1], ri * wi[2]};
+              R vrel[3];
+              vrel[0] = vi[0] + (wr[1] * nrm[2] - wr[2] * nrm[1]);
+              vrel[1] = vi[1] + (wr[2] * nrm[0] - wr[0] * nrm[2]);
+              vrel[2] = vi[2] + (wr[0] * nrm[1] - wr[1] * nrm[0]);
+              add_contact<P>(V, p, cin, -1 - pp, bp, mi, ri, nrm, delta, vrel, wi, Fi, Ti, cout);
+            }
+          }
+        }
+        V.H.cnt[p] = (unsigned char)cout;
+#pragma unroll
+        for (int qq = 0; qq < 3; ++qq) { V.F[qq][p] = Fi[qq]; V.Tq[qq][p] = Ti[qq]; }
+        if (V.diag) V.diag[(size_t)DG_NCONTACT * V.cap + p] = (double)cout;
+      }
+      __syncwarp();
+    }
+  }
+}
 
 // ---------------------------------------------------------------------------------------
 // Gas-particle terms, kinetics, second half kick, temperature and mass update; writes the
@@ -401,14 +882,14 @@ __global__ void k_gas_particle(StepView<P> V) {
   const R vh[3] = {V.B.v[0][i], V.B.v[1][i], V.B.v[2][i]};
   const R sv[3] = {-vh[0], -vh[1], g.uz - vh[2]};
   const R slip = sqrt(sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]);
-  const R Re = g.rho * g.eps * d * slip / g.mu;
+  const R Re = fdiv<R>(g.rho * g.eps * d * slip, g.mu);
   const R re02 = pos_pow(Re, (R)0.2);
   const R re07 = re02 * sqrt(Re);
   const R bo = beta_over_epsp<R>(bp, ore, d, g, slip, Re);
   const R Kp = (fl & DEM_NO_DRAG) ? (R)0 : bo * Vp;
   const R Fd[3] = {Kp * sv[0], Kp * sv[1], Kp * sv[2]};
   const R Nu = gunn(g.eps, re02, re07, g.pr13);
-  const R hA = (fl & DEM_NO_HEAT) ? (R)0 : bp.k3 * Nu * g.lam / d * ((R)kPI * d * d);
+  const R hA = (fl & DEM_NO_HEAT) ? (R)0 : fdiv<R>(bp.k3 * Nu * g.lam, d) * ((R)kPI * d * d);
   const R Tp = V.B.T[i];
   const R Qconv = hA * (g.T - Tp);
   R m[4];
@@ -423,12 +904,12 @@ __global__ void k_gas_particle(StepView<P> V) {
   const R F[3] = {V.F[0][i], V.F[1][i], V.F[2][i]};
   const R Tq[3] = {V.Tq[0][i], V.Tq[1][i], V.Tq[2][i]};
   R a[3];
-  a[0] = (F[0] + Fd[0]) / mp;
-  a[1] = (F[1] + Fd[1]) / mp;
-  a[2] = (F[2] + Fd[2] - Vp * bp.dpdz) / mp + bp.grav;
+  a[0] = fdiv<R>(F[0] + Fd[0], mp);
+  a[1] = fdiv<R>(F[1] + Fd[1], mp);
+  a[2] = fdiv<R>(F[2] + Fd[2] - Vp * bp.dpdz, mp) + bp.grav;
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    const R al = Tq[q] / I;
+    const R al = fdiv<R>(Tq[q], I);
     V.B.v[q][i] = vh[q] + a[q] * bp.half_dt;
     V.B.w[q][i] = V.B.w[q][i] + al * bp.half_dt;
     V.B.a[q][i] = a[q];
@@ -436,10 +917,10 @@ __global__ void k_gas_particle(StepView<P> V) {
   }
   const Tab<R> &t = tab<R>();
   R cpp = 0;
-  const R inv_mp = (R)1 / mp;
+  const R inv_mp = frcp<R>(mp);
 #pragma unroll
   for (int q = 0; q < 4; ++q) cpp += m[q] * inv_mp * cp_over_R<R>(3 + q, Tp) * t.RMz[q];
-  const R Tn = Tp + bp.dt * (Qconv + kn.Qr + kn.Qrm) / (mp * cpp);
+  const R Tn = Tp + fdiv<R>(bp.dt * (Qconv + kn.Qr + kn.Qrm), mp * cpp);
   V.B.T[i] = Tn;
   if (cpl) {
 #pragma unroll
@@ -790,6 +1271,6 @@ __global__ void k_scatter_hist(StepView<P> V, int *cnt, int *partner, double *xi
 }
 
 __global__ void k_mark_cells(const DevBed *beds, const int *cell_bed, unsigned char *mark, long long ncells);
-__global__ void k_step_counter(long long *ctr);
+__global__ void k_step_counter(long long *ctr, int *rebuild, int lists);
 
 }  // namespace dem

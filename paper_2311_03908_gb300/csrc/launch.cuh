@@ -30,6 +30,8 @@ StepView<P> make_view(dem_ctx *c, bool for_step) {
     for (int q = 0; q < 4; ++q) Pp.m[q] = c->pm[k][q];
     Pp.meta = c->pmeta[k];
     Pp.orig = c->porig[k];
+    Pp.bidx = c->pbidx[k];
+    for (int q = 0; q < 3; ++q) Pp.dsp[q] = c->pdsp[k][q];
   };
   fill(V.A, a);
   fill(V.B, b);
@@ -40,6 +42,13 @@ StepView<P> make_view(dem_ctx *c, bool for_step) {
   V.cstart = c->cstart; V.cend = c->cend;
   V.xl = c->xl;
   V.xlk = c->xlk;
+  V.plist = c->plist;
+  V.pcode = c->pcode;
+  V.pcnt = c->pcnt;
+  V.nl = c->nl;
+  V.nlc = c->nlc;
+  V.cur = c->curpos;
+  V.rebuild = c->rebuild;
   V.corner = c->corner;
   V.kprev = c->kres ? c->kres : c->keys;
   V.mass = (R *)c->mass;
@@ -54,6 +63,7 @@ StepView<P> make_view(dem_ctx *c, bool for_step) {
   V.dep = c->dep;
   V.err = c->err;
   V.step_ctr = c->step_ctr;
+  V.list_acc = (unsigned long long *)(c->step_ctr + 3);
   return V;
 }
 
@@ -94,16 +104,30 @@ int enqueue_steps(dem_ctx *c, int nsteps) {
     int e = enqueue_binning<P>(c, 1);
     if (e) return e;
     StepView<P> V = make_view<P>(c, true);
-    int ps = prof_begin(c, "k_contacts");
-    k_contacts<P><<<grid_for(c->n, c->bs_contacts), c->bs_contacts, contacts_smem(c->bs_contacts), st>>>(V);
-    prof_end(c, ps);
+    int ps;
+    if (c->contact_mode == 1) {
+      ps = prof_begin(c, "k_contacts_cell");
+      k_contacts_cell<P><<<grid_for(c->n, CW_WARPS * 32), CW_WARPS * 32, 0, st>>>(V);
+      prof_end(c, ps);
+    } else {
+      ps = prof_begin(c, "k_pair_list");
+      k_pair_list<P><<<grid_for(c->n, c->bs_search), c->bs_search, 0, st>>>(V);
+      prof_end(c, ps);
+      ps = prof_begin(c, "k_pair_search");
+      k_pair_search<P><<<grid_for(c->n, c->bs_search), c->bs_search, 0, st>>>(V);
+      prof_end(c, ps);
+      ps = prof_begin(c, "k_pair_forces");
+      k_pair_forces<P><<<grid_for(c->n, c->bs_contacts), c->bs_contacts, 0, st>>>(V);
+      prof_end(c, ps);
+      c->launches += 2;
+    }
     ps = prof_begin(c, "k_gas_particle");
     k_gas_particle<P><<<grid_for(c->n, c->bs_gp), c->bs_gp, 0, st>>>(V);
     prof_end(c, ps);
     ps = prof_begin(c, "k_cells");
     k_cells<P><<<grid_for(c->ncells, c->bs_cells), c->bs_cells, 0, st>>>(V, 0);
     prof_end(c, ps);
-    k_step_counter<<<1, 1, 0, st>>>(c->step_ctr);
+    k_step_counter<<<1, 1, 0, st>>>(c->step_ctr, c->rebuild, c->contact_mode == 0);
     c->launches += 4;
     e = (int)cudaPeekAtLastError();
     if (e) return e;
@@ -174,7 +198,21 @@ int enqueue_props(dem_ctx *c) {
   return (int)cudaPeekAtLastError();
 }
 
+// largest block each tunable kernel can launch with (registers per thread decide it)
+template <class P>
+int kernel_limits(int *lim) {
+  const void *fn[6] = {(const void *)k_key<P>, (const void *)k_gather<P>, (const void *)k_pair_search<P>,
+                       (const void *)k_pair_forces<P>, (const void *)k_gas_particle<P>, (const void *)k_cells<P>};
+  for (int k = 0; k < 6; ++k) {
+    cudaFuncAttributes a;
+    if (cudaFuncGetAttributes(&a, fn[k]) != cudaSuccess) return -1;
+    lim[k] = a.maxThreadsPerBlock;
+  }
+  return 0;
+}
+
 #define DEM_INSTANTIATE(P)                                                             \
+  template int kernel_limits<P>(int *);                                                 \
   template StepView<P> make_view<P>(dem_ctx *, bool);                                   \
   template int enqueue_steps<P>(dem_ctx *, int);                                        \
   template int enqueue_init<P>(dem_ctx *);                                              \
