@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=100_000, help="parcels in the oracle's sample")
     ap.add_argument("--parcels", type=int, default=0, help="override the workload's parcel count "
                     "(smaller cases for profiler captures; same geometry and packing)")
+    ap.add_argument("--form-steps", type=int, default=0, help="steps of the three-form comparison "
+                    "(0: the workload's own step count)")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--autotune", type=int, default=30, help="steps per autotuner candidate before the "
                     "warm-up (0: keep the default launch configuration)")
     return ap.parse_args()
@@ -168,6 +171,29 @@ def cpu_baseline(bed, steps: int, sample: int):
     dt = time.perf_counter() - t0
     return {"value": n * steps / dt, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
             "sample": f"{n} of {bed.n} parcels of the same bed (random subset), {steps} step(s), FP64"}
+
+
+def adjoint_cost(binding, stream):
+    """Wall time of dem_adjoint with the gradient against its forward sweep alone."""
+    import torch
+    from paper_2311_03908_gb300 import synth
+    abed = synth.config_adjoint_64k()
+    steps, ck = int(abed.meta["steps"]), int(abed.meta["ckpt"])
+    cx = binding.Context(abed, precision="fp64", stream=stream.cuda_stream)
+    cx.dem_adjoint(ck, ck, want_grad=True)           # warm-up (buffers, code paths)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, _ = cx.dem_adjoint(steps, ck, want_grad=False)
+    torch.cuda.synchronize()
+    tf = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    J2, g = cx.dem_adjoint(steps, ck, want_grad=True)
+    torch.cuda.synchronize()
+    ta = time.perf_counter() - t0
+    cx.close()
+    return {"parcels": abed.n, "steps": steps, "ckpt_every": ck, "forward_ms": tf * 1e3,
+            "adjoint_ms": ta * 1e3, "adjoint_over_forward": ta / tf, "J": J, "J_adjoint_run": J2,
+            "grad": [float(v) for v in g]}
 
 
 def reference_arm(args):
@@ -298,24 +324,37 @@ def main():
                                 "steps_total": steps_done},
             "tuning": tuning}
 
-    # the all-FP64 form of the same workload (split vs FP64 comparison)
-    if not args.no_fp64_form and args.precision != "fp64":
-        ctx64 = binding.Context(bed, precision="fp64", stream=stream.cuda_stream)
-        k64 = max(3, args.steps // 10)
-        for _ in range(3):
-            ctx64.dem_step_graph(1)
-        ctx64.dem_sync()
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        for _ in range(k64):
-            ctx64.dem_step_graph(1)
-        a1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = a0.elapsed_time(a1)
-        line["fp64_form"] = {"value": n * k64 / (ms64 * 1e-3), "unit": UNIT, "steps": k64,
-                             "ms_per_step": ms64 / k64}
-        ctx64.close()
+    # the three forms on fresh copies of the workload, each run for the workload's own step
+    # count: device time per step and the bed-mean reduction degree against the FP64 form
+    if not args.no_fp64_form:
+        fsteps = args.form_steps or int(bed.meta.get("steps", 500))
+        forms = {}
+        for prec in ("fp64", "split", "split_kahan"):
+            cx = binding.Context(bed, precision=prec, stream=stream.cuda_stream)
+            if prec != "fp64":
+                cx.dem_set_tuning(**tuning)
+            cx.dem_step_graph(1)          # captures the graphs; untimed, but counted in fsteps
+            cx.dem_step_graph(1)
+            cx.dem_sync()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(fsteps - 2):
+                cx.dem_step_graph(1)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            msf = a0.elapsed_time(a1) / max(1, fsteps - 2)
+            fm, _ = cx.dem_reduction_degree()
+            forms[prec] = {"ms_per_step": msf, "value": n / (msf * 1e-3), "f_ov_mean": float(fm.mean())}
+            cx.close()
+        for prec in forms:
+            forms[prec]["f_ov_abs_diff_vs_fp64"] = abs(forms[prec]["f_ov_mean"] - forms["fp64"]["f_ov_mean"])
+        line["forms"] = {"steps": fsteps, "unit": UNIT, **forms}
+
+    # cost of the adjoint (drag-heat-reaction sub-step, checkpoints + recomputation + reverse
+    # sweep) against its forward sweep, on the 64,000-parcel adjoint workload
+    if rank == 0 and not args.no_adjoint:
+        line["adjoint"] = adjoint_cost(binding, stream)
 
     # end to end through the C ABI with host buffers: every step the gas field comes from
     # pinned host memory (the coupling input) and the bed-mean reduction degree goes back

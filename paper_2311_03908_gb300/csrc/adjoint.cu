@@ -9,9 +9,9 @@
 //
 // One thread per parcel runs the whole time loop (parcels do not interact in this map):
 // a forward sweep that stores a checkpoint every `ckpt` sub-steps, then, segment by segment
-// from the last, a recompute of the segment's states into a buffer and the reverse sweep
-// through them. Every reverse step recomputes that step's forward intermediates and
-// back-propagates the adjoint by hand. The network's derivative uses the loop-matrix form:
+// from the last, a recompute of the segment that keeps every sub-step's state and forward
+// intermediates in a device buffer, and the reverse sweep through them, back-propagating the
+// adjoint by hand (two forward evaluations per sub-step in all, plus the reverse). The network's derivative uses the loop-matrix form:
 // J = R^{-1}(x - x_eq) gives adj(R) = -(V adj(J)) J^T with V = R^{-1}.
 #include "launch.cuh"
 
@@ -40,6 +40,10 @@ struct Fwd {          // intermediates of one forward sub-step
   double xid[3], mdot[4], tot, Qx, C;
   bool clampm[4];
 };
+
+static_assert(sizeof(Fwd) % 8 == 0, "forward intermediates are stored as 8-byte words");
+constexpr int kFwdWords = (int)(sizeof(Fwd) / 8);
+constexpr int kSegWords = 8 + kFwdWords;   // per parcel and sub-step of a recomputed segment
 
 __device__ inline double cz_mass(int s, double T, double M) { return cp_over_R<double>(s, T) * kRgas / M; }
 
@@ -390,14 +394,22 @@ __global__ void __launch_bounds__(128) k_adjoint(StepView<Pp> V, const BedP<doub
       for (int sg = nseg - 1; sg >= 0; --sg) {
         const int st0 = sg * ckpt, st1 = min(st0 + ckpt, nsteps);
         for (int q = 0; q < 8; ++q) s[q] = cks[((size_t)sg * 8 + q) * n + i];
+        // recompute the segment, keeping each sub-step's state and forward intermediates
         for (int k = st0; k < st1; ++k) {
-          for (int q = 0; q < 8; ++q) seg[((size_t)(k - st0) * 8 + q) * n + i] = s[q];
+          double *slot = seg + (size_t)(k - st0) * kSegWords * n + i;
+          for (int q = 0; q < 8; ++q) slot[(size_t)q * n] = s[q];
           fwd(P, s, th, F, sn);
+          const unsigned long long *fw = reinterpret_cast<const unsigned long long *>(&F);
+          unsigned long long *sw = reinterpret_cast<unsigned long long *>(slot + 8 * n);
+          for (int q = 0; q < kFwdWords; ++q) sw[(size_t)q * n] = fw[q];
           for (int q = 0; q < 8; ++q) s[q] = sn[q];
         }
         for (int k = st1 - 1; k >= st0; --k) {
-          for (int q = 0; q < 8; ++q) s[q] = seg[((size_t)(k - st0) * 8 + q) * n + i];
-          fwd(P, s, th, F, sn);
+          const double *slot = seg + (size_t)(k - st0) * kSegWords * n + i;
+          for (int q = 0; q < 8; ++q) s[q] = slot[(size_t)q * n];
+          unsigned long long *fw = reinterpret_cast<unsigned long long *>(&F);
+          const unsigned long long *sw = reinterpret_cast<const unsigned long long *>(slot + 8 * n);
+          for (int q = 0; q < kFwdWords; ++q) fw[q] = sw[(size_t)q * n];
           bwd(P, s, th, F, lam, lout, g);
           for (int q = 0; q < 8; ++q) lam[q] = lout[q];
         }
@@ -423,7 +435,7 @@ int run_adjoint(dem_ctx *c, int nsteps, int ckpt, double *J, double *grad) {
   const int n = c->n;
   const int nseg = (nsteps + ckpt - 1) / ckpt;
   const int bs = 128, grid = (n + bs - 1) / bs;
-  const size_t need = sizeof(double) * ((want_grad ? ((size_t)nseg * 8 * n + (size_t)ckpt * 8 * n) : 0) + (size_t)grid * 7);
+  const size_t need = sizeof(double) * ((want_grad ? ((size_t)nseg * 8 * n + (size_t)ckpt * kSegWords * n) : 0) + (size_t)grid * 7);
   if (c->adj_bytes < need) {
     if (c->adj) cudaFree(c->adj);
     c->adj = nullptr;
@@ -433,7 +445,7 @@ int run_adjoint(dem_ctx *c, int nsteps, int ckpt, double *J, double *grad) {
   }
   double *cks = c->adj;
   double *seg = cks + (want_grad ? (size_t)nseg * 8 * n : 0);
-  double *partial = seg + (want_grad ? (size_t)ckpt * 8 * n : 0);
+  double *partial = seg + (want_grad ? (size_t)ckpt * kSegWords * n : 0);
   StepView<Pp> V = make_view<Pp>(c, false);
   Params6 th;
   for (int r = 0; r < 3; ++r) { th.v[r] = c->cfg[0].k0[r]; th.v[3 + r] = c->cfg[0].Ea[r]; }

@@ -341,7 +341,7 @@ void layout(dem_ctx *c, Bump &m) {
   c->gp = m.take<char>(C * GP_N, R);
   c->mark = m.take<unsigned char>(C);
   c->cell_bed = m.take<int>(C);
-  c->fv = m.take<double>(N * 3);
+  c->fv = m.take<double>((size_t)c->nbeds * FOV_CHUNKS * 4);
   c->fvbed = m.take<double>((size_t)c->nbeds * 4);
   c->err = m.take<int>(1);
   c->step_ctr = m.take<long long>(4);

@@ -1171,45 +1171,46 @@ __global__ void k_volume(StepView<P> V) {
 // ---------------------------------------------------------------------------------------
 // Reduction degree (eqs (2-15)..(2-19)) per parcel and per bed (deterministic two-pass).
 // ---------------------------------------------------------------------------------------
-template <class P>
-__global__ void k_fov_parcel(StepView<P> V, double *per_parcel_orig, double *fv /* [3][n] */) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= V.n) return;
-  const int ore = V.A.meta[i] & 255;
-  const Tab<double> &td = tab<double>();
-  double n[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) n[q] = mass_d<P>(V.A.m[q], i) / td.Mz[q];
-  const double nfe = 2.0 * n[0] + 3.0 * n[1] + n[2] + n[3];
-  double f = 0.0;
-  if (nfe > 0.0) {
-    const double fh = (3.0 * n[1] + n[2] + n[3]) / nfe, fm = (n[2] + n[3]) / nfe, fw = n[3] / nfe;
-    f = ore == 0 ? fh / 9.0 + 2.0 * fm / 9.0 + 6.0 * fw / 9.0 : 0.25 * fm + 0.75 * fw;
-  }
-  if (per_parcel_orig) per_parcel_orig[V.A.orig[i]] = f;
-  fv[i] = f;
-  fv[(size_t)V.n + i] = 3.0 * n[0] + 4.0 * n[1] + n[2];
-  fv[2 * (size_t)V.n + i] = (ore == 0 ? 1.5 : 4.0 / 3.0) * nfe;
-}
+constexpr int FOV_CHUNKS = 64;   // blocks per bed of the reduction-degree sums
 
-// One block per bed: the bed's parcels are contiguous in the sorted order; sum them in a
-// fixed order (strided per thread, then a shared-memory tree) so the result is
-// reproducible bit for bit.
+// Each bed's parcels are contiguous in the sorted order; block (bed, chunk) sums a fixed
+// slice of them (strided per thread, then a shared-memory tree), and k_fov_beds adds the
+// slices in chunk order, so the result is reproducible bit for bit.
 template <class P>
-__global__ void k_fov_bed(StepView<P> V, const double *fv, double *out /* [nbeds][4] */) {
+__global__ void k_fov_chunks(StepView<P> V, double *per_parcel_orig, double *part /* [nbeds][FOV_CHUNKS][4] */) {
   __shared__ double sh[3][256];
-  const int b = blockIdx.x;
-  const unsigned klo = (unsigned)V.beds[b].cell_off;
-  const unsigned khi = (b + 1 < V.nbeds) ? (unsigned)V.beds[b + 1].cell_off : 0xffffffffu;
-  int lo = 0, hi = V.n;
-  while (lo < hi) { int mid = (lo + hi) >> 1; if (V.keys[mid] < klo) lo = mid + 1; else hi = mid; }
-  const int beg = lo;
-  hi = V.n;
-  while (lo < hi) { int mid = (lo + hi) >> 1; if (V.keys[mid] < khi) lo = mid + 1; else hi = mid; }
-  const int end = lo;
+  __shared__ int range[2];
+  const int b = blockIdx.x / FOV_CHUNKS, ch = blockIdx.x % FOV_CHUNKS;
+  if (threadIdx.x == 0) {
+    const unsigned klo = (unsigned)V.beds[b].cell_off;
+    const unsigned khi = (b + 1 < V.nbeds) ? (unsigned)V.beds[b + 1].cell_off : 0xffffffffu;
+    int lo = 0, hi = V.n;
+    while (lo < hi) { int mid = (lo + hi) >> 1; if (V.keys[mid] < klo) lo = mid + 1; else hi = mid; }
+    range[0] = lo;
+    hi = V.n;
+    while (lo < hi) { int mid = (lo + hi) >> 1; if (V.keys[mid] < khi) lo = mid + 1; else hi = mid; }
+    range[1] = lo;
+  }
+  __syncthreads();
+  const long long len = range[1] - range[0];
+  const int c0 = range[0] + (int)(len * ch / FOV_CHUNKS), c1 = range[0] + (int)(len * (ch + 1) / FOV_CHUNKS);
+  const Tab<double> &td = tab<double>();
   double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-  for (int i = beg + (int)threadIdx.x; i < end; i += blockDim.x) {
-    a0 += fv[i]; a1 += fv[(size_t)V.n + i]; a2 += fv[2 * (size_t)V.n + i];
+  for (int i = c0 + (int)threadIdx.x; i < c1; i += blockDim.x) {
+    const int ore = V.A.meta[i] & 255;
+    double n[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) n[q] = mass_d<P>(V.A.m[q], i) / td.Mz[q];
+    const double nfe = 2.0 * n[0] + 3.0 * n[1] + n[2] + n[3];
+    double f = 0.0;
+    if (nfe > 0.0) {
+      const double fh = (3.0 * n[1] + n[2] + n[3]) / nfe, fm = (n[2] + n[3]) / nfe, fw = n[3] / nfe;
+      f = ore == 0 ? fh / 9.0 + 2.0 * fm / 9.0 + 6.0 * fw / 9.0 : 0.25 * fm + 0.75 * fw;
+    }
+    if (per_parcel_orig) per_parcel_orig[V.A.orig[i]] = f;
+    a0 += f;
+    a1 += 3.0 * n[0] + 4.0 * n[1] + n[2];
+    a2 += (ore == 0 ? 1.5 : 4.0 / 3.0) * nfe;
   }
   sh[0][threadIdx.x] = a0; sh[1][threadIdx.x] = a1; sh[2][threadIdx.x] = a2;
   __syncthreads();
@@ -1219,9 +1220,18 @@ __global__ void k_fov_bed(StepView<P> V, const double *fv, double *out /* [nbeds
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    out[b * 4 + 0] = sh[0][0]; out[b * 4 + 1] = sh[1][0]; out[b * 4 + 2] = sh[2][0];
-    out[b * 4 + 3] = (double)(end - beg);
+    double *o = part + (size_t)blockIdx.x * 4;
+    o[0] = sh[0][0]; o[1] = sh[1][0]; o[2] = sh[2][0]; o[3] = (double)(c1 - c0);
   }
+}
+
+static __global__ void k_fov_beds(const double *part, int nbeds, double *out /* [nbeds][4] */) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbeds) return;
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int ch = 0; ch < FOV_CHUNKS; ++ch)
+    for (int q = 0; q < 4; ++q) s[q] += part[((size_t)b * FOV_CHUNKS + ch) * 4 + q];
+  for (int q = 0; q < 4; ++q) out[b * 4 + q] = s[q];
 }
 
 // ---------------------------------------------------------------------------------------

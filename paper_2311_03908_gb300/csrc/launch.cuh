@@ -153,8 +153,8 @@ int enqueue_init(dem_ctx *c) {
 template <class P>
 int enqueue_fov(dem_ctx *c, double *per_parcel_dev) {
   StepView<P> V = make_view<P>(c, false);
-  k_fov_parcel<P><<<grid_for(c->n, 256), 256, 0, c->st>>>(V, per_parcel_dev, c->fv);
-  k_fov_bed<P><<<c->nbeds, 256, 0, c->st>>>(V, c->fv, c->fvbed);
+  k_fov_chunks<P><<<c->nbeds * FOV_CHUNKS, 256, 0, c->st>>>(V, per_parcel_dev, c->fv);
+  k_fov_beds<<<(c->nbeds + 63) / 64, 64, 0, c->st>>>(c->fv, c->nbeds, c->fvbed);
   return (int)cudaPeekAtLastError();
 }
 
