@@ -23,6 +23,8 @@ constexpr double kPI = 3.14159265358979323846;
 constexpr double kRgas = 8.314;  // gas constant of Sec. 2.1
 constexpr double kGrav = 9.81;
 
+// kahan: layer masses and positions are compensated FP32 pairs (no FP64 arithmetic in the
+// step); exact: the FP64 form, whose pair tests follow the oracle bit for bit
 struct PrecF64 { using R = double; static constexpr bool kahan = false; static constexpr bool exact = true; };
 struct PrecSplit { using R = float; static constexpr bool kahan = false; static constexpr bool exact = false; };
 struct PrecKahan { using R = float; static constexpr bool kahan = true; static constexpr bool exact = false; };
@@ -56,6 +58,7 @@ struct DevBed {
   int nx, ny, nz;
   long long cell_off;           // first global gas cell (and sort key) of this bed
   int corner_off;               // first entry of this bed in the cell-corner table
+  int cornerp_off;              // the same in the FP32-pair table (nx+1, ny+1, nz+1 entries)
   float inv_nx_f, inv_nxy_f;    // 1/nx, 1/(nx ny): cell offsets from key differences
   int fast_offsets;             // nx, ny >= 5: offsets in [-2, 2] decode by rounding
   double R_bed, H, cos_a, sin_a, z_apex, plate_z, pitch, inv_pitch, r_hole;
@@ -516,6 +519,15 @@ template <class P> __device__ __forceinline__ typename P::R mass_r(const double 
     return (typename P::R)m[i];
   }
 }
+// the same from a mass word already loaded
+template <class P> __device__ __forceinline__ typename P::R mass_word_r(double w) {
+  if constexpr (P::kahan) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(w);
+    return __uint_as_float((unsigned)u) + __uint_as_float((unsigned)(u >> 32));
+  } else {
+    return (typename P::R)w;
+  }
+}
 template <class P> __device__ __forceinline__ double mass_d(const double *m, int i) {
   if constexpr (P::kahan) {
     const float2 v = reinterpret_cast<const float2 *>(m)[i];
@@ -570,6 +582,26 @@ __device__ __forceinline__ void gas_put(double *G, size_t k, double v, bool pair
   } else {
     const float hi = (float)v;
     reinterpret_cast<float2 *>(G)[k] = make_float2(hi, (float)(v - (double)hi));
+  }
+}
+// (hi, lo) + b with the rounding error of hi + b carried into lo (two-sum, Knuth), then
+// renormalised; the pair keeps ~48 significant bits
+__device__ __forceinline__ float2 pair_add_exact(float2 a, float b) {
+  const float s = a.x + b;
+  const float bb = s - a.x;
+  const float err = (a.x - (s - bb)) + (b - bb);
+  const float lo = a.y + err;
+  const float hi = s + lo;
+  return make_float2(hi, lo - (hi - s));
+}
+// position word of parcel i: FP64 value, or in the split-Kahan form a (hi, lo) pair of FP32
+// relative to the bed's corner (origin)
+template <class P> __device__ __forceinline__ double pos_abs(const double *x, int i, double origin) {
+  if constexpr (P::kahan) {
+    const float2 v = reinterpret_cast<const float2 *>(x)[i];
+    return origin + ((double)v.x + (double)v.y);
+  } else {
+    return x[i];
   }
 }
 // (hi, lo) + inc, compensated

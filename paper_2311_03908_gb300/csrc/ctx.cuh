@@ -47,6 +47,8 @@ struct dem_ctx {
   double skin_frac = 0.1;         // neighbour-list skin as a fraction of the largest diameter
   double *corner = nullptr;         // cell-corner coordinates: per bed x0+i dx, y0+j dy, z0+k dz
   std::vector<double> hcorner;
+  float2 *cornerp = nullptr;        // cell corners relative to the bed corner as FP32 pairs
+  std::vector<float2> hcornerp;
   void *mass = nullptr, *F[3] = {}, *Tq[3] = {}, *src = nullptr;
   // gas: two state buffers (gcur = current), properties, marks
   double *gas[2] = {};

@@ -45,14 +45,25 @@ __global__ void k_load(int n, const double *const *src /* 8 + 4 arrays */, const
   using R = typename P::R;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  x[i] = src[0][i]; y[i] = src[1][i]; z[i] = src[2][i];
+  const DevBed &B = beds[bed[i]];
+  if constexpr (P::kahan) {
+    // FP32 pairs relative to the bed corner
+    const double o[3] = {B.x0, B.y0, B.z0};
+    double *const pd[3] = {x, y, z};
+    for (int q = 0; q < 3; ++q) {
+      const double rel = src[q][i] - o[q];
+      const float hi = (float)rel;
+      reinterpret_cast<float2 *>(pd[q])[i] = make_float2(hi, (float)(rel - (double)hi));
+    }
+  } else {
+    x[i] = src[0][i]; y[i] = src[1][i]; z[i] = src[2][i];
+  }
   for (int q = 0; q < 3; ++q) {
     rv[q][i] = (R)src[3 + q][i];
     rv[3 + q][i] = (R)0;
     rv[6 + q][i] = (R)0;
     rv[9 + q][i] = (R)0;
   }
-  const DevBed &B = beds[bed[i]];
   rv[8][i] = (B.flags & DEM_NO_GRAVITY) ? (R)0 : (R)(-kGrav);
   rv[12][i] = (R)src[7][i];
   rv[13][i] = (R)src[6][i];
@@ -333,6 +344,7 @@ void layout(dem_ctx *c, Bump &m) {
   c->curpos = m.take<int>(N);
   c->rebuild = m.take<int>(1);
   c->corner = m.take<double>(c->hcorner.size());
+  c->cornerp = m.take<float2>(c->hcornerp.size());
   c->mass = m.take<char>(N, R);
   for (int q = 0; q < 3; ++q) { c->F[q] = m.take<char>(N, R); c->Tq[q] = m.take<char>(N, R); }
   c->src = m.take<char>(N * SR_N, R);
@@ -505,6 +517,17 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
     if (nb[b] > 0 && std::sqrt(beds[b].kn / (0.5 * mmin[b])) * beds[b].dt >= 2.0) { delete c; return DEM_EINVAL; }
     B.cell_off = coff;
     coff += (long long)B.nx * B.ny * B.nz;
+    B.cornerp_off = (int)c->hcornerp.size();
+    {
+      const int nn[3] = {B.nx, B.ny, B.nz};
+      const double hh[3] = {B.dx, B.dy, B.dz};
+      for (int a = 0; a < 3; ++a)
+        for (int q = 0; q <= nn[a]; ++q) {
+          const double cv = q * hh[a];
+          const float hi = (float)cv;
+          c->hcornerp.push_back(make_float2(hi, (float)(cv - (double)hi)));
+        }
+    }
     B.corner_off = (int)c->hcorner.size();
     B.inv_nx_f = 1.0f / (float)B.nx;
     B.inv_nxy_f = 1.0f / (float)((long long)B.nx * B.ny);
@@ -541,6 +564,7 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
   ck(cudaMemcpyAsync(c->dbp_d, c->hbp_d.data(), sizeof(BedP<double>) * n_beds, cudaMemcpyHostToDevice, c->st));
   ck(cudaMemcpyAsync(c->dbp_f, c->hbp_f.data(), sizeof(BedP<float>) * n_beds, cudaMemcpyHostToDevice, c->st));
   ck(cudaMemcpyAsync(c->corner, c->hcorner.data(), sizeof(double) * c->hcorner.size(), cudaMemcpyHostToDevice, c->st));
+  ck(cudaMemcpyAsync(c->cornerp, c->hcornerp.data(), sizeof(float2) * c->hcornerp.size(), cudaMemcpyHostToDevice, c->st));
   // staging copies of the inputs (freed at the end of init)
   double *dsrc = nullptr;
   int *dint = nullptr;

@@ -49,6 +49,7 @@ template <class P> struct StepView {
   int *cur;                     // current sorted position of each build position
   int *rebuild;                 // device flag: rebuild the neighbour lists this step
   const double *corner;         // cell-corner coordinates (see DevBed::corner_off)
+  const float2 *cornerp;        // cell corners relative to the bed corner, FP32 pairs
   const unsigned *kprev;        // keys of the state before the step (its order)
   R *mass;                      // parcel mass (new order)
   R *F[3], *Tq[3];              // contact force and torque
@@ -109,6 +110,24 @@ __device__ __forceinline__ void key_cell(const DevBed &B, unsigned key, int &ix,
 // parcel stays more than 1e-3 of an edge inside it (the local coordinates then decide
 // it exactly, their error being ~1e-10 m); otherwise, and always in the FP64 form, the key
 // is the FP64 definition.
+// Cell of a position given as an FP32 pair p relative to the bed corner (split-Kahan form):
+// the q with corner[q] <= p < corner[q+1], corners being FP32 pairs too; the differences
+// hi - c_hi are exact (Sterbenz), so the test and the local coordinate agree.
+__device__ __forceinline__ float pair_minus(float2 p, float2 c) { return (p.x - c.x) + (p.y - c.y); }
+__device__ __forceinline__ int pair_cell(float2 p, const float2 *c, float inv_h, int n, bool &out) {
+  int q = (int)floorf(p.x * inv_h);
+  q = min(max(q, 0), n - 1);
+  if (pair_minus(p, c[q]) < 0.f && q > 0) --q;
+  else if (pair_minus(p, c[q + 1]) >= 0.f && q < n - 1) ++q;
+  if (pair_minus(p, c[q]) < 0.f || pair_minus(p, c[q + 1]) >= 0.f) out = true;
+  return q;
+}
+
+// Half kick + drift (written back to the positions), the sort key, and the FP32 cell-local
+// coordinates. The FP32 forms take the key from the previous cell when the parcel stays more
+// than 1e-3 of an edge inside it (the local coordinates then decide it exactly, their error
+// being ~1e-10 m); otherwise, and always in the FP64 form, the key is recomputed from the
+// position: FP64 floor((x - x0) / dx), or in the split-Kahan form the pair comparison.
 template <class P>
 __global__ void k_key(StepView<P> V, int drift) {
   using R = typename P::R;
@@ -117,7 +136,14 @@ __global__ void k_key(StepView<P> V, int drift) {
   const int b = V.A.meta[i] >> 8;
   const DevBed &B = V.beds[b];
   const BedP<R> &bp = V.bp[b];
-  double x = V.A.x[i], y = V.A.y[i], z = V.A.z[i];
+  double x = 0, y = 0, z = 0;
+  float2 p2[3];
+  if constexpr (P::kahan) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) p2[q] = reinterpret_cast<const float2 *>(q == 0 ? V.A.x : q == 1 ? V.A.y : V.A.z)[i];
+  } else {
+    x = V.A.x[i]; y = V.A.y[i]; z = V.A.z[i];
+  }
   bool fast = false;
   unsigned key = 0;
   if (drift) {
@@ -128,12 +154,20 @@ __global__ void k_key(StepView<P> V, int drift) {
       if constexpr (sizeof(R) == 8) disp[q] = __dmul_rn(vh, B.dt);
       else disp[q] = vh * bp.dt;
     }
-    if constexpr (sizeof(R) == 8) {
-      x = __dadd_rn(x, disp[0]); y = __dadd_rn(y, disp[1]); z = __dadd_rn(z, disp[2]);
+    if constexpr (P::kahan) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        p2[q] = pair_add_exact(p2[q], (float)disp[q]);
+        reinterpret_cast<float2 *>(q == 0 ? V.A.x : q == 1 ? V.A.y : V.A.z)[i] = p2[q];
+      }
     } else {
-      x = x + (double)disp[0]; y = y + (double)disp[1]; z = z + (double)disp[2];
+      if constexpr (sizeof(R) == 8) {
+        x = __dadd_rn(x, disp[0]); y = __dadd_rn(y, disp[1]); z = __dadd_rn(z, disp[2]);
+      } else {
+        x = x + (double)disp[0]; y = y + (double)disp[1]; z = z + (double)disp[2];
+      }
+      V.A.x[i] = x; V.A.y[i] = y; V.A.z[i] = z;
     }
-    V.A.x[i] = x; V.A.y[i] = y; V.A.z[i] = z;
     // displacement since the neighbour lists were built; past half the skin they are rebuilt
     float s2 = 0.f;
 #pragma unroll
@@ -152,16 +186,32 @@ __global__ void k_key(StepView<P> V, int drift) {
       if (fast) key = V.kprev[i];
     }
   }
-  if (!fast) {
-    bool out;
-    key = point_key_d(B, x, y, z, out);
-    if (out) set_error(V.err, ERR_DOMAIN);
-  }
   int ix, iy, iz;
-  key_cell(B, key, ix, iy, iz);
   const float r = (float)(bp.k * V.A.d[i]) * 0.5f;
-  const double *cn = V.corner + B.corner_off;
-  V.xlk[i] = make_float4((float)(x - cn[ix]), (float)(y - cn[B.nx + iy]), (float)(z - cn[B.nx + B.ny + iz]), r);
+  if constexpr (P::kahan) {
+    const float2 *cp = V.cornerp + B.cornerp_off;
+    const float2 *cy = cp + B.nx + 1, *cz = cy + B.ny + 1;
+    if (fast) {
+      key_cell(B, key, ix, iy, iz);
+    } else {
+      bool out = false;
+      ix = pair_cell(p2[0], cp, (float)bp.inv_dx, B.nx, out);
+      iy = pair_cell(p2[1], cy, (float)bp.inv_dy, B.ny, out);
+      iz = pair_cell(p2[2], cz, (float)bp.inv_dz, B.nz, out);
+      if (out) set_error(V.err, ERR_DOMAIN);
+      key = (unsigned)(B.cell_off + ((long long)iz * B.ny + iy) * B.nx + ix);
+    }
+    V.xlk[i] = make_float4(pair_minus(p2[0], cp[ix]), pair_minus(p2[1], cy[iy]), pair_minus(p2[2], cz[iz]), r);
+  } else {
+    if (!fast) {
+      bool out;
+      key = point_key_d(B, x, y, z, out);
+      if (out) set_error(V.err, ERR_DOMAIN);
+    }
+    key_cell(B, key, ix, iy, iz);
+    const double *cn = V.corner + B.corner_off;
+    V.xlk[i] = make_float4((float)(x - cn[ix]), (float)(y - cn[B.nx + iy]), (float)(z - cn[B.nx + B.ny + iz]), r);
+  }
   V.keys[i] = key;
   V.vals[i] = (unsigned)i;
 }
@@ -174,45 +224,59 @@ __global__ void k_gather(StepView<P> V, int drift) {
   using R = typename P::R;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V.n) return;
-  const int j = (int)V.vals[i];
-  const int meta = V.A.meta[j];
-  const DevBed &B = V.beds[meta >> 8];
-  const BedP<R> &bp = V.bp[meta >> 8];
-  V.B.x[i] = V.A.x[j]; V.B.y[i] = V.A.y[j]; V.B.z[i] = V.A.z[j];
+  // every load first (read-only path), then the stores: many loads in flight per thread
+  const int j = (int)__ldg(V.vals + i);
+  const unsigned k = __ldg(V.keys + i);
+  const bool first = i == 0 || __ldg(V.keys + i - 1) != k;
+  const bool last = i == V.n - 1 || __ldg(V.keys + i + 1) != k;
+  const int meta = __ldg(V.A.meta + j);
+  const double x = __ldg(V.A.x + j), y = __ldg(V.A.y + j), z = __ldg(V.A.z + j);
+  R v[3], w[3], a[3], al[3];
+  float dsp[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    R v = V.A.v[q][j], w = V.A.w[q][j];
-    const R a = V.A.a[q][j], al = V.A.al[q][j];
-    if (drift) {
-      v = half_kick<R>(bp.half_dt, B.dt, v, a);
-      w = w + al * bp.half_dt;
-    }
-    V.B.v[q][i] = v; V.B.w[q][i] = w; V.B.a[q][i] = a; V.B.al[q][i] = al;
+    v[q] = __ldg(V.A.v[q] + j); w[q] = __ldg(V.A.w[q] + j);
+    a[q] = __ldg(V.A.a[q] + j); al[q] = __ldg(V.A.al[q] + j);
+    dsp[q] = __ldg(V.A.dsp[q] + j);
   }
-  V.B.T[i] = V.A.T[j];
-  V.B.d[i] = V.A.d[j];
+  const R T = __ldg(V.A.T + j), d = __ldg(V.A.d + j);
+  double m[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) m[q] = __ldg(V.A.m[q] + j);   // FP64 value or Kahan pair, bit for bit
+  const int orig = __ldg(V.A.orig + j), bi = __ldg(V.A.bidx + j);
+  const float4 xl = __ldg(V.xlk + j);
+  const int c = __ldg(V.H.cnt + j);
+  const int rebuild = *V.rebuild;
+  const DevBed &B = V.beds[meta >> 8];
+  const BedP<R> &bp = V.bp[meta >> 8];
+  V.B.x[i] = x; V.B.y[i] = y; V.B.z[i] = z;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    if (drift) {
+      v[q] = half_kick<R>(bp.half_dt, B.dt, v[q], a[q]);
+      w[q] = w[q] + al[q] * bp.half_dt;
+    }
+    V.B.v[q][i] = v[q]; V.B.w[q][i] = w[q]; V.B.a[q][i] = a[q]; V.B.al[q][i] = al[q];
+    V.B.dsp[q][i] = dsp[q];
+  }
+  V.B.T[i] = T;
+  V.B.d[i] = d;
   R msum = 0;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const double mq = V.A.m[q][j];   // copied bit for bit (FP64 value or Kahan pair)
-    V.B.m[q][i] = mq;
-    msum += mass_r<P>(V.B.m[q], i);
+    V.B.m[q][i] = m[q];
+    msum += mass_word_r<P>(m[q]);
   }
   V.B.meta[i] = meta;
-  V.B.orig[i] = V.A.orig[j];
-  const int bi = V.A.bidx[j];
+  V.B.orig[i] = orig;
   V.B.bidx[i] = bi;
-#pragma unroll
-  for (int q = 0; q < 3; ++q) V.B.dsp[q][i] = V.A.dsp[q][j];
-  if (!*V.rebuild) V.cur[bi] = i;
+  if (!rebuild) V.cur[bi] = i;
   V.mass[i] = msum;
-  V.xl[i] = V.xlk[j];
+  V.xl[i] = xl;
   // occupied ranges
-  const unsigned k = V.keys[i];
-  if (i == 0 || V.keys[i - 1] != k) V.cstart[k] = (unsigned)i;
-  if (i == V.n - 1 || V.keys[i + 1] != k) V.cend[k] = (unsigned)(i + 1);
+  if (first) V.cstart[k] = (unsigned)i;
+  if (last) V.cend[k] = (unsigned)(i + 1);
   // history slots travel with the parcel
-  const int c = V.H.cnt[j];
   V.Hn.cnt[i] = (unsigned char)c;
   for (int s = 0; s < c; ++s) {
     V.Hn.id[(size_t)s * V.cap + i] = V.H.id[(size_t)s * V.cap + j];
@@ -507,7 +571,7 @@ __global__ void k_pair_forces(StepView<P> V) {
       add_contact<P>(V, i, cin, V.B.orig[j], bp, mstar, ri, nrm, delta, vrel, wi, Fi, Ti, cout);
     }
     if (near) {
-      const double xd = V.B.x[i], yd = V.B.y[i], zd = V.B.z[i];
+      const double xd = pos_abs<P>(V.B.x, i, B.x0), yd = pos_abs<P>(V.B.y, i, B.y0), zd = pos_abs<P>(V.B.z, i, B.z0);
       const double rid = __dmul_rn(0.5, __dmul_rn(B.k, (double)di));
       double dist[4], nw[4][3];
       wall_primitives<double>(B, xd, yd, zd, dist, nw);
@@ -827,7 +891,7 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_contacts_cell(StepView<P> V) 
 #pragma unroll
           for (int pp = 0; pp < 4; ++pp) near |= distf[pp] < me.w + 1e-6f;
           if (near) {
-            const double xd = V.B.x[p], yd = V.B.y[p], zd = V.B.z[p];
+            const double xd = pos_abs<P>(V.B.x, p, B.x0), yd = pos_abs<P>(V.B.y, p, B.y0), zd = pos_abs<P>(V.B.z, p, B.z0);
             double dist[4], nw[4][3];
             wall_primitives<double>(B, xd, yd, zd, dist, nw);
             for (int pp = 0; pp < 4; ++pp) {
@@ -1243,7 +1307,9 @@ __global__ void k_scatter_state(StepView<P> V, double *out /* [DEM_NSTATE][n] */
   if (i >= V.n) return;
   const size_t n = (size_t)V.n;
   const int o = V.A.orig[i];
-  out[0 * n + o] = V.A.x[i]; out[1 * n + o] = V.A.y[i]; out[2 * n + o] = V.A.z[i];
+  const DevBed &B = V.beds[V.A.meta[i] >> 8];
+  out[0 * n + o] = pos_abs<P>(V.A.x, i, B.x0); out[1 * n + o] = pos_abs<P>(V.A.y, i, B.y0);
+  out[2 * n + o] = pos_abs<P>(V.A.z, i, B.z0);
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     out[(3 + q) * n + o] = (double)V.A.v[q][i];

@@ -50,6 +50,7 @@ StepView<P> make_view(dem_ctx *c, bool for_step) {
   V.cur = c->curpos;
   V.rebuild = c->rebuild;
   V.corner = c->corner;
+  V.cornerp = c->cornerp;
   V.kprev = c->kres ? c->kres : c->keys;
   V.mass = (R *)c->mass;
   for (int q = 0; q < 3; ++q) { V.F[q] = (R *)c->F[q]; V.Tq[q] = (R *)c->Tq[q]; }
