@@ -82,6 +82,8 @@ def algorithmic_bytes(kernel: str, n: int, ncells: int, zbar: float, L: float, r
         return n * ((4 + 24 + 6 * R + 12 + 16 + 4 + R) + (24 + 12 + 16 + 8))
     if kernel == "radix_sort":
         return n * passes * (8 + 8)
+    if kernel == "resort":       # new and old keys read, sorted keys and permutation written
+        return n * (4 + 4 + 8)
     if kernel == "k_gather":
         return n * ((8 + state + 16 + 1 + zbar * slot) + (state + R + 16 + 4 + 1 + zbar * slot))
     if kernel == "k_pair_search":

@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdem_gb300.so")
-SOURCES = ["dem_api.cu", "inst_f64.cu", "inst_f32.cu", "inst_kahan.cu", "radix.cu", "adjoint.cu", "noalloc.cu"]
+SOURCES = ["dem_api.cu", "inst_f64.cu", "inst_f32.cu", "inst_kahan.cu", "radix.cu", "resort.cu", "adjoint.cu",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

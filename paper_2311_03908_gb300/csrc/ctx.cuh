@@ -36,7 +36,10 @@ struct dem_ctx {
   void *hxi[2] = {};
   // binning
   unsigned *keys = nullptr, *vals = nullptr, *keys2 = nullptr, *vals2 = nullptr, *rhist = nullptr;
-  unsigned *kres = nullptr, *vres = nullptr;   // where the last sort left its result
+  unsigned *kres = nullptr, *vres = nullptr;   // where the last radix sort left its result
+  unsigned *skey[2] = {}, *sval[2] = {};       // sorted keys / permutation of state buffer k
+  unsigned *rsw = nullptr;                     // scratch of the incremental re-sort
+  int rs_pow2 = 1;
   unsigned *cstart = nullptr, *cend = nullptr;
   float4 *xl = nullptr;             // cell-local position and radius, sorted order
   float4 *xlk = nullptr;            // the same, written by the key kernel (pre-sort order)

@@ -332,6 +332,8 @@ void layout(dem_ctx *c, Bump &m) {
   }
   c->keys = m.take<unsigned>(N); c->vals = m.take<unsigned>(N);
   c->keys2 = m.take<unsigned>(N); c->vals2 = m.take<unsigned>(N);
+  for (int k = 0; k < 2; ++k) { c->skey[k] = m.take<unsigned>(N); c->sval[k] = m.take<unsigned>(N); }
+  c->rsw = m.take<unsigned>(resort_words((int)N, &c->rs_pow2));
   c->rhist = m.take<unsigned>(radix_hist_words((int)N));
   c->cstart = m.take<unsigned>(C); c->cend = m.take<unsigned>(C);
   c->xl = m.take<float4>(N);
@@ -708,8 +710,8 @@ int dem_step_graph(dem_ctx *c, int32_t n_steps) {
     c->cur = cur0;
     c->gcur = gcur0;
   }
-  // the host-side bookkeeping advances as the captured steps do; every sort of this
-  // context leaves its result in the same buffer, so kres/vres already point there
+  // the host-side bookkeeping advances as the captured steps do (the sorted keys of a state
+  // buffer live in the key buffer of the same parity)
   for (int k = 0; k < n_steps; ++k) {
     c->cur = 1 - c->cur;
     c->gcur = 1 - c->gcur;
@@ -977,22 +979,21 @@ int dem_autotune(dem_ctx *c, int32_t n_steps) {
   if (cudaMalloc(&snap, c->arena_bytes) != cudaSuccess) return DEM_ENOMEM;
   CK(cudaMemcpyAsync(snap, c->arena, c->arena_bytes, cudaMemcpyDeviceToDevice, c->st));
   const int cur0 = c->cur, gcur0 = c->gcur;
-  unsigned *kres0 = c->kres, *vres0 = c->vres;
   const bool prof0 = c->prof_on;
   int32_t best[DEM_NTUNE];
   get_tuning(c, best);
   int rc = DEM_OK;
   auto restore = [&]() {
     cudaMemcpyAsync(c->arena, snap, c->arena_bytes, cudaMemcpyDeviceToDevice, c->st);
-    c->cur = cur0; c->gcur = gcur0; c->kres = kres0; c->vres = vres0;
+    c->cur = cur0; c->gcur = gcur0;
   };
   // one candidate: per-kernel mean times (ms) and the total, or a negative total on error
-  auto trial = [&](const int32_t *t, std::map<std::string, double> &per) -> double {
+  auto trial = [&](const int32_t *t, std::map<std::string, double> &per, int steps) -> double {
     restore();
     if (apply_tuning(c, t) != DEM_OK) return -1.0;
     c->prof_on = true;
     c->prof_marks.clear(); c->prof_names.clear(); c->prof_ms.clear(); c->prof_n.clear();
-    if (enqueue_steps_any(c, n_steps) != 0) { c->prof_on = false; return -1.0; }
+    if (enqueue_steps_any(c, steps) != 0) { c->prof_on = false; return -1.0; }
     if (cudaStreamSynchronize(c->st) != cudaSuccess) { c->prof_on = false; return -1.0; }
     c->prof_on = false;
     for (const auto &mk : c->prof_marks) {
@@ -1024,7 +1025,7 @@ int dem_autotune(dem_ctx *c, int32_t n_steps) {
     std::memcpy(t, tb, sizeof t);
     for (int k = 1; k <= 6; ++k) t[k] = std::min(bs, lim[k - 1] / 32 * 32);
     std::map<std::string, double> per;
-    if (trial(t, per) < 0) { rc = DEM_ECUDA; break; }
+    if (trial(t, per, n_steps) < 0) { rc = DEM_ECUDA; break; }
     for (int k = 0; k < 6; ++k) {
       auto it = per.find(kname[k]);
       if (it != per.end() && it->second < bt[k]) { bt[k] = it->second; best[1 + k] = t[1 + k]; }
@@ -1040,7 +1041,7 @@ int dem_autotune(dem_ctx *c, int32_t n_steps) {
       t[0] = 0;
       t[7] = sk;
       std::map<std::string, double> per;
-      const double tot = trial(t, per);
+      const double tot = trial(t, per, 4 * n_steps);   // rebuilds amortise over long windows
       if (tot < 0) { rc = DEM_ECUDA; break; }
       if (tot < best_tot) { best_tot = tot; best[7] = sk; }
     }
@@ -1053,7 +1054,7 @@ int dem_autotune(dem_ctx *c, int32_t n_steps) {
     std::memcpy(t, best, sizeof t);
     t[0] = 1;
     std::map<std::string, double> per;
-    const double tot = trial(t, per);
+    const double tot = trial(t, per, 4 * n_steps);
     if (tot < 0) rc = DEM_ECUDA;
     else if (tot < best_tot) best[0] = 1;
   }

@@ -51,6 +51,7 @@ template <class P> struct StepView {
   const double *corner;         // cell-corner coordinates (see DevBed::corner_off)
   const float2 *cornerp;        // cell corners relative to the bed corner, FP32 pairs
   const unsigned *kprev;        // keys of the state before the step (its order)
+  int *moved;                   // per 1024 positions: keys that changed (incremental re-sort)
   R *mass;                      // parcel mass (new order)
   R *F[3], *Tq[3];              // contact force and torque
   R *src;                       // [SR_N][cap] per-parcel cell sources
@@ -214,6 +215,7 @@ __global__ void k_key(StepView<P> V, int drift) {
   }
   V.keys[i] = key;
   V.vals[i] = (unsigned)i;
+  if (drift && key != V.kprev[i]) atomicAdd(V.moved + (i >> 10), 1);
 }
 
 // Gather the state into the sorted order (positions already drifted by k_key; the half

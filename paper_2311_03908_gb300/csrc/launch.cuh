@@ -37,8 +37,8 @@ StepView<P> make_view(dem_ctx *c, bool for_step) {
   fill(V.B, b);
   V.H.cnt = c->hcnt[0]; V.H.id = c->hid[0]; V.H.xi = (R *)c->hxi[0];
   V.Hn.cnt = c->hcnt[1]; V.Hn.id = c->hid[1]; V.Hn.xi = (R *)c->hxi[1];
-  V.keys = c->kres ? c->kres : c->keys;
-  V.vals = c->vres ? c->vres : c->vals;
+  V.keys = c->skey[b];
+  V.vals = c->sval[b];
   V.cstart = c->cstart; V.cend = c->cend;
   V.xl = c->xl;
   V.xlk = c->xlk;
@@ -51,7 +51,7 @@ StepView<P> make_view(dem_ctx *c, bool for_step) {
   V.rebuild = c->rebuild;
   V.corner = c->corner;
   V.cornerp = c->cornerp;
-  V.kprev = c->kres ? c->kres : c->keys;
+  V.kprev = c->skey[a];
   V.mass = (R *)c->mass;
   for (int q = 0; q < 3; ++q) { V.F[q] = (R *)c->F[q]; V.Tq[q] = (R *)c->Tq[q]; }
   V.src = (R *)c->src;
@@ -75,20 +75,35 @@ int enqueue_binning(dem_ctx *c, int drift) {
   StepView<P> V = make_view<P>(c, true);
   V.keys = c->keys;
   V.vals = c->vals;
+  V.moved = resort_counts(c->rsw, c->rs_pow2, c->n);
+  if (drift) cudaMemsetAsync(V.moved, 0, sizeof(int) * (size_t)((c->n + 1023) / 1024 + 1), st);
   int ps = prof_begin(c, "k_key");
   k_key<P><<<grid_for(c->n, c->bs_key), c->bs_key, 0, st>>>(V, drift);
   prof_end(c, ps);
   ++c->launches;
-  unsigned *kr = nullptr, *vr = nullptr;
-  ps = prof_begin(c, "radix_sort");
-  int e = radix_sort_pairs(c->keys, c->vals, c->keys2, c->vals2, c->rhist, c->n, c->key_bits, st,
-                           &kr, &vr, &c->launches);
-  prof_end(c, ps);
-  if (e) return e;
-  c->kres = kr;
-  c->vres = vr;
-  V.keys = kr;
-  V.vals = vr;
+  const int nxt = 1 - c->cur;
+  if (drift) {
+    // few keys change per step: re-sort incrementally from the previous sorted order
+    ps = prof_begin(c, "resort");
+    int e = resort_pairs(c->skey[c->cur], c->keys, c->skey[nxt], c->sval[nxt], c->rsw, c->rs_pow2, c->n, st,
+                         &c->launches);
+    prof_end(c, ps);
+    if (e) return e;
+  } else {
+    // first binning: full LSD radix sort of (key, index)
+    unsigned *kr = nullptr, *vr = nullptr;
+    ps = prof_begin(c, "radix_sort");
+    int e = radix_sort_pairs(c->keys, c->vals, c->keys2, c->vals2, c->rhist, c->n, c->key_bits, st,
+                             &kr, &vr, &c->launches);
+    prof_end(c, ps);
+    if (e) return e;
+    c->kres = kr;
+    c->vres = vr;
+    cudaMemcpyAsync(c->skey[nxt], kr, sizeof(unsigned) * c->n, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(c->sval[nxt], vr, sizeof(unsigned) * c->n, cudaMemcpyDeviceToDevice, st);
+  }
+  V.keys = c->skey[nxt];
+  V.vals = c->sval[nxt];
   cudaMemsetAsync(c->cstart, 0, sizeof(unsigned) * c->ncells, st);
   cudaMemsetAsync(c->cend, 0, sizeof(unsigned) * c->ncells, st);
   ps = prof_begin(c, "k_gather");

@@ -1,0 +1,217 @@
+// resort.cu -- re-sorting parcels whose cell keys changed little since the last sort.
+//
+// Input: kold, the previous sorted keys (position = previous index), and knew[i], the new key
+// of the parcel at previous index i. Output: (kout, vout) = the stable sort of (knew, i), i.e.
+// keys ascending and equal keys in previous-index order -- the same permutation the LSD radix
+// sort gives, bit for bit. Parcels whose key did not change ("stayers") are already in
+// order; the few that changed ("movers") are compacted in previous-index order (a
+// deterministic block scan), ranked on (key, index) by counting (every mover against every
+// other, in shared memory, up to 4096 movers; one block's bitonic sort in global memory
+// beyond), and every parcel's output position follows from two counts (a merge of two sorted
+// sequences):
+//   stayer i:  (stayers before i) + (movers with (key, index) < (knew[i], i));
+//   mover t:   t + (stayers before it) = t + P(clamp(idx, lb, ub)), where [lb, ub) is the run
+//              of kold equal to its new key and P(x) the number of stayers in positions < x
+//              (stayers keep their key, so kold orders them).
+#include <cuda_runtime.h>
+
+#include "radix.cuh"
+
+namespace dem {
+namespace {
+
+constexpr int RZ_BLOCK = 1024;
+constexpr int RZ_SMEM_SORT = 4096;
+
+// exclusive scan of the per-block counts (one block); blk[nb] = total movers
+__global__ void __launch_bounds__(RZ_BLOCK) rz_scan(int *blk, int nb) {
+  __shared__ int part[RZ_BLOCK];
+  const int per = (nb + RZ_BLOCK - 1) / RZ_BLOCK;
+  const int b = threadIdx.x * per, e = min(b + per, nb);
+  int s = 0;
+  for (int t = b; t < e; ++t) s += blk[t];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < RZ_BLOCK; off <<= 1) {
+    const int v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+  for (int t = b; t < e; ++t) {
+    const int v = blk[t];
+    blk[t] = run;
+    run += v;
+  }
+  if (threadIdx.x == RZ_BLOCK - 1) blk[nb] = part[RZ_BLOCK - 1];
+}
+
+// movers before each position (pre[0..n], pre[n] = total) and the compacted movers
+__global__ void __launch_bounds__(RZ_BLOCK) rz_compact(const unsigned *kold, const unsigned *knew, int n,
+                                                       const int *blk, int nb, int *pre,
+                                                       unsigned long long *comp) {
+  __shared__ int wsum[RZ_BLOCK / 32];
+  const int i = blockIdx.x * RZ_BLOCK + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned key = i < n ? knew[i] : 0u;
+  const bool moved = i < n && key != kold[i];
+  const unsigned m = __ballot_sync(0xffffffffu, moved);
+  if (lane == 0) wsum[warp] = __popc(m);
+  __syncthreads();
+  if (warp == 0) {
+    const int v = wsum[lane];
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    wsum[lane] = incl - v;
+  }
+  __syncthreads();
+  const int rank = blk[blockIdx.x] + wsum[warp] + __popc(m & ((1u << lane) - 1u));
+  if (i < n) {
+    pre[i] = rank;
+    if (moved) comp[rank] = ((unsigned long long)key << 32) | (unsigned)i;
+  }
+  if (i == n - 1) pre[n] = blk[nb];
+}
+
+__device__ __forceinline__ void cmpswap(unsigned long long &a, unsigned long long &b, bool asc) {
+  if ((a > b) == asc) { const unsigned long long t = a; a = b; b = t; }
+}
+
+// rank of every mover by counting the movers below it (composites are unique), written to
+// sorted[rank]; more than RZ_SMEM_SORT movers: left to rz_sort_big
+__global__ void __launch_bounds__(256) rz_rank(const int *blk, int nb, const unsigned long long *comp,
+                                               unsigned long long *sorted) {
+  __shared__ unsigned long long s[RZ_SMEM_SORT];
+  const int m = blk[nb];
+  if (m > RZ_SMEM_SORT) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.x * blockDim.x >= m) return;   // whole block beyond the movers
+  for (int q = threadIdx.x; q < m; q += blockDim.x) s[q] = comp[q];
+  __syncthreads();
+  if (t < m) {
+    const unsigned long long v = s[t];
+    int r = 0;
+    for (int q = 0; q < m; ++q) r += s[q] < v ? 1 : 0;
+    sorted[r] = v;
+  }
+}
+
+// more movers than fit: one block sorts them in global memory (bitonic; padded with the
+// largest value up to a power of two)
+__global__ void __launch_bounds__(RZ_BLOCK) rz_sort_big(const int *blk, int nb, const unsigned long long *comp,
+                                                        unsigned long long *a, int cap) {
+  const int m = blk[nb];
+  if (m <= RZ_SMEM_SORT) return;
+  int P = 1;
+  while (P < m) P <<= 1;
+  if (P > cap) return;   // cannot happen: cap is the next power of two of n
+  for (int t = threadIdx.x; t < P; t += RZ_BLOCK) a[t] = t < m ? comp[t] : ~0ull;
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < P; t += RZ_BLOCK) {
+        const int u = t ^ j;
+        if (u > t) {
+          unsigned long long x = a[t], y = a[u];
+          cmpswap(x, y, (t & k) == 0);
+          a[t] = x;
+          a[u] = y;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__device__ __forceinline__ int count_less(const unsigned long long *c, int lo, int hi, unsigned long long v) {
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (c[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// output positions. A block of stayers sees only the movers between the composites of its
+// first and last position (kold is sorted, so (kold[g], g) increases with g): two searches
+// per block, then a short scan per thread.
+constexpr int RZ_MERGE = 256;
+__global__ void __launch_bounds__(RZ_MERGE) rz_merge(const unsigned *kold, const unsigned *knew, int n,
+                                                     const int *pre, const unsigned long long *sorted,
+                                                     unsigned *kout, unsigned *vout) {
+  __shared__ int bounds[2];
+  const int m = pre[n];
+  const int g0 = blockIdx.x * RZ_MERGE;
+  const int g = g0 + threadIdx.x;
+  if (threadIdx.x == 0) {
+    const int g1 = min(g0 + RZ_MERGE, n) - 1;
+    const unsigned long long c0 = ((unsigned long long)kold[g0] << 32) | (unsigned)g0;
+    const unsigned long long c1 = ((unsigned long long)kold[g1] << 32) | (unsigned)g1;
+    bounds[0] = count_less(sorted, 0, m, c0);
+    bounds[1] = count_less(sorted, bounds[0], m, c1 + 1);
+  }
+  __syncthreads();
+  if (g < n) {
+    const unsigned key = knew[g];
+    if (key == kold[g]) {   // stayer
+      const unsigned long long c = ((unsigned long long)key << 32) | (unsigned)g;
+      int below = bounds[0];
+      for (int t = bounds[0]; t < bounds[1]; ++t) below += sorted[t] < c ? 1 : 0;
+      const int pos = g - pre[g] + below;
+      kout[pos] = key;
+      vout[pos] = (unsigned)g;
+    }
+  }
+  for (int t = g; t < m; t += gridDim.x * RZ_MERGE) {
+    const unsigned long long c = sorted[t];
+    const unsigned key = (unsigned)(c >> 32);
+    const int idx = (int)(c & 0xffffffffu);
+    int lo = 0, hi = n;
+    while (lo < hi) { const int mid = (lo + hi) >> 1; if (kold[mid] < key) lo = mid + 1; else hi = mid; }
+    const int lb = lo;
+    hi = n;
+    while (lo < hi) { const int mid = (lo + hi) >> 1; if (kold[mid] <= key) lo = mid + 1; else hi = mid; }
+    const int ub = lo;
+    const int x = idx < lb ? lb : (idx > ub ? ub : idx);
+    const int pos = t + (x - pre[x]);
+    kout[pos] = key;
+    vout[pos] = (unsigned)idx;
+  }
+}
+
+}  // namespace
+
+size_t resort_words(int n, int *pow2) {
+  int P = 1;
+  while (P < n) P <<= 1;
+  *pow2 = P;
+  const size_t nb = (size_t)(n + RZ_BLOCK - 1) / RZ_BLOCK;
+  // comp and sorted (2 words per entry each), pre (n + 1), blk (nb + 1)
+  return 4 * (size_t)P + (size_t)n + 1 + nb + 1 + 2;
+}
+
+int *resort_counts(unsigned *scratch, int pow2, int n) {
+  return reinterpret_cast<int *>(scratch + 4 * (size_t)pow2) + n + 1;
+}
+
+int resort_pairs(const unsigned *kold, const unsigned *knew, unsigned *kout, unsigned *vout,
+                 unsigned *scratch, int pow2, int n, cudaStream_t st, long long *launches) {
+  const int nb = (n + RZ_BLOCK - 1) / RZ_BLOCK;
+  unsigned long long *comp = reinterpret_cast<unsigned long long *>(scratch);
+  unsigned long long *sorted = comp + pow2;
+  int *pre = reinterpret_cast<int *>(scratch + 4 * (size_t)pow2);
+  int *blk = pre + n + 1;
+  rz_scan<<<1, RZ_BLOCK, 0, st>>>(blk, nb);
+  rz_compact<<<nb, RZ_BLOCK, 0, st>>>(kold, knew, n, blk, nb, pre, comp);
+  rz_rank<<<RZ_SMEM_SORT / 256, 256, 0, st>>>(blk, nb, comp, sorted);
+  rz_sort_big<<<1, RZ_BLOCK, 0, st>>>(blk, nb, comp, sorted, pow2);
+  rz_merge<<<(n + RZ_MERGE - 1) / RZ_MERGE, RZ_MERGE, 0, st>>>(kold, knew, n, pre, sorted, kout, vout);
+  if (launches) *launches += 5;
+  return (int)cudaPeekAtLastError();
+}
+
+}  // namespace dem
