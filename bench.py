@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--autotune", type=int, default=30, help="steps per autotuner candidate before the "
                     "warm-up (0: keep the default launch configuration)")
+    ap.add_argument("--tuning", default="", help="fixed launch configuration instead of the autotuner, "
+                    "e.g. contact_kernel=0,bs_key=64,skin_permille=50 (profiler runs repeat a plain run's)")
     return ap.parse_args()
 
 
@@ -97,6 +99,37 @@ def algorithmic_bytes(kernel: str, n: int, ncells: int, zbar: float, L: float, r
     if kernel == "k_cells":
         return ncells * ((4 + 1 + 8 + 5 * 8 + 2 * R) + (5 * 8 + 14 * R)) + n * 14 * R
     return 0.0
+
+
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one full-size ncu
+# capture of the 2M-parcel split-precision bed; per parcel), valid only for the sources it
+# was taken on (profiles/traffic_ibm_2m_split.md gives the command).
+TRAFFIC_SOURCE_SHA256 = "7ebdf1665b947705ce74b77b49d117eabf39436bf0d35601467a15ab149f52e4"
+TRAFFIC_WORKLOAD = ("ibm_2m", "split", 2_000_000)
+TRAFFIC_BYTES_PER_PARCEL = {"k_gas_particle": 226.06, "k_gather": 300.32, "k_key": 124.49, "k_cells": 117.60,
+                            "k_pair_list": 55.80, "k_pair_forces": 28.08, "rz_merge": 12.00}
+
+
+def source_sha256() -> str:
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2311_03908_gb300", "csrc", "*.cu")) +
+                   glob.glob(os.path.join(ROOT, "paper_2311_03908_gb300", "csrc", "*.cuh")) +
+                   [os.path.join(ROOT, "include", "dem.h")])
+    for f in files:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel: str, workload: str, precision: str, n: int):
+    """Bytes per launch from the committed ncu capture, or None when it does not apply."""
+    if (workload, precision, n) != TRAFFIC_WORKLOAD or kernel not in TRAFFIC_BYTES_PER_PARCEL:
+        return None
+    if source_sha256() != TRAFFIC_SOURCE_SHA256:
+        return None   # the kernels changed since the counters were taken
+    return TRAFFIC_BYTES_PER_PARCEL[kernel] * n
 
 
 class ClockSampler:
@@ -245,7 +278,11 @@ def main():
     bed = make_workload(args.workload, rank, args.parcels)
     ctx = binding.Context(bed, precision=args.precision, stream=stream.cuda_stream)
     n = bed.n
-    tuning = ctx.dem_autotune(args.autotune) if args.autotune > 0 else ctx.dem_get_tuning()
+    if args.tuning:
+        ctx.dem_set_tuning(**{k: int(v) for k, v in (kv.split("=") for kv in args.tuning.split(","))})
+        tuning = ctx.dem_get_tuning()
+    else:
+        tuning = ctx.dem_autotune(args.autotune) if args.autotune > 0 else ctx.dem_get_tuning()
 
     def barrier():
         torch.cuda.synchronize()
@@ -308,7 +345,9 @@ def main():
     if dom:
         ach = kernels[dom]["gbs"] or 0.0
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "peak_kind": f"{peak_kind} HBM copy bandwidth", "traffic": None}
+                "frac": ach / peak, "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                "traffic": measured_traffic(dom, args.workload, args.precision, n),
+                "traffic_unit": "bytes per launch (ncu dram read + write)"}
     step_alg = sum(v["alg_bytes"] for v in kernels.values())
     step_ms = ms_max / args.steps
 
