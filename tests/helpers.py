@@ -28,3 +28,18 @@ def bed_from_arrays(cfg, x, y, z, v=None, d_real=100e-6, T=873.0, comp=(1.0, 0.0
 
 ISOLATED = (synth.NO_GRAVITY | synth.NO_DRAG | synth.NO_HEAT | synth.NO_KINETICS |
             synth.NO_GAS_UPDATE)
+
+
+def paper_values():
+    """Numbers printed in the paper (tests/golden/paper_printed_values.txt), by name."""
+    import os
+    out = {}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_printed_values.txt")
+    with open(path) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            name, rest = line.split("=", 1)
+            out[name.strip()] = float(rest.split("|", 1)[0])
+    return out

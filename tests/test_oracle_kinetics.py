@@ -13,7 +13,9 @@ import pytest
 
 import oracle
 from paper_2311_03908_gb300 import synth
-from tests.helpers import bed_from_arrays
+from tests.helpers import bed_from_arrays, paper_values
+
+PV = paper_values()
 
 RG = 8.314
 
@@ -21,9 +23,9 @@ RG = 8.314
 def test_printed_q_values():
     # Sec. 2.3: q_{m,h} = 0.9666, q_{w,m} = 0.9309, q_{Fe,w} = 0.7773 (eq (2-36))
     M = {s: oracle.molar_mass(s) for s in oracle.SPECIES}
-    assert round(2 * M["Fe3O4"] / (3 * M["Fe2O3"]), 4) == 0.9666
-    assert round(3 * M["FeO"] / M["Fe3O4"], 4) == 0.9309
-    assert round(M["Fe"] / M["FeO"], 4) == 0.7773
+    assert round(2 * M["Fe3O4"] / (3 * M["Fe2O3"]), 4) == PV["q_m_h"]
+    assert round(3 * M["FeO"] / M["Fe3O4"], 4) == PV["q_w_m"]
+    assert round(M["Fe"] / M["FeO"], 4) == PV["q_Fe_w"]
 
 
 def test_layer_porosity_chain_against_table3():
@@ -32,12 +34,13 @@ def test_layer_porosity_chain_against_table3():
     # printed q values.
     cfg = synth.BedConfig()
     xi = oracle.layer_porosity(cfg, synth.ORE_HEMATITE)
-    rho_eff_h = (1 - xi[0]) * 5180.0 / 0.9666
-    assert abs(rho_eff_h - 3500.0) < 0.002 * 3500.0
-    assert abs((1 - xi[1]) * 5390.0 - rho_eff_h * 0.9666 * 0.9309) < 1.0
-    assert abs((1 - xi[2]) * 7900.0 - rho_eff_h * 0.9666 * 0.9309 * 0.7773) < 1.0
+    q1, q2, q3 = PV["q_m_h"], PV["q_w_m"], PV["q_Fe_w"]
+    rho_eff_h = (1 - xi[0]) * 5180.0 / q1
+    assert abs(rho_eff_h - PV["rho_eff_bed2"]) < 0.002 * PV["rho_eff_bed2"]
+    assert abs((1 - xi[1]) * 5390.0 - rho_eff_h * q1 * q2) < 1.0
+    assert abs((1 - xi[2]) * 7900.0 - rho_eff_h * q1 * q2 * q3) < 1.0
     # final (iron) porosity of hematite about 0.65 in the paper's run (Sec. 5.2.2): loose
-    assert abs(xi[2] - 0.65) < 0.1 * 0.65
+    assert abs(xi[2] - PV["porosity_Fe_final_hematite"]) < 0.1 * PV["porosity_Fe_final_hematite"]
 
 
 def _pure_bed(comp, ore):
@@ -280,7 +283,7 @@ def test_bed1_film_resistance_loose():
     cfg = synth.BedConfig(T_in=943.0, Y_in=tuple(Y), k0=synth.MAGNETITE_FIT[0], Ea=synth.MAGNETITE_FIT[1])
     k = oracle.kinetics(cfg, np.array([0, 0.6994, 0.3006, 0]) * 1e-7, 943.0, 100e-6, 1, 0.5,
                         0.18 / 0.5, 943.0, Y, 1e-5)
-    assert abs(k["F"] - 0.048) < 0.3 * 0.048
+    assert abs(k["F"] - PV["film_resistance_bed1"]) < 0.3 * PV["film_resistance_bed1"]
 
 
 def test_bed1_resistance_ordering_loose():
