@@ -42,7 +42,6 @@ struct dem_ctx {
   int rs_pow2 = 1;
   unsigned *cstart = nullptr, *cend = nullptr;
   float4 *xl = nullptr;             // cell-local position and radius, sorted order
-  float4 *xlk = nullptr;            // the same, written by the key kernel (pre-sort order)
   int *plist = nullptr;             // pair-search hit lists [KLIST][cap]
   unsigned char *pcode = nullptr, *pcnt = nullptr;
   int *nl = nullptr, *curpos = nullptr, *rebuild = nullptr;   // neighbour lists

@@ -337,7 +337,6 @@ void layout(dem_ctx *c, Bump &m) {
   c->rhist = m.take<unsigned>(radix_hist_words((int)N));
   c->cstart = m.take<unsigned>(C); c->cend = m.take<unsigned>(C);
   c->xl = m.take<float4>(N);
-  c->xlk = m.take<float4>(N);
   c->plist = m.take<int>(N * KLIST);
   c->pcode = m.take<unsigned char>(N * KLIST);
   c->pcnt = m.take<unsigned char>(N);

@@ -40,7 +40,6 @@ template <class P> struct StepView {
   unsigned *keys, *vals;        // sorted keys (global gas cell) and the permutation
   unsigned *cstart, *cend;      // parcel range of every gas cell (empty: 0, 0)
   float4 *xl;                   // FP32 position relative to the own cell's corner, radius
-  float4 *xlk;                  // the same in pre-sort order (written by k_key)
   int *plist;                   // [KLIST][cap] candidate partners found by k_pair_search
   unsigned char *pcode;         // [KLIST][cap] their cell offset codes
   unsigned char *pcnt;          // number of listed candidates per parcel
@@ -124,8 +123,8 @@ __device__ __forceinline__ int pair_cell(float2 p, const float2 *c, float inv_h,
   return q;
 }
 
-// Half kick + drift (written back to the positions), the sort key, and the FP32 cell-local
-// coordinates. The FP32 forms take the key from the previous cell when the parcel stays more
+// Half kick + drift (written back to the positions) and the sort key. The FP32 forms take
+// the key from the previous cell when the parcel stays more
 // than 1e-3 of an edge inside it (the local coordinates then decide it exactly, their error
 // being ~1e-10 m); otherwise, and always in the FP64 form, the key is recomputed from the
 // position: FP64 floor((x - x0) / dx), or in the split-Kahan form the pair comparison.
@@ -187,40 +186,28 @@ __global__ void k_key(StepView<P> V, int drift) {
       if (fast) key = V.kprev[i];
     }
   }
-  int ix, iy, iz;
-  const float r = (float)(bp.k * V.A.d[i]) * 0.5f;
-  if constexpr (P::kahan) {
-    const float2 *cp = V.cornerp + B.cornerp_off;
-    const float2 *cy = cp + B.nx + 1, *cz = cy + B.ny + 1;
-    if (fast) {
-      key_cell(B, key, ix, iy, iz);
-    } else {
-      bool out = false;
-      ix = pair_cell(p2[0], cp, (float)bp.inv_dx, B.nx, out);
-      iy = pair_cell(p2[1], cy, (float)bp.inv_dy, B.ny, out);
-      iz = pair_cell(p2[2], cz, (float)bp.inv_dz, B.nz, out);
-      if (out) set_error(V.err, ERR_DOMAIN);
+  if (!fast) {
+    bool out = false;
+    if constexpr (P::kahan) {
+      const float2 *cp = V.cornerp + B.cornerp_off;
+      const float2 *cy = cp + B.nx + 1, *cz = cy + B.ny + 1;
+      const int ix = pair_cell(p2[0], cp, (float)bp.inv_dx, B.nx, out);
+      const int iy = pair_cell(p2[1], cy, (float)bp.inv_dy, B.ny, out);
+      const int iz = pair_cell(p2[2], cz, (float)bp.inv_dz, B.nz, out);
       key = (unsigned)(B.cell_off + ((long long)iz * B.ny + iy) * B.nx + ix);
-    }
-    V.xlk[i] = make_float4(pair_minus(p2[0], cp[ix]), pair_minus(p2[1], cy[iy]), pair_minus(p2[2], cz[iz]), r);
-  } else {
-    if (!fast) {
-      bool out;
+    } else {
       key = point_key_d(B, x, y, z, out);
-      if (out) set_error(V.err, ERR_DOMAIN);
     }
-    key_cell(B, key, ix, iy, iz);
-    const double *cn = V.corner + B.corner_off;
-    V.xlk[i] = make_float4((float)(x - cn[ix]), (float)(y - cn[B.nx + iy]), (float)(z - cn[B.nx + B.ny + iz]), r);
+    if (out) set_error(V.err, ERR_DOMAIN);
   }
   V.keys[i] = key;
-  V.vals[i] = (unsigned)i;
+  if (!drift) V.vals[i] = (unsigned)i;   // the first binning's radix sort needs the identity
   if (drift && key != V.kprev[i]) atomicAdd(V.moved + (i >> 10), 1);
 }
 
 // Gather the state into the sorted order (positions already drifted by k_key; the half
-// kicks applied here); record the cell ranges by boundary detection on the sorted keys;
-// copy the history slots.
+// kicks applied here) and derive the FP32 cell-local coordinates; record the cell ranges by
+// boundary detection on the sorted keys; copy the history slots.
 template <class P>
 __global__ void k_gather(StepView<P> V, int drift) {
   using R = typename P::R;
@@ -246,7 +233,6 @@ __global__ void k_gather(StepView<P> V, int drift) {
 #pragma unroll
   for (int q = 0; q < 4; ++q) m[q] = __ldg(V.A.m[q] + j);   // FP64 value or Kahan pair, bit for bit
   const int orig = __ldg(V.A.orig + j), bi = __ldg(V.A.bidx + j);
-  const float4 xl = __ldg(V.xlk + j);
   const int c = __ldg(V.H.cnt + j);
   const int rebuild = *V.rebuild;
   const DevBed &B = V.beds[meta >> 8];
@@ -274,7 +260,28 @@ __global__ void k_gather(StepView<P> V, int drift) {
   V.B.bidx[i] = bi;
   if (!rebuild) V.cur[bi] = i;
   V.mass[i] = msum;
-  V.xl[i] = xl;
+  // FP32 position relative to the corner of the parcel's cell, and its radius
+  {
+    int ix, iy, iz;
+    key_cell(B, k, ix, iy, iz);
+    const float r = (float)(bp.k * d) * 0.5f;
+    float4 xl;
+    if constexpr (P::kahan) {
+      const float2 *cp = V.cornerp + B.cornerp_off;
+      const float2 *cy = cp + B.nx + 1, *cz = cy + B.ny + 1;
+      const unsigned long long ux = (unsigned long long)__double_as_longlong(x);
+      const unsigned long long uy = (unsigned long long)__double_as_longlong(y);
+      const unsigned long long uz = (unsigned long long)__double_as_longlong(z);
+      const float2 px = make_float2(__uint_as_float((unsigned)ux), __uint_as_float((unsigned)(ux >> 32)));
+      const float2 py = make_float2(__uint_as_float((unsigned)uy), __uint_as_float((unsigned)(uy >> 32)));
+      const float2 pz = make_float2(__uint_as_float((unsigned)uz), __uint_as_float((unsigned)(uz >> 32)));
+      xl = make_float4(pair_minus(px, cp[ix]), pair_minus(py, cy[iy]), pair_minus(pz, cz[iz]), r);
+    } else {
+      const double *cn = V.corner + B.corner_off;
+      xl = make_float4((float)(x - cn[ix]), (float)(y - cn[B.nx + iy]), (float)(z - cn[B.nx + B.ny + iz]), r);
+    }
+    V.xl[i] = xl;
+  }
   // occupied ranges
   if (first) V.cstart[k] = (unsigned)i;
   if (last) V.cend[k] = (unsigned)(i + 1);

@@ -41,7 +41,6 @@ StepView<P> make_view(dem_ctx *c, bool for_step) {
   V.vals = c->sval[b];
   V.cstart = c->cstart; V.cend = c->cend;
   V.xl = c->xl;
-  V.xlk = c->xlk;
   V.plist = c->plist;
   V.pcode = c->pcode;
   V.pcnt = c->pcnt;
