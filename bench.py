@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--autotune", type=int, default=30, help="steps per autotuner candidate before the "
                     "warm-up (0: keep the default launch configuration)")
     ap.add_argument("--tuning", default="", help="fixed launch configuration instead of the autotuner, "
-                    "e.g. contact_kernel=0,bs_key=64,skin_permille=50 (profiler runs repeat a plain run's)")
+                    "e.g. neighbour_lists=1,bs_key=64,skin_permille=50 (profiler runs repeat a plain run's)")
     return ap.parse_args()
 
 

@@ -204,9 +204,9 @@ int dem_get_diag(dem_ctx *c, double *out_host);
 
 /* Launch configuration of the step kernels (no counterpart in the paper: it only changes how
  * the same step is computed), DEM_NTUNE int32 values:
- *   [0] contact kernels: 0 = one thread per parcel (neighbour-list search + force kernel),
- *       1 = one warp per occupied cell (cell-list search every step, fused forces);
- *   [1]..[6] block sizes of the key, gather, pair-search, pair-force, gas-particle and
+ *   [0] contact search: 1 = Verlet neighbour lists rebuilt from the cell list when a parcel
+ *       has moved half the skin (default), 0 = the cell-list search every step;
+ *   [1]..[6] block sizes of the key, re-store, pair-search, pair-force, gas-particle and
  *       gas-cell kernels (multiples of 32 in [32, 1024], and no larger than the kernel's
  *       register use allows: the FP64 form's larger kernels stop below 512);
  *   [7] neighbour-list skin in thousandths of the bed's largest parcel diameter (1..1000).
@@ -218,7 +218,7 @@ int dem_get_tuning(dem_ctx *c, int32_t *out);
 int dem_set_tuning(dem_ctx *c, const int32_t *in);
 
 /* Pick the tuning above by timing candidates, each over n_steps steps started from the same
- * saved state (contact kernel, block sizes, skin). The state is restored afterwards and the
+ * saved state (block sizes, skin, lists or not). The state is restored afterwards and the
  * chosen tuning applied (as dem_set_tuning). Needs a temporary device copy of the context's
  * arena (DEM_ENOMEM if it cannot be allocated); clears the dem_profile record. Synchronous. */
 int dem_autotune(dem_ctx *c, int32_t n_steps);

@@ -340,7 +340,7 @@ __device__ void load_par(const StepView<Pp> &V, const BedP<double> *bpd, int i, 
   P.dt = B.dt;
   P.p0 = B.p0;
   const size_t nc = (size_t)V.ncells;
-  const unsigned c = V.keys[i];
+  const unsigned c = V.keyp[i];   // the parcel's gas cell (storage order)
   const double *G = V.gas;
   const double Y[3] = {gas_d<Pp>(G, GS_Y0 * nc + c), gas_d<Pp>(G, GS_Y1 * nc + c), gas_d<Pp>(G, GS_Y2 * nc + c)};
   const CellProps<double> cp = gas_cell_props<double>(B, gas_d<Pp>(G, GS_EPS * nc + c), Y, gas_d<Pp>(G, GS_T * nc + c));

@@ -24,11 +24,11 @@ struct dem_ctx {
   char *arena = nullptr;
   size_t arena_bytes = 0;
   size_t rsize = 8;                 // sizeof(R)
-  // parcel state, two buffers (cur = current)
+  // parcel state: buffer 0 the state (in place), buffer 1 the scratch of a re-store
   double *px[2][3] = {};
   void *pv[2][3] = {}, *pw[2][3] = {}, *pa[2][3] = {}, *pal[2][3] = {}, *pT[2] = {}, *pd[2] = {};
   double *pm[2][4] = {};
-  int *pmeta[2] = {}, *porig[2] = {}, *pbidx[2] = {};
+  int *pmeta[2] = {}, *porig[2] = {};
   float *pdsp[2][3] = {};
   // contact history: [0] current, [1] gather target
   unsigned char *hcnt[2] = {};
@@ -44,14 +44,14 @@ struct dem_ctx {
   float4 *xl = nullptr;             // cell-local position and radius, sorted order
   int *plist = nullptr;             // pair-search hit lists [KLIST][cap]
   unsigned char *pcode = nullptr, *pcnt = nullptr;
-  int *nl = nullptr, *curpos = nullptr, *rebuild = nullptr;   // neighbour lists
+  int *nl = nullptr, *rebuild = nullptr;   // neighbour lists (storage positions), build flag
   unsigned char *nlc = nullptr;
   double skin_frac = 0.1;         // neighbour-list skin as a fraction of the largest diameter
   double *corner = nullptr;         // cell-corner coordinates: per bed x0+i dx, y0+j dy, z0+k dz
   std::vector<double> hcorner;
   float2 *cornerp = nullptr;        // cell corners relative to the bed corner as FP32 pairs
   std::vector<float2> hcornerp;
-  void *mass = nullptr, *F[3] = {}, *Tq[3] = {}, *src = nullptr;
+  void *F[3] = {}, *Tq[3] = {}, *src = nullptr;
   // gas: two state buffers (gcur = current), properties, marks
   double *gas[2] = {};
   void *gp = nullptr;
@@ -72,7 +72,7 @@ struct dem_ctx {
   int sticky = DEM_OK;
   long long launches = 0;
   int bs_contacts = 128, bs_gp = 128, bs_gather = 256, bs_cells = 256, bs_key = 256;
-  int contact_mode = 0;            // 0: one thread per parcel (search + forces), 1: one warp per occupied cell
+  int use_lists = 1;               // 1: Verlet neighbour lists, 0: cell-list search every step
   int bs_search = 256;
   std::map<std::tuple<int, int, int>, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;
   std::map<std::tuple<int, int, int>, long long> graph_launches;

@@ -324,7 +324,6 @@ void layout(dem_ctx *c, Bump &m) {
     for (int q = 0; q < 4; ++q) c->pm[k][q] = m.take<double>(N);
     c->pmeta[k] = m.take<int>(N);
     c->porig[k] = m.take<int>(N);
-    c->pbidx[k] = m.take<int>(N);
     for (int q = 0; q < 3; ++q) c->pdsp[k][q] = m.take<float>(N);
     c->hcnt[k] = m.take<unsigned char>(N);
     c->hid[k] = m.take<int>(N * KMAX);
@@ -342,11 +341,9 @@ void layout(dem_ctx *c, Bump &m) {
   c->pcnt = m.take<unsigned char>(N);
   c->nl = m.take<int>(N * KNL);
   c->nlc = m.take<unsigned char>(N);
-  c->curpos = m.take<int>(N);
   c->rebuild = m.take<int>(1);
   c->corner = m.take<double>(c->hcorner.size());
   c->cornerp = m.take<float2>(c->hcornerp.size());
-  c->mass = m.take<char>(N, R);
   for (int q = 0; q < 3; ++q) { c->F[q] = m.take<char>(N, R); c->Tq[q] = m.take<char>(N, R); }
   c->src = m.take<char>(N * SR_N, R);
   c->gas[0] = m.take<double>(C * GS_N);
@@ -376,7 +373,7 @@ void drop_graphs(dem_ctx *c) {
 }
 
 void get_tuning(const dem_ctx *c, int32_t *t) {
-  t[0] = c->contact_mode;
+  t[0] = c->use_lists;
   t[1] = c->bs_key; t[2] = c->bs_gather; t[3] = c->bs_search; t[4] = c->bs_contacts;
   t[5] = c->bs_gp; t[6] = c->bs_cells;
   t[7] = (int32_t)std::lround(c->skin_frac * 1000.0);
@@ -389,7 +386,7 @@ int apply_tuning(dem_ctx *c, const int32_t *t) {
   for (int k = 1; k <= 6; ++k)
     if (t[k] < 32 || t[k] > 1024 || t[k] % 32 != 0 || t[k] > lim[k - 1]) return DEM_EINVAL;
   if (t[7] < 1 || t[7] > 1000) return DEM_EINVAL;
-  c->contact_mode = t[0];
+  c->use_lists = t[0];
   c->bs_key = t[1]; c->bs_gather = t[2]; c->bs_search = t[3]; c->bs_contacts = t[4];
   c->bs_gp = t[5]; c->bs_cells = t[6];
   c->skin_frac = t[7] / 1000.0;
@@ -609,11 +606,9 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
   // neighbour lists: none yet (the first step builds them); no displacement
   ck(cudaMemsetAsync(c->rebuild, 1, sizeof(int), c->st));
   for (int k = 0; k < 2; ++k) {
-    ck(cudaMemsetAsync(c->pbidx[k], 0, sizeof(int) * (size_t)n, c->st));
     for (int q = 0; q < 3; ++q) ck(cudaMemsetAsync(c->pdsp[k][q], 0, sizeof(float) * (size_t)n, c->st));
   }
   ck(cudaMemsetAsync(c->nlc, 0, (size_t)n, c->st));
-  ck(cudaMemsetAsync(c->curpos, 0, sizeof(int) * (size_t)n, c->st));
   // gas: cell -> bed, marks, initial state
   {
     std::vector<int> cb(c->ncells);
@@ -1010,12 +1005,12 @@ int dem_autotune(dem_ctx *c, int32_t n_steps) {
     return tot;
   };
   // 1) block sizes, every per-thread kernel at once, each kernel keeping its fastest
-  const char *kname[6] = {"k_key", "k_gather", "k_pair_search", "k_pair_forces", "k_gas_particle", "k_cells"};
+  const char *kname[6] = {"k_key", "k_restore", "k_pair_search", "k_pair_forces", "k_gas_particle", "k_cells"};
   double bt[6];
   for (int k = 0; k < 6; ++k) bt[k] = 1e300;
   int32_t tb[DEM_NTUNE];
   std::memcpy(tb, best, sizeof tb);
-  tb[0] = 0;
+  tb[0] = 1;
   int lim[6];
   if (DEM_DISPATCH(c, kernel_limits, lim) != 0) rc = DEM_ECUDA;
   for (int bs : {64, 128, 256, 512}) {
@@ -1037,7 +1032,7 @@ int dem_autotune(dem_ctx *c, int32_t n_steps) {
     for (int sk : {25, 50, 100, 200}) {
       int32_t t[DEM_NTUNE];
       std::memcpy(t, best, sizeof t);
-      t[0] = 0;
+      t[0] = 1;
       t[7] = sk;
       std::map<std::string, double> per;
       const double tot = trial(t, per, 4 * n_steps);   // rebuilds amortise over long windows
@@ -1046,16 +1041,16 @@ int dem_autotune(dem_ctx *c, int32_t n_steps) {
     }
     if (rc != DEM_OK) best[7] = skin0;
   }
-  // 3) the warp-per-cell contact kernel against the best per-thread configuration
-  best[0] = 0;
+  // 3) the cell-list search every step (no lists) against the best list configuration
+  best[0] = 1;
   if (rc == DEM_OK) {
     int32_t t[DEM_NTUNE];
     std::memcpy(t, best, sizeof t);
-    t[0] = 1;
+    t[0] = 0;
     std::map<std::string, double> per;
     const double tot = trial(t, per, 4 * n_steps);
     if (tot < 0) rc = DEM_ECUDA;
-    else if (tot < best_tot) best[0] = 1;
+    else if (tot < best_tot) best[0] = 0;
   }
   restore();
   if (rc == DEM_OK) rc = apply_tuning(c, best);

@@ -6,52 +6,59 @@
 
 namespace dem {
 
-// One parcel-state buffer, structure of arrays in the current sorted order.
+// One parcel-state buffer, structure of arrays. The parcels stay where they are between
+// neighbour-list builds ("storage order"); each build re-stores them in the sorted order of
+// that step, so the storage order is always the cell order of the last build, and parcels
+// have moved less than half the skin since.
 template <class R> struct PState {
   double *x, *y, *z;
   R *v[3], *w[3], *a[3], *al[3], *T, *d;
   double *m[4];  // FP64 masses, or (value, compensation) FP32 pairs in the split-Kahan form
   int *meta;     // bed << 8 | ore
   int *orig;     // parcel index (input order)
-  int *bidx;     // position of the parcel when the neighbour lists were last built
-  float *dsp[3]; // displacement since that build (FP32)
+  float *dsp[3]; // displacement since the last list build (FP32)
 };
 
-// Contact-history table: count per parcel, then KMAX slots of partner index and 3-vector.
 // Verlet neighbour lists: slots per parcel, and the count that marks an overflowed list
 constexpr int KNL = 32;
 constexpr int NL_OVERFLOW = 255;
 
+// Contact-history table: count per parcel, then KMAX slots of partner index and 3-vector.
 template <class R> struct Hist {
   unsigned char *cnt;
   int *id;     // [KMAX][cap]
   R *xi;       // [KMAX*3][cap]
 };
 
-// Everything a step's kernels touch.
+// Everything a step's kernels touch. Parcel arrays are indexed by storage position; the
+// cell ranges and sorted keys by sorted position (vals maps sorted to storage positions).
 template <class P> struct StepView {
   using R = typename P::R;
   int n, cap, nbeds;
   long long ncells;
   const DevBed *beds;
   const BedP<R> *bp;
-  PState<R> A, B;               // A: state before the step, B: gather target
-  Hist<R> H, Hn;                // H: current history, Hn: gather target
-  unsigned *keys, *vals;        // sorted keys (global gas cell) and the permutation
-  unsigned *cstart, *cend;      // parcel range of every gas cell (empty: 0, 0)
+  PState<R> A, S;               // A: the state (updated in place); S: scratch of a re-store
+  Hist<R> H, Hn;                // H: history before the step, Hn: after it
+  Hist<R> Hs;                   // scratch of a re-store
+  unsigned *keyp;               // gas-cell key of each parcel (storage order)
+  unsigned *keys, *vals;        // sorted keys and the storage position at each sorted position
+  const unsigned *keys_prev, *vals_prev;   // the same for the previous step
+  unsigned *knew, *vrel;        // re-sort input (new keys in the previous sorted order) and output
+  unsigned *cstart, *cend;      // sorted-position range of every gas cell (empty: 0, 0)
   float4 *xl;                   // FP32 position relative to the own cell's corner, radius
-  int *plist;                   // [KLIST][cap] candidate partners found by k_pair_search
+  float4 *xls;                  // scratch of a re-store (aliases the per-parcel sources,
+                                // which the gas-particle kernel rewrites later in the step)
+  int *plist;                   // [KLIST][cap] partners in contact range this step
   unsigned char *pcode;         // [KLIST][cap] their cell offset codes
-  unsigned char *pcnt;          // number of listed candidates per parcel
-  int *nl;                      // [KNL][cap] neighbour lists (build positions), by build position
-  unsigned char *nlc;           // list lengths by build position (NL_OVERFLOW: none)
-  int *cur;                     // current sorted position of each build position
-  int *rebuild;                 // device flag: rebuild the neighbour lists this step
+  unsigned char *pcnt;          // number of them per parcel
+  int *nl;                      // [KNL][cap] neighbour lists (storage positions)
+  unsigned char *nlc;           // list lengths (NL_OVERFLOW: none, search the cells)
+  int *rebuild;                 // device flag: rebuild the lists (and re-store) this step
+  int nolists;                  // search the cell list every step instead of using lists
   const double *corner;         // cell-corner coordinates (see DevBed::corner_off)
   const float2 *cornerp;        // cell corners relative to the bed corner, FP32 pairs
-  const unsigned *kprev;        // keys of the state before the step (its order)
-  int *moved;                   // per 1024 positions: keys that changed (incremental re-sort)
-  R *mass;                      // parcel mass (new order)
+  int *moved;                   // per 1024 sorted positions: keys that changed (re-sort)
   R *F[3], *Tq[3];              // contact force and torque
   R *src;                       // [SR_N][cap] per-parcel cell sources
   double *gas, *gas_new;        // [GS_N][ncells]
@@ -64,6 +71,14 @@ template <class P> struct StepView {
   const long long *step_ctr;    // steps completed so far (device)
   unsigned long long *list_acc; // list entries of the build in progress
 };
+
+// total layer mass of parcel i in the form's type (the same sum everywhere it is needed)
+template <class P> __device__ __forceinline__ typename P::R parcel_mass(const PState<typename P::R> &A, int i) {
+  typename P::R s = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) s += mass_r<P>(A.m[q], i);
+  return s;
+}
 
 __device__ __forceinline__ bool coupled_step(int ncouple, const long long *ctr) {
   return ncouple == 1 || (((int)(*ctr % ncouple)) + 1) % ncouple == 0;
@@ -123,10 +138,25 @@ __device__ __forceinline__ int pair_cell(float2 p, const float2 *c, float inv_h,
   return q;
 }
 
-// Half kick + drift (written back to the positions) and the sort key. The FP32 forms take
-// the key from the previous cell when the parcel stays more
-// than 1e-3 of an edge inside it (the local coordinates then decide it exactly, their error
-// being ~1e-10 m); otherwise, and always in the FP64 form, the key is recomputed from the
+// FP32 position relative to the corner of cell (ix, iy, iz) and the radius
+template <class P>
+__device__ __forceinline__ float4 local_coords(const StepView<P> &V, const DevBed &B, int ix, int iy, int iz,
+                                               double x, double y, double z, const float2 *p2, float r) {
+  if constexpr (P::kahan) {
+    const float2 *cp = V.cornerp + B.cornerp_off;
+    const float2 *cy = cp + B.nx + 1, *cz = cy + B.ny + 1;
+    return make_float4(pair_minus(p2[0], cp[ix]), pair_minus(p2[1], cy[iy]), pair_minus(p2[2], cz[iz]), r);
+  } else {
+    const double *cn = V.corner + B.corner_off;
+    return make_float4((float)(x - cn[ix]), (float)(y - cn[B.nx + iy]), (float)(z - cn[B.nx + B.ny + iz]), r);
+  }
+}
+
+// First half kick (velocity and spin, written back) and drift of velocity Verlet, the gas
+// cell of the new position, and the FP32 cell-local coordinates; in place, storage order.
+// The FP32 forms take the key from the previous cell when the parcel stays more than 1e-3 of
+// an edge inside it (the local coordinates then decide it exactly, their error being
+// ~1e-10 m); otherwise, and always in the FP64 form, the key is recomputed from the
 // position: FP64 floor((x - x0) / dx), or in the split-Kahan form the pair comparison.
 template <class P>
 __global__ void k_key(StepView<P> V, int drift) {
@@ -146,11 +176,14 @@ __global__ void k_key(StepView<P> V, int drift) {
   }
   bool fast = false;
   unsigned key = 0;
+  int ix = 0, iy = 0, iz = 0;
   if (drift) {
     R disp[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       const R vh = half_kick<R>(bp.half_dt, B.dt, V.A.v[q][i], V.A.a[q][i]);
+      V.A.v[q][i] = vh;
+      V.A.w[q][i] = V.A.w[q][i] + V.A.al[q][i] * bp.half_dt;
       if constexpr (sizeof(R) == 8) disp[q] = __dmul_rn(vh, B.dt);
       else disp[q] = vh * bp.dt;
     }
@@ -183,7 +216,10 @@ __global__ void k_key(StepView<P> V, int drift) {
       const float ux = o.x + (float)disp[0], uy = o.y + (float)disp[1], uz = o.z + (float)disp[2];
       fast = ux > 1e-3f * hx && ux < 0.999f * hx && uy > 1e-3f * hy && uy < 0.999f * hy &&
              uz > 1e-3f * hz && uz < 0.999f * hz;
-      if (fast) key = V.kprev[i];
+      if (fast) {
+        key = V.keyp[i];
+        key_cell(B, key, ix, iy, iz);
+      }
     }
   }
   if (!fast) {
@@ -191,106 +227,107 @@ __global__ void k_key(StepView<P> V, int drift) {
     if constexpr (P::kahan) {
       const float2 *cp = V.cornerp + B.cornerp_off;
       const float2 *cy = cp + B.nx + 1, *cz = cy + B.ny + 1;
-      const int ix = pair_cell(p2[0], cp, (float)bp.inv_dx, B.nx, out);
-      const int iy = pair_cell(p2[1], cy, (float)bp.inv_dy, B.ny, out);
-      const int iz = pair_cell(p2[2], cz, (float)bp.inv_dz, B.nz, out);
+      ix = pair_cell(p2[0], cp, (float)bp.inv_dx, B.nx, out);
+      iy = pair_cell(p2[1], cy, (float)bp.inv_dy, B.ny, out);
+      iz = pair_cell(p2[2], cz, (float)bp.inv_dz, B.nz, out);
       key = (unsigned)(B.cell_off + ((long long)iz * B.ny + iy) * B.nx + ix);
     } else {
       key = point_key_d(B, x, y, z, out);
+      key_cell(B, key, ix, iy, iz);
     }
     if (out) set_error(V.err, ERR_DOMAIN);
   }
-  V.keys[i] = key;
-  if (!drift) V.vals[i] = (unsigned)i;   // the first binning's radix sort needs the identity
-  if (drift && key != V.kprev[i]) atomicAdd(V.moved + (i >> 10), 1);
+  V.keyp[i] = key;
+  V.xl[i] = local_coords<P>(V, B, ix, iy, iz, x, y, z, p2, (float)(bp.k * V.A.d[i]) * 0.5f);
 }
 
-// Gather the state into the sorted order (positions already drifted by k_key; the half
-// kicks applied here) and derive the FP32 cell-local coordinates; record the cell ranges by
-// boundary detection on the sorted keys; copy the history slots.
+// The new keys in the previous sorted order (the re-sort's input), and how many of them
+// changed in each block of 1024 sorted positions.
 template <class P>
-__global__ void k_gather(StepView<P> V, int drift) {
-  using R = typename P::R;
+__global__ void __launch_bounds__(1024) k_sorted_keys(StepView<P> V) {
+  const int i = blockIdx.x * 1024 + threadIdx.x;
+  bool moved = false;
+  if (i < V.n) {
+    const unsigned k = V.keyp[V.vals_prev[i]];
+    V.knew[i] = k;
+    moved = k != V.keys_prev[i];
+  }
+  const int c = __syncthreads_count(moved);
+  if (threadIdx.x == 0) V.moved[blockIdx.x] = c;
+}
+
+// Storage position at each new sorted position (the re-sort returns previous sorted
+// positions), and the sorted-position range of every occupied cell.
+template <class P>
+__global__ void k_compose(StepView<P> V) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V.n) return;
-  // every load first (read-only path), then the stores: many loads in flight per thread
+  V.vals[i] = V.vals_prev[V.vrel[i]];
+  const unsigned k = V.keys[i];
+  if (i == 0 || V.keys[i - 1] != k) V.cstart[k] = (unsigned)i;
+  if (i == V.n - 1 || V.keys[i + 1] != k) V.cend[k] = (unsigned)(i + 1);
+}
+
+// Re-store (list-build steps, and the first binning): copy every parcel's record, local
+// coordinates, key and history to its sorted position in the scratch buffers ...
+template <class P>
+__global__ void k_restore_out(StepView<P> V, int force) {
+  if (!force && !*V.rebuild) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V.n) return;
   const int j = (int)__ldg(V.vals + i);
-  const unsigned k = __ldg(V.keys + i);
-  const bool first = i == 0 || __ldg(V.keys + i - 1) != k;
-  const bool last = i == V.n - 1 || __ldg(V.keys + i + 1) != k;
-  const int meta = __ldg(V.A.meta + j);
   const double x = __ldg(V.A.x + j), y = __ldg(V.A.y + j), z = __ldg(V.A.z + j);
-  R v[3], w[3], a[3], al[3];
-  float dsp[3];
+  V.S.x[i] = x; V.S.y[i] = y; V.S.z[i] = z;
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    v[q] = __ldg(V.A.v[q] + j); w[q] = __ldg(V.A.w[q] + j);
-    a[q] = __ldg(V.A.a[q] + j); al[q] = __ldg(V.A.al[q] + j);
-    dsp[q] = __ldg(V.A.dsp[q] + j);
+    V.S.v[q][i] = __ldg(V.A.v[q] + j); V.S.w[q][i] = __ldg(V.A.w[q] + j);
+    V.S.a[q][i] = __ldg(V.A.a[q] + j); V.S.al[q][i] = __ldg(V.A.al[q] + j);
+    V.S.dsp[q][i] = __ldg(V.A.dsp[q] + j);
   }
-  const R T = __ldg(V.A.T + j), d = __ldg(V.A.d + j);
-  double m[4];
+  V.S.T[i] = __ldg(V.A.T + j);
+  V.S.d[i] = __ldg(V.A.d + j);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) m[q] = __ldg(V.A.m[q] + j);   // FP64 value or Kahan pair, bit for bit
-  const int orig = __ldg(V.A.orig + j), bi = __ldg(V.A.bidx + j);
+  for (int q = 0; q < 4; ++q) V.S.m[q][i] = __ldg(V.A.m[q] + j);
+  V.S.meta[i] = __ldg(V.A.meta + j);
+  V.S.orig[i] = __ldg(V.A.orig + j);
+  V.xls[i] = __ldg(V.xl + j);
   const int c = __ldg(V.H.cnt + j);
-  const int rebuild = *V.rebuild;
-  const DevBed &B = V.beds[meta >> 8];
-  const BedP<R> &bp = V.bp[meta >> 8];
-  V.B.x[i] = x; V.B.y[i] = y; V.B.z[i] = z;
+  V.Hs.cnt[i] = (unsigned char)c;
+  for (int s = 0; s < c; ++s) {
+    V.Hs.id[(size_t)s * V.cap + i] = V.H.id[(size_t)s * V.cap + j];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) V.Hs.xi[(size_t)(s * 3 + q) * V.cap + i] = V.H.xi[(size_t)(s * 3 + q) * V.cap + j];
+  }
+}
+
+// ... and back into the state, which is then in sorted order (storage = sorted position).
+template <class P>
+__global__ void k_restore_in(StepView<P> V, int force) {
+  if (!force && !*V.rebuild) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V.n) return;
+  V.A.x[i] = V.S.x[i]; V.A.y[i] = V.S.y[i]; V.A.z[i] = V.S.z[i];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    if (drift) {
-      v[q] = half_kick<R>(bp.half_dt, B.dt, v[q], a[q]);
-      w[q] = w[q] + al[q] * bp.half_dt;
-    }
-    V.B.v[q][i] = v[q]; V.B.w[q][i] = w[q]; V.B.a[q][i] = a[q]; V.B.al[q][i] = al[q];
-    V.B.dsp[q][i] = dsp[q];
+    V.A.v[q][i] = V.S.v[q][i]; V.A.w[q][i] = V.S.w[q][i];
+    V.A.a[q][i] = V.S.a[q][i]; V.A.al[q][i] = V.S.al[q][i];
+    V.A.dsp[q][i] = V.S.dsp[q][i];
   }
-  V.B.T[i] = T;
-  V.B.d[i] = d;
-  R msum = 0;
+  V.A.T[i] = V.S.T[i];
+  V.A.d[i] = V.S.d[i];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    V.B.m[q][i] = m[q];
-    msum += mass_word_r<P>(m[q]);
-  }
-  V.B.meta[i] = meta;
-  V.B.orig[i] = orig;
-  V.B.bidx[i] = bi;
-  if (!rebuild) V.cur[bi] = i;
-  V.mass[i] = msum;
-  // FP32 position relative to the corner of the parcel's cell, and its radius
-  {
-    int ix, iy, iz;
-    key_cell(B, k, ix, iy, iz);
-    const float r = (float)(bp.k * d) * 0.5f;
-    float4 xl;
-    if constexpr (P::kahan) {
-      const float2 *cp = V.cornerp + B.cornerp_off;
-      const float2 *cy = cp + B.nx + 1, *cz = cy + B.ny + 1;
-      const unsigned long long ux = (unsigned long long)__double_as_longlong(x);
-      const unsigned long long uy = (unsigned long long)__double_as_longlong(y);
-      const unsigned long long uz = (unsigned long long)__double_as_longlong(z);
-      const float2 px = make_float2(__uint_as_float((unsigned)ux), __uint_as_float((unsigned)(ux >> 32)));
-      const float2 py = make_float2(__uint_as_float((unsigned)uy), __uint_as_float((unsigned)(uy >> 32)));
-      const float2 pz = make_float2(__uint_as_float((unsigned)uz), __uint_as_float((unsigned)(uz >> 32)));
-      xl = make_float4(pair_minus(px, cp[ix]), pair_minus(py, cy[iy]), pair_minus(pz, cz[iz]), r);
-    } else {
-      const double *cn = V.corner + B.corner_off;
-      xl = make_float4((float)(x - cn[ix]), (float)(y - cn[B.nx + iy]), (float)(z - cn[B.nx + B.ny + iz]), r);
-    }
-    V.xl[i] = xl;
-  }
-  // occupied ranges
-  if (first) V.cstart[k] = (unsigned)i;
-  if (last) V.cend[k] = (unsigned)(i + 1);
-  // history slots travel with the parcel
-  V.Hn.cnt[i] = (unsigned char)c;
+  for (int q = 0; q < 4; ++q) V.A.m[q][i] = V.S.m[q][i];
+  V.A.meta[i] = V.S.meta[i];
+  V.A.orig[i] = V.S.orig[i];
+  V.xl[i] = V.xls[i];
+  V.keyp[i] = V.keys[i];
+  V.vals[i] = (unsigned)i;
+  const int c = V.Hs.cnt[i];
+  V.H.cnt[i] = (unsigned char)c;
   for (int s = 0; s < c; ++s) {
-    V.Hn.id[(size_t)s * V.cap + i] = V.H.id[(size_t)s * V.cap + j];
+    V.H.id[(size_t)s * V.cap + i] = V.Hs.id[(size_t)s * V.cap + i];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) V.Hn.xi[(size_t)(s * 3 + q) * V.cap + i] = V.H.xi[(size_t)(s * 3 + q) * V.cap + j];
+    for (int q = 0; q < 3; ++q) V.H.xi[(size_t)(s * 3 + q) * V.cap + i] = V.Hs.xi[(size_t)(s * 3 + q) * V.cap + i];
   }
 }
 
@@ -309,9 +346,9 @@ __device__ __forceinline__ void add_contact(const StepView<P> &V, int i, int cin
   using R = typename P::R;
   R xo[3] = {0, 0, 0};
   for (int sl = 0; sl < cin; ++sl)
-    if (V.Hn.id[(size_t)sl * V.cap + i] == pid) {
+    if (V.H.id[(size_t)sl * V.cap + i] == pid) {
 #pragma unroll
-      for (int q = 0; q < 3; ++q) xo[q] = V.Hn.xi[(size_t)(sl * 3 + q) * V.cap + i];
+      for (int q = 0; q < 3; ++q) xo[q] = V.H.xi[(size_t)(sl * 3 + q) * V.cap + i];
       break;
     }
   R Fc[3], Tc[3], xn[3];
@@ -319,9 +356,9 @@ __device__ __forceinline__ void add_contact(const StepView<P> &V, int i, int cin
 #pragma unroll
   for (int q = 0; q < 3; ++q) { Fi[q] += Fc[q]; Ti[q] += Tc[q]; }
   if (cout < KMAX) {
-    V.H.id[(size_t)cout * V.cap + i] = pid;
+    V.Hn.id[(size_t)cout * V.cap + i] = pid;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) V.H.xi[(size_t)(cout * 3 + q) * V.cap + i] = xn[q];
+    for (int q = 0; q < 3; ++q) V.Hn.xi[(size_t)(cout * 3 + q) * V.cap + i] = xn[q];
     ++cout;
   } else {
     set_error(V.err, ERR_CAPACITY);
@@ -363,22 +400,23 @@ template <class P>
 __global__ void k_pair_search(StepView<P> V) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V.n) return;
-  const int b = V.B.meta[i] >> 8;
+  const int b = V.A.meta[i] >> 8;
   const DevBed &B = V.beds[b];
   const BedP<typename P::R> &bp = V.bp[b];
   const size_t cap = (size_t)V.cap;
   const bool rebuild = *V.rebuild != 0;
   // between rebuilds the parcels with a list are k_pair_list's
-  if (!rebuild && V.nlc[V.B.bidx[i]] != NL_OVERFLOW) return;
+  if (!V.nolists && !rebuild && V.nlc[i] != NL_OVERFLOW) return;
+  const bool build = rebuild && !V.nolists;
   int nh = 0, nn = 0;
   if (!(bp.flags & DEM_NO_CONTACTS)) {
     const float4 me = V.xl[i];
-    const unsigned key = V.keys[i];
+    const unsigned key = V.keyp[i];
     const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
     const float pm = P::exact ? (float)bp.pf_margin : 0.f;
     {
       // cell-list path (list rebuild, or a parcel whose list overflowed)
-      const float skin = rebuild ? (float)bp.skin : 0.f;
+      const float skin = build ? (float)bp.skin : 0.f;
       int X, Y, Z;
       key_cell(B, key, X, Y, Z);
       // no partner centre lies farther than r_i + r_max (+ skin); the margin is far above
@@ -398,36 +436,45 @@ __global__ void k_pair_search(StepView<P> V) {
             const unsigned jb = __ldg(V.cstart + krow + dx), je = __ldg(V.cend + krow + dx);
             const float ox = dx * hx - me.x;
             const unsigned char code = (unsigned char)((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
-#define DEM_PAIR_TEST(o, jj)                                                          \
+#define DEM_PAIR_TEST(o, j)                                                           \
   do {                                                                                \
     const float ex = (o).x + ox, ey = (o).y + oy, ez = (o).z + oz; /* x_j - x_i */   \
     const float d2 = ex * ex + ey * ey + ez * ez;                                     \
     const float rs = me.w + (o).w;                                                    \
     const float lim = rs + pm, liml = rs + skin;                                      \
-    if (rebuild && d2 < liml * liml && (int)(jj) != i) {                              \
-      if (nn < KNL) V.nl[nn * cap + i] = (int)(jj);                                   \
+    if (build && d2 < liml * liml && (j) != i) {                                      \
+      if (nn < KNL) V.nl[nn * cap + i] = (j);                                         \
       ++nn;                                                                           \
     }                                                                                 \
-    if (d2 < lim * lim && (int)(jj) != i) {                                           \
+    if (d2 < lim * lim && (j) != i) {                                                 \
       if (nh < KLIST) {                                                               \
-        V.plist[nh * cap + i] = (int)(jj);                                            \
+        V.plist[nh * cap + i] = (j);                                                  \
         V.pcode[nh * cap + i] = code;                                                 \
       }                                                                               \
       ++nh;                                                                           \
     }                                                                                 \
   } while (0)
-            unsigned jj = jb;
-            for (; jj + 4 <= je; jj += 4) {
-              const float4 o0 = __ldg(V.xl + jj), o1 = __ldg(V.xl + jj + 1);
-              const float4 o2 = __ldg(V.xl + jj + 2), o3 = __ldg(V.xl + jj + 3);
-              DEM_PAIR_TEST(o0, jj);
-              DEM_PAIR_TEST(o1, jj + 1);
-              DEM_PAIR_TEST(o2, jj + 2);
-              DEM_PAIR_TEST(o3, jj + 3);
-            }
-            for (; jj < je; ++jj) {
-              const float4 o0 = __ldg(V.xl + jj);
-              DEM_PAIR_TEST(o0, jj);
+            if (rebuild) {
+              // just re-stored: storage position = sorted position
+              int jj = (int)jb;
+              for (; jj + 4 <= (int)je; jj += 4) {
+                const float4 o0 = __ldg(V.xl + jj), o1 = __ldg(V.xl + jj + 1);
+                const float4 o2 = __ldg(V.xl + jj + 2), o3 = __ldg(V.xl + jj + 3);
+                DEM_PAIR_TEST(o0, jj);
+                DEM_PAIR_TEST(o1, jj + 1);
+                DEM_PAIR_TEST(o2, jj + 2);
+                DEM_PAIR_TEST(o3, jj + 3);
+              }
+              for (; jj < (int)je; ++jj) {
+                const float4 o0 = __ldg(V.xl + jj);
+                DEM_PAIR_TEST(o0, jj);
+              }
+            } else {
+              for (unsigned jj = jb; jj < je; ++jj) {
+                const int j = (int)__ldg(V.vals + jj);
+                const float4 o0 = __ldg(V.xl + j);
+                DEM_PAIR_TEST(o0, j);
+              }
             }
 #undef DEM_PAIR_TEST
           }
@@ -436,52 +483,48 @@ __global__ void k_pair_search(StepView<P> V) {
     }
   }
   if (rebuild) {
-    // this step's positions become the build positions
+#pragma unroll
+    for (int q = 0; q < 3; ++q) V.A.dsp[q][i] = 0.f;   // displacements count from this build
+  }
+  if (build) {
     V.nlc[i] = (unsigned char)(nn > KNL ? NL_OVERFLOW : nn);
     const unsigned am = __activemask();   // one atomic per group of lanes running together
     const unsigned tot = __reduce_add_sync(am, (unsigned)min(nn, KNL));
     if ((threadIdx.x & 31) == __ffs(am) - 1) atomicAdd(V.list_acc, (unsigned long long)tot);
-    V.B.bidx[i] = i;
-    V.cur[i] = i;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) V.B.dsp[q][i] = 0.f;
   }
   if (nh > KLIST) { set_error(V.err, ERR_CAPACITY); nh = KLIST; }
   V.pcnt[i] = (unsigned char)nh;
 }
 
-// Between rebuilds: test the partners listed at the last build. Four list entries are
-// resolved at a time (entry -> current position -> key and local position) so that several
-// of these dependent loads are in flight per thread.
+// Between rebuilds: test the partners listed at the last build (storage positions, which
+// have not changed since). Four entries are resolved at a time (entry -> key and local
+// position) so that several dependent loads are in flight per thread.
 template <class P>
 __global__ void k_pair_list(StepView<P> V) {
-  if (*V.rebuild) return;   // k_pair_search rebuilds the lists this step
+  if (*V.rebuild || V.nolists) return;   // k_pair_search handles this step
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V.n) return;
-  const int bi = V.B.bidx[i];
-  const int listed = V.nlc[bi];
+  const int listed = V.nlc[i];
   if (listed == NL_OVERFLOW) return;   // k_pair_search handles it
   const size_t cap = (size_t)V.cap;
   int nh = 0;
   if (listed > 0) {
-    const int b = V.B.meta[i] >> 8;
+    const int b = V.A.meta[i] >> 8;
     const DevBed &B = V.beds[b];
     const BedP<typename P::R> &bp = V.bp[b];
     const float4 me = V.xl[i];
-    const unsigned key = V.keys[i];
+    const unsigned key = V.keyp[i];
     const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
     const float pm = P::exact ? (float)bp.pf_margin : 0.f;
     for (int k0 = 0; k0 < listed; k0 += 4) {
       int j[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) j[u] = k0 + u < listed ? V.nl[(k0 + u) * cap + bi] : -1;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) j[u] = j[u] >= 0 ? V.cur[j[u]] : -1;
+      for (int u = 0; u < 4; ++u) j[u] = k0 + u < listed ? V.nl[(k0 + u) * cap + i] : -1;
       unsigned kj[4];
       float4 o[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        kj[u] = j[u] >= 0 ? V.keys[j[u]] : key;
+        kj[u] = j[u] >= 0 ? V.keyp[j[u]] : key;
         o[u] = j[u] >= 0 ? __ldg(V.xl + j[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
 #pragma unroll
@@ -512,18 +555,18 @@ __global__ void k_pair_forces(StepView<P> V) {
   using R = typename P::R;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V.n) return;
-  const int meta = V.B.meta[i];
+  const int meta = V.A.meta[i];
   const int b = meta >> 8;
   const DevBed &B = V.beds[b];
   const BedP<R> &bp = V.bp[b];
   R Fi[3] = {0, 0, 0}, Ti[3] = {0, 0, 0};
   int cout = 0;
-  const int cin = V.Hn.cnt[i];
+  const int cin = V.H.cnt[i];
   const float4 me = V.xl[i];
   const int nh = V.pcnt[i];
   // walls: FP32 pre-screen on the absolute position rebuilt from the cell corner
   int X, Y, Z;
-  key_cell(B, V.keys[i], X, Y, Z);
+  key_cell(B, V.keyp[i], X, Y, Z);
   const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
   const float xa = (float)bp.x0 + X * hx + me.x, ya = (float)bp.y0 + Y * hy + me.y, za = (float)bp.z0 + Z * hz + me.z;
   float distf[4], nwf[4][3];
@@ -533,13 +576,13 @@ __global__ void k_pair_forces(StepView<P> V) {
   for (int p = 0; p < 4; ++p) near |= distf[p] < me.w + 1e-6f;
   // the parcel's own state is read only when it has a partner or a wall within reach
   if (!(bp.flags & DEM_NO_CONTACTS) && (nh > 0 || near)) {
-    const R di = V.B.d[i];
-    const R mi = V.mass[i];
-    const R vi[3] = {V.B.v[0][i], V.B.v[1][i], V.B.v[2][i]};
-    const R wi[3] = {V.B.w[0][i], V.B.w[1][i], V.B.w[2][i]};
+    const R di = V.A.d[i];
+    const R mi = parcel_mass<P>(V.A, i);
+    const R vi[3] = {V.A.v[0][i], V.A.v[1][i], V.A.v[2][i]};
+    const R wi[3] = {V.A.w[0][i], V.A.w[1][i], V.A.w[2][i]};
     double xi_d = 0, yi_d = 0, zi_d = 0, ri_d = 0;
     if constexpr (P::exact) {
-      xi_d = V.B.x[i]; yi_d = V.B.y[i]; zi_d = V.B.z[i];
+      xi_d = V.A.x[i]; yi_d = V.A.y[i]; zi_d = V.A.z[i];
       ri_d = __dmul_rn(0.5, __dmul_rn(B.k, (double)di));
     }
     const R ri = P::exact ? (R)ri_d : (R)me.w;
@@ -549,8 +592,8 @@ __global__ void k_pair_forces(StepView<P> V) {
       R nrm[3], delta;
       double rj_d = 0;
       if constexpr (P::exact) {
-        const double dxd = V.B.x[j] - xi_d, dyd = V.B.y[j] - yi_d, dzd = V.B.z[j] - zi_d;
-        rj_d = __dmul_rn(0.5, __dmul_rn(B.k, (double)V.B.d[j]));
+        const double dxd = V.A.x[j] - xi_d, dyd = V.A.y[j] - yi_d, dzd = V.A.z[j] - zi_d;
+        rj_d = __dmul_rn(0.5, __dmul_rn(B.k, (double)V.A.d[j]));
         const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dxd, dxd), __dmul_rn(dyd, dyd)), __dmul_rn(dzd, dzd));
         const double rs = __dadd_rn(ri_d, rj_d);
         if (!(d2 < __dmul_rn(rs, rs))) continue;
@@ -570,17 +613,17 @@ __global__ void k_pair_forces(StepView<P> V) {
         delta = (R)((rsf * rsf - d2f) / (rsf + df));
       }
       const R rj = P::exact ? (R)rj_d : (R)__ldg(&V.xl[j].w);
-      const R mj = V.mass[j];
+      const R mj = parcel_mass<P>(V.A, j);
       const R mstar = mi * mj / (mi + mj);
-      const R ws[3] = {ri * wi[0] + rj * V.B.w[0][j], ri * wi[1] + rj * V.B.w[1][j], ri * wi[2] + rj * V.B.w[2][j]};
+      const R ws[3] = {ri * wi[0] + rj * V.A.w[0][j], ri * wi[1] + rj * V.A.w[1][j], ri * wi[2] + rj * V.A.w[2][j]};
       R vrel[3];
-      vrel[0] = (vi[0] - V.B.v[0][j]) + (ws[1] * nrm[2] - ws[2] * nrm[1]);
-      vrel[1] = (vi[1] - V.B.v[1][j]) + (ws[2] * nrm[0] - ws[0] * nrm[2]);
-      vrel[2] = (vi[2] - V.B.v[2][j]) + (ws[0] * nrm[1] - ws[1] * nrm[0]);
-      add_contact<P>(V, i, cin, V.B.orig[j], bp, mstar, ri, nrm, delta, vrel, wi, Fi, Ti, cout);
+      vrel[0] = (vi[0] - V.A.v[0][j]) + (ws[1] * nrm[2] - ws[2] * nrm[1]);
+      vrel[1] = (vi[1] - V.A.v[1][j]) + (ws[2] * nrm[0] - ws[0] * nrm[2]);
+      vrel[2] = (vi[2] - V.A.v[2][j]) + (ws[0] * nrm[1] - ws[1] * nrm[0]);
+      add_contact<P>(V, i, cin, V.A.orig[j], bp, mstar, ri, nrm, delta, vrel, wi, Fi, Ti, cout);
     }
     if (near) {
-      const double xd = pos_abs<P>(V.B.x, i, B.x0), yd = pos_abs<P>(V.B.y, i, B.y0), zd = pos_abs<P>(V.B.z, i, B.z0);
+      const double xd = pos_abs<P>(V.A.x, i, B.x0), yd = pos_abs<P>(V.A.y, i, B.y0), zd = pos_abs<P>(V.A.z, i, B.z0);
       const double rid = __dmul_rn(0.5, __dmul_rn(B.k, (double)di));
       double dist[4], nw[4][3];
       wall_primitives<double>(B, xd, yd, zd, dist, nw);
@@ -598,334 +641,12 @@ __global__ void k_pair_forces(StepView<P> V) {
       }
     }
   }
-  V.H.cnt[i] = (unsigned char)cout;
+  V.Hn.cnt[i] = (unsigned char)cout;
 #pragma unroll
   for (int q = 0; q < 3; ++q) { V.F[q][i] = Fi[q]; V.Tq[q][i] = Ti[q]; }
   if (V.diag) V.diag[(size_t)DG_NCONTACT * V.cap + i] = (double)cout;
 }
 
-
-// ---------------------------------------------------------------------------------------
-// Contacts, one warp per occupied cell. Warp w takes the cells whose first parcel lies in
-// sorted positions [32w, 32w+32). For a cell (up to 32 own parcels at a time):
-//  * the 27 neighbouring cells form 9 contiguous runs of sorted parcels (rows dz, dy);
-//    lanes read 32 candidates at a time, keep those within reach of the own cell's box
-//    (r_j + the largest own radius) and compact them in order with a ballot;
-//  * each round tests 32 compacted candidates against one own parcel, one per lane, and
-//    appends the hits of that parcel in candidate order;
-//  * hits are then evaluated flattened over the lanes (32 pairs at a time) and each own
-//    parcel's lane accumulates its own results in order, so force sums and history slots
-//    come out in the same order as a sequential 27-cell loop (dz, dy, dx, then index).
-// ---------------------------------------------------------------------------------------
-constexpr int CW_WARPS = 4;   // warps per block of k_contacts_cell
-
-template <class R> struct CellWarpSmem {
-  int list[32][KLIST];          // hits per own parcel: sorted index of the partner
-  unsigned char code[32][KLIST];
-  float4 own[32];               // own parcels: cell-local position, radius
-  float4 cbuf[64];              // compacted candidates, relative to the own cell's corner
-  int cj[64];
-  unsigned char cc[64];
-  int nh[32];                   // hits per own parcel (may exceed KLIST: capacity error)
-  int rb[9], pre[10];           // row starts and exclusive prefix of row lengths
-  unsigned kc[9];               // key of the row's centre cell
-  int hex[33];                  // exclusive prefix of the (capped) hit counts
-  R res[10][32];                // evaluated pairs: F, T, xi, accepted
-  int rid[32];
-};
-
-template <class P>
-__global__ void __launch_bounds__(CW_WARPS * 32) k_contacts_cell(StepView<P> V) {
-  using R = typename P::R;
-  __shared__ CellWarpSmem<R> sm_all[CW_WARPS];
-  CellWarpSmem<R> &S = sm_all[threadIdx.x >> 5];
-  const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  const int i0 = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
-  if (i0 >= V.n) return;   // whole warp
-  const int iv = i0 + lane;
-  const bool valid = iv < V.n;
-  const unsigned key_i = valid ? V.keys[iv] : 0u;
-  const bool head = valid && (iv == 0 || V.keys[iv - 1] != key_i);
-  unsigned hm = __ballot_sync(FULL, head);
-  while (hm) {
-    const int h = __ffs(hm) - 1;
-    hm &= hm - 1;
-    const int s = i0 + h;
-    const unsigned key = __shfl_sync(FULL, key_i, h);
-    const int e = (int)V.cend[key];
-    const int b = V.B.meta[s] >> 8;
-    const DevBed &B = V.beds[b];
-    const BedP<R> &bp = V.bp[b];
-    const bool no_contacts = (bp.flags & DEM_NO_CONTACTS) != 0;
-    int X, Y, Z;
-    key_cell(B, key, X, Y, Z);
-    const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
-    const float pm = (float)bp.pf_margin;
-    for (int g0 = s; g0 < e; g0 += 32) {
-      const int nq = min(32, e - g0);
-      // own parcels
-      float ow_r = 0.f;
-      if (lane < nq) {
-        const float4 o = V.xl[g0 + lane];
-        S.own[lane] = o;
-        ow_r = o.w;
-      }
-      S.nh[lane] = 0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) ow_r = fmaxf(ow_r, __shfl_xor_sync(FULL, ow_r, o));
-      // rows of the 27-cell block
-      int len = 0;
-      if (lane < 9 && !no_contacts) {
-        const int dz = lane / 3 - 1, dy = lane % 3 - 1;
-        const int Y2 = Y + dy, Z2 = Z + dz;
-        unsigned jb = 0xffffffffu, je = 0;
-        if (Y2 >= 0 && Y2 < B.ny && Z2 >= 0 && Z2 < B.nz) {
-          const unsigned kcen = key + (unsigned)(dy * B.nx) + (unsigned)(dz * B.nx * B.ny);
-          S.kc[lane] = kcen;
-          for (int dx = -1; dx <= 1; ++dx) {
-            if (X + dx < 0 || X + dx >= B.nx) continue;
-            const unsigned a = V.cstart[kcen + dx], z = V.cend[kcen + dx];
-            if (z > a) { jb = min(jb, a); je = max(je, z); }
-          }
-        }
-        if (je > 0) { S.rb[lane] = (int)jb; len = (int)(je - jb); }
-      }
-      int incl = len;
-#pragma unroll
-      for (int o = 1; o < 16; o <<= 1) {
-        const int t = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += t;
-      }
-      if (lane < 9) S.pre[lane] = incl - len;
-      const int C = __shfl_sync(FULL, incl, 8);
-      if (lane == 9) S.pre[9] = C;
-      __syncwarp();
-      const float reach_own = ow_r * 1.0001f + pm + 1e-9f;
-      int nb = 0;
-      for (int t0 = 0; t0 < C; t0 += 32) {
-        const int t = t0 + lane;
-        bool rel = false;
-        float4 cpos = make_float4(0.f, 0.f, 0.f, 0.f);
-        int j = 0;
-        unsigned char code = 0;
-        if (t < C) {
-          int r = 0;
-#pragma unroll
-          for (int q = 1; q < 9; ++q) r += (t >= S.pre[q]) ? 1 : 0;
-          j = S.rb[r] + (t - S.pre[r]);
-          const float4 o = __ldg(V.xl + j);
-          const int dz = r / 3 - 1, dy = r % 3 - 1;
-          const int dx = (int)(V.keys[j] - S.kc[r]);
-          cpos = make_float4(o.x + dx * hx, o.y + dy * hy, o.z + dz * hz, o.w);
-          code = (unsigned char)((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
-          // distance from the candidate to the own cell's box
-          const float gx = fmaxf(fmaxf(-cpos.x, cpos.x - hx), 0.f);
-          const float gy = fmaxf(fmaxf(-cpos.y, cpos.y - hy), 0.f);
-          const float gz = fmaxf(fmaxf(-cpos.z, cpos.z - hz), 0.f);
-          const float rr = o.w * 1.0001f + reach_own;
-          rel = gx * gx + gy * gy + gz * gz < rr * rr;
-        }
-        const unsigned m = __ballot_sync(FULL, rel);
-        if (rel) {
-          const int p = nb + __popc(m & lt);
-          S.cbuf[p] = cpos;
-          S.cj[p] = j;
-          S.cc[p] = code;
-        }
-        nb += __popc(m);
-        __syncwarp();
-        const bool last = t0 + 32 >= C;
-        while (nb >= 32 || (last && nb > 0)) {
-          const int mcnt = min(nb, 32);
-          const bool has = lane < mcnt;
-          const float4 c = S.cbuf[lane];
-          const int cjl = S.cj[lane];
-          const unsigned char ccl = S.cc[lane];
-          for (int q = 0; q < nq; ++q) {
-            const float4 ow = S.own[q];
-            const float ex = c.x - ow.x, ey = c.y - ow.y, ez = c.z - ow.z;
-            const float d2 = ex * ex + ey * ey + ez * ez;
-            const float rs = c.w + ow.w;
-            const float lim = P::exact ? rs + pm : rs;
-            const bool hit = has && d2 < lim * lim && cjl != g0 + q;
-            const unsigned hb = __ballot_sync(FULL, hit);
-            if (hb) {
-              const int base = S.nh[q];
-              if (hit) {
-                const int p = base + __popc(hb & lt);
-                if (p < KLIST) { S.list[q][p] = cjl; S.code[q][p] = ccl; }
-              }
-              __syncwarp();
-              if (lane == 0) S.nh[q] = base + __popc(hb);
-              __syncwarp();
-            }
-          }
-          // move the rest of the buffer to its front
-          __syncwarp();
-          if (nb > 32 && lane < nb - 32) {
-            const float4 c2 = S.cbuf[32 + lane];
-            const int j2 = S.cj[32 + lane];
-            const unsigned char k2 = S.cc[32 + lane];
-            // source [32, nb) and target [0, nb - 32) do not overlap
-            S.cbuf[lane] = c2; S.cj[lane] = j2; S.cc[lane] = k2;
-          }
-          nb -= mcnt;
-          __syncwarp();
-        }
-      }
-      // ---- phase B: evaluate the hits, flattened over the lanes ----
-      int nhq = lane < nq ? S.nh[lane] : 0;
-      if (nhq > KLIST) { set_error(V.err, ERR_CAPACITY); nhq = KLIST; }
-      int hin = nhq;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(FULL, hin, o);
-        if (lane >= o) hin += t;
-      }
-      S.hex[lane] = hin - nhq;
-      const int Htot = __shfl_sync(FULL, hin, 31);
-      if (lane == 0) S.hex[32] = Htot;
-      __syncwarp();
-      // own parcel of this lane (consumer)
-      const int p = g0 + lane;
-      R Fi[3] = {0, 0, 0}, Ti[3] = {0, 0, 0};
-      int cout = 0;
-      for (int e0 = 0; e0 < Htot; e0 += 32) {
-        const int ee = e0 + lane;
-        if (ee < Htot) {
-          int q = 0;
-          while (S.hex[q + 1] <= ee) ++q;
-          const int k = ee - S.hex[q];
-          const int j = S.list[q][k];
-          const int code = S.code[q][k];
-          const int ip = g0 + q;   // own parcel of the pair
-          const R di = V.B.d[ip];
-          const R mi = V.mass[ip];
-          const R vi[3] = {V.B.v[0][ip], V.B.v[1][ip], V.B.v[2][ip]};
-          const R wi[3] = {V.B.w[0][ip], V.B.w[1][ip], V.B.w[2][ip]};
-          const float4 me = S.own[q];
-          R nrm[3], delta;
-          bool ok = true;
-          R ri, rj;
-          if constexpr (P::exact) {
-            const double xi_d = V.B.x[ip], yi_d = V.B.y[ip], zi_d = V.B.z[ip];
-            const double ri_d = __dmul_rn(0.5, __dmul_rn(B.k, (double)di));
-            const double dxd = V.B.x[j] - xi_d, dyd = V.B.y[j] - yi_d, dzd = V.B.z[j] - zi_d;
-            const double rj_d = __dmul_rn(0.5, __dmul_rn(B.k, (double)V.B.d[j]));
-            const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dxd, dxd), __dmul_rn(dyd, dyd)), __dmul_rn(dzd, dzd));
-            const double rs = __dadd_rn(ri_d, rj_d);
-            ok = d2 < __dmul_rn(rs, rs);
-            const double dd = sqrt(d2);
-            nrm[0] = (R)(dxd / dd); nrm[1] = (R)(dyd / dd); nrm[2] = (R)(dzd / dd);
-            delta = (R)(rs - dd);
-            ri = (R)ri_d; rj = (R)rj_d;
-          } else {
-            const int cdx = code % 3 - 1, cdy = (code / 3) % 3 - 1, cdz = code / 9 - 1;
-            const float4 o = __ldg(V.xl + j);
-            const float ex = o.x + (cdx * hx - me.x), ey = o.y + (cdy * hy - me.y), ez = o.z + (cdz * hz - me.z);
-            const float d2f = ex * ex + ey * ey + ez * ez;
-            const float rsf = me.w + o.w;
-            const float df = sqrtf(d2f);
-            const float inv = 1.0f / df;
-            nrm[0] = (R)(ex * inv); nrm[1] = (R)(ey * inv); nrm[2] = (R)(ez * inv);
-            delta = (R)((rsf * rsf - d2f) / (rsf + df));
-            ri = (R)me.w; rj = (R)o.w;
-          }
-          const int pid = V.B.orig[j];
-          R Fc[3] = {0, 0, 0}, Tc[3] = {0, 0, 0}, xn[3] = {0, 0, 0};
-          if (ok) {
-            const R mj = V.mass[j];
-            const R mstar = mi * mj / (mi + mj);
-            const R ws[3] = {ri * wi[0] + rj * V.B.w[0][j], ri * wi[1] + rj * V.B.w[1][j], ri * wi[2] + rj * V.B.w[2][j]};
-            R vrel[3];
-            vrel[0] = (vi[0] - V.B.v[0][j]) + (ws[1] * nrm[2] - ws[2] * nrm[1]);
-            vrel[1] = (vi[1] - V.B.v[1][j]) + (ws[2] * nrm[0] - ws[0] * nrm[2]);
-            vrel[2] = (vi[2] - V.B.v[2][j]) + (ws[0] * nrm[1] - ws[1] * nrm[0]);
-            R xo[3] = {0, 0, 0};
-            const int cin = V.Hn.cnt[ip];
-            for (int sl = 0; sl < cin; ++sl)
-              if (V.Hn.id[(size_t)sl * V.cap + ip] == pid) {
-#pragma unroll
-                for (int qq = 0; qq < 3; ++qq) xo[qq] = V.Hn.xi[(size_t)(sl * 3 + qq) * V.cap + ip];
-                break;
-              }
-            contact_force<R>(bp, mstar, ri, nrm, delta, vrel, xo, wi, Fc, Tc, xn);
-          }
-#pragma unroll
-          for (int qq = 0; qq < 3; ++qq) {
-            S.res[qq][lane] = Fc[qq];
-            S.res[3 + qq][lane] = Tc[qq];
-            S.res[6 + qq][lane] = xn[qq];
-          }
-          S.res[9][lane] = ok ? (R)1 : (R)0;
-          S.rid[lane] = pid;
-        }
-        __syncwarp();
-        if (lane < nq) {
-          const int a0 = max(S.hex[lane], e0), a1 = min(S.hex[lane + 1], e0 + 32);
-          for (int a = a0; a < a1; ++a) {
-            const int slot = a - e0;
-            if (S.res[9][slot] == (R)0) continue;
-#pragma unroll
-            for (int qq = 0; qq < 3; ++qq) { Fi[qq] += S.res[qq][slot]; Ti[qq] += S.res[3 + qq][slot]; }
-            if (cout < KMAX) {
-              V.H.id[(size_t)cout * V.cap + p] = S.rid[slot];
-#pragma unroll
-              for (int qq = 0; qq < 3; ++qq) V.H.xi[(size_t)(cout * 3 + qq) * V.cap + p] = S.res[6 + qq][slot];
-              ++cout;
-            } else {
-              set_error(V.err, ERR_CAPACITY);
-            }
-          }
-        }
-        __syncwarp();
-      }
-      // walls and outputs, one lane per own parcel
-      if (lane < nq) {
-        const int cin = V.Hn.cnt[p];
-        if (!no_contacts) {
-          const float4 me = S.own[lane];
-          const R di = V.B.d[p];
-          const R mi = V.mass[p];
-          const R vi[3] = {V.B.v[0][p], V.B.v[1][p], V.B.v[2][p]};
-          const R wi[3] = {V.B.w[0][p], V.B.w[1][p], V.B.w[2][p]};
-          const double rid = __dmul_rn(0.5, __dmul_rn(B.k, (double)di));
-          const R ri = P::exact ? (R)rid : (R)me.w;
-          const float xa = (float)bp.x0 + X * hx + me.x, ya = (float)bp.y0 + Y * hy + me.y, za = (float)bp.z0 + Z * hz + me.z;
-          float distf[4], nwf[4][3];
-          wall_primitives<float>(bp, xa, ya, za, distf, nwf);
-          bool near = false;
-#pragma unroll
-          for (int pp = 0; pp < 4; ++pp) near |= distf[pp] < me.w + 1e-6f;
-          if (near) {
-            const double xd = pos_abs<P>(V.B.x, p, B.x0), yd = pos_abs<P>(V.B.y, p, B.y0), zd = pos_abs<P>(V.B.z, p, B.z0);
-            double dist[4], nw[4][3];
-            wall_primitives<double>(B, xd, yd, zd, dist, nw);
-            for (int pp = 0; pp < 4; ++pp) {
-              const double gap = rid - dist[pp];
-              if (!(gap > 0.0)) continue;
-              const R nrm[3] = {(R)-nw[pp][0], (R)-nw[pp][1], (R)-nw[pp][2]};
-              const R delta = (R)gap;
-              const R wr[3] = {ri * wi[0], ri * wi[1], ri * wi[2]};
-              R vrel[3];
-              vrel[0] = vi[0] + (wr[1] * nrm[2] - wr[2] * nrm[1]);
-              vrel[1] = vi[1] + (wr[2] * nrm[0] - wr[0] * nrm[2]);
-              vrel[2] = vi[2] + (wr[0] * nrm[1] - wr[1] * nrm[0]);
-              add_contact<P>(V, p, cin, -1 - pp, bp, mi, ri, nrm, delta, vrel, wi, Fi, Ti, cout);
-            }
-          }
-        }
-        V.H.cnt[p] = (unsigned char)cout;
-#pragma unroll
-        for (int qq = 0; qq < 3; ++qq) { V.F[qq][p] = Fi[qq]; V.Tq[qq][p] = Ti[qq]; }
-        if (V.diag) V.diag[(size_t)DG_NCONTACT * V.cap + p] = (double)cout;
-      }
-      __syncwarp();
-    }
-  }
-}
 
 // ---------------------------------------------------------------------------------------
 // Gas-particle terms, kinetics, second half kick, temperature and mass update; writes the
@@ -936,11 +657,11 @@ __global__ void k_gas_particle(StepView<P> V) {
   using R = typename P::R;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V.n) return;
-  const int meta = V.B.meta[i];
+  const int meta = V.A.meta[i];
   const int ore = meta & 255;
   const BedP<R> &bp = V.bp[meta >> 8];
   const unsigned fl = bp.flags;
-  const unsigned c = V.keys[i];
+  const unsigned c = V.keyp[i];
   const size_t nc = (size_t)V.ncells;
   Gas<R> g;
   g.rho = V.gp[GP_RHO * nc + c]; g.mu = V.gp[GP_MU * nc + c]; g.lam = V.gp[GP_LAM * nc + c];
@@ -948,11 +669,11 @@ __global__ void k_gas_particle(StepView<P> V) {
   g.sc13 = V.gp[GP_SC13 * nc + c]; g.pr13 = V.gp[GP_PR13 * nc + c]; g.epow = V.gp[GP_EPOW * nc + c];
   g.D = V.gp[(ore ? GP_D1 : GP_D0) * nc + c]; g.uz = V.gp[GP_UZ * nc + c];
   g.eps = V.gp[GP_EPS * nc + c]; g.T = V.gp[GP_TG * nc + c];
-  const R d = V.B.d[i];
+  const R d = V.A.d[i];
   const R dc = bp.k * d;
   const R Vp = (R)(kPI / 6.0) * dc * dc * dc;
   const R r = (R)0.5 * dc;
-  const R vh[3] = {V.B.v[0][i], V.B.v[1][i], V.B.v[2][i]};
+  const R vh[3] = {V.A.v[0][i], V.A.v[1][i], V.A.v[2][i]};
   const R sv[3] = {-vh[0], -vh[1], g.uz - vh[2]};
   const R slip = sqrt(sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]);
   const R Re = fdiv<R>(g.rho * g.eps * d * slip, g.mu);
@@ -963,16 +684,18 @@ __global__ void k_gas_particle(StepView<P> V) {
   const R Fd[3] = {Kp * sv[0], Kp * sv[1], Kp * sv[2]};
   const R Nu = gunn(g.eps, re02, re07, g.pr13);
   const R hA = (fl & DEM_NO_HEAT) ? (R)0 : fdiv<R>(bp.k3 * Nu * g.lam, d) * ((R)kPI * d * d);
-  const R Tp = V.B.T[i];
+  const R Tp = V.A.T[i];
   const R Qconv = hA * (g.T - Tp);
   R m[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) m[q] = mass_r<P>(V.B.m[q], i);
+  for (int q = 0; q < 4; ++q) m[q] = mass_r<P>(V.A.m[q], i);
   const bool cpl = coupled_step(bp.ncouple, V.step_ctr);
   const R dtm = bp.dtg;
   KinOut<R> kn;
   uscm<R>(bp, m, Tp, d, ore, g, re02, re07, dtm, kn);
-  const R mp = V.mass[i];
+  R mp = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) mp += m[q];   // the same sum as parcel_mass
   const R I = (R)0.4 * mp * r * r;
   const R F[3] = {V.F[0][i], V.F[1][i], V.F[2][i]};
   const R Tq[3] = {V.Tq[0][i], V.Tq[1][i], V.Tq[2][i]};
@@ -983,10 +706,10 @@ __global__ void k_gas_particle(StepView<P> V) {
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     const R al = fdiv<R>(Tq[q], I);
-    V.B.v[q][i] = vh[q] + a[q] * bp.half_dt;
-    V.B.w[q][i] = V.B.w[q][i] + al * bp.half_dt;
-    V.B.a[q][i] = a[q];
-    V.B.al[q][i] = al;
+    V.A.v[q][i] = vh[q] + a[q] * bp.half_dt;
+    V.A.w[q][i] = V.A.w[q][i] + al * bp.half_dt;
+    V.A.a[q][i] = a[q];
+    V.A.al[q][i] = al;
   }
   const Tab<R> &t = tab<R>();
   R cpp = 0;
@@ -994,12 +717,12 @@ __global__ void k_gas_particle(StepView<P> V) {
 #pragma unroll
   for (int q = 0; q < 4; ++q) cpp += m[q] * inv_mp * cp_over_R<R>(3 + q, Tp) * t.RMz[q];
   const R Tn = Tp + fdiv<R>(bp.dt * (Qconv + kn.Qr + kn.Qrm), mp * cpp);
-  V.B.T[i] = Tn;
+  V.A.T[i] = Tn;
   if (cpl) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) mass_add<P>(V.B.m[q], i, kn.mdot[q] * dtm);
+    for (int q = 0; q < 4; ++q) mass_add<P>(V.A.m[q], i, kn.mdot[q] * dtm);
   }
-  if (!isfinite(Tn) || !isfinite(V.B.v[0][i] + V.B.v[1][i] + V.B.v[2][i])) set_error(V.err, ERR_NONFINITE);
+  if (!isfinite(Tn) || !isfinite(V.A.v[0][i] + V.A.v[1][i] + V.A.v[2][i])) set_error(V.err, ERR_NONFINITE);
   // contributions to the cell sums
   const size_t cp = (size_t)V.cap;
   R *s = V.src;
@@ -1062,12 +785,13 @@ __device__ __forceinline__ void store_props(StepView<P> &V, long long c, const C
 template <class P> struct CellSum {
   using S = typename P::R;
   S s[SR_N];
-  __device__ __forceinline__ void run(const S *src, size_t cp, unsigned jb, unsigned je) {
+  __device__ __forceinline__ void run(const S *src, size_t cp, const unsigned *vals, unsigned jb, unsigned je) {
     if constexpr (!P::exact) {
       float cc[SR_N];
 #pragma unroll
       for (int f = 0; f < SR_N; ++f) { s[f] = 0.f; cc[f] = 0.f; }
-      for (unsigned j = jb; j < je; ++j) {
+      for (unsigned jj = jb; jj < je; ++jj) {
+        const unsigned j = vals[jj];
 #pragma unroll
         for (int f = 0; f < SR_N; ++f) {
           const float y = src[f * cp + j] - cc[f];
@@ -1081,7 +805,8 @@ template <class P> struct CellSum {
     } else {
 #pragma unroll
       for (int f = 0; f < SR_N; ++f) s[f] = 0.0;
-      for (unsigned j = jb; j < je; ++j) {
+      for (unsigned jj = jb; jj < je; ++jj) {
+        const unsigned j = vals[jj];
 #pragma unroll
         for (int f = 0; f < SR_N; ++f) s[f] += src[f * cp + j];
       }
@@ -1110,11 +835,11 @@ __global__ void k_cells(StepView<P> V, int mode /* 0 step, 1 eps init, 2 props o
     double T = G[GS_T * nc + c];
     if (mode == 1) {
       double vs = 0.0;
-      for (unsigned j = V.cstart[c]; j < V.cend[c]; ++j) vs += (double)V.src[SR_VS * cp + j];
+      for (unsigned j = V.cstart[c]; j < V.cend[c]; ++j) vs += (double)V.src[SR_VS * cp + V.vals[j]];
       eps = solid ? B.eps_min : fmax(1.0 - vs / B.vcell, B.eps_min);
     } else if (update) {
       CellSum<P> S;
-      S.run(V.src, cp, V.cstart[c], V.cend[c]);
+      S.run(V.src, cp, V.vals, V.cstart[c], V.cend[c]);
       const bool up = c - B.cell_off >= layer && !V.mark[c - layer];
       const double dtg = B.ncouple * B.dt;
       const double rho = (double)V.gp[GP_RHO * nc + c], cpg = (double)V.gp[GP_CP * nc + c];
@@ -1161,7 +886,7 @@ __global__ void k_cells(StepView<P> V, int mode /* 0 step, 1 eps init, 2 props o
     if (mode == 1) {
       float vs = 0.f, cc = 0.f;
       for (unsigned j = V.cstart[c]; j < V.cend[c]; ++j) {
-        const float y = V.src[SR_VS * cp + j] - cc, t = vs + y;
+        const float y = V.src[SR_VS * cp + V.vals[j]] - cc, t = vs + y;
         cc = (t - vs) - y;
         vs = t;
       }
@@ -1169,7 +894,7 @@ __global__ void k_cells(StepView<P> V, int mode /* 0 step, 1 eps init, 2 props o
       eps2 = make_float2(solid ? bp.eps_min : (e > bp.eps_min ? e : bp.eps_min), 0.f);
     } else if (update) {
       CellSum<P> S;
-      S.run(V.src, cp, V.cstart[c], V.cend[c]);
+      S.run(V.src, cp, V.vals, V.cstart[c], V.cend[c]);
       const bool up = c - B.cell_off >= layer && !V.mark[c - layer];
       const Tab<R> &t = tab<R>();
       const R dtg = bp.dtg;
@@ -1225,7 +950,7 @@ __global__ void k_sources(StepView<P> V) {
   if (c >= V.ncells) return;
   const size_t cp = (size_t)V.cap;
   CellSum<P> S;
-  S.run(V.src, cp, V.cstart[c], V.cend[c]);
+  S.run(V.src, cp, V.vals, V.cstart[c], V.cend[c]);
   const bool solid = V.mark[c] != 0;
   for (int f = 0; f < SR_N; ++f) V.dep[(size_t)c * SR_N + f] = solid ? 0.0 : (double)S.s[f];
 }
@@ -1236,8 +961,8 @@ __global__ void k_volume(StepView<P> V) {
   using R = typename P::R;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V.n) return;
-  const BedP<R> &bp = V.bp[V.B.meta[i] >> 8];
-  const R dc = bp.k * V.B.d[i];
+  const BedP<R> &bp = V.bp[V.A.meta[i] >> 8];
+  const R dc = bp.k * V.A.d[i];
   V.src[SR_VS * (size_t)V.cap + i] = (R)(kPI / 6.0) * dc * dc * dc;
 }
 

@@ -1,5 +1,5 @@
 // launch.cuh -- host-side orchestration of the per-step kernels for one arithmetic type.
-// Included by inst_f64.cu and inst_f32.cu, which instantiate it for double and float.
+// Included by inst_f64.cu, inst_f32.cu and inst_kahan.cu, which instantiate it per precision form.
 #pragma once
 #include "ctx.cuh"
 #include "radix.cuh"
@@ -18,6 +18,7 @@ StepView<P> make_view(dem_ctx *c, bool for_step) {
   V.ncells = c->ncells;
   V.beds = c->dbeds;
   if constexpr (sizeof(R) == 8) V.bp = c->dbp_d; else V.bp = c->dbp_f;
+  // a: buffers of the state before the step (the current ones between steps), b: after it
   const int a = c->cur, b = for_step ? 1 - c->cur : c->cur;
   auto fill = [&](PState<R> &Pp, int k) {
     Pp.x = c->px[k][0]; Pp.y = c->px[k][1]; Pp.z = c->px[k][2];
@@ -30,28 +31,33 @@ StepView<P> make_view(dem_ctx *c, bool for_step) {
     for (int q = 0; q < 4; ++q) Pp.m[q] = c->pm[k][q];
     Pp.meta = c->pmeta[k];
     Pp.orig = c->porig[k];
-    Pp.bidx = c->pbidx[k];
     for (int q = 0; q < 3; ++q) Pp.dsp[q] = c->pdsp[k][q];
   };
-  fill(V.A, a);
-  fill(V.B, b);
-  V.H.cnt = c->hcnt[0]; V.H.id = c->hid[0]; V.H.xi = (R *)c->hxi[0];
-  V.Hn.cnt = c->hcnt[1]; V.Hn.id = c->hid[1]; V.Hn.xi = (R *)c->hxi[1];
+  fill(V.A, 0);   // the state, always in buffer 0
+  fill(V.S, 1);   // scratch of a re-store
+  V.H.cnt = c->hcnt[a]; V.H.id = c->hid[a]; V.H.xi = (R *)c->hxi[a];
+  V.Hn.cnt = c->hcnt[b]; V.Hn.id = c->hid[b]; V.Hn.xi = (R *)c->hxi[b];
+  V.Hs = V.Hn;    // the re-store runs before the contacts write the new history
+  V.keyp = c->keys;
   V.keys = c->skey[b];
   V.vals = c->sval[b];
+  V.keys_prev = c->skey[a];
+  V.vals_prev = c->sval[a];
+  V.knew = c->keys2;
+  V.vrel = c->vals2;
   V.cstart = c->cstart; V.cend = c->cend;
   V.xl = c->xl;
+  V.xls = reinterpret_cast<float4 *>(c->src);
   V.plist = c->plist;
   V.pcode = c->pcode;
   V.pcnt = c->pcnt;
   V.nl = c->nl;
   V.nlc = c->nlc;
-  V.cur = c->curpos;
   V.rebuild = c->rebuild;
+  V.nolists = c->use_lists ? 0 : 1;
   V.corner = c->corner;
   V.cornerp = c->cornerp;
-  V.kprev = c->skey[a];
-  V.mass = (R *)c->mass;
+  V.moved = resort_counts(c->rsw, c->rs_pow2, c->n);
   for (int q = 0; q < 3; ++q) { V.F[q] = (R *)c->F[q]; V.Tq[q] = (R *)c->Tq[q]; }
   V.src = (R *)c->src;
   V.gas = c->gas[c->gcur];
@@ -67,48 +73,69 @@ StepView<P> make_view(dem_ctx *c, bool for_step) {
   return V;
 }
 
-// binning: keys of the (drifted) positions, radix sort, gather into the sorted order
+// storage positions 0..n-1 (the radix sort's values at the first binning)
+static __global__ void k_iota(unsigned *v, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = (unsigned)i;
+}
+
+// sorted-position range of every occupied cell (first binning)
+template <class P>
+__global__ void k_ranges(StepView<P> V) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V.n) return;
+  const unsigned k = V.keys[i];
+  if (i == 0 || V.keys[i - 1] != k) V.cstart[k] = (unsigned)i;
+  if (i == V.n - 1 || V.keys[i + 1] != k) V.cend[k] = (unsigned)(i + 1);
+}
+
+// Binning: drift and keys in storage order, then the sorted order of the keys (incremental
+// re-sort from the previous step's; LSD radix sort at the first binning), the cell ranges,
+// and on list-build steps a re-store of the parcels in that order.
 template <class P>
 int enqueue_binning(dem_ctx *c, int drift) {
   cudaStream_t st = c->st;
   StepView<P> V = make_view<P>(c, true);
-  V.keys = c->keys;
-  V.vals = c->vals;
-  V.moved = resort_counts(c->rsw, c->rs_pow2, c->n);
-  if (drift) cudaMemsetAsync(V.moved, 0, sizeof(int) * (size_t)((c->n + 1023) / 1024 + 1), st);
   int ps = prof_begin(c, "k_key");
   k_key<P><<<grid_for(c->n, c->bs_key), c->bs_key, 0, st>>>(V, drift);
   prof_end(c, ps);
   ++c->launches;
   const int nxt = 1 - c->cur;
   if (drift) {
-    // few keys change per step: re-sort incrementally from the previous sorted order
     ps = prof_begin(c, "resort");
-    int e = resort_pairs(c->skey[c->cur], c->keys, c->skey[nxt], c->sval[nxt], c->rsw, c->rs_pow2, c->n, st,
+    k_sorted_keys<P><<<grid_for(c->n, 1024), 1024, 0, st>>>(V);
+    int e = resort_pairs(c->skey[c->cur], c->keys2, c->skey[nxt], c->vals2, c->rsw, c->rs_pow2, c->n, st,
                          &c->launches);
-    prof_end(c, ps);
     if (e) return e;
+    cudaMemsetAsync(c->cstart, 0, sizeof(unsigned) * c->ncells, st);
+    cudaMemsetAsync(c->cend, 0, sizeof(unsigned) * c->ncells, st);
+    k_compose<P><<<grid_for(c->n, c->bs_gather), c->bs_gather, 0, st>>>(V);
+    prof_end(c, ps);
+    c->launches += 2;
   } else {
-    // first binning: full LSD radix sort of (key, index)
-    unsigned *kr = nullptr, *vr = nullptr;
+    // first binning: LSD radix sort of (key, storage position)
     ps = prof_begin(c, "radix_sort");
-    int e = radix_sort_pairs(c->keys, c->vals, c->keys2, c->vals2, c->rhist, c->n, c->key_bits, st,
+    cudaMemcpyAsync(c->keys2, c->keys, sizeof(unsigned) * c->n, cudaMemcpyDeviceToDevice, st);
+    k_iota<<<grid_for(c->n, 256), 256, 0, st>>>(c->vals2, c->n);
+    unsigned *kr = nullptr, *vr = nullptr;
+    int e = radix_sort_pairs(c->keys2, c->vals2, c->skey[nxt], c->sval[nxt], c->rhist, c->n, c->key_bits, st,
                              &kr, &vr, &c->launches);
-    prof_end(c, ps);
     if (e) return e;
-    c->kres = kr;
-    c->vres = vr;
-    cudaMemcpyAsync(c->skey[nxt], kr, sizeof(unsigned) * c->n, cudaMemcpyDeviceToDevice, st);
-    cudaMemcpyAsync(c->sval[nxt], vr, sizeof(unsigned) * c->n, cudaMemcpyDeviceToDevice, st);
+    if (kr != c->skey[nxt]) {
+      cudaMemcpyAsync(c->skey[nxt], kr, sizeof(unsigned) * c->n, cudaMemcpyDeviceToDevice, st);
+      cudaMemcpyAsync(c->sval[nxt], vr, sizeof(unsigned) * c->n, cudaMemcpyDeviceToDevice, st);
+    }
+    cudaMemsetAsync(c->cstart, 0, sizeof(unsigned) * c->ncells, st);
+    cudaMemsetAsync(c->cend, 0, sizeof(unsigned) * c->ncells, st);
+    k_ranges<P><<<grid_for(c->n, 256), 256, 0, st>>>(V);
+    prof_end(c, ps);
+    c->launches += 2;
   }
-  V.keys = c->skey[nxt];
-  V.vals = c->sval[nxt];
-  cudaMemsetAsync(c->cstart, 0, sizeof(unsigned) * c->ncells, st);
-  cudaMemsetAsync(c->cend, 0, sizeof(unsigned) * c->ncells, st);
-  ps = prof_begin(c, "k_gather");
-  k_gather<P><<<grid_for(c->n, c->bs_gather), c->bs_gather, 0, st>>>(V, drift);
+  ps = prof_begin(c, "k_restore");
+  k_restore_out<P><<<grid_for(c->n, c->bs_gather), c->bs_gather, 0, st>>>(V, drift ? 0 : 1);
+  k_restore_in<P><<<grid_for(c->n, c->bs_gather), c->bs_gather, 0, st>>>(V, drift ? 0 : 1);
   prof_end(c, ps);
-  ++c->launches;
+  c->launches += 2;
   return (int)cudaPeekAtLastError();
 }
 
@@ -120,30 +147,26 @@ int enqueue_steps(dem_ctx *c, int nsteps) {
     if (e) return e;
     StepView<P> V = make_view<P>(c, true);
     int ps;
-    if (c->contact_mode == 1) {
-      ps = prof_begin(c, "k_contacts_cell");
-      k_contacts_cell<P><<<grid_for(c->n, CW_WARPS * 32), CW_WARPS * 32, 0, st>>>(V);
-      prof_end(c, ps);
-    } else {
+    if (c->use_lists) {
       ps = prof_begin(c, "k_pair_list");
       k_pair_list<P><<<grid_for(c->n, c->bs_search), c->bs_search, 0, st>>>(V);
       prof_end(c, ps);
-      ps = prof_begin(c, "k_pair_search");
-      k_pair_search<P><<<grid_for(c->n, c->bs_search), c->bs_search, 0, st>>>(V);
-      prof_end(c, ps);
-      ps = prof_begin(c, "k_pair_forces");
-      k_pair_forces<P><<<grid_for(c->n, c->bs_contacts), c->bs_contacts, 0, st>>>(V);
-      prof_end(c, ps);
-      c->launches += 2;
+      ++c->launches;
     }
+    ps = prof_begin(c, "k_pair_search");
+    k_pair_search<P><<<grid_for(c->n, c->bs_search), c->bs_search, 0, st>>>(V);
+    prof_end(c, ps);
+    ps = prof_begin(c, "k_pair_forces");
+    k_pair_forces<P><<<grid_for(c->n, c->bs_contacts), c->bs_contacts, 0, st>>>(V);
+    prof_end(c, ps);
     ps = prof_begin(c, "k_gas_particle");
     k_gas_particle<P><<<grid_for(c->n, c->bs_gp), c->bs_gp, 0, st>>>(V);
     prof_end(c, ps);
     ps = prof_begin(c, "k_cells");
     k_cells<P><<<grid_for(c->ncells, c->bs_cells), c->bs_cells, 0, st>>>(V, 0);
     prof_end(c, ps);
-    k_step_counter<<<1, 1, 0, st>>>(c->step_ctr, c->rebuild, c->contact_mode == 0);
-    c->launches += 4;
+    k_step_counter<<<1, 1, 0, st>>>(c->step_ctr, c->rebuild, c->use_lists);
+    c->launches += 5;
     e = (int)cudaPeekAtLastError();
     if (e) return e;
     c->cur = 1 - c->cur;
@@ -216,7 +239,7 @@ int enqueue_props(dem_ctx *c) {
 // largest block each tunable kernel can launch with (registers per thread decide it)
 template <class P>
 int kernel_limits(int *lim) {
-  const void *fn[6] = {(const void *)k_key<P>, (const void *)k_gather<P>, (const void *)k_pair_search<P>,
+  const void *fn[6] = {(const void *)k_key<P>, (const void *)k_restore_out<P>, (const void *)k_pair_search<P>,
                        (const void *)k_pair_forces<P>, (const void *)k_gas_particle<P>, (const void *)k_cells<P>};
   for (int k = 0; k < 6; ++k) {
     cudaFuncAttributes a;

@@ -1,5 +1,5 @@
-"""Launch configurations of the step -- contact kernel (per-parcel neighbour lists or one
-warp per cell), block sizes, neighbour-list skin -- and the autotuner. Each configuration
+"""Launch configurations of the step -- neighbour lists or the cell-list search every step,
+block sizes, neighbour-list skin -- and the autotuner. Each configuration
 computes the same step, so each is held to the FP64 oracle: pair sets bit-exact, states to
 relative 1e-7 over several list rebuilds."""
 import numpy as np
@@ -30,11 +30,11 @@ def _pairs(cnt, partner):
     return {(i, int(partner[i, k])) for i in range(len(cnt)) for k in range(cnt[i])}
 
 
-@pytest.mark.parametrize("kernel,skin,bs", [(0, 100, 128), (0, 5, 64), (0, 600, 384), (1, 100, 256)])
-def test_contact_configurations_match_oracle(kernel, skin, bs):
+@pytest.mark.parametrize("lists,skin,bs", [(1, 100, 128), (1, 5, 64), (1, 600, 384), (0, 100, 256)])
+def test_contact_configurations_match_oracle(lists, skin, bs):
     bed = synth.small_packed(seed=21, n=3000, v_scale=0.3, wall_kind=synth.WALL_CONE)
     ctx = _ctx(bed)
-    ctx.dem_set_tuning(contact_kernel=kernel, skin_permille=skin, bs_key=bs, bs_gather=bs, bs_search=bs,
+    ctx.dem_set_tuning(neighbour_lists=lists, skin_permille=skin, bs_key=bs, bs_restore=bs, bs_search=bs,
                        bs_forces=bs, bs_gas_particle=bs, bs_cells=bs)
     ref = oracle.Oracle(bed)
     for _ in range(4):
@@ -49,12 +49,12 @@ def test_contact_configurations_match_oracle(kernel, skin, bs):
     assert sum(cg) > 100
     steps, builds, entries = ctx.dem_get_counters()
     assert steps == 60
-    if kernel == 0:
+    if lists:
         assert builds >= 1 and entries >= sum(cg)
         if skin == 5:
             assert builds > 5          # a thin skin forces frequent rebuilds
     else:
-        assert builds == 0             # the per-cell kernel searches the cell list every step
+        assert builds == 0             # no lists: the cell list is searched every step
     ctx.close()
 
 
@@ -74,7 +74,7 @@ def test_set_tuning_rejects_invalid_values():
     t0 = ctx.dem_get_tuning()
     assert set(t0) == set(binding.TUNING_KEYS)
     # the FP64 form's gas-particle kernel holds too many registers for 1024-thread blocks
-    for bad in (dict(contact_kernel=2), dict(bs_key=48), dict(bs_cells=2048), dict(bs_search=0),
+    for bad in (dict(neighbour_lists=2), dict(bs_key=48), dict(bs_cells=2048), dict(bs_search=0),
                 dict(skin_permille=0), dict(skin_permille=1001), dict(bs_gas_particle=1024)):
         with pytest.raises(binding.DemError) as e:
             ctx.dem_set_tuning(**bad)
@@ -92,7 +92,7 @@ def test_autotune_restores_the_state_and_keeps_parity():
     s0 = ctx.dem_get_state()
     c0 = ctx.dem_get_counters()
     t = ctx.dem_autotune(8)
-    assert set(t) == set(binding.TUNING_KEYS) and t["contact_kernel"] in (0, 1)
+    assert set(t) == set(binding.TUNING_KEYS) and t["neighbour_lists"] in (0, 1)
     assert np.array_equal(ctx.dem_get_state(), s0)
     assert ctx.dem_get_counters() == c0
     ctx.dem_step(10)
