@@ -76,28 +76,30 @@ def make_workload(name: str, rank: int = 0, parcels: int = 0):
 # live contact slots (z_bar per parcel) and neighbour-list entries (L per parcel) once -- not
 # counting the re-reads of neighbours' records, which the caches serve.
 # ---------------------------------------------------------------------------------------
-def algorithmic_bytes(kernel: str, n: int, ncells: int, zbar: float, L: float, rsize: int, passes: int) -> float:
+def algorithmic_bytes(kernel: str, n: int, ncells: int, zbar: float, L: float, rsize: int, passes: int,
+                      fbuild: float = 0.0) -> float:
+    """Per launch; fbuild = fraction of steps that rebuild the lists (and re-store the state)."""
     R = rsize
     slot = 4 + 3 * R                                  # partner id + tangential displacement
-    state = 24 + 12 * R + 2 * R + 32 + 4 * 3 + 12     # x; v,w,a,al; T,d; masses; meta,orig,bidx; dsp
-    if kernel == "k_key":
-        return n * ((4 + 24 + 6 * R + 12 + 16 + 4 + R) + (24 + 12 + 16 + 8))
+    state = 24 + 12 * R + 2 * R + 32 + 8 + 12         # x; v,w,a,al; T,d; masses; meta,orig; dsp
+    if kernel == "k_key":            # in place: half kicks, drift, displacement, key, local coordinates
+        return n * ((4 + 24 + 12 * R + 12 + 16 + 4 + R) + (24 + 6 * R + 12 + 4 + 16))
     if kernel == "radix_sort":
         return n * passes * (8 + 8)
-    if kernel == "resort":       # new and old keys read, sorted keys and permutation written
-        return n * (4 + 4 + 8)
-    if kernel == "k_gather":
-        return n * ((8 + state + 16 + 1 + zbar * slot) + (state + R + 16 + 4 + 1 + zbar * slot))
-    if kernel == "k_pair_search":
-        return n * ((4 + 16 + 4 + 4 + 1 + 4 * L) + (1 + 5 * zbar))
+    if kernel == "resort":           # new keys in sorted order, re-sort, permutation and cell ranges
+        return n * (16 + 16 + 16)
+    if kernel == "k_restore":        # list-build steps: state, local coordinates, history out and back
+        return fbuild * n * (4 * (state + 16 + 1 + zbar * slot) + 4 + 8)
+    if kernel == "k_pair_list":
+        return (1 - fbuild) * n * ((4 + 16 + 4 + 1 + 4 * L) + (1 + 5 * zbar))
+    if kernel == "k_pair_search":    # list builds (the cell-list search) only
+        return fbuild * n * ((4 + 16 + 4) + (4 * L + 1 + 1 + 12 + 5 * zbar))
     if kernel == "k_pair_forces":
-        return n * ((4 + 1 + 1 + 16 + 4 + 2 * R + 6 * R + 5 * zbar + zbar * slot) + (1 + zbar * slot + 6 * R))
-    if kernel == "k_contacts_cell":
-        return n * ((4 + 16 + 4 + 1 + 2 * R + 6 * R + zbar * slot) + (1 + zbar * slot + 6 * R))
+        return n * ((4 + 16 + 1 + 4 + 1 + zbar * (5 + 2 * (slot + 8 * R + 32))) + (1 + zbar * slot + 6 * R))
     if kernel == "k_gas_particle":
-        return n * ((4 + 4 + R + 3 * R + R + 32 + R + 6 * R + 3 * R) + (12 * R + R + 32 + 14 * R)) + ncells * 13 * R
+        return n * ((4 + 4 + R + 3 * R + R + 32 + 6 * R + 3 * R) + (12 * R + R + 32 + 14 * R)) + ncells * 13 * R
     if kernel == "k_cells":
-        return ncells * ((4 + 1 + 8 + 5 * 8 + 2 * R) + (5 * 8 + 14 * R)) + n * 14 * R
+        return ncells * ((4 + 1 + 8 + 5 * 8 + 2 * R) + (5 * 8 + 14 * R)) + n * (14 * R + 4)
     return 0.0
 
 
@@ -330,6 +332,7 @@ def main():
     ncells = ctx.ncells
     steps_done, builds, entries = ctx.dem_get_counters()
     L = entries / n
+    fbuild = (c_post[1] - c_pre[1]) / max(1, args.steps)
     rsize = 8 if args.precision == "fp64" else 4
     key_bits = max(1, math.ceil(math.log2(max(2, sum(c.nx * c.ny * c.nz for c in bed.beds)))))
     passes = (key_bits + 7) // 8
@@ -337,7 +340,7 @@ def main():
     kernels = {}
     for name, (nl, tot) in times.items():
         avg = tot / max(nl, 1)
-        b = algorithmic_bytes(name, n, ncells, zbar, L, rsize, passes)
+        b = algorithmic_bytes(name, n, ncells, zbar, L, rsize, passes, fbuild)
         kernels[name] = {"launches": nl, "avg_ms": avg, "alg_bytes": b,
                          "gbs": (b / (avg * 1e-3) / 1e9) if avg > 0 and b > 0 else None}
     dom = max(kernels, key=lambda k: kernels[k]["avg_ms"]) if kernels else None

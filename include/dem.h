@@ -208,7 +208,7 @@ int dem_get_diag(dem_ctx *c, double *out_host);
  *       has moved half the skin (default), 0 = the cell-list search every step;
  *   [1]..[6] block sizes of the key, re-store, pair-search, pair-force, gas-particle and
  *       gas-cell kernels (multiples of 32 in [32, 1024], and no larger than the kernel's
- *       register use allows: the FP64 form's larger kernels stop below 512);
+ *       launch bounds and register use allow: the gas-particle kernel stops at 256);
  *   [7] neighbour-list skin in thousandths of the bed's largest parcel diameter (1..1000).
  * dem_set_tuning validates every value (DEM_EINVAL, nothing changed), drops captured graphs
  * and makes the next step rebuild the neighbour lists; results can then differ from an

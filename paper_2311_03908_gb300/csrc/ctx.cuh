@@ -37,7 +37,8 @@ struct dem_ctx {
   // binning
   unsigned *keys = nullptr, *vals = nullptr, *keys2 = nullptr, *vals2 = nullptr, *rhist = nullptr;
   unsigned *kres = nullptr, *vres = nullptr;   // where the last radix sort left its result
-  unsigned *skey[2] = {}, *sval[2] = {};       // sorted keys / permutation of state buffer k
+  unsigned *skey[2] = {}, *sval[2] = {};       // sorted keys / permutation, by step parity
+  unsigned *inv = nullptr;                     // sorted position of each storage position
   unsigned *rsw = nullptr;                     // scratch of the incremental re-sort
   int rs_pow2 = 1;
   unsigned *cstart = nullptr, *cend = nullptr;

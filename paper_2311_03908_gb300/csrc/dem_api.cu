@@ -333,6 +333,7 @@ void layout(dem_ctx *c, Bump &m) {
   c->keys2 = m.take<unsigned>(N); c->vals2 = m.take<unsigned>(N);
   for (int k = 0; k < 2; ++k) { c->skey[k] = m.take<unsigned>(N); c->sval[k] = m.take<unsigned>(N); }
   c->rsw = m.take<unsigned>(resort_words((int)N, &c->rs_pow2));
+  c->inv = m.take<unsigned>(N);
   c->rhist = m.take<unsigned>(radix_hist_words((int)N));
   c->cstart = m.take<unsigned>(C); c->cend = m.take<unsigned>(C);
   c->xl = m.take<float4>(N);

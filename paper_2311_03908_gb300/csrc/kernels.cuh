@@ -44,7 +44,9 @@ template <class P> struct StepView {
   unsigned *keyp;               // gas-cell key of each parcel (storage order)
   unsigned *keys, *vals;        // sorted keys and the storage position at each sorted position
   const unsigned *keys_prev, *vals_prev;   // the same for the previous step
-  unsigned *knew, *vrel;        // re-sort input (new keys in the previous sorted order) and output
+  unsigned *knew;               // re-sort input: new keys in the previous sorted order
+  unsigned *inv;                // sorted position of each storage position (previous sort until
+                                // the ranges kernel of this step rewrites it)
   unsigned *cstart, *cend;      // sorted-position range of every gas cell (empty: 0, 0)
   float4 *xl;                   // FP32 position relative to the own cell's corner, radius
   float4 *xls;                  // scratch of a re-store (aliases the per-parcel sources,
@@ -237,35 +239,27 @@ __global__ void k_key(StepView<P> V, int drift) {
     }
     if (out) set_error(V.err, ERR_DOMAIN);
   }
+  if (drift) {
+    // the re-sort's input: the new key at the parcel's previous sorted position, and the
+    // count of changed keys per 1024 sorted positions
+    const unsigned sp = V.inv[i];
+    V.knew[sp] = key;
+    if (key != V.keyp[i]) atomicAdd(V.moved + (sp >> 10), 1);
+  }
   V.keyp[i] = key;
   V.xl[i] = local_coords<P>(V, B, ix, iy, iz, x, y, z, p2, (float)(bp.k * V.A.d[i]) * 0.5f);
 }
 
-// The new keys in the previous sorted order (the re-sort's input), and how many of them
-// changed in each block of 1024 sorted positions.
+// Sorted-position range of every occupied cell, and the sorted position of every storage
+// position (the next step's key kernel scatters its keys through it).
 template <class P>
-__global__ void __launch_bounds__(1024) k_sorted_keys(StepView<P> V) {
-  const int i = blockIdx.x * 1024 + threadIdx.x;
-  bool moved = false;
-  if (i < V.n) {
-    const unsigned k = V.keyp[V.vals_prev[i]];
-    V.knew[i] = k;
-    moved = k != V.keys_prev[i];
-  }
-  const int c = __syncthreads_count(moved);
-  if (threadIdx.x == 0) V.moved[blockIdx.x] = c;
-}
-
-// Storage position at each new sorted position (the re-sort returns previous sorted
-// positions), and the sorted-position range of every occupied cell.
-template <class P>
-__global__ void k_compose(StepView<P> V) {
+__global__ void k_ranges(StepView<P> V) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V.n) return;
-  V.vals[i] = V.vals_prev[V.vrel[i]];
   const unsigned k = V.keys[i];
   if (i == 0 || V.keys[i - 1] != k) V.cstart[k] = (unsigned)i;
   if (i == V.n - 1 || V.keys[i + 1] != k) V.cend[k] = (unsigned)(i + 1);
+  V.inv[V.vals[i]] = (unsigned)i;
 }
 
 // Re-store (list-build steps, and the first binning): copy every parcel's record, local
@@ -322,6 +316,7 @@ __global__ void k_restore_in(StepView<P> V, int force) {
   V.xl[i] = V.xls[i];
   V.keyp[i] = V.keys[i];
   V.vals[i] = (unsigned)i;
+  V.inv[i] = (unsigned)i;
   const int c = V.Hs.cnt[i];
   V.H.cnt[i] = (unsigned char)c;
   for (int s = 0; s < c; ++s) {
@@ -652,8 +647,10 @@ __global__ void k_pair_forces(StepView<P> V) {
 // Gas-particle terms, kinetics, second half kick, temperature and mass update; writes the
 // parcel's contributions to its cell sums.
 // ---------------------------------------------------------------------------------------
+// The FP32 forms are held to 64 registers (4 blocks of 256 threads per SM): a few spills
+// to L1 cost less than the latency the extra occupancy hides (ncu: 33 % -> 50 % warps).
 template <class P>
-__global__ void k_gas_particle(StepView<P> V) {
+__global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView<P> V) {
   using R = typename P::R;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V.n) return;

@@ -44,7 +44,7 @@ StepView<P> make_view(dem_ctx *c, bool for_step) {
   V.keys_prev = c->skey[a];
   V.vals_prev = c->sval[a];
   V.knew = c->keys2;
-  V.vrel = c->vals2;
+  V.inv = c->inv;
   V.cstart = c->cstart; V.cend = c->cend;
   V.xl = c->xl;
   V.xls = reinterpret_cast<float4 *>(c->src);
@@ -79,16 +79,6 @@ static __global__ void k_iota(unsigned *v, int n) {
   if (i < n) v[i] = (unsigned)i;
 }
 
-// sorted-position range of every occupied cell (first binning)
-template <class P>
-__global__ void k_ranges(StepView<P> V) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= V.n) return;
-  const unsigned k = V.keys[i];
-  if (i == 0 || V.keys[i - 1] != k) V.cstart[k] = (unsigned)i;
-  if (i == V.n - 1 || V.keys[i + 1] != k) V.cend[k] = (unsigned)(i + 1);
-}
-
 // Binning: drift and keys in storage order, then the sorted order of the keys (incremental
 // re-sort from the previous step's; LSD radix sort at the first binning), the cell ranges,
 // and on list-build steps a re-store of the parcels in that order.
@@ -96,6 +86,7 @@ template <class P>
 int enqueue_binning(dem_ctx *c, int drift) {
   cudaStream_t st = c->st;
   StepView<P> V = make_view<P>(c, true);
+  if (drift) cudaMemsetAsync(V.moved, 0, sizeof(int) * (size_t)((c->n + 1023) / 1024 + 1), st);
   int ps = prof_begin(c, "k_key");
   k_key<P><<<grid_for(c->n, c->bs_key), c->bs_key, 0, st>>>(V, drift);
   prof_end(c, ps);
@@ -103,15 +94,14 @@ int enqueue_binning(dem_ctx *c, int drift) {
   const int nxt = 1 - c->cur;
   if (drift) {
     ps = prof_begin(c, "resort");
-    k_sorted_keys<P><<<grid_for(c->n, 1024), 1024, 0, st>>>(V);
-    int e = resort_pairs(c->skey[c->cur], c->keys2, c->skey[nxt], c->vals2, c->rsw, c->rs_pow2, c->n, st,
-                         &c->launches);
+    int e = resort_pairs(c->skey[c->cur], c->keys2, c->sval[c->cur], c->skey[nxt], c->sval[nxt], c->rsw, c->rs_pow2,
+                         c->n, st, &c->launches);
     if (e) return e;
     cudaMemsetAsync(c->cstart, 0, sizeof(unsigned) * c->ncells, st);
     cudaMemsetAsync(c->cend, 0, sizeof(unsigned) * c->ncells, st);
-    k_compose<P><<<grid_for(c->n, c->bs_gather), c->bs_gather, 0, st>>>(V);
+    k_ranges<P><<<grid_for(c->n, c->bs_gather), c->bs_gather, 0, st>>>(V);
     prof_end(c, ps);
-    c->launches += 2;
+    ++c->launches;
   } else {
     // first binning: LSD radix sort of (key, storage position)
     ps = prof_begin(c, "radix_sort");

@@ -142,7 +142,7 @@ __device__ __forceinline__ int count_less(const unsigned long long *c, int lo, i
 constexpr int RZ_MERGE = 256;
 __global__ void __launch_bounds__(RZ_MERGE) rz_merge(const unsigned *kold, const unsigned *knew, int n,
                                                      const int *pre, const unsigned long long *sorted,
-                                                     unsigned *kout, unsigned *vout) {
+                                                     const unsigned *vmap, unsigned *kout, unsigned *vout) {
   __shared__ int bounds[2];
   const int m = pre[n];
   const int g0 = blockIdx.x * RZ_MERGE;
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(RZ_MERGE) rz_merge(const unsigned *kold, const
       for (int t = bounds[0]; t < bounds[1]; ++t) below += sorted[t] < c ? 1 : 0;
       const int pos = g - pre[g] + below;
       kout[pos] = key;
-      vout[pos] = (unsigned)g;
+      vout[pos] = vmap ? vmap[g] : (unsigned)g;
     }
   }
   for (int t = g; t < m; t += gridDim.x * RZ_MERGE) {
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(RZ_MERGE) rz_merge(const unsigned *kold, const
     const int x = idx < lb ? lb : (idx > ub ? ub : idx);
     const int pos = t + (x - pre[x]);
     kout[pos] = key;
-    vout[pos] = (unsigned)idx;
+    vout[pos] = vmap ? vmap[idx] : (unsigned)idx;
   }
 }
 
@@ -198,7 +198,7 @@ int *resort_counts(unsigned *scratch, int pow2, int n) {
   return reinterpret_cast<int *>(scratch + 4 * (size_t)pow2) + n + 1;
 }
 
-int resort_pairs(const unsigned *kold, const unsigned *knew, unsigned *kout, unsigned *vout,
+int resort_pairs(const unsigned *kold, const unsigned *knew, const unsigned *vmap, unsigned *kout, unsigned *vout,
                  unsigned *scratch, int pow2, int n, cudaStream_t st, long long *launches) {
   const int nb = (n + RZ_BLOCK - 1) / RZ_BLOCK;
   unsigned long long *comp = reinterpret_cast<unsigned long long *>(scratch);
@@ -209,7 +209,7 @@ int resort_pairs(const unsigned *kold, const unsigned *knew, unsigned *kout, uns
   rz_compact<<<nb, RZ_BLOCK, 0, st>>>(kold, knew, n, blk, nb, pre, comp);
   rz_rank<<<RZ_SMEM_SORT / 256, 256, 0, st>>>(blk, nb, comp, sorted);
   rz_sort_big<<<1, RZ_BLOCK, 0, st>>>(blk, nb, comp, sorted, pow2);
-  rz_merge<<<(n + RZ_MERGE - 1) / RZ_MERGE, RZ_MERGE, 0, st>>>(kold, knew, n, pre, sorted, kout, vout);
+  rz_merge<<<(n + RZ_MERGE - 1) / RZ_MERGE, RZ_MERGE, 0, st>>>(kold, knew, n, pre, sorted, vmap, kout, vout);
   if (launches) *launches += 5;
   return (int)cudaPeekAtLastError();
 }

@@ -30,7 +30,7 @@ def _pairs(cnt, partner):
     return {(i, int(partner[i, k])) for i in range(len(cnt)) for k in range(cnt[i])}
 
 
-@pytest.mark.parametrize("lists,skin,bs", [(1, 100, 128), (1, 5, 64), (1, 600, 384), (0, 100, 256)])
+@pytest.mark.parametrize("lists,skin,bs", [(1, 100, 128), (1, 5, 64), (1, 600, 256), (0, 100, 256)])
 def test_contact_configurations_match_oracle(lists, skin, bs):
     bed = synth.small_packed(seed=21, n=3000, v_scale=0.3, wall_kind=synth.WALL_CONE)
     ctx = _ctx(bed)
@@ -73,7 +73,7 @@ def test_set_tuning_rejects_invalid_values():
     ctx = _ctx(bed)
     t0 = ctx.dem_get_tuning()
     assert set(t0) == set(binding.TUNING_KEYS)
-    # the FP64 form's gas-particle kernel holds too many registers for 1024-thread blocks
+    # the gas-particle kernel launches at most 256 threads per block (launch bounds)
     for bad in (dict(neighbour_lists=2), dict(bs_key=48), dict(bs_cells=2048), dict(bs_search=0),
                 dict(skin_permille=0), dict(skin_permille=1001), dict(bs_gas_particle=1024)):
         with pytest.raises(binding.DemError) as e:
