@@ -935,7 +935,17 @@ __global__ void k_cells(StepView<P> V, int mode /* 0 step, 1 eps init, 2 props o
     Gn2[GS_Y0 * nc + c] = Y2[0]; Gn2[GS_Y1 * nc + c] = Y2[1]; Gn2[GS_Y2 * nc + c] = Y2[2];
     Gn2[GS_T * nc + c] = T2;
     const R Yr[3] = {Y2[0].x + Y2[0].y, Y2[1].x + Y2[1].y, Y2[2].x + Y2[2].y};
-    const CellProps<R> p = gas_cell_props<R>(bp, eps2.x + eps2.y, Yr, T2.x + T2.y);
+    const R epsr = eps2.x + eps2.y, Tr = T2.x + T2.y;
+    if (mode == 0) {
+      // the properties are a function of the FP32 values of (eps, Y, T): when none of them
+      // changed in this step, the stored properties are already the ones they give
+      const float2 eo = G2[GS_EPS * nc + c], to = G2[GS_T * nc + c];
+      const float2 y0 = G2[GS_Y0 * nc + c], y1 = G2[GS_Y1 * nc + c], y2 = G2[GS_Y2 * nc + c];
+      if (epsr == eo.x + eo.y && Tr == to.x + to.y && Yr[0] == y0.x + y0.y && Yr[1] == y1.x + y1.y &&
+          Yr[2] == y2.x + y2.y)
+        return;
+    }
+    const CellProps<R> p = gas_cell_props<R>(bp, epsr, Yr, Tr);
     store_props(V, c, p);
   }
 }
