@@ -976,11 +976,13 @@ __global__ void k_volume(StepView<P> V) {
 // ---------------------------------------------------------------------------------------
 // Reduction degree (eqs (2-15)..(2-19)) per parcel and per bed (deterministic two-pass).
 // ---------------------------------------------------------------------------------------
-constexpr int FOV_CHUNKS = 64;   // blocks per bed of the reduction-degree sums
+constexpr int FOV_CHUNKS = 256;   // blocks per bed of the reduction-degree sums
 
-// Each bed's parcels are contiguous in the sorted order; block (bed, chunk) sums a fixed
-// slice of them (strided per thread, then a shared-memory tree), and k_fov_beds adds the
-// slices in chunk order, so the result is reproducible bit for bit.
+// Each bed's parcels are contiguous (in storage as in sorted order); block (bed, chunk) sums a
+// fixed slice of them (strided per thread, then a shared-memory tree in FP64), and k_fov_beds
+// adds the slices in chunk order, so the result is reproducible bit for bit. The FP64 form
+// evaluates f_ov in FP64; the FP32 forms in FP32 (relative error ~1e-7 per parcel) with
+// compensated per-thread sums.
 template <class P>
 __global__ void k_fov_chunks(StepView<P> V, double *per_parcel_orig, double *part /* [nbeds][FOV_CHUNKS][4] */) {
   __shared__ double sh[3][256];
@@ -999,23 +1001,55 @@ __global__ void k_fov_chunks(StepView<P> V, double *per_parcel_orig, double *par
   __syncthreads();
   const long long len = range[1] - range[0];
   const int c0 = range[0] + (int)(len * ch / FOV_CHUNKS), c1 = range[0] + (int)(len * (ch + 1) / FOV_CHUNKS);
-  const Tab<double> &td = tab<double>();
   double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-  for (int i = c0 + (int)threadIdx.x; i < c1; i += blockDim.x) {
-    const int ore = V.A.meta[i] & 255;
-    double n[4];
+  if constexpr (P::exact) {
+    const Tab<double> &td = tab<double>();
+    for (int i = c0 + (int)threadIdx.x; i < c1; i += blockDim.x) {
+      const int ore = V.A.meta[i] & 255;
+      double n[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) n[q] = mass_d<P>(V.A.m[q], i) / td.Mz[q];
-    const double nfe = 2.0 * n[0] + 3.0 * n[1] + n[2] + n[3];
-    double f = 0.0;
-    if (nfe > 0.0) {
-      const double fh = (3.0 * n[1] + n[2] + n[3]) / nfe, fm = (n[2] + n[3]) / nfe, fw = n[3] / nfe;
-      f = ore == 0 ? fh / 9.0 + 2.0 * fm / 9.0 + 6.0 * fw / 9.0 : 0.25 * fm + 0.75 * fw;
+      for (int q = 0; q < 4; ++q) n[q] = mass_d<P>(V.A.m[q], i) / td.Mz[q];
+      const double nfe = 2.0 * n[0] + 3.0 * n[1] + n[2] + n[3];
+      double f = 0.0;
+      if (nfe > 0.0) {
+        const double fh = (3.0 * n[1] + n[2] + n[3]) / nfe, fm = (n[2] + n[3]) / nfe, fw = n[3] / nfe;
+        f = ore == 0 ? fh / 9.0 + 2.0 * fm / 9.0 + 6.0 * fw / 9.0 : 0.25 * fm + 0.75 * fw;
+      }
+      if (per_parcel_orig) per_parcel_orig[V.A.orig[i]] = f;
+      a0 += f;
+      a1 += 3.0 * n[0] + 4.0 * n[1] + n[2];
+      a2 += (ore == 0 ? 1.5 : 4.0 / 3.0) * nfe;
     }
-    if (per_parcel_orig) per_parcel_orig[V.A.orig[i]] = f;
-    a0 += f;
-    a1 += 3.0 * n[0] + 4.0 * n[1] + n[2];
-    a2 += (ore == 0 ? 1.5 : 4.0 / 3.0) * nfe;
+  } else {
+    const Tab<float> &tf = tab<float>();
+    float iM[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) iM[q] = 1.0f / tf.Mz[q];
+    float s[3] = {0.f, 0.f, 0.f}, cc[3] = {0.f, 0.f, 0.f};
+    for (int i = c0 + (int)threadIdx.x; i < c1; i += blockDim.x) {
+      const int ore = V.A.meta[i] & 255;
+      float n[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) n[q] = mass_r<P>(V.A.m[q], i) * iM[q];
+      const float nfe = 2.f * n[0] + 3.f * n[1] + n[2] + n[3];
+      float f = 0.f;
+      if (nfe > 0.f) {
+        const float inv = 1.0f / nfe;
+        const float fh = (3.f * n[1] + n[2] + n[3]) * inv, fm = (n[2] + n[3]) * inv, fw = n[3] * inv;
+        f = ore == 0 ? (fh + 2.f * fm + 6.f * fw) * (1.0f / 9.0f) : 0.25f * fm + 0.75f * fw;
+      }
+      if (per_parcel_orig) per_parcel_orig[V.A.orig[i]] = (double)f;
+      const float v[3] = {f, 3.f * n[0] + 4.f * n[1] + n[2], (ore == 0 ? 1.5f : 4.0f / 3.0f) * nfe};
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float y = v[q] - cc[q], t = s[q] + y;
+        cc[q] = (t - s[q]) - y;
+        s[q] = t;
+      }
+    }
+    a0 = (double)s[0] - (double)cc[0];
+    a1 = (double)s[1] - (double)cc[1];
+    a2 = (double)s[2] - (double)cc[2];
   }
   sh[0][threadIdx.x] = a0; sh[1][threadIdx.x] = a1; sh[2][threadIdx.x] = a2;
   __syncthreads();
