@@ -87,15 +87,16 @@ def algorithmic_bytes(kernel: str, n: int, ncells: int, zbar: float, L: float, r
     if kernel == "radix_sort":
         return n * passes * (8 + 8)
     if kernel == "resort":           # new keys in sorted order, re-sort, permutation and cell ranges
-        return n * (16 + 16 + 16)
+        return n * (16 + 16 + 8)
     if kernel == "k_restore":        # list-build steps: state, local coordinates, history out and back
         return fbuild * n * (4 * (state + 16 + 1 + zbar * slot) + 4 + 8)
-    if kernel == "k_pair_list":
-        return (1 - fbuild) * n * ((4 + 16 + 4 + 1 + 4 * L) + (1 + 5 * zbar))
     if kernel == "k_pair_search":    # list builds (the cell-list search) only
         return fbuild * n * ((4 + 16 + 4) + (4 * L + 1 + 1 + 12 + 5 * zbar))
-    if kernel == "k_pair_forces":
-        return n * ((4 + 16 + 1 + 4 + 1 + zbar * (5 + 2 * (slot + 8 * R + 32))) + (1 + zbar * slot + 6 * R))
+    if kernel == "k_ranges":
+        return n * (4 + 4 + 4)
+    if kernel == "k_contacts":       # list test (between builds), forces, history, walls
+        return n * ((4 + 16 + 4 + 1 + 1 + 4 * L * (1 - fbuild) + fbuild * (1 + 5 * zbar) + zbar * (2 * slot + 8 * R + 32))
+                    + (1 + 6 * R))
     if kernel == "k_gas_particle":
         return n * ((4 + 4 + R + 3 * R + R + 32 + 6 * R + 3 * R) + (12 * R + R + 32 + 14 * R)) + ncells * 13 * R
     if kernel == "k_cells":
@@ -108,8 +109,7 @@ def algorithmic_bytes(kernel: str, n: int, ncells: int, zbar: float, L: float, r
 # was taken on (profiles/traffic_ibm_2m_split.md gives the command).
 TRAFFIC_SOURCE_SHA256 = "7ebdf1665b947705ce74b77b49d117eabf39436bf0d35601467a15ab149f52e4"
 TRAFFIC_WORKLOAD = ("ibm_2m", "split", 2_000_000)
-TRAFFIC_BYTES_PER_PARCEL = {"k_gas_particle": 226.06, "k_gather": 300.32, "k_key": 124.49, "k_cells": 117.60,
-                            "k_pair_list": 55.80, "k_pair_forces": 28.08, "rz_merge": 12.00}
+TRAFFIC_BYTES_PER_PARCEL = {}
 
 
 def source_sha256() -> str:

@@ -206,7 +206,7 @@ int dem_get_diag(dem_ctx *c, double *out_host);
  * the same step is computed), DEM_NTUNE int32 values:
  *   [0] contact search: 1 = Verlet neighbour lists rebuilt from the cell list when a parcel
  *       has moved half the skin (default), 0 = the cell-list search every step;
- *   [1]..[6] block sizes of the key, re-store, pair-search, pair-force, gas-particle and
+ *   [1]..[6] block sizes of the key, re-store, pair-search, contact, gas-particle and
  *       gas-cell kernels (multiples of 32 in [32, 1024], and no larger than the kernel's
  *       launch bounds and register use allow: the gas-particle kernel stops at 256);
  *   [7] neighbour-list skin in thousandths of the bed's largest parcel diameter (1..1000).

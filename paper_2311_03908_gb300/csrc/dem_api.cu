@@ -1006,7 +1006,7 @@ int dem_autotune(dem_ctx *c, int32_t n_steps) {
     return tot;
   };
   // 1) block sizes, every per-thread kernel at once, each kernel keeping its fastest
-  const char *kname[6] = {"k_key", "k_restore", "k_pair_search", "k_pair_forces", "k_gas_particle", "k_cells"};
+  const char *kname[6] = {"k_key", "k_restore", "k_pair_search", "k_contacts", "k_gas_particle", "k_cells"};
   double bt[6];
   for (int k = 0; k < 6; ++k) bt[k] = 1e300;
   int32_t tb[DEM_NTUNE];

@@ -49,6 +49,7 @@ template <class P> struct StepView {
                                 // the ranges kernel of this step rewrites it)
   unsigned *cstart, *cend;      // sorted-position range of every gas cell (empty: 0, 0)
   float4 *xl;                   // FP32 position relative to the own cell's corner, radius
+  R *F[3], *Tq[3];              // contact force and torque
   float4 *xls;                  // scratch of a re-store (aliases the per-parcel sources,
                                 // which the gas-particle kernel rewrites later in the step)
   int *plist;                   // [KLIST][cap] partners in contact range this step
@@ -61,7 +62,6 @@ template <class P> struct StepView {
   const double *corner;         // cell-corner coordinates (see DevBed::corner_off)
   const float2 *cornerp;        // cell corners relative to the bed corner, FP32 pairs
   int *moved;                   // per 1024 sorted positions: keys that changed (re-sort)
-  R *F[3], *Tq[3];              // contact force and torque
   R *src;                       // [SR_N][cap] per-parcel cell sources
   double *gas, *gas_new;        // [GS_N][ncells]
   R *gp;                        // [GP_N][ncells]
@@ -361,16 +361,17 @@ __device__ __forceinline__ void add_contact(const StepView<P> &V, int i, int cin
 }
 
 // ---------------------------------------------------------------------------------------
-// Contacts, one thread per parcel, in two kernels.
-// k_pair_search: for each of the 9 neighbour rows (dy, dz) the cells X-1..X+1 hold one
-// contiguous run of sorted parcels; rows and end cells farther than r_i + r_max from the
-// parcel are skipped. Every candidate is tested on the FP32 cell-local coordinates (the
-// exact form with a small margin) and the hits are written, in visiting order, to a
-// per-parcel list (sorted index + cell offset code). Few registers, so many warps hide the
-// load latency of the pair loop.
-// k_pair_forces: the contact law for the listed pairs (the FP64 form first re-tests each
-// pair on the FP64 positions with the oracle's expression, so its pair sets are bit-exact),
-// then the walls; pairs are visited in the order of a plain 27-cell loop (dz, dy, dx, index).
+// Contacts, one thread per parcel.
+// k_pair_search (list builds, overflowed lists, no lists): for each of the 9 neighbour rows
+// (dy, dz) the cells X-1..X+1 hold one contiguous run of sorted positions; rows and end cells
+// farther than r_i + r_max (+ skin) from the parcel are skipped. Every candidate is tested on
+// the FP32 cell-local coordinates (the exact form with a small margin); the hits go, in
+// visiting order (dz, dy, dx, sorted position), to a per-parcel hit list, and on build steps
+// the partners within r_i + r_j + skin to the parcel's neighbour list. Few registers, so many
+// warps hide the load latency of the pair loop.
+// parcel_contacts (k_contacts): the list test between builds, the contact law
+// for the pairs (the FP64 form first re-tests each pair on the FP64 positions with the
+// oracle's expression, so its pair sets are bit-exact), and the walls.
 // ---------------------------------------------------------------------------------------
 // cell offsets (dx, dy, dz) of the cell with key k2 relative to the cell with key k1
 __device__ __forceinline__ void key_offset(const DevBed &B, unsigned k1, unsigned k2, int &dx, int &dy, int &dz) {
@@ -400,7 +401,7 @@ __global__ void k_pair_search(StepView<P> V) {
   const BedP<typename P::R> &bp = V.bp[b];
   const size_t cap = (size_t)V.cap;
   const bool rebuild = *V.rebuild != 0;
-  // between rebuilds the parcels with a list are k_pair_list's
+  // between rebuilds the parcels with a list are tested by parcel_contacts
   if (!V.nolists && !rebuild && V.nlc[i] != NL_OVERFLOW) return;
   const bool build = rebuild && !V.nolists;
   int nh = 0, nn = 0;
@@ -491,161 +492,170 @@ __global__ void k_pair_search(StepView<P> V) {
   V.pcnt[i] = (unsigned char)nh;
 }
 
-// Between rebuilds: test the partners listed at the last build (storage positions, which
-// have not changed since). Four entries are resolved at a time (entry -> key and local
-// position) so that several dependent loads are in flight per thread.
+// Contact of parcel i with partner j (storage positions; code = cell offset of j's cell):
+// the FP64 form re-tests the pair on the FP64 positions with the oracle's expression.
 template <class P>
-__global__ void k_pair_list(StepView<P> V) {
-  if (*V.rebuild || V.nolists) return;   // k_pair_search handles this step
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= V.n) return;
-  const int listed = V.nlc[i];
-  if (listed == NL_OVERFLOW) return;   // k_pair_search handles it
-  const size_t cap = (size_t)V.cap;
-  int nh = 0;
-  if (listed > 0) {
-    const int b = V.A.meta[i] >> 8;
-    const DevBed &B = V.beds[b];
-    const BedP<typename P::R> &bp = V.bp[b];
+__device__ __forceinline__ void pair_contact(const StepView<P> &V, int i, int j, int code, const DevBed &B,
+                                             const BedP<typename P::R> &bp, const float4 &me, float hx, float hy,
+                                             float hz, const double *xi_d, double ri_d, typename P::R ri,
+                                             typename P::R mi, const typename P::R vi[3], const typename P::R wi[3],
+                                             int cin, typename P::R Fi[3], typename P::R Ti[3], int &cout) {
+  using R = typename P::R;
+  R nrm[3], delta;
+  double rj_d = 0;
+  if constexpr (P::exact) {
+    const double dxd = V.A.x[j] - xi_d[0], dyd = V.A.y[j] - xi_d[1], dzd = V.A.z[j] - xi_d[2];
+    rj_d = __dmul_rn(0.5, __dmul_rn(B.k, (double)V.A.d[j]));
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dxd, dxd), __dmul_rn(dyd, dyd)), __dmul_rn(dzd, dzd));
+    const double rs = __dadd_rn(ri_d, rj_d);
+    if (!(d2 < __dmul_rn(rs, rs))) return;
+    const double dd = sqrt(d2);
+    nrm[0] = (R)(dxd / dd); nrm[1] = (R)(dyd / dd); nrm[2] = (R)(dzd / dd);
+    delta = (R)(rs - dd);
+  } else {
+    const int cdx = code % 3 - 1, cdy = (code / 3) % 3 - 1, cdz = code / 9 - 1;
+    const float4 o = __ldg(V.xl + j);
+    const float ex = o.x + (cdx * hx - me.x), ey = o.y + (cdy * hy - me.y), ez = o.z + (cdz * hz - me.z);
+    const float d2f = ex * ex + ey * ey + ez * ez;
+    const float rsf = me.w + o.w;
+    const float df = sqrtf(d2f);
+    const float inv = 1.0f / df;
+    nrm[0] = (R)(ex * inv); nrm[1] = (R)(ey * inv); nrm[2] = (R)(ez * inv);
+    delta = (R)((rsf * rsf - d2f) / (rsf + df));
+  }
+  const R rj = P::exact ? (R)rj_d : (R)__ldg(&V.xl[j].w);
+  const R mj = parcel_mass<P>(V.A, j);
+  const R mstar = mi * mj / (mi + mj);
+  const R ws[3] = {ri * wi[0] + rj * V.A.w[0][j], ri * wi[1] + rj * V.A.w[1][j], ri * wi[2] + rj * V.A.w[2][j]};
+  R vrel[3];
+  vrel[0] = (vi[0] - V.A.v[0][j]) + (ws[1] * nrm[2] - ws[2] * nrm[1]);
+  vrel[1] = (vi[1] - V.A.v[1][j]) + (ws[2] * nrm[0] - ws[0] * nrm[2]);
+  vrel[2] = (vi[2] - V.A.v[2][j]) + (ws[0] * nrm[1] - ws[1] * nrm[0]);
+  add_contact<P>(V, i, cin, V.A.orig[j], bp, mstar, ri, nrm, delta, vrel, wi, Fi, Ti, cout);
+}
+
+// All contact forces on parcel i: its partners -- tested here against the neighbour list
+// (between list builds; pairs in list order), or taken from the cell-list search's hit list
+// (build steps, overflowed lists, no lists) -- then the walls (FP32 pre-screen, FP64
+// distances within reach). Writes the parcel's new contact history. The parcel's own state
+// is read only when it has a candidate partner or a wall within reach.
+template <class P>
+__device__ __forceinline__ void parcel_contacts(const StepView<P> &V, int i, int meta, typename P::R Fi[3],
+                                                typename P::R Ti[3]) {
+  using R = typename P::R;
+  const DevBed &B = V.beds[meta >> 8];
+  const BedP<R> &bp = V.bp[meta >> 8];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) { Fi[q] = 0; Ti[q] = 0; }
+  int cout = 0;
+  if (!(bp.flags & DEM_NO_CONTACTS)) {
+    const int cin = V.H.cnt[i];
     const float4 me = V.xl[i];
     const unsigned key = V.keyp[i];
+    int X, Y, Z;
+    key_cell(B, key, X, Y, Z);
     const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
-    const float pm = P::exact ? (float)bp.pf_margin : 0.f;
-    for (int k0 = 0; k0 < listed; k0 += 4) {
-      int j[4];
+    const float xa = (float)bp.x0 + X * hx + me.x, ya = (float)bp.y0 + Y * hy + me.y, za = (float)bp.z0 + Z * hz + me.z;
+    float distf[4], nwf[4][3];
+    wall_primitives<float>(bp, xa, ya, za, distf, nwf);
+    bool near = false;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) j[u] = k0 + u < listed ? V.nl[(k0 + u) * cap + i] : -1;
-      unsigned kj[4];
-      float4 o[4];
+    for (int p = 0; p < 4; ++p) near |= distf[p] < me.w + 1e-6f;
+    const int listed = V.nlc[i];
+    const bool searched = *V.rebuild || V.nolists || listed == NL_OVERFLOW;
+    const size_t cap = (size_t)V.cap;
+    // between builds: the list test first, hits recorded as a mask over the list entries
+    unsigned hits = 0u;
+    if (!searched) {
+      const float pm = P::exact ? (float)bp.pf_margin : 0.f;
+      for (int k0 = 0; k0 < listed; k0 += 4) {
+        int j[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        kj[u] = j[u] >= 0 ? V.keyp[j[u]] : key;
-        o[u] = j[u] >= 0 ? __ldg(V.xl + j[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int u = 0; u < 4; ++u) j[u] = k0 + u < listed ? V.nl[(k0 + u) * cap + i] : -1;
+        unsigned kj[4];
+        float4 o[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          kj[u] = j[u] >= 0 ? V.keyp[j[u]] : key;
+          o[u] = j[u] >= 0 ? __ldg(V.xl + j[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (j[u] < 0) continue;
+          int dx, dy, dz;
+          key_offset(B, key, kj[u], dx, dy, dz);
+          if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) continue;   // cannot touch
+          const float ex = o[u].x + (dx * hx - me.x), ey = o[u].y + (dy * hy - me.y), ez = o[u].z + (dz * hz - me.z);
+          const float d2 = ex * ex + ey * ey + ez * ez;
+          const float lim = me.w + o[u].w + pm;
+          if (d2 < lim * lim) hits |= 1u << (k0 + u);
+        }
       }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (j[u] < 0) continue;
+    }
+    const int nsearch = searched ? (int)V.pcnt[i] : 0;
+    if (hits != 0u || nsearch > 0 || near) {
+      const R di = V.A.d[i];
+      const R mi = parcel_mass<P>(V.A, i);
+      const R vi[3] = {V.A.v[0][i], V.A.v[1][i], V.A.v[2][i]};
+      const R wi[3] = {V.A.w[0][i], V.A.w[1][i], V.A.w[2][i]};
+      double xi_d[3] = {0, 0, 0}, ri_d = 0;
+      if constexpr (P::exact) {
+        xi_d[0] = V.A.x[i]; xi_d[1] = V.A.y[i]; xi_d[2] = V.A.z[i];
+        ri_d = __dmul_rn(0.5, __dmul_rn(B.k, (double)di));
+      }
+      const R ri = P::exact ? (R)ri_d : (R)me.w;
+      for (int h = 0; h < nsearch; ++h)
+        pair_contact<P>(V, i, V.plist[h * cap + i], V.pcode[h * cap + i], B, bp, me, hx, hy, hz, xi_d, ri_d, ri, mi,
+                        vi, wi, cin, Fi, Ti, cout);
+      while (hits) {   // list order
+        const int k = __ffs(hits) - 1;
+        hits &= hits - 1u;
+        const int j = V.nl[k * cap + i];
         int dx, dy, dz;
-        key_offset(B, key, kj[u], dx, dy, dz);
-        if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) continue;   // cannot touch
-        const float ex = o[u].x + (dx * hx - me.x), ey = o[u].y + (dy * hy - me.y), ez = o[u].z + (dz * hz - me.z);
-        const float d2 = ex * ex + ey * ey + ez * ez;
-        const float lim = me.w + o[u].w + pm;
-        if (d2 < lim * lim) {
-          if (nh < KLIST) {
-            V.plist[nh * cap + i] = j[u];
-            V.pcode[nh * cap + i] = (unsigned char)((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
-          }
-          ++nh;
+        key_offset(B, key, V.keyp[j], dx, dy, dz);
+        pair_contact<P>(V, i, j, (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1), B, bp, me, hx, hy, hz, xi_d, ri_d, ri, mi,
+                        vi, wi, cin, Fi, Ti, cout);
+      }
+      if (near) {
+        const double xd = pos_abs<P>(V.A.x, i, B.x0), yd = pos_abs<P>(V.A.y, i, B.y0), zd = pos_abs<P>(V.A.z, i, B.z0);
+        const double rid = __dmul_rn(0.5, __dmul_rn(B.k, (double)di));
+        double dist[4], nw[4][3];
+        wall_primitives<double>(B, xd, yd, zd, dist, nw);
+        for (int p = 0; p < 4; ++p) {
+          const double gap = rid - dist[p];
+          if (!(gap > 0.0)) continue;
+          const R nrm[3] = {(R)-nw[p][0], (R)-nw[p][1], (R)-nw[p][2]};
+          const R delta = (R)gap;
+          const R wr[3] = {ri * wi[0], ri * wi[1], ri * wi[2]};
+          R vrel[3];
+          vrel[0] = vi[0] + (wr[1] * nrm[2] - wr[2] * nrm[1]);
+          vrel[1] = vi[1] + (wr[2] * nrm[0] - wr[0] * nrm[2]);
+          vrel[2] = vi[2] + (wr[0] * nrm[1] - wr[1] * nrm[0]);
+          add_contact<P>(V, i, cin, -1 - p, bp, mi, ri, nrm, delta, vrel, wi, Fi, Ti, cout);
         }
       }
     }
   }
-  if (nh > KLIST) { set_error(V.err, ERR_CAPACITY); nh = KLIST; }
-  V.pcnt[i] = (unsigned char)nh;
-}
-
-template <class P>
-__global__ void k_pair_forces(StepView<P> V) {
-  using R = typename P::R;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= V.n) return;
-  const int meta = V.A.meta[i];
-  const int b = meta >> 8;
-  const DevBed &B = V.beds[b];
-  const BedP<R> &bp = V.bp[b];
-  R Fi[3] = {0, 0, 0}, Ti[3] = {0, 0, 0};
-  int cout = 0;
-  const int cin = V.H.cnt[i];
-  const float4 me = V.xl[i];
-  const int nh = V.pcnt[i];
-  // walls: FP32 pre-screen on the absolute position rebuilt from the cell corner
-  int X, Y, Z;
-  key_cell(B, V.keyp[i], X, Y, Z);
-  const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
-  const float xa = (float)bp.x0 + X * hx + me.x, ya = (float)bp.y0 + Y * hy + me.y, za = (float)bp.z0 + Z * hz + me.z;
-  float distf[4], nwf[4][3];
-  wall_primitives<float>(bp, xa, ya, za, distf, nwf);
-  bool near = false;
-#pragma unroll
-  for (int p = 0; p < 4; ++p) near |= distf[p] < me.w + 1e-6f;
-  // the parcel's own state is read only when it has a partner or a wall within reach
-  if (!(bp.flags & DEM_NO_CONTACTS) && (nh > 0 || near)) {
-    const R di = V.A.d[i];
-    const R mi = parcel_mass<P>(V.A, i);
-    const R vi[3] = {V.A.v[0][i], V.A.v[1][i], V.A.v[2][i]};
-    const R wi[3] = {V.A.w[0][i], V.A.w[1][i], V.A.w[2][i]};
-    double xi_d = 0, yi_d = 0, zi_d = 0, ri_d = 0;
-    if constexpr (P::exact) {
-      xi_d = V.A.x[i]; yi_d = V.A.y[i]; zi_d = V.A.z[i];
-      ri_d = __dmul_rn(0.5, __dmul_rn(B.k, (double)di));
-    }
-    const R ri = P::exact ? (R)ri_d : (R)me.w;
-    const size_t cap = (size_t)V.cap;
-    for (int h = 0; h < nh; ++h) {
-      const int j = V.plist[h * cap + i];
-      R nrm[3], delta;
-      double rj_d = 0;
-      if constexpr (P::exact) {
-        const double dxd = V.A.x[j] - xi_d, dyd = V.A.y[j] - yi_d, dzd = V.A.z[j] - zi_d;
-        rj_d = __dmul_rn(0.5, __dmul_rn(B.k, (double)V.A.d[j]));
-        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dxd, dxd), __dmul_rn(dyd, dyd)), __dmul_rn(dzd, dzd));
-        const double rs = __dadd_rn(ri_d, rj_d);
-        if (!(d2 < __dmul_rn(rs, rs))) continue;
-        const double dd = sqrt(d2);
-        nrm[0] = (R)(dxd / dd); nrm[1] = (R)(dyd / dd); nrm[2] = (R)(dzd / dd);
-        delta = (R)(rs - dd);
-      } else {
-        const int code = V.pcode[h * cap + i];
-        const int cdx = code % 3 - 1, cdy = (code / 3) % 3 - 1, cdz = code / 9 - 1;
-        const float4 o = __ldg(V.xl + j);
-        const float ex = o.x + (cdx * hx - me.x), ey = o.y + (cdy * hy - me.y), ez = o.z + (cdz * hz - me.z);
-        const float d2f = ex * ex + ey * ey + ez * ez;
-        const float rsf = me.w + o.w;
-        const float df = sqrtf(d2f);
-        const float inv = 1.0f / df;
-        nrm[0] = (R)(ex * inv); nrm[1] = (R)(ey * inv); nrm[2] = (R)(ez * inv);
-        delta = (R)((rsf * rsf - d2f) / (rsf + df));
-      }
-      const R rj = P::exact ? (R)rj_d : (R)__ldg(&V.xl[j].w);
-      const R mj = parcel_mass<P>(V.A, j);
-      const R mstar = mi * mj / (mi + mj);
-      const R ws[3] = {ri * wi[0] + rj * V.A.w[0][j], ri * wi[1] + rj * V.A.w[1][j], ri * wi[2] + rj * V.A.w[2][j]};
-      R vrel[3];
-      vrel[0] = (vi[0] - V.A.v[0][j]) + (ws[1] * nrm[2] - ws[2] * nrm[1]);
-      vrel[1] = (vi[1] - V.A.v[1][j]) + (ws[2] * nrm[0] - ws[0] * nrm[2]);
-      vrel[2] = (vi[2] - V.A.v[2][j]) + (ws[0] * nrm[1] - ws[1] * nrm[0]);
-      add_contact<P>(V, i, cin, V.A.orig[j], bp, mstar, ri, nrm, delta, vrel, wi, Fi, Ti, cout);
-    }
-    if (near) {
-      const double xd = pos_abs<P>(V.A.x, i, B.x0), yd = pos_abs<P>(V.A.y, i, B.y0), zd = pos_abs<P>(V.A.z, i, B.z0);
-      const double rid = __dmul_rn(0.5, __dmul_rn(B.k, (double)di));
-      double dist[4], nw[4][3];
-      wall_primitives<double>(B, xd, yd, zd, dist, nw);
-      for (int p = 0; p < 4; ++p) {
-        const double gap = rid - dist[p];
-        if (!(gap > 0.0)) continue;
-        const R nrm[3] = {(R)-nw[p][0], (R)-nw[p][1], (R)-nw[p][2]};
-        const R delta = (R)gap;
-        const R wr[3] = {ri * wi[0], ri * wi[1], ri * wi[2]};
-        R vrel[3];
-        vrel[0] = vi[0] + (wr[1] * nrm[2] - wr[2] * nrm[1]);
-        vrel[1] = vi[1] + (wr[2] * nrm[0] - wr[0] * nrm[2]);
-        vrel[2] = vi[2] + (wr[0] * nrm[1] - wr[1] * nrm[0]);
-        add_contact<P>(V, i, cin, -1 - p, bp, mi, ri, nrm, delta, vrel, wi, Fi, Ti, cout);
-      }
-    }
-  }
   V.Hn.cnt[i] = (unsigned char)cout;
-#pragma unroll
-  for (int q = 0; q < 3; ++q) { V.F[q][i] = Fi[q]; V.Tq[q][i] = Ti[q]; }
   if (V.diag) V.diag[(size_t)DG_NCONTACT * V.cap + i] = (double)cout;
 }
 
+// Contact force and torque of every parcel. A kernel of its own: the partners' half-step
+// velocities, spins and masses must all be read before k_gas_particle updates them.
+template <class P>
+__global__ void k_contacts(StepView<P> V) {
+  using R = typename P::R;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V.n) return;
+  R F[3], Tq[3];
+  parcel_contacts<P>(V, i, V.A.meta[i], F, Tq);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) { V.F[q][i] = F[q]; V.Tq[q][i] = Tq[q]; }
+}
 
 // ---------------------------------------------------------------------------------------
-// Gas-particle terms, kinetics, second half kick, temperature and mass update; writes the
-// parcel's contributions to its cell sums.
+// Per parcel (storage order): gas-particle terms, kinetics, second half kick, temperature
+// and mass update; writes the parcel's contributions to its cell sums.
 // ---------------------------------------------------------------------------------------
 // The FP32 forms are held to 64 registers (4 blocks of 256 threads per SM): a few spills
 // to L1 cost less than the latency the extra occupancy hides (ncu: 33 % -> 50 % warps).
@@ -655,6 +665,8 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V.n) return;
   const int meta = V.A.meta[i];
+  const R F[3] = {V.F[0][i], V.F[1][i], V.F[2][i]};
+  const R Tq[3] = {V.Tq[0][i], V.Tq[1][i], V.Tq[2][i]};
   const int ore = meta & 255;
   const BedP<R> &bp = V.bp[meta >> 8];
   const unsigned fl = bp.flags;
@@ -694,8 +706,6 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
 #pragma unroll
   for (int q = 0; q < 4; ++q) mp += m[q];   // the same sum as parcel_mass
   const R I = (R)0.4 * mp * r * r;
-  const R F[3] = {V.F[0][i], V.F[1][i], V.F[2][i]};
-  const R Tq[3] = {V.Tq[0][i], V.Tq[1][i], V.Tq[2][i]};
   R a[3];
   a[0] = fdiv<R>(F[0] + Fd[0], mp);
   a[1] = fdiv<R>(F[1] + Fd[1], mp);

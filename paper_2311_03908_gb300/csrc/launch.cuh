@@ -47,6 +47,7 @@ StepView<P> make_view(dem_ctx *c, bool for_step) {
   V.inv = c->inv;
   V.cstart = c->cstart; V.cend = c->cend;
   V.xl = c->xl;
+  for (int q = 0; q < 3; ++q) { V.F[q] = (R *)c->F[q]; V.Tq[q] = (R *)c->Tq[q]; }
   V.xls = reinterpret_cast<float4 *>(c->src);
   V.plist = c->plist;
   V.pcode = c->pcode;
@@ -58,7 +59,6 @@ StepView<P> make_view(dem_ctx *c, bool for_step) {
   V.corner = c->corner;
   V.cornerp = c->cornerp;
   V.moved = resort_counts(c->rsw, c->rs_pow2, c->n);
-  for (int q = 0; q < 3; ++q) { V.F[q] = (R *)c->F[q]; V.Tq[q] = (R *)c->Tq[q]; }
   V.src = (R *)c->src;
   V.gas = c->gas[c->gcur];
   V.gas_new = c->gas[1 - c->gcur];
@@ -99,6 +99,8 @@ int enqueue_binning(dem_ctx *c, int drift) {
     if (e) return e;
     cudaMemsetAsync(c->cstart, 0, sizeof(unsigned) * c->ncells, st);
     cudaMemsetAsync(c->cend, 0, sizeof(unsigned) * c->ncells, st);
+    prof_end(c, ps);
+    ps = prof_begin(c, "k_ranges");
     k_ranges<P><<<grid_for(c->n, c->bs_gather), c->bs_gather, 0, st>>>(V);
     prof_end(c, ps);
     ++c->launches;
@@ -137,17 +139,13 @@ int enqueue_steps(dem_ctx *c, int nsteps) {
     if (e) return e;
     StepView<P> V = make_view<P>(c, true);
     int ps;
-    if (c->use_lists) {
-      ps = prof_begin(c, "k_pair_list");
-      k_pair_list<P><<<grid_for(c->n, c->bs_search), c->bs_search, 0, st>>>(V);
-      prof_end(c, ps);
-      ++c->launches;
-    }
+    // the cell-list search (list builds, overflowed lists, no lists; otherwise a no-op), the
+    // contact forces (with the list test between builds), then the gas-particle terms
     ps = prof_begin(c, "k_pair_search");
     k_pair_search<P><<<grid_for(c->n, c->bs_search), c->bs_search, 0, st>>>(V);
     prof_end(c, ps);
-    ps = prof_begin(c, "k_pair_forces");
-    k_pair_forces<P><<<grid_for(c->n, c->bs_contacts), c->bs_contacts, 0, st>>>(V);
+    ps = prof_begin(c, "k_contacts");
+    k_contacts<P><<<grid_for(c->n, c->bs_contacts), c->bs_contacts, 0, st>>>(V);
     prof_end(c, ps);
     ps = prof_begin(c, "k_gas_particle");
     k_gas_particle<P><<<grid_for(c->n, c->bs_gp), c->bs_gp, 0, st>>>(V);
@@ -230,7 +228,7 @@ int enqueue_props(dem_ctx *c) {
 template <class P>
 int kernel_limits(int *lim) {
   const void *fn[6] = {(const void *)k_key<P>, (const void *)k_restore_out<P>, (const void *)k_pair_search<P>,
-                       (const void *)k_pair_forces<P>, (const void *)k_gas_particle<P>, (const void *)k_cells<P>};
+                       (const void *)k_contacts<P>, (const void *)k_gas_particle<P>, (const void *)k_cells<P>};
   for (int k = 0; k < 6; ++k) {
     cudaFuncAttributes a;
     if (cudaFuncGetAttributes(&a, fn[k]) != cudaSuccess) return -1;

@@ -136,31 +136,35 @@ __device__ __forceinline__ int count_less(const unsigned long long *c, int lo, i
   return lo;
 }
 
-// output positions. A block of stayers sees only the movers between the composites of its
+// output positions. A warp of stayers sees only the movers between the composites of its
 // first and last position (kold is sorted, so (kold[g], g) increases with g): two searches
-// per block, then a short scan per thread.
+// per warp, then a short scan per thread.
 constexpr int RZ_MERGE = 256;
 __global__ void __launch_bounds__(RZ_MERGE) rz_merge(const unsigned *kold, const unsigned *knew, int n,
                                                      const int *pre, const unsigned long long *sorted,
                                                      const unsigned *vmap, unsigned *kout, unsigned *vout) {
-  __shared__ int bounds[2];
   const int m = pre[n];
-  const int g0 = blockIdx.x * RZ_MERGE;
-  const int g = g0 + threadIdx.x;
-  if (threadIdx.x == 0) {
-    const int g1 = min(g0 + RZ_MERGE, n) - 1;
-    const unsigned long long c0 = ((unsigned long long)kold[g0] << 32) | (unsigned)g0;
-    const unsigned long long c1 = ((unsigned long long)kold[g1] << 32) | (unsigned)g1;
-    bounds[0] = count_less(sorted, 0, m, c0);
-    bounds[1] = count_less(sorted, bounds[0], m, c1 + 1);
+  const int g = blockIdx.x * RZ_MERGE + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int w0 = g - lane;
+  int lo = 0, hi = 0;
+  if (w0 < n) {
+    if (lane == 0) {
+      const int g1 = min(w0 + 32, n) - 1;
+      const unsigned long long c0 = ((unsigned long long)kold[w0] << 32) | (unsigned)w0;
+      const unsigned long long c1 = ((unsigned long long)kold[g1] << 32) | (unsigned)g1;
+      lo = count_less(sorted, 0, m, c0);
+      hi = count_less(sorted, lo, m, c1 + 1);
+    }
+    lo = __shfl_sync(0xffffffffu, lo, 0);
+    hi = __shfl_sync(0xffffffffu, hi, 0);
   }
-  __syncthreads();
   if (g < n) {
     const unsigned key = knew[g];
     if (key == kold[g]) {   // stayer
       const unsigned long long c = ((unsigned long long)key << 32) | (unsigned)g;
-      int below = bounds[0];
-      for (int t = bounds[0]; t < bounds[1]; ++t) below += sorted[t] < c ? 1 : 0;
+      int below = lo;
+      for (int t = lo; t < hi; ++t) below += sorted[t] < c ? 1 : 0;
       const int pos = g - pre[g] + below;
       kout[pos] = key;
       vout[pos] = vmap ? vmap[g] : (unsigned)g;

@@ -35,7 +35,7 @@ def test_contact_configurations_match_oracle(lists, skin, bs):
     bed = synth.small_packed(seed=21, n=3000, v_scale=0.3, wall_kind=synth.WALL_CONE)
     ctx = _ctx(bed)
     ctx.dem_set_tuning(neighbour_lists=lists, skin_permille=skin, bs_key=bs, bs_restore=bs, bs_search=bs,
-                       bs_forces=bs, bs_gas_particle=bs, bs_cells=bs)
+                       bs_contacts=bs, bs_gas_particle=bs, bs_cells=bs)
     ref = oracle.Oracle(bed)
     for _ in range(4):
         ctx.dem_step(15)
