@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--form-steps", type=int, default=0, help="steps of the three-form comparison "
                     "(0: the workload's own step count)")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--settle", type=int, default=300, help="untimed steps before the autotuner and the warm-up, so that the timed steps see the fluidised bed (contacts, list builds) rather than the packing at rest")
     ap.add_argument("--autotune", type=int, default=30, help="steps per autotuner candidate before the "
                     "warm-up (0: keep the default launch configuration)")
     ap.add_argument("--tuning", default="", help="fixed launch configuration instead of the autotuner, "
@@ -77,8 +78,12 @@ def make_workload(name: str, rank: int = 0, parcels: int = 0):
 # counting the re-reads of neighbours' records, which the caches serve.
 # ---------------------------------------------------------------------------------------
 def algorithmic_bytes(kernel: str, n: int, ncells: int, zbar: float, L: float, rsize: int, passes: int,
-                      fbuild: float = 0.0) -> float:
-    """Per launch; fbuild = fraction of steps that rebuild the lists (and re-store the state)."""
+                      fbuild: float = 0.0, fc: float = 1.0, frestore: float = None) -> float:
+    """Per launch; fbuild = fraction of steps that rebuild the lists, frestore = fraction that
+    re-store the state in cell order (default: every build), fc = fraction of parcels in
+    contact (only those have a contact force and torque to pass on)."""
+    if frestore is None:
+        frestore = fbuild
     R = rsize
     slot = 4 + 3 * R                                  # partner id + tangential displacement
     state = 24 + 12 * R + 2 * R + 32 + 8 + 12         # x; v,w,a,al; T,d; masses; meta,orig; dsp
@@ -89,18 +94,19 @@ def algorithmic_bytes(kernel: str, n: int, ncells: int, zbar: float, L: float, r
     if kernel == "resort":           # new keys in sorted order, re-sort, permutation and cell ranges
         return n * (16 + 16 + 8)
     if kernel == "k_restore":        # list-build steps: state, local coordinates, history out and back
-        return fbuild * n * (4 * (state + 16 + 1 + zbar * slot) + 4 + 8)
+        return frestore * n * (4 * (state + 16 + 1 + zbar * slot) + 4 + 8)
     if kernel == "k_pair_search":    # list builds (the cell-list search) only
         return fbuild * n * ((4 + 16 + 4) + (4 * L + 1 + 1 + 12 + 5 * zbar))
     if kernel == "k_ranges":
         return n * (4 + 4 + 4)
-    if kernel == "k_contacts":       # list test (between builds), forces, history, walls
-        return n * ((4 + 16 + 4 + 1 + 1 + 4 * L * (1 - fbuild) + fbuild * (1 + 5 * zbar) + zbar * (2 * slot + 8 * R + 32))
-                    + (1 + 6 * R))
+    if kernel == "k_contact_screen":  # list test (between builds), wall pre-screen; empty histories
+        return n * ((4 + 16 + 4 + 1 + 4 * L * (1 - fbuild) + fbuild * 1) + 1)
+    if kernel == "k_contact_forces":  # parcels in contact: own state, partners, history in and out, F, T
+        return n * (fbuild * 5 * zbar + zbar * (2 * slot + 8 * R + 32) + fc * (8 + 6 * R + 32 + 6 * R))
     if kernel == "k_gas_particle":
-        return n * ((4 + 4 + R + 3 * R + R + 32 + 6 * R + 3 * R) + (12 * R + R + 32 + 14 * R)) + ncells * 13 * R
+        return n * ((4 + 4 + R + 3 * R + R + 32 + 1 + fc * 6 * R + 3 * R) + (12 * R + R + 32 + 13 * R)) + ncells * 13 * R
     if kernel == "k_cells":
-        return ncells * ((4 + 1 + 8 + 5 * 8 + 2 * R) + (5 * 8 + 14 * R)) + n * (14 * R + 4)
+        return ncells * ((4 + 1 + 8 + 5 * 8 + 2 * R) + (5 * 8 + 14 * R)) + n * (6 * R + 4)
     return 0.0
 
 
@@ -280,6 +286,9 @@ def main():
     bed = make_workload(args.workload, rank, args.parcels)
     ctx = binding.Context(bed, precision=args.precision, stream=stream.cuda_stream)
     n = bed.n
+    if args.settle > 0:
+        ctx.dem_step(args.settle)
+        ctx.dem_sync()
     if args.tuning:
         ctx.dem_set_tuning(**{k: int(v) for k, v in (kv.split("=") for kv in args.tuning.split(","))})
         tuning = ctx.dem_get_tuning()
@@ -329,6 +338,7 @@ def main():
     ctx.dem_profile(False)
     cnt, _, _ = ctx.dem_get_contacts()
     zbar = float(cnt.mean())
+    fc = float((cnt > 0).mean())
     ncells = ctx.ncells
     steps_done, builds, entries = ctx.dem_get_counters()
     L = entries / n
@@ -340,7 +350,8 @@ def main():
     kernels = {}
     for name, (nl, tot) in times.items():
         avg = tot / max(nl, 1)
-        b = algorithmic_bytes(name, n, ncells, zbar, L, rsize, passes, fbuild)
+        b = algorithmic_bytes(name, n, ncells, zbar, L, rsize, passes, fbuild, fc,
+                              fbuild / max(1, int(tuning.get("restore_every", 1))))
         kernels[name] = {"launches": nl, "avg_ms": avg, "alg_bytes": b,
                          "gbs": (b / (avg * 1e-3) / 1e9) if avg > 0 and b > 0 else None}
     dom = max(kernels, key=lambda k: kernels[k]["avg_ms"]) if kernels else None
@@ -358,12 +369,12 @@ def main():
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64" if args.precision != "fp64" else "f64", "data": "synthetic",
             "config": {"workload": f"{args.workload} ({bed.n} parcels, {ncells} gas cells, {len(bed.beds)} bed(s))",
-                       "precision": args.precision, "stepping": "CUDA graph of one step, replayed",
+                       "precision": args.precision, "stepping": "CUDA graph of one step, replayed", "settle_steps": args.settle,
                        "l2": "inputs larger than L2 (parcel state and history ~ 1 GB)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "gpu_launches": total_launches, "clocks": ck,
             "kernels": kernels, "step_alg_bytes": step_alg,
-            "step_alg_gbs": step_alg / (step_ms * 1e-3) / 1e9, "zbar_contacts": zbar,
+            "step_alg_gbs": step_alg / (step_ms * 1e-3) / 1e9, "zbar_contacts": zbar, "fraction_in_contact": fc,
             "neighbour_lists": {"mean_length": L, "builds_in_timed_steps": c_post[1] - c_pre[1], "builds_total": builds,
                                 "steps_total": steps_done},
             "tuning": tuning}

@@ -209,11 +209,14 @@ int dem_get_diag(dem_ctx *c, double *out_host);
  *   [1]..[6] block sizes of the key, re-store, pair-search, contact, gas-particle and
  *       gas-cell kernels (multiples of 32 in [32, 1024], and no larger than the kernel's
  *       launch bounds and register use allow: the gas-particle kernel stops at 256);
- *   [7] neighbour-list skin in thousandths of the bed's largest parcel diameter (1..1000).
+ *   [7] neighbour-list skin in thousandths of the bed's largest parcel diameter (1..1000);
+ *   [8] re-store the parcel state in cell order at every k-th neighbour-list build (1..64;
+ *       1 = every build): between re-stores the records stay where they are and the
+ *       search reads them through the sort's permutation.
  * dem_set_tuning validates every value (DEM_EINVAL, nothing changed), drops captured graphs
  * and makes the next step rebuild the neighbour lists; results can then differ from an
  * untuned run in the last bits (order of the force sums), never in the pair sets. */
-enum { DEM_NTUNE = 8 };
+enum { DEM_NTUNE = 9 };
 int dem_get_tuning(dem_ctx *c, int32_t *out);
 int dem_set_tuning(dem_ctx *c, const int32_t *in);
 

@@ -550,7 +550,7 @@ template <class P> __device__ __forceinline__ void mass_add(double *m, int i, ty
     reinterpret_cast<float2 *>(m)[i] = v;
   } else {
     const double mn = m[i] + (double)inc;
-    m[i] = mn > 0.0 ? mn : 0.0;
+    m[i] = __double_as_longlong(mn) < 0 ? 0.0 : mn;   // max(mn, 0) by the sign bit: no FP64 compare
   }
 }
 

@@ -48,6 +48,7 @@ struct dem_ctx {
   int *nl = nullptr, *rebuild = nullptr;   // neighbour lists (storage positions), build flag
   unsigned char *nlc = nullptr;
   double skin_frac = 0.1;         // neighbour-list skin as a fraction of the largest diameter
+  int restore_every = 1;          // re-store the state in cell order at every k-th list build
   double *corner = nullptr;         // cell-corner coordinates: per bed x0+i dx, y0+j dy, z0+k dz
   std::vector<double> hcorner;
   float2 *cornerp = nullptr;        // cell corners relative to the bed corner as FP32 pairs
@@ -75,6 +76,11 @@ struct dem_ctx {
   int bs_contacts = 128, bs_gp = 128, bs_gather = 256, bs_cells = 256, bs_key = 256;
   int use_lists = 1;               // 1: Verlet neighbour lists, 0: cell-list search every step
   int bs_search = 256;
+  int nsm = 152;                   // SMs of the device (one wave of a grid-stride launch)
+  unsigned char *wnear = nullptr;   // per cell: a wall primitive may be within a parcel's reach
+  int *ovf = nullptr, *novf = nullptr;   // parcels whose neighbour list overflowed, and their count
+  uint2 *work = nullptr;           // contact work list (parcel, list-hit mask)
+  int *nwork = nullptr;            // its length
   std::map<std::tuple<int, int, int>, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;
   std::map<std::tuple<int, int, int>, long long> graph_launches;
   cudaStream_t gst = nullptr;     // private stream used to capture graphs

@@ -13,8 +13,10 @@ using dem::DevBed;
 
 namespace dem {
 
-__global__ void k_step_counter(long long *ctr, int *rebuild, int lists) {
+__global__ void k_step_counter(long long *ctr, int *rebuild, int lists, int *nwork, int restore_every) {
   ctr[0] += 1;
+  *nwork = 0;   // the next step's contact work list starts empty
+  if (*rebuild) ctr[4] = ctr[4] + 1 >= restore_every ? 0 : ctr[4] + 1;   // builds since the last re-store
   if (lists && *rebuild) {   // neighbour-list builds, and the list entries of the last one
     ctr[1] += 1;
     ctr[2] = ctr[3];
@@ -23,10 +25,18 @@ __global__ void k_step_counter(long long *ctr, int *rebuild, int lists) {
   *rebuild = 0;   // the lists built this step (if any) are current
 }
 
-__global__ void k_mark_cells(const DevBed *beds, const int *cell_bed, unsigned char *mark, long long ncells) {
+// Solid (IBM-marked) gas cells, and the cells near a wall: those whose parcels may touch a
+// wall primitive. Every primitive's distance is 1-Lipschitz in the position (the plate's
+// is bounded below by |z - z_plate|), so a cell is far from all walls when each distance at
+// its centre exceeds the half-diagonal plus the largest parcel radius plus a margin of
+// 1e-5 m (far above the FP32 error of the contact kernels' wall pre-screen, which would
+// then find nothing within reach either).
+__global__ void k_mark_cells(const DevBed *beds, const BedP<double> *bps, const int *cell_bed, unsigned char *mark,
+                             unsigned char *wnear, long long ncells) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncells) return;
   const DevBed &B = beds[cell_bed[c]];
+  const BedP<double> &bp = bps[cell_bed[c]];
   const long long l = c - B.cell_off;
   const int ix = (int)(l % B.nx), iy = (int)((l / B.nx) % B.ny), iz = (int)(l / ((long long)B.nx * B.ny));
   const double xc = B.x0 + (ix + 0.5) * B.dx, yc = B.y0 + (iy + 0.5) * B.dy, zc = B.z0 + (iz + 0.5) * B.dz;
@@ -35,6 +45,15 @@ __global__ void k_mark_cells(const DevBed *beds, const int *cell_bed, unsigned c
   double sd = B.R_bed - rho;
   if (B.wall == DEM_WALL_CONE) sd = fmin(sd, (zc - B.z_apex) * B.sin_a - rho * B.cos_a);
   mark[c] = sd < -hd ? 1 : 0;
+  const double far = hd + bp.reach_max + 1e-5;
+  bool near = B.R_bed - rho < far || B.H - zc < far;
+  if (B.wall == DEM_WALL_FLAT) {
+    near |= zc < far;
+  } else {
+    if (zc - 0.5 * B.dz < B.plate_z) near |= (zc - B.z_apex) * B.sin_a - rho * B.cos_a < far;
+    near |= fabs(zc - B.plate_z) < far;
+  }
+  wnear[c] = near ? 1 : 0;
 }
 
 // Initial parcel state in input order (accelerations start as gravity, spins at rest).
@@ -343,19 +362,24 @@ void layout(dem_ctx *c, Bump &m) {
   c->nl = m.take<int>(N * KNL);
   c->nlc = m.take<unsigned char>(N);
   c->rebuild = m.take<int>(1);
+  c->ovf = m.take<int>(N);
+  c->novf = m.take<int>(1);
+  c->work = m.take<uint2>(N);
+  c->nwork = m.take<int>(1);
   c->corner = m.take<double>(c->hcorner.size());
   c->cornerp = m.take<float2>(c->hcornerp.size());
   for (int q = 0; q < 3; ++q) { c->F[q] = m.take<char>(N, R); c->Tq[q] = m.take<char>(N, R); }
-  c->src = m.take<char>(N * SR_N, R);
+  c->src = m.take<char>(N * SR_CNT, R);
   c->gas[0] = m.take<double>(C * GS_N);
   c->gas[1] = m.take<double>(C * GS_N);
   c->gp = m.take<char>(C * GP_N, R);
   c->mark = m.take<unsigned char>(C);
+  c->wnear = m.take<unsigned char>(C);
   c->cell_bed = m.take<int>(C);
   c->fv = m.take<double>((size_t)c->nbeds * FOV_CHUNKS * 4);
   c->fvbed = m.take<double>((size_t)c->nbeds * 4);
   c->err = m.take<int>(1);
-  c->step_ctr = m.take<long long>(4);
+  c->step_ctr = m.take<long long>(6);
   c->dbeds = m.take<DevBed>(c->nbeds);
   c->dbp_d = m.take<BedP<double>>(c->nbeds);
   c->dbp_f = m.take<BedP<float>>(c->nbeds);
@@ -378,6 +402,7 @@ void get_tuning(const dem_ctx *c, int32_t *t) {
   t[1] = c->bs_key; t[2] = c->bs_gather; t[3] = c->bs_search; t[4] = c->bs_contacts;
   t[5] = c->bs_gp; t[6] = c->bs_cells;
   t[7] = (int32_t)std::lround(c->skin_frac * 1000.0);
+  t[8] = c->restore_every;
 }
 
 int apply_tuning(dem_ctx *c, const int32_t *t) {
@@ -387,10 +412,12 @@ int apply_tuning(dem_ctx *c, const int32_t *t) {
   for (int k = 1; k <= 6; ++k)
     if (t[k] < 32 || t[k] > 1024 || t[k] % 32 != 0 || t[k] > lim[k - 1]) return DEM_EINVAL;
   if (t[7] < 1 || t[7] > 1000) return DEM_EINVAL;
+  if (t[8] < 1 || t[8] > 64) return DEM_EINVAL;
   c->use_lists = t[0];
   c->bs_key = t[1]; c->bs_gather = t[2]; c->bs_search = t[3]; c->bs_contacts = t[4];
   c->bs_gp = t[5]; c->bs_cells = t[6];
   c->skin_frac = t[7] / 1000.0;
+  c->restore_every = t[8];
   for (int b = 0; b < c->nbeds; ++b) {
     const double dmax = 2.0 * c->hbp_d[b].reach_max;
     set_skin(c->hbp_d[b], c->skin_frac * dmax);
@@ -498,6 +525,11 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
     nb[b]++;
   }
   dem_ctx *c = new dem_ctx();
+  {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+      c->nsm = nsm;
+  }
   c->n = n;
   c->cap = n;
   c->nbeds = n_beds;
@@ -603,13 +635,14 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
   ck(cudaMemsetAsync(c->hcnt[0], 0, (size_t)n, c->st));
   ck(cudaMemsetAsync(c->hcnt[1], 0, (size_t)n, c->st));
   ck(cudaMemsetAsync(c->err, 0, sizeof(int), c->st));
-  ck(cudaMemsetAsync(c->step_ctr, 0, 4 * sizeof(long long), c->st));
+  ck(cudaMemsetAsync(c->step_ctr, 0, 6 * sizeof(long long), c->st));
   // neighbour lists: none yet (the first step builds them); no displacement
   ck(cudaMemsetAsync(c->rebuild, 1, sizeof(int), c->st));
   for (int k = 0; k < 2; ++k) {
     for (int q = 0; q < 3; ++q) ck(cudaMemsetAsync(c->pdsp[k][q], 0, sizeof(float) * (size_t)n, c->st));
   }
   ck(cudaMemsetAsync(c->nlc, 0, (size_t)n, c->st));
+  ck(cudaMemsetAsync(c->nwork, 0, sizeof(int), c->st));
   // gas: cell -> bed, marks, initial state
   {
     std::vector<int> cb(c->ncells);
@@ -642,7 +675,7 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
       ck(cudaMemcpyAsync(dT, T.data(), sizeof(double) * T.size(), cudaMemcpyHostToDevice, c->st));
       const int gg = (int)((c->ncells + 255) / 256);
       k_gas_load<<<gg, 256, 0, c->st>>>(c->ncells, dY, dT, c->gas[0], c->prec != DEM_PREC_FP64);
-      k_mark_cells<<<gg, 256, 0, c->st>>>(c->dbeds, c->cell_bed, c->mark, c->ncells);
+      k_mark_cells<<<gg, 256, 0, c->st>>>(c->dbeds, c->dbp_d, c->cell_bed, c->mark, c->wnear, c->ncells);
     }
     ck(cudaStreamSynchronize(c->st));
     cudaFree(dY);
@@ -1006,7 +1039,7 @@ int dem_autotune(dem_ctx *c, int32_t n_steps) {
     return tot;
   };
   // 1) block sizes, every per-thread kernel at once, each kernel keeping its fastest
-  const char *kname[6] = {"k_key", "k_restore", "k_pair_search", "k_contacts", "k_gas_particle", "k_cells"};
+  const char *kname[6] = {"k_key", "k_restore", "k_pair_search", "k_contact_screen", "k_gas_particle", "k_cells"};
   double bt[6];
   for (int k = 0; k < 6; ++k) bt[k] = 1e300;
   int32_t tb[DEM_NTUNE];
@@ -1042,7 +1075,24 @@ int dem_autotune(dem_ctx *c, int32_t n_steps) {
     }
     if (rc != DEM_OK) best[7] = skin0;
   }
-  // 3) the cell-list search every step (no lists) against the best list configuration
+  // 3) re-store interval (whole-step time over long windows, as the skin)
+  if (rc == DEM_OK) {
+    const int32_t re0 = best[8];
+    double bt_re = 1e300;
+    for (int re : {1, 2, 4, 8}) {
+      int32_t t[DEM_NTUNE];
+      std::memcpy(t, best, sizeof t);
+      t[0] = 1;
+      t[8] = re;
+      std::map<std::string, double> per;
+      const double tot = trial(t, per, 4 * n_steps);
+      if (tot < 0) { rc = DEM_ECUDA; break; }
+      if (tot < bt_re) { bt_re = tot; best[8] = re; }
+    }
+    if (rc != DEM_OK) best[8] = re0;
+    else best_tot = bt_re;
+  }
+  // 4) the cell-list search every step (no lists) against the best list configuration
   best[0] = 1;
   if (rc == DEM_OK) {
     int32_t t[DEM_NTUNE];

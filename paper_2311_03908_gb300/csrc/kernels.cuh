@@ -62,7 +62,7 @@ template <class P> struct StepView {
   const double *corner;         // cell-corner coordinates (see DevBed::corner_off)
   const float2 *cornerp;        // cell corners relative to the bed corner, FP32 pairs
   int *moved;                   // per 1024 sorted positions: keys that changed (re-sort)
-  R *src;                       // [SR_N][cap] per-parcel cell sources
+  R *src;                       // [SR_CNT][cap] per-parcel cell sources (the count is je - jb)
   double *gas, *gas_new;        // [GS_N][ncells]
   R *gp;                        // [GP_N][ncells]
   unsigned char *mark;          // solid (IBM) cell mark
@@ -70,8 +70,13 @@ template <class P> struct StepView {
   double *diag;                 // [DG_N][cap] or null
   double *dep;                  // [ncells][SR_N] or null (written by k_sources)
   int *err;
-  const long long *step_ctr;    // steps completed so far (device)
+  const long long *step_ctr;    // steps completed so far (device); [4] list builds since the last re-store
+  int restore_every;            // the state is re-stored in cell order at every k-th list build
   unsigned long long *list_acc; // list entries of the build in progress
+  int *ovf, *novf;              // parcels whose list overflowed at the last build, and their count
+  uint2 *work;                  // contact work list: (parcel, list-hit mask) ...
+  int *nwork;                   // ... and its length (reset by the step counter)
+  const unsigned char *wnear;   // per cell: a wall may be within a parcel's reach
 };
 
 // total layer mass of parcel i in the form's type (the same sum everywhere it is needed)
@@ -80,6 +85,12 @@ template <class P> __device__ __forceinline__ typename P::R parcel_mass(const PS
 #pragma unroll
   for (int q = 0; q < 4; ++q) s += mass_r<P>(A.m[q], i);
   return s;
+}
+
+// whether this step re-stores the state in cell order: a list-build step that completes
+// restore_every builds since the last re-store (the same answer in every kernel of the step)
+template <class P> __device__ __forceinline__ bool restore_now(const StepView<P> &V) {
+  return *V.rebuild != 0 && V.step_ctr[4] + 1 >= V.restore_every;
 }
 
 __device__ __forceinline__ bool coupled_step(int ncouple, const long long *ctr) {
@@ -256,6 +267,7 @@ template <class P>
 __global__ void k_ranges(StepView<P> V) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V.n) return;
+  if (i == 0 && *V.rebuild) *V.novf = 0;   // a list build lists the overflowed parcels anew
   const unsigned k = V.keys[i];
   if (i == 0 || V.keys[i - 1] != k) V.cstart[k] = (unsigned)i;
   if (i == V.n - 1 || V.keys[i + 1] != k) V.cend[k] = (unsigned)(i + 1);
@@ -265,10 +277,7 @@ __global__ void k_ranges(StepView<P> V) {
 // Re-store (list-build steps, and the first binning): copy every parcel's record, local
 // coordinates, key and history to its sorted position in the scratch buffers ...
 template <class P>
-__global__ void k_restore_out(StepView<P> V, int force) {
-  if (!force && !*V.rebuild) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= V.n) return;
+__device__ __forceinline__ void restore_out_one(const StepView<P> &V, int i) {
   const int j = (int)__ldg(V.vals + i);
   const double x = __ldg(V.A.x + j), y = __ldg(V.A.y + j), z = __ldg(V.A.z + j);
   V.S.x[i] = x; V.S.y[i] = y; V.S.z[i] = z;
@@ -294,12 +303,16 @@ __global__ void k_restore_out(StepView<P> V, int force) {
   }
 }
 
+template <class P>
+__global__ void k_restore_out(StepView<P> V, int force) {
+  if (!force && !restore_now(V)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V.n; i += gridDim.x * blockDim.x)
+    restore_out_one<P>(V, i);
+}
+
 // ... and back into the state, which is then in sorted order (storage = sorted position).
 template <class P>
-__global__ void k_restore_in(StepView<P> V, int force) {
-  if (!force && !*V.rebuild) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= V.n) return;
+__device__ __forceinline__ void restore_in_one(const StepView<P> &V, int i) {
   V.A.x[i] = V.S.x[i]; V.A.y[i] = V.S.y[i]; V.A.z[i] = V.S.z[i];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
@@ -324,6 +337,13 @@ __global__ void k_restore_in(StepView<P> V, int force) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) V.H.xi[(size_t)(s * 3 + q) * V.cap + i] = V.Hs.xi[(size_t)(s * 3 + q) * V.cap + i];
   }
+}
+
+template <class P>
+__global__ void k_restore_in(StepView<P> V, int force) {
+  if (!force && !restore_now(V)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V.n; i += gridDim.x * blockDim.x)
+    restore_in_one<P>(V, i);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -369,9 +389,9 @@ __device__ __forceinline__ void add_contact(const StepView<P> &V, int i, int cin
 // visiting order (dz, dy, dx, sorted position), to a per-parcel hit list, and on build steps
 // the partners within r_i + r_j + skin to the parcel's neighbour list. Few registers, so many
 // warps hide the load latency of the pair loop.
-// parcel_contacts (k_contacts): the list test between builds, the contact law
-// for the pairs (the FP64 form first re-tests each pair on the FP64 positions with the
-// oracle's expression, so its pair sets are bit-exact), and the walls.
+// k_contact_screen / k_contact_forces: the list test between builds, the contact law for the
+// pairs (the FP64 form first re-tests each pair on the FP64 positions with the oracle's
+// expression, so its pair sets are bit-exact), and the walls.
 // ---------------------------------------------------------------------------------------
 // cell offsets (dx, dy, dz) of the cell with key k2 relative to the cell with key k1
 __device__ __forceinline__ void key_offset(const DevBed &B, unsigned k1, unsigned k2, int &dx, int &dy, int &dz) {
@@ -393,16 +413,11 @@ __device__ __forceinline__ void key_offset(const DevBed &B, unsigned k1, unsigne
 }
 
 template <class P>
-__global__ void k_pair_search(StepView<P> V) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= V.n) return;
+__device__ __forceinline__ void pair_search(const StepView<P> &V, int i, bool rebuild, bool restored) {
   const int b = V.A.meta[i] >> 8;
   const DevBed &B = V.beds[b];
   const BedP<typename P::R> &bp = V.bp[b];
   const size_t cap = (size_t)V.cap;
-  const bool rebuild = *V.rebuild != 0;
-  // between rebuilds the parcels with a list are tested by parcel_contacts
-  if (!V.nolists && !rebuild && V.nlc[i] != NL_OVERFLOW) return;
   const bool build = rebuild && !V.nolists;
   int nh = 0, nn = 0;
   if (!(bp.flags & DEM_NO_CONTACTS)) {
@@ -450,7 +465,7 @@ __global__ void k_pair_search(StepView<P> V) {
       ++nh;                                                                           \
     }                                                                                 \
   } while (0)
-            if (rebuild) {
+            if (restored) {
               // just re-stored: storage position = sorted position
               int jj = (int)jb;
               for (; jj + 4 <= (int)je; jj += 4) {
@@ -484,12 +499,27 @@ __global__ void k_pair_search(StepView<P> V) {
   }
   if (build) {
     V.nlc[i] = (unsigned char)(nn > KNL ? NL_OVERFLOW : nn);
+    if (nn > KNL) V.ovf[atomicAdd(V.novf, 1)] = i;   // searched again every step until the next build
     const unsigned am = __activemask();   // one atomic per group of lanes running together
     const unsigned tot = __reduce_add_sync(am, (unsigned)min(nn, KNL));
     if ((threadIdx.x & 31) == __ffs(am) - 1) atomicAdd(V.list_acc, (unsigned long long)tot);
   }
   if (nh > KLIST) { set_error(V.err, ERR_CAPACITY); nh = KLIST; }
   V.pcnt[i] = (unsigned char)nh;
+}
+
+// The cell-list search: every parcel on list-build steps (and every step with the lists
+// off), otherwise only the parcels whose list overflowed at the last build (their storage
+// positions do not change between builds). Grid-stride over at most one wave of blocks, so
+// that the steps between builds cost one flag read per block.
+template <class P>
+__global__ void k_pair_search(StepView<P> V) {
+  const bool rebuild = *V.rebuild != 0;
+  const bool restored = restore_now(V);
+  const bool all = rebuild || V.nolists;
+  const int cnt = all ? V.n : *V.novf;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x)
+    pair_search<P>(V, all ? t : V.ovf[t], rebuild, restored);
 }
 
 // Contact of parcel i with partner j (storage positions; code = cell offset of j's cell):
@@ -534,123 +564,176 @@ __device__ __forceinline__ void pair_contact(const StepView<P> &V, int i, int j,
   add_contact<P>(V, i, cin, V.A.orig[j], bp, mstar, ri, nrm, delta, vrel, wi, Fi, Ti, cout);
 }
 
-// All contact forces on parcel i: its partners -- tested here against the neighbour list
-// (between list builds; pairs in list order), or taken from the cell-list search's hit list
-// (build steps, overflowed lists, no lists) -- then the walls (FP32 pre-screen, FP64
-// distances within reach). Writes the parcel's new contact history. The parcel's own state
-// is read only when it has a candidate partner or a wall within reach.
+// Contacts in two passes. The screen pass runs over every parcel: the neighbour-list test
+// (between list builds; hits kept as a mask over the list entries), the search hits of
+// build steps (and of overflowed lists, or with the lists off), and an FP32 wall
+// pre-screen in the cells that may hold a parcel within reach of a wall. Parcels with none
+// of these get an empty contact history at once; the others are appended to a work list,
+// so that the force pass runs on dense warps of parcels that have something to evaluate (a
+// few per cent of them) instead of leaving most lanes of most warps idle. Results do not
+// depend on the order of the work list: each entry writes only its own parcel's forces and
+// history.
 template <class P>
-__device__ __forceinline__ void parcel_contacts(const StepView<P> &V, int i, int meta, typename P::R Fi[3],
-                                                typename P::R Ti[3]) {
+__device__ __forceinline__ bool wall_near(const StepView<P> &V, const DevBed &B, const BedP<typename P::R> &bp,
+                                          unsigned key, const float4 &me) {
+  if (!V.wnear[key]) return false;
+  int X, Y, Z;
+  key_cell(B, key, X, Y, Z);
+  const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
+  const float xa = (float)bp.x0 + X * hx + me.x, ya = (float)bp.y0 + Y * hy + me.y, za = (float)bp.z0 + Z * hz + me.z;
+  float distf[4], nwf[4][3];
+  wall_primitives<float>(bp, xa, ya, za, distf, nwf);
+  bool near = false;
+#pragma unroll
+  for (int p = 0; p < 4; ++p) near |= distf[p] < me.w + 1e-6f;
+  return near;
+}
+
+template <class P>
+__device__ __forceinline__ bool contact_screen(const StepView<P> &V, int i, unsigned &hits) {
+  const int meta = V.A.meta[i];
+  const DevBed &B = V.beds[meta >> 8];
+  const BedP<typename P::R> &bp = V.bp[meta >> 8];
+  hits = 0u;
+  if (bp.flags & DEM_NO_CONTACTS) return false;
+  const float4 me = V.xl[i];
+  const unsigned key = V.keyp[i];
+  const bool near = wall_near<P>(V, B, bp, key, me);
+  const int listed = V.nlc[i];
+  const bool searched = *V.rebuild || V.nolists || listed == NL_OVERFLOW;
+  if (searched) return near || V.pcnt[i] != 0;
+  const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
+  const size_t cap = (size_t)V.cap;
+  const float pm = P::exact ? (float)bp.pf_margin : 0.f;
+  for (int k0 = 0; k0 < listed; k0 += 4) {
+    int j[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) j[u] = k0 + u < listed ? V.nl[(k0 + u) * cap + i] : -1;
+    unsigned kj[4];
+    float4 o[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      kj[u] = j[u] >= 0 ? V.keyp[j[u]] : key;
+      o[u] = j[u] >= 0 ? __ldg(V.xl + j[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (j[u] < 0) continue;
+      int dx, dy, dz;
+      key_offset(B, key, kj[u], dx, dy, dz);
+      if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) continue;   // cannot touch
+      const float ex = o[u].x + (dx * hx - me.x), ey = o[u].y + (dy * hy - me.y), ez = o[u].z + (dz * hz - me.z);
+      const float d2 = ex * ex + ey * ey + ez * ez;
+      const float lim = me.w + o[u].w + pm;
+      if (d2 < lim * lim) hits |= 1u << (k0 + u);
+    }
+  }
+  return near || hits != 0u;
+}
+
+// All contact forces on a parcel of the work list: its partners (the list hits in list
+// order, or the search hits), then the walls (FP64 distances for the primitives within
+// reach). Writes the parcel's new contact history; returns its number of contacts.
+template <class P>
+__device__ __forceinline__ int contact_forces(const StepView<P> &V, int i, unsigned hits, typename P::R Fi[3],
+                                              typename P::R Ti[3]) {
   using R = typename P::R;
+  const int meta = V.A.meta[i];
   const DevBed &B = V.beds[meta >> 8];
   const BedP<R> &bp = V.bp[meta >> 8];
 #pragma unroll
   for (int q = 0; q < 3; ++q) { Fi[q] = 0; Ti[q] = 0; }
   int cout = 0;
-  if (!(bp.flags & DEM_NO_CONTACTS)) {
-    const int cin = V.H.cnt[i];
-    const float4 me = V.xl[i];
-    const unsigned key = V.keyp[i];
-    int X, Y, Z;
-    key_cell(B, key, X, Y, Z);
-    const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
-    const float xa = (float)bp.x0 + X * hx + me.x, ya = (float)bp.y0 + Y * hy + me.y, za = (float)bp.z0 + Z * hz + me.z;
-    float distf[4], nwf[4][3];
-    wall_primitives<float>(bp, xa, ya, za, distf, nwf);
-    bool near = false;
-#pragma unroll
-    for (int p = 0; p < 4; ++p) near |= distf[p] < me.w + 1e-6f;
-    const int listed = V.nlc[i];
-    const bool searched = *V.rebuild || V.nolists || listed == NL_OVERFLOW;
-    const size_t cap = (size_t)V.cap;
-    // between builds: the list test first, hits recorded as a mask over the list entries
-    unsigned hits = 0u;
-    if (!searched) {
-      const float pm = P::exact ? (float)bp.pf_margin : 0.f;
-      for (int k0 = 0; k0 < listed; k0 += 4) {
-        int j[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) j[u] = k0 + u < listed ? V.nl[(k0 + u) * cap + i] : -1;
-        unsigned kj[4];
-        float4 o[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          kj[u] = j[u] >= 0 ? V.keyp[j[u]] : key;
-          o[u] = j[u] >= 0 ? __ldg(V.xl + j[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (j[u] < 0) continue;
-          int dx, dy, dz;
-          key_offset(B, key, kj[u], dx, dy, dz);
-          if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) continue;   // cannot touch
-          const float ex = o[u].x + (dx * hx - me.x), ey = o[u].y + (dy * hy - me.y), ez = o[u].z + (dz * hz - me.z);
-          const float d2 = ex * ex + ey * ey + ez * ez;
-          const float lim = me.w + o[u].w + pm;
-          if (d2 < lim * lim) hits |= 1u << (k0 + u);
-        }
-      }
-    }
-    const int nsearch = searched ? (int)V.pcnt[i] : 0;
-    if (hits != 0u || nsearch > 0 || near) {
-      const R di = V.A.d[i];
-      const R mi = parcel_mass<P>(V.A, i);
-      const R vi[3] = {V.A.v[0][i], V.A.v[1][i], V.A.v[2][i]};
-      const R wi[3] = {V.A.w[0][i], V.A.w[1][i], V.A.w[2][i]};
-      double xi_d[3] = {0, 0, 0}, ri_d = 0;
-      if constexpr (P::exact) {
-        xi_d[0] = V.A.x[i]; xi_d[1] = V.A.y[i]; xi_d[2] = V.A.z[i];
-        ri_d = __dmul_rn(0.5, __dmul_rn(B.k, (double)di));
-      }
-      const R ri = P::exact ? (R)ri_d : (R)me.w;
-      for (int h = 0; h < nsearch; ++h)
-        pair_contact<P>(V, i, V.plist[h * cap + i], V.pcode[h * cap + i], B, bp, me, hx, hy, hz, xi_d, ri_d, ri, mi,
-                        vi, wi, cin, Fi, Ti, cout);
-      while (hits) {   // list order
-        const int k = __ffs(hits) - 1;
-        hits &= hits - 1u;
-        const int j = V.nl[k * cap + i];
-        int dx, dy, dz;
-        key_offset(B, key, V.keyp[j], dx, dy, dz);
-        pair_contact<P>(V, i, j, (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1), B, bp, me, hx, hy, hz, xi_d, ri_d, ri, mi,
-                        vi, wi, cin, Fi, Ti, cout);
-      }
-      if (near) {
-        const double xd = pos_abs<P>(V.A.x, i, B.x0), yd = pos_abs<P>(V.A.y, i, B.y0), zd = pos_abs<P>(V.A.z, i, B.z0);
-        const double rid = __dmul_rn(0.5, __dmul_rn(B.k, (double)di));
-        double dist[4], nw[4][3];
-        wall_primitives<double>(B, xd, yd, zd, dist, nw);
-        for (int p = 0; p < 4; ++p) {
-          const double gap = rid - dist[p];
-          if (!(gap > 0.0)) continue;
-          const R nrm[3] = {(R)-nw[p][0], (R)-nw[p][1], (R)-nw[p][2]};
-          const R delta = (R)gap;
-          const R wr[3] = {ri * wi[0], ri * wi[1], ri * wi[2]};
-          R vrel[3];
-          vrel[0] = vi[0] + (wr[1] * nrm[2] - wr[2] * nrm[1]);
-          vrel[1] = vi[1] + (wr[2] * nrm[0] - wr[0] * nrm[2]);
-          vrel[2] = vi[2] + (wr[0] * nrm[1] - wr[1] * nrm[0]);
-          add_contact<P>(V, i, cin, -1 - p, bp, mi, ri, nrm, delta, vrel, wi, Fi, Ti, cout);
-        }
-      }
+  const int cin = V.H.cnt[i];
+  const float4 me = V.xl[i];
+  const unsigned key = V.keyp[i];
+  const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
+  const size_t cap = (size_t)V.cap;
+  const int listed = V.nlc[i];
+  const bool searched = *V.rebuild || V.nolists || listed == NL_OVERFLOW;
+  const int nsearch = searched ? (int)V.pcnt[i] : 0;
+  const R di = V.A.d[i];
+  const R mi = parcel_mass<P>(V.A, i);
+  const R vi[3] = {V.A.v[0][i], V.A.v[1][i], V.A.v[2][i]};
+  const R wi[3] = {V.A.w[0][i], V.A.w[1][i], V.A.w[2][i]};
+  double xi_d[3] = {0, 0, 0}, ri_d = 0;
+  if constexpr (P::exact) {
+    xi_d[0] = V.A.x[i]; xi_d[1] = V.A.y[i]; xi_d[2] = V.A.z[i];
+    ri_d = __dmul_rn(0.5, __dmul_rn(B.k, (double)di));
+  }
+  const R ri = P::exact ? (R)ri_d : (R)me.w;
+  for (int h = 0; h < nsearch; ++h)
+    pair_contact<P>(V, i, V.plist[h * cap + i], V.pcode[h * cap + i], B, bp, me, hx, hy, hz, xi_d, ri_d, ri, mi,
+                    vi, wi, cin, Fi, Ti, cout);
+  while (hits) {   // list order
+    const int k = __ffs(hits) - 1;
+    hits &= hits - 1u;
+    const int j = V.nl[k * cap + i];
+    int dx, dy, dz;
+    key_offset(B, key, V.keyp[j], dx, dy, dz);
+    pair_contact<P>(V, i, j, (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1), B, bp, me, hx, hy, hz, xi_d, ri_d, ri, mi,
+                    vi, wi, cin, Fi, Ti, cout);
+  }
+  // walls: the FP32 pre-screen again, FP64 distances for the primitives within reach
+  if (!(bp.flags & DEM_NO_CONTACTS) && wall_near<P>(V, B, bp, key, me)) {
+    const double xd = pos_abs<P>(V.A.x, i, B.x0), yd = pos_abs<P>(V.A.y, i, B.y0), zd = pos_abs<P>(V.A.z, i, B.z0);
+    const double rid = __dmul_rn(0.5, __dmul_rn(B.k, (double)di));
+    double dist[4], nw[4][3];
+    wall_primitives<double>(B, xd, yd, zd, dist, nw);
+    for (int p = 0; p < 4; ++p) {
+      const double gap = rid - dist[p];
+      if (!(gap > 0.0)) continue;
+      const R nrm[3] = {(R)-nw[p][0], (R)-nw[p][1], (R)-nw[p][2]};
+      const R delta = (R)gap;
+      const R wr[3] = {ri * wi[0], ri * wi[1], ri * wi[2]};
+      R vrel[3];
+      vrel[0] = vi[0] + (wr[1] * nrm[2] - wr[2] * nrm[1]);
+      vrel[1] = vi[1] + (wr[2] * nrm[0] - wr[0] * nrm[2]);
+      vrel[2] = vi[2] + (wr[0] * nrm[1] - wr[1] * nrm[0]);
+      add_contact<P>(V, i, cin, -1 - p, bp, mi, ri, nrm, delta, vrel, wi, Fi, Ti, cout);
     }
   }
   V.Hn.cnt[i] = (unsigned char)cout;
   if (V.diag) V.diag[(size_t)DG_NCONTACT * V.cap + i] = (double)cout;
+  return cout;
 }
 
-// Contact force and torque of every parcel. A kernel of its own: the partners' half-step
-// velocities, spins and masses must all be read before k_gas_particle updates them.
+// Screen pass: one thread per parcel; a warp appends its parcels with work in one atomic.
 template <class P>
-__global__ void k_contacts(StepView<P> V) {
-  using R = typename P::R;
+__global__ void k_contact_screen(StepView<P> V) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= V.n) return;
-  R F[3], Tq[3];
-  parcel_contacts<P>(V, i, V.A.meta[i], F, Tq);
+  unsigned hits = 0u;
+  bool work = false;
+  if (i < V.n) {
+    work = contact_screen<P>(V, i, hits);
+    if (!work) {
+      V.Hn.cnt[i] = 0;
+      if (V.diag) V.diag[(size_t)DG_NCONTACT * V.cap + i] = 0.0;
+    }
+  }
+  const unsigned bal = __ballot_sync(0xffffffffu, work);
+  if (bal == 0u) return;
+  const int lane = threadIdx.x & 31, lead = __ffs(bal) - 1;
+  int base = 0;
+  if (lane == lead) base = atomicAdd(V.nwork, __popc(bal));
+  base = __shfl_sync(0xffffffffu, base, lead);
+  if (work) V.work[base + __popc(bal & ((1u << lane) - 1u))] = make_uint2((unsigned)i, hits);
+}
+
+// Force pass over the work list (grid-stride over at most one wave of blocks). Force and
+// torque are written only for parcels in contact; k_gas_particle reads them only there.
+template <class P>
+__global__ void k_contact_forces(StepView<P> V) {
+  using R = typename P::R;
+  const int cnt = *V.nwork;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
+    const uint2 w = V.work[t];
+    const int i = (int)w.x;
+    R F[3], Tq[3];
+    if (contact_forces<P>(V, i, w.y, F, Tq) == 0) continue;
 #pragma unroll
-  for (int q = 0; q < 3; ++q) { V.F[q][i] = F[q]; V.Tq[q][i] = Tq[q]; }
+    for (int q = 0; q < 3; ++q) { V.F[q][i] = F[q]; V.Tq[q][i] = Tq[q]; }
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -665,8 +748,11 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V.n) return;
   const int meta = V.A.meta[i];
-  const R F[3] = {V.F[0][i], V.F[1][i], V.F[2][i]};
-  const R Tq[3] = {V.Tq[0][i], V.Tq[1][i], V.Tq[2][i]};
+  R F[3] = {0, 0, 0}, Tq[3] = {0, 0, 0};
+  if (V.Hn.cnt[i] != 0) {   // the contact kernel wrote them only for parcels in contact
+#pragma unroll
+    for (int q = 0; q < 3; ++q) { F[q] = V.F[q][i]; Tq[q] = V.Tq[q][i]; }
+  }
   const int ore = meta & 255;
   const BedP<R> &bp = V.bp[meta >> 8];
   const unsigned fl = bp.flags;
@@ -746,7 +832,6 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
   s[SR_QR * cp + i] = kn.Qr;
   s[SR_EQ * cp + i] = kn.EQ;
   s[SR_ES * cp + i] = kn.ES;
-  s[SR_CNT * cp + i] = (R)1;
   if (V.diag) {
     double *dg = V.diag;
 #pragma unroll
@@ -794,13 +879,13 @@ template <class P> struct CellSum {
   S s[SR_N];
   __device__ __forceinline__ void run(const S *src, size_t cp, const unsigned *vals, unsigned jb, unsigned je) {
     if constexpr (!P::exact) {
-      float cc[SR_N];
+      float cc[SR_CNT];
 #pragma unroll
-      for (int f = 0; f < SR_N; ++f) { s[f] = 0.f; cc[f] = 0.f; }
+      for (int f = 0; f < SR_CNT; ++f) { s[f] = 0.f; cc[f] = 0.f; }
       for (unsigned jj = jb; jj < je; ++jj) {
         const unsigned j = vals[jj];
 #pragma unroll
-        for (int f = 0; f < SR_N; ++f) {
+        for (int f = 0; f < SR_CNT; ++f) {
           const float y = src[f * cp + j] - cc[f];
           const float t = s[f] + y;
           cc[f] = (t - s[f]) - y;
@@ -808,16 +893,17 @@ template <class P> struct CellSum {
         }
       }
 #pragma unroll
-      for (int f = 0; f < SR_N; ++f) s[f] -= cc[f];
+      for (int f = 0; f < SR_CNT; ++f) s[f] -= cc[f];
     } else {
 #pragma unroll
-      for (int f = 0; f < SR_N; ++f) s[f] = 0.0;
+      for (int f = 0; f < SR_CNT; ++f) s[f] = 0.0;
       for (unsigned jj = jb; jj < je; ++jj) {
         const unsigned j = vals[jj];
 #pragma unroll
-        for (int f = 0; f < SR_N; ++f) s[f] += src[f * cp + j];
+        for (int f = 0; f < SR_CNT; ++f) s[f] += src[f * cp + j];
       }
     }
+    s[SR_CNT] = (S)(je - jb);
   }
 };
 
@@ -1132,6 +1218,6 @@ __global__ void k_scatter_hist(StepView<P> V, int *cnt, int *partner, double *xi
 }
 
 __global__ void k_mark_cells(const DevBed *beds, const int *cell_bed, unsigned char *mark, long long ncells);
-__global__ void k_step_counter(long long *ctr, int *rebuild, int lists);
+__global__ void k_step_counter(long long *ctr, int *rebuild, int lists, int *nwork, int restore_every);
 
 }  // namespace dem

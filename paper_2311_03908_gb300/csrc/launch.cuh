@@ -7,6 +7,11 @@
 namespace dem {
 
 inline int grid_for(long long n, int bs) { return (int)((n + bs - 1) / bs); }
+// grid of a grid-stride kernel: at most one wave of full-occupancy blocks
+inline int grid_wave(const dem_ctx *c, long long n, int bs) {
+  const int g = grid_for(n, bs), w = c->nsm * (2048 / bs);
+  return g < w ? g : w;
+}
 
 template <class P>
 StepView<P> make_view(dem_ctx *c, bool for_step) {
@@ -69,7 +74,13 @@ StepView<P> make_view(dem_ctx *c, bool for_step) {
   V.dep = c->dep;
   V.err = c->err;
   V.step_ctr = c->step_ctr;
+  V.restore_every = c->restore_every;
   V.list_acc = (unsigned long long *)(c->step_ctr + 3);
+  V.ovf = c->ovf;
+  V.novf = c->novf;
+  V.work = c->work;
+  V.nwork = c->nwork;
+  V.wnear = c->wnear;
   return V;
 }
 
@@ -124,8 +135,8 @@ int enqueue_binning(dem_ctx *c, int drift) {
     c->launches += 2;
   }
   ps = prof_begin(c, "k_restore");
-  k_restore_out<P><<<grid_for(c->n, c->bs_gather), c->bs_gather, 0, st>>>(V, drift ? 0 : 1);
-  k_restore_in<P><<<grid_for(c->n, c->bs_gather), c->bs_gather, 0, st>>>(V, drift ? 0 : 1);
+  k_restore_out<P><<<grid_wave(c, c->n, c->bs_gather), c->bs_gather, 0, st>>>(V, drift ? 0 : 1);
+  k_restore_in<P><<<grid_wave(c, c->n, c->bs_gather), c->bs_gather, 0, st>>>(V, drift ? 0 : 1);
   prof_end(c, ps);
   c->launches += 2;
   return (int)cudaPeekAtLastError();
@@ -142,10 +153,13 @@ int enqueue_steps(dem_ctx *c, int nsteps) {
     // the cell-list search (list builds, overflowed lists, no lists; otherwise a no-op), the
     // contact forces (with the list test between builds), then the gas-particle terms
     ps = prof_begin(c, "k_pair_search");
-    k_pair_search<P><<<grid_for(c->n, c->bs_search), c->bs_search, 0, st>>>(V);
+    k_pair_search<P><<<grid_wave(c, c->n, c->bs_search), c->bs_search, 0, st>>>(V);
     prof_end(c, ps);
-    ps = prof_begin(c, "k_contacts");
-    k_contacts<P><<<grid_for(c->n, c->bs_contacts), c->bs_contacts, 0, st>>>(V);
+    ps = prof_begin(c, "k_contact_screen");
+    k_contact_screen<P><<<grid_for(c->n, c->bs_contacts), c->bs_contacts, 0, st>>>(V);
+    prof_end(c, ps);
+    ps = prof_begin(c, "k_contact_forces");
+    k_contact_forces<P><<<grid_wave(c, c->n, 128), 128, 0, st>>>(V);
     prof_end(c, ps);
     ps = prof_begin(c, "k_gas_particle");
     k_gas_particle<P><<<grid_for(c->n, c->bs_gp), c->bs_gp, 0, st>>>(V);
@@ -153,8 +167,8 @@ int enqueue_steps(dem_ctx *c, int nsteps) {
     ps = prof_begin(c, "k_cells");
     k_cells<P><<<grid_for(c->ncells, c->bs_cells), c->bs_cells, 0, st>>>(V, 0);
     prof_end(c, ps);
-    k_step_counter<<<1, 1, 0, st>>>(c->step_ctr, c->rebuild, c->use_lists);
-    c->launches += 5;
+    k_step_counter<<<1, 1, 0, st>>>(c->step_ctr, c->rebuild, c->use_lists, c->nwork, c->restore_every);
+    c->launches += 6;
     e = (int)cudaPeekAtLastError();
     if (e) return e;
     c->cur = 1 - c->cur;
@@ -228,7 +242,7 @@ int enqueue_props(dem_ctx *c) {
 template <class P>
 int kernel_limits(int *lim) {
   const void *fn[6] = {(const void *)k_key<P>, (const void *)k_restore_out<P>, (const void *)k_pair_search<P>,
-                       (const void *)k_contacts<P>, (const void *)k_gas_particle<P>, (const void *)k_cells<P>};
+                       (const void *)k_contact_screen<P>, (const void *)k_gas_particle<P>, (const void *)k_cells<P>};
   for (int k = 0; k < 6; ++k) {
     cudaFuncAttributes a;
     if (cudaFuncGetAttributes(&a, fn[k]) != cudaSuccess) return -1;

@@ -1,5 +1,5 @@
 """Launch configurations of the step -- neighbour lists or the cell-list search every step,
-block sizes, neighbour-list skin -- and the autotuner. Each configuration
+block sizes, neighbour-list skin, re-store interval -- and the autotuner. Each configuration
 computes the same step, so each is held to the FP64 oracle: pair sets bit-exact, states to
 relative 1e-7 over several list rebuilds."""
 import numpy as np
@@ -30,12 +30,13 @@ def _pairs(cnt, partner):
     return {(i, int(partner[i, k])) for i in range(len(cnt)) for k in range(cnt[i])}
 
 
-@pytest.mark.parametrize("lists,skin,bs", [(1, 100, 128), (1, 5, 64), (1, 600, 256), (0, 100, 256)])
-def test_contact_configurations_match_oracle(lists, skin, bs):
+@pytest.mark.parametrize("lists,skin,bs,every", [(1, 100, 128, 1), (1, 5, 64, 3), (1, 600, 256, 1), (0, 100, 256, 1),
+                                               (1, 50, 128, 64)])
+def test_contact_configurations_match_oracle(lists, skin, bs, every):
     bed = synth.small_packed(seed=21, n=3000, v_scale=0.3, wall_kind=synth.WALL_CONE)
     ctx = _ctx(bed)
     ctx.dem_set_tuning(neighbour_lists=lists, skin_permille=skin, bs_key=bs, bs_restore=bs, bs_search=bs,
-                       bs_contacts=bs, bs_gas_particle=bs, bs_cells=bs)
+                       bs_contacts=bs, bs_gas_particle=bs, bs_cells=bs, restore_every=every)
     ref = oracle.Oracle(bed)
     for _ in range(4):
         ctx.dem_step(15)
@@ -75,7 +76,8 @@ def test_set_tuning_rejects_invalid_values():
     assert set(t0) == set(binding.TUNING_KEYS)
     # the gas-particle kernel launches at most 256 threads per block (launch bounds)
     for bad in (dict(neighbour_lists=2), dict(bs_key=48), dict(bs_cells=2048), dict(bs_search=0),
-                dict(skin_permille=0), dict(skin_permille=1001), dict(bs_gas_particle=1024)):
+                dict(skin_permille=0), dict(skin_permille=1001), dict(bs_gas_particle=1024),
+                dict(restore_every=0), dict(restore_every=65)):
         with pytest.raises(binding.DemError) as e:
             ctx.dem_set_tuning(**bad)
         assert e.value.status == binding.DEM_EINVAL
