@@ -12,6 +12,7 @@
 #include <stdint.h>
 
 #include "../../include/dem.h"
+#include "pdl.cuh"
 
 namespace dem {
 

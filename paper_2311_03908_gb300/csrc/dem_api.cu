@@ -14,6 +14,7 @@ using dem::DevBed;
 namespace dem {
 
 __global__ void k_step_counter(long long *ctr, int *rebuild, int lists, int *nwork, int restore_every) {
+  pdl_wait();
   ctr[0] += 1;
   *nwork = 0;   // the next step's contact work list starts empty
   if (*rebuild) ctr[4] = ctr[4] + 1 >= restore_every ? 0 : ctr[4] + 1;   // builds since the last re-store

@@ -173,9 +173,14 @@ __device__ __forceinline__ float4 local_coords(const StepView<P> &V, const DevBe
 // position: FP64 floor((x - x0) / dx), or in the split-Kahan form the pair comparison.
 template <class P>
 __global__ void k_key(StepView<P> V, int drift) {
+  pdl_wait();
   using R = typename P::R;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V.n) return;
+  if (drift) {   // empty the previous step's cell ranges (k_ranges writes this step's)
+    const unsigned kp = V.keys_prev[i];
+    if (i == 0 || V.keys_prev[i - 1] != kp) { V.cstart[kp] = 0u; V.cend[kp] = 0u; }
+  }
   const int b = V.A.meta[i] >> 8;
   const DevBed &B = V.beds[b];
   const BedP<R> &bp = V.bp[b];
@@ -265,13 +270,17 @@ __global__ void k_key(StepView<P> V, int drift) {
 // position (the next step's key kernel scatters its keys through it).
 template <class P>
 __global__ void k_ranges(StepView<P> V) {
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V.n) return;
   if (i == 0 && *V.rebuild) *V.novf = 0;   // a list build lists the overflowed parcels anew
   const unsigned k = V.keys[i];
   if (i == 0 || V.keys[i - 1] != k) V.cstart[k] = (unsigned)i;
   if (i == V.n - 1 || V.keys[i + 1] != k) V.cend[k] = (unsigned)(i + 1);
-  V.inv[V.vals[i]] = (unsigned)i;
+  const unsigned j = V.vals[i];
+  V.inv[j] = (unsigned)i;
+  // a search of every parcel without a re-store reads the local coordinates in sorted order
+  if ((*V.rebuild || V.nolists) && !restore_now(V)) V.xls[i] = V.xl[j];
 }
 
 // Re-store (list-build steps, and the first binning): copy every parcel's record, local
@@ -305,6 +314,7 @@ __device__ __forceinline__ void restore_out_one(const StepView<P> &V, int i) {
 
 template <class P>
 __global__ void k_restore_out(StepView<P> V, int force) {
+  pdl_wait();
   if (!force && !restore_now(V)) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V.n; i += gridDim.x * blockDim.x)
     restore_out_one<P>(V, i);
@@ -341,6 +351,7 @@ __device__ __forceinline__ void restore_in_one(const StepView<P> &V, int i) {
 
 template <class P>
 __global__ void k_restore_in(StepView<P> V, int force) {
+  pdl_wait();
   if (!force && !restore_now(V)) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V.n; i += gridDim.x * blockDim.x)
     restore_in_one<P>(V, i);
@@ -413,7 +424,7 @@ __device__ __forceinline__ void key_offset(const DevBed &B, unsigned k1, unsigne
 }
 
 template <class P>
-__device__ __forceinline__ void pair_search(const StepView<P> &V, int i, bool rebuild, bool restored) {
+__device__ __forceinline__ void pair_search(const StepView<P> &V, int i, bool rebuild, bool restored, bool copy) {
   const int b = V.A.meta[i] >> 8;
   const DevBed &B = V.beds[b];
   const BedP<typename P::R> &bp = V.bp[b];
@@ -423,8 +434,12 @@ __device__ __forceinline__ void pair_search(const StepView<P> &V, int i, bool re
   if (!(bp.flags & DEM_NO_CONTACTS)) {
     const float4 me = V.xl[i];
     const unsigned key = V.keyp[i];
+    const int si = (int)V.inv[i];   // the parcel's own sorted position
     const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
     const float pm = P::exact ? (float)bp.pf_margin : 0.f;
+    // the candidates' records in sorted order: the state itself just after a re-store, else
+    // the copy k_ranges gathered on a search-all step; otherwise through the permutation
+    const float4 *xs = restored ? V.xl : V.xls;
     {
       // cell-list path (list rebuild, or a parcel whose list overflowed)
       const float skin = build ? (float)bp.skin : 0.f;
@@ -447,44 +462,76 @@ __device__ __forceinline__ void pair_search(const StepView<P> &V, int i, bool re
             const unsigned jb = __ldg(V.cstart + krow + dx), je = __ldg(V.cend + krow + dx);
             const float ox = dx * hx - me.x;
             const unsigned char code = (unsigned char)((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
-#define DEM_PAIR_TEST(o, j)                                                           \
+// test of the candidate at sorted position s, storage position js
+#define DEM_PAIR_TEST(o, s, js)                                                       \
   do {                                                                                \
     const float ex = (o).x + ox, ey = (o).y + oy, ez = (o).z + oz; /* x_j - x_i */   \
     const float d2 = ex * ex + ey * ey + ez * ez;                                     \
     const float rs = me.w + (o).w;                                                    \
     const float lim = rs + pm, liml = rs + skin;                                      \
-    if (build && d2 < liml * liml && (j) != i) {                                      \
-      if (nn < KNL) V.nl[nn * cap + i] = (j);                                         \
-      ++nn;                                                                           \
-    }                                                                                 \
-    if (d2 < lim * lim && (j) != i) {                                                 \
-      if (nh < KLIST) {                                                               \
-        V.plist[nh * cap + i] = (j);                                                  \
-        V.pcode[nh * cap + i] = code;                                                 \
+    const bool inl = build && d2 < liml * liml, inh = d2 < lim * lim;                 \
+    if ((inl || inh) && (s) != si) {                                                  \
+      const int j = (js);                                                             \
+      if (inl) {                                                                      \
+        if (nn < KNL) V.nl[nn * cap + i] = j;                                         \
+        ++nn;                                                                         \
       }                                                                               \
-      ++nh;                                                                           \
+      if (inh) {                                                                      \
+        if (nh < KLIST) {                                                             \
+          V.plist[nh * cap + i] = j;                                                  \
+          V.pcode[nh * cap + i] = code;                                               \
+        }                                                                             \
+        ++nh;                                                                         \
+      }                                                                               \
     }                                                                                 \
   } while (0)
+            int jj = (int)jb;
             if (restored) {
-              // just re-stored: storage position = sorted position
-              int jj = (int)jb;
               for (; jj + 4 <= (int)je; jj += 4) {
-                const float4 o0 = __ldg(V.xl + jj), o1 = __ldg(V.xl + jj + 1);
-                const float4 o2 = __ldg(V.xl + jj + 2), o3 = __ldg(V.xl + jj + 3);
-                DEM_PAIR_TEST(o0, jj);
-                DEM_PAIR_TEST(o1, jj + 1);
-                DEM_PAIR_TEST(o2, jj + 2);
-                DEM_PAIR_TEST(o3, jj + 3);
+                const float4 o0 = __ldg(xs + jj), o1 = __ldg(xs + jj + 1);
+                const float4 o2 = __ldg(xs + jj + 2), o3 = __ldg(xs + jj + 3);
+                DEM_PAIR_TEST(o0, jj, jj);
+                DEM_PAIR_TEST(o1, jj + 1, jj + 1);
+                DEM_PAIR_TEST(o2, jj + 2, jj + 2);
+                DEM_PAIR_TEST(o3, jj + 3, jj + 3);
               }
               for (; jj < (int)je; ++jj) {
-                const float4 o0 = __ldg(V.xl + jj);
-                DEM_PAIR_TEST(o0, jj);
+                const float4 o0 = __ldg(xs + jj);
+                DEM_PAIR_TEST(o0, jj, jj);
+              }
+            } else if (copy) {
+              // the storage positions are loaded with the records, not after a hit
+              for (; jj + 4 <= (int)je; jj += 4) {
+                const float4 o0 = __ldg(xs + jj), o1 = __ldg(xs + jj + 1);
+                const float4 o2 = __ldg(xs + jj + 2), o3 = __ldg(xs + jj + 3);
+                const int j0 = (int)__ldg(V.vals + jj), j1 = (int)__ldg(V.vals + jj + 1);
+                const int j2 = (int)__ldg(V.vals + jj + 2), j3 = (int)__ldg(V.vals + jj + 3);
+                DEM_PAIR_TEST(o0, jj, j0);
+                DEM_PAIR_TEST(o1, jj + 1, j1);
+                DEM_PAIR_TEST(o2, jj + 2, j2);
+                DEM_PAIR_TEST(o3, jj + 3, j3);
+              }
+              for (; jj < (int)je; ++jj) {
+                const float4 o0 = __ldg(xs + jj);
+                const int j0 = (int)__ldg(V.vals + jj);
+                DEM_PAIR_TEST(o0, jj, j0);
               }
             } else {
-              for (unsigned jj = jb; jj < je; ++jj) {
-                const int j = (int)__ldg(V.vals + jj);
-                const float4 o0 = __ldg(V.xl + j);
-                DEM_PAIR_TEST(o0, j);
+              // overflowed lists between builds: through the permutation, four at a time
+              for (; jj + 4 <= (int)je; jj += 4) {
+                const int j0 = (int)__ldg(V.vals + jj), j1 = (int)__ldg(V.vals + jj + 1);
+                const int j2 = (int)__ldg(V.vals + jj + 2), j3 = (int)__ldg(V.vals + jj + 3);
+                const float4 o0 = __ldg(V.xl + j0), o1 = __ldg(V.xl + j1);
+                const float4 o2 = __ldg(V.xl + j2), o3 = __ldg(V.xl + j3);
+                DEM_PAIR_TEST(o0, jj, j0);
+                DEM_PAIR_TEST(o1, jj + 1, j1);
+                DEM_PAIR_TEST(o2, jj + 2, j2);
+                DEM_PAIR_TEST(o3, jj + 3, j3);
+              }
+              for (; jj < (int)je; ++jj) {
+                const int j0 = (int)__ldg(V.vals + jj);
+                const float4 o0 = __ldg(V.xl + j0);
+                DEM_PAIR_TEST(o0, jj, j0);
               }
             }
 #undef DEM_PAIR_TEST
@@ -514,12 +561,13 @@ __device__ __forceinline__ void pair_search(const StepView<P> &V, int i, bool re
 // that the steps between builds cost one flag read per block.
 template <class P>
 __global__ void k_pair_search(StepView<P> V) {
+  pdl_wait();
   const bool rebuild = *V.rebuild != 0;
   const bool restored = restore_now(V);
   const bool all = rebuild || V.nolists;
   const int cnt = all ? V.n : *V.novf;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x)
-    pair_search<P>(V, all ? t : V.ovf[t], rebuild, restored);
+    pair_search<P>(V, all ? t : V.ovf[t], rebuild, restored, all && !restored);
 }
 
 // Contact of parcel i with partner j (storage positions; code = cell offset of j's cell):
@@ -701,6 +749,7 @@ __device__ __forceinline__ int contact_forces(const StepView<P> &V, int i, unsig
 // Screen pass: one thread per parcel; a warp appends its parcels with work in one atomic.
 template <class P>
 __global__ void k_contact_screen(StepView<P> V) {
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned hits = 0u;
   bool work = false;
@@ -724,6 +773,7 @@ __global__ void k_contact_screen(StepView<P> V) {
 // torque are written only for parcels in contact; k_gas_particle reads them only there.
 template <class P>
 __global__ void k_contact_forces(StepView<P> V) {
+  pdl_wait();
   using R = typename P::R;
   const int cnt = *V.nwork;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
@@ -744,6 +794,7 @@ __global__ void k_contact_forces(StepView<P> V) {
 // to L1 cost less than the latency the extra occupancy hides (ncu: 33 % -> 50 % warps).
 template <class P>
 __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView<P> V) {
+  pdl_wait();
   using R = typename P::R;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V.n) return;
@@ -909,6 +960,7 @@ template <class P> struct CellSum {
 
 template <class P>
 __global__ void k_cells(StepView<P> V, int mode /* 0 step, 1 eps init, 2 props only */) {
+  pdl_wait();
   using R = typename P::R;
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= V.ncells) return;
@@ -1217,7 +1269,8 @@ __global__ void k_scatter_hist(StepView<P> V, int *cnt, int *partner, double *xi
   }
 }
 
-__global__ void k_mark_cells(const DevBed *beds, const int *cell_bed, unsigned char *mark, long long ncells);
+__global__ void k_mark_cells(const DevBed *beds, const BedP<double> *bps, const int *cell_bed, unsigned char *mark,
+                             unsigned char *wnear, long long ncells);
 __global__ void k_step_counter(long long *ctr, int *rebuild, int lists, int *nwork, int restore_every);
 
 }  // namespace dem

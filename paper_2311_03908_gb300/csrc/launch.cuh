@@ -98,21 +98,20 @@ int enqueue_binning(dem_ctx *c, int drift) {
   cudaStream_t st = c->st;
   StepView<P> V = make_view<P>(c, true);
   if (drift) cudaMemsetAsync(V.moved, 0, sizeof(int) * (size_t)((c->n + 1023) / 1024 + 1), st);
+  const bool pdl = !c->prof_on;   // per-kernel event timing wants plain stream order
   int ps = prof_begin(c, "k_key");
-  k_key<P><<<grid_for(c->n, c->bs_key), c->bs_key, 0, st>>>(V, drift);
+  launch_k(pdl, k_key<P>, grid_for(c->n, c->bs_key), c->bs_key, st, V, drift);
   prof_end(c, ps);
   ++c->launches;
   const int nxt = 1 - c->cur;
   if (drift) {
     ps = prof_begin(c, "resort");
     int e = resort_pairs(c->skey[c->cur], c->keys2, c->sval[c->cur], c->skey[nxt], c->sval[nxt], c->rsw, c->rs_pow2,
-                         c->n, st, &c->launches);
+                         c->n, st, &c->launches, pdl);
     if (e) return e;
-    cudaMemsetAsync(c->cstart, 0, sizeof(unsigned) * c->ncells, st);
-    cudaMemsetAsync(c->cend, 0, sizeof(unsigned) * c->ncells, st);
     prof_end(c, ps);
-    ps = prof_begin(c, "k_ranges");
-    k_ranges<P><<<grid_for(c->n, c->bs_gather), c->bs_gather, 0, st>>>(V);
+    ps = prof_begin(c, "k_ranges");   // the key kernel emptied the previous step's ranges
+    launch_k(pdl, k_ranges<P>, grid_for(c->n, c->bs_gather), c->bs_gather, st, V);
     prof_end(c, ps);
     ++c->launches;
   } else {
@@ -135,8 +134,8 @@ int enqueue_binning(dem_ctx *c, int drift) {
     c->launches += 2;
   }
   ps = prof_begin(c, "k_restore");
-  k_restore_out<P><<<grid_wave(c, c->n, c->bs_gather), c->bs_gather, 0, st>>>(V, drift ? 0 : 1);
-  k_restore_in<P><<<grid_wave(c, c->n, c->bs_gather), c->bs_gather, 0, st>>>(V, drift ? 0 : 1);
+  launch_k(pdl, k_restore_out<P>, grid_wave(c, c->n, c->bs_gather), c->bs_gather, st, V, drift ? 0 : 1);
+  launch_k(pdl, k_restore_in<P>, grid_wave(c, c->n, c->bs_gather), c->bs_gather, st, V, drift ? 0 : 1);
   prof_end(c, ps);
   c->launches += 2;
   return (int)cudaPeekAtLastError();
@@ -149,25 +148,26 @@ int enqueue_steps(dem_ctx *c, int nsteps) {
     int e = enqueue_binning<P>(c, 1);
     if (e) return e;
     StepView<P> V = make_view<P>(c, true);
+    const bool pdl = !c->prof_on;
     int ps;
     // the cell-list search (list builds, overflowed lists, no lists; otherwise a no-op), the
     // contact forces (with the list test between builds), then the gas-particle terms
     ps = prof_begin(c, "k_pair_search");
-    k_pair_search<P><<<grid_wave(c, c->n, c->bs_search), c->bs_search, 0, st>>>(V);
+    launch_k(pdl, k_pair_search<P>, grid_wave(c, c->n, c->bs_search), c->bs_search, st, V);
     prof_end(c, ps);
     ps = prof_begin(c, "k_contact_screen");
-    k_contact_screen<P><<<grid_for(c->n, c->bs_contacts), c->bs_contacts, 0, st>>>(V);
+    launch_k(pdl, k_contact_screen<P>, grid_for(c->n, c->bs_contacts), c->bs_contacts, st, V);
     prof_end(c, ps);
     ps = prof_begin(c, "k_contact_forces");
-    k_contact_forces<P><<<grid_wave(c, c->n, 128), 128, 0, st>>>(V);
+    launch_k(pdl, k_contact_forces<P>, grid_wave(c, c->n, 128), 128, st, V);
     prof_end(c, ps);
     ps = prof_begin(c, "k_gas_particle");
-    k_gas_particle<P><<<grid_for(c->n, c->bs_gp), c->bs_gp, 0, st>>>(V);
+    launch_k(pdl, k_gas_particle<P>, grid_for(c->n, c->bs_gp), c->bs_gp, st, V);
     prof_end(c, ps);
     ps = prof_begin(c, "k_cells");
-    k_cells<P><<<grid_for(c->ncells, c->bs_cells), c->bs_cells, 0, st>>>(V, 0);
+    launch_k(pdl, k_cells<P>, grid_for(c->ncells, c->bs_cells), c->bs_cells, st, V, 0);
     prof_end(c, ps);
-    k_step_counter<<<1, 1, 0, st>>>(c->step_ctr, c->rebuild, c->use_lists, c->nwork, c->restore_every);
+    launch_k(pdl, k_step_counter, 1, 1, st, c->step_ctr, c->rebuild, c->use_lists, c->nwork, c->restore_every);
     c->launches += 6;
     e = (int)cudaPeekAtLastError();
     if (e) return e;

@@ -20,5 +20,5 @@ int radix_sort_pairs(unsigned *k, unsigned *v, unsigned *k2, unsigned *v2, unsig
 size_t resort_words(int n, int *pow2);
 int *resort_counts(unsigned *scratch, int pow2, int n);
 int resort_pairs(const unsigned *kold, const unsigned *knew, const unsigned *vmap, unsigned *kout, unsigned *vout,
-                 unsigned *scratch, int pow2, int n, cudaStream_t st, long long *launches);
+                 unsigned *scratch, int pow2, int n, cudaStream_t st, long long *launches, bool pdl = false);
 }  // namespace dem

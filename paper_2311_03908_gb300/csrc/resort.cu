@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include "radix.cuh"
+#include "pdl.cuh"
 
 namespace dem {
 namespace {
@@ -25,6 +26,7 @@ constexpr int RZ_SMEM_SORT = 4096;
 
 // exclusive scan of the per-block counts (one block); blk[nb] = total movers
 __global__ void __launch_bounds__(RZ_BLOCK) rz_scan(int *blk, int nb) {
+  pdl_wait();
   __shared__ int part[RZ_BLOCK];
   const int per = (nb + RZ_BLOCK - 1) / RZ_BLOCK;
   const int b = threadIdx.x * per, e = min(b + per, nb);
@@ -51,6 +53,7 @@ __global__ void __launch_bounds__(RZ_BLOCK) rz_scan(int *blk, int nb) {
 __global__ void __launch_bounds__(RZ_BLOCK) rz_compact(const unsigned *kold, const unsigned *knew, int n,
                                                        const int *blk, int nb, int *pre,
                                                        unsigned long long *comp) {
+  pdl_wait();
   __shared__ int wsum[RZ_BLOCK / 32];
   const int i = blockIdx.x * RZ_BLOCK + threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -86,6 +89,7 @@ __device__ __forceinline__ void cmpswap(unsigned long long &a, unsigned long lon
 // sorted[rank]; more than RZ_SMEM_SORT movers: left to rz_sort_big
 __global__ void __launch_bounds__(256) rz_rank(const int *blk, int nb, const unsigned long long *comp,
                                                unsigned long long *sorted) {
+  pdl_wait();
   __shared__ unsigned long long s[RZ_SMEM_SORT];
   const int m = blk[nb];
   if (m > RZ_SMEM_SORT) return;
@@ -105,6 +109,7 @@ __global__ void __launch_bounds__(256) rz_rank(const int *blk, int nb, const uns
 // largest value up to a power of two)
 __global__ void __launch_bounds__(RZ_BLOCK) rz_sort_big(const int *blk, int nb, const unsigned long long *comp,
                                                         unsigned long long *a, int cap) {
+  pdl_wait();
   const int m = blk[nb];
   if (m <= RZ_SMEM_SORT) return;
   int P = 1;
@@ -143,6 +148,7 @@ constexpr int RZ_MERGE = 256;
 __global__ void __launch_bounds__(RZ_MERGE) rz_merge(const unsigned *kold, const unsigned *knew, int n,
                                                      const int *pre, const unsigned long long *sorted,
                                                      const unsigned *vmap, unsigned *kout, unsigned *vout) {
+  pdl_wait();
   const int m = pre[n];
   const int g = blockIdx.x * RZ_MERGE + threadIdx.x;
   const int lane = threadIdx.x & 31;
@@ -203,17 +209,18 @@ int *resort_counts(unsigned *scratch, int pow2, int n) {
 }
 
 int resort_pairs(const unsigned *kold, const unsigned *knew, const unsigned *vmap, unsigned *kout, unsigned *vout,
-                 unsigned *scratch, int pow2, int n, cudaStream_t st, long long *launches) {
+                 unsigned *scratch, int pow2, int n, cudaStream_t st, long long *launches, bool pdl) {
   const int nb = (n + RZ_BLOCK - 1) / RZ_BLOCK;
   unsigned long long *comp = reinterpret_cast<unsigned long long *>(scratch);
   unsigned long long *sorted = comp + pow2;
   int *pre = reinterpret_cast<int *>(scratch + 4 * (size_t)pow2);
   int *blk = pre + n + 1;
-  rz_scan<<<1, RZ_BLOCK, 0, st>>>(blk, nb);
-  rz_compact<<<nb, RZ_BLOCK, 0, st>>>(kold, knew, n, blk, nb, pre, comp);
-  rz_rank<<<RZ_SMEM_SORT / 256, 256, 0, st>>>(blk, nb, comp, sorted);
-  rz_sort_big<<<1, RZ_BLOCK, 0, st>>>(blk, nb, comp, sorted, pow2);
-  rz_merge<<<(n + RZ_MERGE - 1) / RZ_MERGE, RZ_MERGE, 0, st>>>(kold, knew, n, pre, sorted, vmap, kout, vout);
+  launch_k(pdl, rz_scan, 1, RZ_BLOCK, st, blk, nb);
+  launch_k(pdl, rz_compact, nb, RZ_BLOCK, st, kold, knew, n, (const int *)blk, nb, pre, comp);
+  launch_k(pdl, rz_rank, RZ_SMEM_SORT / 256, 256, st, (const int *)blk, nb, (const unsigned long long *)comp, sorted);
+  launch_k(pdl, rz_sort_big, 1, RZ_BLOCK, st, (const int *)blk, nb, (const unsigned long long *)comp, sorted, pow2);
+  launch_k(pdl, rz_merge, (n + RZ_MERGE - 1) / RZ_MERGE, RZ_MERGE, st, kold, knew, n, (const int *)pre,
+           (const unsigned long long *)sorted, vmap, kout, vout);
   if (launches) *launches += 5;
   return (int)cudaPeekAtLastError();
 }
