@@ -32,10 +32,12 @@ struct PrecKahan { using R = float; static constexpr bool kahan = true; static c
 
 enum : int { ERR_CAPACITY = 1, ERR_NONFINITE = 2, ERR_DOMAIN = 4, ERR_TIMEOUT = 8 };
 
-// per-cell gas-property rows (derived from the gas state by gas_cell_props)
+// per-cell gas properties (derived from the gas state by gas_cell_props), stored cell by
+// cell in records of GP_STRIDE words, so that a parcel reads its cell's record in a few
+// vector loads
 enum : int {
   GP_RHO = 0, GP_MU, GP_LAM, GP_CP, GP_X, GP_DM, GP_SC13, GP_PR13, GP_EPOW, GP_D0, GP_D1,
-  GP_UZ, GP_EPS, GP_TG, GP_N
+  GP_UZ, GP_EPS, GP_TG, GP_N, GP_STRIDE = 16
 };
 // gas state rows (double)
 enum : int { GS_EPS = 0, GS_Y0, GS_Y1, GS_Y2, GS_T, GS_N };

@@ -373,7 +373,7 @@ void layout(dem_ctx *c, Bump &m) {
   c->src = m.take<char>(N * SR_CNT, R);
   c->gas[0] = m.take<double>(C * GS_N);
   c->gas[1] = m.take<double>(C * GS_N);
-  c->gp = m.take<char>(C * GP_N, R);
+  c->gp = m.take<char>(C * GP_STRIDE, R);
   c->mark = m.take<unsigned char>(C);
   c->wnear = m.take<unsigned char>(C);
   c->cell_bed = m.take<int>(C);

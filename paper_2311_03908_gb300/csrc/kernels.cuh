@@ -810,11 +810,25 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
   const unsigned c = V.keyp[i];
   const size_t nc = (size_t)V.ncells;
   Gas<R> g;
-  g.rho = V.gp[GP_RHO * nc + c]; g.mu = V.gp[GP_MU * nc + c]; g.lam = V.gp[GP_LAM * nc + c];
-  g.cp = V.gp[GP_CP * nc + c]; g.x = V.gp[GP_X * nc + c]; g.Dm = V.gp[GP_DM * nc + c];
-  g.sc13 = V.gp[GP_SC13 * nc + c]; g.pr13 = V.gp[GP_PR13 * nc + c]; g.epow = V.gp[GP_EPOW * nc + c];
-  g.D = V.gp[(ore ? GP_D1 : GP_D0) * nc + c]; g.uz = V.gp[GP_UZ * nc + c];
-  g.eps = V.gp[GP_EPS * nc + c]; g.T = V.gp[GP_TG * nc + c];
+  R gv[GP_STRIDE];   // the cell's property record, in vector loads
+  if constexpr (sizeof(R) == 4) {
+    const float4 *q = reinterpret_cast<const float4 *>(V.gp + (size_t)c * GP_STRIDE);
+#pragma unroll
+    for (int k = 0; k < GP_STRIDE / 4; ++k) {
+      const float4 t = __ldg(q + k);
+      gv[4 * k] = t.x; gv[4 * k + 1] = t.y; gv[4 * k + 2] = t.z; gv[4 * k + 3] = t.w;
+    }
+  } else {
+    const double2 *q = reinterpret_cast<const double2 *>(V.gp + (size_t)c * GP_STRIDE);
+#pragma unroll
+    for (int k = 0; k < GP_N / 2; ++k) {
+      const double2 t = __ldg(q + k);
+      gv[2 * k] = t.x; gv[2 * k + 1] = t.y;
+    }
+  }
+  g.rho = gv[GP_RHO]; g.mu = gv[GP_MU]; g.lam = gv[GP_LAM]; g.cp = gv[GP_CP]; g.x = gv[GP_X];
+  g.Dm = gv[GP_DM]; g.sc13 = gv[GP_SC13]; g.pr13 = gv[GP_PR13]; g.epow = gv[GP_EPOW];
+  g.D = ore ? gv[GP_D1] : gv[GP_D0]; g.uz = gv[GP_UZ]; g.eps = gv[GP_EPS]; g.T = gv[GP_TG];
   const R d = V.A.d[i];
   const R dc = bp.k * d;
   const R Vp = (R)(kPI / 6.0) * dc * dc * dc;
@@ -915,12 +929,10 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
 template <class P>
 __device__ __forceinline__ void store_props(StepView<P> &V, long long c, const CellProps<typename P::R> &p) {
   const size_t nc = (size_t)V.ncells;
-  V.gp[GP_RHO * nc + c] = p.rho; V.gp[GP_MU * nc + c] = p.mu; V.gp[GP_LAM * nc + c] = p.lam;
-  V.gp[GP_CP * nc + c] = p.cp; V.gp[GP_X * nc + c] = p.x; V.gp[GP_DM * nc + c] = p.Dm;
-  V.gp[GP_SC13 * nc + c] = p.sc13; V.gp[GP_PR13 * nc + c] = p.pr13;
-  V.gp[GP_EPOW * nc + c] = p.epow; V.gp[GP_D0 * nc + c] = p.D[0];
-  V.gp[GP_D1 * nc + c] = p.D[1]; V.gp[GP_UZ * nc + c] = p.uz;
-  V.gp[GP_EPS * nc + c] = p.eps; V.gp[GP_TG * nc + c] = p.T;
+  typename P::R *q = V.gp + (size_t)c * GP_STRIDE;
+  q[GP_RHO] = p.rho; q[GP_MU] = p.mu; q[GP_LAM] = p.lam; q[GP_CP] = p.cp; q[GP_X] = p.x; q[GP_DM] = p.Dm;
+  q[GP_SC13] = p.sc13; q[GP_PR13] = p.pr13; q[GP_EPOW] = p.epow; q[GP_D0] = p.D[0]; q[GP_D1] = p.D[1];
+  q[GP_UZ] = p.uz; q[GP_EPS] = p.eps; q[GP_TG] = p.T;
 }
 
 // sums of the per-parcel sources of [jb, je): FP64 in the FP64 form, compensated FP32
@@ -987,7 +999,7 @@ __global__ void k_cells(StepView<P> V, int mode /* 0 step, 1 eps init, 2 props o
       S.run(V.src, cp, V.vals, V.cstart[c], V.cend[c]);
       const bool up = c - B.cell_off >= layer && !V.mark[c - layer];
       const double dtg = B.ncouple * B.dt;
-      const double rho = (double)V.gp[GP_RHO * nc + c], cpg = (double)V.gp[GP_CP * nc + c];
+      const double rho = (double)V.gp[(size_t)c * GP_STRIDE + GP_RHO], cpg = (double)V.gp[(size_t)c * GP_STRIDE + GP_CP];
       const double uz = B.U_in / eps;
       double Yup[3] = {B.Y_in[0], B.Y_in[1], B.Y_in[2]}, Tup = B.T_in;
       if (up) {
@@ -1043,7 +1055,7 @@ __global__ void k_cells(StepView<P> V, int mode /* 0 step, 1 eps init, 2 props o
       const bool up = c - B.cell_off >= layer && !V.mark[c - layer];
       const Tab<R> &t = tab<R>();
       const R dtg = bp.dtg;
-      const R rho = V.gp[GP_RHO * nc + c], cpg = V.gp[GP_CP * nc + c];
+      const R rho = V.gp[(size_t)c * GP_STRIDE + GP_RHO], cpg = V.gp[(size_t)c * GP_STRIDE + GP_CP];
       const R eps_r = eps2.x + eps2.y, T_r = T2.x + T2.y;
       const R uz = bp.U_in / eps_r;
       const R Yr[3] = {Y2[0].x + Y2[0].y, Y2[1].x + Y2[1].y, Y2[2].x + Y2[2].y};
