@@ -928,11 +928,22 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
 // ---------------------------------------------------------------------------------------
 template <class P>
 __device__ __forceinline__ void store_props(StepView<P> &V, long long c, const CellProps<typename P::R> &p) {
-  const size_t nc = (size_t)V.ncells;
-  typename P::R *q = V.gp + (size_t)c * GP_STRIDE;
-  q[GP_RHO] = p.rho; q[GP_MU] = p.mu; q[GP_LAM] = p.lam; q[GP_CP] = p.cp; q[GP_X] = p.x; q[GP_DM] = p.Dm;
-  q[GP_SC13] = p.sc13; q[GP_PR13] = p.pr13; q[GP_EPOW] = p.epow; q[GP_D0] = p.D[0]; q[GP_D1] = p.D[1];
-  q[GP_UZ] = p.uz; q[GP_EPS] = p.eps; q[GP_TG] = p.T;
+  using R = typename P::R;
+  R r[GP_STRIDE];
+  r[GP_RHO] = p.rho; r[GP_MU] = p.mu; r[GP_LAM] = p.lam; r[GP_CP] = p.cp; r[GP_X] = p.x; r[GP_DM] = p.Dm;
+  r[GP_SC13] = p.sc13; r[GP_PR13] = p.pr13; r[GP_EPOW] = p.epow; r[GP_D0] = p.D[0]; r[GP_D1] = p.D[1];
+  r[GP_UZ] = p.uz; r[GP_EPS] = p.eps; r[GP_TG] = p.T;
+  r[GP_N] = (R)0; r[GP_N + 1] = (R)0;
+  // the record in vector stores (a warp writes whole sectors)
+  if constexpr (sizeof(R) == 4) {
+    float4 *q = reinterpret_cast<float4 *>(V.gp + (size_t)c * GP_STRIDE);
+#pragma unroll
+    for (int k = 0; k < GP_STRIDE / 4; ++k) q[k] = make_float4(r[4 * k], r[4 * k + 1], r[4 * k + 2], r[4 * k + 3]);
+  } else {
+    double2 *q = reinterpret_cast<double2 *>(V.gp + (size_t)c * GP_STRIDE);
+#pragma unroll
+    for (int k = 0; k < GP_N / 2; ++k) q[k] = make_double2(r[2 * k], r[2 * k + 1]);
+  }
 }
 
 // sums of the per-parcel sources of [jb, je): FP64 in the FP64 form, compensated FP32
