@@ -87,8 +87,9 @@ def algorithmic_bytes(kernel: str, n: int, ncells: int, zbar: float, L: float, r
     R = rsize
     slot = 4 + 3 * R                                  # partner id + tangential displacement
     state = 24 + 12 * R + 2 * R + 32 + 8 + 12         # x; v,w,a,al; T,d; masses; meta,orig; dsp
-    if kernel == "k_key":            # in place: half kicks, drift, displacement, key, local coordinates
-        return n * ((4 + 24 + 12 * R + 12 + 16 + 4 + R) + (24 + 6 * R + 12 + 4 + 16))
+    if kernel == "k_key":            # in place: half kicks, drift, displacement, key, local coordinates;
+        # the previous step's sorted keys (to empty its cell ranges)
+        return n * ((4 + 24 + 12 * R + 12 + 16 + 4 + R + 4) + (24 + 6 * R + 12 + 4 + 16))
     if kernel == "radix_sort":
         return n * passes * (8 + 8)
     if kernel == "resort":           # new keys in sorted order, re-sort, permutation and cell ranges
@@ -111,11 +112,12 @@ def algorithmic_bytes(kernel: str, n: int, ncells: int, zbar: float, L: float, r
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one full-size ncu
-# capture of the 2M-parcel split-precision bed; per parcel), valid only for the sources it
-# was taken on (profiles/traffic_ibm_2m_split.md gives the command).
-TRAFFIC_SOURCE_SHA256 = "7ebdf1665b947705ce74b77b49d117eabf39436bf0d35601467a15ab149f52e4"
+# capture of the 2M-parcel split-precision bed between list builds, after the 300-step
+# settle; per parcel), valid only for the CUDA sources it was taken on.
+TRAFFIC_SOURCE_SHA256 = "7e50e5fc4343e32470f70f85c12b63e04eccdd0054fb2ac76d08d79a82ac6890"
 TRAFFIC_WORKLOAD = ("ibm_2m", "split", 2_000_000)
-TRAFFIC_BYTES_PER_PARCEL = {}
+TRAFFIC_BYTES_PER_PARCEL = {"k_gas_particle": 202.4, "k_key": 178.8, "k_cells": 145.9, "k_contact_screen": 58.4,
+                            "k_contact_forces": 17.1, "k_ranges": 8.0}
 
 
 def source_sha256() -> str:
