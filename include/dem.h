@@ -236,8 +236,10 @@ int64_t dem_last_launch_count(dem_ctx *c);
 /* Replace the gas field (the coupling input of Sec. 4: cell fields from the gas solver).
  * g->Y is (total cells) x 3 mass fractions, g->T the temperatures (host or device by
  * g->on_device); the gas volume fraction is kept; the cells' derived properties are
- * recomputed. Asynchronous on the context stream (host buffers are copied before return
- * when they are pageable; pinned buffers are read by the copy engine). */
+ * recomputed. Asynchronous on the context stream: host buffers in page-locked memory that
+ * the device can address (cudaHostAlloc / cudaHostRegister) are read by the kernel itself
+ * when the stream reaches it, so they must stay unchanged until then (as for any
+ * asynchronous copy from pinned memory); pageable host buffers are staged by a copy. */
 int dem_set_gas(dem_ctx *c, const dem_gas *g);
 
 /* Per-kernel timing: while on, every kernel that dem_step launches is bracketed by CUDA

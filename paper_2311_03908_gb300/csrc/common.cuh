@@ -60,6 +60,8 @@ struct DevBed {
   double x0, y0, z0, dx, dy, dz, inv_dx, inv_dy, inv_dz, vcell, inv_vcell;
   int nx, ny, nz;
   long long cell_off;           // first global gas cell (and sort key) of this bed
+  int pstart, pend;             // storage positions of this bed's parcels (fixed: beds are stored
+                                // in bed order after the first binning and parcels never change bed)
   int corner_off;               // first entry of this bed in the cell-corner table
   int cornerp_off;              // the same in the FP32-pair table (nx+1, ny+1, nz+1 entries)
   float inv_nx_f, inv_nxy_f;    // 1/nx, 1/(nx ny): cell offsets from key differences

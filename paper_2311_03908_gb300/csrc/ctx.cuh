@@ -108,7 +108,7 @@ template <class P> int enqueue_scatter_state(dem_ctx *c, double *out_dev);
 template <class P> int enqueue_scatter_diag(dem_ctx *c, double *out_dev);
 template <class P> int enqueue_scatter_hist(dem_ctx *c, int *cnt, int *partner, double *xi);
 template <class P> int enqueue_sources(dem_ctx *c);
-template <class P> int enqueue_props(dem_ctx *c);
+template <class P> int enqueue_gas_set(dem_ctx *c, const double *Y, const double *T);
 template <class P> int run_adjoint(dem_ctx *c, int nsteps, int ckpt, double *J, double *grad);
 
 // event pair around one kernel when profiling is on (returns the start-event slot or -1)

@@ -99,16 +99,6 @@ __global__ void k_load(int n, const double *const *src /* 8 + 4 arrays */, const
   orig[i] = i;
 }
 
-// Gas state from the coupling input, keeping the volume fraction.
-__global__ void k_gas_set(long long nc, const double *Y /* nc*3 */, const double *T, double *G, bool pairs) {
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nc) return;
-  gas_put(G, GS_Y0 * nc + c, Y[c * 3 + 0], pairs);
-  gas_put(G, GS_Y1 * nc + c, Y[c * 3 + 1], pairs);
-  gas_put(G, GS_Y2 * nc + c, Y[c * 3 + 2], pairs);
-  gas_put(G, GS_T * nc + c, T[c], pairs);
-}
-
 int prof_begin(dem_ctx *c, const char *name) {
   if (!c->prof_on) return -1;
   int id = -1;
@@ -540,7 +530,7 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
   c->cfg.assign(beds, beds + n_beds);
   // per-bed constants and grid offsets; the gas cells are the cell list of the contact
   // search, so no parcel may be wider than a cell edge
-  long long coff = 0;
+  long long coff = 0, pacc = 0;
   for (int b = 0; b < n_beds; ++b) {
     DevBed B = derive_bed(beds[b]);
     const double edge = std::min(B.dx, std::min(B.dy, B.dz));
@@ -548,6 +538,9 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
     // stability of the stiffest contact: omega_0 dt < 2 with m* = m_min / 2
     if (nb[b] > 0 && std::sqrt(beds[b].kn / (0.5 * mmin[b])) * beds[b].dt >= 2.0) { delete c; return DEM_EINVAL; }
     B.cell_off = coff;
+    B.pstart = (int)pacc;
+    pacc += nb[b];
+    B.pend = (int)pacc;
     coff += (long long)B.nx * B.ny * B.nz;
     B.cornerp_off = (int)c->hcornerp.size();
     {
@@ -922,21 +915,39 @@ int dem_get_diag(dem_ctx *c, double *out_host) {
 
 int64_t dem_last_launch_count(dem_ctx *c) { return c ? c->launches : 0; }
 
+// device address of page-locked host memory the current device can reach, or null
+static const double *mapped_host(const double *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();   // not a CUDA-known pointer (pageable memory): clear the error
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || a.devicePointer == nullptr) return nullptr;
+  return static_cast<const double *>(a.devicePointer);
+}
+
 int dem_set_gas(dem_ctx *c, const dem_gas *g) {
   if (!c || !g || !g->Y || !g->T) return DEM_EINVAL;
   int s = poll(c, false);
   if (s != DEM_OK) return s;
   const size_t nc = (size_t)c->ncells;
-  if (!c->gas_stage && cudaMalloc(&c->gas_stage, sizeof(double) * 4 * nc) != cudaSuccess) return DEM_ENOMEM;
   const double *Y = g->Y, *T = g->T;
   if (!g->on_device) {
-    CK(cudaMemcpyAsync(c->gas_stage, g->Y, sizeof(double) * 3 * nc, cudaMemcpyHostToDevice, c->st));
-    CK(cudaMemcpyAsync(c->gas_stage + 3 * nc, g->T, sizeof(double) * nc, cudaMemcpyHostToDevice, c->st));
-    Y = c->gas_stage;
-    T = c->gas_stage + 3 * nc;
+    // host arrays in page-locked memory that the device can address (e.g. from
+    // cudaHostAlloc) are read by the kernel itself; others are staged by a copy
+    const double *Yd = mapped_host(g->Y), *Td = mapped_host(g->T);
+    if (Yd && Td) {
+      Y = Yd;
+      T = Td;
+    } else {
+      if (!c->gas_stage && cudaMalloc(&c->gas_stage, sizeof(double) * 4 * nc) != cudaSuccess) return DEM_ENOMEM;
+      CK(cudaMemcpyAsync(c->gas_stage, g->Y, sizeof(double) * 3 * nc, cudaMemcpyHostToDevice, c->st));
+      CK(cudaMemcpyAsync(c->gas_stage + 3 * nc, g->T, sizeof(double) * nc, cudaMemcpyHostToDevice, c->st));
+      Y = c->gas_stage;
+      T = c->gas_stage + 3 * nc;
+    }
   }
-  k_gas_set<<<(int)((nc + 255) / 256), 256, 0, c->st>>>((long long)nc, Y, T, c->gas[c->gcur], c->prec != DEM_PREC_FP64);
-  int e = DEM_DISPATCH(c, enqueue_props, c);
+  int e = DEM_DISPATCH(c, enqueue_gas_set, c, Y, T);
   if (e) return c->sticky = DEM_ECUDA;
   return DEM_OK;
 }

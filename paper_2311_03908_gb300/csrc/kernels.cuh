@@ -1121,6 +1121,44 @@ __global__ void k_cells(StepView<P> V, int mode /* 0 step, 1 eps init, 2 props o
   }
 }
 
+// The coupling input (dem_set_gas): the gas composition and temperature of every cell from
+// the caller (FP64; device memory, or mapped pinned host memory read directly), written to
+// the other gas-state buffer with the volume fraction kept, and the cell's property record
+// for the next step; in the FP32 forms only where the FP32 state changed (as in k_cells).
+template <class P>
+__global__ void k_gas_set_props(StepView<P> V, const double *__restrict__ Yin /* ncells*3 */,
+                                const double *__restrict__ Tin) {
+  using R = typename P::R;
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= V.ncells) return;
+  const BedP<R> &bp = V.bp[V.cell_bed[c]];
+  const size_t nc = (size_t)V.ncells;
+  const double y0 = Yin[c * 3], y1 = Yin[c * 3 + 1], y2 = Yin[c * 3 + 2], tg = Tin[c];
+  if constexpr (P::exact) {
+    const double eps = V.gas[GS_EPS * nc + c];
+    V.gas_new[GS_EPS * nc + c] = eps;
+    V.gas_new[GS_Y0 * nc + c] = y0; V.gas_new[GS_Y1 * nc + c] = y1; V.gas_new[GS_Y2 * nc + c] = y2;
+    V.gas_new[GS_T * nc + c] = tg;
+    const double Y[3] = {y0, y1, y2};
+    store_props(V, c, gas_cell_props<double>(bp, eps, Y, tg));
+  } else {
+    const float2 *G2 = reinterpret_cast<const float2 *>(V.gas);
+    const float2 eps2 = G2[GS_EPS * nc + c];
+    V.gas_new[GS_EPS * nc + c] = V.gas[GS_EPS * nc + c];
+    gas_put(V.gas_new, GS_Y0 * nc + c, y0, true);
+    gas_put(V.gas_new, GS_Y1 * nc + c, y1, true);
+    gas_put(V.gas_new, GS_Y2 * nc + c, y2, true);
+    gas_put(V.gas_new, GS_T * nc + c, tg, true);
+    const float2 *N2 = reinterpret_cast<const float2 *>(V.gas_new);
+    const float2 n0 = N2[GS_Y0 * nc + c], n1 = N2[GS_Y1 * nc + c], n2 = N2[GS_Y2 * nc + c], nt = N2[GS_T * nc + c];
+    const R Yr[3] = {n0.x + n0.y, n1.x + n1.y, n2.x + n2.y};
+    const R Tr = nt.x + nt.y, epsr = eps2.x + eps2.y;
+    const float2 to = G2[GS_T * nc + c], o0 = G2[GS_Y0 * nc + c], o1 = G2[GS_Y1 * nc + c], o2 = G2[GS_Y2 * nc + c];
+    if (Tr == to.x + to.y && Yr[0] == o0.x + o0.y && Yr[1] == o1.x + o1.y && Yr[2] == o2.x + o2.y) return;
+    store_props(V, c, gas_cell_props<R>(bp, epsr, Yr, Tr));
+  }
+}
+
 // Cell sums of the last step's per-parcel sources (dem_get_sources).
 template <class P>
 __global__ void k_sources(StepView<P> V) {
@@ -1147,31 +1185,22 @@ __global__ void k_volume(StepView<P> V) {
 // ---------------------------------------------------------------------------------------
 // Reduction degree (eqs (2-15)..(2-19)) per parcel and per bed (deterministic two-pass).
 // ---------------------------------------------------------------------------------------
-constexpr int FOV_CHUNKS = 256;   // blocks per bed of the reduction-degree sums
+constexpr int FOV_CHUNKS = 1024;  // blocks per bed of the reduction-degree sums
+constexpr int FOV_BLOCK = 128;    // threads per block of k_fov_chunks
+static_assert(FOV_CHUNKS % 256 == 0, "k_fov_beds adds FOV_CHUNKS / 256 slices per thread");
 
-// Each bed's parcels are contiguous (in storage as in sorted order); block (bed, chunk) sums a
+// Each bed's parcels occupy a fixed range of storage positions; block (bed, chunk) sums a
 // fixed slice of them (strided per thread, then a shared-memory tree in FP64), and k_fov_beds
-// adds the slices in chunk order, so the result is reproducible bit for bit. The FP64 form
+// adds the slices in a fixed order, so the result is reproducible bit for bit. The FP64 form
 // evaluates f_ov in FP64; the FP32 forms in FP32 (relative error ~1e-7 per parcel) with
 // compensated per-thread sums.
 template <class P>
 __global__ void k_fov_chunks(StepView<P> V, double *per_parcel_orig, double *part /* [nbeds][FOV_CHUNKS][4] */) {
-  __shared__ double sh[3][256];
-  __shared__ int range[2];
+  __shared__ double sh[3][FOV_BLOCK];
   const int b = blockIdx.x / FOV_CHUNKS, ch = blockIdx.x % FOV_CHUNKS;
-  if (threadIdx.x == 0) {
-    const unsigned klo = (unsigned)V.beds[b].cell_off;
-    const unsigned khi = (b + 1 < V.nbeds) ? (unsigned)V.beds[b + 1].cell_off : 0xffffffffu;
-    int lo = 0, hi = V.n;
-    while (lo < hi) { int mid = (lo + hi) >> 1; if (V.keys[mid] < klo) lo = mid + 1; else hi = mid; }
-    range[0] = lo;
-    hi = V.n;
-    while (lo < hi) { int mid = (lo + hi) >> 1; if (V.keys[mid] < khi) lo = mid + 1; else hi = mid; }
-    range[1] = lo;
-  }
-  __syncthreads();
-  const long long len = range[1] - range[0];
-  const int c0 = range[0] + (int)(len * ch / FOV_CHUNKS), c1 = range[0] + (int)(len * (ch + 1) / FOV_CHUNKS);
+  const int p0 = V.beds[b].pstart;
+  const long long len = V.beds[b].pend - p0;
+  const int c0 = p0 + (int)(len * ch / FOV_CHUNKS), c1 = p0 + (int)(len * (ch + 1) / FOV_CHUNKS);
   double a0 = 0.0, a1 = 0.0, a2 = 0.0;
   if constexpr (P::exact) {
     const Tab<double> &td = tab<double>();
@@ -1235,13 +1264,27 @@ __global__ void k_fov_chunks(StepView<P> V, double *per_parcel_orig, double *par
   }
 }
 
-static __global__ void k_fov_beds(const double *part, int nbeds, double *out /* [nbeds][4] */) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nbeds) return;
+// One block per bed: each thread adds FOV_CHUNKS / 256 consecutive slices in order, then a
+// fixed shared-memory tree.
+static __global__ void __launch_bounds__(256) k_fov_beds(const double *part, int nbeds, double *out /* [nbeds][4] */) {
+  __shared__ double sh[4][256];
+  const int b = blockIdx.x;
+  constexpr int per = FOV_CHUNKS / 256;
   double s[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int ch = 0; ch < FOV_CHUNKS; ++ch)
-    for (int q = 0; q < 4; ++q) s[q] += part[((size_t)b * FOV_CHUNKS + ch) * 4 + q];
-  for (int q = 0; q < 4; ++q) out[b * 4 + q] = s[q];
+  for (int k = 0; k < per; ++k) {
+    const double *p = part + ((size_t)b * FOV_CHUNKS + threadIdx.x * per + k) * 4;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s[q] += p[q];
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] = s[q];
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off)
+      for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) out[b * 4 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
 // ---------------------------------------------------------------------------------------

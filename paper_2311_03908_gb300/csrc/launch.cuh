@@ -193,8 +193,8 @@ int enqueue_init(dem_ctx *c) {
 template <class P>
 int enqueue_fov(dem_ctx *c, double *per_parcel_dev) {
   StepView<P> V = make_view<P>(c, false);
-  k_fov_chunks<P><<<c->nbeds * FOV_CHUNKS, 256, 0, c->st>>>(V, per_parcel_dev, c->fv);
-  k_fov_beds<<<(c->nbeds + 63) / 64, 64, 0, c->st>>>(c->fv, c->nbeds, c->fvbed);
+  k_fov_chunks<P><<<c->nbeds * FOV_CHUNKS, FOV_BLOCK, 0, c->st>>>(V, per_parcel_dev, c->fv);
+  k_fov_beds<<<c->nbeds, 256, 0, c->st>>>(c->fv, c->nbeds, c->fvbed);
   return (int)cudaPeekAtLastError();
 }
 
@@ -229,11 +229,11 @@ int enqueue_sources(dem_ctx *c) {
 }
 
 template <class P>
-int enqueue_props(dem_ctx *c) {
+int enqueue_gas_set(dem_ctx *c, const double *Y, const double *T) {
   StepView<P> V = make_view<P>(c, false);
   V.gas = c->gas[c->gcur];
   V.gas_new = c->gas[1 - c->gcur];
-  k_cells<P><<<grid_for(c->ncells, 256), 256, 0, c->st>>>(V, 2);
+  k_gas_set_props<P><<<grid_for(c->ncells, 256), 256, 0, c->st>>>(V, Y, T);
   c->gcur = 1 - c->gcur;
   return (int)cudaPeekAtLastError();
 }
@@ -261,6 +261,6 @@ int kernel_limits(int *lim) {
   template int enqueue_scatter_diag<P>(dem_ctx *, double *);                            \
   template int enqueue_scatter_hist<P>(dem_ctx *, int *, int *, double *);              \
   template int enqueue_sources<P>(dem_ctx *);                                           \
-  template int enqueue_props<P>(dem_ctx *);
+  template int enqueue_gas_set<P>(dem_ctx *, const double *, const double *);
 
 }  // namespace dem

@@ -260,3 +260,34 @@ def test_coupling_interval_parity():
     for row in range(binding.DEM_NSTATE):
         assert _rel(sg[row], so[row]) < 1e-7, binding.STATE_ROWS[row]
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "split"])
+def test_set_gas_input_paths_agree(prec):
+    """The coupling input through its three paths -- pageable host arrays (staged by a copy),
+    page-locked host memory (read by the kernel itself) and device tensors -- gives the same
+    state bit for bit; handing back the current field changes nothing."""
+    bed = synth.small_packed(seed=5, n=2000, v_scale=0.2)
+    ctxs = [_ctx(bed, prec) for _ in range(5)]
+    for c in ctxs:
+        c.dem_step(5)
+    g = ctxs[0].dem_get_gas()
+    Y0, T0 = np.ascontiguousarray(g[:, 1:4]), np.ascontiguousarray(g[:, 4])
+    Y = Y0.copy()
+    Y[:, 0] *= 0.9
+    Y[:, 1] = 1.0 - Y[:, 0] - Y[:, 2]
+    T = T0 + 15.0
+    ctxs[1].dem_set_gas(Y, T)
+    ctxs[2].dem_set_gas(torch.from_numpy(Y).pin_memory(), torch.from_numpy(T).pin_memory())
+    ctxs[3].dem_set_gas(torch.from_numpy(Y).cuda(), torch.from_numpy(T).cuda())
+    ctxs[4].dem_set_gas(Y0, T0)
+    for c in ctxs:
+        c.dem_step(5)
+    s = [c.dem_get_state() for c in ctxs]
+    gs = [c.dem_get_gas() for c in ctxs]
+    assert np.array_equal(s[1], s[2]) and np.array_equal(s[1], s[3])
+    assert np.array_equal(gs[1], gs[2]) and np.array_equal(gs[1], gs[3])
+    assert np.array_equal(s[4], s[0]) and np.array_equal(gs[4], gs[0])
+    assert not np.array_equal(s[1], s[0])
+    for c in ctxs:
+        c.close()
