@@ -747,8 +747,10 @@ __device__ __forceinline__ int contact_forces(const StepView<P> &V, int i, unsig
 }
 
 // Screen pass: one thread per parcel; a warp appends its parcels with work in one atomic.
+// Held to 48 registers in the FP32 forms (five 256-thread blocks per SM): more warps to
+// hide the latency of the list loads.
 template <class P>
-__global__ void k_contact_screen(StepView<P> V) {
+__global__ void __launch_bounds__(256, P::exact ? 1 : 5) k_contact_screen(StepView<P> V) {
   pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned hits = 0u;
@@ -981,8 +983,9 @@ template <class P> struct CellSum {
   }
 };
 
+// (48 registers in the FP32 forms, as the screen pass)
 template <class P>
-__global__ void k_cells(StepView<P> V, int mode /* 0 step, 1 eps init, 2 props only */) {
+__global__ void __launch_bounds__(256, P::exact ? 1 : 5) k_cells(StepView<P> V, int mode /* 0 step, 1 eps init, 2 props only */) {
   pdl_wait();
   using R = typename P::R;
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
