@@ -637,6 +637,7 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
   }
   ck(cudaMemsetAsync(c->nlc, 0, (size_t)n, c->st));
   ck(cudaMemsetAsync(c->nwork, 0, sizeof(int), c->st));
+  ck(cudaMemsetAsync(resort_counts(c->rsw, c->rs_pow2, n), 0, sizeof(int) * (size_t)((n + 1023) / 1024 + 1), c->st));
   // gas: cell -> bed, marks, initial state
   {
     std::vector<int> cb(c->ncells);

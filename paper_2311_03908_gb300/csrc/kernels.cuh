@@ -281,6 +281,7 @@ __global__ void k_ranges(StepView<P> V) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V.n) return;
   if (i == 0 && *V.rebuild) *V.novf = 0;   // a list build lists the overflowed parcels anew
+  if (i < (V.n + 1023) / 1024) V.moved[i] = 0;   // the re-sort is done with the counts: zero for the next step
   const unsigned k = V.keys[i];
   if (i == 0 || V.keys[i - 1] != k) V.cstart[k] = (unsigned)i;
   if (i == V.n - 1 || V.keys[i + 1] != k) V.cend[k] = (unsigned)(i + 1);

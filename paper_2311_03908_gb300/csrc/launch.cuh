@@ -97,7 +97,7 @@ template <class P>
 int enqueue_binning(dem_ctx *c, int drift) {
   cudaStream_t st = c->st;
   StepView<P> V = make_view<P>(c, true);
-  if (drift) cudaMemsetAsync(V.moved, 0, sizeof(int) * (size_t)((c->n + 1023) / 1024 + 1), st);
+  // the per-1024 counts of changed keys start at zero (k_ranges clears them after use)
   const bool pdl = !c->prof_on;   // per-kernel event timing wants plain stream order
   int ps = prof_begin(c, "k_key");
   launch_k(pdl, k_key<P>, grid_for(c->n, c->bs_key), c->bs_key, st, V, drift);
