@@ -133,6 +133,11 @@ __device__ __forceinline__ void key_cell(const DevBed &B, unsigned key, int &ix,
   iy = (int)(row - (unsigned)iz * ny);
 }
 
+// Half kick + drift (written back to the FP64 positions), the sort key, and the FP32
+// cell-local coordinates. The FP32 forms take the key from the previous cell when the
+// parcel stays more than 1e-3 of an edge inside it (the local coordinates then decide
+// it exactly, their error being ~1e-10 m); otherwise, and always in the FP64 form, the key
+// is the FP64 definition.
 // Cell of a position given as an FP32 pair p relative to the bed corner (split-Kahan form):
 // the q with corner[q] <= p < corner[q+1], corners being FP32 pairs too; the differences
 // hi - c_hi are exact (Sterbenz), so the test and the local coordinate agree.
@@ -190,7 +195,6 @@ __global__ void k_key(StepView<P> V, int drift) {
   bool fast = false;
   unsigned key = 0;
   int ix = 0, iy = 0, iz = 0;
-  float4 xl_fast = make_float4(0.f, 0.f, 0.f, 0.f);
   if (drift) {
     R disp[3];
 #pragma unroll
@@ -225,19 +229,14 @@ __global__ void k_key(StepView<P> V, int drift) {
     }
     if (s2 > (float)bp.half_skin2) atomicOr(V.rebuild, 1);
     if constexpr (!P::exact) {
-      // the local coordinates in the previous cell: a parcel still more than 1e-3 of an edge
-      // inside it is in that cell (their error is ~1e-10 m), and they are its new ones
-      const unsigned kp = V.keyp[i];
-      int jx, jy, jz;
-      key_cell(B, kp, jx, jy, jz);
-      const float4 u = local_coords<P>(V, B, jx, jy, jz, x, y, z, p2, 0.f);
+      const float4 o = V.xl[i];
       const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
-      fast = u.x > 1e-3f * hx && u.x < 0.999f * hx && u.y > 1e-3f * hy && u.y < 0.999f * hy &&
-             u.z > 1e-3f * hz && u.z < 0.999f * hz;
+      const float ux = o.x + (float)disp[0], uy = o.y + (float)disp[1], uz = o.z + (float)disp[2];
+      fast = ux > 1e-3f * hx && ux < 0.999f * hx && uy > 1e-3f * hy && uy < 0.999f * hy &&
+             uz > 1e-3f * hz && uz < 0.999f * hz;
       if (fast) {
-        key = kp;
-        ix = jx; iy = jy; iz = jz;
-        xl_fast = u;
+        key = V.keyp[i];
+        key_cell(B, key, ix, iy, iz);
       }
     }
   }
@@ -264,13 +263,7 @@ __global__ void k_key(StepView<P> V, int drift) {
     if (key != V.keyp[i]) atomicAdd(V.moved + (sp >> 10), 1);
   }
   V.keyp[i] = key;
-  const float r = (float)(bp.k * V.A.d[i]) * 0.5f;
-  if (fast) {
-    xl_fast.w = r;
-    V.xl[i] = xl_fast;
-  } else {
-    V.xl[i] = local_coords<P>(V, B, ix, iy, iz, x, y, z, p2, r);
-  }
+  V.xl[i] = local_coords<P>(V, B, ix, iy, iz, x, y, z, p2, (float)(bp.k * V.A.d[i]) * 0.5f);
 }
 
 // Sorted-position range of every occupied cell, and the sorted position of every storage
