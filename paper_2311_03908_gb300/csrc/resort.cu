@@ -150,21 +150,6 @@ __device__ __forceinline__ int count_less(const unsigned long long *c, int lo, i
 constexpr int RZ_MERGE = 256;
 constexpr int RZ_COARSE = 2048;
 constexpr int RZ_COARSE_MAX = 4096;   // table entries: n up to 8,388,608 uses the table
-constexpr int RZ_MC = 32;             // every RZ_MC-th mover composite goes to a shared table ...
-constexpr int RZ_MC_MAX = 512;        // ... of at most this many entries (up to 16,384 movers)
-
-// movers with composite < v: a search in the shared table of every RZ_MC-th composite, then
-// within one RZ_MC-wide window of the sorted movers
-__device__ __forceinline__ int count_less_mc(const unsigned long long *c, int m, const unsigned long long *mc,
-                                             int nmc, unsigned long long v) {
-  int lo = 0, hi = nmc;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (mc[mid] < v) lo = mid + 1; else hi = mid;
-  }
-  if (lo == 0) return 0;
-  return count_less(c, (lo - 1) * RZ_MC + 1, min(lo * RZ_MC, m), v);
-}
 
 // first position p in [0, n) with kold[p] >= key (strict = false) or > key (strict = true)
 __device__ __forceinline__ int bound_in(const unsigned *kold, int n, const unsigned *coarse, int nc, unsigned key,
@@ -192,26 +177,14 @@ __global__ void __launch_bounds__(RZ_MERGE) rz_merge(const unsigned *kold, const
   const int g = blockIdx.x * RZ_MERGE + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const int w0 = g - lane;
-  __shared__ unsigned long long mct[RZ_MC_MAX];
-  const int nmc = (m + RZ_MC - 1) / RZ_MC;
-  const bool mtab = nmc <= RZ_MC_MAX;
-  if (mtab) {
-    for (int k = threadIdx.x; k < nmc; k += RZ_MERGE) mct[k] = sorted[k * RZ_MC];
-    __syncthreads();
-  }
   int lo = 0, hi = 0;
   if (w0 < n) {
     if (lane == 0) {
       const int g1 = min(w0 + 32, n) - 1;
       const unsigned long long c0 = ((unsigned long long)kold[w0] << 32) | (unsigned)w0;
       const unsigned long long c1 = ((unsigned long long)kold[g1] << 32) | (unsigned)g1;
-      if (mtab) {
-        lo = count_less_mc(sorted, m, mct, nmc, c0);
-        hi = count_less_mc(sorted, m, mct, nmc, c1 + 1);
-      } else {
-        lo = count_less(sorted, 0, m, c0);
-        hi = count_less(sorted, lo, m, c1 + 1);
-      }
+      lo = count_less(sorted, 0, m, c0);
+      hi = count_less(sorted, lo, m, c1 + 1);
     }
     lo = __shfl_sync(0xffffffffu, lo, 0);
     hi = __shfl_sync(0xffffffffu, hi, 0);
