@@ -143,32 +143,8 @@ __device__ __forceinline__ int count_less(const unsigned long long *c, int lo, i
 
 // output positions. A warp of stayers sees only the movers between the composites of its
 // first and last position (kold is sorted, so (kold[g], g) increases with g): two searches
-// per warp, then a short scan per thread. A mover's bounds in kold come from two searches:
-// first in a table of every RZ_COARSE-th key held in shared memory, then within one
-// RZ_COARSE-wide window of kold (a short chain of nearby, cached loads instead of ~21 loads
-// across the whole array).
+// per warp, then a short scan per thread.
 constexpr int RZ_MERGE = 256;
-constexpr int RZ_COARSE = 2048;
-constexpr int RZ_COARSE_MAX = 4096;   // table entries: n up to 8,388,608 uses the table
-
-// first position p in [0, n) with kold[p] >= key (strict = false) or > key (strict = true)
-__device__ __forceinline__ int bound_in(const unsigned *kold, int n, const unsigned *coarse, int nc, unsigned key,
-                                        bool strict) {
-  int lo = 0, hi = nc;   // first table entry k with kold[k * RZ_COARSE] past the key
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    const unsigned v = coarse[mid];
-    if (strict ? v <= key : v < key) lo = mid + 1; else hi = mid;
-  }
-  if (lo == 0) return 0;
-  int a = (lo - 1) * RZ_COARSE + 1, b = min(lo * RZ_COARSE, n);   // the bound lies in [a, b]
-  while (a < b) {
-    const int mid = (a + b) >> 1;
-    const unsigned v = kold[mid];
-    if (strict ? v <= key : v < key) a = mid + 1; else b = mid;
-  }
-  return a;
-}
 __global__ void __launch_bounds__(RZ_MERGE) rz_merge(const unsigned *kold, const unsigned *knew, int n,
                                                      const int *pre, const unsigned long long *sorted,
                                                      const unsigned *vmap, unsigned *kout, unsigned *vout) {
@@ -200,29 +176,16 @@ __global__ void __launch_bounds__(RZ_MERGE) rz_merge(const unsigned *kold, const
       vout[pos] = vmap ? vmap[g] : (unsigned)g;
     }
   }
-  __shared__ unsigned coarse[RZ_COARSE_MAX];
-  const int nc = (n + RZ_COARSE - 1) / RZ_COARSE;
-  const bool table = nc <= RZ_COARSE_MAX;
-  if (table && blockIdx.x * RZ_MERGE < m) {   // blocks with movers (block-uniform)
-    for (int k = threadIdx.x; k < nc; k += RZ_MERGE) coarse[k] = kold[k * RZ_COARSE];
-    __syncthreads();
-  }
   for (int t = g; t < m; t += gridDim.x * RZ_MERGE) {
     const unsigned long long c = sorted[t];
     const unsigned key = (unsigned)(c >> 32);
     const int idx = (int)(c & 0xffffffffu);
-    int lb, ub;
-    if (table) {
-      lb = bound_in(kold, n, coarse, nc, key, false);
-      ub = bound_in(kold, n, coarse, nc, key, true);
-    } else {
-      int lo = 0, hi = n;
-      while (lo < hi) { const int mid = (lo + hi) >> 1; if (kold[mid] < key) lo = mid + 1; else hi = mid; }
-      lb = lo;
-      hi = n;
-      while (lo < hi) { const int mid = (lo + hi) >> 1; if (kold[mid] <= key) lo = mid + 1; else hi = mid; }
-      ub = lo;
-    }
+    int lo = 0, hi = n;
+    while (lo < hi) { const int mid = (lo + hi) >> 1; if (kold[mid] < key) lo = mid + 1; else hi = mid; }
+    const int lb = lo;
+    hi = n;
+    while (lo < hi) { const int mid = (lo + hi) >> 1; if (kold[mid] <= key) lo = mid + 1; else hi = mid; }
+    const int ub = lo;
     const int x = idx < lb ? lb : (idx > ub ? ub : idx);
     const int pos = t + (x - pre[x]);
     kout[pos] = key;
