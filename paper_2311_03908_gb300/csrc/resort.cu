@@ -141,9 +141,31 @@ __device__ __forceinline__ int count_less(const unsigned long long *c, int lo, i
   return lo;
 }
 
+// Movers in c[lo, hi) below v, by the whole warp: each round every lane tests one of 32
+// evenly spaced entries and the ballot narrows the range 32-fold (three dependent loads for
+// a few thousand movers instead of a dozen). All 32 lanes must call it together.
+__device__ __forceinline__ int warp_count_less(const unsigned long long *c, int lo, int hi, unsigned long long v,
+                                               int lane) {
+  while (hi > lo) {
+    const int len = hi - lo;
+    if (len <= 32) {
+      const bool lt = lane < len && c[lo + lane] < v;
+      return lo + __popc(__ballot_sync(0xffffffffu, lt));
+    }
+    const int s = (len + 31) / 32;
+    const int p = lo + lane * s;
+    const int k = __popc(__ballot_sync(0xffffffffu, p < hi && c[p] < v));   // samples below v
+    const int nlo = k > 0 ? lo + (k - 1) * s + 1 : lo;
+    hi = min(lo + k * s, hi);
+    lo = nlo;
+  }
+  return lo;
+}
+
 // output positions. A warp of stayers sees only the movers between the composites of its
 // first and last position (kold is sorted, so (kold[g], g) increases with g): two searches
-// per warp, then a short scan per thread.
+// per warp, then a short scan per thread. The per-position loads are issued before the
+// searches, so that their latency overlaps.
 constexpr int RZ_MERGE = 256;
 __global__ void __launch_bounds__(RZ_MERGE) rz_merge(const unsigned *kold, const unsigned *knew, int n,
                                                      const int *pre, const unsigned long long *sorted,
@@ -153,28 +175,31 @@ __global__ void __launch_bounds__(RZ_MERGE) rz_merge(const unsigned *kold, const
   const int g = blockIdx.x * RZ_MERGE + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const int w0 = g - lane;
-  int lo = 0, hi = 0;
-  if (w0 < n) {
-    if (lane == 0) {
-      const int g1 = min(w0 + 32, n) - 1;
-      const unsigned long long c0 = ((unsigned long long)kold[w0] << 32) | (unsigned)w0;
-      const unsigned long long c1 = ((unsigned long long)kold[g1] << 32) | (unsigned)g1;
-      lo = count_less(sorted, 0, m, c0);
-      hi = count_less(sorted, lo, m, c1 + 1);
-    }
-    lo = __shfl_sync(0xffffffffu, lo, 0);
-    hi = __shfl_sync(0xffffffffu, hi, 0);
-  }
+  unsigned key = 0u, ko = 0u, vg = 0u;
+  int pg = 0;
   if (g < n) {
-    const unsigned key = knew[g];
-    if (key == kold[g]) {   // stayer
-      const unsigned long long c = ((unsigned long long)key << 32) | (unsigned)g;
-      int below = lo;
-      for (int t = lo; t < hi; ++t) below += sorted[t] < c ? 1 : 0;
-      const int pos = g - pre[g] + below;
-      kout[pos] = key;
-      vout[pos] = vmap ? vmap[g] : (unsigned)g;
-    }
+    key = knew[g];
+    ko = kold[g];
+    pg = pre[g];
+    vg = vmap ? vmap[g] : (unsigned)g;
+  }
+  int lo = 0, hi = 0;
+  if (w0 < n) {   // warp-uniform
+    const int g1 = min(w0 + 32, n) - 1;
+    const unsigned k0 = __shfl_sync(0xffffffffu, ko, 0);
+    const unsigned k1 = __shfl_sync(0xffffffffu, ko, g1 - w0);
+    const unsigned long long c0 = ((unsigned long long)k0 << 32) | (unsigned)w0;
+    const unsigned long long c1 = ((unsigned long long)k1 << 32) | (unsigned)g1;
+    lo = warp_count_less(sorted, 0, m, c0, lane);
+    hi = warp_count_less(sorted, lo, m, c1 + 1, lane);
+  }
+  if (g < n && key == ko) {   // stayer
+    const unsigned long long c = ((unsigned long long)key << 32) | (unsigned)g;
+    int below = lo;
+    for (int t = lo; t < hi; ++t) below += sorted[t] < c ? 1 : 0;
+    const int pos = g - pg + below;
+    kout[pos] = key;
+    vout[pos] = vg;
   }
   for (int t = g; t < m; t += gridDim.x * RZ_MERGE) {
     const unsigned long long c = sorted[t];
