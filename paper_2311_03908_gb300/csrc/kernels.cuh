@@ -267,21 +267,45 @@ __global__ void k_key(StepView<P> V, int drift) {
 }
 
 // Sorted-position range of every occupied cell, and the sorted position of every storage
-// position (the next step's key kernel scatters its keys through it).
+// position (the next step's key kernel scatters its keys through it). Four consecutive
+// sorted positions per thread (vector loads of keys and permutation).
 template <class P>
 __global__ void k_ranges(StepView<P> V) {
   pdl_wait();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= V.n) return;
-  if (i == 0 && *V.rebuild) *V.novf = 0;   // a list build lists the overflowed parcels anew
-  if (i < (V.n + 1023) / 1024) V.moved[i] = 0;   // the re-sort is done with the counts: zero for the next step
-  const unsigned k = V.keys[i];
-  if (i == 0 || V.keys[i - 1] != k) V.cstart[k] = (unsigned)i;
-  if (i == V.n - 1 || V.keys[i + 1] != k) V.cend[k] = (unsigned)(i + 1);
-  const unsigned j = V.vals[i];
-  V.inv[j] = (unsigned)i;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i0 = 4 * q;
+  if (i0 >= V.n) return;
+  if (q == 0 && *V.rebuild) *V.novf = 0;   // a list build lists the overflowed parcels anew
+  if (q < (V.n + 1023) / 1024) V.moved[q] = 0;   // the re-sort is done with the counts: zero for the next step
   // a search of every parcel without a re-store reads the local coordinates in sorted order
-  if ((*V.rebuild || V.nolists) && !restore_now(V)) V.xls[i] = V.xl[j];
+  const bool copy = (*V.rebuild || V.nolists) && !restore_now(V);
+  const int cnt = min(4, V.n - i0);
+  unsigned k[4], j[4];
+  if (cnt == 4) {
+    const uint4 kk = *reinterpret_cast<const uint4 *>(V.keys + i0);
+    const uint4 jj = *reinterpret_cast<const uint4 *>(V.vals + i0);
+    k[0] = kk.x; k[1] = kk.y; k[2] = kk.z; k[3] = kk.w;
+    j[0] = jj.x; j[1] = jj.y; j[2] = jj.z; j[3] = jj.w;
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      k[u] = u < cnt ? V.keys[i0 + u] : 0u;
+      j[u] = u < cnt ? V.vals[i0 + u] : 0u;
+    }
+  }
+  const bool has_prev = i0 > 0, has_next = i0 + cnt < V.n;
+  const unsigned kprev = has_prev ? V.keys[i0 - 1] : 0u, knext = has_next ? V.keys[i0 + cnt] : 0u;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    if (u >= cnt) break;
+    const int i = i0 + u;
+    const bool first = u == 0 ? (!has_prev || kprev != k[0]) : k[u - 1] != k[u];
+    const bool last = u == cnt - 1 ? (!has_next || knext != k[u]) : k[u + 1] != k[u];
+    if (first) V.cstart[k[u]] = (unsigned)i;
+    if (last) V.cend[k[u]] = (unsigned)(i + 1);
+    V.inv[j[u]] = (unsigned)i;
+    if (copy) V.xls[i] = V.xl[j[u]];
+  }
 }
 
 // Re-store (list-build steps, and the first binning): copy every parcel's record, local

@@ -111,7 +111,7 @@ int enqueue_binning(dem_ctx *c, int drift) {
     if (e) return e;
     prof_end(c, ps);
     ps = prof_begin(c, "k_ranges");   // the key kernel emptied the previous step's ranges
-    launch_k(pdl, k_ranges<P>, grid_for(c->n, c->bs_gather), c->bs_gather, st, V);
+    launch_k(pdl, k_ranges<P>, grid_for((c->n + 3) / 4, c->bs_gather), c->bs_gather, st, V);
     prof_end(c, ps);
     ++c->launches;
   } else {
@@ -129,7 +129,7 @@ int enqueue_binning(dem_ctx *c, int drift) {
     }
     cudaMemsetAsync(c->cstart, 0, sizeof(unsigned) * c->ncells, st);
     cudaMemsetAsync(c->cend, 0, sizeof(unsigned) * c->ncells, st);
-    k_ranges<P><<<grid_for(c->n, 256), 256, 0, st>>>(V);
+    k_ranges<P><<<grid_for((c->n + 3) / 4, 256), 256, 0, st>>>(V);
     prof_end(c, ps);
     c->launches += 2;
   }

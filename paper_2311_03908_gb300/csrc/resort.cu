@@ -86,23 +86,27 @@ __device__ __forceinline__ void cmpswap(unsigned long long &a, unsigned long lon
 }
 
 // rank of every mover by counting the movers below it (composites are unique), written to
-// sorted[rank]; more than RZ_SMEM_SORT movers: left to rz_sort_big
+// sorted[rank]; RZ_RANK_SPLIT consecutive lanes share a mover and count a share of the others
+// each; more than RZ_SMEM_SORT movers: left to rz_sort_big
+constexpr int RZ_RANK_SPLIT = 8;
 __global__ void __launch_bounds__(256) rz_rank(const int *blk, int nb, const unsigned long long *comp,
                                                unsigned long long *sorted) {
   pdl_wait();
   __shared__ unsigned long long s[RZ_SMEM_SORT];
   const int m = blk[nb];
   if (m > RZ_SMEM_SORT) return;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (blockIdx.x * blockDim.x >= m) return;   // whole block beyond the movers
+  if (blockIdx.x * blockDim.x >= m * RZ_RANK_SPLIT) return;   // whole block beyond the movers
   for (int q = threadIdx.x; q < m; q += blockDim.x) s[q] = comp[q];
   __syncthreads();
-  if (t < m) {
-    const unsigned long long v = s[t];
-    int r = 0;
-    for (int q = 0; q < m; ++q) r += s[q] < v ? 1 : 0;
-    sorted[r] = v;
-  }
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) / RZ_RANK_SPLIT;
+  const int part = threadIdx.x % RZ_RANK_SPLIT;
+  const unsigned long long v = t < m ? s[t] : 0ull;
+  int r = 0;
+  if (t < m)
+    for (int q = part; q < m; q += RZ_RANK_SPLIT) r += s[q] < v ? 1 : 0;
+#pragma unroll
+  for (int o = RZ_RANK_SPLIT / 2; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o, RZ_RANK_SPLIT);
+  if (t < m && part == 0) sorted[r] = v;
 }
 
 // more movers than fit: one block sorts them in global memory (bitonic; padded with the
@@ -233,7 +237,7 @@ int resort_pairs(const unsigned *kold, const unsigned *knew, const unsigned *vma
   int *blk = pre + n + 1;
   launch_k(pdl, rz_scan, 1, RZ_BLOCK, st, blk, nb);
   launch_k(pdl, rz_compact, nb, RZ_BLOCK, st, kold, knew, n, (const int *)blk, nb, pre, comp);
-  launch_k(pdl, rz_rank, RZ_SMEM_SORT / 256, 256, st, (const int *)blk, nb, (const unsigned long long *)comp, sorted);
+  launch_k(pdl, rz_rank, RZ_SMEM_SORT * RZ_RANK_SPLIT / 256, 256, st, (const int *)blk, nb, (const unsigned long long *)comp, sorted);
   launch_k(pdl, rz_sort_big, 1, RZ_BLOCK, st, (const int *)blk, nb, (const unsigned long long *)comp, sorted, pow2);
   launch_k(pdl, rz_merge, (n + RZ_MERGE - 1) / RZ_MERGE, RZ_MERGE, st, kold, knew, n, (const int *)pre,
            (const unsigned long long *)sorted, vmap, kout, vout);
