@@ -49,36 +49,67 @@ __global__ void __launch_bounds__(RZ_BLOCK) rz_scan(int *blk, int nb) {
   if (threadIdx.x == RZ_BLOCK - 1) blk[nb] = part[RZ_BLOCK - 1];
 }
 
-// movers before each position (pre[0..n], pre[n] = total) and the compacted movers
-__global__ void __launch_bounds__(RZ_BLOCK) rz_compact(const unsigned *kold, const unsigned *knew, int n,
-                                                       const int *blk, int nb, int *pre,
-                                                       unsigned long long *comp) {
+// movers before each position (pre[0..n], pre[n] = total) and the compacted movers; a block
+// of RZ_COMPACT threads covers RZ_BLOCK positions, four consecutive ones per thread (vector
+// loads and stores)
+constexpr int RZ_COMPACT = RZ_BLOCK / 4;
+__global__ void __launch_bounds__(RZ_COMPACT) rz_compact(const unsigned *kold, const unsigned *knew, int n,
+                                                         const int *blk, int nb, int *pre,
+                                                         unsigned long long *comp) {
   pdl_wait();
-  __shared__ int wsum[RZ_BLOCK / 32];
-  const int i = blockIdx.x * RZ_BLOCK + threadIdx.x;
+  __shared__ int wsum[RZ_COMPACT / 32];
+  const int i0 = blockIdx.x * RZ_BLOCK + 4 * threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned key = i < n ? knew[i] : 0u;
-  const bool moved = i < n && key != kold[i];
-  const unsigned m = __ballot_sync(0xffffffffu, moved);
-  if (lane == 0) wsum[warp] = __popc(m);
+  unsigned kn[4] = {0u, 0u, 0u, 0u};
+  bool mv[4] = {false, false, false, false};
+  if (i0 + 4 <= n) {
+    const uint4 a = *reinterpret_cast<const uint4 *>(knew + i0);
+    const uint4 b = *reinterpret_cast<const uint4 *>(kold + i0);
+    kn[0] = a.x; kn[1] = a.y; kn[2] = a.z; kn[3] = a.w;
+    mv[0] = a.x != b.x; mv[1] = a.y != b.y; mv[2] = a.z != b.z; mv[3] = a.w != b.w;
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (i0 + u < n) { kn[u] = knew[i0 + u]; mv[u] = kn[u] != kold[i0 + u]; }
+  }
+  const int c = (int)mv[0] + (int)mv[1] + (int)mv[2] + (int)mv[3];
+  int incl = c;   // inclusive scan of the counts over the warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) wsum[warp] = incl;
   __syncthreads();
   if (warp == 0) {
-    const int v = wsum[lane];
-    int incl = v;
+    const int v = lane < RZ_COMPACT / 32 ? wsum[lane] : 0;
+    int wi = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
+      const int t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
     }
-    wsum[lane] = incl - v;
+    if (lane < RZ_COMPACT / 32) wsum[lane] = wi - v;
   }
   __syncthreads();
-  const int rank = blk[blockIdx.x] + wsum[warp] + __popc(m & ((1u << lane) - 1u));
-  if (i < n) {
-    pre[i] = rank;
-    if (moved) comp[rank] = ((unsigned long long)key << 32) | (unsigned)i;
+  int rank = blk[blockIdx.x] + wsum[warp] + incl - c;
+  int r[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    r[u] = rank;
+    if (mv[u]) {
+      comp[rank] = ((unsigned long long)kn[u] << 32) | (unsigned)(i0 + u);
+      ++rank;
+    }
   }
-  if (i == n - 1) pre[n] = blk[nb];
+  if (i0 + 4 <= n) {
+    *reinterpret_cast<int4 *>(pre + i0) = make_int4(r[0], r[1], r[2], r[3]);
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (i0 + u < n) pre[i0 + u] = r[u];
+  }
+  if (i0 <= n - 1 && n - 1 < i0 + 4) pre[n] = blk[nb];
 }
 
 __device__ __forceinline__ void cmpswap(unsigned long long &a, unsigned long long &b, bool asc) {
@@ -236,7 +267,7 @@ int resort_pairs(const unsigned *kold, const unsigned *knew, const unsigned *vma
   int *pre = reinterpret_cast<int *>(scratch + 4 * (size_t)pow2);
   int *blk = pre + n + 1;
   launch_k(pdl, rz_scan, 1, RZ_BLOCK, st, blk, nb);
-  launch_k(pdl, rz_compact, nb, RZ_BLOCK, st, kold, knew, n, (const int *)blk, nb, pre, comp);
+  launch_k(pdl, rz_compact, nb, RZ_COMPACT, st, kold, knew, n, (const int *)blk, nb, pre, comp);
   launch_k(pdl, rz_rank, RZ_SMEM_SORT * RZ_RANK_SPLIT / 256, 256, st, (const int *)blk, nb, (const unsigned long long *)comp, sorted);
   launch_k(pdl, rz_sort_big, 1, RZ_BLOCK, st, (const int *)blk, nb, (const unsigned long long *)comp, sorted, pow2);
   launch_k(pdl, rz_merge, (n + RZ_MERGE - 1) / RZ_MERGE, RZ_MERGE, st, kold, knew, n, (const int *)pre,
