@@ -388,20 +388,33 @@ __global__ void k_restore_in(StepView<P> V, int force) {
 // survivors on the FP64 positions with the oracle's expression, so its pair sets are
 // bit-exact. Walls: FP32 pre-screen, FP64 distances for the primitives within reach.
 // ---------------------------------------------------------------------------------------
+// the parcel's contact history before the step: its count and the first partners, loaded
+// once per parcel (the rest, if any, are read from memory)
+constexpr int HPRE = 4;
+struct HistIn {
+  int cin;
+  int id[HPRE];
+};
+
 template <class P>
-__device__ __forceinline__ void add_contact(const StepView<P> &V, int i, int cin, int pid, const BedP<typename P::R> &bp,
+__device__ __forceinline__ void add_contact(const StepView<P> &V, int i, const HistIn &hin, int pid,
+                                            const BedP<typename P::R> &bp,
                                             typename P::R mstar, typename P::R ri, const typename P::R nrm[3],
                                             typename P::R delta, const typename P::R vrel[3],
                                             const typename P::R wi[3], typename P::R Fi[3], typename P::R Ti[3],
                                             int &cout) {
   using R = typename P::R;
   R xo[3] = {0, 0, 0};
-  for (int sl = 0; sl < cin; ++sl)
-    if (V.H.id[(size_t)sl * V.cap + i] == pid) {
+  int found = -1;
 #pragma unroll
-      for (int q = 0; q < 3; ++q) xo[q] = V.H.xi[(size_t)(sl * 3 + q) * V.cap + i];
-      break;
-    }
+  for (int sl = 0; sl < HPRE; ++sl)
+    if (found < 0 && sl < hin.cin && hin.id[sl] == pid) found = sl;
+  for (int sl = HPRE; found < 0 && sl < hin.cin; ++sl)
+    if (V.H.id[(size_t)sl * V.cap + i] == pid) found = sl;
+  if (found >= 0) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) xo[q] = V.H.xi[(size_t)(found * 3 + q) * V.cap + i];
+  }
   R Fc[3], Tc[3], xn[3];
   contact_force<R>(bp, mstar, ri, nrm, delta, vrel, xo, wi, Fc, Tc, xn);
 #pragma unroll
@@ -602,7 +615,7 @@ __device__ __forceinline__ void pair_contact(const StepView<P> &V, int i, int j,
                                              const BedP<typename P::R> &bp, const float4 &me, float hx, float hy,
                                              float hz, const double *xi_d, double ri_d, typename P::R ri,
                                              typename P::R mi, const typename P::R vi[3], const typename P::R wi[3],
-                                             int cin, typename P::R Fi[3], typename P::R Ti[3], int &cout) {
+                                             const HistIn &hin, typename P::R Fi[3], typename P::R Ti[3], int &cout) {
   using R = typename P::R;
   R nrm[3], delta;
   double rj_d = 0;
@@ -634,7 +647,7 @@ __device__ __forceinline__ void pair_contact(const StepView<P> &V, int i, int j,
   vrel[0] = (vi[0] - V.A.v[0][j]) + (ws[1] * nrm[2] - ws[2] * nrm[1]);
   vrel[1] = (vi[1] - V.A.v[1][j]) + (ws[2] * nrm[0] - ws[0] * nrm[2]);
   vrel[2] = (vi[2] - V.A.v[2][j]) + (ws[0] * nrm[1] - ws[1] * nrm[0]);
-  add_contact<P>(V, i, cin, V.A.orig[j], bp, mstar, ri, nrm, delta, vrel, wi, Fi, Ti, cout);
+  add_contact<P>(V, i, hin, V.A.orig[j], bp, mstar, ri, nrm, delta, vrel, wi, Fi, Ti, cout);
 }
 
 // Contacts in two passes. The screen pass runs over every parcel: the neighbour-list test
@@ -717,7 +730,10 @@ __device__ __forceinline__ int contact_forces(const StepView<P> &V, int i, unsig
 #pragma unroll
   for (int q = 0; q < 3; ++q) { Fi[q] = 0; Ti[q] = 0; }
   int cout = 0;
-  const int cin = V.H.cnt[i];
+  HistIn hin;
+  hin.cin = V.H.cnt[i];
+#pragma unroll
+  for (int sl = 0; sl < HPRE; ++sl) hin.id[sl] = sl < hin.cin ? V.H.id[(size_t)sl * V.cap + i] : 0;
   const float4 me = V.xl[i];
   const unsigned key = V.keyp[i];
   const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
@@ -737,7 +753,7 @@ __device__ __forceinline__ int contact_forces(const StepView<P> &V, int i, unsig
   const R ri = P::exact ? (R)ri_d : (R)me.w;
   for (int h = 0; h < nsearch; ++h)
     pair_contact<P>(V, i, V.plist[h * cap + i], V.pcode[h * cap + i], B, bp, me, hx, hy, hz, xi_d, ri_d, ri, mi,
-                    vi, wi, cin, Fi, Ti, cout);
+                    vi, wi, hin, Fi, Ti, cout);
   while (hits) {   // list order
     const int k = __ffs(hits) - 1;
     hits &= hits - 1u;
@@ -745,7 +761,7 @@ __device__ __forceinline__ int contact_forces(const StepView<P> &V, int i, unsig
     int dx, dy, dz;
     key_offset(B, key, V.keyp[j], dx, dy, dz);
     pair_contact<P>(V, i, j, (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1), B, bp, me, hx, hy, hz, xi_d, ri_d, ri, mi,
-                    vi, wi, cin, Fi, Ti, cout);
+                    vi, wi, hin, Fi, Ti, cout);
   }
   // walls: the FP32 pre-screen again, FP64 distances for the primitives within reach
   if (!(bp.flags & DEM_NO_CONTACTS) && wall_near<P>(V, B, bp, key, me)) {
@@ -763,7 +779,7 @@ __device__ __forceinline__ int contact_forces(const StepView<P> &V, int i, unsig
       vrel[0] = vi[0] + (wr[1] * nrm[2] - wr[2] * nrm[1]);
       vrel[1] = vi[1] + (wr[2] * nrm[0] - wr[0] * nrm[2]);
       vrel[2] = vi[2] + (wr[0] * nrm[1] - wr[1] * nrm[0]);
-      add_contact<P>(V, i, cin, -1 - p, bp, mi, ri, nrm, delta, vrel, wi, Fi, Ti, cout);
+      add_contact<P>(V, i, hin, -1 - p, bp, mi, ri, nrm, delta, vrel, wi, Fi, Ti, cout);
     }
   }
   V.Hn.cnt[i] = (unsigned char)cout;
