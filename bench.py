@@ -251,10 +251,10 @@ def reference_arm(args):
     bed = make_workload(args.workload, 0, args.parcels)
     import oracle
     n = min(args.cpu_sample, bed.n)
-    sub = bed.subset(np.arange(n)) if n < bed.n else bed
+    sub = bed.subset(np.arange(n)) if n < bed.n else bed   # parcel indices are shuffled
     o = oracle.Oracle(sub)
     ksteps = max(1, min(args.steps, 20))
-    wsteps = max(0, min(args.warmup, 2))
+    wsteps = max(0, min(args.warmup, 3))   # the timing rules' minimum, bounded: the oracle is slow
     o.step(wsteps)
     t0 = time.perf_counter()
     o.step(ksteps)
