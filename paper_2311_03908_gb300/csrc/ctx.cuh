@@ -46,7 +46,6 @@ struct dem_ctx {
   int *plist = nullptr;             // pair-search hit lists [KLIST][cap]
   unsigned char *pcode = nullptr, *pcnt = nullptr;
   int *nl = nullptr, *rebuild = nullptr;   // neighbour lists (storage positions), build flag
-  unsigned *kbuild = nullptr;      // cell keys at the last list build
   unsigned char *nlc = nullptr;
   double skin_frac = 0.1;         // neighbour-list skin as a fraction of the largest diameter
   int restore_every = 1;          // re-store the state in cell order at every k-th list build

@@ -351,7 +351,6 @@ void layout(dem_ctx *c, Bump &m) {
   c->pcode = m.take<unsigned char>(N * KLIST);
   c->pcnt = m.take<unsigned char>(N);
   c->nl = m.take<int>(N * KNL);
-  c->kbuild = m.take<unsigned>(N);
   c->nlc = m.take<unsigned char>(N);
   c->rebuild = m.take<int>(1);
   c->ovf = m.take<int>(N);
@@ -468,7 +467,6 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
   if (!out) return DEM_EINVAL;
   *out = nullptr;
   if (!beds || !p || n_beds < 1 || n_beds > DEM_MAX_BEDS || p->n <= 0) return DEM_EINVAL;
-  if (p->n > (1 << 27)) return DEM_EINVAL;   // neighbour-list entries hold 27-bit positions
   if (precision != DEM_PREC_FP64 && precision != DEM_PREC_SPLIT && precision != DEM_PREC_SPLIT_KAHAN) return DEM_EINVAL;
   if (!p->x || !p->y || !p->z || !p->vx || !p->vy || !p->vz || !p->d_real || !p->T || !p->ore_type || !p->bed)
     return DEM_EINVAL;
@@ -638,7 +636,6 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
     for (int q = 0; q < 3; ++q) ck(cudaMemsetAsync(c->pdsp[k][q], 0, sizeof(float) * (size_t)n, c->st));
   }
   ck(cudaMemsetAsync(c->nlc, 0, (size_t)n, c->st));
-  ck(cudaMemsetAsync(c->kbuild, 0, sizeof(unsigned) * (size_t)n, c->st));
   ck(cudaMemsetAsync(c->nwork, 0, sizeof(int), c->st));
   ck(cudaMemsetAsync(resort_counts(c->rsw, c->rs_pow2, n), 0, sizeof(int) * (size_t)((n + 1023) / 1024 + 1), c->st));
   // gas: cell -> bed, marks, initial state

@@ -22,11 +22,6 @@ template <class R> struct PState {
 // Verlet neighbour lists: slots per parcel, and the count that marks an overflowed list
 constexpr int KNL = 32;
 constexpr int NL_OVERFLOW = 255;
-// A neighbour-list entry holds the partner's storage position (low 27 bits) and the offset
-// code of the partner's cell relative to the parcel's at the build (high 5 bits: (dx + 1) +
-// 3 (dy + 1) + 9 (dz + 1)). While neither parcel has left its build cell (the sign bit of
-// the radius in its local-coordinate record marks one that has), the code is current.
-constexpr unsigned NL_POS_BITS = 27, NL_POS_MASK = (1u << NL_POS_BITS) - 1u;
 
 // Contact-history table: count per parcel, then KMAX slots of partner index and 3-vector.
 template <class R> struct Hist {
@@ -60,8 +55,7 @@ template <class P> struct StepView {
   int *plist;                   // [KLIST][cap] partners in contact range this step
   unsigned char *pcode;         // [KLIST][cap] their cell offset codes
   unsigned char *pcnt;          // number of them per parcel
-  int *nl;                      // [KNL][cap] neighbour lists (storage position | cell code << 27)
-  unsigned *kbuild;             // [cap] each parcel's cell key at the last list build
+  int *nl;                      // [KNL][cap] neighbour lists (storage positions)
   unsigned char *nlc;           // list lengths (NL_OVERFLOW: none, search the cells)
   int *rebuild;                 // device flag: rebuild the lists (and re-store) this step
   int nolists;                  // search the cell list every step instead of using lists
@@ -269,9 +263,7 @@ __global__ void k_key(StepView<P> V, int drift) {
     if (key != V.keyp[i]) atomicAdd(V.moved + (sp >> 10), 1);
   }
   V.keyp[i] = key;
-  // the radius, negative once the parcel is no longer in its cell of the last list build
-  const float r = (float)(bp.k * V.A.d[i]) * 0.5f;
-  V.xl[i] = local_coords<P>(V, B, ix, iy, iz, x, y, z, p2, key != V.kbuild[i] ? -r : r);
+  V.xl[i] = local_coords<P>(V, B, ix, iy, iz, x, y, z, p2, (float)(bp.k * V.A.d[i]) * 0.5f);
 }
 
 // Sorted-position range of every occupied cell, and the sorted position of every storage
@@ -493,7 +485,7 @@ __device__ __forceinline__ void pair_search(const StepView<P> &V, int i, bool re
       key_cell(B, key, X, Y, Z);
       // no partner centre lies farther than r_i + r_max (+ skin); the margin is far above
       // the ~1e-10 m resolution of the local coordinates
-      const float reach = (fabsf(me.w) + (float)bp.reach_max + skin) * 1.0001f + pm + 1e-9f;
+      const float reach = (me.w + (float)bp.reach_max + skin) * 1.0001f + pm + 1e-9f;
       const int xlo = (X > 0 && me.x < reach) ? -1 : 0, xhi = (X < B.nx - 1 && hx - me.x < reach) ? 1 : 0;
       const int ylo = (Y > 0 && me.y < reach) ? -1 : 0, yhi = (Y < B.ny - 1 && hy - me.y < reach) ? 1 : 0;
       const int zlo = (Z > 0 && me.z < reach) ? -1 : 0, zhi = (Z < B.nz - 1 && hz - me.z < reach) ? 1 : 0;
@@ -513,13 +505,13 @@ __device__ __forceinline__ void pair_search(const StepView<P> &V, int i, bool re
   do {                                                                                \
     const float ex = (o).x + ox, ey = (o).y + oy, ez = (o).z + oz; /* x_j - x_i */   \
     const float d2 = ex * ex + ey * ey + ez * ez;                                     \
-    const float rs = fabsf(me.w) + fabsf((o).w);                                      \
+    const float rs = me.w + (o).w;                                                    \
     const float lim = rs + pm, liml = rs + skin;                                      \
     const bool inl = build && d2 < liml * liml, inh = d2 < lim * lim;                 \
     if ((inl || inh) && (s) != si) {                                                  \
       const int j = (js);                                                             \
       if (inl) {                                                                      \
-        if (nn < KNL) V.nl[nn * cap + i] = (int)((unsigned)j | ((unsigned)code << NL_POS_BITS)); \
+        if (nn < KNL) V.nl[nn * cap + i] = j;                                         \
         ++nn;                                                                         \
       }                                                                               \
       if (inh) {                                                                      \
@@ -589,7 +581,6 @@ __device__ __forceinline__ void pair_search(const StepView<P> &V, int i, bool re
   if (rebuild) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) V.A.dsp[q][i] = 0.f;   // displacements count from this build
-    V.kbuild[i] = V.keyp[i];                            // and cells too
   }
   if (build) {
     V.nlc[i] = (unsigned char)(nn > KNL ? NL_OVERFLOW : nn);
@@ -642,13 +633,13 @@ __device__ __forceinline__ void pair_contact(const StepView<P> &V, int i, int j,
     const float4 o = __ldg(V.xl + j);
     const float ex = o.x + (cdx * hx - me.x), ey = o.y + (cdy * hy - me.y), ez = o.z + (cdz * hz - me.z);
     const float d2f = ex * ex + ey * ey + ez * ez;
-    const float rsf = fabsf(me.w) + fabsf(o.w);
+    const float rsf = me.w + o.w;
     const float df = sqrtf(d2f);
     const float inv = 1.0f / df;
     nrm[0] = (R)(ex * inv); nrm[1] = (R)(ey * inv); nrm[2] = (R)(ez * inv);
     delta = (R)((rsf * rsf - d2f) / (rsf + df));
   }
-  const R rj = P::exact ? (R)rj_d : (R)fabsf(__ldg(&V.xl[j].w));
+  const R rj = P::exact ? (R)rj_d : (R)__ldg(&V.xl[j].w);
   const R mj = parcel_mass<P>(V.A, j);
   const R mstar = mi * mj / (mi + mj);
   const R ws[3] = {ri * wi[0] + rj * V.A.w[0][j], ri * wi[1] + rj * V.A.w[1][j], ri * wi[2] + rj * V.A.w[2][j]};
@@ -680,7 +671,7 @@ __device__ __forceinline__ bool wall_near(const StepView<P> &V, const DevBed &B,
   wall_primitives<float>(bp, xa, ya, za, distf, nwf);
   bool near = false;
 #pragma unroll
-  for (int p = 0; p < 4; ++p) near |= distf[p] < fabsf(me.w) + 1e-6f;
+  for (int p = 0; p < 4; ++p) near |= distf[p] < me.w + 1e-6f;
   return near;
 }
 
@@ -700,37 +691,26 @@ __device__ __forceinline__ bool contact_screen(const StepView<P> &V, int i, unsi
   const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
   const size_t cap = (size_t)V.cap;
   const float pm = P::exact ? (float)bp.pf_margin : 0.f;
-  const bool moved = me.w < 0.f;   // the parcel left its cell of the build
-  const float mr = fabsf(me.w);
   for (int k0 = 0; k0 < listed; k0 += 4) {
-    unsigned e[4];
     int j[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      e[u] = k0 + u < listed ? (unsigned)V.nl[(k0 + u) * cap + i] : 0u;
-      j[u] = k0 + u < listed ? (int)(e[u] & NL_POS_MASK) : -1;
-    }
+    for (int u = 0; u < 4; ++u) j[u] = k0 + u < listed ? V.nl[(k0 + u) * cap + i] : -1;
+    unsigned kj[4];
     float4 o[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) o[u] = j[u] >= 0 ? __ldg(V.xl + j[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
-    // the partner's current key only where one of the two has left its build cell
-    unsigned kj[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) kj[u] = (j[u] >= 0 && (moved || o[u].w < 0.f)) ? V.keyp[j[u]] : key;
+    for (int u = 0; u < 4; ++u) {
+      kj[u] = j[u] >= 0 ? V.keyp[j[u]] : key;
+      o[u] = j[u] >= 0 ? __ldg(V.xl + j[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       if (j[u] < 0) continue;
       int dx, dy, dz;
-      if (moved || o[u].w < 0.f) {
-        key_offset(B, key, kj[u], dx, dy, dz);
-        if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) continue;   // cannot touch
-      } else {
-        const unsigned code = e[u] >> NL_POS_BITS;
-        dx = (int)(code % 3u) - 1; dy = (int)((code / 3u) % 3u) - 1; dz = (int)(code / 9u) - 1;
-      }
+      key_offset(B, key, kj[u], dx, dy, dz);
+      if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) continue;   // cannot touch
       const float ex = o[u].x + (dx * hx - me.x), ey = o[u].y + (dy * hy - me.y), ez = o[u].z + (dz * hz - me.z);
       const float d2 = ex * ex + ey * ey + ez * ez;
-      const float lim = mr + fabsf(o[u].w) + pm;
+      const float lim = me.w + o[u].w + pm;
       if (d2 < lim * lim) hits |= 1u << (k0 + u);
     }
   }
@@ -770,14 +750,14 @@ __device__ __forceinline__ int contact_forces(const StepView<P> &V, int i, unsig
     xi_d[0] = V.A.x[i]; xi_d[1] = V.A.y[i]; xi_d[2] = V.A.z[i];
     ri_d = __dmul_rn(0.5, __dmul_rn(B.k, (double)di));
   }
-  const R ri = P::exact ? (R)ri_d : (R)fabsf(me.w);
+  const R ri = P::exact ? (R)ri_d : (R)me.w;
   for (int h = 0; h < nsearch; ++h)
     pair_contact<P>(V, i, V.plist[h * cap + i], V.pcode[h * cap + i], B, bp, me, hx, hy, hz, xi_d, ri_d, ri, mi,
                     vi, wi, hin, Fi, Ti, cout);
   while (hits) {   // list order
     const int k = __ffs(hits) - 1;
     hits &= hits - 1u;
-    const int j = (int)((unsigned)V.nl[k * cap + i] & NL_POS_MASK);
+    const int j = V.nl[k * cap + i];
     int dx, dy, dz;
     key_offset(B, key, V.keyp[j], dx, dy, dz);
     pair_contact<P>(V, i, j, (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1), B, bp, me, hx, hy, hz, xi_d, ri_d, ri, mi,

@@ -58,7 +58,6 @@ StepView<P> make_view(dem_ctx *c, bool for_step) {
   V.pcode = c->pcode;
   V.pcnt = c->pcnt;
   V.nl = c->nl;
-  V.kbuild = c->kbuild;
   V.nlc = c->nlc;
   V.rebuild = c->rebuild;
   V.nolists = c->use_lists ? 0 : 1;
