@@ -130,9 +130,11 @@ typedef struct dem_ctx dem_ctx;
 
 /* Create a context: validates the inputs, allocates one device arena, copies the parcels
  * and bins them once. cuda_stream is a cudaStream_t (NULL = legacy default stream).
- * precision: DEM_PREC_FP64 (everything FP64), DEM_PREC_SPLIT (FP32 forces, drag, kinetics
- * and velocities; FP64 positions, layer masses and cell-source sums) or
- * DEM_PREC_SPLIT_KAHAN (as SPLIT but masses and cell sums in Kahan-compensated FP32).
+ * precision: DEM_PREC_FP64 (everything FP64), DEM_PREC_SPLIT (FP32 contact geometry,
+ * forces, drag, heat, kinetics and velocities; FP64 positions and layer masses; cell-source
+ * sums and the gas state in Kahan-compensated FP32) or DEM_PREC_SPLIT_KAHAN (as SPLIT but
+ * positions and layer masses as Kahan-compensated FP32 pairs too: no FP64 arithmetic in
+ * the step).
  * Errors: DEM_EINVAL for n <= 0, n_beds outside [1, DEM_MAX_BEDS], a bad grid, a parcel
  * outside its bed, coupling_interval < 1, k*d_p larger than a gas cell, or a time step at
  * or above the stability limit omega_0 dt >= 2 of the stiffest pair; DEM_ENOMEM/DEM_ECUDA. */
