@@ -165,6 +165,45 @@ __device__ __forceinline__ float4 local_coords(const StepView<P> &V, const DevBe
   }
 }
 
+// one parcel's inputs of the key kernel, loaded before any of its work, so that a thread's
+// two parcels have all their loads in flight together
+template <class P> struct KeyIn {
+  typename P::R v[3], a[3], w[3], al[3], d;
+  double x, y, z;
+  float2 p2[3];
+  float dsp[3];
+  float4 xl;
+  unsigned keyp, inv, kprev, kprev1;
+  int meta;
+};
+
+template <class P>
+__device__ __forceinline__ void key_load(const StepView<P> &V, int i, int drift, KeyIn<P> &in) {
+  if (drift) {
+    in.kprev = V.keys_prev[i];
+    in.kprev1 = i > 0 ? V.keys_prev[i - 1] : ~in.kprev;
+  }
+  in.meta = V.A.meta[i];
+  if constexpr (P::kahan) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) in.p2[q] = reinterpret_cast<const float2 *>(q == 0 ? V.A.x : q == 1 ? V.A.y : V.A.z)[i];
+    in.x = in.y = in.z = 0.0;
+  } else {
+    in.x = V.A.x[i]; in.y = V.A.y[i]; in.z = V.A.z[i];
+  }
+  if (drift) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      in.v[q] = V.A.v[q][i]; in.a[q] = V.A.a[q][i]; in.w[q] = V.A.w[q][i]; in.al[q] = V.A.al[q][i];
+      in.dsp[q] = V.A.dsp[q][i];
+    }
+    in.inv = V.inv[i];
+    if constexpr (!P::exact) in.xl = V.xl[i];
+  }
+  in.keyp = V.keyp[i];
+  in.d = V.A.d[i];
+}
+
 // First half kick (velocity and spin, written back) and drift of velocity Verlet, the gas
 // cell of the new position, and the FP32 cell-local coordinates; in place, storage order.
 // The FP32 forms take the key from the previous cell when the parcel stays more than 1e-3 of
@@ -172,26 +211,17 @@ __device__ __forceinline__ float4 local_coords(const StepView<P> &V, const DevBe
 // ~1e-10 m); otherwise, and always in the FP64 form, the key is recomputed from the
 // position: FP64 floor((x - x0) / dx), or in the split-Kahan form the pair comparison.
 template <class P>
-__global__ void k_key(StepView<P> V, int drift) {
-  pdl_wait();
+__device__ __forceinline__ void key_work(const StepView<P> &V, int i, int drift, KeyIn<P> &in) {
   using R = typename P::R;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= V.n) return;
-  if (drift) {   // empty the previous step's cell ranges (k_ranges writes this step's)
-    const unsigned kp = V.keys_prev[i];
-    if (i == 0 || V.keys_prev[i - 1] != kp) { V.cstart[kp] = 0u; V.cend[kp] = 0u; }
+  if (drift && in.kprev1 != in.kprev) {   // empty the previous step's cell ranges (k_ranges writes this step's)
+    V.cstart[in.kprev] = 0u;
+    V.cend[in.kprev] = 0u;
   }
-  const int b = V.A.meta[i] >> 8;
+  const int b = in.meta >> 8;
   const DevBed &B = V.beds[b];
   const BedP<R> &bp = V.bp[b];
-  double x = 0, y = 0, z = 0;
-  float2 p2[3];
-  if constexpr (P::kahan) {
-#pragma unroll
-    for (int q = 0; q < 3; ++q) p2[q] = reinterpret_cast<const float2 *>(q == 0 ? V.A.x : q == 1 ? V.A.y : V.A.z)[i];
-  } else {
-    x = V.A.x[i]; y = V.A.y[i]; z = V.A.z[i];
-  }
+  double x = in.x, y = in.y, z = in.z;
+  float2 p2[3] = {in.p2[0], in.p2[1], in.p2[2]};
   bool fast = false;
   unsigned key = 0;
   int ix = 0, iy = 0, iz = 0;
@@ -199,9 +229,9 @@ __global__ void k_key(StepView<P> V, int drift) {
     R disp[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      const R vh = half_kick<R>(bp.half_dt, B.dt, V.A.v[q][i], V.A.a[q][i]);
+      const R vh = half_kick<R>(bp.half_dt, B.dt, in.v[q], in.a[q]);
       V.A.v[q][i] = vh;
-      V.A.w[q][i] = V.A.w[q][i] + V.A.al[q][i] * bp.half_dt;
+      V.A.w[q][i] = in.w[q] + in.al[q] * bp.half_dt;
       if constexpr (sizeof(R) == 8) disp[q] = __dmul_rn(vh, B.dt);
       else disp[q] = vh * bp.dt;
     }
@@ -223,19 +253,19 @@ __global__ void k_key(StepView<P> V, int drift) {
     float s2 = 0.f;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      const float dq = V.A.dsp[q][i] + (float)disp[q];
+      const float dq = in.dsp[q] + (float)disp[q];
       V.A.dsp[q][i] = dq;
       s2 += dq * dq;
     }
     if (s2 > (float)bp.half_skin2) atomicOr(V.rebuild, 1);
     if constexpr (!P::exact) {
-      const float4 o = V.xl[i];
+      const float4 o = in.xl;
       const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
       const float ux = o.x + (float)disp[0], uy = o.y + (float)disp[1], uz = o.z + (float)disp[2];
       fast = ux > 1e-3f * hx && ux < 0.999f * hx && uy > 1e-3f * hy && uy < 0.999f * hy &&
              uz > 1e-3f * hz && uz < 0.999f * hz;
       if (fast) {
-        key = V.keyp[i];
+        key = in.keyp;
         key_cell(B, key, ix, iy, iz);
       }
     }
@@ -258,12 +288,27 @@ __global__ void k_key(StepView<P> V, int drift) {
   if (drift) {
     // the re-sort's input: the new key at the parcel's previous sorted position, and the
     // count of changed keys per 1024 sorted positions
-    const unsigned sp = V.inv[i];
-    V.knew[sp] = key;
-    if (key != V.keyp[i]) atomicAdd(V.moved + (sp >> 10), 1);
+    V.knew[in.inv] = key;
+    if (key != in.keyp) atomicAdd(V.moved + (in.inv >> 10), 1);
   }
   V.keyp[i] = key;
-  V.xl[i] = local_coords<P>(V, B, ix, iy, iz, x, y, z, p2, (float)(bp.k * V.A.d[i]) * 0.5f);
+  V.xl[i] = local_coords<P>(V, B, ix, iy, iz, x, y, z, p2, (float)(bp.k * in.d) * 0.5f);
+}
+
+// Two parcels per thread, 32 apart (each load instruction of a warp stays coalesced); all
+// the loads of both come first.
+template <class P>
+__global__ void k_key(StepView<P> V, int drift) {
+  pdl_wait();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i0 = (t >> 5) * 64 + (t & 31), i1 = i0 + 32;
+  if (i0 >= V.n) return;
+  const bool two = i1 < V.n;
+  KeyIn<P> a, b;
+  key_load<P>(V, i0, drift, a);
+  if (two) key_load<P>(V, i1, drift, b);
+  key_work<P>(V, i0, drift, a);
+  if (two) key_work<P>(V, i1, drift, b);
 }
 
 // Sorted-position range of every occupied cell, and the sorted position of every storage

@@ -100,7 +100,8 @@ int enqueue_binning(dem_ctx *c, int drift) {
   // the per-1024 counts of changed keys start at zero (k_ranges clears them after use)
   const bool pdl = !c->prof_on;   // per-kernel event timing wants plain stream order
   int ps = prof_begin(c, "k_key");
-  launch_k(pdl, k_key<P>, grid_for(c->n, c->bs_key), c->bs_key, st, V, drift);
+  // two parcels per thread, 32 apart: ceil(n / 64) warps
+  launch_k(pdl, k_key<P>, grid_for(((long long)c->n + 63) / 64 * 32, c->bs_key), c->bs_key, st, V, drift);
   prof_end(c, ps);
   ++c->launches;
   const int nxt = 1 - c->cur;
