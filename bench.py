@@ -243,6 +243,21 @@ def adjoint_cost(binding, stream):
             "grad": [float(v) for v in g]}
 
 
+def max_over_ranks(value: float, dist=None, device: str = "cpu") -> float:
+    """The largest of the ranks' values: a job's time is that of its slowest rank."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(n_per_rank: int, world: int, steps: int, ms_max: float) -> float:
+    """Parcel-updates/s of the whole job: every rank's parcels, over the slowest rank's time."""
+    return n_per_rank * world * steps / (ms_max * 1e-3)
+
+
 def reference_arm(args):
     """--impl reference: the oracle (FP64 CPU) on the host cores, same workload and metric."""
     rank = int(os.environ.get("RANK", "0"))
@@ -337,11 +352,8 @@ def main():
     ck = clocks.stop()
     ctx.dem_sync()
     c_post = ctx.dem_get_counters()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = n * world * args.steps / (ms_max * 1e-3)
+    ms_max = max_over_ranks(ms, dist, "cuda")
+    value = job_throughput(n, world, args.steps, ms_max)
 
     # per-kernel device times (CUDA events on the library's stream) over K plain steps
     ctx.dem_profile(True)
@@ -440,11 +452,8 @@ def main():
             ctx.dem_reduction_degree()
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        tt = torch.tensor([te], dtype=torch.float64, device="cuda")
-        if dist is not None:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = float(tt.item())
-        line["e2e"] = {"value": n * world * ke / te, "unit": UNIT, "steps": ke,
+        te = max_over_ranks(te, dist, "cuda")
+        line["e2e"] = {"value": job_throughput(n, world, ke, te * 1e3), "unit": UNIT, "steps": ke,
                        "h2d_bytes_per_step": int(nc * 4 * 8), "d2h_bytes_per_step": int(len(bed.beds) * 2 * 8),
                        "api": "dem_set_gas (pinned host) + dem_step_graph + dem_reduction_degree"}
 
