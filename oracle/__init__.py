@@ -33,7 +33,7 @@ for _i, _name in enumerate(
          "NZ", "DT", "KN", "KT_KN", "REST", "MU_S", "MU_R", "CG", "NCOUPLE", "U_IN", "T_IN", "P0",
          "Y_IN", "Y_IN1", "Y_IN2", "K0", "K01", "K02", "EA", "EA1", "EA2", "TAU", "PSI", "PSI1",
          "XI0", "XI01", "PORE", "PORE1", "RHOT", "RHOT1", "RHOT2", "RHOT3", "DPDZ", "EPS_MIN",
-         "FLAGS"]):
+         "FLAGS", "EMISS"]):
     _B[_name] = _i
 NB = len(_B)
 
@@ -46,7 +46,8 @@ STATE_NAMES = ["x", "y", "z", "vx", "vy", "vz", "wx", "wy", "wz", "T", "m_h", "m
 
 D_FC, D_TC, D_FD, D_K, D_QCONV, D_QR, D_QRM = 0, 3, 6, 9, 10, 11, 12
 D_XIDOT, D_MDOT, D_FFILM, D_A, D_B, D_SH, D_NU, D_RE, D_NCONTACT, D_CELL = 13, 16, 20, 21, 24, 27, 28, 29, 30, 31
-ND = 32
+D_TSE, D_QRAD = 32, 33
+ND = 34
 
 G_EPS, G_Y, G_T, G_MARK = 0, 1, 4, 5
 NG = 6
@@ -153,6 +154,7 @@ def bed_vector(cfg) -> np.ndarray:
     v[_B["DPDZ"]] = c["dpdz"]
     v[_B["EPS_MIN"]] = c["eps_min"]
     v[_B["FLAGS"]] = c["flags"]
+    v[_B["EMISS"]] = c["emissivity"]
     return v
 
 
@@ -239,8 +241,10 @@ class Oracle:
     def adjoint(self, nsteps: int, mode: int = 0, rel: float = 1e-6):
         J = np.zeros(1)
         g = np.zeros(6)
-        lib().orc_adjoint(self.h, int(nsteps), int(mode), float(rel),
-                          J.ctypes.data_as(C.POINTER(C.c_double)), g.ctypes.data_as(C.POINTER(C.c_double)))
+        st = lib().orc_adjoint(self.h, int(nsteps), int(mode), float(rel),
+                               J.ctypes.data_as(C.POINTER(C.c_double)), g.ctypes.data_as(C.POINTER(C.c_double)))
+        if st != 0:
+            raise ValueError("the adjoint map is per parcel: not defined with radiation switched on")
         return float(J[0]), g
 
 

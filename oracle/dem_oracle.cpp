@@ -23,6 +23,7 @@ namespace {
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kRg = 8.314;      // gas constant used by the paper, Sec. 2.1
 constexpr double kG = 9.81;        // gravity magnitude, -z
+constexpr double kSigma = 5.67e-8;  // Stefan-Boltzmann constant as printed with eq (3-16), W/m^2/K^4
 
 // Molar masses, kg/mol. Solids z: Fe2O3 (h), Fe3O4 (m), FeO (w), Fe; gases j: H2, H2O, N2.
 constexpr double kMz[4] = {159.69e-3, 231.533e-3, 71.844e-3, 55.845e-3};
@@ -779,6 +780,49 @@ void step_once(Oracle &o) {
       o.diag[(size_t)ORC_D_NCONTACT * n + i] = (double)cands.size();
     }
   }
+  // 2b. particle radiation, eqs (3-16), (3-17), (3-51), in beds that switch it on. T_se is
+  // the mean temperature over a sphere of radius 1.5 d around the parcel, with these
+  // readings: d is the parcel's own diameter k d_p (the neighbourhood is one of parcels);
+  // the parcel itself is one of the n_p,Omega parcels averaged (so n >= 1); a parcel is in
+  // the sphere when its centre is (d^2 < R^2, the pair test's expression); eps_g and T_g are
+  // those of the parcel's gas cell (eps_g lagged as in the drag); the temperatures are the
+  // ones before this step's update. The area is that of the real particle, pi d_p^2 (as in
+  // the convective heat), and k^3 scales it to the parcel (eq 3-51).
+  std::vector<double> Qrad(n, 0.0), Tse(n, 0.0);
+  for (int b = 0; b < o.nb; ++b) {
+    const double *bd = o.B(b);
+    if (!((unsigned)ib(bd, ORC_B_FLAGS) & ORC_RADIATION)) continue;
+    const auto &ids = o.members[b];
+    const double k = bd[ORC_B_CG];
+    double Rmax = 0.0;
+    for (int32_t i : ids) Rmax = std::max(Rmax, 1.5 * (k * o.dreal[i]));
+    const double *X = o.s[0].data(), *Y = o.s[1].data(), *Z = o.s[2].data();
+    const double *Tp = o.s[ORC_S_T].data();
+    CellList cl;   // cells of edge R_max: every centre within R lies in the 27 cells around
+    cl.build(ids, X, Y, Z, std::max(Rmax, 1e-12));
+    Grid g = make_grid(bd);
+#pragma omp parallel for schedule(dynamic, 256)
+    for (size_t t = 0; t < ids.size(); ++t) {
+      int32_t i = ids[t];
+      const double R = 1.5 * (k * o.dreal[i]);
+      double sumT = 0.0;
+      int64_t cnt = 0;
+      cl.neighbours(X[i], Y[i], Z[i], [&](int32_t j) {
+        if (!touching(X[i], Y[i], Z[i], X[j], Y[j], Z[j], R)) return;
+        sumT += Tp[j];
+        ++cnt;
+      });
+      bool outside = false;
+      int64_t c = o.cell_off[b] + cell_of(g, X[i], Y[i], Z[i], &outside);
+      const double eps = o.gas[c * ORC_NG + ORC_G_EPS];
+      const double Ts = eps * gp[c].T + (1.0 - eps) * (sumT / (double)cnt);   // eq (3-17)
+      const double dp = o.dreal[i];
+      const double Qp = kSigma * bd[ORC_B_EMISS] * (kPi * dp * dp) *
+                        (Ts * Ts * Ts * Ts - Tp[i] * Tp[i] * Tp[i] * Tp[i]);   // eq (3-16)
+      Qrad[i] = k * k * k * Qp;                                                 // eq (3-51)
+      Tse[i] = Ts;
+    }
+  }
   // 3. gas-particle terms, kinetics, second half kick, temperature and mass update
   std::vector<double> pdep((size_t)n * ORC_NDEP, 0.0);
   std::vector<int64_t> pcell(n, -1);
@@ -842,7 +886,7 @@ void step_once(Oracle &o) {
     double cpp = 0.0;
     for (int z = 0; z < 4; ++z) cpp += (m[z] / mp) * nasa_cp(3 + z, Tp);
     double Qrx = kn.Qr + kn.Qrm;
-    o.s[ORC_S_T][i] = Tp + dt * (Qconv + Qrx) / (mp * cpp);
+    o.s[ORC_S_T][i] = Tp + dt * (Qconv + Qrx + Qrad[i]) / (mp * cpp);
     // eq (3-4): layer masses change only at coupling steps (Sec. 4)
     if (coupled[b])
       for (int z = 0; z < 4; ++z) o.s[ORC_S_M + z][i] = std::max(m[z] + kn.mdot[z] * dtm, 0.0);
@@ -881,6 +925,8 @@ void step_once(Oracle &o) {
     dg[(size_t)ORC_D_NU * n + i] = Nu;
     dg[(size_t)ORC_D_RE * n + i] = Re;
     dg[(size_t)ORC_D_CELL * n + i] = (double)lc;
+    dg[(size_t)ORC_D_TSE * n + i] = Tse[i];
+    dg[(size_t)ORC_D_QRAD * n + i] = Qrad[i];
   }
   // 4. deposition: per-cell sums in parcel order (eqs (3-25), (3-27a), (3-38), (3-39),
   //    (4-4), (4-5), (4-10), (4-11)); only at coupling steps
@@ -1138,6 +1184,9 @@ void orc_destroy(void *h) { delete (Oracle *)h; }
 
 int32_t orc_adjoint(void *h, int32_t nsteps, int32_t mode, double rel, double *J, double *grad6) {
   Oracle *o = (Oracle *)h;
+  // the differentiated map is per parcel; radiation couples parcels through T_se
+  for (int b = 0; b < o->nb; ++b)
+    if ((unsigned)ib(o->B(b), ORC_B_FLAGS) & ORC_RADIATION) return -1;
   std::vector<GasProps> gp(o->ncell_total);
   for (int b = 0; b < o->nb; ++b) {
     const double *bd = o->B(b);

@@ -26,14 +26,15 @@ enum {
   ORC_B_T_IN, ORC_B_P0, ORC_B_Y_IN /* 3 */, ORC_B_K0 = ORC_B_Y_IN + 3, ORC_B_EA = ORC_B_K0 + 3,
   ORC_B_TAU = ORC_B_EA + 3, ORC_B_PSI /* 2 */, ORC_B_XI0 = ORC_B_PSI + 2,
   ORC_B_PORE = ORC_B_XI0 + 2, ORC_B_RHOT = ORC_B_PORE + 2, ORC_B_DPDZ = ORC_B_RHOT + 4,
-  ORC_B_EPS_MIN, ORC_B_FLAGS, ORC_NB
+  ORC_B_EPS_MIN, ORC_B_FLAGS, ORC_B_EMISS /* particle emissivity, eq (3-16) */, ORC_NB
 };
 
 /* physics switches (bit mask in ORC_B_FLAGS) */
 enum {
   ORC_NO_GRAVITY = 1, ORC_NO_DRAG = 2, ORC_NO_HEAT = 4, ORC_NO_KINETICS = 8,
   ORC_NO_GAS_UPDATE = 16, ORC_NO_FILM = 32, ORC_NO_LAYER = 64, ORC_NO_RXN_HEAT = 128,
-  ORC_NO_CONTACTS = 256
+  ORC_NO_CONTACTS = 256,
+  ORC_RADIATION = 512   /* switch ON the particle radiation of eqs (3-16), (3-17), (3-51) */
 };
 
 /* per-parcel state returned by orc_get_state: ORC_NS rows of n doubles */
@@ -49,7 +50,8 @@ enum {
   ORC_D_FD = 6 /* 3 drag force */, ORC_D_K = 9, ORC_D_QCONV, ORC_D_QR, ORC_D_QRM,
   ORC_D_XIDOT /* 3, mol/s per real particle, after limiting */ = 13,
   ORC_D_MDOT = 16 /* 4, kg/s per parcel */, ORC_D_FFILM = 20, ORC_D_A = 21 /* 3 */,
-  ORC_D_B = 24 /* 3 */, ORC_D_SH = 27, ORC_D_NU, ORC_D_RE, ORC_D_NCONTACT, ORC_D_CELL, ORC_ND
+  ORC_D_B = 24 /* 3 */, ORC_D_SH = 27, ORC_D_NU, ORC_D_RE, ORC_D_NCONTACT, ORC_D_CELL,
+  ORC_D_TSE /* eq (3-17), 0 without radiation */, ORC_D_QRAD /* eq (3-51), W per parcel */, ORC_ND
 };
 
 /* per gas cell: ORC_NG doubles */

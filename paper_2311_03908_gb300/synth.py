@@ -46,6 +46,7 @@ NO_FILM = 1 << 5
 NO_LAYER = 1 << 6
 NO_RXN_HEAT = 1 << 7
 NO_CONTACTS = 1 << 8
+RADIATION = 1 << 9   # switches ON the particle radiation (off by default)
 
 # Kinetic presets: (k0 [m/s], Ea [J/mol]) for R1 (h->m), R2 (m->w), R3 (w->Fe).
 TAKENAKA = ((29.17, 15.56, 2858.0), (66974.0, 75345.0, 117204.0))        # Table 2
@@ -132,7 +133,8 @@ class BedConfig:
     rho_true: tuple = (5300.0, 5180.0, 5390.0, 7900.0)  # Fe2O3, Fe3O4, FeO, Fe (Table 3)
     dpdz: float = 0.0                       # prescribed gas pressure gradient, Pa/m
     eps_min: float = 0.36                   # lower clamp of the gas volume fraction
-    flags: int = 0                          # physics switches (NO_* bits)
+    flags: int = 0                          # physics switches (NO_* bits, RADIATION)
+    emissivity: float = 0.85                # particle emissivity (Table 3), used with RADIATION
 
     def as_dict(self) -> dict:
         return dict(self.__dict__)
