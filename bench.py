@@ -53,24 +53,31 @@ def parse():
     ap.add_argument("--settle", type=int, default=300, help="untimed steps before the autotuner and the warm-up, so that the timed steps see the fluidised bed (contacts, list builds) rather than the packing at rest")
     ap.add_argument("--autotune", type=int, default=30, help="steps per autotuner candidate before the "
                     "warm-up (0: keep the default launch configuration)")
+    ap.add_argument("--radiation", action="store_true", help="switch on the particle radiation of "
+                    "eqs (3-16), (3-17), (3-51) in every bed (a widening of the step; off by default)")
     ap.add_argument("--tuning", default="", help="fixed launch configuration instead of the autotuner, "
                     "e.g. neighbour_lists=1,bs_key=64,skin_permille=50 (profiler runs repeat a plain run's)")
     return ap.parse_args()
 
 
-def make_workload(name: str, rank: int = 0, parcels: int = 0):
+def make_workload(name: str, rank: int = 0, parcels: int = 0, radiation: bool = False):
     from paper_2311_03908_gb300 import synth
     seed_shift = 7919 * rank
     kw = {"n": parcels} if parcels else {}
     if name == "ibm_2m":
-        return synth.config_ibm_2m(seed=2311039083 + seed_shift, **kw)
-    if name == "split_200k":
-        return synth.config_split_200k(seed=2311039082 + seed_shift, **kw)
-    if name == "plain_2k":
-        return synth.config_plain_2k(seed=2311039081 + seed_shift, **kw)
-    if name == "batched_32":
-        return synth.config_batched_32(seed=2311039085 + seed_shift)
-    raise ValueError(name)
+        bed = synth.config_ibm_2m(seed=2311039083 + seed_shift, **kw)
+    elif name == "split_200k":
+        bed = synth.config_split_200k(seed=2311039082 + seed_shift, **kw)
+    elif name == "plain_2k":
+        bed = synth.config_plain_2k(seed=2311039081 + seed_shift, **kw)
+    elif name == "batched_32":
+        bed = synth.config_batched_32(seed=2311039085 + seed_shift)
+    else:
+        raise ValueError(name)
+    if radiation:
+        for cfg in bed.beds:
+            cfg.flags |= synth.RADIATION
+    return bed
 
 
 # ---------------------------------------------------------------------------------------
@@ -110,6 +117,9 @@ def algorithmic_bytes(kernel: str, n: int, ncells: int, zbar: float, L: float, r
         return n * ((4 + 4 + R + 3 * R + R + 32 + 1 + fc * 6 * R + 3 * R) + (12 * R + R + 32 + 13 * R)) + ncells * 13 * R
     if kernel == "k_cells":
         return ncells * ((4 + 1 + 8 + 5 * 8 + 2 * R) + (5 * 8 + 14 * R)) + n * (6 * R + 4)
+    if kernel == "k_radiation":      # own meta, local coordinates, key, d, T (+ FP64 position); the
+        # cell's eps_g and T_g; Q_rad out (the neighbours' records are cache re-reads)
+        return n * ((4 + 16 + 4 + 2 * R + (24 if R == 8 else 0)) + R) + ncells * 2 * R
     return 0.0
 
 
@@ -263,7 +273,7 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    bed = make_workload(args.workload, 0, args.parcels)
+    bed = make_workload(args.workload, 0, args.parcels, args.radiation)
     import oracle
     n = min(args.cpu_sample, bed.n)
     sub = bed.subset(np.arange(n)) if n < bed.n else bed   # parcel indices are shuffled
@@ -279,7 +289,8 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": ksteps, "warmup": wsteps, "ms_per_step": 1e3 * dt / ksteps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}", "parcels_sampled": n, "precision": "fp64 oracle"},
+            "config": {"workload": f"{args.workload}", "parcels_sampled": n, "precision": "fp64 oracle",
+                       "radiation": bool(args.radiation)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -302,7 +313,7 @@ def main():
     torch.cuda.set_device(local)
     from paper_2311_03908_gb300 import binding
     stream = torch.cuda.current_stream()
-    bed = make_workload(args.workload, rank, args.parcels)
+    bed = make_workload(args.workload, rank, args.parcels, args.radiation)
     ctx = binding.Context(bed, precision=args.precision, stream=stream.cuda_stream)
     n = bed.n
     if args.settle > 0:
@@ -394,7 +405,7 @@ def main():
             "warmup": warm, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64" if args.precision != "fp64" else "f64", "data": "synthetic",
             "config": {"workload": f"{args.workload} ({bed.n} parcels, {ncells} gas cells, {len(bed.beds)} bed(s))",
-                       "precision": args.precision, "stepping": f"CUDA graph of {G} step(s), replayed", "settle_steps": args.settle,
+                       "precision": args.precision, "radiation": bool(args.radiation), "stepping": f"CUDA graph of {G} step(s), replayed", "settle_steps": args.settle,
                        "l2": "inputs larger than L2 (parcel state and history ~ 1 GB)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "gpu_launches": total_launches, "clocks": ck,

@@ -51,11 +51,17 @@ enum {
 
 enum { DEM_PREC_FP64 = 0, DEM_PREC_SPLIT = 1, DEM_PREC_SPLIT_KAHAN = 2 };
 
-/* physics switches (bit mask in dem_bed_config.flags); 0 = the full method */
+/* physics switches (bit mask in dem_bed_config.flags); 0 = the full method without
+ * radiation. DEM_RADIATION switches ON the particle radiation of eqs (3-16), (3-17) and
+ * (3-51): Q_rad = k^3 sigma eta_p pi d_p^2 (T_se^4 - T_p^4), T_se = eps_g T_g + (1 - eps_g)
+ * times the mean temperature of the parcels whose centres lie within 1.5 k d_p of the
+ * parcel's centre (the parcel itself included), eps_g and T_g those of the parcel's gas
+ * cell, all temperatures from before the step's update; Q_rad adds to the parcel's heat
+ * balance (eq 3-8) and, as the paper neglects gas radiation, not to the gas. */
 enum {
   DEM_NO_GRAVITY = 1, DEM_NO_DRAG = 2, DEM_NO_HEAT = 4, DEM_NO_KINETICS = 8,
   DEM_NO_GAS_UPDATE = 16, DEM_NO_FILM = 32, DEM_NO_LAYER = 64, DEM_NO_RXN_HEAT = 128,
-  DEM_NO_CONTACTS = 256
+  DEM_NO_CONTACTS = 256, DEM_RADIATION = 512
 };
 
 enum { DEM_WALL_FLAT = 0, DEM_WALL_CONE = 1 };
@@ -97,7 +103,9 @@ typedef struct {
   double rho_true[4];     /* true densities of Fe2O3, Fe3O4, FeO, Fe (Table 3) */
   double dpdz;            /* prescribed gas pressure gradient along z, Pa/m (force -V dp/dz) */
   double eps_min;         /* lower clamp of the gas volume fraction */
-  uint32_t flags;         /* DEM_NO_* switches */
+  uint32_t flags;         /* DEM_NO_* switches and DEM_RADIATION */
+  double emissivity;      /* particle emissivity eta_p of eq (3-16), in [0, 1] (Table 3: 0.85);
+                             read only with DEM_RADIATION */
 } dem_bed_config;
 
 /*
@@ -167,7 +175,8 @@ int dem_reduction_degree(dem_ctx *c, double *mean_per_bed, double *oxygen_per_be
  * adjoint kernel back through it. The context's state is not changed. Synchronous.
  * grad may be NULL: then only the forward sweep runs and only J is written. The sub-step
  * is evaluated in FP64 whatever the context's precision. Errors: DEM_EINVAL for n_steps < 0
- * or ckpt_every < 1; DEM_ENOMEM when the checkpoint and segment buffers (8 doubles per
+ * or ckpt_every < 1, and when a bed has DEM_RADIATION (radiation couples the parcels'
+ * temperatures, and the differentiated map is per parcel); DEM_ENOMEM when the checkpoint and segment buffers (8 doubles per
  * parcel per checkpoint and per sub-step of a segment) cannot be allocated. */
 int dem_adjoint(dem_ctx *c, int32_t n_steps, int32_t ckpt_every, double *J, double *grad);
 
@@ -199,8 +208,9 @@ int dem_get_contacts(dem_ctx *c, int32_t *count, int32_t *partner, double *xi);
 
 /* Per-parcel diagnostics of the last step (enable with dem_set_diagnostics before stepping),
  * DEM_NDIAG rows of n doubles (host), parcel-index order:
- * Fc(3) Tc(3) Fd(3) K Qconv Qr Qrm xidot(3) mdot(4) F_film A(3) B(3) Sh Nu Re ncontact cell */
-enum { DEM_NDIAG = 32 };
+ * Fc(3) Tc(3) Fd(3) K Qconv Qr Qrm xidot(3) mdot(4) F_film A(3) B(3) Sh Nu Re ncontact cell
+ * T_se Q_rad (the last two are 0 in beds without DEM_RADIATION) */
+enum { DEM_NDIAG = 34 };
 int dem_set_diagnostics(dem_ctx *c, int32_t on);
 int dem_get_diag(dem_ctx *c, double *out_host);
 

@@ -23,6 +23,7 @@ constexpr int KLIST = KMAX + 8;
 constexpr double kPI = 3.14159265358979323846;
 constexpr double kRgas = 8.314;  // gas constant of Sec. 2.1
 constexpr double kGrav = 9.81;
+constexpr double kSigmaSB = 5.67e-8;   // Stefan-Boltzmann constant printed with eq (3-16), W/m^2/K^4
 
 // kahan: layer masses and positions are compensated FP32 pairs (no FP64 arithmetic in the
 // step); exact: the FP64 form, whose pair tests follow the oracle bit for bit
@@ -50,7 +51,7 @@ static_assert((int)SR_N == (int)DEM_NDEP, "source rows");
 // diagnostics rows (same order as documented in dem.h)
 enum : int {
   DG_FC = 0, DG_TC = 3, DG_FD = 6, DG_K = 9, DG_QCONV, DG_QR, DG_QRM, DG_XIDOT = 13, DG_MDOT = 16,
-  DG_FFILM = 20, DG_A = 21, DG_B = 24, DG_SH = 27, DG_NU, DG_RE, DG_NCONTACT, DG_CELL, DG_N
+  DG_FFILM = 20, DG_A = 21, DG_B = 24, DG_SH = 27, DG_NU, DG_RE, DG_NCONTACT, DG_CELL, DG_TSE, DG_QRAD, DG_N
 };
 static_assert((int)DG_N == (int)DEM_NDIAG, "diag rows");
 
@@ -90,6 +91,7 @@ template <class R> struct BedP {
   R pf_margin;                  // prefilter margin of the exact (FP64) pair test, m
   R reach_max;                  // largest parcel radius of the bed (CGP), m
   R skin, half_skin2;           // neighbour-list skin (m) and (skin / 2)^2
+  R rad_c;                      // k^3 sigma eta_p pi: eqs (3-16) and (3-51) without d_p^2 and the temperatures
   unsigned flags;
   int ncouple, wall;
 };

@@ -81,6 +81,8 @@ struct dem_ctx {
   int *ovf = nullptr, *novf = nullptr;   // parcels whose neighbour list overflowed, and their count
   uint2 *work = nullptr;           // contact work list (parcel, list-hit mask)
   int *nwork = nullptr;            // its length
+  char *qrad = nullptr;            // radiation heat of each parcel this step (form's type)
+  bool any_rad = false;            // some bed has DEM_RADIATION: the radiation kernel runs
   std::map<std::tuple<int, int, int>, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;
   std::map<std::tuple<int, int, int>, long long> graph_launches;
   cudaStream_t gst = nullptr;     // private stream used to capture graphs

@@ -225,6 +225,7 @@ int validate_bed(const dem_bed_config &b) {
   for (int z = 0; z < 4; ++z) if (!(b.rho_true[z] > 0)) return DEM_EINVAL;
   for (int r = 0; r < 3; ++r) if (!(b.k0[r] >= 0 && b.Ea[r] >= 0)) return DEM_EINVAL;
   if (b.wall_kind != DEM_WALL_FLAT && b.wall_kind != DEM_WALL_CONE) return DEM_EINVAL;
+  if ((b.flags & DEM_RADIATION) && !(b.emissivity >= 0 && b.emissivity <= 1)) return DEM_EINVAL;
   if (b.wall_kind == DEM_WALL_CONE &&
       !(b.cone_half_angle > 0 && b.cone_half_angle < 1.5707963 && b.cone_height > 0 && b.hole_pitch > 0 &&
         b.hole_d > 0 && b.hole_d < b.hole_pitch && b.plate_z > 0 && b.plate_z < b.bed_H))
@@ -298,6 +299,8 @@ BedP<R> derive_params(const dem_bed_config &b, const DevBed &G) {
   P.grav = (b.flags & DEM_NO_GRAVITY) ? (R)0 : (R)(-kGrav);
   P.dtg = (R)(b.coupling_interval * b.dt);
   P.pf_margin = (R)1e-8;
+  P.rad_c = (b.flags & DEM_RADIATION)
+                ? (R)(b.cg_ratio * b.cg_ratio * b.cg_ratio * kSigmaSB * b.emissivity * kPI) : (R)0;
   P.flags = b.flags;
   P.ncouple = b.coupling_interval;
   P.wall = b.wall_kind;
@@ -357,6 +360,7 @@ void layout(dem_ctx *c, Bump &m) {
   c->novf = m.take<int>(1);
   c->work = m.take<uint2>(N);
   c->nwork = m.take<int>(1);
+  c->qrad = m.take<char>(N, R);
   c->corner = m.take<double>(c->hcorner.size());
   c->cornerp = m.take<float2>(c->hcornerp.size());
   for (int q = 0; q < 3; ++q) { c->F[q] = m.take<char>(N, R); c->Tq[q] = m.take<char>(N, R); }
@@ -528,6 +532,7 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
   c->rsize = precision == DEM_PREC_FP64 ? sizeof(double) : sizeof(float);
   c->st = (cudaStream_t)cuda_stream;
   c->cfg.assign(beds, beds + n_beds);
+  for (int b = 0; b < n_beds; ++b) c->any_rad = c->any_rad || (beds[b].flags & DEM_RADIATION) != 0;
   // per-bed constants and grid offsets; the gas cells are the cell list of the contact
   // search, so no parcel may be wider than a cell edge
   long long coff = 0, pacc = 0;
@@ -1128,6 +1133,7 @@ int dem_autotune(dem_ctx *c, int32_t n_steps) {
 
 int dem_adjoint(dem_ctx *c, int32_t n_steps, int32_t ckpt_every, double *J, double *grad) {
   if (!c || !J || n_steps < 0 || ckpt_every < 1) return DEM_EINVAL;
+  if (c->any_rad) return DEM_EINVAL;   // radiation couples the parcels; the map is per parcel
   int s = sync_all(c);
   if (s != DEM_OK) return s;
   return DEM_DISPATCH(c, run_adjoint, c, n_steps, ckpt_every, J, grad);

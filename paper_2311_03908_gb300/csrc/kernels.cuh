@@ -77,6 +77,7 @@ template <class P> struct StepView {
   uint2 *work;                  // contact work list: (parcel, list-hit mask) ...
   int *nwork;                   // ... and its length (reset by the step counter)
   const unsigned char *wnear;   // per cell: a wall may be within a parcel's reach
+  R *qrad;                      // radiation heat of each parcel this step (radiating beds)
 };
 
 // total layer mass of parcel i in the form's type (the same sum everywhere it is needed)
@@ -875,12 +876,97 @@ __global__ void k_contact_forces(StepView<P> V) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Particle radiation, eqs (3-16), (3-17), (3-51), in beds with DEM_RADIATION: one thread
+// per parcel (storage order). T_se averages the temperatures of the parcels whose centres
+// lie within R = 1.5 k d_p of the parcel's centre, the parcel itself included, weighted with
+// the gas cell's eps_g and T_g. No parcel is wider than a cell edge, so R < 2 edges and the
+// sphere lies in the 5 x 5 x 5 cells around the parcel's own; cells (and whole rows) farther
+// than R are skipped. The candidates are tested on the FP32 cell-local coordinates; the FP64
+// form re-tests every candidate within R plus a margin on the FP64 positions with the
+// oracle's expression, so its neighbourhoods are exact. Reads the temperatures before this
+// step's update (k_gas_particle runs after it); writes Q_rad and, with diagnostics, T_se.
+// T_se^4 - T_p^4 is evaluated as (T_se - T_p)(T_se + T_p)(T_se^2 + T_p^2), which keeps the
+// FP32 forms accurate when T_se is close to T_p.
+// ---------------------------------------------------------------------------------------
+template <class P>
+__global__ void __launch_bounds__(128) k_radiation(StepView<P> V) {
+  pdl_wait();
+  using R = typename P::R;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V.n) return;
+  const int b = V.A.meta[i] >> 8;
+  const BedP<R> &bp = V.bp[b];
+  if (!(bp.flags & DEM_RADIATION)) return;
+  const DevBed &B = V.beds[b];
+  const float4 me = V.xl[i];
+  const unsigned key = V.keyp[i];
+  const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
+  const R d = V.A.d[i];
+  double Rd = 0.0, xi_d[3] = {0.0, 0.0, 0.0};
+  if constexpr (P::exact) {
+    Rd = __dmul_rn(1.5, __dmul_rn(B.k, (double)d));
+    xi_d[0] = V.A.x[i]; xi_d[1] = V.A.y[i]; xi_d[2] = V.A.z[i];
+  }
+  const float rf = 1.5f * ((float)bp.k * (float)d);
+  const float hi = P::exact ? rf + (float)bp.pf_margin : rf;   // FP32 screen (with margin in FP64)
+  const float hi2 = hi * hi;
+  const float reach = hi * 1.0001f + 1e-9f;                    // cell pruning, with a margin
+  int X, Y, Z;
+  key_cell(B, key, X, Y, Z);
+  R sumT = 0;
+  int cnt = 0;
+  for (int dz = -2; dz <= 2; ++dz) {
+    if (Z + dz < 0 || Z + dz >= B.nz) continue;
+    const float gz = fmaxf(0.f, dz < 0 ? me.z - (dz + 1) * hz : dz * hz - me.z);   // gap to the layer
+    if (gz >= reach) continue;
+    const float oz = dz * hz - me.z;
+    for (int dy = -2; dy <= 2; ++dy) {
+      if (Y + dy < 0 || Y + dy >= B.ny) continue;
+      const float gy = fmaxf(0.f, dy < 0 ? me.y - (dy + 1) * hy : dy * hy - me.y);
+      if (gy * gy + gz * gz >= reach * reach) continue;
+      const float oy = dy * hy - me.y;
+      const unsigned krow = key + (unsigned)(dy * B.nx) + (unsigned)(dz * B.nx * B.ny);
+      for (int dx = -2; dx <= 2; ++dx) {
+        if (X + dx < 0 || X + dx >= B.nx) continue;
+        const float gx = fmaxf(0.f, dx < 0 ? me.x - (dx + 1) * hx : dx * hx - me.x);
+        if (gx * gx + gy * gy + gz * gz >= reach * reach) continue;
+        const float ox = dx * hx - me.x;
+        const unsigned jb = __ldg(V.cstart + krow + dx), je = __ldg(V.cend + krow + dx);
+        for (unsigned s = jb; s < je; ++s) {
+          const int j = (int)__ldg(V.vals + s);
+          const float4 o = __ldg(V.xl + j);
+          const float ex = o.x + ox, ey = o.y + oy, ez = o.z + oz;
+          bool in = ex * ex + ey * ey + ez * ez < hi2;
+          if constexpr (P::exact) {
+            if (in) {
+              const double dxd = V.A.x[j] - xi_d[0], dyd = V.A.y[j] - xi_d[1], dzd = V.A.z[j] - xi_d[2];
+              const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dxd, dxd), __dmul_rn(dyd, dyd)), __dmul_rn(dzd, dzd));
+              in = d2 < __dmul_rn(Rd, Rd);
+            }
+          }
+          if (in) { sumT += V.A.T[j]; ++cnt; }
+        }
+      }
+    }
+  }
+  const R *gv = V.gp + (size_t)key * GP_STRIDE;
+  const R eps = gv[GP_EPS], Tg = gv[GP_TG];
+  const R Tp = V.A.T[i];
+  // the parcel is in its own sphere, so cnt >= 1
+  const R Ts = eps * Tg + ((R)1 - eps) * (sumT / (R)max(cnt, 1));
+  const R Q = bp.rad_c * d * d * ((Ts - Tp) * (Ts + Tp) * (Ts * Ts + Tp * Tp));
+  V.qrad[i] = Q;
+  if (V.diag) V.diag[(size_t)DG_TSE * V.cap + i] = (double)Ts;
+}
+
+// ---------------------------------------------------------------------------------------
 // Per parcel (storage order): gas-particle terms, kinetics, second half kick, temperature
 // and mass update; writes the parcel's contributions to its cell sums.
 // ---------------------------------------------------------------------------------------
 // The FP32 forms are held to 64 registers (4 blocks of 256 threads per SM): a few spills
 // to L1 cost less than the latency the extra occupancy hides (ncu: 33 % -> 50 % warps).
-template <class P>
+// RAD: some bed has radiation (the variant that adds k_radiation's Q_rad to the heat balance).
+template <class P, bool RAD>
 __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView<P> V) {
   pdl_wait();
   using R = typename P::R;
@@ -962,7 +1048,10 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
   const R inv_mp = frcp<R>(mp);
 #pragma unroll
   for (int q = 0; q < 4; ++q) cpp += m[q] * inv_mp * cp_over_R<R>(3 + q, Tp) * t.RMz[q];
-  const R Tn = Tp + fdiv<R>(bp.dt * (Qconv + kn.Qr + kn.Qrm), mp * cpp);
+  R Qrad = 0;
+  if constexpr (RAD) Qrad = (fl & DEM_RADIATION) ? V.qrad[i] : (R)0;   // k_radiation, this step
+  const R Tn = RAD ? Tp + fdiv<R>(bp.dt * (Qconv + kn.Qr + kn.Qrm + Qrad), mp * cpp)
+                   : Tp + fdiv<R>(bp.dt * (Qconv + kn.Qr + kn.Qrm), mp * cpp);
   V.A.T[i] = Tn;
   if (cpl) {
 #pragma unroll
@@ -1007,6 +1096,8 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
     dg[DG_NU * cp + i] = (double)Nu;
     dg[DG_RE * cp + i] = (double)Re;
     dg[DG_CELL * cp + i] = (double)(c - V.beds[meta >> 8].cell_off);
+    dg[DG_QRAD * cp + i] = (double)Qrad;
+    if (!RAD || !(fl & DEM_RADIATION)) dg[DG_TSE * cp + i] = 0.0;
   }
 }
 

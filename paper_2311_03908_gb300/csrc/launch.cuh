@@ -81,6 +81,7 @@ StepView<P> make_view(dem_ctx *c, bool for_step) {
   V.work = c->work;
   V.nwork = c->nwork;
   V.wnear = c->wnear;
+  V.qrad = (R *)c->qrad;
   return V;
 }
 
@@ -162,8 +163,15 @@ int enqueue_steps(dem_ctx *c, int nsteps) {
     ps = prof_begin(c, "k_contact_forces");
     launch_k(pdl, k_contact_forces<P>, grid_wave(c, c->n, 128), 128, st, V);
     prof_end(c, ps);
+    if (c->any_rad) {   // particle radiation, from the temperatures before the update
+      ps = prof_begin(c, "k_radiation");
+      launch_k(pdl, k_radiation<P>, grid_for(c->n, 128), 128, st, V);
+      prof_end(c, ps);
+      ++c->launches;
+    }
     ps = prof_begin(c, "k_gas_particle");
-    launch_k(pdl, k_gas_particle<P>, grid_for(c->n, c->bs_gp), c->bs_gp, st, V);
+    if (c->any_rad) launch_k(pdl, k_gas_particle<P, true>, grid_for(c->n, c->bs_gp), c->bs_gp, st, V);
+    else launch_k(pdl, k_gas_particle<P, false>, grid_for(c->n, c->bs_gp), c->bs_gp, st, V);
     prof_end(c, ps);
     ps = prof_begin(c, "k_cells");
     launch_k(pdl, k_cells<P>, grid_for(c->ncells, c->bs_cells), c->bs_cells, st, V, 0);
@@ -243,7 +251,7 @@ int enqueue_gas_set(dem_ctx *c, const double *Y, const double *T) {
 template <class P>
 int kernel_limits(int *lim) {
   const void *fn[6] = {(const void *)k_key<P>, (const void *)k_restore_out<P>, (const void *)k_pair_search<P>,
-                       (const void *)k_contact_screen<P>, (const void *)k_gas_particle<P>, (const void *)k_cells<P>};
+                       (const void *)k_contact_screen<P>, (const void *)k_gas_particle<P, false>, (const void *)k_cells<P>};
   for (int k = 0; k < 6; ++k) {
     cudaFuncAttributes a;
     if (cudaFuncGetAttributes(&a, fn[k]) != cudaSuccess) return -1;
