@@ -82,6 +82,8 @@ struct dem_ctx {
   uint2 *work = nullptr;           // contact work list (parcel, list-hit mask)
   int *nwork = nullptr;            // its length
   char *qrad = nullptr;            // radiation heat of each parcel this step (form's type)
+  char *tsrt = nullptr;            // FP64 temperatures in sorted order for the radiation kernel
+  float4 *xr = nullptr;            // local coordinates and temperature in sorted order (radiation)
   bool any_rad = false;            // some bed has DEM_RADIATION: the radiation kernel runs
   std::map<std::tuple<int, int, int>, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;
   std::map<std::tuple<int, int, int>, long long> graph_launches;

@@ -361,6 +361,8 @@ void layout(dem_ctx *c, Bump &m) {
   c->work = m.take<uint2>(N);
   c->nwork = m.take<int>(1);
   c->qrad = m.take<char>(N, R);
+  c->tsrt = m.take<char>(N, R);
+  c->xr = m.take<float4>(N);
   c->corner = m.take<double>(c->hcorner.size());
   c->cornerp = m.take<float2>(c->hcornerp.size());
   for (int q = 0; q < 3; ++q) { c->F[q] = m.take<char>(N, R); c->Tq[q] = m.take<char>(N, R); }

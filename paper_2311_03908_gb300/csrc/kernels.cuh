@@ -78,6 +78,9 @@ template <class P> struct StepView {
   int *nwork;                   // ... and its length (reset by the step counter)
   const unsigned char *wnear;   // per cell: a wall may be within a parcel's reach
   R *qrad;                      // radiation heat of each parcel this step (radiating beds)
+  float4 *xr;                   // radiation: local coordinates in sorted order, w = T (FP32 forms)
+  R *tsrt;                      // radiation, FP64 form: temperatures in sorted order
+  int rad;                      // some bed radiates: k_ranges writes the sorted copies every step
 };
 
 // total layer mass of parcel i in the form's type (the same sum everywhere it is needed)
@@ -351,6 +354,12 @@ __global__ void k_ranges(StepView<P> V) {
     if (last) V.cend[k[u]] = (unsigned)(i + 1);
     V.inv[j[u]] = (unsigned)i;
     if (copy) V.xls[i] = V.xl[j[u]];
+    if (V.rad) {   // the radiation kernel's candidates: coordinates and temperature, sorted order
+      const float4 o = V.xl[j[u]];
+      const typename P::R t = V.A.T[j[u]];
+      V.xr[i] = make_float4(o.x, o.y, o.z, (float)t);
+      if constexpr (P::exact) V.tsrt[i] = t;
+    }
   }
 }
 
@@ -877,29 +886,39 @@ __global__ void k_contact_forces(StepView<P> V) {
 
 // ---------------------------------------------------------------------------------------
 // Particle radiation, eqs (3-16), (3-17), (3-51), in beds with DEM_RADIATION: one thread
-// per parcel (storage order). T_se averages the temperatures of the parcels whose centres
-// lie within R = 1.5 k d_p of the parcel's centre, the parcel itself included, weighted with
-// the gas cell's eps_g and T_g. No parcel is wider than a cell edge, so R < 2 edges and the
-// sphere lies in the 5 x 5 x 5 cells around the parcel's own; cells (and whole rows) farther
-// than R are skipped. The candidates are tested on the FP32 cell-local coordinates; the FP64
-// form re-tests every candidate within R plus a margin on the FP64 positions with the
-// oracle's expression, so its neighbourhoods are exact. Reads the temperatures before this
-// step's update (k_gas_particle runs after it); writes Q_rad and, with diagnostics, T_se.
-// T_se^4 - T_p^4 is evaluated as (T_se - T_p)(T_se + T_p)(T_se^2 + T_p^2), which keeps the
-// FP32 forms accurate when T_se is close to T_p.
+// per sorted position, so the threads of a warp work on a few neighbouring cells and read
+// the same candidates. T_se averages the temperatures of the parcels whose centres lie
+// within R = 1.5 k d_p of the parcel's centre, the parcel itself included, weighted with the
+// gas cell's eps_g and T_g. No parcel is wider than a cell edge, so R < 2 edges and the
+// sphere lies in the 5 x 5 x 5 cells around the parcel's own; only the cells within R are
+// visited. Candidates come in sorted order from the contiguous copy k_ranges writes (local
+// coordinates with the temperature as w, one 16-byte load; the FP64 form reads its FP64
+// temperatures from a second copy), with no indirection. They are tested on the FP32
+// cell-local coordinates;
+// the FP64 form re-tests every candidate within R plus a margin on the FP64 positions with
+// the oracle's expression, so its neighbourhoods are exact. The temperatures are the ones
+// before this step's update (k_gas_particle runs after this kernel). Writes Q_rad and, with
+// diagnostics, T_se, at the parcel's storage position. T_se^4 - T_p^4 is evaluated as
+// (T_se - T_p)(T_se + T_p)(T_se^2 + T_p^2), which keeps the FP32 forms accurate when T_se is
+// close to T_p.
 // ---------------------------------------------------------------------------------------
 template <class P>
-__global__ void __launch_bounds__(128) k_radiation(StepView<P> V) {
+__global__ void __launch_bounds__(128, 8) k_radiation(StepView<P> V) {
   pdl_wait();
   using R = typename P::R;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= V.n) return;
-  const int b = V.A.meta[i] >> 8;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;   // sorted position
+  if (s >= V.n) return;
+  const unsigned key = V.keys[s];
+  const int b = V.cell_bed[key];
   const BedP<R> &bp = V.bp[b];
   if (!(bp.flags & DEM_RADIATION)) return;
+  const bool restored = restore_now(V);   // storage order is sorted order after a re-store
+  const float4 *xs = V.xr;
+  const int i = restored ? s : (int)__ldg(V.vals + s);   // storage position
   const DevBed &B = V.beds[b];
-  const float4 me = V.xl[i];
-  const unsigned key = V.keyp[i];
+  const float4 me = xs[s];
+  R Tp;
+  if constexpr (P::exact) Tp = V.tsrt[s]; else Tp = me.w;
   const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
   const R d = V.A.d[i];
   double Rd = 0.0, xi_d[3] = {0.0, 0.0, 0.0};
@@ -915,48 +934,63 @@ __global__ void __launch_bounds__(128) k_radiation(StepView<P> V) {
   key_cell(B, key, X, Y, Z);
   R sumT = 0;
   int cnt = 0;
-  for (int dz = -2; dz <= 2; ++dz) {
-    if (Z + dz < 0 || Z + dz >= B.nz) continue;
+  float ox = 0.f, oy = 0.f, oz = 0.f;   // offset of the candidate's cell corner from the parcel
+  // one candidate at sorted position q
+  auto test = [&](const float4 &o, unsigned q) {
+    const float ex = o.x + ox, ey = o.y + oy, ez = o.z + oz;
+    bool in = ex * ex + ey * ey + ez * ez < hi2;
+    if constexpr (P::exact) {
+      if (in) {
+        const int j = restored ? (int)q : (int)__ldg(V.vals + q);
+        const double dxd = V.A.x[j] - xi_d[0], dyd = V.A.y[j] - xi_d[1], dzd = V.A.z[j] - xi_d[2];
+        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dxd, dxd), __dmul_rn(dyd, dyd)), __dmul_rn(dzd, dzd));
+        in = d2 < __dmul_rn(Rd, Rd);
+      }
+    }
+    if (in) {
+      if constexpr (P::exact) sumT += __ldg(V.tsrt + q); else sumT += o.w;
+      ++cnt;
+    }
+  };
+  // the cell offsets along one axis that the sphere can reach (within the grid)
+  auto lo_of = [reach](float m, float h, int c) {
+    return (c > 0 && m < reach) ? ((c > 1 && m + h < reach) ? -2 : -1) : 0;
+  };
+  auto hi_of = [reach](float m, float h, int c, int nc) {
+    return (c < nc - 1 && h - m < reach) ? ((c < nc - 2 && 2.f * h - m < reach) ? 2 : 1) : 0;
+  };
+  const int xlo = lo_of(me.x, hx, X), xhi = hi_of(me.x, hx, X, B.nx);
+  const int ylo = lo_of(me.y, hy, Y), yhi = hi_of(me.y, hy, Y, B.ny);
+  const int zlo = lo_of(me.z, hz, Z), zhi = hi_of(me.z, hz, Z, B.nz);
+  for (int dz = zlo; dz <= zhi; ++dz) {
     const float gz = fmaxf(0.f, dz < 0 ? me.z - (dz + 1) * hz : dz * hz - me.z);   // gap to the layer
-    if (gz >= reach) continue;
-    const float oz = dz * hz - me.z;
-    for (int dy = -2; dy <= 2; ++dy) {
-      if (Y + dy < 0 || Y + dy >= B.ny) continue;
+    oz = dz * hz - me.z;
+    for (int dy = ylo; dy <= yhi; ++dy) {
       const float gy = fmaxf(0.f, dy < 0 ? me.y - (dy + 1) * hy : dy * hy - me.y);
       if (gy * gy + gz * gz >= reach * reach) continue;
-      const float oy = dy * hy - me.y;
+      oy = dy * hy - me.y;
       const unsigned krow = key + (unsigned)(dy * B.nx) + (unsigned)(dz * B.nx * B.ny);
-      for (int dx = -2; dx <= 2; ++dx) {
-        if (X + dx < 0 || X + dx >= B.nx) continue;
+      for (int dx = xlo; dx <= xhi; ++dx) {
         const float gx = fmaxf(0.f, dx < 0 ? me.x - (dx + 1) * hx : dx * hx - me.x);
         if (gx * gx + gy * gy + gz * gz >= reach * reach) continue;
-        const float ox = dx * hx - me.x;
+        ox = dx * hx - me.x;
         const unsigned jb = __ldg(V.cstart + krow + dx), je = __ldg(V.cend + krow + dx);
-        for (unsigned s = jb; s < je; ++s) {
-          const int j = (int)__ldg(V.vals + s);
-          const float4 o = __ldg(V.xl + j);
-          const float ex = o.x + ox, ey = o.y + oy, ez = o.z + oz;
-          bool in = ex * ex + ey * ey + ez * ez < hi2;
-          if constexpr (P::exact) {
-            if (in) {
-              const double dxd = V.A.x[j] - xi_d[0], dyd = V.A.y[j] - xi_d[1], dzd = V.A.z[j] - xi_d[2];
-              const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dxd, dxd), __dmul_rn(dyd, dyd)), __dmul_rn(dzd, dzd));
-              in = d2 < __dmul_rn(Rd, Rd);
-            }
-          }
-          if (in) { sumT += V.A.T[j]; ++cnt; }
+        unsigned q = jb;
+        for (; q + 4 <= je; q += 4) {   // four candidates' loads in flight before their tests
+          const float4 o0 = __ldg(xs + q), o1 = __ldg(xs + q + 1), o2 = __ldg(xs + q + 2), o3 = __ldg(xs + q + 3);
+          test(o0, q); test(o1, q + 1); test(o2, q + 2); test(o3, q + 3);
         }
+        for (; q < je; ++q) test(__ldg(xs + q), q);
       }
     }
   }
   const R *gv = V.gp + (size_t)key * GP_STRIDE;
   const R eps = gv[GP_EPS], Tg = gv[GP_TG];
-  const R Tp = V.A.T[i];
   // the parcel is in its own sphere, so cnt >= 1
-  const R Ts = eps * Tg + ((R)1 - eps) * (sumT / (R)max(cnt, 1));
-  const R Q = bp.rad_c * d * d * ((Ts - Tp) * (Ts + Tp) * (Ts * Ts + Tp * Tp));
+  const R Tse = eps * Tg + ((R)1 - eps) * (sumT / (R)max(cnt, 1));
+  const R Q = bp.rad_c * d * d * ((Tse - Tp) * (Tse + Tp) * (Tse * Tse + Tp * Tp));
   V.qrad[i] = Q;
-  if (V.diag) V.diag[(size_t)DG_TSE * V.cap + i] = (double)Ts;
+  if (V.diag) V.diag[(size_t)DG_TSE * V.cap + i] = (double)Tse;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -972,7 +1006,17 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
   using R = typename P::R;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V.n) return;
+  // every load of the parcel's own record first, so that they are all in flight together
+  // (the compiler, held to 64 registers, would otherwise issue some only where they are used)
   const int meta = V.A.meta[i];
+  const unsigned c = V.keyp[i];
+  const R d = V.A.d[i];
+  const R vh[3] = {V.A.v[0][i], V.A.v[1][i], V.A.v[2][i]};
+  const R Tp = V.A.T[i];
+  R m[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) m[q] = mass_r<P>(V.A.m[q], i);
+  const R wv[3] = {V.A.w[0][i], V.A.w[1][i], V.A.w[2][i]};
   R F[3] = {0, 0, 0}, Tq[3] = {0, 0, 0};
   if (V.Hn.cnt[i] != 0) {   // the contact kernel wrote them only for parcels in contact
 #pragma unroll
@@ -981,7 +1025,6 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
   const int ore = meta & 255;
   const BedP<R> &bp = V.bp[meta >> 8];
   const unsigned fl = bp.flags;
-  const unsigned c = V.keyp[i];
   const size_t nc = (size_t)V.ncells;
   Gas<R> g;
   R gv[GP_STRIDE];   // the cell's property record, in vector loads
@@ -1003,11 +1046,9 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
   g.rho = gv[GP_RHO]; g.mu = gv[GP_MU]; g.lam = gv[GP_LAM]; g.cp = gv[GP_CP]; g.x = gv[GP_X];
   g.Dm = gv[GP_DM]; g.sc13 = gv[GP_SC13]; g.pr13 = gv[GP_PR13]; g.epow = gv[GP_EPOW];
   g.D = ore ? gv[GP_D1] : gv[GP_D0]; g.uz = gv[GP_UZ]; g.eps = gv[GP_EPS]; g.T = gv[GP_TG];
-  const R d = V.A.d[i];
   const R dc = bp.k * d;
   const R Vp = (R)(kPI / 6.0) * dc * dc * dc;
   const R r = (R)0.5 * dc;
-  const R vh[3] = {V.A.v[0][i], V.A.v[1][i], V.A.v[2][i]};
   const R sv[3] = {-vh[0], -vh[1], g.uz - vh[2]};
   const R slip = sqrt(sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]);
   const R Re = fdiv<R>(g.rho * g.eps * d * slip, g.mu);
@@ -1018,11 +1059,7 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
   const R Fd[3] = {Kp * sv[0], Kp * sv[1], Kp * sv[2]};
   const R Nu = gunn(g.eps, re02, re07, g.pr13);
   const R hA = (fl & DEM_NO_HEAT) ? (R)0 : fdiv<R>(bp.k3 * Nu * g.lam, d) * ((R)kPI * d * d);
-  const R Tp = V.A.T[i];
   const R Qconv = hA * (g.T - Tp);
-  R m[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) m[q] = mass_r<P>(V.A.m[q], i);
   const bool cpl = coupled_step(bp.ncouple, V.step_ctr);
   const R dtm = bp.dtg;
   KinOut<R> kn;
@@ -1039,7 +1076,7 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
   for (int q = 0; q < 3; ++q) {
     const R al = fdiv<R>(Tq[q], I);
     V.A.v[q][i] = vh[q] + a[q] * bp.half_dt;
-    V.A.w[q][i] = V.A.w[q][i] + al * bp.half_dt;
+    V.A.w[q][i] = wv[q] + al * bp.half_dt;
     V.A.a[q][i] = a[q];
     V.A.al[q][i] = al;
   }

@@ -82,6 +82,9 @@ StepView<P> make_view(dem_ctx *c, bool for_step) {
   V.nwork = c->nwork;
   V.wnear = c->wnear;
   V.qrad = (R *)c->qrad;
+  V.tsrt = (R *)c->tsrt;
+  V.xr = c->xr;
+  V.rad = c->any_rad ? 1 : 0;
   return V;
 }
 
