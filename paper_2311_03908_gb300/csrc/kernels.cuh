@@ -732,15 +732,17 @@ __device__ __forceinline__ bool wall_near(const StepView<P> &V, const DevBed &B,
 
 template <class P>
 __device__ __forceinline__ bool contact_screen(const StepView<P> &V, int i, unsigned &hits) {
+  // the parcel's own loads first, all in flight together (3 % faster than issuing them after
+  // the bed's switches are read)
   const int meta = V.A.meta[i];
+  const float4 me = V.xl[i];
+  const unsigned key = V.keyp[i];
+  const int listed = V.nlc[i];
   const DevBed &B = V.beds[meta >> 8];
   const BedP<typename P::R> &bp = V.bp[meta >> 8];
   hits = 0u;
   if (bp.flags & DEM_NO_CONTACTS) return false;
-  const float4 me = V.xl[i];
-  const unsigned key = V.keyp[i];
   const bool near = wall_near<P>(V, B, bp, key, me);
-  const int listed = V.nlc[i];
   const bool searched = *V.rebuild || V.nolists || listed == NL_OVERFLOW;
   if (searched) return near || V.pcnt[i] != 0;
   const float hx = (float)bp.dx, hy = (float)bp.dy, hz = (float)bp.dz;
