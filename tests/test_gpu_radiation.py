@@ -122,3 +122,26 @@ def test_adjoint_and_bad_emissivity_are_refused():
     with pytest.raises(binding.DemError) as e:
         binding.Context(bad, precision="fp64", stream=torch.cuda.current_stream().cuda_stream)
     assert e.value.status == binding.DEM_EINVAL
+
+
+@pytest.mark.parametrize("tuning", [dict(neighbour_lists=1, skin_permille=5, restore_every=1),
+                                    dict(neighbour_lists=1, skin_permille=5, restore_every=64),
+                                    dict(neighbour_lists=0)])
+def test_radiation_with_restores_graphs_and_search_modes(tuning):
+    # frequent list builds re-storing the state at every build (the kernel's sorted-order
+    # path right after a re-store) or almost never, and the cell search without lists;
+    # stepped through a captured CUDA graph
+    bed = _bed(47, n=1200, cg=6.0)
+    ctx, ref = _ctx(bed), oracle.Oracle(bed)
+    ctx.dem_set_tuning(**tuning)
+    ctx.dem_step_graph(4)
+    ctx.dem_step_graph(4)
+    ref.step(8)
+    steps, builds, _ = ctx.dem_get_counters()
+    assert steps == 8 and (builds >= 2 or tuning["neighbour_lists"] == 0)
+    sg, so = ctx.dem_get_state(), ref.state()
+    for row in range(binding.DEM_NSTATE):
+        assert _rel(sg[row], so[row]) < 1e-9, binding.STATE_ROWS[row]
+    dg, do = ctx.dem_get_diag(), ref.diag()
+    assert _rel(dg[TSE], do[oracle.D_TSE]) < 1e-9 and _rel(dg[QRAD], do[oracle.D_QRAD]) < 1e-9
+    ctx.close()
