@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--settle", type=int, default=300, help="untimed steps before the autotuner and the warm-up, so that the timed steps see the fluidised bed (contacts, list builds) rather than the packing at rest")
     ap.add_argument("--autotune", type=int, default=30, help="steps per autotuner candidate before the "
                     "warm-up (0: keep the default launch configuration)")
+    ap.add_argument("--no-radiation-leg", action="store_true", help="skip the extra measurement of the "
+                    "step with radiation switched on")
     ap.add_argument("--radiation", action="store_true", help="switch on the particle radiation of "
                     "eqs (3-16), (3-17), (3-51) in every bed (a widening of the step; off by default)")
     ap.add_argument("--tuning", default="", help="fixed launch configuration instead of the autotuner, "
@@ -228,6 +230,43 @@ def cpu_baseline(bed, steps: int, sample: int):
     dt = time.perf_counter() - t0
     return {"value": n * steps / dt, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
             "sample": f"{n} of {bed.n} parcels of the same bed (random subset), {steps} step(s), FP64"}
+
+
+def radiation_leg(binding, stream, bed, tuning, settle, steps, precision):
+    """The step with the particle radiation of eqs (3-16), (3-17), (3-51) switched on in every
+    bed (off in the headline step): a fresh context of the same workload, settled like the
+    main one, 10-step graphs timed with CUDA events, and the radiation kernel's own time
+    from an eager pass."""
+    import dataclasses
+    import torch
+    from paper_2311_03908_gb300 import synth
+    rb = dataclasses.replace(bed, beds=[dataclasses.replace(c, flags=c.flags | synth.RADIATION) for c in bed.beds])
+    cx = binding.Context(rb, precision=precision, stream=stream.cuda_stream)
+    if settle > 0:
+        cx.dem_step(settle)
+    cx.dem_set_tuning(**tuning)
+    G = 10
+    steps = max(G, steps // G * G)
+    cx.dem_step_graph(G)
+    cx.dem_step_graph(G)
+    cx.dem_sync()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(steps // G):
+        cx.dem_step_graph(G)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms = a0.elapsed_time(a1)
+    cx.dem_profile(True)
+    cx.dem_step(20)
+    t = cx.dem_kernel_times()
+    cx.dem_profile(False)
+    cx.close()
+    nl, tot = t.get("k_radiation", (1, 0.0))
+    return {"ms_per_step": ms / steps, "value": bed.n * steps / (ms * 1e-3), "unit": UNIT, "steps": steps,
+            "settle_steps": settle, "k_radiation_ms": tot / max(nl, 1),
+            "what": "eqs (3-16), (3-17), (3-51) on, same workload, tuning and stepping"}
 
 
 def adjoint_cost(binding, stream):
@@ -444,6 +483,9 @@ def main():
 
     # cost of the adjoint (drag-heat-reaction sub-step, checkpoints + recomputation + reverse
     # sweep) against its forward sweep, on the 64,000-parcel adjoint workload
+    if not args.no_radiation_leg and not args.radiation:
+        line["radiation"] = radiation_leg(binding, stream, bed, tuning, args.settle, min(args.steps, 200),
+                                          args.precision)
     if rank == 0 and not args.no_adjoint:
         line["adjoint"] = adjoint_cost(binding, stream)
 
