@@ -128,9 +128,9 @@ def algorithmic_bytes(kernel: str, n: int, ncells: int, zbar: float, L: float, r
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one full-size ncu
 # capture of the 2M-parcel split-precision bed between list builds, after the 300-step
 # settle; per parcel), valid only for the CUDA sources it was taken on.
-TRAFFIC_SOURCE_SHA256 = "bfbe21b14e56cb42fb28beeaccf3d7b5b458ba5641fa46e22d8bb38832a33e8b"
+TRAFFIC_SOURCE_SHA256 = "8d6de96c4c898e16c19eb7f1288b540aa559e528b588115804f867fccba45fe2"
 TRAFFIC_WORKLOAD = ("ibm_2m", "split", 2_000_000)
-TRAFFIC_BYTES_PER_PARCEL = {"k_gas_particle": 205.0, "k_key": 177.8, "k_cells": 146.5, "k_contact_screen": 58.4,
+TRAFFIC_BYTES_PER_PARCEL = {"k_gas_particle": 205.5, "k_key": 177.8, "k_cells": 146.4, "k_contact_screen": 58.4,
                             "k_contact_forces": 17.1, "k_ranges": 8.1}
 
 

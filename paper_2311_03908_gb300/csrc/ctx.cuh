@@ -30,13 +30,13 @@ struct dem_ctx {
   double *pm[2][4] = {};
   int *pmeta[2] = {}, *porig[2] = {};
   float *pdsp[2][3] = {};
-  // contact history: [0] current, [1] gather target
+  // contact history, double-buffered by step parity: before the step and after it (the
+  // latter is also the re-store's scratch)
   unsigned char *hcnt[2] = {};
   int *hid[2] = {};
   void *hxi[2] = {};
   // binning
   unsigned *keys = nullptr, *vals = nullptr, *keys2 = nullptr, *vals2 = nullptr, *rhist = nullptr;
-  unsigned *kres = nullptr, *vres = nullptr;   // where the last radix sort left its result
   unsigned *skey[2] = {}, *sval[2] = {};       // sorted keys / permutation, by step parity
   unsigned *inv = nullptr;                     // sorted position of each storage position
   unsigned *rsw = nullptr;                     // scratch of the incremental re-sort
@@ -73,7 +73,7 @@ struct dem_ctx {
   bool pending = false;
   int sticky = DEM_OK;
   long long launches = 0;
-  int bs_contacts = 128, bs_gp = 128, bs_gather = 256, bs_cells = 256, bs_key = 256;
+  int bs_contacts = 128, bs_gp = 128, bs_restore = 256, bs_cells = 256, bs_key = 256;
   int use_lists = 1;               // 1: Verlet neighbour lists, 0: cell-list search every step
   int bs_search = 256;
   int nsm = 152;                   // SMs of the device (one wave of a grid-stride launch)

@@ -360,9 +360,10 @@ void layout(dem_ctx *c, Bump &m) {
   c->novf = m.take<int>(1);
   c->work = m.take<uint2>(N);
   c->nwork = m.take<int>(1);
-  c->qrad = m.take<char>(N, R);
-  c->tsrt = m.take<char>(N, R);
-  c->xr = m.take<float4>(N);
+  const size_t Nr = c->any_rad ? N : 0;   // the radiation buffers exist only where a bed radiates
+  c->qrad = m.take<char>(Nr, R);
+  c->tsrt = m.take<char>(c->rsize == sizeof(double) ? Nr : 0, R);   // FP64 form only
+  c->xr = m.take<float4>(Nr);
   c->corner = m.take<double>(c->hcorner.size());
   c->cornerp = m.take<float2>(c->hcornerp.size());
   for (int q = 0; q < 3; ++q) { c->F[q] = m.take<char>(N, R); c->Tq[q] = m.take<char>(N, R); }
@@ -396,7 +397,7 @@ void drop_graphs(dem_ctx *c) {
 
 void get_tuning(const dem_ctx *c, int32_t *t) {
   t[0] = c->use_lists;
-  t[1] = c->bs_key; t[2] = c->bs_gather; t[3] = c->bs_search; t[4] = c->bs_contacts;
+  t[1] = c->bs_key; t[2] = c->bs_restore; t[3] = c->bs_search; t[4] = c->bs_contacts;
   t[5] = c->bs_gp; t[6] = c->bs_cells;
   t[7] = (int32_t)std::lround(c->skin_frac * 1000.0);
   t[8] = c->restore_every;
@@ -411,7 +412,7 @@ int apply_tuning(dem_ctx *c, const int32_t *t) {
   if (t[7] < 1 || t[7] > 1000) return DEM_EINVAL;
   if (t[8] < 1 || t[8] > 64) return DEM_EINVAL;
   c->use_lists = t[0];
-  c->bs_key = t[1]; c->bs_gather = t[2]; c->bs_search = t[3]; c->bs_contacts = t[4];
+  c->bs_key = t[1]; c->bs_restore = t[2]; c->bs_search = t[3]; c->bs_contacts = t[4];
   c->bs_gp = t[5]; c->bs_cells = t[6];
   c->skin_frac = t[7] / 1000.0;
   c->restore_every = t[8];

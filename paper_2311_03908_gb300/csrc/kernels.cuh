@@ -102,9 +102,9 @@ __device__ __forceinline__ bool coupled_step(int ncouple, const long long *ctr) 
 }
 
 // ---------------------------------------------------------------------------------------
-// Velocity Verlet (kick-drift-kick). The first half kick is evaluated by the key kernel
-// (for the drift) and again by the gather kernel with the same expression, so both see the
-// same bits; the drift is applied once, by the key kernel, to the FP64 positions.
+// Velocity Verlet (kick-drift-kick). The key kernel applies the first half kick, writes the
+// half-step velocity back (the contact and gas-particle kernels read it) and drifts the FP64
+// positions with it; the gas-particle kernel applies the second half kick.
 // ---------------------------------------------------------------------------------------
 template <class R>
 __device__ __forceinline__ R half_kick(R half_dt, double dt_d, R v, R a) {

@@ -116,7 +116,7 @@ int enqueue_binning(dem_ctx *c, int drift) {
     if (e) return e;
     prof_end(c, ps);
     ps = prof_begin(c, "k_ranges");   // the key kernel emptied the previous step's ranges
-    launch_k(pdl, k_ranges<P>, grid_for((c->n + 3) / 4, c->bs_gather), c->bs_gather, st, V);
+    launch_k(pdl, k_ranges<P>, grid_for((c->n + 3) / 4, c->bs_restore), c->bs_restore, st, V);
     prof_end(c, ps);
     ++c->launches;
   } else {
@@ -139,8 +139,8 @@ int enqueue_binning(dem_ctx *c, int drift) {
     c->launches += 2;
   }
   ps = prof_begin(c, "k_restore");
-  launch_k(pdl, k_restore_out<P>, grid_wave(c, c->n, c->bs_gather), c->bs_gather, st, V, drift ? 0 : 1);
-  launch_k(pdl, k_restore_in<P>, grid_wave(c, c->n, c->bs_gather), c->bs_gather, st, V, drift ? 0 : 1);
+  launch_k(pdl, k_restore_out<P>, grid_wave(c, c->n, c->bs_restore), c->bs_restore, st, V, drift ? 0 : 1);
+  launch_k(pdl, k_restore_in<P>, grid_wave(c, c->n, c->bs_restore), c->bs_restore, st, V, drift ? 0 : 1);
   prof_end(c, ps);
   c->launches += 2;
   return (int)cudaPeekAtLastError();
