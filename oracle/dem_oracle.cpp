@@ -397,7 +397,10 @@ void kinetics(const double *bed, const S m[4], const S &Tp, double dreal, int or
 // Gidaspow-Ganser drag, eqs (3-5), (3-5-2)..(3-5-5). Returns beta/eps_p, so that the
 // force beta V/(1-eps_g) (u-v) of eq (3-5) is (beta/eps_p) V (u-v); eps_p cancels exactly,
 // which keeps a parcel that entered an empty cell (eps_g = 1, lagged) finite.
-// Reading: the inertial Ergun term is taken as printed (eps_g, not eps_p).
+// Reading: the inertial Ergun term takes eps_p, as in the Gidaspow correlation that eq (3-5-1)
+// cites and as Ergun's fixed-bed pressure drop requires (beta (u-v) = eps_g dp/dL); the printed
+// eps_g there is read as a misprint. Then beta/eps_p = 150 eps_p mu/(eps_g d^2 psi^2)
+// + 1.75 rho |u-v| / (d psi).
 template <class S>
 S drag_beta_over_epsp(const double *bed, double dreal, int ore, double eps, const S &slip,
                       const GasProps &g, S *Re_out) {
@@ -407,7 +410,7 @@ S drag_beta_over_epsp(const double *bed, double dreal, int ore, double eps, cons
   if (Re_out) *Re_out = Re;
   if (eps < 0.8) {
     return 150.0 * ep * g.mu / (eps * dreal * dreal * psi * psi) +
-           1.75 * eps * g.rho * slip / (dreal * psi * ep);
+           1.75 * g.rho * slip / (dreal * psi);
   }
   const double K1 = 1.0 / (1.0 / 3.0 + (2.0 / 3.0) / std::sqrt(psi)) - 2.25 * dreal / bed[ORC_B_D];  // (3-5-4)
   const double K2 = std::pow(10.0, 1.8148 * std::pow(-std::log10(psi), 0.5743));                  // (3-5-5)

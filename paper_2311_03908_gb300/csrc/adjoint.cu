@@ -350,7 +350,7 @@ __device__ void load_par(const StepView<Pp> &V, const BedP<double> *bpd, int i, 
   const double ep = 1.0 - P.eps, psi = B.psi[P.ore];
   P.ergun = P.eps < 0.8;
   P.aE = 150.0 * ep * P.mu / (P.eps * P.d * P.d * psi * psi);
-  P.bE = 1.75 * P.eps * P.rho / (P.d * psi * ep);
+  P.bE = 1.75 * P.rho / (P.d * psi);
   P.K1 = B.K1b[P.ore] - B.wall_K1 * P.d;
   P.K2 = B.K2[P.ore];
   P.cW = 0.75 * P.eps * P.rho / P.d * P.epow;

@@ -270,13 +270,15 @@ template <class R> __device__ __forceinline__ R gunn(R eps, R re02, R re07, R c1
 }
 
 // Gidaspow-Ganser drag coefficient divided by the solid fraction (eqs (3-5-2)..(3-5-5)):
-// F_d = (beta / eps_p) V_p (u_g - v_p), the form of eq (3-5) with eps_p cancelled.
+// F_d = (beta / eps_p) V_p (u_g - v_p), the form of eq (3-5) with eps_p cancelled. The
+// inertial Ergun term carries eps_p (Gidaspow's correlation, which eq (3-5-1) cites, and
+// Ergun's fixed-bed pressure drop), so it is 1.75 rho |u - v| / (d psi) after the division.
 template <class R>
 __device__ __forceinline__ R beta_over_epsp(const BedP<R> &B, int ore, R d, const Gas<R> &g, R slip, R Re) {
   const R eps = g.eps, ep = (R)1 - eps;
   const R psi = B.psi[ore];
   if (eps < (R)0.8)
-    return fdiv<R>((R)150 * ep * g.mu, eps * d * d * psi * psi) + fdiv<R>((R)1.75 * eps * g.rho * slip, d * psi * ep);
+    return fdiv<R>((R)150 * ep * g.mu, eps * d * d * psi * psi) + fdiv<R>((R)1.75 * g.rho * slip, d * psi);
   const R K1 = B.K1b[ore] - B.wall_K1 * d;
   const R K2 = B.K2[ore];
   if (Re > (R)0) {

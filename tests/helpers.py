@@ -32,9 +32,18 @@ ISOLATED = (synth.NO_GRAVITY | synth.NO_DRAG | synth.NO_HEAT | synth.NO_KINETICS
 
 def paper_values():
     """Numbers printed in the paper (tests/golden/paper_printed_values.txt), by name."""
+    return golden_values("paper_printed_values.txt")
+
+
+def handbook_values():
+    """Tabulated reference values independent of the paper (tests/golden/handbook_values.txt)."""
+    return golden_values("handbook_values.txt")
+
+
+def golden_values(fname):
     import os
     out = {}
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_printed_values.txt")
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", fname)
     with open(path) as f:
         for line in f:
             line = line.split("#", 1)[0].strip()
