@@ -137,7 +137,13 @@ typedef struct {
 typedef struct dem_ctx dem_ctx;
 
 /* Create a context: validates the inputs, allocates one device arena, copies the parcels
- * and bins them once. cuda_stream is a cudaStream_t (NULL = legacy default stream).
+ * and bins them once. The validation follows the paper's statement of the problem: a
+ * coarse-grained parcel of diameter k d_p (Sec. 3.3, eq (3-41)) must fit inside one gas
+ * cell, since the particle-to-gas coupling of Sec. 3.2 (eqs (3-24), (3-25)) assigns each
+ * parcel to the single cell that holds its centre; the soft-sphere contact of eq (3-3) is
+ * integrated explicitly, so the DEM step must resolve the stiffest contact (omega_0 dt < 2
+ * with omega_0 = sqrt(k_n / m*)); and masses are updated every n = dt_CFD / dt_DEM steps
+ * (Sec. 4), so n >= 1. cuda_stream is a cudaStream_t (NULL = legacy default stream).
  * precision: DEM_PREC_FP64 (everything FP64), DEM_PREC_SPLIT (FP32 contact geometry,
  * forces, drag, heat, kinetics and velocities; FP64 positions and layer masses; cell-source
  * sums and the gas state in Kahan-compensated FP32) or DEM_PREC_SPLIT_KAHAN (as SPLIT but
@@ -180,11 +186,20 @@ int dem_reduction_degree(dem_ctx *c, double *mean_per_bed, double *oxygen_per_be
  * parcel per checkpoint and per sub-step of a segment) cannot be allocated. */
 int dem_adjoint(dem_ctx *c, int32_t n_steps, int32_t ckpt_every, double *J, double *grad);
 
-/* Replace the kinetic parameters of every bed (R1..R3). */
+/* Replace the kinetic parameters of every bed: the pre-exponential factors k0 (m/s) and
+ * activation energies Ea (J/mol) of the interface rate constants k_r = k0 exp(-Ea / (R T_p))
+ * of eq (2-13) for R1 (Fe2O3 -> Fe3O4), R2 (Fe3O4 -> FeO), R3 (FeO -> Fe) (Table 2 lists
+ * one set; Sec. 5.1.1 and Sec. 5.2.1 fit others). Host arrays of 3 doubles, k0 >= 0 and
+ * Ea >= 0 (DEM_EINVAL otherwise, NaN included). Waits for the context stream, then takes
+ * effect from the next step (captured step graphs read the parameters from device memory). */
 int dem_set_kinetics(dem_ctx *c, const double k0[3], const double Ea[3]);
 
-/* Per-parcel state in parcel-index order, DEM_NSTATE rows of n doubles (host):
- * x y z vx vy vz wx wy wz T m_Fe2O3 m_Fe3O4 m_FeO m_Fe ax ay az alx aly alz. Synchronous. */
+/* Per-parcel state in parcel-index order, DEM_NSTATE rows of n doubles (host): the
+ * position and velocity of the translational equation (3-3), the angular velocity of the
+ * rotational equation (3-6), the temperature of the energy equation (3-8), the layer masses
+ * m_z of eqs (3-1), (3-2), (3-4), and the accelerations of eqs (3-3) and (3-6) at the end of
+ * the last step: x y z vx vy vz wx wy wz T m_Fe2O3 m_Fe3O4 m_FeO m_Fe ax ay az alx aly alz.
+ * Synchronous. */
 enum { DEM_NSTATE = 20 };
 int dem_get_state(dem_ctx *c, double *out_host);
 
@@ -274,11 +289,16 @@ int dem_kernel_times(dem_ctx *c, int32_t max_kernels, char *names, int64_t *laun
  * Scratch: a file-scope __device__ array of 4096 x 3 doubles (96 KiB) that every GPU loading
  * the library holds until the process exits; n is limited to DEM_NOALLOC_MAX_PARCELS and a
  * larger n returns DEM_EINVAL before any work is enqueued. No cudaMalloc, cudaFree or
- * allocating library routine is called. The first call on a device (with that device
- * current) looks up the array's device address with cudaGetSymbolAddress; make that first
- * call before any stream capture. Every call shares the array and overwrites the rows it
- * reads, so the array keeps the last call's partial sums; calls that overlap on the GPU
- * (other streams, other threads) race on it and must be ordered by the caller. */
+ * allocating library routine is called. Every call made outside a stream capture (with its
+ * device current) looks up the array's device address with cudaGetSymbolAddress; a call
+ * made while cuda_stream is capturing uses the address found by the last uncaptured call on
+ * that device, and returns DEM_ESTATE if there was none. So make one uncaptured call on a
+ * device before capturing a call, and again after anything that tears the device's context
+ * down and creates it anew (cudaDeviceReset). Every call shares the array and overwrites
+ * the rows it reads, so the array keeps the last call's partial sums; calls that overlap on
+ * the GPU (other streams, other threads) race on it and must be ordered by the caller.
+ * DEM_ECUDA reports a failure of this call's own lookups or launches only, not an error
+ * that other code left pending. */
 #define DEM_NOALLOC_MAX_PARCELS 8388608
 int dem_reduction_degree_noalloc(const double *m_fe2o3, const double *m_fe3o4, const double *m_feo,
                                  const double *m_fe, const int32_t *ore_type, int32_t n,

@@ -759,11 +759,12 @@ int dem_sync(dem_ctx *c) {
 
 int dem_set_kinetics(dem_ctx *c, const double k0[3], const double Ea[3]) {
   if (!c || !k0 || !Ea) return DEM_EINVAL;
+  for (int r = 0; r < 3; ++r)
+    if (!(k0[r] >= 0 && Ea[r] >= 0)) return DEM_EINVAL;   // nothing changed
   int s = sync_all(c);
   if (s != DEM_OK) return s;
   for (int b = 0; b < c->nbeds; ++b)
     for (int r = 0; r < 3; ++r) {
-      if (!(k0[r] >= 0 && Ea[r] >= 0)) return DEM_EINVAL;
       c->hbp_d[b].k0[r] = k0[r];
       c->hbp_d[b].Ea_R[r] = Ea[r] / kRgas;
       c->hbp_f[b].k0[r] = (float)k0[r];
