@@ -9,6 +9,8 @@
 // the bed's reduction degree. The paper has no counterpart of this entry point.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "../../include/dem.h"
 
 namespace {
@@ -85,10 +87,14 @@ __global__ void __launch_bounds__(kThreads) k_fov_final(const double *partials, 
   }
 }
 
-// Device address of g_partials, looked up once per device. In host code the name
-// g_partials is only a host-side stand-in, so kernels must be given this address.
+// Device address of g_partials per device. In host code the name g_partials is only a
+// host-side stand-in, so kernels must be given this address. It is looked up again on every
+// call made outside a stream capture (the lookup is cheap, and a context that was torn down
+// and created again may have loaded the module at another address); a call made inside a
+// capture uses the address of the last uncaptured call on that device. Atomic, because host
+// threads may make their first calls on one device at the same time.
 constexpr int kMaxDevices = 64;
-double *s_scratch[kMaxDevices] = {};
+std::atomic<double *> s_scratch[kMaxDevices];
 
 }  // namespace
 
@@ -101,16 +107,32 @@ extern "C" int dem_reduction_degree_noalloc(const double *m_fe2o3, const double 
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return DEM_ECUDA;
   if (dev < 0 || dev >= kMaxDevices) return DEM_EINVAL;
-  if (!s_scratch[dev]) {
-    // first call on this device (it must be current): resolve the array's device address
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return DEM_ECUDA;
+  double *scratch = nullptr;
+  if (cap == cudaStreamCaptureStatusNone) {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_partials) != cudaSuccess || !p) return DEM_ECUDA;
-    s_scratch[dev] = (double *)p;
+    scratch = (double *)p;
+    s_scratch[dev].store(scratch, std::memory_order_release);
+  } else {
+    // inside a capture no lookup is made: an uncaptured call on this device must come first
+    scratch = s_scratch[dev].load(std::memory_order_acquire);
+    if (!scratch) return DEM_ESTATE;
   }
-  cudaStream_t st = (cudaStream_t)cuda_stream;
   const int nblocks = (n + kPerBlock - 1) / kPerBlock;
-  // pass 1 writes every row that pass 2 reads, so nothing has to be cleared first
-  k_fov_partials<<<nblocks, kThreads, 0, st>>>(m_fe2o3, m_fe3o4, m_feo, m_fe, ore_type, n, s_scratch[dev]);
-  k_fov_final<<<1, kThreads, 0, st>>>(s_scratch[dev], nblocks, n, out);
-  return cudaPeekAtLastError() == cudaSuccess ? DEM_OK : DEM_ECUDA;
+  // pass 1 writes every row that pass 2 reads, so nothing has to be cleared first. Each
+  // launch's own status is checked (an error left pending by other code is not reported).
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(kThreads);
+  cfg.stream = st;
+  cfg.gridDim = dim3(nblocks);
+  if (cudaLaunchKernelEx(&cfg, k_fov_partials, m_fe2o3, m_fe3o4, m_feo, m_fe, ore_type, n, scratch) !=
+      cudaSuccess)
+    return DEM_ECUDA;
+  cfg.gridDim = dim3(1);
+  if (cudaLaunchKernelEx(&cfg, k_fov_final, (const double *)scratch, nblocks, n, out) != cudaSuccess)
+    return DEM_ECUDA;
+  return DEM_OK;
 }
