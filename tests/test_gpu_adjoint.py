@@ -67,3 +67,20 @@ def test_autograd_function_returns_the_adjoint_gradient():
     assert float(J.detach()) == Jr
     assert np.allclose(params.grad.numpy(), gr, rtol=1e-13, atol=0)
     ctx.close()
+
+
+def test_adjoint_at_the_benchmarked_size():
+    # the adjoint workload as the bench times it: 64,000 parcels, 2,000 sub-steps, a
+    # checkpoint every 100; the gradient against the oracle's FP64 dual numbers and central
+    # differences (relative step 1e-6) of the same map, per component to 1e-4
+    bed = synth.config_adjoint_64k()
+    steps, ck = int(bed.meta["steps"]), int(bed.meta["ckpt"])
+    ctx = _ctx(bed)
+    J, g = ctx.dem_adjoint(steps, ck)
+    ctx.close()
+    ref = oracle.Oracle(bed)
+    Jd, gd = ref.adjoint(steps, mode=2)
+    assert abs(J - Jd) < 1e-9 * abs(Jd)
+    assert np.all(np.abs(g - gd) <= 1e-4 * np.abs(gd)), (g, gd)
+    Jf, gf = ref.adjoint(steps, mode=1, rel=1e-6)
+    assert np.all(np.abs(g - gf) <= 1e-4 * np.abs(gf)), (g, gf)

@@ -291,3 +291,62 @@ def test_set_gas_input_paths_agree(prec):
     assert not np.array_equal(s[1], s[0])
     for c in ctxs:
         c.close()
+
+
+def test_batched_32_beds_of_uneven_size():
+    # the batched workload's shape scaled down: 32 beds of 500..5,000 parcels, 773..1073 K,
+    # inlet velocities 0.2..0.5 m/s, 20 x 20 x 120 cells each, stepped as replayed graphs
+    bed = synth.config_batched_32(n_min=500, n_max=5000, v_scale=0.2)
+    counts = np.bincount(bed.bed, minlength=32)
+    assert counts.min() >= 500 and counts.max() <= 5000 and counts.max() > 3 * counts.min()
+    ref = oracle.Oracle(bed)
+    ref.step(10)
+    so = ref.state()
+    mo, oo, _ = ref.reduction_degree()
+    co, po, _ = ref.contacts()
+    ctx = _ctx(bed)
+    ctx.dem_step_graph(10)
+    sg = ctx.dem_get_state()
+    for row in range(binding.DEM_NSTATE):
+        assert _rel(sg[row], so[row]) < 1e-7, binding.STATE_ROWS[row]
+    cg, pg, _ = ctx.dem_get_contacts()
+    assert _pairs(cg, pg) == _pairs(co, po)
+    assert sum(co) > 1000
+    mg, og = ctx.dem_reduction_degree()
+    assert np.allclose(mg, mo, rtol=0, atol=1e-12) and np.allclose(og, oo, rtol=0, atol=1e-12)
+    ctx.close()
+    ctx = _ctx(bed, "split")
+    ctx.dem_step_graph(10)
+    mg, _ = ctx.dem_reduction_degree()
+    assert np.all(np.abs(mg - mo) < 1e-6)      # every bed's reduction degree (target 1e-3)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "split", "split_kahan"])
+def test_kinetics_at_a_chemistry_time_step(prec):
+    # the reduction-degree curve where it moves: the bed's chemistry stepped at dt = 1e-3 s
+    # for 3,000 steps (3 s of reduction at 1073 K), contacts, drag and gravity off so the
+    # parcels stay in their cells; heat, kinetics and the gas update on. The FP32 forms'
+    # bed-mean f_ov against the FP64 oracle to 1e-3 absolute (the target) -- in practice
+    # much closer -- and the FP64 form to 1e-9.
+    bed = synth.small_packed(seed=14, n=1500, T0=1073.0, v_scale=0.0)
+    c = bed.beds[0]
+    c.dt = 1e-3
+    c.kn = 0.1                          # no contact is evaluated; keeps the stability check
+    c.flags = synth.NO_CONTACTS | synth.NO_GRAVITY | synth.NO_DRAG
+    ref = oracle.Oracle(bed)
+    ctx = _ctx(bed, prec)
+    worst = 0.0
+    f_first = None
+    for k in range(6):
+        ctx.dem_step(500)
+        ref.step(500)
+        mg, _ = ctx.dem_reduction_degree()
+        mo, _, _ = ref.reduction_degree()
+        f_first = f_first if f_first is not None else mo[0]
+        worst = max(worst, abs(mg[0] - mo[0]))
+    assert mo[0] > 0.02 and mo[0] > 2 * f_first        # the curve really moves
+    assert worst < (1e-9 if prec == "fp64" else 1e-3), worst
+    if prec != "fp64":
+        assert worst < 1e-4, worst
+    ctx.close()
