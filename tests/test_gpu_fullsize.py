@@ -35,6 +35,21 @@ def _rel(a, b):
     return np.abs(a - b).max() / (scale if scale > 0 else 1.0)
 
 
+# rows of the state that are components of one vector: each is compared relative to the
+# largest component of its vector (a component that is zero in exact arithmetic, such as the
+# spin about the vertical of parcels resting on horizontal walls, carries only round-off)
+_VECTOR_OF_ROW = {r: (r // 3) * 3 for r in range(9)}
+_VECTOR_OF_ROW.update({r: 14 + ((r - 14) // 3) * 3 for r in range(14, 20)})
+
+
+def _rel_state(g, r, row):
+    if row not in _VECTOR_OF_ROW:
+        return _rel(g[row], r[row])
+    v0 = _VECTOR_OF_ROW[row]
+    scale = max(np.abs(r[q]).max() for q in range(v0, v0 + 3))
+    return np.abs(g[row] - r[row]).max() / (scale if scale > 0 else 1.0)
+
+
 def _pair_keys(cnt, partner):
     """Every (parcel, partner) of the contact table as one sorted int64 key per slot."""
     mask = np.arange(partner.shape[1])[None, :] < cnt[:, None]
@@ -71,7 +86,7 @@ def _check_fp64(g, r, what):
     if r["xi"].size:
         assert np.allclose(g["xi"], r["xi"], rtol=1e-9, atol=1e-18), what
     for row in range(binding.DEM_NSTATE):
-        assert _rel(g["state"][row], r["state"][row]) < 1e-7, (what, binding.STATE_ROWS[row])
+        assert _rel_state(g["state"], r["state"], row) < 1e-7, (what, binding.STATE_ROWS[row])
     for col in range(binding.DEM_NDEP):
         assert _rel(g["src"][:, col], r["src"][:, col]) < 1e-9, (what, binding.SOURCE_ROWS[col])
     for col in range(binding.DEM_NGAS):
@@ -185,7 +200,7 @@ def test_many_movers_on_the_full_grid():
         prev = cur
         sg = ctx.dem_get_state()
         for row in range(binding.DEM_NSTATE):
-            assert _rel(sg[row], so[row]) < 1e-7, (k, binding.STATE_ROWS[row])
+            assert _rel_state(sg, so, row) < 1e-7, (k, binding.STATE_ROWS[row])
         cg, pg, _ = ctx.dem_get_contacts()
         co, po, _ = ref.contacts()
         assert np.array_equal(_pair_keys(cg, pg)[0], _pair_keys(co, po)[0]), k
