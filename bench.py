@@ -5,9 +5,10 @@ deposition + gas update) on GB300, in parcel-updates per second.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 One JSON line on rank 0. The default workload is the 2,000,000-parcel two-ore bed with the
-conical bottom and perforated distributor plate (64x64x384 gas cells), split precision
-(FP32 forces/kinetics, FP64 positions, masses and cell sums), stepped by replaying a CUDA
-graph of one step. Under torchrun every rank steps its own replica of the workload (the
+conical bottom and perforated distributor plate (64x64x384 gas cells), in the precision form
+with FP32 forces and kinetics and compensated FP32 pairs for positions, layer masses and cell
+sums (the FP64-position form and the all-FP64 form are timed beside it), stepped by replaying
+CUDA graphs of ten steps. Under torchrun every rank steps its own replica of the workload (the
 path has no exchange between beds): weak scaling, max-over-ranks time.
 """
 from __future__ import annotations
@@ -38,7 +39,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ibm_2m", choices=["ibm_2m", "split_200k", "plain_2k", "batched_32"])
-    ap.add_argument("--precision", default="split", choices=["split", "fp64", "split_kahan"])
+    ap.add_argument("--precision", default="split_kahan", choices=["split", "fp64", "split_kahan"],
+                    help="split_kahan (default): FP32 forces and kinetics, positions, layer masses and cell "
+                    "sums as compensated FP32 pairs; split: the same with FP64 positions and masses")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
@@ -59,6 +62,10 @@ def parse():
                     "eqs (3-16), (3-17), (3-51) in every bed (a widening of the step; off by default)")
     ap.add_argument("--tuning", default="", help="fixed launch configuration instead of the autotuner, "
                     "e.g. neighbour_lists=1,bs_key=64,skin_permille=50 (profiler runs repeat a plain run's)")
+    ap.add_argument("--no-dense-leg", action="store_true", help="skip the contact-dominated 2M bed")
+    ap.add_argument("--no-batched-leg", action="store_true", help="skip the 32-bed batch")
+    ap.add_argument("--coupling", default="10,1,20", help="coupling intervals n = dt_CFD/dt_DEM of the "
+                    "end-to-end legs; the first one is the e2e headline (Table 3: n = 10 for Bed II)")
     return ap.parse_args()
 
 
@@ -123,6 +130,21 @@ def algorithmic_bytes(kernel: str, n: int, ncells: int, zbar: float, L: float, r
         # cell's eps_g and T_g; Q_rad out (the neighbours' records are cache re-reads)
         return n * ((4 + 16 + 4 + 2 * R + (24 if R == 8 else 0)) + R) + ncells * 2 * R
     return 0.0
+
+
+def survey_step_bytes(n: int, ncells: int, zbar: float, rsize: int, passes: int) -> float:
+    """Minimum traffic of one step by the per-parcel and per-cell list of the method's scope
+    table (parcel state gathered and written once, key and sort passes, live contact history,
+    per-parcel source staging as this layout does it, and ~256 B per gas cell), recomputed
+    from this layout's sizes: the method's floor, against which the builder's kernel-by-kernel
+    algorithmic bytes (which include neighbour lists, the list screen and the cell-property
+    records) are the larger figure."""
+    if rsize == 4:
+        read, write, slot = 24 + 12 + 12 + 4 + 32 + 12, 24 + 12 + 12 + 4 + 32, 4 + 12
+    else:
+        read, write, slot = 24 + 24 + 24 + 8 + 32 + 16, 24 + 24 + 24 + 8 + 32, 4 + 24
+    staging = (13 + 6) * rsize              # per-parcel sources written, then read by the cell sums
+    return n * (read + write + 4 + passes * 16 + zbar * slot * 2 + staging) + ncells * 256
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one full-size ncu
@@ -267,6 +289,113 @@ def radiation_leg(binding, stream, bed, tuning, settle, steps, precision):
     return {"ms_per_step": ms / steps, "value": bed.n * steps / (ms * 1e-3), "unit": UNIT, "steps": steps,
             "settle_steps": settle, "k_radiation_ms": tot / max(nl, 1),
             "what": "eqs (3-16), (3-17), (3-51) on, same workload, tuning and stepping"}
+
+
+def e2e_coupling(binding, stream, bed, ncouple, tuning, settle, steps):
+    """End to end through the C ABI, the paper's coupling round trip (Sec. 4, Fig. 5): every
+    n = coupling_interval steps the gas field comes in from page-locked host memory
+    (dem_set_gas: mass fractions and temperature of every cell), the n steps run as one
+    replayed graph, and the cell sources of the coupling step go back to page-locked host
+    memory (dem_get_sources: 14 doubles per cell) with the bed reduction degrees."""
+    import dataclasses
+    import torch
+    b2 = dataclasses.replace(bed, beds=[dataclasses.replace(c, coupling_interval=ncouple) for c in bed.beds])
+    cx = binding.Context(b2, precision=tuning.pop("_precision"), stream=stream.cuda_stream)
+    if settle > 0:
+        cx.dem_step(settle)
+    cx.dem_set_tuning(**tuning)
+    gas = cx.dem_get_gas()
+    Y = torch.from_numpy(np.ascontiguousarray(gas[:, 1:4])).pin_memory()
+    T = torch.from_numpy(np.ascontiguousarray(gas[:, 4])).pin_memory()
+    out = torch.empty((cx.ncells, 14), dtype=torch.float64).pin_memory()
+    ncpl = max(3, steps // ncouple)
+    for _ in range(2):             # warm-up couplings (graphs captured)
+        cx.dem_set_gas(Y, T)
+        cx.dem_step_graph(ncouple)
+        cx.dem_get_sources(out)
+        cx.dem_reduction_degree()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ncpl):
+        cx.dem_set_gas(Y, T)
+        cx.dem_step_graph(ncouple)
+        cx.dem_get_sources(out)
+        cx.dem_reduction_degree()
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    nsteps = ncpl * ncouple
+    cx.close()
+    return {"coupling_interval": ncouple, "steps": nsteps, "seconds": te, "ms_per_step": 1e3 * te / nsteps,
+            "h2d_bytes_per_step": int(Y.numel() * 8 + T.numel() * 8) / ncouple,
+            "d2h_bytes_per_step": int(out.numel() * 8 + len(bed.beds) * 16) / ncouple}
+
+
+def dense_leg(binding, stream, tuning, settle, steps, precision, parcels=0):
+    """The 2M cone-and-plate bed as a jammed packing below minimum fluidisation: the
+    contact-dominated regime of a settled bed (about 2.7 contacts per parcel), 50 untimed
+    steps (neighbour lists built), then timed like the headline step; the mean number of
+    live contacts is read after the timed steps."""
+    import torch
+    from paper_2311_03908_gb300 import synth
+    kw = {"n": parcels} if parcels else {}
+    bed = synth.config_ibm_2m_dense(U_in=0.02, v_scale=0.01, **kw)
+    cx = binding.Context(bed, precision=precision, stream=stream.cuda_stream)
+    cx.dem_step(settle)
+    cx.dem_set_tuning(**tuning)
+    G = 10
+    steps = max(G, steps // G * G)
+    cx.dem_step_graph(G)
+    cx.dem_step_graph(G)
+    cx.dem_sync()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(steps // G):
+        cx.dem_step_graph(G)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms = a0.elapsed_time(a1)
+    cnt, _, _ = cx.dem_get_contacts()
+    cx.dem_profile(True)
+    cx.dem_step(20)
+    t = cx.dem_kernel_times()
+    cx.dem_profile(False)
+    cx.close()
+    return {"workload": f"ibm_2m_dense ({bed.n} parcels, jammed lattice, U_in 0.02 m/s)",
+            "ms_per_step": ms / steps, "value": bed.n * steps / (ms * 1e-3), "unit": UNIT, "steps": steps,
+            "settle_steps": settle, "zbar_contacts": float(cnt.mean()), "fraction_in_contact": float((cnt > 0).mean()),
+            "contact_kernels_ms": {k: v[1] / max(v[0], 1) for k, v in t.items()
+                                   if k in ("k_contact_screen", "k_contact_forces", "k_pair_search")}}
+
+
+def batched_leg(binding, stream, settle, steps, precision):
+    """The 32-bed sweep (uneven parcel counts, 773-1073 K, 0.2-0.5 m/s inlet): one context,
+    one sort and one launch per kernel for all beds, the steps replayed as CUDA graphs."""
+    import torch
+    bed = make_workload("batched_32")
+    cx = binding.Context(bed, precision=precision, stream=stream.cuda_stream)
+    cx.dem_step(settle)
+    tuning = cx.dem_autotune(20)
+    G = 10
+    steps = max(G, steps // G * G)
+    cx.dem_step_graph(G)
+    cx.dem_step_graph(G)
+    cx.dem_sync()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(steps // G):
+        cx.dem_step_graph(G)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms = a0.elapsed_time(a1)
+    mean, _ = cx.dem_reduction_degree()
+    cx.close()
+    return {"workload": f"batched_32 ({bed.n} parcels in {len(bed.beds)} beds of "
+                        f"{min(bed.meta['counts'])}..{max(bed.meta['counts'])})",
+            "ms_per_step": ms / steps, "value": bed.n * steps / (ms * 1e-3), "unit": UNIT, "steps": steps,
+            "settle_steps": settle, "tuning": tuning, "stepping": "one context, graphs of 10 steps",
+            "f_ov_mean_per_bed_range": [float(mean.min()), float(mean.max())]}
 
 
 def adjoint_cost(binding, stream):
@@ -442,14 +571,19 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": warm, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64" if args.precision != "fp64" else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "split": "f32+f64", "split_kahan": "f32"}[args.precision],
+            "data": "synthetic",
             "config": {"workload": f"{args.workload} ({bed.n} parcels, {ncells} gas cells, {len(bed.beds)} bed(s))",
                        "precision": args.precision, "radiation": bool(args.radiation), "stepping": f"CUDA graph of {G} step(s), replayed", "settle_steps": args.settle,
                        "l2": "inputs larger than L2 (parcel state and history ~ 1 GB)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "gpu_launches": total_launches, "clocks": ck,
             "kernels": kernels, "step_alg_bytes": step_alg,
-            "step_alg_gbs": step_alg / (step_ms * 1e-3) / 1e9, "zbar_contacts": zbar, "fraction_in_contact": fc,
+            "step_alg_gbs": step_alg / (step_ms * 1e-3) / 1e9,
+            "step_alg_frac": step_alg / (step_ms * 1e-3) / 1e9 / peak,
+            "step_survey_bytes": survey_step_bytes(n, ncells, zbar, rsize, passes),
+            "step_survey_frac": survey_step_bytes(n, ncells, zbar, rsize, passes) / (step_ms * 1e-3) / 1e9 / peak,
+            "zbar_contacts": zbar, "fraction_in_contact": fc,
             "neighbour_lists": {"mean_length": L, "builds_in_timed_steps": c_post[1] - c_pre[1], "builds_total": builds,
                                 "steps_total": steps_done},
             "tuning": tuning}
@@ -489,26 +623,32 @@ def main():
     if rank == 0 and not args.no_adjoint:
         line["adjoint"] = adjoint_cost(binding, stream)
 
-    # end to end through the C ABI with host buffers: every step the gas field comes from
-    # pinned host memory (the coupling input) and the bed-mean reduction degree goes back
+    # end to end through the C ABI with host buffers: the coupling round trip of Sec. 4 at
+    # each coupling interval n (gas field in, n steps, cell sources and reduction degree out)
     if not args.no_e2e:
-        nc = ctx.ncells
-        gas = ctx.dem_get_gas()
-        Y = torch.from_numpy(np.ascontiguousarray(gas[:, 1:4])).pin_memory()
-        T = torch.from_numpy(np.ascontiguousarray(gas[:, 4])).pin_memory()
-        ke = max(3, min(args.steps, 200))
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(ke):
-            ctx.dem_set_gas(Y, T)
-            ctx.dem_step_graph(1)
-            ctx.dem_reduction_degree()
-        torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        te = max_over_ranks(te, dist, "cuda")
-        line["e2e"] = {"value": job_throughput(n, world, ke, te * 1e3), "unit": UNIT, "steps": ke,
-                       "h2d_bytes_per_step": int(nc * 4 * 8), "d2h_bytes_per_step": int(len(bed.beds) * 2 * 8),
-                       "api": "dem_set_gas (pinned host) + dem_step_graph + dem_reduction_degree"}
+        legs = {}
+        ke = max(60, min(args.steps, 200))
+        for k, ncouple in enumerate(int(v) for v in args.coupling.split(",")):
+            barrier()
+            r = e2e_coupling(binding, stream, bed, ncouple, dict(tuning, _precision=args.precision),
+                             args.settle, ke)
+            te = max_over_ranks(r["seconds"], dist, "cuda")
+            r["value"] = job_throughput(n, world, r["steps"], te * 1e3)
+            legs[str(ncouple)] = r
+            if k == 0:
+                line["e2e"] = {"value": r["value"], "unit": UNIT, "steps": r["steps"],
+                               "h2d_bytes_per_step": int(r["h2d_bytes_per_step"]),
+                               "d2h_bytes_per_step": int(r["d2h_bytes_per_step"]),
+                               "coupling_interval": ncouple,
+                               "api": "every n steps: dem_set_gas (pinned host Y, T) + dem_step_graph(n) + "
+                                      "dem_get_sources (pinned host, 14 doubles per cell) + dem_reduction_degree"}
+        line["e2e_coupling"] = legs
+    if not args.no_dense_leg:
+        line["dense"] = dense_leg(binding, stream, tuning, 50, min(max(args.steps, 100), 200),
+                                  args.precision, args.parcels)
+    if rank == 0 and not args.no_batched_leg and not args.parcels:
+        line["batched_32"] = batched_leg(binding, stream, args.settle, min(max(args.steps, 100), 200),
+                                         args.precision)
 
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(bed, 1, args.cpu_sample)

@@ -260,13 +260,16 @@ int dem_get_counters(dem_ctx *c, int64_t *out);
 /* Number of kernels launched by the last dem_step/dem_step_graph call (for accounting). */
 int64_t dem_last_launch_count(dem_ctx *c);
 
-/* Replace the gas field (the coupling input of Sec. 4: cell fields from the gas solver).
- * g->Y is (total cells) x 3 mass fractions, g->T the temperatures (host or device by
- * g->on_device); the gas volume fraction is kept; the cells' derived properties are
- * recomputed. Asynchronous on the context stream: host buffers in page-locked memory that
- * the device can address (cudaHostAlloc / cudaHostRegister) are read by the kernel itself
- * when the stream reaches it, so they must stay unchanged until then (as for any
- * asynchronous copy from pinned memory); pageable host buffers are staged by a copy. */
+/* Replace the gas field (the coupling input of Sec. 4, Fig. 5: cell fields from the gas
+ * solver). g->Y is (total cells) x 3 mass fractions, g->T the temperatures (host or device
+ * by g->on_device); the gas volume fraction is kept; the cells' derived properties are
+ * recomputed. Asynchronous: the input is taken on a stream of the context's own, after the
+ * work already enqueued on the context stream; host arrays are copied by a copy engine
+ * (page-locked host memory at the link's rate, without occupying the GPU's SMs), so the
+ * transfer runs beside the next step's binning and contact kernels, which read no gas
+ * state; the step's first kernel that does read it waits for the input. Host buffers must
+ * stay unchanged until the next call that synchronises with the context (as for any
+ * asynchronous copy); device buffers likewise. */
 int dem_set_gas(dem_ctx *c, const dem_gas *g);
 
 /* Per-kernel timing: while on, every kernel that dem_step launches is bracketed by CUDA

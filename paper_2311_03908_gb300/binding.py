@@ -257,9 +257,13 @@ class Context:
         _check(lib().dem_get_gas(self.h, out.ctypes.data_as(C.POINTER(C.c_double))), "dem_get_gas")
         return out
 
-    def dem_get_sources(self):
-        out = np.zeros((self.ncells, DEM_NDEP))
-        _check(lib().dem_get_sources(self.h, out.ctypes.data_as(C.POINTER(C.c_double))), "dem_get_sources")
+    def dem_get_sources(self, out=None):
+        """Cell sources of the last coupling step, (cells, DEM_NDEP) doubles. out: optional
+        host buffer of that shape to fill (a page-locked torch tensor makes the copy fast)."""
+        if out is None:
+            out = np.zeros((self.ncells, DEM_NDEP))
+        _check(lib().dem_get_sources(self.h, C.cast(C.c_void_p(_ptr(out)), C.POINTER(C.c_double))),
+               "dem_get_sources")
         return out
 
     def dem_get_contacts(self):

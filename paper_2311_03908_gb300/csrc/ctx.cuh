@@ -88,6 +88,12 @@ struct dem_ctx {
   std::map<std::tuple<int, int, int>, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;
   std::map<std::tuple<int, int, int>, long long> graph_launches;
   cudaStream_t gst = nullptr;     // private stream used to capture graphs
+  // the coupling input (dem_set_gas) runs on its own stream: the host arrays cross by a
+  // copy engine into gas_stage while the next step's binning and contact kernels run (those
+  // read no gas state); the step's first kernel that reads the gas waits for ev_gas
+  cudaStream_t sst = nullptr;
+  cudaEvent_t ev_main = nullptr, ev_gas = nullptr;
+  bool gas_pending = false;
   // per-kernel event timing
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -112,7 +118,7 @@ template <class P> int enqueue_scatter_state(dem_ctx *c, double *out_dev);
 template <class P> int enqueue_scatter_diag(dem_ctx *c, double *out_dev);
 template <class P> int enqueue_scatter_hist(dem_ctx *c, int *cnt, int *partner, double *xi);
 template <class P> int enqueue_sources(dem_ctx *c);
-template <class P> int enqueue_gas_set(dem_ctx *c, const double *Y, const double *T);
+template <class P> int enqueue_gas_set(dem_ctx *c, const double *Y, const double *T, cudaStream_t st);
 template <class P> int run_adjoint(dem_ctx *c, int nsteps, int ckpt, double *J, double *grad);
 
 // event pair around one kernel when profiling is on (returns the start-event slot or -1)

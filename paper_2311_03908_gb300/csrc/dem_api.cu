@@ -187,9 +187,18 @@ int mark_pending(dem_ctx *c) {
   return DEM_OK;
 }
 
+// the context stream takes up a coupling input still crossing on its own stream
+int join_gas(dem_ctx *c) {
+  if (!c->gas_pending) return DEM_OK;
+  if (cudaStreamWaitEvent(c->st, c->ev_gas, 0) != cudaSuccess) return DEM_ECUDA;
+  c->gas_pending = false;
+  return DEM_OK;
+}
+
 int sync_all(dem_ctx *c) {
   int s = poll(c, true);
   if (s != DEM_OK) return s;
+  if (join_gas(c) != DEM_OK) return c->sticky = DEM_ECUDA;
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return DEM_ECUDA;
   return DEM_OK;
 }
@@ -453,6 +462,12 @@ void dem_destroy(dem_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->st);
   if (c->gst) cudaStreamDestroy(c->gst);
+  if (c->sst) {
+    cudaStreamSynchronize(c->sst);
+    cudaStreamDestroy(c->sst);
+  }
+  if (c->ev_main) cudaEventDestroy(c->ev_main);
+  if (c->ev_gas) cudaEventDestroy(c->ev_gas);
   for (auto &kv : c->graphs) {
     if (kv.second.second) cudaGraphExecDestroy(kv.second.second);
     if (kv.second.first) cudaGraphDestroy(kv.second.first);
@@ -590,7 +605,13 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
   layout(c, real);
   if (cudaMallocHost(&c->h_err, sizeof(int)) != cudaSuccess) { dem_destroy(c); return DEM_ENOMEM; }
   *c->h_err = 0;
-  if (cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) != cudaSuccess) { dem_destroy(c); return DEM_ECUDA; }
+  if (cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_main, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_gas, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->sst, cudaStreamNonBlocking) != cudaSuccess) {
+    dem_destroy(c);
+    return DEM_ECUDA;
+  }
   int rc = DEM_OK;
   auto ck = [&](cudaError_t e) { if (e != cudaSuccess && rc == DEM_OK) rc = e == cudaErrorMemoryAllocation ? DEM_ENOMEM : DEM_ECUDA; };
   ck(cudaMemcpyAsync(c->dbeds, c->hbeds.data(), sizeof(DevBed) * n_beds, cudaMemcpyHostToDevice, c->st));
@@ -748,6 +769,7 @@ int dem_step_graph(dem_ctx *c, int32_t n_steps) {
     c->gcur = 1 - c->gcur;
   }
   if (cudaGraphLaunch(it->second.second, c->st) != cudaSuccess) return c->sticky = DEM_ECUDA;
+  c->gas_pending = false;   // every captured step graph waits for the coupling input's event
   c->launches = c->graph_launches[key];
   return mark_pending(c);
 }
@@ -925,40 +947,29 @@ int dem_get_diag(dem_ctx *c, double *out_host) {
 
 int64_t dem_last_launch_count(dem_ctx *c) { return c ? c->launches : 0; }
 
-// device address of page-locked host memory the current device can reach, or null
-static const double *mapped_host(const double *p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();   // not a CUDA-known pointer (pageable memory): clear the error
-    return nullptr;
-  }
-  if (a.type != cudaMemoryTypeHost || a.devicePointer == nullptr) return nullptr;
-  return static_cast<const double *>(a.devicePointer);
-}
-
 int dem_set_gas(dem_ctx *c, const dem_gas *g) {
   if (!c || !g || !g->Y || !g->T) return DEM_EINVAL;
   int s = poll(c, false);
   if (s != DEM_OK) return s;
   const size_t nc = (size_t)c->ncells;
   const double *Y = g->Y, *T = g->T;
+  // on the input's own stream, after everything the context stream holds so far (the last
+  // step's gas update): host arrays cross by a copy engine into the staging buffer (no SM is
+  // needed, so the transfer overlaps the next step's binning and contact kernels), then one
+  // kernel writes the gas state and the cell properties
+  CK(cudaEventRecord(c->ev_main, c->st));
+  CK(cudaStreamWaitEvent(c->sst, c->ev_main, 0));
   if (!g->on_device) {
-    // host arrays in page-locked memory that the device can address (e.g. from
-    // cudaHostAlloc) are read by the kernel itself; others are staged by a copy
-    const double *Yd = mapped_host(g->Y), *Td = mapped_host(g->T);
-    if (Yd && Td) {
-      Y = Yd;
-      T = Td;
-    } else {
-      if (!c->gas_stage && cudaMalloc(&c->gas_stage, sizeof(double) * 4 * nc) != cudaSuccess) return DEM_ENOMEM;
-      CK(cudaMemcpyAsync(c->gas_stage, g->Y, sizeof(double) * 3 * nc, cudaMemcpyHostToDevice, c->st));
-      CK(cudaMemcpyAsync(c->gas_stage + 3 * nc, g->T, sizeof(double) * nc, cudaMemcpyHostToDevice, c->st));
-      Y = c->gas_stage;
-      T = c->gas_stage + 3 * nc;
-    }
+    if (!c->gas_stage && cudaMalloc(&c->gas_stage, sizeof(double) * 4 * nc) != cudaSuccess) return DEM_ENOMEM;
+    CK(cudaMemcpyAsync(c->gas_stage, g->Y, sizeof(double) * 3 * nc, cudaMemcpyHostToDevice, c->sst));
+    CK(cudaMemcpyAsync(c->gas_stage + 3 * nc, g->T, sizeof(double) * nc, cudaMemcpyHostToDevice, c->sst));
+    Y = c->gas_stage;
+    T = c->gas_stage + 3 * nc;
   }
-  int e = DEM_DISPATCH(c, enqueue_gas_set, c, Y, T);
+  int e = DEM_DISPATCH(c, enqueue_gas_set, c, Y, T, c->sst);
   if (e) return c->sticky = DEM_ECUDA;
+  CK(cudaEventRecord(c->ev_gas, c->sst));
+  c->gas_pending = true;
   return DEM_OK;
 }
 

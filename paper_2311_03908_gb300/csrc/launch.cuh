@@ -149,6 +149,9 @@ int enqueue_binning(dem_ctx *c, int drift) {
 template <class P>
 int enqueue_steps(dem_ctx *c, int nsteps) {
   cudaStream_t st = c->st;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return -1;
+  const bool capturing = cap != cudaStreamCaptureStatusNone;
   for (int s = 0; s < nsteps; ++s) {
     int e = enqueue_binning<P>(c, 1);
     if (e) return e;
@@ -166,15 +169,25 @@ int enqueue_steps(dem_ctx *c, int nsteps) {
     ps = prof_begin(c, "k_contact_forces");
     launch_k(pdl, k_contact_forces<P>, grid_wave(c, c->n, 128), 128, st, V);
     prof_end(c, ps);
+    // the first kernel that reads the gas state or the cell properties waits for a coupling
+    // input still crossing on its own stream (dem_set_gas); a captured graph always carries
+    // the wait, as an external-event node, since a later replay may follow a new input
+    bool waited = false;
+    if (s == 0 && (c->gas_pending || capturing)) {
+      if (cudaStreamWaitEvent(st, c->ev_gas, capturing ? cudaEventWaitExternal : 0) != cudaSuccess) return -1;
+      c->gas_pending = false;
+      waited = true;
+    }
     if (c->any_rad) {   // particle radiation, from the temperatures before the update
       ps = prof_begin(c, "k_radiation");
-      launch_k(pdl, k_radiation<P>, grid_for(c->n, 128), 128, st, V);
+      launch_k(pdl && !waited, k_radiation<P>, grid_for(c->n, 128), 128, st, V);
       prof_end(c, ps);
       ++c->launches;
+      waited = false;
     }
     ps = prof_begin(c, "k_gas_particle");
-    if (c->any_rad) launch_k(pdl, k_gas_particle<P, true>, grid_for(c->n, c->bs_gp), c->bs_gp, st, V);
-    else launch_k(pdl, k_gas_particle<P, false>, grid_for(c->n, c->bs_gp), c->bs_gp, st, V);
+    if (c->any_rad) launch_k(pdl && !waited, k_gas_particle<P, true>, grid_for(c->n, c->bs_gp), c->bs_gp, st, V);
+    else launch_k(pdl && !waited, k_gas_particle<P, false>, grid_for(c->n, c->bs_gp), c->bs_gp, st, V);
     prof_end(c, ps);
     ps = prof_begin(c, "k_cells");
     launch_k(pdl, k_cells<P>, grid_for(c->ncells, c->bs_cells), c->bs_cells, st, V, 0);
@@ -241,11 +254,11 @@ int enqueue_sources(dem_ctx *c) {
 }
 
 template <class P>
-int enqueue_gas_set(dem_ctx *c, const double *Y, const double *T) {
+int enqueue_gas_set(dem_ctx *c, const double *Y, const double *T, cudaStream_t st) {
   StepView<P> V = make_view<P>(c, false);
   V.gas = c->gas[c->gcur];
   V.gas_new = c->gas[1 - c->gcur];
-  k_gas_set_props<P><<<grid_for(c->ncells, 256), 256, 0, c->st>>>(V, Y, T);
+  k_gas_set_props<P><<<grid_for(c->ncells, 256), 256, 0, st>>>(V, Y, T);
   c->gcur = 1 - c->gcur;
   return (int)cudaPeekAtLastError();
 }
@@ -273,6 +286,6 @@ int kernel_limits(int *lim) {
   template int enqueue_scatter_diag<P>(dem_ctx *, double *);                            \
   template int enqueue_scatter_hist<P>(dem_ctx *, int *, int *, double *);              \
   template int enqueue_sources<P>(dem_ctx *);                                           \
-  template int enqueue_gas_set<P>(dem_ctx *, const double *, const double *);
+  template int enqueue_gas_set<P>(dem_ctx *, const double *, const double *, cudaStream_t);
 
 }  // namespace dem

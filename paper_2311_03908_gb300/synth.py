@@ -177,7 +177,7 @@ def _masses(d_cgp: np.ndarray, rho: float, comp: np.ndarray) -> np.ndarray:
 
 
 def _stratified_lattice(seed: int, d: np.ndarray, R: float, z0: float, solid_fraction: float,
-                        stream: int = 0, fill: float = 0.75, jitter: float = 1.0):
+                        stream: int = 0, fill: float = 0.75, jitter: float = 1.0, compress: float = 0.0):
     """Overlap-free positions for spheres of diameters d inside a cylinder of radius R.
 
     Spheres are sorted by size and cut into strata of similar size; each stratum fills
@@ -185,7 +185,9 @@ def _stratified_lattice(seed: int, d: np.ndarray, R: float, z0: float, solid_fra
     target solid fraction) inside the disk, strata are stacked in random order from z0
     upward, and every sphere is jittered inside its own lattice box, so no two spheres
     overlap. fill is the fraction of a layer's sites a stratum of median spheres occupies;
-    jitter scales the displacement inside the box (0: every sphere on its site). Returns x,
+    jitter scales the displacement inside the box (0: every sphere on its site); compress
+    shrinks the pitch below the largest diameter by that fraction, so that neighbouring
+    spheres overlap by up to compress times their diameter (a jammed packing). Returns x,
     y, z in the order of d.
     """
     n = d.size
@@ -205,7 +207,7 @@ def _stratified_lattice(seed: int, d: np.ndarray, R: float, z0: float, solid_fra
     ju = uniform(seed, 3 * n, stream + 12).reshape(3, n)
     for si in perm:
         members = strata[si]
-        pitch = c * float(d[members].max())
+        pitch = c * float(d[members].max()) * (1.0 - compress)
         # sites of a square lattice inside the disk of radius R - pitch/2
         m = int(math.floor(R / pitch)) + 1
         g = (np.arange(-m, m + 1) * pitch)
@@ -223,7 +225,7 @@ def _stratified_lattice(seed: int, d: np.ndarray, R: float, z0: float, solid_fra
             k = layer.size
             # consecutive layers are (p_prev + p)/2 apart, so boxes never overlap
             zc += 0.5 * pitch if prev_pitch is None else 0.5 * (pitch + prev_pitch)
-            slack = 0.49 * jitter * (pitch - d[layer])
+            slack = 0.49 * jitter * np.maximum(pitch - d[layer], 0.0)
             sel = np.argsort(uniform(seed, sx.size, stream + 1000 + layer_no), kind="stable")[:k]
             x[layer] = sx[sel] + slack * (2.0 * ju[0, layer] - 1.0)
             y[layer] = sy[sel] + slack * (2.0 * ju[1, layer] - 1.0)
@@ -323,7 +325,7 @@ def packed_bed(seed: int, n: int, cfg: BedConfig, d_median: float, sigma: float,
                comp=COMP_PURE_HEMATITE, ore: int = ORE_HEMATITE, T0: float | None = None,
                rho: float = 5000.0, solid_fraction: float = 0.4, v_scale: float = 0.0,
                z0: float = 0.0, two_ores: bool = False, name: str = "packed",
-               fill: float = 0.75, jitter: float = 1.0) -> Bed:
+               fill: float = 0.75, jitter: float = 1.0, compress: float = 0.0) -> Bed:
     """A packed bed of n parcels on the bottom of the bed (stratified jittered lattice)."""
     if sigma > 0.0:
         d_real = lognormal_truncated(seed, n, d_median, sigma)
@@ -331,7 +333,8 @@ def packed_bed(seed: int, n: int, cfg: BedConfig, d_median: float, sigma: float,
         d_real = np.full(n, d_median)
     d_cgp = cfg.cg_ratio * d_real
     R = 0.5 * cfg.D
-    x, y, z = _stratified_lattice(seed, d_cgp, R, z0, solid_fraction, fill=fill, jitter=jitter)
+    x, y, z = _stratified_lattice(seed, d_cgp, R, z0, solid_fraction, fill=fill, jitter=jitter,
+                                  compress=compress)
     if two_ores:
         # equal mass of the two ores: alternate parcels by a seeded coin so sizes stay mixed
         coin = uniform(seed, n, 31) < 0.5
@@ -359,26 +362,26 @@ def config_split_200k(seed: int = 2311039082, n: int = 200_000) -> Bed:
 
 def config_ibm_2m(seed: int = 2311039083, n: int = 2_000_000, v_scale: float = 0.0,
                   solid_fraction: float = 0.4, U_in: float = 0.3, name: str = "ibm_2m",
-                  fill: float = 0.75, jitter: float = 1.0) -> Bed:
+                  fill: float = 0.75, jitter: float = 1.0, compress: float = 0.0) -> Bed:
     cfg = BedConfig(D=0.1, H=0.6, wall_kind=WALL_CONE, cone_half_angle=math.radians(45.0),
                     cone_height=0.05, plate_z=0.05, hole_d=1e-3, hole_pitch=4e-3,
                     nx=64, ny=64, nz=384, dt=1e-5, cg_ratio=6.0, U_in=U_in, T_in=1023.0,
                     Y_in=(1.0, 0.0, 0.0), sphericity=(0.86, 0.85))
     b = packed_bed(seed, n, cfg, 120e-6, 0.25, two_ores=True, z0=cfg.plate_z, name=name,
-                   v_scale=v_scale, solid_fraction=solid_fraction, fill=fill, jitter=jitter)
+                   v_scale=v_scale, solid_fraction=solid_fraction, fill=fill, jitter=jitter, compress=compress)
     b.meta["steps"] = 500
     return b
 
 
 def config_ibm_2m_dense(seed: int = 2311039086, n: int = 2_000_000, v_scale: float = 0.05,
-                        U_in: float = 0.3) -> Bed:
-    """The 2M bed packed at touching pitch: every lattice site filled, each sphere on its
-    site, a stratum's largest spheres exactly one diameter apart and the others within a few
-    micrometres of their neighbours, with random velocities, so contacts form in the first
-    steps and stay (the contact-dominated regime of a settled bed). U_in below about
+                        U_in: float = 0.3, compress: float = 0.005) -> Bed:
+    """The 2M bed as a jammed packing: every lattice site filled, each sphere on its site, the
+    pitch 0.5 % below the largest diameter of its stratum, so that lattice neighbours overlap
+    by up to a few micrometres (about 2.7 contacts per parcel from the first step: the
+    contact-dominated regime of a settled bed), with random velocities. U_in below about
     0.03 m/s keeps it packed (below minimum fluidisation of 120 um ore in H2 at 1023 K)."""
     return config_ibm_2m(seed, n, v_scale=v_scale, solid_fraction=0.6, U_in=U_in, name="ibm_2m_dense",
-                         fill=1.0, jitter=0.0)
+                         fill=1.0, jitter=0.0, compress=compress)
 
 
 def config_adjoint_64k(seed: int = 2311039084, n: int = 64_000) -> Bed:

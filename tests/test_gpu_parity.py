@@ -268,7 +268,7 @@ def test_set_gas_input_paths_agree(prec):
     page-locked host memory (read by the kernel itself) and device tensors -- gives the same
     state bit for bit; handing back the current field changes nothing."""
     bed = synth.small_packed(seed=5, n=2000, v_scale=0.2)
-    ctxs = [_ctx(bed, prec) for _ in range(5)]
+    ctxs = [_ctx(bed, prec) for _ in range(7)]
     for c in ctxs:
         c.dem_step(5)
     g = ctxs[0].dem_get_gas()
@@ -281,12 +281,27 @@ def test_set_gas_input_paths_agree(prec):
     ctxs[2].dem_set_gas(torch.from_numpy(Y).pin_memory(), torch.from_numpy(T).pin_memory())
     ctxs[3].dem_set_gas(torch.from_numpy(Y).cuda(), torch.from_numpy(T).cuda())
     ctxs[4].dem_set_gas(Y0, T0)
-    for c in ctxs:
+    # the input read back before any step, and taken by a replayed step graph (whose first
+    # gas-reading kernel waits for the input's own stream)
+    ctxs[5].dem_set_gas(torch.from_numpy(Y).pin_memory(), torch.from_numpy(T).pin_memory())
+    g5 = ctxs[5].dem_get_gas()
+    assert np.allclose(g5[:, 1:4], Y, rtol=0, atol=1e-7) and np.allclose(g5[:, 4], T, rtol=1e-7)
+    ctxs[6].dem_step_graph(2)
+    ctxs[6].dem_set_gas(torch.from_numpy(Y).pin_memory(), torch.from_numpy(T).pin_memory())
+    for c in ctxs[:6]:
         c.dem_step(5)
+    ctxs[6].dem_step_graph(5)
     s = [c.dem_get_state() for c in ctxs]
     gs = [c.dem_get_gas() for c in ctxs]
-    assert np.array_equal(s[1], s[2]) and np.array_equal(s[1], s[3])
-    assert np.array_equal(gs[1], gs[2]) and np.array_equal(gs[1], gs[3])
+    assert np.array_equal(s[1], s[2]) and np.array_equal(s[1], s[3]) and np.array_equal(s[1], s[5])
+    assert np.array_equal(gs[1], gs[2]) and np.array_equal(gs[1], gs[3]) and np.array_equal(gs[1], gs[5])
+    ref = _ctx(bed, prec)        # the graph-stepped context against eager steps of its own history
+    ref.dem_step(5)
+    ref.dem_step(2)
+    ref.dem_set_gas(Y, T)
+    ref.dem_step(5)
+    assert np.array_equal(ref.dem_get_state(), s[6]) and np.array_equal(ref.dem_get_gas(), gs[6])
+    ref.close()
     assert np.array_equal(s[4], s[0]) and np.array_equal(gs[4], gs[0])
     assert not np.array_equal(s[1], s[0])
     for c in ctxs:
