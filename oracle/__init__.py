@@ -33,7 +33,7 @@ for _i, _name in enumerate(
          "NZ", "DT", "KN", "KT_KN", "REST", "MU_S", "MU_R", "CG", "NCOUPLE", "U_IN", "T_IN", "P0",
          "Y_IN", "Y_IN1", "Y_IN2", "K0", "K01", "K02", "EA", "EA1", "EA2", "TAU", "PSI", "PSI1",
          "XI0", "XI01", "PORE", "PORE1", "RHOT", "RHOT1", "RHOT2", "RHOT3", "DPDZ", "EPS_MIN",
-         "FLAGS", "EMISS"]):
+         "FLAGS", "EMISS", "LAMP", "LAMP1", "LAMW"]):
     _B[_name] = _i
 NB = len(_B)
 
@@ -46,8 +46,8 @@ STATE_NAMES = ["x", "y", "z", "vx", "vy", "vz", "wx", "wy", "wz", "T", "m_h", "m
 
 D_FC, D_TC, D_FD, D_K, D_QCONV, D_QR, D_QRM = 0, 3, 6, 9, 10, 11, 12
 D_XIDOT, D_MDOT, D_FFILM, D_A, D_B, D_SH, D_NU, D_RE, D_NCONTACT, D_CELL = 13, 16, 20, 21, 24, 27, 28, 29, 30, 31
-D_TSE, D_QRAD = 32, 33
-ND = 34
+D_TSE, D_QRAD, D_QCOND = 32, 33, 34
+ND = 35
 
 G_EPS, G_Y, G_T, G_MARK = 0, 1, 4, 5
 NG = 6
@@ -105,6 +105,12 @@ def lib():
             getattr(L, f).argtypes = [C.c_int32, dp, dp, dp, dp, ip, C.c_int64]
             getattr(L, f).restype = C.c_int64
         L.orc_wall_distance.argtypes = [dp, C.c_double, C.c_double, C.c_double, dp, dp]
+        L.orc_restitution_f.argtypes = [C.c_double]
+        L.orc_restitution_f.restype = C.c_double
+        L.orc_e_cgp.argtypes = [C.c_double, C.c_double]
+        L.orc_e_cgp.restype = C.c_double
+        L.orc_conduction_pair.argtypes = [dp] + [C.c_double] * 8 + [dp]
+        L.orc_conduction_wall.argtypes = [dp] + [C.c_double] * 5 + [dp]
         _lib = L
     return _lib
 
@@ -155,6 +161,8 @@ def bed_vector(cfg) -> np.ndarray:
     v[_B["EPS_MIN"]] = c["eps_min"]
     v[_B["FLAGS"]] = c["flags"]
     v[_B["EMISS"]] = c["emissivity"]
+    v[_B["LAMP"]:_B["LAMP"] + 2] = c["lambda_p"]
+    v[_B["LAMW"]] = c["lambda_wall"]
     return v
 
 
@@ -360,3 +368,31 @@ def wall_distance(cfg, x, y, z):
     lib().orc_wall_distance(bp, float(x), float(y), float(z), dist.ctypes.data_as(C.POINTER(C.c_double)),
                             nrm.ctypes.data_as(C.POINTER(C.c_double)))
     return dist, nrm.reshape(4, 3)
+
+
+def restitution_f(e):
+    """f(e) of eqs (3-43), (3-44) (the reading: maximum overlap of a damped linear collision)."""
+    return float(lib().orc_restitution_f(float(e)))
+
+
+def e_cgp(e, k):
+    """Restitution coefficient of a coarse-grained parcel, eq (3-45), clamped at 0."""
+    return float(lib().orc_e_cgp(float(e), float(k)))
+
+
+def conduction_pair(cfg, Ra, Rb, d, Ta, Tb, lam_a, lam_b, lam_g):
+    """Heat into parcel a from parcel b in contact: dict(Qpp, Qpfp, Rc, I) (coarse-grained)."""
+    bv, bp = _d(bed_vector(cfg))
+    out = np.zeros(4)
+    lib().orc_conduction_pair(bp, float(Ra), float(Rb), float(d), float(Ta), float(Tb), float(lam_a),
+                              float(lam_b), float(lam_g), out.ctypes.data_as(C.POINTER(C.c_double)))
+    return dict(Qpp=out[0], Qpfp=out[1], Rc=out[2], I=out[3])
+
+
+def conduction_wall(cfg, R, h, Ta, lam_a, lam_g):
+    """Heat into a parcel from the wall at distance h: dict(Qpp, Qpfp, Rc, I) (coarse-grained)."""
+    bv, bp = _d(bed_vector(cfg))
+    out = np.zeros(4)
+    lib().orc_conduction_wall(bp, float(R), float(h), float(Ta), float(lam_a), float(lam_g),
+                              out.ctypes.data_as(C.POINTER(C.c_double)))
+    return dict(Qpp=out[0], Qpfp=out[1], Rc=out[2], I=out[3])

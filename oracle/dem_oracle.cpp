@@ -546,6 +546,117 @@ void contact_law(const double *bed, double mstar, double ri, const double n[3], 
   for (int c = 0; c < 3; ++c) o.xi[c] = xi[c];
 }
 
+// ---------------------------------------------------------------------------------------
+// Contact heat conduction: particle-particle (eq (3-14)), particle-fluid-particle
+// (eq (3-15)), particle-wall and particle-fluid-wall (eqs (3-15-1), (3-15-2)), with the
+// coarse-grained scaling of Sec. 3.3 (eqs (3-42)..(3-48-2)). The paper takes the meaning
+// of R_c, lambda_e and the integration limits from another paper; the readings:
+//   * both sums run over the contacts of eq (3-3) (the same n_b parcels and walls);
+//   * R_c is the radius of the circle in which the two overlapping spheres intersect (for
+//     a wall: in which the sphere meets the wall's tangent plane);
+//   * lambda_e is the series conductance of the two constrictions, lambda_a lambda_b /
+//     (lambda_a + lambda_b) (for two equal spheres Q = 2 lambda a dT, the constriction
+//     resistance 1/(4 lambda a) of each side in series); lambda_p per ore type and the
+//     wall's lambda_w are bed parameters;
+//   * the fluid lens of eq (3-15) spans the smaller sphere's projected disk (R_out =
+//     min(R_a, R_b); a wall: r_out = R) and ends where the gap between the surfaces falls
+//     below the gas mean free path of Sec. 2.3 for hydrogen at the bed pressure,
+//     L_min = 1.013 / p cm (R_in, r_in); lambda_g is the mean of the two parcels' cells'
+//     (a wall: the parcel's cell);
+//   * the wall is at the bed's inlet temperature (Table 3 lists them equal);
+//   * eq (3-43) as printed is garbled; it is read as the maximum overlap of a damped
+//     linear spring-dashpot collision in units of v/omega_0,
+//     f(e) = exp(-zeta arccos(zeta) / sqrt(1 - zeta^2)), zeta of eq (3-44);
+//   * e_CGP of eq (3-45) has no real value for k >= 1/(1 - e^2) (5.26 at e = 0.9); it is
+//     clamped at 0, where f takes its limit exp(-1) (critical damping).
+// ---------------------------------------------------------------------------------------
+double restitution_f(double e) {
+  if (!(e > 0.0)) return std::exp(-1.0);
+  if (e >= 1.0) return 1.0;
+  const double le = std::log(e);
+  const double zeta = -le / std::sqrt(kPi * kPi + le * le);         // eq (3-44)
+  return std::exp(-zeta * std::acos(zeta) / std::sqrt(1.0 - zeta * zeta));   // eq (3-43)
+}
+double e_cgp(double e, double k) {                                   // eq (3-45)
+  const double a = 1.0 + k * (e * e - 1.0);
+  return a > 0.0 ? std::sqrt(a) : 0.0;
+}
+// adaptive Simpson quadrature of f over [a, b] to an absolute tolerance
+template <class F> double simpson_rec(F &f, double a, double b, double fa, double fm, double fb, double whole,
+                                      double tol, int depth) {
+  const double m = 0.5 * (a + b), lm = 0.5 * (a + m), rm = 0.5 * (m + b);
+  const double flm = f(lm), frm = f(rm);
+  const double left = (m - a) / 6.0 * (fa + 4.0 * flm + fm), right = (b - m) / 6.0 * (fm + 4.0 * frm + fb);
+  const double diff = left + right - whole;
+  if (depth <= 0 || std::fabs(diff) <= 15.0 * tol) return left + right + diff / 15.0;
+  return simpson_rec(f, a, m, fa, flm, fm, left, 0.5 * tol, depth - 1) +
+         simpson_rec(f, m, b, fm, frm, fb, right, 0.5 * tol, depth - 1);
+}
+template <class F> double simpson(F f, double a, double b, double tol) {
+  const double fa = f(a), fb = f(b), fm = f(0.5 * (a + b));
+  return simpson_rec(f, a, b, fa, fm, fb, (b - a) / 6.0 * (fa + 4.0 * fm + fb), tol, 48);
+}
+inline double gap_lmin(const double *bed) { return 1.013e-2 / bed[ORC_B_P0]; }   // m (Sec. 2.3, x = 1)
+// eq (3-15): int_{R_in}^{R_out} R / (d - sqrt(Ra^2 - R^2) - sqrt(Rb^2 - R^2)) dR
+double lens_integral_pair(double Ra, double Rb, double d, double Lmin) {
+  auto L = [&](double R) { return d - std::sqrt(Ra * Ra - R * R) - std::sqrt(Rb * Rb - R * R); };
+  const double Rout = std::min(Ra, Rb);
+  if (!(L(Rout) > Lmin)) return 0.0;
+  double lo = 0.0, hi = Rout;   // L increases with R: R_in where L(R_in) = L_min
+  if (L(lo) < Lmin) {
+    for (int it = 0; it < 200 && hi - lo > 1e-20; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (L(mid) < Lmin) lo = mid; else hi = mid;
+    }
+    lo = hi;
+  }
+  const double scale = Rout * Rout / Lmin;
+  return simpson([&](double R) { return R / L(R); }, lo, Rout, 1e-13 * scale);
+}
+// eq (3-15-2): int_{r_in}^{r_out} r / L_w dr with L_w = h - sqrt(R^2 - r^2)
+double lens_integral_wall(double R, double h, double Lmin) {
+  if (!(h > Lmin)) return 0.0;
+  const double u = h - Lmin;
+  const double rin = u < R ? std::sqrt(R * R - u * u) : 0.0;
+  const double scale = R * R / Lmin;
+  return simpson([&](double r) { return r / (h - std::sqrt(R * R - r * r)); }, rin, R, 1e-13 * scale);
+}
+// Q into parcel a from a parcel b in contact (scaled to the coarse-grained system)
+void conduction_pair(const double *bed, double Ra, double Rb, double d, double Ta, double Tb, double lam_a,
+                     double lam_b, double lam_g, double out[4]) {
+  const double k = bed[ORC_B_CG];
+  const double e = bed[ORC_B_REST];
+  const double delta = Ra + Rb - d;
+  // radius of the intersection circle of the two spheres
+  const double Rc = std::sqrt(delta * (d + Ra + Rb) * (d + Ra - Rb) * (d - Ra + Rb)) / (2.0 * d);
+  const double lam_e = lam_a * lam_b / (lam_a + lam_b);
+  const double Qpp = 4.0 * Rc * lam_e * (Tb - Ta);                              // eq (3-14)
+  const double I = lens_integral_pair(Ra, Rb, d, gap_lmin(bed));
+  const double Qpfp = 2.0 * kPi * lam_g * (Tb - Ta) * I;                        // eq (3-15)
+  const double sc = std::pow(k, 0.75) * std::sqrt(restitution_f(e) / restitution_f(e_cgp(e, k)));
+  out[0] = sc * Qpp;                                                            // eq (3-46)
+  out[1] = k * k * Qpfp;                                                        // eq (3-48)
+  out[2] = Rc;
+  out[3] = I;
+}
+void conduction_wall(const double *bed, double R, double h, double Ta, double lam_a, double lam_g, double out[4]) {
+  const double k = bed[ORC_B_CG];
+  const double e = bed[ORC_B_REST];
+  const double Tw = bed[ORC_B_T_IN];
+  const double lam_w = bed[ORC_B_LAMW];
+  const double delta = R - h;
+  const double Rc = std::sqrt(delta * (2.0 * R - delta));
+  const double lam_e = lam_a * lam_w / (lam_a + lam_w);
+  const double Qpw = 4.0 * Rc * lam_e * (Tw - Ta);                              // eq (3-15-1)
+  const double I = lens_integral_wall(R, h, gap_lmin(bed));
+  const double Qpfw = 2.0 * kPi * lam_g * (Tw - Ta) * I;                        // eq (3-15-2)
+  const double sc = std::pow(k, 0.75) * std::sqrt(restitution_f(e) / restitution_f(e_cgp(e, k)));
+  out[0] = sc * Qpw;                                                            // eq (3-48-1)
+  out[1] = k * k * Qpfw;                                                        // eq (3-48-2)
+  out[2] = Rc;
+  out[3] = I;
+}
+
 struct Contact { int32_t partner; double xi[3]; };
 
 struct Grid {
@@ -711,8 +822,13 @@ void step_once(Oracle &o) {
     int nc = std::max(1, ib(o.B(b), ORC_B_NCOUPLE));
     coupled[b] = ((o.step_no + 1) % nc) == 0;
   }
-  // 2. contacts, per bed
-  std::vector<double> Fc(3 * (size_t)n, 0.0), Tc(3 * (size_t)n, 0.0);
+  // 2. contacts, per bed (and the contact conduction of beds that switch it on)
+  std::vector<double> Fc(3 * (size_t)n, 0.0), Tc(3 * (size_t)n, 0.0), Qcond(n, 0.0);
+  std::vector<double> lamg(n, 0.0);   // gas conductivity of each parcel's cell (after the drift)
+  for (int i = 0; i < n; ++i) {
+    Grid g = make_grid(o.B(o.bed[i]));
+    lamg[i] = gp[o.cell_off[o.bed[i]] + cell_of(g, o.s[0][i], o.s[1][i], o.s[2][i], nullptr)].lam;
+  }
   for (int b = 0; b < o.nb; ++b) {
     const double *bd = o.B(b);
     const auto &ids = o.members[b];
@@ -721,6 +837,7 @@ void step_once(Oracle &o) {
       continue;
     }
     const double k = bd[ORC_B_CG];
+    const bool cond = ((unsigned)ib(bd, ORC_B_FLAGS) & ORC_CONDUCTION) != 0;
     double hmax = 0.0;
     for (int32_t i : ids) hmax = std::max(hmax, k * o.dreal[i]);
     CellList cl;
@@ -731,7 +848,7 @@ void step_once(Oracle &o) {
       int32_t i = ids[t];
       double ri = 0.5 * (k * o.dreal[i]);
       double mi = parcel_mass(o, i);
-      struct Cand { int32_t id; double n[3]; double delta; double mstar; double vrel[3]; };
+      struct Cand { int32_t id; double n[3]; double delta; double dist; double mstar; double vrel[3]; };
       std::vector<Cand> cands;
       cl.neighbours(X[i], Y[i], Z[i], [&](int32_t j) {
         if (j == i) return;
@@ -744,6 +861,7 @@ void step_once(Oracle &o) {
         c.id = j;
         c.n[0] = dx / d; c.n[1] = dy / d; c.n[2] = dz / d;
         c.delta = rs - d;
+        c.dist = d;
         double mj = parcel_mass(o, j);
         c.mstar = mi * mj / (mi + mj);
         double wsum[3];
@@ -761,6 +879,7 @@ void step_once(Oracle &o) {
         c.id = -1 - p;
         for (int q = 0; q < 3; ++q) c.n[q] = -nw[p][q];
         c.delta = ri - dist[p];
+        c.dist = dist[p];
         c.mstar = mi;
         double w[3] = {ri * o.s[ORC_S_WX][i], ri * o.s[ORC_S_WY][i], ri * o.s[ORC_S_WZ][i]};
         double cr[3] = {w[1] * c.n[2] - w[2] * c.n[1], w[2] * c.n[0] - w[0] * c.n[2], w[0] * c.n[1] - w[1] * c.n[0]};
@@ -778,6 +897,19 @@ void step_once(Oracle &o) {
         contact_law(bd, c.mstar, ri, c.n, c.delta, c.vrel, xo, w, co);
         for (int q = 0; q < 3; ++q) { Fc[3 * (size_t)i + q] += co.F[q]; Tc[3 * (size_t)i + q] += co.Tq[q]; }
         if ((int)nh.size() < ORC_MAX_CONTACTS) nh.push_back(Contact{c.id, {co.xi[0], co.xi[1], co.xi[2]}});
+        if (cond) {
+          double q4[4];
+          const double lam_a = bd[ORC_B_LAMP + o.ore[i]];
+          if (c.id >= 0) {
+            const int32_t j = c.id;
+            const double rj = 0.5 * (k * o.dreal[j]);
+            conduction_pair(bd, ri, rj, c.dist, o.s[ORC_S_T][i], o.s[ORC_S_T][j], lam_a,
+                            bd[ORC_B_LAMP + o.ore[j]], 0.5 * (lamg[i] + lamg[j]), q4);
+          } else {
+            conduction_wall(bd, ri, c.dist, o.s[ORC_S_T][i], lam_a, lamg[i], q4);
+          }
+          Qcond[i] += q4[0] + q4[1];
+        }
       }
       o.hist[i] = nh;
       o.diag[(size_t)ORC_D_NCONTACT * n + i] = (double)cands.size();
@@ -889,7 +1021,7 @@ void step_once(Oracle &o) {
     double cpp = 0.0;
     for (int z = 0; z < 4; ++z) cpp += (m[z] / mp) * nasa_cp(3 + z, Tp);
     double Qrx = kn.Qr + kn.Qrm;
-    o.s[ORC_S_T][i] = Tp + dt * (Qconv + Qrx + Qrad[i]) / (mp * cpp);
+    o.s[ORC_S_T][i] = Tp + dt * (Qconv + Qrx + Qrad[i] + Qcond[i]) / (mp * cpp);
     // eq (3-4): layer masses change only at coupling steps (Sec. 4)
     if (coupled[b])
       for (int z = 0; z < 4; ++z) o.s[ORC_S_M + z][i] = std::max(m[z] + kn.mdot[z] * dtm, 0.0);
@@ -930,6 +1062,7 @@ void step_once(Oracle &o) {
     dg[(size_t)ORC_D_CELL * n + i] = (double)lc;
     dg[(size_t)ORC_D_TSE * n + i] = Tse[i];
     dg[(size_t)ORC_D_QRAD * n + i] = Qrad[i];
+    dg[(size_t)ORC_D_QCOND * n + i] = Qcond[i];
   }
   // 4. deposition: per-cell sums in parcel order (eqs (3-25), (3-27a), (3-38), (3-39),
   //    (4-4), (4-5), (4-10), (4-11)); only at coupling steps
@@ -1322,6 +1455,17 @@ int64_t orc_pairs_cells(int32_t n, const double *x, const double *y, const doubl
   int64_t np = (int64_t)out.size();
   for (int64_t t = 0; t < std::min(np, max_pairs); ++t) { pairs[2 * t] = out[t].first; pairs[2 * t + 1] = out[t].second; }
   return np;
+}
+
+double orc_restitution_f(double e) { return restitution_f(e); }
+double orc_e_cgp(double e, double k) { return e_cgp(e, k); }
+void orc_conduction_pair(const double *bed, double Ra, double Rb, double d, double Ta, double Tb,
+                         double lam_a, double lam_b, double lam_g, double *out4) {
+  conduction_pair(bed, Ra, Rb, d, Ta, Tb, lam_a, lam_b, lam_g, out4);
+}
+void orc_conduction_wall(const double *bed, double R, double h, double Ta, double lam_a, double lam_g,
+                         double *out4) {
+  conduction_wall(bed, R, h, Ta, lam_a, lam_g, out4);
 }
 
 void orc_wall_distance(const double *bed, double x, double y, double z, double *dist4, double *n12) {

@@ -26,7 +26,9 @@ enum {
   ORC_B_T_IN, ORC_B_P0, ORC_B_Y_IN /* 3 */, ORC_B_K0 = ORC_B_Y_IN + 3, ORC_B_EA = ORC_B_K0 + 3,
   ORC_B_TAU = ORC_B_EA + 3, ORC_B_PSI /* 2 */, ORC_B_XI0 = ORC_B_PSI + 2,
   ORC_B_PORE = ORC_B_XI0 + 2, ORC_B_RHOT = ORC_B_PORE + 2, ORC_B_DPDZ = ORC_B_RHOT + 4,
-  ORC_B_EPS_MIN, ORC_B_FLAGS, ORC_B_EMISS /* particle emissivity, eq (3-16) */, ORC_NB
+  ORC_B_EPS_MIN, ORC_B_FLAGS, ORC_B_EMISS /* particle emissivity, eq (3-16) */,
+  ORC_B_LAMP /* 2: particle thermal conductivity per ore, W/m/K */, ORC_B_LAMW = ORC_B_LAMP + 2 /* wall, W/m/K */,
+  ORC_NB
 };
 
 /* physics switches (bit mask in ORC_B_FLAGS) */
@@ -34,7 +36,8 @@ enum {
   ORC_NO_GRAVITY = 1, ORC_NO_DRAG = 2, ORC_NO_HEAT = 4, ORC_NO_KINETICS = 8,
   ORC_NO_GAS_UPDATE = 16, ORC_NO_FILM = 32, ORC_NO_LAYER = 64, ORC_NO_RXN_HEAT = 128,
   ORC_NO_CONTACTS = 256,
-  ORC_RADIATION = 512   /* switch ON the particle radiation of eqs (3-16), (3-17), (3-51) */
+  ORC_RADIATION = 512,  /* switch ON the particle radiation of eqs (3-16), (3-17), (3-51) */
+  ORC_CONDUCTION = 1024 /* switch ON the contact conduction of eqs (3-14)..(3-15-2), (3-42)..(3-48-2) */
 };
 
 /* per-parcel state returned by orc_get_state: ORC_NS rows of n doubles */
@@ -51,7 +54,8 @@ enum {
   ORC_D_XIDOT /* 3, mol/s per real particle, after limiting */ = 13,
   ORC_D_MDOT = 16 /* 4, kg/s per parcel */, ORC_D_FFILM = 20, ORC_D_A = 21 /* 3 */,
   ORC_D_B = 24 /* 3 */, ORC_D_SH = 27, ORC_D_NU, ORC_D_RE, ORC_D_NCONTACT, ORC_D_CELL,
-  ORC_D_TSE /* eq (3-17), 0 without radiation */, ORC_D_QRAD /* eq (3-51), W per parcel */, ORC_ND
+  ORC_D_TSE /* eq (3-17), 0 without radiation */, ORC_D_QRAD /* eq (3-51), W per parcel */,
+  ORC_D_QCOND /* contact conduction with parcels and walls, W per parcel, 0 when off */, ORC_ND
 };
 
 /* per gas cell: ORC_NG doubles */
@@ -124,6 +128,17 @@ int64_t orc_pairs_bruteforce(int32_t n, const double *x, const double *y, const 
 int64_t orc_pairs_cells(int32_t n, const double *x, const double *y, const double *z,
                         const double *r, int32_t *pairs, int64_t max_pairs);
 void orc_wall_distance(const double *bed, double x, double y, double z, double *dist4, double *n12);
+/* contact conduction pieces: f(e) of eqs (3-43), (3-44); e_CGP of eq (3-45) (clamped at 0);
+ * one parcel pair (radii, centre distance, temperatures, particle and gas conductivities)
+ * -> out[0] Q_pp' and out[1] Q_pfp' into parcel a (eqs (3-14), (3-15), (3-46), (3-48)),
+ * out[2] the contact radius R_c, out[3] the lens integral of eq (3-15); one parcel and a
+ * wall at distance h -> the same for eqs (3-15-1), (3-15-2), (3-48-1), (3-48-2). */
+double orc_restitution_f(double e);
+double orc_e_cgp(double e, double k);
+void orc_conduction_pair(const double *bed, double Ra, double Rb, double d, double Ta, double Tb,
+                         double lam_a, double lam_b, double lam_g, double *out4);
+void orc_conduction_wall(const double *bed, double R, double h, double Ta, double lam_a, double lam_g,
+                         double *out4);
 
 #ifdef __cplusplus
 }

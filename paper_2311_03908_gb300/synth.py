@@ -47,6 +47,7 @@ NO_LAYER = 1 << 6
 NO_RXN_HEAT = 1 << 7
 NO_CONTACTS = 1 << 8
 RADIATION = 1 << 9   # switches ON the particle radiation (off by default)
+CONDUCTION = 1 << 10  # switches ON the contact heat conduction (off by default)
 
 # Kinetic presets: (k0 [m/s], Ea [J/mol]) for R1 (h->m), R2 (m->w), R3 (w->Fe).
 TAKENAKA = ((29.17, 15.56, 2858.0), (66974.0, 75345.0, 117204.0))        # Table 2
@@ -135,6 +136,8 @@ class BedConfig:
     eps_min: float = 0.36                   # lower clamp of the gas volume fraction
     flags: int = 0                          # physics switches (NO_* bits, RADIATION)
     emissivity: float = 0.85                # particle emissivity (Table 3), used with RADIATION
+    lambda_p: tuple = (2.5, 2.5)            # particle thermal conductivity per ore type, W/m/K (CONDUCTION)
+    lambda_wall: float = 16.0               # reactor wall thermal conductivity, W/m/K (CONDUCTION)
 
     def as_dict(self) -> dict:
         return dict(self.__dict__)
