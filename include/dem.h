@@ -52,7 +52,18 @@ enum {
 enum { DEM_PREC_FP64 = 0, DEM_PREC_SPLIT = 1, DEM_PREC_SPLIT_KAHAN = 2 };
 
 /* physics switches (bit mask in dem_bed_config.flags); 0 = the full method without
- * radiation. DEM_RADIATION switches ON the particle radiation of eqs (3-16), (3-17) and
+ * radiation and contact conduction. DEM_CONDUCTION switches ON the contact heat conduction
+ * of eqs (3-14), (3-15) (parcel-parcel and parcel-fluid-parcel) and (3-15-1), (3-15-2)
+ * (parcel-wall and parcel-fluid-wall), scaled to the coarse-grained parcels by eqs (3-46),
+ * (3-48), (3-48-1), (3-48-2), over the contacts of eq (3-3): R_c is the radius of the
+ * circle in which the overlapping spheres (or a sphere and the wall's tangent plane) meet;
+ * lambda_e = lambda_a lambda_b / (lambda_a + lambda_b) with the per-ore lambda_p and the
+ * wall's lambda_wall; the fluid lens spans the smaller sphere's disk down to a gap of
+ * 1.013 / p0 cm (the Sec. 2.3 mean free path of H2), with the mean lambda_g of the two
+ * parcels' cells (a wall: the parcel's); walls are at T_in; f(e) of eq (3-43) is
+ * exp(-zeta arccos(zeta) / sqrt(1 - zeta^2)) with zeta of eq (3-44), and e_CGP of
+ * eq (3-45) is clamped at 0. The heat enters each parcel's balance (eq (3-8)), not the gas.
+ * Radiation: DEM_RADIATION switches ON the particle radiation of eqs (3-16), (3-17) and
  * (3-51): Q_rad = k^3 sigma eta_p pi d_p^2 (T_se^4 - T_p^4), T_se = eps_g T_g + (1 - eps_g)
  * times the mean temperature of the parcels whose centres lie within 1.5 k d_p of the
  * parcel's centre (the parcel itself included), eps_g and T_g those of the parcel's gas
@@ -61,7 +72,7 @@ enum { DEM_PREC_FP64 = 0, DEM_PREC_SPLIT = 1, DEM_PREC_SPLIT_KAHAN = 2 };
 enum {
   DEM_NO_GRAVITY = 1, DEM_NO_DRAG = 2, DEM_NO_HEAT = 4, DEM_NO_KINETICS = 8,
   DEM_NO_GAS_UPDATE = 16, DEM_NO_FILM = 32, DEM_NO_LAYER = 64, DEM_NO_RXN_HEAT = 128,
-  DEM_NO_CONTACTS = 256, DEM_RADIATION = 512
+  DEM_NO_CONTACTS = 256, DEM_RADIATION = 512, DEM_CONDUCTION = 1024
 };
 
 enum { DEM_WALL_FLAT = 0, DEM_WALL_CONE = 1 };
@@ -106,6 +117,9 @@ typedef struct {
   uint32_t flags;         /* DEM_NO_* switches and DEM_RADIATION */
   double emissivity;      /* particle emissivity eta_p of eq (3-16), in [0, 1] (Table 3: 0.85);
                              read only with DEM_RADIATION */
+  double lambda_p[2];     /* particle thermal conductivity per ore type, W/m/K (> 0); read only
+                             with DEM_CONDUCTION (not printed in the paper) */
+  double lambda_wall;     /* reactor wall thermal conductivity, W/m/K (> 0); DEM_CONDUCTION */
 } dem_bed_config;
 
 /*
@@ -181,8 +195,8 @@ int dem_reduction_degree(dem_ctx *c, double *mean_per_bed, double *oxygen_per_be
  * adjoint kernel back through it. The context's state is not changed. Synchronous.
  * grad may be NULL: then only the forward sweep runs and only J is written. The sub-step
  * is evaluated in FP64 whatever the context's precision. Errors: DEM_EINVAL for n_steps < 0
- * or ckpt_every < 1, and when a bed has DEM_RADIATION (radiation couples the parcels'
- * temperatures, and the differentiated map is per parcel); DEM_ENOMEM when the checkpoint and segment buffers (8 doubles per
+ * or ckpt_every < 1, and when a bed has DEM_RADIATION or DEM_CONDUCTION (they couple the
+ * parcels' temperatures, and the differentiated map is per parcel); DEM_ENOMEM when the checkpoint and segment buffers (8 doubles per
  * parcel per checkpoint and per sub-step of a segment) cannot be allocated. */
 int dem_adjoint(dem_ctx *c, int32_t n_steps, int32_t ckpt_every, double *J, double *grad);
 
@@ -224,8 +238,9 @@ int dem_get_contacts(dem_ctx *c, int32_t *count, int32_t *partner, double *xi);
 /* Per-parcel diagnostics of the last step (enable with dem_set_diagnostics before stepping),
  * DEM_NDIAG rows of n doubles (host), parcel-index order:
  * Fc(3) Tc(3) Fd(3) K Qconv Qr Qrm xidot(3) mdot(4) F_film A(3) B(3) Sh Nu Re ncontact cell
- * T_se Q_rad (the last two are 0 in beds without DEM_RADIATION) */
-enum { DEM_NDIAG = 34 };
+ * T_se Q_rad Q_cond (T_se and Q_rad are 0 in beds without DEM_RADIATION, Q_cond in beds
+ * without DEM_CONDUCTION) */
+enum { DEM_NDIAG = 35 };
 int dem_set_diagnostics(dem_ctx *c, int32_t on);
 int dem_get_diag(dem_ctx *c, double *out_host);
 

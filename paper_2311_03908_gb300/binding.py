@@ -18,7 +18,7 @@ DEM_OK, DEM_EINVAL, DEM_ENOMEM, DEM_ECUDA, DEM_ECAPACITY, DEM_ENONFINITE, DEM_ET
     0, -1, -2, -3, -4, -5, -6, -7, -8
 DEM_PREC_FP64, DEM_PREC_SPLIT, DEM_PREC_SPLIT_KAHAN = 0, 1, 2
 DEM_MAX_CONTACTS = 24
-DEM_NSTATE, DEM_NGAS, DEM_NDEP, DEM_NDIAG = 20, 6, 14, 34
+DEM_NSTATE, DEM_NGAS, DEM_NDEP, DEM_NDIAG = 20, 6, 14, 35
 DEM_NOALLOC_MAX_PARCELS = 8388608
 PRECISIONS = {"fp64": DEM_PREC_FP64, "split": DEM_PREC_SPLIT, "split_kahan": DEM_PREC_SPLIT_KAHAN}
 DEM_NTUNE = 9
@@ -29,7 +29,7 @@ STATE_ROWS = ["x", "y", "z", "vx", "vy", "vz", "wx", "wy", "wz", "T", "m_h", "m_
               "ax", "ay", "az", "alx", "aly", "alz"]
 DIAG_ROWS = (["Fcx", "Fcy", "Fcz", "Tcx", "Tcy", "Tcz", "Fdx", "Fdy", "Fdz", "K", "Qconv", "Qr", "Qrm",
               "xidot0", "xidot1", "xidot2", "mdot0", "mdot1", "mdot2", "mdot3", "F_film", "A0", "A1",
-              "A2", "B0", "B1", "B2", "Sh", "Nu", "Re", "ncontact", "cell", "Tse", "Qrad"])
+              "A2", "B0", "B1", "B2", "Sh", "Nu", "Re", "ncontact", "cell", "Tse", "Qrad", "Qcond"])
 SOURCE_ROWS = ["Vs", "SH2", "SH2O", "K", "Kvx", "Kvy", "Kvz", "hA", "hAT", "Qrm", "Qr", "EQ", "ES", "count"]
 
 
@@ -47,6 +47,7 @@ class DemBedConfig(C.Structure):
         ("sphericity", C.c_double * 2), ("xi0", C.c_double * 2), ("pore_d_cm", C.c_double * 2),
         ("rho_true", C.c_double * 4), ("dpdz", C.c_double), ("eps_min", C.c_double),
         ("flags", C.c_uint32), ("emissivity", C.c_double),
+        ("lambda_p", C.c_double * 2), ("lambda_wall", C.c_double),
     ]
 
 
@@ -145,6 +146,8 @@ def bed_struct(cfg) -> DemBedConfig:
     s.rho_true[:] = list(c["rho_true"])
     s.dpdz, s.eps_min, s.flags = c["dpdz"], c["eps_min"], int(c["flags"])
     s.emissivity = c["emissivity"]
+    s.lambda_p[:] = list(c["lambda_p"])
+    s.lambda_wall = c["lambda_wall"]
     return s
 
 

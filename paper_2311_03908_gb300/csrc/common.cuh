@@ -51,7 +51,8 @@ static_assert((int)SR_N == (int)DEM_NDEP, "source rows");
 // diagnostics rows (same order as documented in dem.h)
 enum : int {
   DG_FC = 0, DG_TC = 3, DG_FD = 6, DG_K = 9, DG_QCONV, DG_QR, DG_QRM, DG_XIDOT = 13, DG_MDOT = 16,
-  DG_FFILM = 20, DG_A = 21, DG_B = 24, DG_SH = 27, DG_NU, DG_RE, DG_NCONTACT, DG_CELL, DG_TSE, DG_QRAD, DG_N
+  DG_FFILM = 20, DG_A = 21, DG_B = 24, DG_SH = 27, DG_NU, DG_RE, DG_NCONTACT, DG_CELL, DG_TSE, DG_QRAD,
+  DG_QCOND, DG_N
 };
 static_assert((int)DG_N == (int)DEM_NDIAG, "diag rows");
 
@@ -92,6 +93,11 @@ template <class R> struct BedP {
   R reach_max;                  // largest parcel radius of the bed (CGP), m
   R skin, half_skin2;           // neighbour-list skin (m) and (skin / 2)^2
   R rad_c;                      // k^3 sigma eta_p pi: eqs (3-16) and (3-51) without d_p^2 and the temperatures
+  // contact conduction (eqs (3-14)..(3-15-2) with the scaling of eqs (3-46), (3-48)..(3-48-2)):
+  R cond_pp;                    // 4 k^(3/4) sqrt(f(e) / f(e_CGP)): eq (3-46) times the 4 of eq (3-14)
+  R cond_pf;                    // 2 pi k^2: eq (3-48) times the 2 pi of eq (3-15)
+  R lam_e[2][2], lam_ew[2];     // series conductances lambda_a lambda_b / (lambda_a + lambda_b), and with the wall
+  R lmin;                       // smallest conducting gap: 1.013 / p0 cm (Sec. 2.3), m
   unsigned flags;
   int ncouple, wall;
 };
@@ -273,6 +279,46 @@ template <class R> __device__ __forceinline__ R gunn(R eps, R re02, R re07, R c1
 // F_d = (beta / eps_p) V_p (u_g - v_p), the form of eq (3-5) with eps_p cancelled. The
 // inertial Ergun term carries eps_p (Gidaspow's correlation, which eq (3-5-1) cites, and
 // Ergun's fixed-bed pressure drop), so it is 1.75 rho |u - v| / (d psi) after the division.
+// Contact conduction of a parcel pair (radii Ra, Rb, centre distance d, overlap
+// delta = Ra + Rb - d > 0), into the parcel at temperature Ta from the one at Tb: the
+// constriction term of eq (3-14) with the radius R_c of the circle in which the spheres
+// meet, and the fluid lens of eq (3-15) over the smaller sphere's disk down to the gap lmin,
+// both scaled by eqs (3-46), (3-48). The lens integral is taken in closed form: with
+// v = d - L (L the gap between the surfaces) the printed integrand R dR / L becomes the
+// rational (v^4 - D^2) / (4 v^3 (d - v)) dv, D = Rb^2 - Ra^2 (Ra the smaller radius), over
+// v from sqrt(D) (the rim of the smaller sphere) to d - lmin.
+template <class R>
+__device__ __forceinline__ R lens_pair(R Ra, R Rb, R d, R lmin) {
+  const R a = fmin(Ra, Rb), b = fmax(Ra, Rb);
+  const R D = (b - a) * (b + a);
+  const R v0 = sqrt(D), v1 = d - lmin;
+  const R top = d - v0;                      // the gap at the rim of the smaller sphere
+  if (!(top > lmin)) return (R)0;
+  const R lg = log(top / lmin);              // ln((d - v0) / (d - v1))
+  R I = d * lg - (v1 - v0);
+  if (D > (R)0) {
+    const R id = (R)1 / d, iv0 = (R)1 / v0, iv1 = (R)1 / v1;
+    I -= D * D * (id * id * id * (log(v1 / v0) + lg) + id * id * (iv0 - iv1) +
+                  (R)0.5 * id * (iv0 * iv0 - iv1 * iv1));
+  }
+  return (R)0.25 * I;
+}
+template <class R>
+__device__ __forceinline__ R conduction_pair(const BedP<R> &B, R Ra, R Rb, R d, R delta, R Ta, R Tb, R lam_e,
+                                             R lam_g) {
+  const R Rc = sqrt(fmax(delta * (d + Ra + Rb) * ((d + Ra) - Rb) * ((d - Ra) + Rb), (R)0)) / ((R)2 * d);
+  return (B.cond_pp * Rc * lam_e + B.cond_pf * lam_g * lens_pair<R>(Ra, Rb, d, B.lmin)) * (Tb - Ta);
+}
+// the same with a wall at distance h = Rp - delta (plane, cone or rim; delta taken in FP64 by
+// the caller): R_c of the sphere's cut by the wall's tangent plane, the lens over the whole sphere's disk in closed form,
+// h ln(h / lmin) - (h - lmin) (eqs (3-15-1), (3-15-2), (3-48-1), (3-48-2))
+template <class R>
+__device__ __forceinline__ R conduction_wall(const BedP<R> &B, R Rp, R h, R delta, R Ta, R lam_ew, R lam_g) {
+  const R Rc = sqrt(fmax(delta * ((R)2 * Rp - delta), (R)0));
+  const R I = h > B.lmin ? h * log(h / B.lmin) - (h - B.lmin) : (R)0;
+  return (B.cond_pp * Rc * lam_ew + B.cond_pf * lam_g * I) * (B.T_in - Ta);
+}
+
 template <class R>
 __device__ __forceinline__ R beta_over_epsp(const BedP<R> &B, int ore, R d, const Gas<R> &g, R slip, R Re) {
   const R eps = g.eps, ep = (R)1 - eps;

@@ -85,6 +85,8 @@ struct dem_ctx {
   char *tsrt = nullptr;            // FP64 temperatures in sorted order for the radiation kernel
   float4 *xr = nullptr;            // local coordinates and temperature in sorted order (radiation)
   bool any_rad = false;            // some bed has DEM_RADIATION: the radiation kernel runs
+  bool any_cond = false;           // some bed has DEM_CONDUCTION
+  char *qc = nullptr;              // contact conduction heat of each parcel in contact (form's type)
   std::map<std::tuple<int, int, int>, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;
   std::map<std::tuple<int, int, int>, long long> graph_launches;
   cudaStream_t gst = nullptr;     // private stream used to capture graphs

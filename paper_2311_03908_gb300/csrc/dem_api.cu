@@ -235,6 +235,10 @@ int validate_bed(const dem_bed_config &b) {
   for (int r = 0; r < 3; ++r) if (!(b.k0[r] >= 0 && b.Ea[r] >= 0)) return DEM_EINVAL;
   if (b.wall_kind != DEM_WALL_FLAT && b.wall_kind != DEM_WALL_CONE) return DEM_EINVAL;
   if ((b.flags & DEM_RADIATION) && !(b.emissivity >= 0 && b.emissivity <= 1)) return DEM_EINVAL;
+  if ((b.flags & DEM_CONDUCTION) &&
+      !(b.lambda_p[0] > 0 && b.lambda_p[1] > 0 && b.lambda_wall > 0 && std::isfinite(b.lambda_p[0]) &&
+        std::isfinite(b.lambda_p[1]) && std::isfinite(b.lambda_wall)))
+    return DEM_EINVAL;
   if (b.wall_kind == DEM_WALL_CONE &&
       !(b.cone_half_angle > 0 && b.cone_half_angle < 1.5707963 && b.cone_height > 0 && b.hole_pitch > 0 &&
         b.hole_d > 0 && b.hole_d < b.hole_pitch && b.plate_z > 0 && b.plate_z < b.bed_H))
@@ -310,6 +314,27 @@ BedP<R> derive_params(const dem_bed_config &b, const DevBed &G) {
   P.pf_margin = (R)1e-8;
   P.rad_c = (b.flags & DEM_RADIATION)
                 ? (R)(b.cg_ratio * b.cg_ratio * b.cg_ratio * kSigmaSB * b.emissivity * kPI) : (R)0;
+  if (b.flags & DEM_CONDUCTION) {
+    // f(e) of eq (3-43): the maximum overlap of a damped linear collision in units of
+    // v / omega_0, exp(-zeta arccos(zeta) / sqrt(1 - zeta^2)) with zeta of eq (3-44); e_CGP
+    // of eq (3-45) clamped at 0, where f is exp(-1) (critical damping)
+    auto f_of = [](double e) {
+      if (!(e > 0.0)) return std::exp(-1.0);
+      if (e >= 1.0) return 1.0;
+      const double l = std::log(e), z = -l / std::sqrt(kPI * kPI + l * l);
+      return std::exp(-z * std::acos(z) / std::sqrt(1.0 - z * z));
+    };
+    const double k = b.cg_ratio, e = b.restitution;
+    const double ecg2 = 1.0 + k * (e * e - 1.0);
+    const double ecg = ecg2 > 0.0 ? std::sqrt(ecg2) : 0.0;
+    P.cond_pp = (R)(4.0 * std::pow(k, 0.75) * std::sqrt(f_of(e) / f_of(ecg)));
+    P.cond_pf = (R)(2.0 * kPI * k * k);
+    for (int o = 0; o < 2; ++o) {
+      for (int q = 0; q < 2; ++q) P.lam_e[o][q] = (R)(b.lambda_p[o] * b.lambda_p[q] / (b.lambda_p[o] + b.lambda_p[q]));
+      P.lam_ew[o] = (R)(b.lambda_p[o] * b.lambda_wall / (b.lambda_p[o] + b.lambda_wall));
+    }
+    P.lmin = (R)(1.013e-2 / b.p0);
+  }
   P.flags = b.flags;
   P.ncouple = b.coupling_interval;
   P.wall = b.wall_kind;
@@ -373,6 +398,7 @@ void layout(dem_ctx *c, Bump &m) {
   c->qrad = m.take<char>(Nr, R);
   c->tsrt = m.take<char>(c->rsize == sizeof(double) ? Nr : 0, R);   // FP64 form only
   c->xr = m.take<float4>(Nr);
+  c->qc = m.take<char>(c->any_cond ? N : 0, R);   // conduction heat of parcels in contact
   c->corner = m.take<double>(c->hcorner.size());
   c->cornerp = m.take<float2>(c->hcornerp.size());
   for (int q = 0; q < 3; ++q) { c->F[q] = m.take<char>(N, R); c->Tq[q] = m.take<char>(N, R); }
@@ -550,7 +576,10 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
   c->rsize = precision == DEM_PREC_FP64 ? sizeof(double) : sizeof(float);
   c->st = (cudaStream_t)cuda_stream;
   c->cfg.assign(beds, beds + n_beds);
-  for (int b = 0; b < n_beds; ++b) c->any_rad = c->any_rad || (beds[b].flags & DEM_RADIATION) != 0;
+  for (int b = 0; b < n_beds; ++b) {
+    c->any_rad = c->any_rad || (beds[b].flags & DEM_RADIATION) != 0;
+    c->any_cond = c->any_cond || (beds[b].flags & DEM_CONDUCTION) != 0;
+  }
   // per-bed constants and grid offsets; the gas cells are the cell list of the contact
   // search, so no parcel may be wider than a cell edge
   long long coff = 0, pacc = 0;
@@ -1148,7 +1177,7 @@ int dem_autotune(dem_ctx *c, int32_t n_steps) {
 
 int dem_adjoint(dem_ctx *c, int32_t n_steps, int32_t ckpt_every, double *J, double *grad) {
   if (!c || !J || n_steps < 0 || ckpt_every < 1) return DEM_EINVAL;
-  if (c->any_rad) return DEM_EINVAL;   // radiation couples the parcels; the map is per parcel
+  if (c->any_rad || c->any_cond) return DEM_EINVAL;   // radiation and conduction couple the parcels; the map is per parcel
   int s = sync_all(c);
   if (s != DEM_OK) return s;
   return DEM_DISPATCH(c, run_adjoint, c, n_steps, ckpt_every, J, grad);

@@ -81,6 +81,7 @@ template <class P> struct StepView {
   float4 *xr;                   // radiation: local coordinates in sorted order, w = T (FP32 forms)
   R *tsrt;                      // radiation, FP64 form: temperatures in sorted order
   int rad;                      // some bed radiates: k_ranges writes the sorted copies every step
+  R *qc;                        // contact conduction heat of each parcel in contact (conducting beds)
 };
 
 // total layer mass of parcel i in the form's type (the same sum everywhere it is needed)
@@ -670,9 +671,10 @@ __device__ __forceinline__ void pair_contact(const StepView<P> &V, int i, int j,
                                              const BedP<typename P::R> &bp, const float4 &me, float hx, float hy,
                                              float hz, const double *xi_d, double ri_d, typename P::R ri,
                                              typename P::R mi, const typename P::R vi[3], const typename P::R wi[3],
-                                             const HistIn &hin, typename P::R Fi[3], typename P::R Ti[3], int &cout) {
+                                             const HistIn &hin, typename P::R Fi[3], typename P::R Ti[3], int &cout,
+                                             const typename P::R cth[3], typename P::R &Qc) {
   using R = typename P::R;
-  R nrm[3], delta;
+  R nrm[3], delta, dist;
   double rj_d = 0;
   if constexpr (P::exact) {
     const double dxd = V.A.x[j] - xi_d[0], dyd = V.A.y[j] - xi_d[1], dzd = V.A.z[j] - xi_d[2];
@@ -683,6 +685,7 @@ __device__ __forceinline__ void pair_contact(const StepView<P> &V, int i, int j,
     const double dd = sqrt(d2);
     nrm[0] = (R)(dxd / dd); nrm[1] = (R)(dyd / dd); nrm[2] = (R)(dzd / dd);
     delta = (R)(rs - dd);
+    dist = (R)dd;
   } else {
     const int cdx = code % 3 - 1, cdy = (code / 3) % 3 - 1, cdz = code / 9 - 1;
     const float4 o = __ldg(V.xl + j);
@@ -693,8 +696,16 @@ __device__ __forceinline__ void pair_contact(const StepView<P> &V, int i, int j,
     const float inv = 1.0f / df;
     nrm[0] = (R)(ex * inv); nrm[1] = (R)(ey * inv); nrm[2] = (R)(ez * inv);
     delta = (R)((rsf * rsf - d2f) / (rsf + df));
+    dist = (R)df;
   }
   const R rj = P::exact ? (R)rj_d : (R)__ldg(&V.xl[j].w);
+  if (bp.flags & DEM_CONDUCTION) {
+    // cth: own temperature, own ore, own cell's gas conductivity
+    const int orej = V.A.meta[j] & 255;
+    const R lamg_j = V.gp[(size_t)V.keyp[j] * GP_STRIDE + GP_LAM];
+    Qc += conduction_pair<R>(bp, ri, rj, dist, delta, cth[0], V.A.T[j], bp.lam_e[(int)cth[1]][orej],
+                             (R)0.5 * (cth[2] + lamg_j));
+  }
   const R mj = parcel_mass<P>(V.A, j);
   const R mstar = mi * mj / (mi + mj);
   const R ws[3] = {ri * wi[0] + rj * V.A.w[0][j], ri * wi[1] + rj * V.A.w[1][j], ri * wi[2] + rj * V.A.w[2][j]};
@@ -779,13 +790,21 @@ __device__ __forceinline__ bool contact_screen(const StepView<P> &V, int i, unsi
 // reach). Writes the parcel's new contact history; returns its number of contacts.
 template <class P>
 __device__ __forceinline__ int contact_forces(const StepView<P> &V, int i, unsigned hits, typename P::R Fi[3],
-                                              typename P::R Ti[3]) {
+                                              typename P::R Ti[3], typename P::R &Qc) {
   using R = typename P::R;
   const int meta = V.A.meta[i];
   const DevBed &B = V.beds[meta >> 8];
   const BedP<R> &bp = V.bp[meta >> 8];
 #pragma unroll
   for (int q = 0; q < 3; ++q) { Fi[q] = 0; Ti[q] = 0; }
+  Qc = 0;
+  // contact conduction (eqs (3-14)..(3-15-2)): own temperature, ore and cell's gas conductivity
+  R cth[3] = {0, 0, 0};
+  if (bp.flags & DEM_CONDUCTION) {
+    cth[0] = V.A.T[i];
+    cth[1] = (R)(meta & 255);
+    cth[2] = V.gp[(size_t)V.keyp[i] * GP_STRIDE + GP_LAM];
+  }
   int cout = 0;
   HistIn hin;
   hin.cin = V.H.cnt[i];
@@ -810,7 +829,7 @@ __device__ __forceinline__ int contact_forces(const StepView<P> &V, int i, unsig
   const R ri = P::exact ? (R)ri_d : (R)me.w;
   for (int h = 0; h < nsearch; ++h)
     pair_contact<P>(V, i, V.plist[h * cap + i], V.pcode[h * cap + i], B, bp, me, hx, hy, hz, xi_d, ri_d, ri, mi,
-                    vi, wi, hin, Fi, Ti, cout);
+                    vi, wi, hin, Fi, Ti, cout, cth, Qc);
   while (hits) {   // list order
     const int k = __ffs(hits) - 1;
     hits &= hits - 1u;
@@ -818,7 +837,7 @@ __device__ __forceinline__ int contact_forces(const StepView<P> &V, int i, unsig
     int dx, dy, dz;
     key_offset(B, key, V.keyp[j], dx, dy, dz);
     pair_contact<P>(V, i, j, (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1), B, bp, me, hx, hy, hz, xi_d, ri_d, ri, mi,
-                    vi, wi, hin, Fi, Ti, cout);
+                    vi, wi, hin, Fi, Ti, cout, cth, Qc);
   }
   // walls: the FP32 pre-screen again, FP64 distances for the primitives within reach
   if (!(bp.flags & DEM_NO_CONTACTS) && wall_near<P>(V, B, bp, key, me)) {
@@ -837,6 +856,8 @@ __device__ __forceinline__ int contact_forces(const StepView<P> &V, int i, unsig
       vrel[1] = vi[1] + (wr[2] * nrm[0] - wr[0] * nrm[2]);
       vrel[2] = vi[2] + (wr[0] * nrm[1] - wr[1] * nrm[0]);
       add_contact<P>(V, i, hin, -1 - p, bp, mi, ri, nrm, delta, vrel, wi, Fi, Ti, cout);
+      if (bp.flags & DEM_CONDUCTION)
+        Qc += conduction_wall<R>(bp, (R)rid, (R)dist[p], delta, cth[0], bp.lam_ew[(int)cth[1]], cth[2]);
     }
   }
   V.Hn.cnt[i] = (unsigned char)cout;
@@ -879,10 +900,11 @@ __global__ void k_contact_forces(StepView<P> V) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
     const uint2 w = V.work[t];
     const int i = (int)w.x;
-    R F[3], Tq[3];
-    if (contact_forces<P>(V, i, w.y, F, Tq) == 0) continue;
+    R F[3], Tq[3], Qc;
+    if (contact_forces<P>(V, i, w.y, F, Tq, Qc) == 0) continue;
 #pragma unroll
     for (int q = 0; q < 3; ++q) { V.F[q][i] = F[q]; V.Tq[q][i] = Tq[q]; }
+    if (V.bp[V.A.meta[i] >> 8].flags & DEM_CONDUCTION) V.qc[i] = Qc;
   }
 }
 
@@ -1020,13 +1042,15 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
   for (int q = 0; q < 4; ++q) m[q] = mass_r<P>(V.A.m[q], i);
   const R wv[3] = {V.A.w[0][i], V.A.w[1][i], V.A.w[2][i]};
   R F[3] = {0, 0, 0}, Tq[3] = {0, 0, 0};
-  if (V.Hn.cnt[i] != 0) {   // the contact kernel wrote them only for parcels in contact
+  const bool touching = V.Hn.cnt[i] != 0;
+  if (touching) {   // the contact kernel wrote them only for parcels in contact
 #pragma unroll
     for (int q = 0; q < 3; ++q) { F[q] = V.F[q][i]; Tq[q] = V.Tq[q][i]; }
   }
   const int ore = meta & 255;
   const BedP<R> &bp = V.bp[meta >> 8];
   const unsigned fl = bp.flags;
+  const R Qcond = (touching && (fl & DEM_CONDUCTION)) ? V.qc[i] : (R)0;   // contact conduction, this step
   const size_t nc = (size_t)V.ncells;
   Gas<R> g;
   R gv[GP_STRIDE];   // the cell's property record, in vector loads
@@ -1089,8 +1113,8 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
   for (int q = 0; q < 4; ++q) cpp += m[q] * inv_mp * cp_over_R<R>(3 + q, Tp) * t.RMz[q];
   R Qrad = 0;
   if constexpr (RAD) Qrad = (fl & DEM_RADIATION) ? V.qrad[i] : (R)0;   // k_radiation, this step
-  const R Tn = RAD ? Tp + fdiv<R>(bp.dt * (Qconv + kn.Qr + kn.Qrm + Qrad), mp * cpp)
-                   : Tp + fdiv<R>(bp.dt * (Qconv + kn.Qr + kn.Qrm), mp * cpp);
+  const R Tn = RAD ? Tp + fdiv<R>(bp.dt * (Qconv + kn.Qr + kn.Qrm + Qrad + Qcond), mp * cpp)
+                   : Tp + fdiv<R>(bp.dt * (Qconv + kn.Qr + kn.Qrm + Qcond), mp * cpp);
   V.A.T[i] = Tn;
   if (cpl) {
 #pragma unroll
@@ -1136,6 +1160,7 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
     dg[DG_RE * cp + i] = (double)Re;
     dg[DG_CELL * cp + i] = (double)(c - V.beds[meta >> 8].cell_off);
     dg[DG_QRAD * cp + i] = (double)Qrad;
+    dg[DG_QCOND * cp + i] = (double)Qcond;
     if (!RAD || !(fl & DEM_RADIATION)) dg[DG_TSE * cp + i] = 0.0;
   }
 }

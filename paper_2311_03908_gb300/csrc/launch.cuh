@@ -85,6 +85,7 @@ StepView<P> make_view(dem_ctx *c, bool for_step) {
   V.tsrt = (R *)c->tsrt;
   V.xr = c->xr;
   V.rad = c->any_rad ? 1 : 0;
+  V.qc = (R *)c->qc;
   return V;
 }
 
