@@ -60,6 +60,8 @@ def parse():
                     "step with radiation switched on")
     ap.add_argument("--radiation", action="store_true", help="switch on the particle radiation of "
                     "eqs (3-16), (3-17), (3-51) in every bed (a widening of the step; off by default)")
+    ap.add_argument("--conduction", action="store_true", help="switch on the contact heat conduction of "
+                    "eqs (3-14)..(3-15-2) in every bed (off by default)")
     ap.add_argument("--tuning", default="", help="fixed launch configuration instead of the autotuner, "
                     "e.g. neighbour_lists=1,bs_key=64,skin_permille=50 (profiler runs repeat a plain run's)")
     ap.add_argument("--no-dense-leg", action="store_true", help="skip the contact-dominated 2M bed")
@@ -69,7 +71,7 @@ def parse():
     return ap.parse_args()
 
 
-def make_workload(name: str, rank: int = 0, parcels: int = 0, radiation: bool = False):
+def make_workload(name: str, rank: int = 0, parcels: int = 0, radiation: bool = False, conduction: bool = False):
     from paper_2311_03908_gb300 import synth
     seed_shift = 7919 * rank
     kw = {"n": parcels} if parcels else {}
@@ -83,9 +85,8 @@ def make_workload(name: str, rank: int = 0, parcels: int = 0, radiation: bool = 
         bed = synth.config_batched_32(seed=2311039085 + seed_shift)
     else:
         raise ValueError(name)
-    if radiation:
-        for cfg in bed.beds:
-            cfg.flags |= synth.RADIATION
+    for cfg in bed.beds:
+        cfg.flags |= (synth.RADIATION if radiation else 0) | (synth.CONDUCTION if conduction else 0)
     return bed
 
 
@@ -330,15 +331,19 @@ def e2e_coupling(binding, stream, bed, ncouple, tuning, settle, steps):
             "d2h_bytes_per_step": int(out.numel() * 8 + len(bed.beds) * 16) / ncouple}
 
 
-def dense_leg(binding, stream, tuning, settle, steps, precision, parcels=0):
+def dense_leg(binding, stream, tuning, settle, steps, precision, parcels=0, conduction=False):
     """The 2M cone-and-plate bed as a jammed packing below minimum fluidisation: the
     contact-dominated regime of a settled bed (about 2.7 contacts per parcel), 50 untimed
     steps (neighbour lists built), then timed like the headline step; the mean number of
-    live contacts is read after the timed steps."""
+    live contacts is read after the timed steps. conduction: the same with the contact heat
+    conduction of eqs (3-14)..(3-15-2) switched on in the bed."""
     import torch
     from paper_2311_03908_gb300 import synth
     kw = {"n": parcels} if parcels else {}
     bed = synth.config_ibm_2m_dense(U_in=0.02, v_scale=0.01, **kw)
+    if conduction:
+        for c in bed.beds:
+            c.flags |= synth.CONDUCTION
     cx = binding.Context(bed, precision=precision, stream=stream.cuda_stream)
     cx.dem_step(settle)
     cx.dem_set_tuning(**tuning)
@@ -361,7 +366,8 @@ def dense_leg(binding, stream, tuning, settle, steps, precision, parcels=0):
     t = cx.dem_kernel_times()
     cx.dem_profile(False)
     cx.close()
-    return {"workload": f"ibm_2m_dense ({bed.n} parcels, jammed lattice, U_in 0.02 m/s)",
+    return {"workload": f"ibm_2m_dense ({bed.n} parcels, jammed lattice, U_in 0.02 m/s)"
+                        + (", contact conduction on" if conduction else ""),
             "ms_per_step": ms / steps, "value": bed.n * steps / (ms * 1e-3), "unit": UNIT, "steps": steps,
             "settle_steps": settle, "zbar_contacts": float(cnt.mean()), "fraction_in_contact": float((cnt > 0).mean()),
             "contact_kernels_ms": {k: v[1] / max(v[0], 1) for k, v in t.items()
@@ -441,7 +447,7 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    bed = make_workload(args.workload, 0, args.parcels, args.radiation)
+    bed = make_workload(args.workload, 0, args.parcels, args.radiation, args.conduction)
     import oracle
     n = min(args.cpu_sample, bed.n)
     sub = bed.subset(np.arange(n)) if n < bed.n else bed   # parcel indices are shuffled
@@ -481,7 +487,7 @@ def main():
     torch.cuda.set_device(local)
     from paper_2311_03908_gb300 import binding
     stream = torch.cuda.current_stream()
-    bed = make_workload(args.workload, rank, args.parcels, args.radiation)
+    bed = make_workload(args.workload, rank, args.parcels, args.radiation, args.conduction)
     ctx = binding.Context(bed, precision=args.precision, stream=stream.cuda_stream)
     n = bed.n
     if args.settle > 0:
@@ -574,7 +580,8 @@ def main():
             "vs_baseline": None, "dtype": {"fp64": "f64", "split": "f32+f64", "split_kahan": "f32"}[args.precision],
             "data": "synthetic",
             "config": {"workload": f"{args.workload} ({bed.n} parcels, {ncells} gas cells, {len(bed.beds)} bed(s))",
-                       "precision": args.precision, "radiation": bool(args.radiation), "stepping": f"CUDA graph of {G} step(s), replayed", "settle_steps": args.settle,
+                       "precision": args.precision, "radiation": bool(args.radiation),
+                       "conduction": bool(args.conduction), "stepping": f"CUDA graph of {G} step(s), replayed", "settle_steps": args.settle,
                        "l2": "inputs larger than L2 (parcel state and history ~ 1 GB)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "gpu_launches": total_launches, "clocks": ck,
@@ -646,6 +653,8 @@ def main():
     if not args.no_dense_leg:
         line["dense"] = dense_leg(binding, stream, tuning, 50, min(max(args.steps, 100), 200),
                                   args.precision, args.parcels)
+        line["dense_conduction"] = dense_leg(binding, stream, tuning, 50, min(max(args.steps, 100), 200),
+                                             args.precision, args.parcels, conduction=True)
     if rank == 0 and not args.no_batched_leg and not args.parcels:
         line["batched_32"] = batched_leg(binding, stream, args.settle, min(max(args.steps, 100), 200),
                                          args.precision)

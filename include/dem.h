@@ -200,6 +200,21 @@ int dem_reduction_degree(dem_ctx *c, double *mean_per_bed, double *oxygen_per_be
  * parcel per checkpoint and per sub-step of a segment) cannot be allocated. */
 int dem_adjoint(dem_ctx *c, int32_t n_steps, int32_t ckpt_every, double *J, double *grad);
 
+/* Observed reduction-degree curves and the gradient of a weighted sum of them, for fitting
+ * the kinetic parameters to measured curves as Sec. 5.1.1 and Sec. 5.2.1 do (there by
+ * hand): the frozen-position sub-step of dem_adjoint is run for n_steps; after obs_steps[k]
+ * sub-steps (1 <= obs_steps[0] < ... < obs_steps[n_obs-1] <= n_steps, n_obs <= DEM_MAX_OBS)
+ * J_obs[k * n_beds + b] (host) gets the mean over bed b's parcels of f_ov - f_ov(now)
+ * (eqs (2-15)..(2-19)). With grad (host, 6 doubles; needs weights, host n_obs x n_beds):
+ * the derivative of sum_k sum_b weights[k * n_beds + b] J_obs[k * n_beds + b] w.r.t. k0[0..2]
+ * and Ea[0..2] (eq (2-13)), by the same checkpointed reverse sweep (a least-squares fit's
+ * gradient is one call with weights 2 (J_obs - target), after a call without grad for J_obs).
+ * State unchanged; synchronous. Errors as dem_adjoint, and DEM_EINVAL for unordered or
+ * out-of-range observation steps, non-finite weights, or grad without weights. */
+#define DEM_MAX_OBS 4096
+int dem_adjoint_obs(dem_ctx *c, int32_t n_steps, int32_t ckpt_every, int32_t n_obs, const int32_t *obs_steps,
+                    const double *weights, double *J_obs, double *grad);
+
 /* Replace the kinetic parameters of every bed: the pre-exponential factors k0 (m/s) and
  * activation energies Ea (J/mol) of the interface rate constants k_r = k0 exp(-Ea / (R T_p))
  * of eq (2-13) for R1 (Fe2O3 -> Fe3O4), R2 (Fe3O4 -> FeO), R3 (FeO -> Fe) (Table 2 lists

@@ -89,6 +89,8 @@ def lib():
         L.orc_destroy.argtypes = [C.c_void_p]
         L.orc_adjoint.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_double, dp, dp]
         L.orc_adjoint.restype = C.c_int32
+        L.orc_adjoint_obs.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, ip, dp, dp, dp]
+        L.orc_adjoint_obs.restype = C.c_int32
         L.orc_gas_props.argtypes = [dp, C.c_double, dp, C.c_double, dp]
         L.orc_network.argtypes = [dp, dp, C.c_double, ip, C.c_double, dp, dp, dp, ip]
         L.orc_kinetics.argtypes = [dp, dp, C.c_double, C.c_double, C.c_int32, C.c_double, C.c_double,
@@ -254,6 +256,22 @@ class Oracle:
         if st != 0:
             raise ValueError("the adjoint map is per parcel: not defined with radiation switched on")
         return float(J[0]), g
+
+
+    def adjoint_obs(self, nsteps: int, obs_steps, weights=None, mode: int = 0):
+        """Bed means of f_ov - f_ov(now) after each of obs_steps sub-steps of the frozen map,
+        (n_obs, n_beds); mode 2 adds the dual-number gradient of sum(weights * J_obs)."""
+        steps = np.ascontiguousarray(obs_steps, dtype=np.int32)
+        nobs = int(steps.size)
+        Jo = np.zeros((nobs, self.nbeds))
+        g = np.zeros(6)
+        w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64).reshape(nobs, self.nbeds)
+        st = lib().orc_adjoint_obs(self.h, int(nsteps), int(mode), nobs, steps.ctypes.data_as(C.POINTER(C.c_int32)),
+                                   None if w is None else w.ctypes.data_as(C.POINTER(C.c_double)),
+                                   Jo.ctypes.data_as(C.POINTER(C.c_double)), g.ctypes.data_as(C.POINTER(C.c_double)))
+        if st != 0:
+            raise ValueError("the adjoint map is per parcel: not defined with radiation or conduction")
+        return Jo, (g if mode == 2 else None)
 
 
 def set_threads(n: int):

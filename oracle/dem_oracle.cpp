@@ -1128,9 +1128,13 @@ void step_once(Oracle &o) {
 
 // Frozen-position drag-heat-reaction sub-step used by the adjoint (positions, cells and
 // the gas field held at their current values; per-parcel state v, T_p, m_z).
+// With observations (nobs > 0): returns sum_k sum_i coef[k][bed i] (f_ov,i(obs[k]) - f_ov,i(0))
+// and writes the values f_ov,i(obs[k]) - f_ov,i(0) to rec[k][i]; otherwise the mean over all
+// parcels of f_ov(after nsteps) - f_ov(0).
 template <class S>
 S adjoint_J(const Oracle &o, const std::vector<GasProps> &gp, const std::vector<int64_t> &pcell,
-            int nsteps, const S k0s[3], const S Eas[3]) {
+            int nsteps, const S k0s[3], const S Eas[3], int nobs = 0, const int *obs = nullptr,
+            const double *coef = nullptr, double *rec = nullptr) {
   S total(0.0);
   const int n = o.n;
   std::vector<S> part(n);
@@ -1150,6 +1154,8 @@ S adjoint_J(const Oracle &o, const std::vector<GasProps> &gp, const std::vector<
     T = S(o.s[ORC_S_T][i]);
     for (int z = 0; z < 4; ++z) m[z] = S(o.s[ORC_S_M + z][i]);
     S f0 = fov_of(m, o.ore[i]);
+    S wsum(0.0);
+    int oi = 0;
     for (int st = 0; st < nsteps; ++st) {
       S sv[3] = {ug[0] - v[0], ug[1] - v[1], ug[2] - v[2]};
       S slip = sqrt(sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]);
@@ -1169,11 +1175,17 @@ S adjoint_J(const Oracle &o, const std::vector<GasProps> &gp, const std::vector<
       for (int q = 0; q < 3; ++q) v[q] = v[q] + dt * Kp * sv[q] / mp;
       for (int z = 0; z < 4; ++z) m[z] = smax(m[z] + kn.mdot[z] * dt, S(0.0));
       T = Tn;
+      if (oi < nobs && st + 1 == obs[oi]) {
+        const S df = fov_of(m, o.ore[i]) - f0;
+        rec[(size_t)oi * n + i] = val(df);
+        wsum = wsum + coef[(size_t)oi * o.nb + o.bed[i]] * df;
+        ++oi;
+      }
     }
-    part[i] = fov_of(m, o.ore[i]) - f0;
+    part[i] = nobs > 0 ? wsum : fov_of(m, o.ore[i]) - f0;
   }
   for (int i = 0; i < n; ++i) total = total + part[i];
-  return total / (double)n;
+  return nobs > 0 ? total : total / (double)n;
 }
 
 }  // namespace
@@ -1182,6 +1194,55 @@ S adjoint_J(const Oracle &o, const std::vector<GasProps> &gp, const std::vector<
 // C API
 // =========================================================================================
 extern "C" {
+
+int32_t orc_adjoint_obs(void *h, int32_t nsteps, int32_t mode, int32_t nobs, const int32_t *obs_steps,
+                        const double *weights, double *J_obs, double *grad6) {
+  Oracle *o = (Oracle *)h;
+  for (int b = 0; b < o->nb; ++b)
+    if ((unsigned)ib(o->B(b), ORC_B_FLAGS) & (ORC_RADIATION | ORC_CONDUCTION)) return -1;
+  std::vector<GasProps> gp(o->ncell_total);
+  for (int b = 0; b < o->nb; ++b) {
+    const double *bd = o->B(b);
+    for (int64_t c = o->cell_off[b]; c < o->cell_off[b + 1]; ++c)
+      gp[c] = gas_props(o->gas[c * ORC_NG + ORC_G_T], &o->gas[c * ORC_NG + ORC_G_Y], bd[ORC_B_P0]);
+  }
+  std::vector<int64_t> pcell(o->n);
+  std::vector<int> cnt(o->nb, 0);
+  for (int i = 0; i < o->n; ++i) {
+    const double *bd = o->B(o->bed[i]);
+    Grid g = make_grid(bd);
+    pcell[i] = o->cell_off[o->bed[i]] + cell_of(g, o->s[0][i], o->s[1][i], o->s[2][i], nullptr);
+    cnt[o->bed[i]]++;
+  }
+  std::vector<int> obs(obs_steps, obs_steps + nobs);
+  std::vector<double> coef((size_t)nobs * o->nb, 0.0);   // weight over the bed's parcel count
+  for (int k = 0; k < nobs; ++k)
+    for (int b = 0; b < o->nb; ++b)
+      coef[(size_t)k * o->nb + b] = weights && cnt[b] ? weights[(size_t)k * o->nb + b] / cnt[b] : 0.0;
+  std::vector<double> rec((size_t)nobs * o->n, 0.0);
+  double th[6];
+  for (int r = 0; r < 3; ++r) { th[r] = o->B(0)[ORC_B_K0 + r]; th[3 + r] = o->B(0)[ORC_B_EA + r]; }
+  if (mode == 2) {
+    Dual k0s[3], Eas[3];
+    for (int r = 0; r < 3; ++r) {
+      k0s[r] = Dual(th[r]); k0s[r].d[r] = 1.0;
+      Eas[r] = Dual(th[3 + r]); Eas[r].d[3 + r] = 1.0;
+    }
+    Dual Jd = adjoint_J<Dual>(*o, gp, pcell, nsteps, k0s, Eas, nobs, obs.data(), coef.data(), rec.data());
+    for (int q = 0; q < 6; ++q) grad6[q] = Jd.d[q];
+  } else {
+    double k0s[3] = {th[0], th[1], th[2]}, Eas[3] = {th[3], th[4], th[5]};
+    adjoint_J<double>(*o, gp, pcell, nsteps, k0s, Eas, nobs, obs.data(), coef.data(), rec.data());
+  }
+  for (int k = 0; k < nobs; ++k)
+    for (int b = 0; b < o->nb; ++b) {
+      double sum = 0.0;
+      for (int i = 0; i < o->n; ++i)
+        if (o->bed[i] == b) sum += rec[(size_t)k * o->n + i];
+      J_obs[(size_t)k * o->nb + b] = cnt[b] ? sum / cnt[b] : 0.0;
+    }
+  return 0;
+}
 
 void orc_set_threads(int32_t nthreads) {
 #ifdef _OPENMP

@@ -107,6 +107,11 @@ void orc_destroy(void *h);
  * frozen-position drag-heat-reaction sub-step; mode 0 = J only, 1 = central finite
  * differences with relative step rel, 2 = forward-mode dual numbers. */
 int32_t orc_adjoint(void *h, int32_t nsteps, int32_t mode, double rel, double *J, double *grad6);
+/* the same map observed after obs_steps[k] sub-steps: J_obs[k * nbeds + b] = mean over bed b
+ * of f_ov - f_ov(now); mode 2 also writes the dual-number gradient of
+ * sum_k sum_b weights[k * nbeds + b] J_obs[k * nbeds + b] to grad6 (weights nullable: zero) */
+int32_t orc_adjoint_obs(void *h, int32_t nsteps, int32_t mode, int32_t nobs, const int32_t *obs_steps,
+                        const double *weights, double *J_obs, double *grad6);
 
 /* ---- single-call pieces for the pins ---- */
 void orc_gas_props(const double *bed, double Tg, const double *Y, double p, double *out);

@@ -86,6 +86,7 @@ def lib() -> C.CDLL:
         "dem_sync": (C.c_int, [vp]),
         "dem_reduction_degree": (C.c_int, [vp, dp, dp, vp]),
         "dem_adjoint": (C.c_int, [vp, C.c_int32, C.c_int32, dp, dp]),
+        "dem_adjoint_obs": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, ip, dp, dp, dp]),
         "dem_set_kinetics": (C.c_int, [vp, dp, dp]),
         "dem_get_state": (C.c_int, [vp, dp]),
         "dem_num_cells": (C.c_int64, [vp]),
@@ -243,6 +244,23 @@ class Context:
         _check(lib().dem_adjoint(self.h, int(nsteps), int(ckpt_every), J.ctypes.data_as(C.POINTER(C.c_double)), gp),
                "dem_adjoint")
         return float(J[0]), (g if want_grad else None)
+
+    def dem_adjoint_obs(self, nsteps, obs_steps, weights=None, ckpt_every=100):
+        """Observed bed reduction-degree curves J_obs (n_obs, n_beds) after obs_steps
+        sub-steps of the frozen-position map, and (with weights, an (n_obs, n_beds) array)
+        the gradient of sum(weights * J_obs) w.r.t. k0[3], Ea[3] (None without weights)."""
+        steps = np.ascontiguousarray(obs_steps, dtype=np.int32)
+        nobs = int(steps.size)
+        Jo = np.zeros((nobs, self.nbeds))
+        g = np.zeros(6) if weights is not None else None
+        w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64).reshape(nobs, self.nbeds)
+        _check(lib().dem_adjoint_obs(self.h, int(nsteps), int(ckpt_every), nobs,
+                                     steps.ctypes.data_as(C.POINTER(C.c_int32)),
+                                     None if w is None else w.ctypes.data_as(C.POINTER(C.c_double)),
+                                     Jo.ctypes.data_as(C.POINTER(C.c_double)),
+                                     None if g is None else g.ctypes.data_as(C.POINTER(C.c_double))),
+               "dem_adjoint_obs")
+        return Jo, g
 
     def dem_set_kinetics(self, k0, Ea):
         a = np.ascontiguousarray(k0, dtype=np.float64)

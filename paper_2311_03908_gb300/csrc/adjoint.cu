@@ -364,10 +364,27 @@ __device__ void load_par(const StepView<Pp> &V, const BedP<double> *bpd, int i, 
   for (int z = 0; z < 4; ++z) s[4 + z] = mass_d<Pp>(V.A.m[z], i);
 }
 
+// Observations of the reduction-degree curve (dem_adjoint_obs): after steps[k] sub-steps
+// every parcel's f_ov - f_ov(0) goes to f[k][i], and the differentiated quantity is
+// sum_k sum_i coef[k][bed of i] (f_ov,i(steps[k]) - f_ov,i(0)). nobs = 0: the plain J.
+struct Obs {
+  int nobs;
+  const int *steps;       // ascending, in [1, nsteps]
+  const double *coef;     // [nobs][nbeds]
+  double *f;              // [nobs][n]
+};
+
+__device__ __forceinline__ void add_dfov(const double *m, int ore, double c, double lam[8]) {
+  double d[4];
+  dfov_dm(m, ore, d);
+  for (int z = 0; z < 4; ++z) lam[4 + z] += c * d[z];
+}
+
 // grad == false: forward sweep only (J). partial: [grid][7] = J sum, then 6 gradient sums.
 template <class Pp>
 __global__ void __launch_bounds__(128) k_adjoint(StepView<Pp> V, const BedP<double> *bpd, int nsteps, int ckpt,
-                                                 Params6 th6, double *cks, double *seg, bool grad, double *partial) {
+                                                 Params6 th6, double *cks, double *seg, bool grad, double *partial,
+                                                 Obs ob) {
   __shared__ double sh[7][128];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -380,16 +397,22 @@ __global__ void __launch_bounds__(128) k_adjoint(StepView<Pp> V, const BedP<doub
     const double f0 = fov(s + 4, ore);
     Fwd F;
     const size_t n = (size_t)V.n;
+    const int bed = V.A.meta[i] >> 8;
+    int oi = 0;
     for (int st = 0; st < nsteps; ++st) {
       if (grad && st % ckpt == 0)
         for (int q = 0; q < 8; ++q) cks[((size_t)(st / ckpt) * 8 + q) * n + i] = s[q];
       fwd(P, s, th, F, sn);
       for (int q = 0; q < 8; ++q) s[q] = sn[q];
+      if (oi < ob.nobs && st + 1 == ob.steps[oi]) ob.f[(size_t)(oi++) * n + i] = fov(s + 4, ore) - f0;
     }
     acc[0] = fov(s + 4, ore) - f0;
     if (grad) {
       double lam[8] = {0, 0, 0, 0, 0, 0, 0, 0}, lout[8], g[6] = {0, 0, 0, 0, 0, 0};
-      dfov_dm(s + 4, ore, lam + 4);
+      // the seed at the end of the horizon: the plain J, or the observation taken there
+      oi = ob.nobs - 1;
+      if (ob.nobs == 0) dfov_dm(s + 4, ore, lam + 4);
+      else if (ob.steps[oi] == nsteps) add_dfov(s + 4, ore, ob.coef[(size_t)(oi--) * V.nbeds + bed], lam);
       const int nseg = (nsteps + ckpt - 1) / ckpt;
       for (int sg = nseg - 1; sg >= 0; --sg) {
         const int st0 = sg * ckpt, st1 = min(st0 + ckpt, nsteps);
@@ -405,6 +428,15 @@ __global__ void __launch_bounds__(128) k_adjoint(StepView<Pp> V, const BedP<doub
           for (int q = 0; q < 8; ++q) s[q] = sn[q];
         }
         for (int k = st1 - 1; k >= st0; --k) {
+          // an observation of the state after sub-step k (k + 1 < nsteps): the adjoint of
+          // that state takes its weight before the reverse of sub-step k
+          if (oi >= 0 && ob.steps[oi] == k + 1) {
+            const double *sk1 = k + 1 < st1 ? seg + (size_t)(k + 1 - st0) * kSegWords * n + i
+                                            : cks + (size_t)(sg + 1) * 8 * n + i;
+            double m1[4];
+            for (int z = 0; z < 4; ++z) m1[z] = sk1[(size_t)(4 + z) * n];
+            add_dfov(m1, ore, ob.coef[(size_t)(oi--) * V.nbeds + bed], lam);
+          }
           const double *slot = seg + (size_t)(k - st0) * kSegWords * n + i;
           for (int q = 0; q < 8; ++q) s[q] = slot[(size_t)q * n];
           unsigned long long *fw = reinterpret_cast<unsigned long long *>(&F);
@@ -430,12 +462,15 @@ __global__ void __launch_bounds__(128) k_adjoint(StepView<Pp> V, const BedP<doub
 }  // namespace
 
 template <class Pp>
-int run_adjoint(dem_ctx *c, int nsteps, int ckpt, double *J, double *grad) {
+int run_adjoint(dem_ctx *c, int nsteps, int ckpt, double *J, double *grad, int nobs, const int *obs_steps,
+                const double *weights, double *J_obs) {
   const bool want_grad = grad != nullptr;
   const int n = c->n;
   const int nseg = (nsteps + ckpt - 1) / ckpt;
   const int bs = 128, grid = (n + bs - 1) / bs;
-  const size_t need = sizeof(double) * ((want_grad ? ((size_t)nseg * 8 * n + (size_t)ckpt * kSegWords * n) : 0) + (size_t)grid * 7);
+  const size_t obs_words = nobs > 0 ? (size_t)nobs * n + (size_t)nobs * c->nbeds + (size_t)nobs + 1 : 0;
+  const size_t need = sizeof(double) * ((want_grad ? ((size_t)nseg * 8 * n + (size_t)ckpt * kSegWords * n) : 0) +
+                                        (size_t)grid * 7 + obs_words);
   if (c->adj_bytes < need) {
     if (c->adj) cudaFree(c->adj);
     c->adj = nullptr;
@@ -446,11 +481,32 @@ int run_adjoint(dem_ctx *c, int nsteps, int ckpt, double *J, double *grad) {
   double *cks = c->adj;
   double *seg = cks + (want_grad ? (size_t)nseg * 8 * n : 0);
   double *partial = seg + (want_grad ? (size_t)ckpt * kSegWords * n : 0);
+  Obs ob{0, nullptr, nullptr, nullptr};
+  std::vector<double> hcoef;
+  std::vector<int> hcount(c->nbeds, 0);
+  if (nobs > 0) {
+    // coefficients per (observation, bed): the weight over the bed's parcel count, so that
+    // the kernel's per-parcel seeds sum to the weighted bed means
+    for (int b = 0; b < c->nbeds; ++b) hcount[b] = c->hbeds[b].pend - c->hbeds[b].pstart;
+    hcoef.assign((size_t)nobs * c->nbeds, 0.0);
+    for (int k = 0; k < nobs; ++k)
+      for (int b = 0; b < c->nbeds; ++b)
+        hcoef[(size_t)k * c->nbeds + b] =
+            weights && hcount[b] > 0 ? weights[(size_t)k * c->nbeds + b] / hcount[b] : 0.0;
+    double *of = partial + (size_t)grid * 7;
+    double *oc = of + (size_t)nobs * n;
+    int *os = reinterpret_cast<int *>(oc + (size_t)nobs * c->nbeds);
+    if (cudaMemcpyAsync(oc, hcoef.data(), sizeof(double) * hcoef.size(), cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
+        cudaMemcpyAsync(os, obs_steps, sizeof(int) * nobs, cudaMemcpyHostToDevice, c->st) != cudaSuccess)
+      return DEM_ECUDA;
+    ob = Obs{nobs, os, oc, of};
+  }
   StepView<Pp> V = make_view<Pp>(c, false);
   Params6 th;
   for (int r = 0; r < 3; ++r) { th.v[r] = c->cfg[0].k0[r]; th.v[3 + r] = c->cfg[0].Ea[r]; }
-  k_adjoint<Pp><<<grid, bs, 0, c->st>>>(V, c->dbp_d, nsteps, ckpt, th, cks, seg, want_grad, partial);
+  k_adjoint<Pp><<<grid, bs, 0, c->st>>>(V, c->dbp_d, nsteps, ckpt, th, cks, seg, want_grad, partial, ob);
   if (cudaPeekAtLastError() != cudaSuccess) return DEM_ECUDA;
+
   std::vector<double> h((size_t)grid * 7);
   if (cudaMemcpyAsync(h.data(), partial, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
     return DEM_ECUDA;
@@ -458,14 +514,28 @@ int run_adjoint(dem_ctx *c, int nsteps, int ckpt, double *J, double *grad) {
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int b = 0; b < grid; ++b)
     for (int q = 0; q < 7; ++q) acc[q] += h[(size_t)b * 7 + q];
-  *J = acc[0] / n;
+  if (J) *J = acc[0] / n;
   if (want_grad)
-    for (int q = 0; q < 6; ++q) grad[q] = acc[1 + q] / n;
+    for (int q = 0; q < 6; ++q) grad[q] = nobs > 0 ? acc[1 + q] : acc[1 + q] / n;
+  if (nobs > 0) {
+    // the observed bed means: per-parcel values back to the host, summed bed by bed in
+    // storage order (each bed's parcels occupy a fixed storage range)
+    std::vector<double> hf((size_t)nobs * n);
+    if (cudaMemcpy(hf.data(), partial + (size_t)grid * 7, sizeof(double) * hf.size(), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      return DEM_ECUDA;
+    for (int k = 0; k < nobs; ++k)
+      for (int b = 0; b < c->nbeds; ++b) {
+        double sum = 0.0;
+        for (int i = c->hbeds[b].pstart; i < c->hbeds[b].pend; ++i) sum += hf[(size_t)k * n + i];
+        J_obs[(size_t)k * c->nbeds + b] = hcount[b] > 0 ? sum / hcount[b] : 0.0;
+      }
+  }
   return DEM_OK;
 }
 
-template int run_adjoint<PrecF64>(dem_ctx *, int, int, double *, double *);
-template int run_adjoint<PrecSplit>(dem_ctx *, int, int, double *, double *);
-template int run_adjoint<PrecKahan>(dem_ctx *, int, int, double *, double *);
+template int run_adjoint<PrecF64>(dem_ctx *, int, int, double *, double *, int, const int *, const double *, double *);
+template int run_adjoint<PrecSplit>(dem_ctx *, int, int, double *, double *, int, const int *, const double *, double *);
+template int run_adjoint<PrecKahan>(dem_ctx *, int, int, double *, double *, int, const int *, const double *, double *);
 
 }  // namespace dem

@@ -121,7 +121,9 @@ template <class P> int enqueue_scatter_diag(dem_ctx *c, double *out_dev);
 template <class P> int enqueue_scatter_hist(dem_ctx *c, int *cnt, int *partner, double *xi);
 template <class P> int enqueue_sources(dem_ctx *c);
 template <class P> int enqueue_gas_set(dem_ctx *c, const double *Y, const double *T, cudaStream_t st);
-template <class P> int run_adjoint(dem_ctx *c, int nsteps, int ckpt, double *J, double *grad);
+template <class P> int run_adjoint(dem_ctx *c, int nsteps, int ckpt, double *J, double *grad, int nobs = 0,
+                                   const int *obs_steps = nullptr, const double *weights = nullptr,
+                                   double *J_obs = nullptr);
 
 // event pair around one kernel when profiling is on (returns the start-event slot or -1)
 int prof_begin(dem_ctx *c, const char *name);

@@ -1183,4 +1183,21 @@ int dem_adjoint(dem_ctx *c, int32_t n_steps, int32_t ckpt_every, double *J, doub
   return DEM_DISPATCH(c, run_adjoint, c, n_steps, ckpt_every, J, grad);
 }
 
+int dem_adjoint_obs(dem_ctx *c, int32_t n_steps, int32_t ckpt_every, int32_t n_obs, const int32_t *obs_steps,
+                    const double *weights, double *J_obs, double *grad) {
+  if (!c || n_steps < 1 || ckpt_every < 1 || n_obs < 1 || n_obs > DEM_MAX_OBS || !obs_steps || !J_obs)
+    return DEM_EINVAL;
+  if (grad && !weights) return DEM_EINVAL;
+  for (int k = 0; k < n_obs; ++k)
+    if (obs_steps[k] < 1 || obs_steps[k] > n_steps || (k > 0 && obs_steps[k] <= obs_steps[k - 1])) return DEM_EINVAL;
+  if (weights)
+    for (int k = 0; k < n_obs * c->nbeds; ++k)
+      if (!std::isfinite(weights[k])) return DEM_EINVAL;
+  if (c->any_rad || c->any_cond) return DEM_EINVAL;
+  int s = sync_all(c);
+  if (s != DEM_OK) return s;
+  std::vector<int> st(obs_steps, obs_steps + n_obs);
+  return DEM_DISPATCH(c, run_adjoint, c, n_steps, ckpt_every, nullptr, grad, n_obs, st.data(), weights, J_obs);
+}
+
 }  // extern "C"

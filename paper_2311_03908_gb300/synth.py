@@ -431,3 +431,24 @@ def small_packed(seed: int = 7, n: int = 3000, sigma: float = 0.2, v_scale: floa
     z0 = cfg.plate_z if wall_kind == WALL_CONE else 0.0
     return packed_bed(seed, n, cfg, 100e-6, sigma, two_ores=two_ores, v_scale=v_scale, z0=z0,
                       T0=T0 - 30.0, name="small_packed")
+
+
+def config_calibration(seed: int = 2311039087, n_per_bed: int = 128, n_beds: int = 8, T_lo: float = 773.0,
+                       T_hi: float = 1073.0, dt: float = 5e-3, k0=TAKENAKA[0], Ea=TAKENAKA[1]) -> Bed:
+    """Beds at n_beds evenly spaced temperatures for fitting the kinetics to reduction-degree
+    curves over minutes (the frozen-position map of the adjoint; no contact is evaluated, so
+    the contact stiffness is only a placeholder that keeps the time step admissible): each
+    bed n_per_bed parcels of the mixed composition, packed, at its own temperature."""
+    cfgs, parts = [], []
+    for b in range(n_beds):
+        Tb = T_lo + (T_hi - T_lo) * b / max(1, n_beds - 1)
+        cfg = BedConfig(D=0.05, H=0.3, nx=10, ny=10, nz=60, dt=dt, cg_ratio=4.0, U_in=0.3, T_in=Tb,
+                        Y_in=(1.0, 0.0, 0.0), kn=1e-6, flags=NO_CONTACTS, k0=tuple(k0), Ea=tuple(Ea))
+        cfgs.append(cfg)
+        parts.append(packed_bed(seed + 97 * b, n_per_bed, cfg, 100e-6, 0.0, comp=COMP_MIXED,
+                                ore=ORE_HEMATITE, name=f"cal{b}"))
+    cat = lambda f: np.concatenate([getattr(p, f) for p in parts])
+    bedid = np.repeat(np.arange(n_beds, dtype=np.int32), n_per_bed)
+    return Bed(cfgs, cat("x"), cat("y"), cat("z"), cat("vx"), cat("vy"), cat("vz"), cat("d_real"), cat("T"),
+               np.concatenate([p.m0 for p in parts], axis=1), cat("ore"), bedid, "calibration",
+               dict(temperatures=[c.T_in for c in cfgs]))
