@@ -332,15 +332,16 @@ def e2e_coupling(binding, stream, bed, ncouple, tuning, settle, steps):
 
 
 def dense_leg(binding, stream, tuning, settle, steps, precision, parcels=0, conduction=False):
-    """The 2M cone-and-plate bed as a jammed packing below minimum fluidisation: the
-    contact-dominated regime of a settled bed (about 2.7 contacts per parcel), 50 untimed
-    steps (neighbour lists built), then timed like the headline step; the mean number of
-    live contacts is read after the timed steps. conduction: the same with the contact heat
-    conduction of eqs (3-14)..(3-15-2) switched on in the bed."""
+    """The 2M cone-and-plate bed as a jammed packing without gas flow (a fixed bed): the
+    contact-dominated regime of a settled bed. It starts with about 2.7 contacts per parcel;
+    the overlaps push the lattice apart and gravity packs it again over the untimed settle
+    steps; then it is timed like the headline step, and the mean number of live contacts is
+    read after the timed steps. conduction: the same with the contact heat conduction of
+    eqs (3-14)..(3-15-2) switched on in the bed."""
     import torch
     from paper_2311_03908_gb300 import synth
     kw = {"n": parcels} if parcels else {}
-    bed = synth.config_ibm_2m_dense(U_in=0.02, v_scale=0.01, **kw)
+    bed = synth.config_ibm_2m_dense(U_in=0.0, v_scale=0.01, **kw)
     if conduction:
         for c in bed.beds:
             c.flags |= synth.CONDUCTION
@@ -366,7 +367,7 @@ def dense_leg(binding, stream, tuning, settle, steps, precision, parcels=0, cond
     t = cx.dem_kernel_times()
     cx.dem_profile(False)
     cx.close()
-    return {"workload": f"ibm_2m_dense ({bed.n} parcels, jammed lattice, U_in 0.02 m/s)"
+    return {"workload": f"ibm_2m_dense ({bed.n} parcels, jammed lattice, no gas flow)"
                         + (", contact conduction on" if conduction else ""),
             "ms_per_step": ms / steps, "value": bed.n * steps / (ms * 1e-3), "unit": UNIT, "steps": steps,
             "settle_steps": settle, "zbar_contacts": float(cnt.mean()), "fraction_in_contact": float((cnt > 0).mean()),
@@ -651,9 +652,9 @@ def main():
                                       "dem_get_sources (pinned host, 14 doubles per cell) + dem_reduction_degree"}
         line["e2e_coupling"] = legs
     if not args.no_dense_leg:
-        line["dense"] = dense_leg(binding, stream, tuning, 50, min(max(args.steps, 100), 200),
+        line["dense"] = dense_leg(binding, stream, tuning, 2000, min(max(args.steps, 100), 200),
                                   args.precision, args.parcels)
-        line["dense_conduction"] = dense_leg(binding, stream, tuning, 50, min(max(args.steps, 100), 200),
+        line["dense_conduction"] = dense_leg(binding, stream, tuning, 2000, min(max(args.steps, 100), 200),
                                              args.precision, args.parcels, conduction=True)
     if rank == 0 and not args.no_batched_leg and not args.parcels:
         line["batched_32"] = batched_leg(binding, stream, args.settle, min(max(args.steps, 100), 200),

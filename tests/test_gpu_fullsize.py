@@ -6,8 +6,9 @@ sort's third pass at the first binning, the incremental re-sort with thousands o
 parcels, the grid-stride neighbour-list search over many waves of blocks, the reactor wall
 at full resolution, and the launch configuration the autotuner picks on this bed (64-thread
 blocks, 200 per mille skin, a re-store at every 8th list build). The FP64 form is held to
-the oracle after 1 and after 20 steps (pair sets bit-exact; states 1e-7; tangential
-displacements 1e-9; cell sources and gas 1e-9; bed reduction degree 1e-12), the split form
+the oracle after 1 and after 20 steps (pair sets bit-exact; states and tangential
+displacements 1e-7 of their vectors' lengths; cell sources and gas 1e-9; bed reduction
+degree 1e-12), the split form
 after 20 steps with its own tolerances. The same bed packed at touching pitch with random
 velocities (the contact-dominated regime) is held to the oracle after 10 steps.
 """
@@ -84,7 +85,11 @@ def bench_bed():
 def _check_fp64(g, r, what):
     assert np.array_equal(g["keys"], r["keys"]), what
     if r["xi"].size:
-        assert np.allclose(g["xi"], r["xi"], rtol=1e-9, atol=1e-18), what
+        # tangential displacements: each slot's vector to 1e-7 of its length (a component that
+        # is zero in exact arithmetic carries only round-off, as for the state's vectors)
+        norm = np.linalg.norm(r["xi"], axis=1)[:, None]
+        err = np.abs(g["xi"] - r["xi"]) / np.maximum(norm, 1e-30)
+        assert float(err.max()) < 1e-7, (what, float(err.max()))
     for row in range(binding.DEM_NSTATE):
         assert _rel_state(g["state"], r["state"], row) < 1e-7, (what, binding.STATE_ROWS[row])
     for col in range(binding.DEM_NDEP):
