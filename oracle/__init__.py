@@ -89,6 +89,8 @@ def lib():
         L.orc_destroy.argtypes = [C.c_void_p]
         L.orc_adjoint.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_double, dp, dp]
         L.orc_adjoint.restype = C.c_int32
+        L.orc_get_flow.argtypes = [C.c_void_p, dp]
+        L.orc_pseudo_turbulence.argtypes = [C.c_double] * 5 + [dp, dp, C.c_double, dp]
         L.orc_adjoint_obs.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, ip, dp, dp, dp]
         L.orc_adjoint_obs.restype = C.c_int32
         L.orc_gas_props.argtypes = [dp, C.c_double, dp, C.c_double, dp]
@@ -227,6 +229,12 @@ class Oracle:
     def gas(self) -> np.ndarray:
         out = np.zeros((self.ncells, NG))
         lib().orc_get_gas(self.h, out.ctypes.data_as(C.POINTER(C.c_double)))
+        return out
+
+    def flow(self) -> np.ndarray:
+        """Per gas cell: the cell-centre gas velocity (3) and the pressure relative to p0."""
+        out = np.zeros((self.ncells, 4))
+        lib().orc_get_flow(self.h, out.ctypes.data_as(C.POINTER(C.c_double)))
         return out
 
     def deposits(self) -> np.ndarray:
@@ -414,3 +422,13 @@ def conduction_wall(cfg, R, h, Ta, lam_a, lam_g):
     lib().orc_conduction_wall(bp, float(R), float(h), float(Ta), float(lam_a), float(lam_g),
                               out.ctypes.data_as(C.POINTER(C.c_double)))
     return dict(Qpp=out[0], Qpfp=out[1], Rc=out[2], I=out[3])
+
+
+def pseudo_turbulence(eps, rho, mu, lam, cp, ug, up, dp):
+    """Closures of eqs (3-28)..(3-37) for one cell: dict(Rpa, Rpe, apa, ape, s)."""
+    a, ap = _d(ug)
+    b, bp = _d(up)
+    out = np.zeros(8)
+    lib().orc_pseudo_turbulence(float(eps), float(rho), float(mu), float(lam), float(cp), ap, bp, float(dp),
+                                out.ctypes.data_as(C.POINTER(C.c_double)))
+    return dict(Rpa=out[0], Rpe=out[1], apa=out[2], ape=out[3], s=out[4:7].copy())

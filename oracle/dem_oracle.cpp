@@ -751,6 +751,9 @@ struct Oracle {
   std::vector<std::vector<int32_t>> members; // parcel ids of each bed
   int64_t step_no = 0;
   int64_t ncell_total = 0;
+  // solved gas phase (beds with ORC_GAS_SOLVER): face velocities on a staggered grid and the
+  // cell pressure relative to p0, per bed; eps of the previous coupling step per cell
+  std::vector<std::vector<double>> fu, fv, fw, pr;
   const double *B(int b) const { return beds.data() + (size_t)b * ORC_NB; }
 };
 
@@ -781,6 +784,410 @@ void deposit_volume_and_eps(Oracle &o) {
   std::fill(o.dep.begin(), o.dep.end(), 0.0);
 }
 
+// ---------------------------------------------------------------------------------------
+// Gas phase solver (Sec. 3.2, Sec. 4.1, Sec. 4.2), in beds with ORC_GAS_SOLVER, once per
+// coupling step with dt_CFD = n dt_DEM: continuity (eq (3-24)), momentum with the
+// semi-implicit drag of eq (4-2), energy with the semi-implicit H0 of eq (4-6), the reducing
+// gas with the semi-implicit C0, C1 of eq (4-9), the pseudo-turbulent stress and heat flux
+// of eqs (3-28)..(3-37). Readings (the paper solves the gas with OpenFOAM's schemes, Table 4):
+//   * staggered (MAC) grid on the gas cells: velocity components on the faces, scalars at
+//     the centres; explicit Euler in time, first-order upwind convection (Table 4 uses
+//     limitedLinear for velocity and species); an incremental pressure projection for the
+//     continuity constraint, in which the change of rho within a coupling step is neglected
+//     (d(eps rho)/dt = rho d eps/dt), solved by conjugate gradients;
+//   * momentum: convection in non-conservative form, viscous stress as div(eps mu grad u)
+//     (the transpose and dilatation parts of eq (3-33) dropped), the divergence of the
+//     pseudo-turbulent stress by its normal components, gravity, the drag of eq (4-2) with
+//     K_gp u_g implicit and K_gp u_p explicit, where K_gp = -(1/V) sum beta V_p/(1 - eps_g)
+//     and K_gp u_p = -(1/V) sum beta V_p/(1 - eps_g) v_p (the reaction to the parcels' drag);
+//   * boundaries: immersed-boundary cells and the box sides are no-slip walls; a face below a
+//     fluid cell whose lower neighbour is solid or outside takes the inlet gas at the
+//     superficial velocity U_in (eps u = U_in, Y_in, T_in); the top is an outlet at p0; walls
+//     hold the bed's inlet temperature (Table 3 lists them equal) and conduct heat to the gas;
+//   * the reducing gas H2 with eqs (4-8)..(4-11) as printed (x_H2 = M_g Y_H2 / (M_H2 X),
+//     M_g and X lagged), H2O produced at M_H2O / M_H2 times the H2 consumed (eq (2-25)), N2
+//     by closure; molecular diffusion with D_H2,m of eq (2-27) for every species;
+//   * the pseudo-turbulence closures with the cell's drag-weighted mean parcel velocity
+//     (u_p = K_gp u_p / K_gp), the volume-mean real diameter of its parcels and
+//     Re_m = eps rho |u_g - u_p| d_p / mu, evaluated as printed (Re_m capped at 100 and
+//     eps_p at 0.5, the upper ends of the closures' ranges); R and alpha_PT are rotated to
+//     the slip direction s: R = R_pe I + (R_pa - R_pe) s s^T (the Gram-Schmidt frame's
+//     perpendicular axes drop out), and only their diagonal enters the fluxes (cross-
+//     derivative terms dropped); D_PT = alpha_PT.
+// ---------------------------------------------------------------------------------------
+struct FlowGrid {
+  int nx, ny, nz;
+  double hx, hy, hz;
+  int64_t off;
+  const double *gas;
+  int64_t cidx(int i, int j, int k) const { return ((int64_t)k * ny + j) * nx + i; }
+  bool fluid(int i, int j, int k) const {
+    if (i < 0 || j < 0 || k < 0 || i >= nx || j >= ny || k >= nz) return false;
+    return gas[(off + cidx(i, j, k)) * ORC_NG + ORC_G_MARK] == 0.0;
+  }
+  int64_t xf(int i, int j, int k) const { return ((int64_t)k * ny + j) * (nx + 1) + i; }
+  int64_t yf(int i, int j, int k) const { return ((int64_t)k * (ny + 1) + j) * nx + i; }
+  int64_t zf(int i, int j, int k) const { return ((int64_t)k * ny + j) * nx + i; }
+};
+// face kind: 0 wall, 1 open (fluid on both sides), 2 inlet, 3 outlet
+int face_kind(const FlowGrid &g, int a, int i, int j, int k) {
+  int di = a == 0, dj = a == 1, dk = a == 2;
+  bool lo = g.fluid(i - di, j - dj, k - dk), hi = g.fluid(i, j, k);
+  if (lo && hi) return 1;
+  if (a == 2 && hi && !lo) return 2;
+  if (a == 2 && lo && k == g.nz) return 3;
+  return 0;
+}
+// pseudo-turbulence coefficients of a cell: R_pa, R_pe, alpha_pa, alpha_pe and the slip direction
+struct PT { double Rpa, Rpe, apa, ape, s[3]; };
+PT pseudo_turbulence(double eps, double rho, double mu, double lam, double cp, const double ug[3],
+                     const double up[3], double dp) {
+  PT t{0, 0, 0, 0, {0, 0, 0}};
+  const double ep = 1.0 - eps;
+  double sl[3] = {ug[0] - up[0], ug[1] - up[1], ug[2] - up[2]};
+  const double sm = std::sqrt(sl[0] * sl[0] + sl[1] * sl[1] + sl[2] * sl[2]);
+  if (!(ep > 0.0) || !(sm > 0.0) || !(dp > 0.0)) return t;
+  for (int q = 0; q < 3; ++q) t.s[q] = sl[q] / sm;
+  const double Rem = std::min(eps * rho * sm * dp / mu, 100.0);
+  const double epc = std::min(ep, 0.5);
+  const double Eg = 0.5 * sm * sm;                                                   // eq (3-30)
+  const double kg = Eg * (2.0 * ep + 2.5 * ep * eps * eps * eps * std::exp(-ep * std::sqrt(Rem)));   // eq (3-29)
+  const double bpa = 0.523 / (1.0 + 0.305 * std::exp(-0.114 * Rem)) *
+                     std::exp(-3.511 * ep / (1.0 + 1.801 * std::exp(-0.005 * Rem)));  // eq (3-31)
+  const double bpe = -0.5 * bpa;                                                     // eq (3-32)
+  t.Rpa = 2.0 * kg * (bpa + 1.0 / 3.0);                                               // eq (3-28)
+  t.Rpe = 2.0 * kg * (bpe + 1.0 / 3.0);
+  const double Pr = cp * mu / lam;
+  const double ag = lam / (rho * cp);
+  const double Num = (-0.46 + 1.77 * eps + 0.69 * eps * eps) / (eps * eps * eps) +
+                     (1.37 - 2.4 * eps + 1.2 * eps * eps) * std::pow(Rem, 0.7) * std::cbrt(Pr);   // eq (3-36)
+  const double num = 1.4 * Rem * (Rem + 1.4) * Pr * std::exp(-0.002089 * Rem) *
+                     (eps * (-5.11 * epc + 10.1 * epc * epc - 10.85 * epc * epc * epc) + 1.0 - std::exp(-10.96 * epc));
+  const double den = 3.0 * kPi * eps * eps * Num *
+                     (1.17 * epc - 0.2021 * std::sqrt(epc) + 0.08568 * std::pow(epc, 0.25)) *
+                     (1.0 - 1.6 * epc * eps - 3.0 * epc * std::pow(eps, 4.0) * std::exp(-std::pow(Rem, 0.4) * epc));
+  t.apa = den > 0.0 ? ag * num / den : 0.0;                                           // eq (3-35)
+  t.ape = (3.0 * bpe + 1.0) / (3.0 * bpa + 1.0) * t.apa;                               // eq (3-37)
+  return t;
+}
+inline double pt_diag(const PT &t, int a, bool heat) {
+  const double pa = heat ? t.apa : t.Rpa, pe = heat ? t.ape : t.Rpe;
+  return pe + (pa - pe) * t.s[a] * t.s[a];
+}
+
+// one gas step of bed b over dt, from the gas state and the parcels' cell sums in o.dep
+void gas_solve(Oracle &o, int b, const std::vector<GasProps> &gp, double dt) {
+  const double *bd = o.B(b);
+  const Grid gg = make_grid(bd);
+  FlowGrid g{gg.nx, gg.ny, gg.nz, gg.dx, gg.dy, gg.dz, o.cell_off[b], o.gas.data()};
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int64_t nc = (int64_t)nx * ny * nz, off = g.off;
+  const double V = g.hx * g.hy * g.hz;
+  const double h[3] = {g.hx, g.hy, g.hz};
+  const double Af[3] = {g.hy * g.hz, g.hx * g.hz, g.hx * g.hy};
+  const double k = bd[ORC_B_CG], k3 = k * k * k;
+  const double Uin = bd[ORC_B_U_IN], Tin = bd[ORC_B_T_IN], p0 = bd[ORC_B_P0];
+  const double grav = ((unsigned)ib(bd, ORC_B_FLAGS) & ORC_NO_GRAVITY) ? 0.0 : -kG;
+  std::vector<double> &U = o.fu[b], &Vv = o.fv[b], &W = o.fw[b], &P = o.pr[b];
+  auto comp = [&](int a) -> std::vector<double> & { return a == 0 ? U : (a == 1 ? Vv : W); };
+  auto fidx = [&](int a, int i, int j, int kk) { return a == 0 ? g.xf(i, j, kk) : (a == 1 ? g.yf(i, j, kk) : g.zf(i, j, kk)); };
+  // per-cell coefficients from the old state and the cell sums (eps: this coupling step's, from
+  // the deposited parcel volume; epso: the last one's)
+  std::vector<double> eps(nc), epso(nc), rho(nc), mu(nc), lam(nc), cp(nc), Dm(nc), Kc(nc), Kv(3 * nc), RT(3 * nc),
+      AT(3 * nc), uc(3 * nc);
+  for (int kk = 0; kk < nz; ++kk)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const int64_t c = g.cidx(i, j, kk);
+        const double *gc = &o.gas[(off + c) * ORC_NG];
+        const double *dp = &o.dep[(off + c) * ORC_NDEP];
+        const GasProps &G = gp[off + c];
+        epso[c] = gc[ORC_G_EPS];   // the last coupling step's
+        eps[c] = g.fluid(i, j, kk) ? std::max(1.0 - dp[ORC_DEP_VS] / V, bd[ORC_B_EPS_MIN]) : bd[ORC_B_EPS_MIN];
+        rho[c] = G.rho; mu[c] = G.mu; lam[c] = G.lam; cp[c] = G.cp; Dm[c] = G.Dm;
+        Kc[c] = dp[ORC_DEP_K] / V;
+        for (int q = 0; q < 3; ++q) Kv[3 * c + q] = dp[ORC_DEP_KV + q] / V;
+        uc[3 * c + 0] = 0.5 * (U[g.xf(i, j, kk)] + U[g.xf(i + 1, j, kk)]);
+        uc[3 * c + 1] = 0.5 * (Vv[g.yf(i, j, kk)] + Vv[g.yf(i, j + 1, kk)]);
+        uc[3 * c + 2] = 0.5 * (W[g.zf(i, j, kk)] + W[g.zf(i, j, kk + 1)]);
+        PT t{0, 0, 0, 0, {0, 0, 0}};
+        if (g.fluid(i, j, kk) && dp[ORC_DEP_K] > 0.0 && dp[ORC_DEP_COUNT] > 0.0) {
+          const double upv[3] = {dp[ORC_DEP_KV] / dp[ORC_DEP_K], dp[ORC_DEP_KV + 1] / dp[ORC_DEP_K],
+                                 dp[ORC_DEP_KV + 2] / dp[ORC_DEP_K]};
+          const double dpm = std::cbrt(6.0 * dp[ORC_DEP_VS] / (kPi * dp[ORC_DEP_COUNT] * k3));
+          t = pseudo_turbulence(eps[c], rho[c], mu[c], lam[c], cp[c], &uc[3 * c], upv, dpm);
+        }
+        for (int a = 0; a < 3; ++a) { RT[3 * c + a] = pt_diag(t, a, false); AT[3 * c + a] = pt_diag(t, a, true); }
+      }
+  // 1. momentum predictor on every face (eq (4-2))
+  std::vector<double> Us[3] = {U, Vv, W};
+  auto fval = [&](int a, int i, int j, int kk, double self) -> double {
+    // a face value seen from a neighbouring face: open, inlet and outlet faces carry theirs,
+    // walls are at rest (no-slip ghost -self for a tangential neighbour is applied by the caller)
+    const int nmax[3] = {nx + (a == 0), ny + (a == 1), nz + (a == 2)};
+    if (i < 0 || j < 0 || kk < 0 || i >= nmax[0] || j >= nmax[1] || kk >= nmax[2]) return std::nan("");
+    const int kd = face_kind(g, a, i, j, kk);
+    (void)self;
+    return kd == 0 ? std::nan("") : comp(a)[fidx(a, i, j, kk)];
+  };
+  for (int a = 0; a < 3; ++a) {
+    const int di = a == 0, dj = a == 1, dk = a == 2;
+    for (int kk = 0; kk < nz + dk; ++kk)
+      for (int j = 0; j < ny + dj; ++j)
+        for (int i = 0; i < nx + di; ++i) {
+          const int kd = face_kind(g, a, i, j, kk);
+          const int64_t f = fidx(a, i, j, kk);
+          if (kd == 0) { Us[a][f] = 0.0; continue; }
+          if (kd == 2) { Us[a][f] = Uin / eps[g.cidx(i, j, kk)]; continue; }
+          if (kd == 3) continue;   // outlet: after the interior faces (zero gradient)
+          const int64_t cP = g.cidx(i - di, j - dj, kk - dk), cN = g.cidx(i, j, kk);
+          const double ef = 0.5 * (eps[cP] + eps[cN]), rf = 0.5 * (rho[cP] + rho[cN]);
+          const double mf = 0.5 * (mu[cP] + mu[cN]), Kf = 0.5 * (Kc[cP] + Kc[cN]);
+          const double Kvf = 0.5 * (Kv[3 * cP + a] + Kv[3 * cN + a]);
+          const double u0 = comp(a)[f];
+          // the velocity at the face: its own component, the others from the four faces around
+          double Uf[3];
+          for (int bb = 0; bb < 3; ++bb) {
+            if (bb == a) { Uf[bb] = u0; continue; }
+            const int ei = bb == 0, ej = bb == 1, ek = bb == 2;
+            // the bb-faces of cells P and N, low and high side
+            double sum = 0.0;
+            sum += comp(bb)[fidx(bb, i - di, j - dj, kk - dk)] + comp(bb)[fidx(bb, i - di + ei, j - dj + ej, kk - dk + ek)];
+            sum += comp(bb)[fidx(bb, i, j, kk)] + comp(bb)[fidx(bb, i + ei, j + ej, kk + ek)];
+            Uf[bb] = 0.25 * sum;
+          }
+          double conv = 0.0, visc = 0.0;
+          for (int bb = 0; bb < 3; ++bb) {
+            const int ei = bb == 0, ej = bb == 1, ek = bb == 2;
+            double lo = fval(a, i - ei, j - ej, kk - ek, u0), hi = fval(a, i + ei, j + ej, kk + ek, u0);
+            if (bb != a) {   // tangential neighbours: no-slip walls halfway between
+              if (std::isnan(lo)) lo = -u0;
+              if (std::isnan(hi)) hi = -u0;
+            } else {         // normal neighbours: walls at rest
+              if (std::isnan(lo)) lo = 0.0;
+              if (std::isnan(hi)) hi = 0.0;
+            }
+            conv += Uf[bb] > 0.0 ? Uf[bb] * (u0 - lo) / h[bb] : Uf[bb] * (hi - u0) / h[bb];
+            visc += (hi - 2.0 * u0 + lo) / (h[bb] * h[bb]);
+          }
+          const double ptrs = -(eps[cN] * rho[cN] * RT[3 * cN + a] - eps[cP] * rho[cP] * RT[3 * cP + a]) / h[a];
+          const double rhs = ef * rf * u0 / dt - ef * rf * conv + ef * mf * visc + ptrs +
+                             (a == 2 ? ef * rf * grav : 0.0) - ef * (P[cN] - P[cP]) / h[a] + Kvf;
+          Us[a][f] = rhs / (ef * rf / dt + Kf);
+        }
+  }
+  for (int j = 0; j < ny; ++j)   // outlet faces: the face below
+    for (int i = 0; i < nx; ++i)
+      if (face_kind(g, 2, i, j, nz) == 3) Us[2][g.zf(i, j, nz)] = Us[2][g.zf(i, j, nz - 1)];
+  // 2. pressure correction (incremental projection): for each fluid cell
+  //    sum_f c_f (p''_nb - p''_P) = sum_f s_f eps_f rho_f u*_f A_f - V (M_P - rho_P (eps - eps_old) / dt)
+  std::vector<double> M(nc, 0.0);
+  for (int64_t c = 0; c < nc; ++c) {
+    const double *dp = &o.dep[(off + c) * ORC_NDEP];
+    M[c] = (dp[ORC_DEP_SH2] + dp[ORC_DEP_SH2O]) / V;   // eq (3-25), kg/m^3/s
+  }
+  auto face_c = [&](int a, int i, int j, int kk, int kd) -> double {   // c_f of an open or outlet face
+    const int di = a == 0, dj = a == 1, dk = a == 2;
+    const int64_t cP = g.cidx(i - di, j - dj, kk - dk);
+    if (kd == 3) {
+      const double beta = eps[cP] / (eps[cP] * rho[cP] / dt + Kc[cP]);
+      return 2.0 * eps[cP] * rho[cP] * beta * Af[a] / h[a];
+    }
+    const int64_t cN = g.cidx(i, j, kk);
+    const double ef = 0.5 * (eps[cP] + eps[cN]), rf = 0.5 * (rho[cP] + rho[cN]), Kf = 0.5 * (Kc[cP] + Kc[cN]);
+    const double beta = ef / (ef * rf / dt + Kf);
+    return ef * rf * beta * Af[a] / h[a];
+  };
+  auto face_flux = [&](int a, int i, int j, int kk, int kd, const std::vector<double> *us) -> double {
+    const int di = a == 0, dj = a == 1, dk = a == 2;
+    if (kd == 0) return 0.0;
+    const int64_t f = fidx(a, i, j, kk);
+    if (kd == 2) { const int64_t cN = g.cidx(i, j, kk); return eps[cN] * rho[cN] * us[a][f] * Af[a]; }
+    const int64_t cP = g.cidx(i - di, j - dj, kk - dk);
+    if (kd == 3) return eps[cP] * rho[cP] * us[a][f] * Af[a];
+    const int64_t cN = g.cidx(i, j, kk);
+    return 0.5 * (eps[cP] + eps[cN]) * 0.5 * (rho[cP] + rho[cN]) * us[a][f] * Af[a];
+  };
+  std::vector<double> rhs(nc, 0.0), diagA(nc, 0.0);
+  for (int kk = 0; kk < nz; ++kk)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        if (!g.fluid(i, j, kk)) continue;
+        const int64_t c = g.cidx(i, j, kk);
+        double net = 0.0, dsum = 0.0;
+        for (int a = 0; a < 3; ++a) {
+          const int di = a == 0, dj = a == 1, dk = a == 2;
+          const int kl = face_kind(g, a, i, j, kk), kh = face_kind(g, a, i + di, j + dj, kk + dk);
+          net += face_flux(a, i + di, j + dj, kk + dk, kh, Us) - face_flux(a, i, j, kk, kl, Us);
+          if (kl == 1) dsum += face_c(a, i, j, kk, kl);
+          if (kh == 1 || kh == 3) dsum += face_c(a, i + di, j + dj, kk + dk, kh);
+        }
+        rhs[c] = net - V * (M[c] - rho[c] * (eps[c] - epso[c]) / dt);
+        diagA[c] = dsum;
+      }
+  // apply L p = sum_f c_f (p_nb - p_P) (outlet neighbours at 0)
+  auto applyL = [&](const std::vector<double> &x, std::vector<double> &y) {
+    for (int kk = 0; kk < nz; ++kk)
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+          const int64_t c = g.cidx(i, j, kk);
+          if (!g.fluid(i, j, kk)) { y[c] = 0.0; continue; }
+          double acc = 0.0;
+          for (int a = 0; a < 3; ++a) {
+            const int di = a == 0, dj = a == 1, dk = a == 2;
+            const int kl = face_kind(g, a, i, j, kk), kh = face_kind(g, a, i + di, j + dj, kk + dk);
+            if (kl == 1) acc += face_c(a, i, j, kk, kl) * (x[g.cidx(i - di, j - dj, kk - dk)] - x[c]);
+            if (kh == 1) acc += face_c(a, i + di, j + dj, kk + dk, kh) * (x[g.cidx(i + di, j + dj, kk + dk)] - x[c]);
+            if (kh == 3) acc += face_c(a, i + di, j + dj, kk + dk, kh) * (0.0 - x[c]);
+          }
+          y[c] = acc;
+        }
+  };
+  // conjugate gradients on -L p'' = -rhs (Jacobi preconditioner), to a relative residual 1e-12
+  std::vector<double> x(nc, 0.0), r(nc), z(nc), pp(nc), Ap(nc);
+  double bnorm = 0.0;
+  for (int64_t c = 0; c < nc; ++c) { r[c] = -rhs[c]; bnorm += r[c] * r[c]; }
+  bnorm = std::sqrt(bnorm);
+  if (bnorm > 0.0) {
+    for (int64_t c = 0; c < nc; ++c) { z[c] = diagA[c] > 0.0 ? r[c] / diagA[c] : 0.0; pp[c] = z[c]; }
+    double rz = 0.0;
+    for (int64_t c = 0; c < nc; ++c) rz += r[c] * z[c];
+    for (int it = 0; it < 20000; ++it) {
+      applyL(pp, Ap);
+      double pAp = 0.0;
+      for (int64_t c = 0; c < nc; ++c) { Ap[c] = -Ap[c]; pAp += pp[c] * Ap[c]; }
+      if (!(pAp > 0.0)) break;
+      const double al = rz / pAp;
+      double rn = 0.0;
+      for (int64_t c = 0; c < nc; ++c) { x[c] += al * pp[c]; r[c] -= al * Ap[c]; rn += r[c] * r[c]; }
+      if (std::sqrt(rn) < 1e-12 * bnorm) break;
+      double rzn = 0.0;
+      for (int64_t c = 0; c < nc; ++c) { z[c] = diagA[c] > 0.0 ? r[c] / diagA[c] : 0.0; rzn += r[c] * z[c]; }
+      const double be = rzn / rz;
+      rz = rzn;
+      for (int64_t c = 0; c < nc; ++c) pp[c] = z[c] + be * pp[c];
+    }
+  }
+  // correct the face velocities and the pressure
+  for (int a = 0; a < 3; ++a) {
+    const int di = a == 0, dj = a == 1, dk = a == 2;
+    for (int kk = 0; kk < nz + dk; ++kk)
+      for (int j = 0; j < ny + dj; ++j)
+        for (int i = 0; i < nx + di; ++i) {
+          const int kd = face_kind(g, a, i, j, kk);
+          if (kd != 1 && kd != 3) continue;
+          const int64_t f = fidx(a, i, j, kk), cP = g.cidx(i - di, j - dj, kk - dk);
+          if (kd == 3) {
+            const double beta = eps[cP] / (eps[cP] * rho[cP] / dt + Kc[cP]);
+            Us[a][f] -= beta * (0.0 - x[cP]) / (0.5 * h[a]);
+          } else {
+            const int64_t cN = g.cidx(i, j, kk);
+            const double ef = 0.5 * (eps[cP] + eps[cN]), rf = 0.5 * (rho[cP] + rho[cN]), Kf = 0.5 * (Kc[cP] + Kc[cN]);
+            Us[a][f] -= ef / (ef * rf / dt + Kf) * (x[cN] - x[cP]) / h[a];
+          }
+        }
+  }
+  for (int64_t c = 0; c < nc; ++c) P[c] += x[c];
+  U = Us[0]; Vv = Us[1]; W = Us[2];
+  // 3. species (eq (4-9)) and energy (eq (4-6)) with the new mass fluxes
+  std::vector<double> nxt(o.gas.begin() + off * ORC_NG, o.gas.begin() + (off + nc) * ORC_NG);
+  const double Yin[3] = {bd[ORC_B_Y_IN], bd[ORC_B_Y_IN + 1], bd[ORC_B_Y_IN + 2]};
+  const double MH2 = kMj[0], MH2O = kMj[1];
+  for (int kk = 0; kk < nz; ++kk)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        if (!g.fluid(i, j, kk)) continue;
+        const int64_t c = g.cidx(i, j, kk);
+        const double *gc = &o.gas[(off + c) * ORC_NG];
+        const double *dp = &o.dep[(off + c) * ORC_NDEP];
+        const GasProps &G = gp[off + c];
+        const double Y0 = gc[ORC_G_Y], Y1 = gc[ORC_G_Y + 1], T = gc[ORC_G_T];
+        double cY0 = 0.0, cY1 = 0.0, cT = 0.0, dY0 = 0.0, dY1 = 0.0, dT = 0.0;
+        for (int a = 0; a < 3; ++a) {
+          const int di = a == 0, dj = a == 1, dk = a == 2;
+          for (int side = 0; side < 2; ++side) {   // 0: low face, 1: high face
+            const int fi = i + side * di, fj = j + side * dj, fk = kk + side * dk;
+            const int kd = face_kind(g, a, fi, fj, fk);
+            const double F = face_flux(a, fi, fj, fk, kd, Us);
+            const double inflow = side == 0 ? F : -F;   // mass into the cell through this face
+            const int ni = i + (side ? di : -di), nj = j + (side ? dj : -dj), nk = kk + (side ? dk : -dk);
+            if (kd == 1) {
+              const int64_t cn = g.cidx(ni, nj, nk);
+              const double *gn = &o.gas[(off + cn) * ORC_NG];
+              if (inflow > 0.0) {
+                cY0 += inflow * (gn[ORC_G_Y] - Y0);
+                cY1 += inflow * (gn[ORC_G_Y + 1] - Y1);
+                cT += inflow * cp[c] * (gn[ORC_G_T] - T);
+              }
+              const double ef = 0.5 * (eps[c] + eps[cn]), rf = 0.5 * (rho[c] + rho[cn]);
+              const double Df = 0.5 * (Dm[c] + Dm[cn]) + 0.5 * (AT[3 * c + a] + AT[3 * cn + a]);
+              const double lf = 0.5 * (lam[c] + lam[cn]) + rf * 0.5 * (cp[c] + cp[cn]) * 0.5 * (AT[3 * c + a] + AT[3 * cn + a]);
+              dY0 += ef * rf * Df * Af[a] / h[a] * (gn[ORC_G_Y] - Y0);
+              dY1 += ef * rf * Df * Af[a] / h[a] * (gn[ORC_G_Y + 1] - Y1);
+              dT += ef * lf * Af[a] / h[a] * (gn[ORC_G_T] - T);
+            } else if (kd == 2) {                 // inlet gas
+              if (inflow > 0.0) {
+                cY0 += inflow * (Yin[0] - Y0);
+                cY1 += inflow * (Yin[1] - Y1);
+                cT += inflow * cp[c] * (Tin - T);
+              }
+            } else if (kd == 0) {                 // wall at the inlet temperature
+              dT += eps[c] * lam[c] * Af[a] / (0.5 * h[a]) * (Tin - T);
+            }                                     // outlet: zero gradient
+          }
+        }
+        const double m = eps[c] * rho[c] * V;
+        // eqs (4-8)..(4-11): H2 consumed at (M_H2 p / R)(x EQ - ES) with x = a Y_H2 (implicit in
+        // Y_H2), H2O produced at M_H2O / M_H2 times that; in the non-conservative form the
+        // net mass source takes Y (and c_p T) of the cell away
+        const double X = G.xp[0] + G.xp[1];
+        const double ax = X > 0.0 ? G.Mg / (MH2 * X) : 0.0;
+        const double C0 = MH2 * p0 * ax * dp[ORC_DEP_EQ] / kRg, C1 = MH2 * p0 * dp[ORC_DEP_ES] / kRg;
+        const double rq = MH2O / MH2 - 1.0;
+        const double Y0n = (m * Y0 / dt + cY0 + dY0 + C1 * (1.0 + Y0 * rq)) / (m / dt + C0 * (1.0 + Y0 * rq));
+        const double cons = C0 * Y0n - C1;                        // H2 consumed, kg/s
+        const double Mnet = rq * cons;                            // net gas mass source, kg/s
+        double Y0f = Y0n;
+        double Y1f = Y1 + dt / m * (cY1 + dY1 + MH2O / MH2 * cons - Y1 * Mnet);
+        Y0f = std::max(Y0f, 0.0);
+        Y1f = std::max(Y1f, 0.0);
+        double Y2f = std::max(1.0 - Y0f - Y1f, 0.0);
+        const double ys = Y0f + Y1f + Y2f;
+        nxt[c * ORC_NG + ORC_G_Y] = Y0f / ys;
+        nxt[c * ORC_NG + ORC_G_Y + 1] = Y1f / ys;
+        nxt[c * ORC_NG + ORC_G_Y + 2] = Y2f / ys;
+        // energy: M_r of eq (3-39) with the species sources, M_rm of eq (3-38)
+        const double Mr = -(nasa_H(0, T) * (-cons) + nasa_H(1, T) * (MH2O / MH2 * cons));
+        const double Mrm = -dp[ORC_DEP_QRM];
+        const double mc = m * cp[c];
+        nxt[c * ORC_NG + ORC_G_T] = (mc * T / dt + cT + dT + dp[ORC_DEP_HAT] + Mr + Mrm - T * cp[c] * Mnet) /
+                                    (mc / dt + dp[ORC_DEP_HA]);
+      }
+  for (int64_t c = 0; c < nc; ++c) nxt[c * ORC_NG + ORC_G_EPS] = eps[c];
+  std::copy(nxt.begin(), nxt.end(), o.gas.begin() + off * ORC_NG);
+}
+
+// initial gas flow of a solved bed: plug flow at the superficial velocity through every fluid
+// column (eps w = U_in on the z-faces that carry gas), no cross flow, p = p0
+void gas_flow_init(Oracle &o, int b) {
+  const double *bd = o.B(b);
+  const Grid gg = make_grid(bd);
+  FlowGrid g{gg.nx, gg.ny, gg.nz, gg.dx, gg.dy, gg.dz, o.cell_off[b], o.gas.data()};
+  o.fu[b].assign((size_t)(g.nx + 1) * g.ny * g.nz, 0.0);
+  o.fv[b].assign((size_t)g.nx * (g.ny + 1) * g.nz, 0.0);
+  o.fw[b].assign((size_t)g.nx * g.ny * (g.nz + 1), 0.0);
+  o.pr[b].assign((size_t)g.nx * g.ny * g.nz, 0.0);
+  for (int k = 0; k <= g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        const int kd = face_kind(g, 2, i, j, k);
+        if (kd == 0) continue;
+        const int kc = kd == 3 ? k - 1 : k;
+        o.fw[b][g.zf(i, j, k)] = bd[ORC_B_U_IN] / o.gas[(g.off + g.cidx(i, j, kc)) * ORC_NG + ORC_G_EPS];
+      }
+}
+
+
 template <class S> S fov_of(const S m[4], int ore) {   // eqs (2-15)..(2-19)
   S n[4];
   for (int z = 0; z < 4; ++z) n[z] = m[z] / kMz[z];
@@ -806,6 +1213,22 @@ void step_once(Oracle &o) {
       const double *gc = &o.gas[(o.cell_off[b] + c) * ORC_NG];
       gp[o.cell_off[b] + c] = gas_props(gc[ORC_G_T], gc + ORC_G_Y, bd[ORC_B_P0]);
     }
+  }
+  // cell-centre gas velocity of the beds whose gas is solved (the mean of the two faces)
+  std::vector<double> ucell(3 * (size_t)o.ncell_total, 0.0);
+  for (int b = 0; b < o.nb; ++b) {
+    const double *bd = o.B(b);
+    if (!((unsigned)ib(bd, ORC_B_FLAGS) & ORC_GAS_SOLVER)) continue;
+    Grid gg = make_grid(bd);
+    FlowGrid g{gg.nx, gg.ny, gg.nz, gg.dx, gg.dy, gg.dz, o.cell_off[b], o.gas.data()};
+    for (int k = 0; k < g.nz; ++k)
+      for (int j = 0; j < g.ny; ++j)
+        for (int i = 0; i < g.nx; ++i) {
+          const int64_t c = o.cell_off[b] + g.cidx(i, j, k);
+          ucell[3 * c] = 0.5 * (o.fu[b][g.xf(i, j, k)] + o.fu[b][g.xf(i + 1, j, k)]);
+          ucell[3 * c + 1] = 0.5 * (o.fv[b][g.yf(i, j, k)] + o.fv[b][g.yf(i, j + 1, k)]);
+          ucell[3 * c + 2] = 0.5 * (o.fw[b][g.zf(i, j, k)] + o.fw[b][g.zf(i, j, k + 1)]);
+        }
   }
   // 1. half kick and drift (velocity Verlet, kick-drift-kick)
   for (int i = 0; i < n; ++i) {
@@ -983,6 +1406,8 @@ void step_once(Oracle &o) {
     const GasProps &G = gp[c];
     double eps = gc[ORC_G_EPS];
     double ug[3] = {0.0, 0.0, bd[ORC_B_U_IN] / eps};
+    if (flags & ORC_GAS_SOLVER)
+      for (int q = 0; q < 3; ++q) ug[q] = ucell[3 * c + q];   // the solved gas, cell centre
     double sv[3] = {ug[0] - o.s[ORC_S_VX][i], ug[1] - o.s[ORC_S_VY][i], ug[2] - o.s[ORC_S_VZ][i]};
     double slip = std::sqrt(sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]);
     double Re = 0.0;
@@ -1073,10 +1498,15 @@ void step_once(Oracle &o) {
     if (o.gas[c * ORC_NG + ORC_G_MARK] != 0.0) continue;   // solid cells take no sources
     for (int f = 0; f < ORC_NDEP; ++f) o.dep[c * ORC_NDEP + f] += pdep[(size_t)i * ORC_NDEP + f];
   }
-  // 5. gas update (prescribed field, simple explicit update; not the paper's solver)
+  // 5. gas update: the gas phase solver of beds that switch it on, else the prescribed field
+  //    with its simple explicit update
   for (int b = 0; b < o.nb; ++b) {
     const double *bd = o.B(b);
     if (!coupled[b] || ((unsigned)ib(bd, ORC_B_FLAGS) & ORC_NO_GAS_UPDATE)) continue;
+    if ((unsigned)ib(bd, ORC_B_FLAGS) & ORC_GAS_SOLVER) {
+      gas_solve(o, b, gp, std::max(1, ib(bd, ORC_B_NCOUPLE)) * bd[ORC_B_DT]);
+      continue;
+    }
     Grid g = make_grid(bd);
     const double dtg = std::max(1, ib(bd, ORC_B_NCOUPLE)) * bd[ORC_B_DT];
     const double V = g.dx * g.dy * g.dz;
@@ -1199,7 +1629,7 @@ int32_t orc_adjoint_obs(void *h, int32_t nsteps, int32_t mode, int32_t nobs, con
                         const double *weights, double *J_obs, double *grad6) {
   Oracle *o = (Oracle *)h;
   for (int b = 0; b < o->nb; ++b)
-    if ((unsigned)ib(o->B(b), ORC_B_FLAGS) & (ORC_RADIATION | ORC_CONDUCTION)) return -1;
+    if ((unsigned)ib(o->B(b), ORC_B_FLAGS) & (ORC_RADIATION | ORC_CONDUCTION | ORC_GAS_SOLVER)) return -1;
   std::vector<GasProps> gp(o->ncell_total);
   for (int b = 0; b < o->nb; ++b) {
     const double *bd = o->B(b);
@@ -1309,6 +1739,9 @@ void *orc_create(int32_t nbeds, const double *beds, int32_t n, const double *x, 
         }
   }
   deposit_volume_and_eps(*o);
+  o->fu.resize(nbeds); o->fv.resize(nbeds); o->fw.resize(nbeds); o->pr.resize(nbeds);
+  for (int b = 0; b < nbeds; ++b)
+    if ((unsigned)ib(o->B(b), ORC_B_FLAGS) & ORC_GAS_SOLVER) gas_flow_init(*o, b);
   return o;
 }
 
@@ -1381,9 +1814,10 @@ void orc_destroy(void *h) { delete (Oracle *)h; }
 
 int32_t orc_adjoint(void *h, int32_t nsteps, int32_t mode, double rel, double *J, double *grad6) {
   Oracle *o = (Oracle *)h;
-  // the differentiated map is per parcel; radiation couples parcels through T_se
+  // the differentiated map is per parcel in a prescribed gas; radiation and conduction couple
+  // parcels, and a solved gas is not the map's prescribed field
   for (int b = 0; b < o->nb; ++b)
-    if ((unsigned)ib(o->B(b), ORC_B_FLAGS) & ORC_RADIATION) return -1;
+    if ((unsigned)ib(o->B(b), ORC_B_FLAGS) & (ORC_RADIATION | ORC_CONDUCTION | ORC_GAS_SOLVER)) return -1;
   std::vector<GasProps> gp(o->ncell_total);
   for (int b = 0; b < o->nb; ++b) {
     const double *bd = o->B(b);
@@ -1516,6 +1950,40 @@ int64_t orc_pairs_cells(int32_t n, const double *x, const double *y, const doubl
   int64_t np = (int64_t)out.size();
   for (int64_t t = 0; t < std::min(np, max_pairs); ++t) { pairs[2 * t] = out[t].first; pairs[2 * t + 1] = out[t].second; }
   return np;
+}
+
+void orc_pseudo_turbulence(double eps, double rho, double mu, double lam, double cp, const double *ug,
+                           const double *up, double dp, double *out8) {
+  const PT t = pseudo_turbulence(eps, rho, mu, lam, cp, ug, up, dp);
+  out8[0] = t.Rpa; out8[1] = t.Rpe; out8[2] = t.apa; out8[3] = t.ape;
+  for (int q = 0; q < 3; ++q) out8[4 + q] = t.s[q];
+  out8[7] = 0.0;
+}
+
+void orc_get_flow(void *h, double *out) {
+  Oracle *o = (Oracle *)h;
+  for (int b = 0; b < o->nb; ++b) {
+    const double *bd = o->B(b);
+    Grid gg = make_grid(bd);
+    FlowGrid g{gg.nx, gg.ny, gg.nz, gg.dx, gg.dy, gg.dz, o->cell_off[b], o->gas.data()};
+    const bool solved = ((unsigned)ib(bd, ORC_B_FLAGS) & ORC_GAS_SOLVER) != 0;
+    for (int k = 0; k < g.nz; ++k)
+      for (int j = 0; j < g.ny; ++j)
+        for (int i = 0; i < g.nx; ++i) {
+          const int64_t c = o->cell_off[b] + g.cidx(i, j, k);
+          double *r = out + c * ORC_NV;
+          if (!solved) {
+            r[0] = r[1] = 0.0;
+            r[2] = bd[ORC_B_U_IN] / o->gas[c * ORC_NG + ORC_G_EPS];
+            r[3] = 0.0;
+            continue;
+          }
+          r[0] = 0.5 * (o->fu[b][g.xf(i, j, k)] + o->fu[b][g.xf(i + 1, j, k)]);
+          r[1] = 0.5 * (o->fv[b][g.yf(i, j, k)] + o->fv[b][g.yf(i, j + 1, k)]);
+          r[2] = 0.5 * (o->fw[b][g.zf(i, j, k)] + o->fw[b][g.zf(i, j, k + 1)]);
+          r[3] = o->pr[b][g.cidx(i, j, k)];
+        }
+  }
 }
 
 double orc_restitution_f(double e) { return restitution_f(e); }

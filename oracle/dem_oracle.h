@@ -37,7 +37,8 @@ enum {
   ORC_NO_GAS_UPDATE = 16, ORC_NO_FILM = 32, ORC_NO_LAYER = 64, ORC_NO_RXN_HEAT = 128,
   ORC_NO_CONTACTS = 256,
   ORC_RADIATION = 512,  /* switch ON the particle radiation of eqs (3-16), (3-17), (3-51) */
-  ORC_CONDUCTION = 1024 /* switch ON the contact conduction of eqs (3-14)..(3-15-2), (3-42)..(3-48-2) */
+  ORC_CONDUCTION = 1024, /* switch ON the contact conduction of eqs (3-14)..(3-15-2), (3-42)..(3-48-2) */
+  ORC_GAS_SOLVER = 2048  /* the gas phase solved by eqs (3-24), (4-2), (4-6), (4-9) instead of the prescribed field */
 };
 
 /* per-parcel state returned by orc_get_state: ORC_NS rows of n doubles */
@@ -57,6 +58,15 @@ enum {
   ORC_D_TSE /* eq (3-17), 0 without radiation */, ORC_D_QRAD /* eq (3-51), W per parcel */,
   ORC_D_QCOND /* contact conduction with parcels and walls, W per parcel, 0 when off */, ORC_ND
 };
+
+/* gas velocity of the solved gas phase (beds with ORC_GAS_SOLVER): per cell ORC_NV doubles,
+ * the cell-centre velocity (3) and the pressure relative to p0 */
+enum { ORC_V_U = 0, ORC_V_P = 3, ORC_NV };
+void orc_get_flow(void *h, double *out);
+/* pseudo-turbulence closures of one cell (eqs (3-28)..(3-37)): out8 = R_pa, R_pe, alpha_pa,
+ * alpha_pe, slip direction (3), 0 */
+void orc_pseudo_turbulence(double eps, double rho, double mu, double lam, double cp, const double *ug,
+                           const double *up, double dp, double *out8);
 
 /* per gas cell: ORC_NG doubles */
 enum { ORC_G_EPS = 0, ORC_G_Y /* 3 */, ORC_G_T = 4, ORC_G_MARK, ORC_NG };

@@ -48,6 +48,7 @@ NO_RXN_HEAT = 1 << 7
 NO_CONTACTS = 1 << 8
 RADIATION = 1 << 9   # switches ON the particle radiation (off by default)
 CONDUCTION = 1 << 10  # switches ON the contact heat conduction (off by default)
+GAS_SOLVER = 1 << 11  # the gas phase solved (momentum, energy, species) instead of the prescribed field
 
 # Kinetic presets: (k0 [m/s], Ea [J/mol]) for R1 (h->m), R2 (m->w), R3 (w->Fe).
 TAKENAKA = ((29.17, 15.56, 2858.0), (66974.0, 75345.0, 117204.0))        # Table 2
