@@ -68,11 +68,34 @@ enum { DEM_PREC_FP64 = 0, DEM_PREC_SPLIT = 1, DEM_PREC_SPLIT_KAHAN = 2 };
  * times the mean temperature of the parcels whose centres lie within 1.5 k d_p of the
  * parcel's centre (the parcel itself included), eps_g and T_g those of the parcel's gas
  * cell, all temperatures from before the step's update; Q_rad adds to the parcel's heat
- * balance (eq 3-8) and, as the paper neglects gas radiation, not to the gas. */
+ * balance (eq 3-8) and, as the paper neglects gas radiation, not to the gas.
+ * Gas solver: DEM_GAS_SOLVER replaces the prescribed gas field (plug flow U_in / eps_g along
+ * z, no cross flow, the explicit upwind update of Y and T along z) with the gas phase solved
+ * on the bed's grid every coupling step, in FP64 in every precision form: continuity
+ * (eq (3-24)) with the mass source of eq (3-25), momentum with the drag of eq (4-2)
+ * (K_gp u_g implicit, K_gp u_p explicit from the parcels' sums), energy with H0 implicit
+ * (eq (4-6)) and the reducing gas with C0, C1 (eqs (4-8)..(4-11)), the pseudo-turbulent
+ * stress and heat flux of eqs (3-28)..(3-37). Readings (the paper solves this with a
+ * finite-volume code and gives no discretisation): a staggered grid with the velocity
+ * components on the cell faces, explicit Euler in dt_CFD = n dt_DEM, first-order upwind
+ * convection, an incremental pressure projection solved by Jacobi-preconditioned conjugate
+ * gradients to a relative residual of 1e-12; immersed-boundary cells and the box sides are
+ * no-slip walls held at T_in (Table 3 lists the wall and inlet temperatures equal); a
+ * z-face below a fluid cell whose lower neighbour is not fluid carries the inlet gas
+ * (eps u = U_in, Y_in, T_in); z-faces on top of the box are an outlet at p0 with zero
+ * gradient; the pseudo-turbulent stress enters by its normal components and the heat flux
+ * by the diagonal of alpha_PT, both rotated to the slip direction of the cell's drag-
+ * weighted parcel velocity, with Re_m capped at 100 and eps_p at 0.5; H2O follows the H2
+ * consumed by stoichiometry (eq (2-25)) and N2 by closure; molecular diffusion takes
+ * D_H2,m of eq (2-27) for every species. Parcels see the cell-centre velocity of the solved
+ * faces; their pressure force keeps the prescribed dpdz. The flow starts as plug flow at
+ * U_in through every fluid column. Either every bed of a context has DEM_GAS_SOLVER, with
+ * one coupling interval for all, or none; it excludes DEM_NO_GAS_UPDATE, and a solving
+ * context takes no dem_set_gas input and no adjoint (DEM_EINVAL). */
 enum {
   DEM_NO_GRAVITY = 1, DEM_NO_DRAG = 2, DEM_NO_HEAT = 4, DEM_NO_KINETICS = 8,
   DEM_NO_GAS_UPDATE = 16, DEM_NO_FILM = 32, DEM_NO_LAYER = 64, DEM_NO_RXN_HEAT = 128,
-  DEM_NO_CONTACTS = 256, DEM_RADIATION = 512, DEM_CONDUCTION = 1024
+  DEM_NO_CONTACTS = 256, DEM_RADIATION = 512, DEM_CONDUCTION = 1024, DEM_GAS_SOLVER = 2048
 };
 
 enum { DEM_WALL_FLAT = 0, DEM_WALL_CONE = 1 };
@@ -114,7 +137,7 @@ typedef struct {
   double rho_true[4];     /* true densities of Fe2O3, Fe3O4, FeO, Fe (Table 3) */
   double dpdz;            /* prescribed gas pressure gradient along z, Pa/m (force -V dp/dz) */
   double eps_min;         /* lower clamp of the gas volume fraction */
-  uint32_t flags;         /* DEM_NO_* switches and DEM_RADIATION */
+  uint32_t flags;         /* DEM_NO_* switches, DEM_RADIATION, DEM_CONDUCTION, DEM_GAS_SOLVER */
   double emissivity;      /* particle emissivity eta_p of eq (3-16), in [0, 1] (Table 3: 0.85);
                              read only with DEM_RADIATION */
   double lambda_p[2];     /* particle thermal conductivity per ore type, W/m/K (> 0); read only
@@ -243,6 +266,14 @@ int dem_get_gas(dem_ctx *c, double *out_host);
  * Recomputed from the per-parcel sources kept from the last step. Synchronous. */
 enum { DEM_NDEP = 14 };
 int dem_get_sources(dem_ctx *c, double *out_host);
+
+/* Gas flow of every cell, DEM_NFLOW doubles per cell (host): the cell-centre gas velocity
+ * u_x u_y u_z (m/s; the mean of the cell's two faces on each axis where the gas is solved,
+ * (0, 0, U_in / eps_g) where it is prescribed) and the pressure relative to p0 (Pa; 0 where
+ * prescribed), and the number of conjugate-gradient iterations of the last pressure solve
+ * in iters (nullable; 0 without DEM_GAS_SOLVER). Synchronous. */
+enum { DEM_NFLOW = 4 };
+int dem_get_flow(dem_ctx *c, double *out_host, int32_t *iters);
 
 /* Contact-history table in parcel-index order (host): count[n]; partner[n*DEM_MAX_CONTACTS]
  * (parcel index of the partner, or -1-p for wall primitive p: 0 side, 1 bottom or cone,

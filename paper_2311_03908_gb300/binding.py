@@ -18,7 +18,7 @@ DEM_OK, DEM_EINVAL, DEM_ENOMEM, DEM_ECUDA, DEM_ECAPACITY, DEM_ENONFINITE, DEM_ET
     0, -1, -2, -3, -4, -5, -6, -7, -8
 DEM_PREC_FP64, DEM_PREC_SPLIT, DEM_PREC_SPLIT_KAHAN = 0, 1, 2
 DEM_MAX_CONTACTS = 24
-DEM_NSTATE, DEM_NGAS, DEM_NDEP, DEM_NDIAG = 20, 6, 14, 35
+DEM_NSTATE, DEM_NGAS, DEM_NDEP, DEM_NDIAG, DEM_NFLOW = 20, 6, 14, 35, 4
 DEM_NOALLOC_MAX_PARCELS = 8388608
 PRECISIONS = {"fp64": DEM_PREC_FP64, "split": DEM_PREC_SPLIT, "split_kahan": DEM_PREC_SPLIT_KAHAN}
 DEM_NTUNE = 9
@@ -92,6 +92,7 @@ def lib() -> C.CDLL:
         "dem_num_cells": (C.c_int64, [vp]),
         "dem_get_gas": (C.c_int, [vp, dp]),
         "dem_get_sources": (C.c_int, [vp, dp]),
+        "dem_get_flow": (C.c_int, [vp, dp, C.POINTER(C.c_int32)]),
         "dem_get_contacts": (C.c_int, [vp, ip, ip, dp]),
         "dem_set_diagnostics": (C.c_int, [vp, C.c_int32]),
         "dem_get_diag": (C.c_int, [vp, dp]),
@@ -286,6 +287,15 @@ class Context:
         _check(lib().dem_get_sources(self.h, C.cast(C.c_void_p(_ptr(out)), C.POINTER(C.c_double))),
                "dem_get_sources")
         return out
+
+    def dem_get_flow(self):
+        """Cell-centre gas velocity (3) and pressure relative to p0 of every cell,
+        (cells, DEM_NFLOW) doubles, and the conjugate-gradient iterations of the last
+        pressure solve (0 without the gas solver)."""
+        out = np.zeros((self.ncells, DEM_NFLOW))
+        it = C.c_int32(0)
+        _check(lib().dem_get_flow(self.h, out.ctypes.data_as(C.POINTER(C.c_double)), C.byref(it)), "dem_get_flow")
+        return out, int(it.value)
 
     def dem_get_contacts(self):
         cnt = np.zeros(self.n, dtype=np.int32)

@@ -35,11 +35,13 @@ enum : int { ERR_CAPACITY = 1, ERR_NONFINITE = 2, ERR_DOMAIN = 4, ERR_TIMEOUT = 
 
 // per-cell gas properties (derived from the gas state by gas_cell_props), stored cell by
 // cell in records of GP_STRIDE words, so that a parcel reads its cell's record in a few
-// vector loads
+// vector loads; the gas velocity (GP_UX, GP_UY, GP_UZ) is the prescribed plug flow, or the
+// cell-centre velocity of the solved gas
 enum : int {
   GP_RHO = 0, GP_MU, GP_LAM, GP_CP, GP_X, GP_DM, GP_SC13, GP_PR13, GP_EPOW, GP_D0, GP_D1,
-  GP_UZ, GP_EPS, GP_TG, GP_N, GP_STRIDE = 16
+  GP_UZ, GP_EPS, GP_TG, GP_UX, GP_UY, GP_N, GP_STRIDE = 16
 };
+static_assert((int)GP_N <= (int)GP_STRIDE, "property record");
 // gas state rows (double)
 enum : int { GS_EPS = 0, GS_Y0, GS_Y1, GS_Y2, GS_T, GS_N };
 // per-parcel source rows
@@ -74,6 +76,7 @@ struct DevBed {
   int ncouple;
   double U_in, T_in, p0, Y_in[3], eps_min;
   unsigned flags;
+  long long fx_off, fy_off, fz_off;   // first x-, y-, z-face of this bed (solved gas)
 };
 
 // Physics parameters of a bed in the form's arithmetic type R (prepared on the host).
@@ -211,7 +214,7 @@ template <class R> __device__ __forceinline__ R dcp_over_R(int s, R T) {
 // Gas-cell properties (eqs (2-1-1), (2-1-2), (2-26)..(2-29), (3-53)..(3-59)), once per cell.
 // ---------------------------------------------------------------------------------------
 template <class R> struct CellProps {
-  R rho, mu, lam, cp, x, Dm, sc13, pr13, epow, D[2], uz, eps, T;
+  R rho, mu, lam, cp, x, Dm, sc13, pr13, epow, D[2], uz, eps, T, ux, uy;
 };
 
 template <class R>
@@ -253,6 +256,8 @@ __device__ inline CellProps<R> gas_cell_props(const BedP<R> &B, R eps, const R Y
     o.D[ore] = ratio <= (R)0.01 ? o.Dm : (ratio >= (R)10 ? DK : frcp<R>(frcp<R>(o.Dm) + frcp<R>(DK)));
   }
   o.uz = fdiv<R>(B.U_in, eps);
+  o.ux = (R)0;
+  o.uy = (R)0;
   o.eps = eps;
   o.T = T;
   return o;
@@ -262,7 +267,7 @@ __device__ inline CellProps<R> gas_cell_props(const BedP<R> &B, R eps, const R Y
 // Per-parcel gas-side terms.
 // ---------------------------------------------------------------------------------------
 template <class R> struct Gas {   // a cell's properties in the parcel's arithmetic type
-  R rho, mu, lam, cp, x, Dm, sc13, pr13, epow, D, uz, eps, T;
+  R rho, mu, lam, cp, x, Dm, sc13, pr13, epow, D, uz, eps, T, ux, uy;
 };
 
 template <class R> __device__ __forceinline__ R pos_pow(R x, R e) {   // x^e for x >= 0

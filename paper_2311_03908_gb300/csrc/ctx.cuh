@@ -6,7 +6,7 @@
 #include <tuple>
 #include <vector>
 
-#include "kernels.cuh"
+#include "gas.cuh"
 
 struct dem_ctx {
   int n = 0, cap = 0, nbeds = 0, prec = DEM_PREC_FP64;
@@ -86,6 +86,9 @@ struct dem_ctx {
   float4 *xr = nullptr;            // local coordinates and temperature in sorted order (radiation)
   bool any_rad = false;            // some bed has DEM_RADIATION: the radiation kernel runs
   bool any_cond = false;           // some bed has DEM_CONDUCTION
+  bool gas_solver = false;         // every bed has DEM_GAS_SOLVER: the gas kernels replace k_cells
+  dem::GasView gsv = {};           // the solver's arrays (in the arena)
+  int gs_grid = 1;                 // blocks of the cooperative pressure solve (all co-resident)
   char *qc = nullptr;              // contact conduction heat of each parcel in contact (form's type)
   std::map<std::tuple<int, int, int>, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;
   std::map<std::tuple<int, int, int>, long long> graph_launches;
@@ -121,6 +124,9 @@ template <class P> int enqueue_scatter_diag(dem_ctx *c, double *out_dev);
 template <class P> int enqueue_scatter_hist(dem_ctx *c, int *cnt, int *partner, double *xi);
 template <class P> int enqueue_sources(dem_ctx *c);
 template <class P> int enqueue_gas_set(dem_ctx *c, const double *Y, const double *T, cudaStream_t st);
+template <class P> int enqueue_gas_solver_init(dem_ctx *c);
+template <class P> int enqueue_flow(dem_ctx *c, double *out_dev);
+template <class P> int gas_cg_occupancy(int *blocks_per_sm);
 template <class P> int run_adjoint(dem_ctx *c, int nsteps, int ckpt, double *J, double *grad, int nobs = 0,
                                    const int *obs_steps = nullptr, const double *weights = nullptr,
                                    double *J_obs = nullptr);

@@ -235,6 +235,7 @@ int validate_bed(const dem_bed_config &b) {
   for (int r = 0; r < 3; ++r) if (!(b.k0[r] >= 0 && b.Ea[r] >= 0)) return DEM_EINVAL;
   if (b.wall_kind != DEM_WALL_FLAT && b.wall_kind != DEM_WALL_CONE) return DEM_EINVAL;
   if ((b.flags & DEM_RADIATION) && !(b.emissivity >= 0 && b.emissivity <= 1)) return DEM_EINVAL;
+  if ((b.flags & DEM_GAS_SOLVER) && (b.flags & DEM_NO_GAS_UPDATE)) return DEM_EINVAL;
   if ((b.flags & DEM_CONDUCTION) &&
       !(b.lambda_p[0] > 0 && b.lambda_p[1] > 0 && b.lambda_wall > 0 && std::isfinite(b.lambda_p[0]) &&
         std::isfinite(b.lambda_p[1]) && std::isfinite(b.lambda_wall)))
@@ -416,6 +417,19 @@ void layout(dem_ctx *c, Bump &m) {
   c->dbeds = m.take<DevBed>(c->nbeds);
   c->dbp_d = m.take<BedP<double>>(c->nbeds);
   c->dbp_f = m.take<BedP<float>>(c->nbeds);
+  if (c->gas_solver) {   // the gas solver's faces, pressure, coefficients and CG vectors
+    GasView &S = c->gsv;
+    S.fu = m.take<double>(S.nfx); S.fv = m.take<double>(S.nfy); S.fw = m.take<double>(S.nfz);
+    S.su = m.take<double>(S.nfx); S.sv = m.take<double>(S.nfy); S.sw = m.take<double>(S.nfz);
+    S.pr = m.take<double>(C);
+    S.co = m.take<double>(C * GC_N);
+    S.x = m.take<double>(C); S.r = m.take<double>(C); S.z = m.take<double>(C);
+    S.pa = m.take<double>(C); S.pb = m.take<double>(C); S.Ap = m.take<double>(C);
+    S.part = m.take<double>((size_t)c->gs_grid * 4);
+    S.cg_iters = m.take<int>(1);
+    S.dep = m.take<double>(C * SR_N);
+    S.bpd = c->dbp_d;
+  }
 }
 
 int enqueue_steps_any(dem_ctx *c, int n) { return DEM_DISPATCH(c, enqueue_steps, c, n); }
@@ -576,10 +590,18 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
   c->rsize = precision == DEM_PREC_FP64 ? sizeof(double) : sizeof(float);
   c->st = (cudaStream_t)cuda_stream;
   c->cfg.assign(beds, beds + n_beds);
+  int nsolve = 0;
   for (int b = 0; b < n_beds; ++b) {
     c->any_rad = c->any_rad || (beds[b].flags & DEM_RADIATION) != 0;
     c->any_cond = c->any_cond || (beds[b].flags & DEM_CONDUCTION) != 0;
+    if (beds[b].flags & DEM_GAS_SOLVER) {
+      ++nsolve;
+      if (beds[b].coupling_interval != beds[0].coupling_interval) { delete c; return DEM_EINVAL; }
+    }
   }
+  // the gas solver runs for every bed or for none, on one coupling interval
+  if (nsolve != 0 && nsolve != n_beds) { delete c; return DEM_EINVAL; }
+  c->gas_solver = nsolve > 0;
   // per-bed constants and grid offsets; the gas cells are the cell list of the contact
   // search, so no parcel may be wider than a cell edge
   long long coff = 0, pacc = 0;
@@ -590,6 +612,12 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
     // stability of the stiffest contact: omega_0 dt < 2 with m* = m_min / 2
     if (nb[b] > 0 && std::sqrt(beds[b].kn / (0.5 * mmin[b])) * beds[b].dt >= 2.0) { delete c; return DEM_EINVAL; }
     B.cell_off = coff;
+    B.fx_off = c->gsv.nfx;
+    B.fy_off = c->gsv.nfy;
+    B.fz_off = c->gsv.nfz;
+    c->gsv.nfx += (long long)(B.nx + 1) * B.ny * B.nz;
+    c->gsv.nfy += (long long)B.nx * (B.ny + 1) * B.nz;
+    c->gsv.nfz += (long long)B.nx * B.ny * (B.nz + 1);
     B.pstart = (int)pacc;
     pacc += nb[b];
     B.pend = (int)pacc;
@@ -624,6 +652,12 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
   c->ncells = coff;
   c->key_bits = 1;
   while ((1LL << c->key_bits) < coff) ++c->key_bits;
+  if (c->gas_solver) {   // the cooperative pressure solve: no more blocks than fit at once
+    int per_sm = 0;
+    if (DEM_DISPATCH(c, gas_cg_occupancy, &per_sm) != 0 || per_sm < 1) { delete c; return DEM_ECUDA; }
+    const long long need = (c->ncells + GS_CG_BLOCK - 1) / GS_CG_BLOCK;
+    c->gs_grid = (int)std::max(1LL, std::min(need, (long long)per_sm * c->nsm));
+  }
   // arena
   Bump meas;
   layout(c, meas);
@@ -688,6 +722,7 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
   ck(cudaMemsetAsync(c->hcnt[1], 0, (size_t)n, c->st));
   ck(cudaMemsetAsync(c->err, 0, sizeof(int), c->st));
   ck(cudaMemsetAsync(c->step_ctr, 0, 6 * sizeof(long long), c->st));
+  if (c->gas_solver) ck(cudaMemsetAsync(c->gsv.cg_iters, 0, sizeof(int), c->st));
   // neighbour lists: none yet (the first step builds them); no displacement
   ck(cudaMemsetAsync(c->rebuild, 1, sizeof(int), c->st));
   for (int k = 0; k < 2; ++k) {
@@ -738,6 +773,7 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
   c->gcur = 0;
   if (rc == DEM_OK) {
     int e = DEM_DISPATCH(c, enqueue_init, c);
+    if (!e && c->gas_solver) e = DEM_DISPATCH(c, enqueue_gas_solver_init, c);
     if (e) rc = DEM_ECUDA;
   }
   ck(cudaStreamSynchronize(c->st));
@@ -908,6 +944,22 @@ int dem_get_sources(dem_ctx *c, double *out_host) {
   return DEM_OK;
 }
 
+int dem_get_flow(dem_ctx *c, double *out_host, int32_t *iters) {
+  if (!c || !out_host) return DEM_EINVAL;
+  int s = sync_all(c);
+  if (s != DEM_OK) return s;
+  const size_t bytes = sizeof(double) * 4 * (size_t)c->ncells;
+  if ((s = ensure_scratch(c, bytes)) != DEM_OK) return s;
+  int e = DEM_DISPATCH(c, enqueue_flow, c, c->scratch_out);
+  if (e) return DEM_ECUDA;
+  CK(cudaMemcpyAsync(out_host, c->scratch_out, bytes, cudaMemcpyDeviceToHost, c->st));
+  int it = 0;
+  if (c->gas_solver) CK(cudaMemcpyAsync(&it, c->gsv.cg_iters, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (iters) *iters = it;
+  return DEM_OK;
+}
+
 int dem_get_contacts(dem_ctx *c, int32_t *count, int32_t *partner, double *xi) {
   if (!c || !count || !partner || !xi) return DEM_EINVAL;
   int s = sync_all(c);
@@ -978,6 +1030,7 @@ int64_t dem_last_launch_count(dem_ctx *c) { return c ? c->launches : 0; }
 
 int dem_set_gas(dem_ctx *c, const dem_gas *g) {
   if (!c || !g || !g->Y || !g->T) return DEM_EINVAL;
+  if (c->gas_solver) return DEM_EINVAL;   // the gas is solved here
   int s = poll(c, false);
   if (s != DEM_OK) return s;
   const size_t nc = (size_t)c->ncells;
@@ -1177,7 +1230,9 @@ int dem_autotune(dem_ctx *c, int32_t n_steps) {
 
 int dem_adjoint(dem_ctx *c, int32_t n_steps, int32_t ckpt_every, double *J, double *grad) {
   if (!c || !J || n_steps < 0 || ckpt_every < 1) return DEM_EINVAL;
-  if (c->any_rad || c->any_cond) return DEM_EINVAL;   // radiation and conduction couple the parcels; the map is per parcel
+  // radiation and conduction couple the parcels (the map is per parcel); the gas solver
+  // couples them through the gas
+  if (c->any_rad || c->any_cond || c->gas_solver) return DEM_EINVAL;
   int s = sync_all(c);
   if (s != DEM_OK) return s;
   return DEM_DISPATCH(c, run_adjoint, c, n_steps, ckpt_every, J, grad);
@@ -1193,7 +1248,7 @@ int dem_adjoint_obs(dem_ctx *c, int32_t n_steps, int32_t ckpt_every, int32_t n_o
   if (weights)
     for (int k = 0; k < n_obs * c->nbeds; ++k)
       if (!std::isfinite(weights[k])) return DEM_EINVAL;
-  if (c->any_rad || c->any_cond) return DEM_EINVAL;
+  if (c->any_rad || c->any_cond || c->gas_solver) return DEM_EINVAL;
   int s = sync_all(c);
   if (s != DEM_OK) return s;
   std::vector<int> st(obs_steps, obs_steps + n_obs);

@@ -1072,10 +1072,11 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
   g.rho = gv[GP_RHO]; g.mu = gv[GP_MU]; g.lam = gv[GP_LAM]; g.cp = gv[GP_CP]; g.x = gv[GP_X];
   g.Dm = gv[GP_DM]; g.sc13 = gv[GP_SC13]; g.pr13 = gv[GP_PR13]; g.epow = gv[GP_EPOW];
   g.D = ore ? gv[GP_D1] : gv[GP_D0]; g.uz = gv[GP_UZ]; g.eps = gv[GP_EPS]; g.T = gv[GP_TG];
+  g.ux = gv[GP_UX]; g.uy = gv[GP_UY];
   const R dc = bp.k * d;
   const R Vp = (R)(kPI / 6.0) * dc * dc * dc;
   const R r = (R)0.5 * dc;
-  const R sv[3] = {-vh[0], -vh[1], g.uz - vh[2]};
+  const R sv[3] = {g.ux - vh[0], g.uy - vh[1], g.uz - vh[2]};
   const R slip = sqrt(sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]);
   const R Re = fdiv<R>(g.rho * g.eps * d * slip, g.mu);
   const R re02 = pos_pow(Re, (R)0.2);
@@ -1175,8 +1176,7 @@ __device__ __forceinline__ void store_props(StepView<P> &V, long long c, const C
   R r[GP_STRIDE];
   r[GP_RHO] = p.rho; r[GP_MU] = p.mu; r[GP_LAM] = p.lam; r[GP_CP] = p.cp; r[GP_X] = p.x; r[GP_DM] = p.Dm;
   r[GP_SC13] = p.sc13; r[GP_PR13] = p.pr13; r[GP_EPOW] = p.epow; r[GP_D0] = p.D[0]; r[GP_D1] = p.D[1];
-  r[GP_UZ] = p.uz; r[GP_EPS] = p.eps; r[GP_TG] = p.T;
-  r[GP_N] = (R)0; r[GP_N + 1] = (R)0;
+  r[GP_UZ] = p.uz; r[GP_EPS] = p.eps; r[GP_TG] = p.T; r[GP_UX] = p.ux; r[GP_UY] = p.uy;
   // the record in vector stores (a warp writes whole sectors)
   if constexpr (sizeof(R) == 4) {
     float4 *q = reinterpret_cast<float4 *>(V.gp + (size_t)c * GP_STRIDE);

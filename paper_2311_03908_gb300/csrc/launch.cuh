@@ -147,6 +147,51 @@ int enqueue_binning(dem_ctx *c, int drift) {
   return (int)cudaPeekAtLastError();
 }
 
+// The gas solver's kernels of one step (beds with DEM_GAS_SOLVER), in place of k_cells: on
+// coupling steps the cell sums and coefficients, the momentum predictor, the pressure
+// equation, the cooperative conjugate-gradient solve, the projection and the species and
+// energy update; on the other steps all but the last return at once and the last copies
+// the state.
+template <class P>
+int enqueue_gas_solve(dem_ctx *c, StepView<P> &V, bool pdl) {
+  cudaStream_t st = c->st;
+  const GasView &S = c->gsv;
+  const long long nf = S.nfx + S.nfy + S.nfz;
+  int ps = prof_begin(c, "k_gs_coeffs");
+  launch_k(pdl, k_gs_coeffs<P>, grid_for(c->ncells, 256), 256, st, V, S);
+  prof_end(c, ps);
+  ps = prof_begin(c, "k_gs_predict");
+  launch_k(pdl, k_gs_predict<P>, grid_for(nf, 256), 256, st, V, S);
+  prof_end(c, ps);
+  ps = prof_begin(c, "k_gs_rhs");
+  launch_k(pdl, k_gs_rhs<P>, grid_for(c->ncells, 256), 256, st, V, S);
+  prof_end(c, ps);
+  ps = prof_begin(c, "k_gs_cg");
+  {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c->gs_grid);
+    cfg.blockDim = dim3(GS_CG_BLOCK);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k_gs_cg<P>, (const DevBed *)c->dbeds, (const int *)c->cell_bed,
+                           (const long long *)c->step_ctr, c->ncells, S) != cudaSuccess)
+      return -1;
+  }
+  prof_end(c, ps);
+  ps = prof_begin(c, "k_gs_correct");
+  k_gs_correct<P><<<grid_for(nf + c->ncells, 256), 256, 0, st>>>(V, S);
+  prof_end(c, ps);
+  ps = prof_begin(c, "k_gs_scalars");
+  k_gs_scalars<P><<<grid_for(c->ncells, 256), 256, 0, st>>>(V, S);
+  prof_end(c, ps);
+  c->launches += 6;
+  return (int)cudaPeekAtLastError();
+}
+
 template <class P>
 int enqueue_steps(dem_ctx *c, int nsteps) {
   cudaStream_t st = c->st;
@@ -190,11 +235,17 @@ int enqueue_steps(dem_ctx *c, int nsteps) {
     if (c->any_rad) launch_k(pdl && !waited, k_gas_particle<P, true>, grid_for(c->n, c->bs_gp), c->bs_gp, st, V);
     else launch_k(pdl && !waited, k_gas_particle<P, false>, grid_for(c->n, c->bs_gp), c->bs_gp, st, V);
     prof_end(c, ps);
-    ps = prof_begin(c, "k_cells");
-    launch_k(pdl, k_cells<P>, grid_for(c->ncells, c->bs_cells), c->bs_cells, st, V, 0);
-    prof_end(c, ps);
+    if (c->gas_solver) {
+      e = enqueue_gas_solve<P>(c, V, pdl);
+      if (e) return e;
+    } else {
+      ps = prof_begin(c, "k_cells");
+      launch_k(pdl, k_cells<P>, grid_for(c->ncells, c->bs_cells), c->bs_cells, st, V, 0);
+      prof_end(c, ps);
+      ++c->launches;
+    }
     launch_k(pdl, k_step_counter, 1, 1, st, c->step_ctr, c->rebuild, c->use_lists, c->nwork, c->restore_every);
-    c->launches += 6;
+    c->launches += 5;
     e = (int)cudaPeekAtLastError();
     if (e) return e;
     c->cur = 1 - c->cur;
@@ -264,6 +315,29 @@ int enqueue_gas_set(dem_ctx *c, const double *Y, const double *T, cudaStream_t s
   return (int)cudaPeekAtLastError();
 }
 
+// the solved beds' initial flow and property records (after enqueue_init)
+template <class P>
+int enqueue_gas_solver_init(dem_ctx *c) {
+  StepView<P> V = make_view<P>(c, false);
+  const GasView &S = c->gsv;
+  const long long nf = S.nfx + S.nfy + S.nfz;
+  k_gs_init_faces<P><<<grid_for(nf + c->ncells, 256), 256, 0, c->st>>>(V, S);
+  k_gs_init_props<P><<<grid_for(c->ncells, 256), 256, 0, c->st>>>(V, S);
+  return (int)cudaPeekAtLastError();
+}
+
+template <class P>
+int enqueue_flow(dem_ctx *c, double *out_dev) {
+  StepView<P> V = make_view<P>(c, false);
+  k_gs_flow<P><<<grid_for(c->ncells, 256), 256, 0, c->st>>>(V, c->gsv, c->gas_solver ? 1 : 0, out_dev);
+  return (int)cudaPeekAtLastError();
+}
+
+template <class P>
+int gas_cg_occupancy(int *blocks_per_sm) {
+  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_gs_cg<P>, GS_CG_BLOCK, 0);
+}
+
 // largest block each tunable kernel can launch with (registers per thread decide it)
 template <class P>
 int kernel_limits(int *lim) {
@@ -287,6 +361,9 @@ int kernel_limits(int *lim) {
   template int enqueue_scatter_diag<P>(dem_ctx *, double *);                            \
   template int enqueue_scatter_hist<P>(dem_ctx *, int *, int *, double *);              \
   template int enqueue_sources<P>(dem_ctx *);                                           \
-  template int enqueue_gas_set<P>(dem_ctx *, const double *, const double *, cudaStream_t);
+  template int enqueue_gas_set<P>(dem_ctx *, const double *, const double *, cudaStream_t); \
+  template int enqueue_gas_solver_init<P>(dem_ctx *);                                   \
+  template int enqueue_flow<P>(dem_ctx *, double *);                                    \
+  template int gas_cg_occupancy<P>(int *);
 
 }  // namespace dem
