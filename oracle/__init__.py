@@ -90,6 +90,7 @@ def lib():
         L.orc_adjoint.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_double, dp, dp]
         L.orc_adjoint.restype = C.c_int32
         L.orc_get_flow.argtypes = [C.c_void_p, dp]
+        L.orc_get_faces.argtypes = [C.c_void_p, C.c_int, dp, dp, dp]
         L.orc_pseudo_turbulence.argtypes = [C.c_double] * 5 + [dp, dp, C.c_double, dp]
         L.orc_adjoint_obs.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, ip, dp, dp, dp]
         L.orc_adjoint_obs.restype = C.c_int32
@@ -177,6 +178,7 @@ class Oracle:
         L = lib()
         self.n = bed.n
         self.nbeds = len(bed.beds)
+        self._grids = [(c.nx, c.ny, c.nz) for c in bed.beds]
         self._keep = []
         bv, bp = _d(np.stack([bed_vector(c) for c in bed.beds]))
         arrs = [bed.x, bed.y, bed.z, bed.vx, bed.vy, bed.vz, bed.d_real, bed.T,
@@ -236,6 +238,16 @@ class Oracle:
         out = np.zeros((self.ncells, 4))
         lib().orc_get_flow(self.h, out.ctypes.data_as(C.POINTER(C.c_double)))
         return out
+
+    def faces(self, b: int = 0):
+        """Face velocities of solved bed b, as arrays (nz, ny, nx+1), (nz, ny+1, nx), (nz+1, ny, nx)."""
+        nx, ny, nz = self._grids[b]
+        fu = np.zeros((nz, ny, nx + 1))
+        fv = np.zeros((nz, ny + 1, nx))
+        fw = np.zeros((nz + 1, ny, nx))
+        lib().orc_get_faces(self.h, b, fu.ctypes.data_as(C.POINTER(C.c_double)),
+                            fv.ctypes.data_as(C.POINTER(C.c_double)), fw.ctypes.data_as(C.POINTER(C.c_double)))
+        return fu, fv, fw
 
     def deposits(self) -> np.ndarray:
         out = np.zeros((self.ncells, NDEP))

@@ -792,9 +792,13 @@ void deposit_volume_and_eps(Oracle &o) {
 // of eqs (3-28)..(3-37). Readings (the paper solves the gas with OpenFOAM's schemes, Table 4):
 //   * staggered (MAC) grid on the gas cells: velocity components on the faces, scalars at
 //     the centres; explicit Euler in time, first-order upwind convection (Table 4 uses
-//     limitedLinear for velocity and species); an incremental pressure projection for the
-//     continuity constraint, in which the change of rho within a coupling step is neglected
-//     (d(eps rho)/dt = rho d eps/dt), solved by conjugate gradients;
+//     limitedLinear for velocity and species); species and energy first, with the mass
+//     fluxes of the last projection, which gives the new density rho'; then momentum and an
+//     incremental pressure projection for the continuity constraint with
+//     d(eps rho)/dt = (eps rho' - eps_old rho) / dt and rho' in the mass fluxes (the
+//     variable-density order: the oxygen the reactions add to the gas raises its density,
+//     instead of leaving as extra volume flow at the old density), solved by conjugate
+//     gradients; the inlet carries the inlet gas's density;
 //   * momentum: convection in non-conservative form, viscous stress as div(eps mu grad u)
 //     (the transpose and dilatation parts of eq (3-33) dropped), the divergence of the
 //     pseudo-turbulent stress by its normal components, gravity, the drag of eq (4-2) with
@@ -919,15 +923,105 @@ void gas_solve(Oracle &o, int b, const std::vector<GasProps> &gp, double dt) {
         }
         for (int a = 0; a < 3; ++a) { RT[3 * c + a] = pt_diag(t, a, false); AT[3 * c + a] = pt_diag(t, a, true); }
       }
-  // 1. momentum predictor on every face (eq (4-2))
+  // face mass flux (kg/s along +axis) of velocity u through a face of kind kd, with the cell
+  // densities r; the inlet carries the inlet gas (eps u = U_in at its density)
+  const double Yin[3] = {bd[ORC_B_Y_IN], bd[ORC_B_Y_IN + 1], bd[ORC_B_Y_IN + 2]};
+  const double rho_in = gas_props(Tin, Yin, p0).rho;
+  auto face_flux = [&](int a, int i, int j, int kk, int kd, double u, const std::vector<double> &r) -> double {
+    const int di = a == 0, dj = a == 1, dk = a == 2;
+    if (kd == 0) return 0.0;
+    if (kd == 2) return rho_in * Uin * Af[a];
+    const int64_t cP = g.cidx(i - di, j - dj, kk - dk);
+    if (kd == 3) return eps[cP] * r[cP] * u * Af[a];
+    const int64_t cN = g.cidx(i, j, kk);
+    return 0.5 * (eps[cP] + eps[cN]) * 0.5 * (r[cP] + r[cN]) * u * Af[a];
+  };
+  // 1. species (eq (4-9)) and energy (eq (4-6)) with the mass fluxes of the last projection
+  //    (the current face velocities, the old densities), then the new densities: the
+  //    continuity equation (eq (3-24)) then takes d(eps rho)/dt with them, so that the mass
+  //    the reactions add is carried as the density it raises and not as extra volume flow
+  std::vector<double> nxt(o.gas.begin() + off * ORC_NG, o.gas.begin() + (off + nc) * ORC_NG);
+  const double MH2 = kMj[0], MH2O = kMj[1];
+  std::vector<double> rhon(rho);
+  for (int kk = 0; kk < nz; ++kk)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        if (!g.fluid(i, j, kk)) continue;
+        const int64_t c = g.cidx(i, j, kk);
+        const double *gc = &o.gas[(off + c) * ORC_NG];
+        const double *dp = &o.dep[(off + c) * ORC_NDEP];
+        const GasProps &G = gp[off + c];
+        const double Y0 = gc[ORC_G_Y], Y1 = gc[ORC_G_Y + 1], T = gc[ORC_G_T];
+        double cY0 = 0.0, cY1 = 0.0, cT = 0.0, dY0 = 0.0, dY1 = 0.0, dT = 0.0;
+        for (int a = 0; a < 3; ++a) {
+          const int di = a == 0, dj = a == 1, dk = a == 2;
+          for (int side = 0; side < 2; ++side) {   // 0: low face, 1: high face
+            const int fi = i + side * di, fj = j + side * dj, fk = kk + side * dk;
+            const int kd = face_kind(g, a, fi, fj, fk);
+            const double F = kd == 0 ? 0.0 : face_flux(a, fi, fj, fk, kd, comp(a)[fidx(a, fi, fj, fk)], rho);
+            const double inflow = side == 0 ? F : -F;   // mass into the cell through this face
+            const int ni = i + (side ? di : -di), nj = j + (side ? dj : -dj), nk = kk + (side ? dk : -dk);
+            if (kd == 1) {
+              const int64_t cn = g.cidx(ni, nj, nk);
+              const double *gn = &o.gas[(off + cn) * ORC_NG];
+              if (inflow > 0.0) {
+                cY0 += inflow * (gn[ORC_G_Y] - Y0);
+                cY1 += inflow * (gn[ORC_G_Y + 1] - Y1);
+                cT += inflow * cp[c] * (gn[ORC_G_T] - T);
+              }
+              const double ef = 0.5 * (eps[c] + eps[cn]), rf = 0.5 * (rho[c] + rho[cn]);
+              const double Df = 0.5 * (Dm[c] + Dm[cn]) + 0.5 * (AT[3 * c + a] + AT[3 * cn + a]);
+              const double lf = 0.5 * (lam[c] + lam[cn]) + rf * 0.5 * (cp[c] + cp[cn]) * 0.5 * (AT[3 * c + a] + AT[3 * cn + a]);
+              dY0 += ef * rf * Df * Af[a] / h[a] * (gn[ORC_G_Y] - Y0);
+              dY1 += ef * rf * Df * Af[a] / h[a] * (gn[ORC_G_Y + 1] - Y1);
+              dT += ef * lf * Af[a] / h[a] * (gn[ORC_G_T] - T);
+            } else if (kd == 2) {                 // inlet gas
+              if (inflow > 0.0) {
+                cY0 += inflow * (Yin[0] - Y0);
+                cY1 += inflow * (Yin[1] - Y1);
+                cT += inflow * cp[c] * (Tin - T);
+              }
+            } else if (kd == 0) {                 // wall at the inlet temperature
+              dT += eps[c] * lam[c] * Af[a] / (0.5 * h[a]) * (Tin - T);
+            }                                     // outlet: zero gradient
+          }
+        }
+        const double m = eps[c] * rho[c] * V;
+        // eqs (4-8)..(4-11): H2 consumed at (M_H2 p / R)(x EQ - ES) with x = a Y_H2 (implicit in
+        // Y_H2), H2O produced at M_H2O / M_H2 times that; in the non-conservative form the
+        // net mass source takes Y (and c_p T) of the cell away
+        const double X = G.xp[0] + G.xp[1];
+        const double ax = X > 0.0 ? G.Mg / (MH2 * X) : 0.0;
+        const double C0 = MH2 * p0 * ax * dp[ORC_DEP_EQ] / kRg, C1 = MH2 * p0 * dp[ORC_DEP_ES] / kRg;
+        const double rq = MH2O / MH2 - 1.0;
+        const double Y0n = (m * Y0 / dt + cY0 + dY0 + C1 * (1.0 + Y0 * rq)) / (m / dt + C0 * (1.0 + Y0 * rq));
+        const double cons = C0 * Y0n - C1;                        // H2 consumed, kg/s
+        const double Mnet = rq * cons;                            // net gas mass source, kg/s
+        double Y0f = Y0n;
+        double Y1f = Y1 + dt / m * (cY1 + dY1 + MH2O / MH2 * cons - Y1 * Mnet);
+        Y0f = std::max(Y0f, 0.0);
+        Y1f = std::max(Y1f, 0.0);
+        double Y2f = std::max(1.0 - Y0f - Y1f, 0.0);
+        const double ys = Y0f + Y1f + Y2f;
+        double *nc_ = &nxt[c * ORC_NG];
+        nc_[ORC_G_Y] = Y0f / ys;
+        nc_[ORC_G_Y + 1] = Y1f / ys;
+        nc_[ORC_G_Y + 2] = Y2f / ys;
+        // energy: M_r of eq (3-39) with the species sources, M_rm of eq (3-38)
+        const double Mr = -(nasa_H(0, T) * (-cons) + nasa_H(1, T) * (MH2O / MH2 * cons));
+        const double Mrm = -dp[ORC_DEP_QRM];
+        const double mc = m * cp[c];
+        nc_[ORC_G_T] = (mc * T / dt + cT + dT + dp[ORC_DEP_HAT] + Mr + Mrm - T * cp[c] * Mnet) / (mc / dt + dp[ORC_DEP_HA]);
+        rhon[c] = gas_props(nc_[ORC_G_T], nc_ + ORC_G_Y, p0).rho;
+      }
+  // 2. momentum predictor on every face (eq (4-2)), with the old state's properties
   std::vector<double> Us[3] = {U, Vv, W};
-  auto fval = [&](int a, int i, int j, int kk, double self) -> double {
-    // a face value seen from a neighbouring face: open, inlet and outlet faces carry theirs,
-    // walls are at rest (no-slip ghost -self for a tangential neighbour is applied by the caller)
+  auto fval = [&](int a, int i, int j, int kk) -> double {
+    // a face value seen from a neighbouring face: open, inlet and outlet faces carry theirs;
+    // NaN for walls and faces off the grid (the caller applies the wall condition)
     const int nmax[3] = {nx + (a == 0), ny + (a == 1), nz + (a == 2)};
     if (i < 0 || j < 0 || kk < 0 || i >= nmax[0] || j >= nmax[1] || kk >= nmax[2]) return std::nan("");
     const int kd = face_kind(g, a, i, j, kk);
-    (void)self;
     return kd == 0 ? std::nan("") : comp(a)[fidx(a, i, j, kk)];
   };
   for (int a = 0; a < 3; ++a) {
@@ -959,7 +1053,7 @@ void gas_solve(Oracle &o, int b, const std::vector<GasProps> &gp, double dt) {
           double conv = 0.0, visc = 0.0;
           for (int bb = 0; bb < 3; ++bb) {
             const int ei = bb == 0, ej = bb == 1, ek = bb == 2;
-            double lo = fval(a, i - ei, j - ej, kk - ek, u0), hi = fval(a, i + ei, j + ej, kk + ek, u0);
+            double lo = fval(a, i - ei, j - ej, kk - ek), hi = fval(a, i + ei, j + ej, kk + ek);
             if (bb != a) {   // tangential neighbours: no-slip walls halfway between
               if (std::isnan(lo)) lo = -u0;
               if (std::isnan(hi)) hi = -u0;
@@ -979,8 +1073,10 @@ void gas_solve(Oracle &o, int b, const std::vector<GasProps> &gp, double dt) {
   for (int j = 0; j < ny; ++j)   // outlet faces: the face below
     for (int i = 0; i < nx; ++i)
       if (face_kind(g, 2, i, j, nz) == 3) Us[2][g.zf(i, j, nz)] = Us[2][g.zf(i, j, nz - 1)];
-  // 2. pressure correction (incremental projection): for each fluid cell
-  //    sum_f c_f (p''_nb - p''_P) = sum_f s_f eps_f rho_f u*_f A_f - V (M_P - rho_P (eps - eps_old) / dt)
+  // 3. pressure correction (incremental projection): for each fluid cell, with the new
+  //    densities in the mass fluxes,
+  //    sum_f c_f (p''_nb - p''_P) = sum_f s_f eps_f rho'_f u*_f A_f - V (M_P - (eps rho' - eps_old rho) / dt)
+  //    c_f = eps_f rho'_f beta_f A_f / h, beta_f = eps_f / (eps_f rho_f / dt + K_f) from eq (4-2)
   std::vector<double> M(nc, 0.0);
   for (int64_t c = 0; c < nc; ++c) {
     const double *dp = &o.dep[(off + c) * ORC_NDEP];
@@ -991,22 +1087,12 @@ void gas_solve(Oracle &o, int b, const std::vector<GasProps> &gp, double dt) {
     const int64_t cP = g.cidx(i - di, j - dj, kk - dk);
     if (kd == 3) {
       const double beta = eps[cP] / (eps[cP] * rho[cP] / dt + Kc[cP]);
-      return 2.0 * eps[cP] * rho[cP] * beta * Af[a] / h[a];
+      return 2.0 * eps[cP] * rhon[cP] * beta * Af[a] / h[a];
     }
     const int64_t cN = g.cidx(i, j, kk);
     const double ef = 0.5 * (eps[cP] + eps[cN]), rf = 0.5 * (rho[cP] + rho[cN]), Kf = 0.5 * (Kc[cP] + Kc[cN]);
     const double beta = ef / (ef * rf / dt + Kf);
-    return ef * rf * beta * Af[a] / h[a];
-  };
-  auto face_flux = [&](int a, int i, int j, int kk, int kd, const std::vector<double> *us) -> double {
-    const int di = a == 0, dj = a == 1, dk = a == 2;
-    if (kd == 0) return 0.0;
-    const int64_t f = fidx(a, i, j, kk);
-    if (kd == 2) { const int64_t cN = g.cidx(i, j, kk); return eps[cN] * rho[cN] * us[a][f] * Af[a]; }
-    const int64_t cP = g.cidx(i - di, j - dj, kk - dk);
-    if (kd == 3) return eps[cP] * rho[cP] * us[a][f] * Af[a];
-    const int64_t cN = g.cidx(i, j, kk);
-    return 0.5 * (eps[cP] + eps[cN]) * 0.5 * (rho[cP] + rho[cN]) * us[a][f] * Af[a];
+    return ef * 0.5 * (rhon[cP] + rhon[cN]) * beta * Af[a] / h[a];
   };
   std::vector<double> rhs(nc, 0.0), diagA(nc, 0.0);
   for (int kk = 0; kk < nz; ++kk)
@@ -1018,11 +1104,12 @@ void gas_solve(Oracle &o, int b, const std::vector<GasProps> &gp, double dt) {
         for (int a = 0; a < 3; ++a) {
           const int di = a == 0, dj = a == 1, dk = a == 2;
           const int kl = face_kind(g, a, i, j, kk), kh = face_kind(g, a, i + di, j + dj, kk + dk);
-          net += face_flux(a, i + di, j + dj, kk + dk, kh, Us) - face_flux(a, i, j, kk, kl, Us);
+          net += face_flux(a, i + di, j + dj, kk + dk, kh, Us[a][fidx(a, i + di, j + dj, kk + dk)], rhon) -
+                 face_flux(a, i, j, kk, kl, Us[a][fidx(a, i, j, kk)], rhon);
           if (kl == 1) dsum += face_c(a, i, j, kk, kl);
           if (kh == 1 || kh == 3) dsum += face_c(a, i + di, j + dj, kk + dk, kh);
         }
-        rhs[c] = net - V * (M[c] - rho[c] * (eps[c] - epso[c]) / dt);
+        rhs[c] = net - V * (M[c] - (eps[c] * rhon[c] - epso[c] * rho[c]) / dt);
         diagA[c] = dsum;
       }
   // apply L p = sum_f c_f (p_nb - p_P) (outlet neighbours at 0)
@@ -1089,80 +1176,6 @@ void gas_solve(Oracle &o, int b, const std::vector<GasProps> &gp, double dt) {
   }
   for (int64_t c = 0; c < nc; ++c) P[c] += x[c];
   U = Us[0]; Vv = Us[1]; W = Us[2];
-  // 3. species (eq (4-9)) and energy (eq (4-6)) with the new mass fluxes
-  std::vector<double> nxt(o.gas.begin() + off * ORC_NG, o.gas.begin() + (off + nc) * ORC_NG);
-  const double Yin[3] = {bd[ORC_B_Y_IN], bd[ORC_B_Y_IN + 1], bd[ORC_B_Y_IN + 2]};
-  const double MH2 = kMj[0], MH2O = kMj[1];
-  for (int kk = 0; kk < nz; ++kk)
-    for (int j = 0; j < ny; ++j)
-      for (int i = 0; i < nx; ++i) {
-        if (!g.fluid(i, j, kk)) continue;
-        const int64_t c = g.cidx(i, j, kk);
-        const double *gc = &o.gas[(off + c) * ORC_NG];
-        const double *dp = &o.dep[(off + c) * ORC_NDEP];
-        const GasProps &G = gp[off + c];
-        const double Y0 = gc[ORC_G_Y], Y1 = gc[ORC_G_Y + 1], T = gc[ORC_G_T];
-        double cY0 = 0.0, cY1 = 0.0, cT = 0.0, dY0 = 0.0, dY1 = 0.0, dT = 0.0;
-        for (int a = 0; a < 3; ++a) {
-          const int di = a == 0, dj = a == 1, dk = a == 2;
-          for (int side = 0; side < 2; ++side) {   // 0: low face, 1: high face
-            const int fi = i + side * di, fj = j + side * dj, fk = kk + side * dk;
-            const int kd = face_kind(g, a, fi, fj, fk);
-            const double F = face_flux(a, fi, fj, fk, kd, Us);
-            const double inflow = side == 0 ? F : -F;   // mass into the cell through this face
-            const int ni = i + (side ? di : -di), nj = j + (side ? dj : -dj), nk = kk + (side ? dk : -dk);
-            if (kd == 1) {
-              const int64_t cn = g.cidx(ni, nj, nk);
-              const double *gn = &o.gas[(off + cn) * ORC_NG];
-              if (inflow > 0.0) {
-                cY0 += inflow * (gn[ORC_G_Y] - Y0);
-                cY1 += inflow * (gn[ORC_G_Y + 1] - Y1);
-                cT += inflow * cp[c] * (gn[ORC_G_T] - T);
-              }
-              const double ef = 0.5 * (eps[c] + eps[cn]), rf = 0.5 * (rho[c] + rho[cn]);
-              const double Df = 0.5 * (Dm[c] + Dm[cn]) + 0.5 * (AT[3 * c + a] + AT[3 * cn + a]);
-              const double lf = 0.5 * (lam[c] + lam[cn]) + rf * 0.5 * (cp[c] + cp[cn]) * 0.5 * (AT[3 * c + a] + AT[3 * cn + a]);
-              dY0 += ef * rf * Df * Af[a] / h[a] * (gn[ORC_G_Y] - Y0);
-              dY1 += ef * rf * Df * Af[a] / h[a] * (gn[ORC_G_Y + 1] - Y1);
-              dT += ef * lf * Af[a] / h[a] * (gn[ORC_G_T] - T);
-            } else if (kd == 2) {                 // inlet gas
-              if (inflow > 0.0) {
-                cY0 += inflow * (Yin[0] - Y0);
-                cY1 += inflow * (Yin[1] - Y1);
-                cT += inflow * cp[c] * (Tin - T);
-              }
-            } else if (kd == 0) {                 // wall at the inlet temperature
-              dT += eps[c] * lam[c] * Af[a] / (0.5 * h[a]) * (Tin - T);
-            }                                     // outlet: zero gradient
-          }
-        }
-        const double m = eps[c] * rho[c] * V;
-        // eqs (4-8)..(4-11): H2 consumed at (M_H2 p / R)(x EQ - ES) with x = a Y_H2 (implicit in
-        // Y_H2), H2O produced at M_H2O / M_H2 times that; in the non-conservative form the
-        // net mass source takes Y (and c_p T) of the cell away
-        const double X = G.xp[0] + G.xp[1];
-        const double ax = X > 0.0 ? G.Mg / (MH2 * X) : 0.0;
-        const double C0 = MH2 * p0 * ax * dp[ORC_DEP_EQ] / kRg, C1 = MH2 * p0 * dp[ORC_DEP_ES] / kRg;
-        const double rq = MH2O / MH2 - 1.0;
-        const double Y0n = (m * Y0 / dt + cY0 + dY0 + C1 * (1.0 + Y0 * rq)) / (m / dt + C0 * (1.0 + Y0 * rq));
-        const double cons = C0 * Y0n - C1;                        // H2 consumed, kg/s
-        const double Mnet = rq * cons;                            // net gas mass source, kg/s
-        double Y0f = Y0n;
-        double Y1f = Y1 + dt / m * (cY1 + dY1 + MH2O / MH2 * cons - Y1 * Mnet);
-        Y0f = std::max(Y0f, 0.0);
-        Y1f = std::max(Y1f, 0.0);
-        double Y2f = std::max(1.0 - Y0f - Y1f, 0.0);
-        const double ys = Y0f + Y1f + Y2f;
-        nxt[c * ORC_NG + ORC_G_Y] = Y0f / ys;
-        nxt[c * ORC_NG + ORC_G_Y + 1] = Y1f / ys;
-        nxt[c * ORC_NG + ORC_G_Y + 2] = Y2f / ys;
-        // energy: M_r of eq (3-39) with the species sources, M_rm of eq (3-38)
-        const double Mr = -(nasa_H(0, T) * (-cons) + nasa_H(1, T) * (MH2O / MH2 * cons));
-        const double Mrm = -dp[ORC_DEP_QRM];
-        const double mc = m * cp[c];
-        nxt[c * ORC_NG + ORC_G_T] = (mc * T / dt + cT + dT + dp[ORC_DEP_HAT] + Mr + Mrm - T * cp[c] * Mnet) /
-                                    (mc / dt + dp[ORC_DEP_HA]);
-      }
   for (int64_t c = 0; c < nc; ++c) nxt[c * ORC_NG + ORC_G_EPS] = eps[c];
   std::copy(nxt.begin(), nxt.end(), o.gas.begin() + off * ORC_NG);
 }
@@ -1958,6 +1971,14 @@ void orc_pseudo_turbulence(double eps, double rho, double mu, double lam, double
   out8[0] = t.Rpa; out8[1] = t.Rpe; out8[2] = t.apa; out8[3] = t.ape;
   for (int q = 0; q < 3; ++q) out8[4 + q] = t.s[q];
   out8[7] = 0.0;
+}
+
+void orc_get_faces(void *h, int b, double *fu, double *fv, double *fw) {
+  Oracle *o = (Oracle *)h;
+  if (b < 0 || b >= o->nb) return;
+  std::copy(o->fu[b].begin(), o->fu[b].end(), fu);
+  std::copy(o->fv[b].begin(), o->fv[b].end(), fv);
+  std::copy(o->fw[b].begin(), o->fw[b].end(), fw);
 }
 
 void orc_get_flow(void *h, double *out) {

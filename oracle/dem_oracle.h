@@ -63,6 +63,9 @@ enum {
  * the cell-centre velocity (3) and the pressure relative to p0 */
 enum { ORC_V_U = 0, ORC_V_P = 3, ORC_NV };
 void orc_get_flow(void *h, double *out);
+// face velocities of a solved bed b: (nx+1) ny nz x-faces, nx (ny+1) nz y-faces, nx ny (nz+1)
+// z-faces, x fastest (zeros before the first step of a bed that is not solved)
+void orc_get_faces(void *h, int b, double *fu, double *fv, double *fw);
 /* pseudo-turbulence closures of one cell (eqs (3-28)..(3-37)): out8 = R_pa, R_pe, alpha_pa,
  * alpha_pe, slip direction (3), 0 */
 void orc_pseudo_turbulence(double eps, double rho, double mu, double lam, double cp, const double *ug,
