@@ -793,12 +793,12 @@ void deposit_volume_and_eps(Oracle &o) {
 //   * staggered (MAC) grid on the gas cells: velocity components on the faces, scalars at
 //     the centres; explicit Euler in time, first-order upwind convection (Table 4 uses
 //     limitedLinear for velocity and species); species and energy first, with the mass
-//     fluxes of the last projection, which gives the new density rho'; then momentum and an
-//     incremental pressure projection for the continuity constraint with
-//     d(eps rho)/dt = (eps rho' - eps_old rho) / dt and rho' in the mass fluxes (the
-//     variable-density order: the oxygen the reactions add to the gas raises its density,
-//     instead of leaving as extra volume flow at the old density), solved by conjugate
-//     gradients; the inlet carries the inlet gas's density;
+//     fluxes of the last projection; continuity in the low-Mach divergence form
+//     div(eps u) = -d eps/dt + M / rho - eps D ln(rho)/Dt (eq (3-24) with rho = p M_g / (R T)
+//     at fixed p0 and the material rates of the species and energy update, so that the
+//     oxygen the reactions add to the gas raises its density instead of leaving as extra
+//     volume flow); then momentum and an incremental pressure projection for that
+//     divergence, solved by conjugate gradients; the inlet carries the inlet gas's density;
 //   * momentum: convection in non-conservative form, viscous stress as div(eps mu grad u)
 //     (the transpose and dilatation parts of eq (3-33) dropped), the divergence of the
 //     pseudo-turbulent stress by its normal components, gravity, the drag of eq (4-2) with
@@ -937,12 +937,16 @@ void gas_solve(Oracle &o, int b, const std::vector<GasProps> &gp, double dt) {
     return 0.5 * (eps[cP] + eps[cN]) * 0.5 * (r[cP] + r[cN]) * u * Af[a];
   };
   // 1. species (eq (4-9)) and energy (eq (4-6)) with the mass fluxes of the last projection
-  //    (the current face velocities, the old densities), then the new densities: the
-  //    continuity equation (eq (3-24)) then takes d(eps rho)/dt with them, so that the mass
-  //    the reactions add is carried as the density it raises and not as extra volume flow
+  //    (the current face velocities, the old densities); from their non-advective rates the
+  //    velocity divergence that continuity (eq (3-24)) requires of the new flow: with
+  //    rho = p M_g / (R T) (eq (3-53)) at fixed p0, d(eps rho)/dt + div(eps rho u) = M reads
+  //    div(eps u) = -d eps/dt + M / rho - eps D ln(rho)/Dt, and
+  //    D ln(rho)/Dt = -M_g sum_j (DY_j/Dt) / M_j - (DT/Dt) / T, DY_j/Dt and DT/Dt the changes
+  //    of the update less its convective part (the low-Mach divergence form: an equimolar
+  //    reaction, H2 to H2O, leaves the volume flow unchanged)
   std::vector<double> nxt(o.gas.begin() + off * ORC_NG, o.gas.begin() + (off + nc) * ORC_NG);
   const double MH2 = kMj[0], MH2O = kMj[1];
-  std::vector<double> rhon(rho);
+  std::vector<double> divg(nc, 0.0);
   for (int kk = 0; kk < nz; ++kk)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
@@ -1007,12 +1011,21 @@ void gas_solve(Oracle &o, int b, const std::vector<GasProps> &gp, double dt) {
         nc_[ORC_G_Y] = Y0f / ys;
         nc_[ORC_G_Y + 1] = Y1f / ys;
         nc_[ORC_G_Y + 2] = Y2f / ys;
-        // energy: M_r of eq (3-39) with the species sources, M_rm of eq (3-38)
-        const double Mr = -(nasa_H(0, T) * (-cons) + nasa_H(1, T) * (MH2O / MH2 * cons));
+        // energy: M_r of eq (3-39) with the parcels' species sources (as the prescribed update
+        // takes it) and M_rm of eq (3-38): together the sensible enthalpy the species bring
+        // from the parcels' temperature, so the temperature form needs no further mass-source
+        // term
+        const double Mr = -(nasa_H(0, T) * dp[ORC_DEP_SH2] + nasa_H(1, T) * dp[ORC_DEP_SH2O]);
         const double Mrm = -dp[ORC_DEP_QRM];
         const double mc = m * cp[c];
-        nc_[ORC_G_T] = (mc * T / dt + cT + dT + dp[ORC_DEP_HAT] + Mr + Mrm - T * cp[c] * Mnet) / (mc / dt + dp[ORC_DEP_HA]);
-        rhon[c] = gas_props(nc_[ORC_G_T], nc_ + ORC_G_Y, p0).rho;
+        nc_[ORC_G_T] = (mc * T / dt + cT + dT + dp[ORC_DEP_HAT] + Mr + Mrm) / (mc / dt + dp[ORC_DEP_HA]);
+        const double Y2 = gc[ORC_G_Y + 2];
+        const double DY0 = (nc_[ORC_G_Y] - Y0) / dt - cY0 / m, DY1 = (nc_[ORC_G_Y + 1] - Y1) / dt - cY1 / m;
+        const double DY2 = (nc_[ORC_G_Y + 2] - Y2) / dt + (cY0 + cY1) / m;   // N2 carried in: -(cY0 + cY1)
+        const double DT = (nc_[ORC_G_T] - T) / dt - cT / mc;
+        const double Dlnrho = -G.Mg * (DY0 / kMj[0] + DY1 / kMj[1] + DY2 / kMj[2]) - DT / T;
+        // M of eq (3-25) as the species update takes it (the H2 sink semi-implicit, eq (4-9))
+        divg[c] = -(eps[c] - epso[c]) / dt + Mnet / (V * rho[c]) - eps[c] * Dlnrho;
       }
   // 2. momentum predictor on every face (eq (4-2)), with the old state's properties
   std::vector<double> Us[3] = {U, Vv, W};
@@ -1073,26 +1086,28 @@ void gas_solve(Oracle &o, int b, const std::vector<GasProps> &gp, double dt) {
   for (int j = 0; j < ny; ++j)   // outlet faces: the face below
     for (int i = 0; i < nx; ++i)
       if (face_kind(g, 2, i, j, nz) == 3) Us[2][g.zf(i, j, nz)] = Us[2][g.zf(i, j, nz - 1)];
-  // 3. pressure correction (incremental projection): for each fluid cell, with the new
-  //    densities in the mass fluxes,
-  //    sum_f c_f (p''_nb - p''_P) = sum_f s_f eps_f rho'_f u*_f A_f - V (M_P - (eps rho' - eps_old rho) / dt)
-  //    c_f = eps_f rho'_f beta_f A_f / h, beta_f = eps_f / (eps_f rho_f / dt + K_f) from eq (4-2)
-  std::vector<double> M(nc, 0.0);
-  for (int64_t c = 0; c < nc; ++c) {
-    const double *dp = &o.dep[(off + c) * ORC_NDEP];
-    M[c] = (dp[ORC_DEP_SH2] + dp[ORC_DEP_SH2O]) / V;   // eq (3-25), kg/m^3/s
-  }
+  // 3. pressure correction (incremental projection): for each fluid cell
+  //    sum_f c_f (p''_nb - p''_P) = sum_f s_f eps_f u*_f A_f - V div(eps u)
+  //    c_f = eps_f beta_f A_f / h, beta_f = eps_f / (eps_f rho_f / dt + K_f) from eq (4-2)
+  auto vflux = [&](int a, int i, int j, int kk, int kd, double u) -> double {   // eps u A of a face
+    const int di = a == 0, dj = a == 1, dk = a == 2;
+    if (kd == 0) return 0.0;
+    if (kd == 2) return Uin * Af[a];
+    const int64_t cP = g.cidx(i - di, j - dj, kk - dk);
+    if (kd == 3) return eps[cP] * u * Af[a];
+    return 0.5 * (eps[cP] + eps[g.cidx(i, j, kk)]) * u * Af[a];
+  };
   auto face_c = [&](int a, int i, int j, int kk, int kd) -> double {   // c_f of an open or outlet face
     const int di = a == 0, dj = a == 1, dk = a == 2;
     const int64_t cP = g.cidx(i - di, j - dj, kk - dk);
     if (kd == 3) {
       const double beta = eps[cP] / (eps[cP] * rho[cP] / dt + Kc[cP]);
-      return 2.0 * eps[cP] * rhon[cP] * beta * Af[a] / h[a];
+      return 2.0 * eps[cP] * beta * Af[a] / h[a];
     }
     const int64_t cN = g.cidx(i, j, kk);
     const double ef = 0.5 * (eps[cP] + eps[cN]), rf = 0.5 * (rho[cP] + rho[cN]), Kf = 0.5 * (Kc[cP] + Kc[cN]);
     const double beta = ef / (ef * rf / dt + Kf);
-    return ef * 0.5 * (rhon[cP] + rhon[cN]) * beta * Af[a] / h[a];
+    return ef * beta * Af[a] / h[a];
   };
   std::vector<double> rhs(nc, 0.0), diagA(nc, 0.0);
   for (int kk = 0; kk < nz; ++kk)
@@ -1104,12 +1119,12 @@ void gas_solve(Oracle &o, int b, const std::vector<GasProps> &gp, double dt) {
         for (int a = 0; a < 3; ++a) {
           const int di = a == 0, dj = a == 1, dk = a == 2;
           const int kl = face_kind(g, a, i, j, kk), kh = face_kind(g, a, i + di, j + dj, kk + dk);
-          net += face_flux(a, i + di, j + dj, kk + dk, kh, Us[a][fidx(a, i + di, j + dj, kk + dk)], rhon) -
-                 face_flux(a, i, j, kk, kl, Us[a][fidx(a, i, j, kk)], rhon);
+          net += vflux(a, i + di, j + dj, kk + dk, kh, Us[a][fidx(a, i + di, j + dj, kk + dk)]) -
+                 vflux(a, i, j, kk, kl, Us[a][fidx(a, i, j, kk)]);
           if (kl == 1) dsum += face_c(a, i, j, kk, kl);
           if (kh == 1 || kh == 3) dsum += face_c(a, i + di, j + dj, kk + dk, kh);
         }
-        rhs[c] = net - V * (M[c] - (eps[c] * rhon[c] - epso[c] * rho[c]) / dt);
+        rhs[c] = net - V * divg[c];
         diagA[c] = dsum;
       }
   // apply L p = sum_f c_f (p_nb - p_P) (outlet neighbours at 0)
