@@ -78,11 +78,15 @@ enum { DEM_PREC_FP64 = 0, DEM_PREC_SPLIT = 1, DEM_PREC_SPLIT_KAHAN = 2 };
  * stress and heat flux of eqs (3-28)..(3-37). Readings (the paper solves this with a
  * finite-volume code and gives no discretisation): a staggered grid with the velocity
  * components on the cell faces, explicit Euler in dt_CFD = n dt_DEM, first-order upwind
- * convection, an incremental pressure projection solved by Jacobi-preconditioned conjugate
+ * convection; species and energy first, with the mass fluxes of the last projection, which
+ * gives the new density rho' (eq (3-53)); then the momentum predictor and an incremental
+ * pressure projection in which continuity takes d(eps rho)/dt = (eps rho' - eps_old rho)/dt
+ * and rho' in the mass fluxes (so the oxygen the reactions add raises the gas density
+ * instead of leaving as extra volume flow), solved by Jacobi-preconditioned conjugate
  * gradients to a relative residual of 1e-12; immersed-boundary cells and the box sides are
  * no-slip walls held at T_in (Table 3 lists the wall and inlet temperatures equal); a
  * z-face below a fluid cell whose lower neighbour is not fluid carries the inlet gas
- * (eps u = U_in, Y_in, T_in); z-faces on top of the box are an outlet at p0 with zero
+ * (eps u = U_in at the inlet gas's density, Y_in, T_in); z-faces on top of the box are an outlet at p0 with zero
  * gradient; the pseudo-turbulent stress enters by its normal components and the heat flux
  * by the diagonal of alpha_PT, both rotated to the slip direction of the cell's drag-
  * weighted parcel velocity, with Re_m capped at 100 and eps_p at 0.5; H2O follows the H2
@@ -300,11 +304,18 @@ int dem_get_diag(dem_ctx *c, double *out_host);
  *   [7] neighbour-list skin in thousandths of the bed's largest parcel diameter (1..1000);
  *   [8] re-store the parcel state in cell order at every k-th neighbour-list build (1..64;
  *       1 = every build): between re-stores the records stay where they are and the
- *       search reads them through the sort's permutation.
+ *       search reads them through the sort's permutation;
+ *   [9] preconditioner of the gas solver's pressure equation (DEM_GAS_SOLVER): 0 = Jacobi,
+ *       1 or 2 = a multigrid V-cycle with that many damped-Jacobi sweeps before and after
+ *       each coarse correction (default 2; Galerkin coarse levels of 2 x 2 x 2 aggregates,
+ *       down to one cell per bed); the solve converges to the same tolerance either way;
+ *   [10] weight of the multigrid coarse correction in percent (50..200, default 150: the
+ *        piecewise-constant aggregates' correction falls short, and over-correcting it
+ *        halves the iterations).
  * dem_set_tuning validates every value (DEM_EINVAL, nothing changed), drops captured graphs
  * and makes the next step rebuild the neighbour lists; results can then differ from an
  * untuned run in the last bits (order of the force sums), never in the pair sets. */
-enum { DEM_NTUNE = 9 };
+enum { DEM_NTUNE = 11 };
 int dem_get_tuning(dem_ctx *c, int32_t *out);
 int dem_set_tuning(dem_ctx *c, const int32_t *in);
 

@@ -21,9 +21,9 @@ DEM_MAX_CONTACTS = 24
 DEM_NSTATE, DEM_NGAS, DEM_NDEP, DEM_NDIAG, DEM_NFLOW = 20, 6, 14, 35, 4
 DEM_NOALLOC_MAX_PARCELS = 8388608
 PRECISIONS = {"fp64": DEM_PREC_FP64, "split": DEM_PREC_SPLIT, "split_kahan": DEM_PREC_SPLIT_KAHAN}
-DEM_NTUNE = 9
+DEM_NTUNE = 11
 TUNING_KEYS = ("neighbour_lists", "bs_key", "bs_restore", "bs_search", "bs_contacts", "bs_gas_particle", "bs_cells",
-               "skin_permille", "restore_every")
+               "skin_permille", "restore_every", "gas_mg_sweeps", "gas_mg_weight_pct")
 
 STATE_ROWS = ["x", "y", "z", "vx", "vy", "vz", "wx", "wy", "wz", "T", "m_h", "m_m", "m_w", "m_fe",
               "ax", "ay", "az", "alx", "aly", "alz"]

@@ -89,6 +89,14 @@ struct dem_ctx {
   bool gas_solver = false;         // every bed has DEM_GAS_SOLVER: the gas kernels replace k_cells
   dem::GasView gsv = {};           // the solver's arrays (in the arena)
   int gs_grid = 1;                 // blocks of the cooperative pressure solve (all co-resident)
+  // multigrid levels of the pressure preconditioner: per level the arrays (level 0: the gas
+  // grid's coefficient rows and CG vectors), per level and bed the dims and first cell
+  std::vector<dem::GsLevel> hlev;
+  std::vector<dem::GsLevelBed> hlb;
+  std::vector<int *> dlbed;        // bed of each cell, levels >= 1 (arena)
+  std::vector<int *> dlpar;        // the coarse cell holding each cell, levels below the coarsest (arena)
+  dem::GsLevel *dlev = nullptr;
+  dem::GsLevelBed *dlb = nullptr;
   char *qc = nullptr;              // contact conduction heat of each parcel in contact (form's type)
   std::map<std::tuple<int, int, int>, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;
   std::map<std::tuple<int, int, int>, long long> graph_launches;

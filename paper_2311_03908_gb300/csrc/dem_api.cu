@@ -429,6 +429,43 @@ void layout(dem_ctx *c, Bump &m) {
     S.cg_iters = m.take<int>(1);
     S.dep = m.take<double>(C * SR_N);
     S.bpd = c->dbp_d;
+    // multigrid levels
+    const int nl = (int)c->hlev.size();
+    c->dlbed.assign(nl, nullptr);
+    for (int l = 1; l < nl; ++l) {
+      GsLevel &Lv = c->hlev[l];
+      const size_t n = (size_t)Lv.n;
+      Lv.L = m.take<double>(3 * n);
+      Lv.diag = m.take<double>(n); Lv.out = m.take<double>(n); Lv.dinv = m.take<double>(n);
+      Lv.b = m.take<double>(n); Lv.xa = m.take<double>(n); Lv.xb = m.take<double>(n);
+      c->dlbed[l] = m.take<int>(n);
+      Lv.bed = c->dlbed[l];
+    }
+    c->dlpar.assign(nl, nullptr);
+    for (int l = 0; l + 1 < nl; ++l) {
+      c->dlpar[l] = m.take<int>((size_t)(l == 0 ? c->ncells : c->hlev[l].n));
+      c->hlev[l].parent = c->dlpar[l];
+    }
+    if (nl > 0) {
+      GsLevel &L0 = c->hlev[0];
+      L0.n = c->ncells;
+      L0.L = S.co + (size_t)GC_L * C; L0.diag = S.co + (size_t)GC_DIAG * C; L0.out = S.co + (size_t)GC_OUT * C;
+      L0.dinv = S.co + (size_t)GC_DINV * C;
+      L0.b = S.r; L0.xa = S.Ap; L0.xb = S.z; L0.bed = c->cell_bed;
+    }
+    for (int l = 0; l < nl; ++l) {   // uniform dims per level
+      const GsLevelBed *g = &c->hlb[(size_t)l * c->nbeds];
+      bool uni = true;
+      for (int b = 1; b < c->nbeds; ++b) uni = uni && g[b].nx == g[0].nx && g[b].ny == g[0].ny && g[b].nz == g[0].nz;
+      c->hlev[l].ux = uni ? g[0].nx : 0;
+      c->hlev[l].uy = uni ? g[0].ny : 0;
+    }
+    c->dlev = m.take<GsLevel>(nl);
+    c->dlb = m.take<GsLevelBed>(c->hlb.size());
+    S.nlev = nl;
+    S.nbeds = c->nbeds;
+    S.lev = c->dlev;
+    S.lb = c->dlb;
   }
 }
 
@@ -450,6 +487,8 @@ void get_tuning(const dem_ctx *c, int32_t *t) {
   t[5] = c->bs_gp; t[6] = c->bs_cells;
   t[7] = (int32_t)std::lround(c->skin_frac * 1000.0);
   t[8] = c->restore_every;
+  t[9] = c->gsv.mg_nu;
+  t[10] = (int32_t)std::lround(c->gsv.mg_alpha * 100.0);
 }
 
 int apply_tuning(dem_ctx *c, const int32_t *t) {
@@ -460,11 +499,14 @@ int apply_tuning(dem_ctx *c, const int32_t *t) {
     if (t[k] < 32 || t[k] > 1024 || t[k] % 32 != 0 || t[k] > lim[k - 1]) return DEM_EINVAL;
   if (t[7] < 1 || t[7] > 1000) return DEM_EINVAL;
   if (t[8] < 1 || t[8] > 64) return DEM_EINVAL;
+  if (t[9] < 0 || t[9] > 2 || t[10] < 50 || t[10] > 200) return DEM_EINVAL;
   c->use_lists = t[0];
   c->bs_key = t[1]; c->bs_restore = t[2]; c->bs_search = t[3]; c->bs_contacts = t[4];
   c->bs_gp = t[5]; c->bs_cells = t[6];
   c->skin_frac = t[7] / 1000.0;
   c->restore_every = t[8];
+  c->gsv.mg_nu = t[9];
+  c->gsv.mg_alpha = t[10] / 100.0;
   for (int b = 0; b < c->nbeds; ++b) {
     const double dmax = 2.0 * c->hbp_d[b].reach_max;
     set_skin(c->hbp_d[b], c->skin_frac * dmax);
@@ -652,6 +694,31 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
   c->ncells = coff;
   c->key_bits = 1;
   while ((1LL << c->key_bits) < coff) ++c->key_bits;
+  if (c->gas_solver) {
+    // multigrid levels of the pressure preconditioner: halve every bed's dims (rounding up)
+    // until each bed is one cell
+    for (int b = 0; b < n_beds; ++b)
+      c->hlb.push_back({c->hbeds[b].nx, c->hbeds[b].ny, c->hbeds[b].nz, c->hbeds[b].cell_off});
+    c->hlev.assign(1, GsLevel{});
+    for (;;) {
+      const GsLevelBed *prev = &c->hlb[(c->hlev.size() - 1) * n_beds];
+      bool single = true;
+      for (int b = 0; b < n_beds; ++b) single = single && prev[b].nx == 1 && prev[b].ny == 1 && prev[b].nz == 1;
+      if (single || (int)c->hlev.size() == GS_MAXLEV) break;
+      long long off = 0;
+      std::vector<GsLevelBed> nxt(n_beds);
+      for (int b = 0; b < n_beds; ++b) {
+        nxt[b] = {(prev[b].nx + 1) / 2, (prev[b].ny + 1) / 2, (prev[b].nz + 1) / 2, off};
+        off += (long long)nxt[b].nx * nxt[b].ny * nxt[b].nz;
+      }
+      c->hlb.insert(c->hlb.end(), nxt.begin(), nxt.end());
+      GsLevel Lv{};
+      Lv.n = off;
+      c->hlev.push_back(Lv);
+    }
+  }
+  c->gsv.mg_nu = 2;        // preconditioner of the gas pressure solve (tuning entries 9, 10)
+  c->gsv.mg_alpha = 1.5;   // the Galerkin aggregates' coarse correction falls short; over-correct
   if (c->gas_solver) {   // the cooperative pressure solve: no more blocks than fit at once
     int per_sm = 0;
     if (DEM_DISPATCH(c, gas_cg_occupancy, &per_sm) != 0 || per_sm < 1) { delete c; return DEM_ECUDA; }
@@ -722,7 +789,32 @@ int dem_init(const dem_bed_config *beds, int32_t n_beds, const dem_parcels *p, c
   ck(cudaMemsetAsync(c->hcnt[1], 0, (size_t)n, c->st));
   ck(cudaMemsetAsync(c->err, 0, sizeof(int), c->st));
   ck(cudaMemsetAsync(c->step_ctr, 0, 6 * sizeof(long long), c->st));
-  if (c->gas_solver) ck(cudaMemsetAsync(c->gsv.cg_iters, 0, sizeof(int), c->st));
+  if (c->gas_solver) {
+    ck(cudaMemsetAsync(c->gsv.cg_iters, 0, sizeof(int), c->st));
+    ck(cudaMemcpyAsync(c->dlev, c->hlev.data(), sizeof(GsLevel) * c->hlev.size(), cudaMemcpyHostToDevice, c->st));
+    ck(cudaMemcpyAsync(c->dlb, c->hlb.data(), sizeof(GsLevelBed) * c->hlb.size(), cudaMemcpyHostToDevice, c->st));
+    for (size_t l = 1; l < c->hlev.size(); ++l) {   // bed of each coarse cell
+      std::vector<int> bl((size_t)c->hlev[l].n);
+      for (int b = 0; b < n_beds; ++b) {
+        const GsLevelBed &g = c->hlb[l * n_beds + b];
+        std::fill(bl.begin() + g.off, bl.begin() + g.off + (long long)g.nx * g.ny * g.nz, b);
+      }
+      ck(cudaMemcpy(c->dlbed[l], bl.data(), sizeof(int) * bl.size(), cudaMemcpyHostToDevice));
+    }
+    for (size_t l = 0; l + 1 < c->hlev.size(); ++l) {   // the coarse cell holding each cell
+      const long long nl = l == 0 ? c->ncells : c->hlev[l].n;
+      std::vector<int> par((size_t)nl, 0);
+      for (int b = 0; b < n_beds; ++b) {
+        const GsLevelBed &g = c->hlb[l * n_beds + b], &gc = c->hlb[(l + 1) * n_beds + b];
+        for (int z = 0; z < g.nz; ++z)
+          for (int y = 0; y < g.ny; ++y)
+            for (int x = 0; x < g.nx; ++x)
+              par[g.off + ((long long)z * g.ny + y) * g.nx + x] =
+                  (int)(gc.off + ((long long)(z / 2) * gc.ny + y / 2) * gc.nx + x / 2);
+      }
+      ck(cudaMemcpy(c->dlpar[l], par.data(), sizeof(int) * par.size(), cudaMemcpyHostToDevice));
+    }
+  }
   // neighbour lists: none yet (the first step builds them); no displacement
   ck(cudaMemsetAsync(c->rebuild, 1, sizeof(int), c->st));
   for (int k = 0; k < 2; ++k) {

@@ -5,10 +5,15 @@
 // pseudo-turbulent stress and heat flux (eqs (3-28)..(3-37)). FP64 in every precision form.
 //
 // Discretisation: the gas cells as a staggered grid (velocity components on the faces,
-// scalars at the centres), explicit Euler, first-order upwind convection, an incremental
-// pressure projection solved by Jacobi-preconditioned conjugate gradients (one global system
-// over all beds, in one cooperative kernel), then species and energy with the projected mass
-// fluxes. Boundaries: immersed-boundary cells and the box sides are no-slip walls held at
+// scalars at the centres), explicit Euler, first-order upwind convection. Species and energy
+// go first, with the mass fluxes of the last projection. Continuity is taken in the low-Mach
+// divergence form: with rho = p M_g / (R T) (eq (3-53)) at fixed p0, eq (3-24) reads
+// div(eps u) = -d eps/dt + M / rho - eps D ln(rho)/Dt, D ln(rho)/Dt from the material rates
+// of the species and energy update (its change less the convective part), so that an
+// equimolar reaction (H2 to H2O) leaves the volume flow unchanged. Then the momentum
+// predictor and an incremental pressure projection for that divergence, solved by Jacobi-
+// preconditioned conjugate gradients (one global system over all beds, in one cooperative
+// kernel). Boundaries: immersed-boundary cells and the box sides are no-slip walls held at
 // T_in; a z-face below a fluid cell whose lower neighbour is not fluid takes the inlet gas
 // (eps u = U_in, Y_in, T_in); a z-face on top of the box above a fluid cell is an outlet at
 // p0 (zero gradient). The pseudo-turbulent stress enters by its normal components in the
@@ -25,13 +30,35 @@ namespace dem {
 enum : int {
   GC_EPS = 0, GC_EPSO, GC_RHO, GC_MU, GC_LAM, GC_CP, GC_DM, GC_K, GC_KV, GC_RT = GC_KV + 3, GC_AT = GC_RT + 3,
   GC_AX = GC_AT + 3,            // x_H2 / Y_H2 of eq (4-8)
-  GC_L = GC_AX + 1,             // pressure-equation coefficients of the 6 open faces (x-, x+, y-, y+, z-, z+)
-  GC_DIAG = GC_L + 6,           // their sum plus the outlet's
-  GC_RHS = GC_DIAG + 1,
+  GC_L = GC_AX + 1,             // pressure-equation coefficient of the cell's lower x-, y-, z-face where
+                                // it is open, else 0 (an upper face's is the upper neighbour's lower one)
+  GC_DIAG = GC_L + 3,           // the sum over the cell's open faces plus its outlet's
+  GC_OUT = GC_DIAG + 1,         // the outlet's coefficient (0 below the top)
+  GC_DINV = GC_OUT + 1,         // the smoother's GS_OMEGA / diag
+  GC_RHS = GC_DINV + 1,
+  GC_DIV = GC_RHS + 1,          // div(eps u) that continuity requires of the new flow, 1/s
   GC_N
 };
 constexpr int GS_CG_MAXIT = 20000;
 constexpr double GS_CG_TOL = 1e-12;   // relative residual of the pressure correction
+
+// One level of the multigrid preconditioner of the pressure equation. Level 0 is the gas
+// grid itself; level l + 1 aggregates the 2 x 2 x 2 cells (fewer at an odd edge) of level l,
+// bed by bed, until every bed is one cell. Operators are Galerkin (P^T A P with P the
+// piecewise-constant prolongation): a coarse cell's lower-face coefficient is the sum of its
+// children's across that face, its diagonal the sum of its external faces' and outlets'.
+constexpr int GS_MAXLEV = 16;
+struct GsLevel {
+  long long n;                  // cells, all beds
+  double *L;                    // [3][n] lower x-, y-, z-face coefficients
+  double *diag, *out;           // diagonal; the outlet's part of it
+  double *dinv;                 // GS_OMEGA / diag (0 for an empty cell), set with the operator
+  double *b, *xa, *xb;          // right-hand side, two iterate buffers (the result ends in xb)
+  const int *bed;               // bed of each cell
+  const int *parent;            // the cell of level l + 1 that holds each cell (none on the coarsest)
+  int ux, uy;                   // nx, ny when every bed has the same dims at this level, else 0
+};
+struct GsLevelBed { int nx, ny, nz; long long off; };   // per level and bed: dims, first cell
 
 struct GasView {
   double *fu, *fv, *fw;         // face velocities (x-, y-, z-faces of every bed, bed by bed)
@@ -44,6 +71,12 @@ struct GasView {
   double *dep;                  // cell sums of the coupling step [ncells][DEM_NDEP]
   const BedP<double> *bpd;
   long long nfx, nfy, nfz;
+  // preconditioner: mg_nu = 0 Jacobi, else a multigrid V-cycle with mg_nu damped-Jacobi
+  // sweeps before and after each coarse correction, the correction weighted by mg_alpha
+  int mg_nu, nlev, nbeds;
+  double mg_alpha;
+  const GsLevel *lev;           // [nlev]
+  const GsLevelBed *lb;         // [nlev][nbeds]
 };
 
 struct GsGrid {
@@ -186,7 +219,8 @@ __global__ void k_gs_coeffs(StepView<P> V, GasView S) {
   for (int q = 0; q < 3; ++q) { co[(GC_RT + q) * nc + c] = RT[q]; co[(GC_AT + q) * nc + c] = AT[q]; }
 }
 
-// 2. momentum predictor on every face (eq (4-2)): the faces of all three axes in one launch
+// 3. momentum predictor on every face (eq (4-2)), with the old state's properties: the faces of
+// all three axes in one launch
 template <class P>
 __global__ void k_gs_predict(StepView<P> V, GasView S) {
   pdl_wait();
@@ -251,41 +285,56 @@ __global__ void k_gs_predict(StepView<P> V, GasView S) {
 
 // projection coefficient c_f of an open face (cells P below, N above along its axis) or of
 // an outlet face (P below; the outlet pressure half a cell away)
+// c_f = eps_f beta_f A_f / h with beta_f = eps_f / (eps_f rho_f / dt + K_f) of eq (4-2)
 __device__ __forceinline__ double gs_face_c(const double *co, size_t nc, long long cP, long long cN, bool outlet,
                                             double dt, double Af, double h) {
   if (outlet) {
     const double e = co[GC_EPS * nc + cP], r = co[GC_RHO * nc + cP];
     const double beta = e / (e * r / dt + co[GC_K * nc + cP]);
-    return 2.0 * e * r * beta * Af / h;
+    return 2.0 * e * beta * Af / h;
   }
   const double ef = 0.5 * (co[GC_EPS * nc + cP] + co[GC_EPS * nc + cN]);
   const double rf = 0.5 * (co[GC_RHO * nc + cP] + co[GC_RHO * nc + cN]);
   const double Kf = 0.5 * (co[GC_K * nc + cP] + co[GC_K * nc + cN]);
   const double beta = ef / (ef * rf / dt + Kf);
-  return ef * rf * beta * Af / h;
+  return ef * beta * Af / h;
 }
-// mass flux through a face (kg/s along +axis) of kind kd with velocity u
-__device__ __forceinline__ double gs_face_flux(const double *co, size_t nc, const GsGrid &g, int a, int i, int j,
-                                               int k, int kd, double u, double Af) {
+// volume flux eps u A through a face of kind kd with velocity u (the inlet: U_in A)
+__device__ __forceinline__ double gs_vflux(const double *co, size_t nc, const GsGrid &g, int a, int i, int j, int k,
+                                           int kd, double u, double Af) {
   if (kd == 0) return 0.0;
+  if (kd == 2) return g.B->U_in * Af;
   const int di = a == 0, dj = a == 1, dk = a == 2;
-  if (kd == 2) {
-    const long long cN = g.cell(i, j, k);
-    return co[GC_EPS * nc + cN] * co[GC_RHO * nc + cN] * u * Af;
-  }
   const long long cP = g.cell(i - di, j - dj, k - dk);
-  if (kd == 3) return co[GC_EPS * nc + cP] * co[GC_RHO * nc + cP] * u * Af;
+  if (kd == 3) return co[GC_EPS * nc + cP] * u * Af;
+  return 0.5 * (co[GC_EPS * nc + cP] + co[GC_EPS * nc + g.cell(i, j, k)]) * u * Af;
+}
+// density of the inlet gas (eq (3-53) at Y_in, T_in, p0)
+__device__ __forceinline__ double gs_rho_in(const DevBed &B) {
+  const Tab<double> &td = tab<double>();
+  const double inv = B.Y_in[0] / td.Mj[0] + B.Y_in[1] / td.Mj[1] + B.Y_in[2] / td.Mj[2];
+  return (1.0 / inv) * B.p0 / (kRgas * B.T_in);
+}
+// mass flux through a face (kg/s along +axis) of kind kd with velocity u and the densities of
+// coefficient row rrow; the inlet carries the inlet gas (eps u = U_in at its density rho_in)
+__device__ __forceinline__ double gs_face_flux(const double *co, size_t nc, const GsGrid &g, int a, int i, int j,
+                                               int k, int kd, double u, double Af, int rrow, double rho_in) {
+  if (kd == 0) return 0.0;
+  if (kd == 2) return rho_in * g.B->U_in * Af;
+  const int di = a == 0, dj = a == 1, dk = a == 2;
+  const double *r = co + (size_t)rrow * nc;
+  const long long cP = g.cell(i - di, j - dj, k - dk);
+  if (kd == 3) return co[GC_EPS * nc + cP] * r[cP] * u * Af;
   const long long cN = g.cell(i, j, k);
-  return 0.5 * (co[GC_EPS * nc + cP] + co[GC_EPS * nc + cN]) * 0.5 * (co[GC_RHO * nc + cP] + co[GC_RHO * nc + cN]) *
-         u * Af;
+  return 0.5 * (co[GC_EPS * nc + cP] + co[GC_EPS * nc + cN]) * 0.5 * (r[cP] + r[cN]) * u * Af;
 }
 __device__ __forceinline__ double gs_face_val(const GasView &S, const GsGrid &g, int a, int i, int j, int k, bool star) {
   return gs_comp(S, a, star)[g.face(a, i, j, k)];
 }
 
-// 3. the pressure equation of every fluid cell: sum_f c_f (p''_nb - p''_P) =
-// net predicted mass outflow - V (M_P - rho_P (eps - eps_old) / dt); the outlet faces take the
-// predicted velocity of the face below (zero gradient)
+// 4. the pressure equation of every fluid cell: sum_f c_f (p''_nb - p''_P) =
+// net predicted volume outflow - V div(eps u); the outlet faces take the predicted velocity
+// of the face below (zero gradient)
 template <class P>
 __global__ void k_gs_rhs(StepView<P> V, GasView S) {
   pdl_wait();
@@ -294,7 +343,8 @@ __global__ void k_gs_rhs(StepView<P> V, GasView S) {
   const DevBed &B = V.beds[V.cell_bed[c]];
   const size_t nc = (size_t)V.ncells;
   double *co = S.co;
-  for (int q = 0; q < 6; ++q) co[(GC_L + q) * nc + c] = 0.0;
+  for (int q = 0; q < 3; ++q) co[(GC_L + q) * nc + c] = 0.0;
+  co[GC_OUT * nc + c] = 0.0;
   if (V.mark[c] != 0) { co[GC_DIAG * nc + c] = 0.0; co[GC_RHS * nc + c] = 0.0; return; }
   GsGrid g{&B, V.mark};
   int i, j, k;
@@ -312,33 +362,33 @@ __global__ void k_gs_rhs(StepView<P> V, GasView S) {
       S.sw[g.face(2, i, j, k + 1)] = uh;
     }
     const double ul = gs_face_val(S, g, a, i, j, k, true);
-    net += gs_face_flux(co, nc, g, a, i + di, j + dj, k + dk, kh, uh, Af[a]) -
-           gs_face_flux(co, nc, g, a, i, j, k, kl, ul, Af[a]);
+    net += gs_vflux(co, nc, g, a, i + di, j + dj, k + dk, kh, uh, Af[a]) - gs_vflux(co, nc, g, a, i, j, k, kl, ul, Af[a]);
     if (kl == 1) {
       const double cf = gs_face_c(co, nc, g.cell(i - di, j - dj, k - dk), c, false, dt, Af[a], h[a]);
-      co[(GC_L + 2 * a) * nc + c] = cf;
+      co[(GC_L + a) * nc + c] = cf;
       dsum += cf;
     }
-    if (kh == 1 || kh == 3) {
+    if (kh == 1 || kh == 3) {   // the same expression the upper neighbour stores for this face
       const double cf = gs_face_c(co, nc, c, kh == 1 ? g.cell(i + di, j + dj, k + dk) : c, kh == 3, dt, Af[a], h[a]);
-      if (kh == 1) co[(GC_L + 2 * a + 1) * nc + c] = cf;
+      if (kh == 3) co[GC_OUT * nc + c] = cf;
       dsum += cf;
     }
   }
-  const double *d = S.dep + (size_t)c * SR_N;
-  const double M = (d[SR_SH2] + d[SR_SH2O]) * B.inv_vcell;   // eq (3-25)
-  co[GC_RHS * nc + c] =
-      net - B.vcell * (M - co[GC_RHO * nc + c] * (co[GC_EPS * nc + c] - co[GC_EPSO * nc + c]) / dt);
+  co[GC_RHS * nc + c] = net - B.vcell * co[GC_DIV * nc + c];
   co[GC_DIAG * nc + c] = dsum;
 }
 
-// 4. conjugate gradients on -L p'' = -rhs with the Jacobi preconditioner, from p'' = 0, to a
-// relative residual GS_CG_TOL (at most GS_CG_MAXIT iterations): one cooperative kernel whose
-// blocks meet at two grid barriers per iteration. The search direction is double-buffered so
-// that p_k = z_k + beta p_{k-1} is formed where -L p_k is (neighbours recomputed from z and
-// p_{k-1}). Sums are per-block partials added in block order by every block: the same value
-// in every block, reproducible run to run.
+// 5. preconditioned conjugate gradients on -L p'' = -rhs, from p'' = 0, to a relative
+// residual GS_CG_TOL (at most GS_CG_MAXIT iterations): one cooperative kernel whose blocks
+// meet at grid barriers. The preconditioner is Jacobi (mg_nu = 0) or one symmetric multigrid
+// V-cycle (damped Jacobi before and after the coarse correction, the coarsest level of one
+// cell per bed solved exactly); either converges to the same tolerance, so the answer
+// differs from the Jacobi-preconditioned solve by rounding only. The search direction is
+// double-buffered so that p_k = z_k + beta p_{k-1} is formed where -L p_k is (neighbours
+// recomputed from z and p_{k-1}). Sums are per-block partials added in block order by every
+// block: the same value in every block, reproducible run to run.
 constexpr int GS_CG_BLOCK = 256;
+constexpr double GS_OMEGA = 0.8;   // damping of the Jacobi smoother
 __device__ __forceinline__ double gs_cg_dir(const double *z, const double *po, double beta, long long c) {
   return z[c] + beta * po[c];
 }
@@ -380,13 +430,241 @@ __device__ __forceinline__ void gs_grid_sums(const double *part, int slot0, doub
   __syncthreads();
 }
 
+// (A x)_i of the operator of a level (A = -L: diag x_i - sum over open faces c_f x_nb); the
+// upper neighbour along an axis is i + stride: where that steps out of the row or the plane
+// the cell reached (same bed) has the box side as its lower face, coefficient 0; out of the
+// bed there is none
+__device__ __forceinline__ double gs_apply(const GsLevel &Lv, const GsLevelBed &g, long long i, const double *x) {
+  const long long st[3] = {1, g.nx, (long long)g.nx * g.ny};
+  const long long end = g.off + st[2] * g.nz;
+  double acc = Lv.diag[i] * x[i];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double cl = Lv.L[a * Lv.n + i];
+    const double ch = i + st[a] < end ? Lv.L[a * Lv.n + i + st[a]] : 0.0;
+    if (cl != 0.0) acc -= cl * x[i - st[a]];
+    if (ch != 0.0) acc -= ch * x[i + st[a]];
+  }
+  return acc;
+}
+// the same where every bed has the same dims: the upper neighbour across a bed's top is the
+// next bed's bottom cell, whose lower z-face coefficient is 0 (an inlet or a wall)
+__device__ __forceinline__ double gs_apply_u(const double *__restrict__ L, const double *__restrict__ diag, long long n,
+                                             long long sy, long long sz, long long i, const double *__restrict__ x) {
+  const long long st[3] = {1, sy, sz};
+  double acc = diag[i] * x[i];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double cl = L[a * n + i];
+    const double ch = i + st[a] < n ? L[a * n + i + st[a]] : 0.0;
+    if (cl != 0.0) acc -= cl * x[i - st[a]];
+    if (ch != 0.0) acc -= ch * x[i + st[a]];
+  }
+  return acc;
+}
+__device__ __forceinline__ void gs_local(const GsLevelBed &g, long long i, int &x, int &y, int &z) {
+  const int l = (int)(i - g.off);   // a bed has fewer than 2^30 cells
+  const int q = l / g.nx;
+  x = l - q * g.nx;
+  z = q / g.ny;
+  y = q - z * g.ny;
+}
+// levels of at most this many cells are smoothed, restricted and prolonged by one block
+// alone (block barriers instead of grid barriers)
+constexpr long long GS_SMALL = 2048;
+
+// Galerkin coefficients of level l + 1 from level l: per coarse cell, over its children
+static __device__ __noinline__ void gs_mg_setup(const GasView &S, const GsLevel *lev, int l, long long c0,
+                                                long long stride) {
+  const GsLevel &F = lev[l], &Cv = lev[l + 1];   // by value: the stores below cannot alias them
+  for (long long I = c0; I < Cv.n; I += stride) {
+    const int b = Cv.bed[I];
+    const GsLevelBed gf = S.lb[(size_t)l * S.nbeds + b], gc = S.lb[(size_t)(l + 1) * S.nbeds + b];
+    int X, Y, Z;
+    gs_local(gc, I, X, Y, Z);
+    const int C[3] = {X, Y, Z}, nf[3] = {gf.nx, gf.ny, gf.nz};
+    const long long st[3] = {1, gf.nx, (long long)gf.nx * gf.ny};
+    double Lc[3] = {0.0, 0.0, 0.0}, dc = 0.0, oc = 0.0;
+    for (int dk = 0; dk < 2; ++dk)
+      for (int dj = 0; dj < 2; ++dj)
+        for (int di = 0; di < 2; ++di) {
+          const int f[3] = {2 * X + di, 2 * Y + dj, 2 * Z + dk};
+          if (f[0] >= nf[0] || f[1] >= nf[1] || f[2] >= nf[2]) continue;
+          const long long i = gf.off + ((long long)f[2] * nf[1] + f[1]) * nf[0] + f[0];
+          oc += F.out[i];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            if ((f[a] - 1) >> 1 != C[a] || f[a] == 0) {   // lower face external (or the box side)
+              const double v = F.L[a * F.n + i];
+              Lc[a] += v;
+              dc += v;
+            }
+            if (f[a] + 1 < nf[a] && (f[a] + 1) >> 1 != C[a]) dc += F.L[a * F.n + i + st[a]];   // upper, external
+          }
+        }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Cv.L[a * Cv.n + I] = Lc[a];
+    Cv.diag[I] = dc + oc;
+    Cv.out[I] = oc;
+    Cv.dinv[I] = dc + oc > 0.0 ? GS_OMEGA / (dc + oc) : 0.0;
+  }
+}
+
+// one damped-Jacobi sweep of level l, x_dst = x_src + omega D^-1 (b - A x_src); from x = 0
+// when src is null. With rz, the r . x_dst partial of the final level-0 sweep.
+__device__ __forceinline__ void gs_mg_sweep(const GasView &S, const GsLevel *lev, int l, const double *src, double *dst,
+                                            long long c0, long long stride, double *rz) {
+  const GsLevel &Lv = lev[l];
+  const double *__restrict__ L = Lv.L;
+  const double *__restrict__ dg = Lv.diag;
+  const double *__restrict__ di = Lv.dinv;
+  const double *__restrict__ b = Lv.b;
+  const long long n = Lv.n;
+  if (Lv.ux > 0) {   // uniform dims: no per-cell bed lookup
+    const long long sy = Lv.ux, sz = (long long)Lv.ux * Lv.uy;
+    for (long long i = c0; i < n; i += stride) {
+      const double w = di[i];
+      double v = 0.0;
+      if (w != 0.0) v = src ? src[i] + (b[i] - gs_apply_u(L, dg, n, sy, sz, i, src)) * w : b[i] * w;
+      dst[i] = v;
+      if (rz) *rz += b[i] * v;
+    }
+    return;
+  }
+  const GsLevelBed *lb = S.lb + (size_t)l * S.nbeds;
+  for (long long i = c0; i < n; i += stride) {
+    const double w = di[i];
+    double v = 0.0;
+    if (w != 0.0) v = src ? src[i] + (b[i] - gs_apply(Lv, lb[Lv.bed[i]], i, src)) * w : b[i] * w;
+    dst[i] = v;
+    if (rz) *rz += b[i] * v;
+  }
+}
+
+// restriction of level l's residual b - A x (x: the iterate xf) to level l + 1's right-hand side,
+// with the first sweep there (from 0), or the exact solve of the coarsest level (one cell
+// per bed) into its xb
+__device__ __forceinline__ void gs_mg_restrict(const GasView &S, const GsLevel *lev, int l, const double *xf,
+                                               long long c0, long long stride) {
+  const GsLevel &F = lev[l], &Cv = lev[l + 1];
+  const bool coarsest = l + 2 == S.nlev;
+  for (long long I = c0; I < Cv.n; I += stride) {
+    const int b = Cv.bed[I];
+    const GsLevelBed gf = S.lb[(size_t)l * S.nbeds + b], gc = S.lb[(size_t)(l + 1) * S.nbeds + b];
+    int X, Y, Z;
+    gs_local(gc, I, X, Y, Z);
+    double sum = 0.0;
+    for (int dk = 0; dk < 2; ++dk)
+      for (int dj = 0; dj < 2; ++dj)
+        for (int di = 0; di < 2; ++di) {
+          const int fx = 2 * X + di, fy = 2 * Y + dj, fz = 2 * Z + dk;
+          if (fx >= gf.nx || fy >= gf.ny || fz >= gf.nz) continue;
+          const long long i = gf.off + ((long long)fz * gf.ny + fy) * gf.nx + fx;
+          if (F.diag[i] > 0.0)
+            sum += F.b[i] - (F.ux > 0 ? gs_apply_u(F.L, F.diag, F.n, F.ux, (long long)F.ux * F.uy, i, xf)
+                                      : gs_apply(F, gf, i, xf));
+        }
+    Cv.b[I] = sum;
+    const double w = Cv.dinv[I];
+    if (coarsest) Cv.xb[I] = sum * (w * (1.0 / GS_OMEGA));   // one cell per bed: exact
+    else Cv.xa[I] = sum * w;
+  }
+}
+
+// prolongation: level l's current iterate += alpha times its parent's correction
+__device__ __forceinline__ void gs_mg_prolong(const GasView &S, const GsLevel *lev, int l, double *x, long long c0,
+                                              long long stride) {
+  const GsLevel &F = lev[l];
+  const double *__restrict__ xc = lev[l + 1].xb;
+  const int *__restrict__ par = F.parent;
+  const double w = S.mg_alpha;
+  for (long long i = c0; i < F.n; i += stride)
+    if (F.diag[i] > 0.0) x[i] += w * xc[par[i]];
+}
+
+// One V-cycle z = M r (r: level 0's b; z: level 0's xb) and the grid's r . z. The sweep
+// counts before and after each coarse correction are equal and the smoother is symmetric,
+// so M is symmetric; every sweep after the first reads its neighbours, so a grid barrier
+// separates the phases.
+static __device__ __noinline__ double gs_vcycle(const GasView &S, const GsLevel *lev,
+                                                cooperative_groups::grid_group &grid, long long c0, long long stride,
+                                                double *sh) {
+  const int nu = S.mg_nu;
+  double rz = 0.0;
+  if (S.nlev == 1) {   // one cell per bed: the exact solve
+    const GsLevel &L0 = lev[0];
+    for (long long i = c0; i < L0.n; i += stride) {
+      const double v = L0.b[i] * (L0.dinv[i] * (1.0 / GS_OMEGA));
+      L0.xb[i] = v;
+      rz += L0.b[i] * v;
+    }
+  } else {
+    int ls = S.nlev;   // the first level that one block handles
+    for (int l = 1; l < S.nlev; ++l)
+      if (lev[l].n <= GS_SMALL) { ls = l; break; }
+    gs_mg_sweep(S, lev, 0, nullptr, lev[0].xa, c0, stride, nullptr);
+    grid.sync();
+    for (int l = 0; l < ls && l + 1 < S.nlev; ++l) {   // down: smooth, restrict (first sweep below fused)
+      if (nu == 2) {
+        gs_mg_sweep(S, lev, l, lev[l].xa, lev[l].xb, c0, stride, nullptr);
+        grid.sync();
+      }
+      gs_mg_restrict(S, lev, l, nu == 2 ? lev[l].xb : lev[l].xa, c0, stride);
+      grid.sync();
+    }
+    if (ls + 1 < S.nlev) {   // the small levels, down and up, in block 0
+      if (blockIdx.x == 0) {
+        const long long t0 = threadIdx.x, ts = blockDim.x;
+        for (int l = ls; l + 1 < S.nlev; ++l) {
+          if (nu == 2) {
+            gs_mg_sweep(S, lev, l, lev[l].xa, lev[l].xb, t0, ts, nullptr);
+            __syncthreads();
+          }
+          gs_mg_restrict(S, lev, l, nu == 2 ? lev[l].xb : lev[l].xa, t0, ts);
+          __syncthreads();
+        }
+        for (int l = S.nlev - 2; l >= ls; --l) {
+          gs_mg_prolong(S, lev, l, nu == 2 ? lev[l].xb : lev[l].xa, t0, ts);
+          __syncthreads();
+          if (nu == 2) {
+            gs_mg_sweep(S, lev, l, lev[l].xb, lev[l].xa, t0, ts, nullptr);
+            __syncthreads();
+          }
+          gs_mg_sweep(S, lev, l, lev[l].xa, lev[l].xb, t0, ts, nullptr);
+          __syncthreads();
+        }
+      }
+      grid.sync();
+    }
+    for (int l = (ls < S.nlev ? ls : S.nlev - 1) - 1; l >= 0; --l) {   // up: correct, smooth
+      gs_mg_prolong(S, lev, l, nu == 2 ? lev[l].xb : lev[l].xa, c0, stride);
+      grid.sync();
+      if (nu == 2) {
+        gs_mg_sweep(S, lev, l, lev[l].xb, lev[l].xa, c0, stride, nullptr);
+        grid.sync();
+      }
+      gs_mg_sweep(S, lev, l, lev[l].xa, lev[l].xb, c0, stride, l == 0 ? &rz : nullptr);
+      if (l > 0) grid.sync();
+    }
+  }
+  double v[1] = {rz};
+  gs_block_sums<1>(v, S.part, 2, sh);
+  grid.sync();
+  double out[1];
+  gs_grid_sums<1>(S.part, 2, sh, out);
+  return out[0];
+}
+
 template <class P>
-__global__ void __launch_bounds__(GS_CG_BLOCK) k_gs_cg(const DevBed *beds, const int *cell_bed,
+__global__ void __launch_bounds__(GS_CG_BLOCK, 4) k_gs_cg(const DevBed *beds, const int *cell_bed,
                                                        const long long *ctr, long long ncells, GasView S) {
   namespace cg = cooperative_groups;
   if (!gs_active(beds, ctr)) return;   // the same answer in every block
   cg::grid_group grid = cg::this_grid();
   __shared__ double sh[4 * 32 + 8];
+  __shared__ GsLevel lev[GS_MAXLEV];   // the level descriptors, read by every phase
+  if (threadIdx.x < S.nlev) lev[threadIdx.x] = S.lev[threadIdx.x];
+  __syncthreads();
   const size_t nc = (size_t)ncells;
   const double *diag = S.co + GC_DIAG * nc, *rhs = S.co + GC_RHS * nc;
   const double *L = S.co + GC_L * nc;
@@ -394,13 +672,36 @@ __global__ void __launch_bounds__(GS_CG_BLOCK) k_gs_cg(const DevBed *beds, const
   const long long c0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double *x = S.x, *r = S.r, *z = S.z, *Ap = S.Ap;
   double *po = S.pa, *pn = S.pb;
+  const bool mg = S.mg_nu > 0;
+  const int uxy[2] = {lev[0].ux, lev[0].uy};
+  double *dinv0 = S.co + GC_DINV * nc;
+  if (mg) {   // the coarse levels' operators of this step's coefficients (small ones in block 0)
+    int l = 0;
+    for (; l + 1 < S.nlev && lev[l + 1].n > GS_SMALL; ++l) {
+      gs_mg_setup(S, lev, l, c0, stride);
+      grid.sync();
+    }
+    if (l + 1 < S.nlev) {
+      if (blockIdx.x == 0)
+        for (; l + 1 < S.nlev; ++l) {
+          gs_mg_setup(S, lev, l, threadIdx.x, blockDim.x);
+          __syncthreads();
+        }
+      grid.sync();
+    }
+  }
   {
     double v[2] = {0.0, 0.0};
     for (long long c = c0; c < ncells; c += stride) {
       const double rc = -rhs[c];
-      const double zc = diag[c] > 0.0 ? rc / diag[c] : 0.0;
-      r[c] = rc; z[c] = zc; x[c] = 0.0; po[c] = 0.0;
-      v[0] += rc * rc; v[1] += rc * zc;
+      r[c] = rc; x[c] = 0.0; po[c] = 0.0;
+      dinv0[c] = diag[c] > 0.0 ? GS_OMEGA / diag[c] : 0.0;
+      v[0] += rc * rc;
+      if (!mg) {
+        const double zc = diag[c] > 0.0 ? rc / diag[c] : 0.0;
+        z[c] = zc;
+        v[1] += rc * zc;
+      }
     }
     gs_block_sums<2>(v, S.part, 1, sh);
   }
@@ -411,6 +712,7 @@ __global__ void __launch_bounds__(GS_CG_BLOCK) k_gs_cg(const DevBed *beds, const
   double rz = s2[1], beta = 0.0;
   int it = 0;
   if (bnorm > 0.0) {
+    if (mg) rz = gs_vcycle(S, lev, grid, c0, stride, sh);
     for (; it < GS_CG_MAXIT; ++it) {
       // p_k and -L p_k
       double v1[1] = {0.0};
@@ -418,12 +720,23 @@ __global__ void __launch_bounds__(GS_CG_BLOCK) k_gs_cg(const DevBed *beds, const
         const double pc = gs_cg_dir(z, po, beta, c);
         pn[c] = pc;
         double acc = diag[c] * pc;
-        if (diag[c] > 0.0) {
-          const DevBed &B = beds[cell_bed[c]];
-          const long long st[3] = {1, B.nx, (long long)B.nx * B.ny};
+        if (diag[c] > 0.0 && uxy[0] > 0) {   // uniform dims: see gs_apply_u
+          const long long st[3] = {1, uxy[0], (long long)uxy[0] * uxy[1]};
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
-            const double cl = L[(2 * a) * nc + c], ch = L[(2 * a + 1) * nc + c];
+            const double cl = L[a * nc + c];
+            const double ch = c + st[a] < ncells ? L[a * nc + c + st[a]] : 0.0;
+            if (cl != 0.0) acc -= cl * gs_cg_dir(z, po, beta, c - st[a]);
+            if (ch != 0.0) acc -= ch * gs_cg_dir(z, po, beta, c + st[a]);
+          }
+        } else if (diag[c] > 0.0) {
+          const DevBed &B = beds[cell_bed[c]];
+          const long long st[3] = {1, B.nx, (long long)B.nx * B.ny};
+          const long long cend = B.cell_off + st[2] * B.nz;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const double cl = L[a * nc + c];
+            const double ch = c + st[a] < cend ? L[a * nc + c + st[a]] : 0.0;
             if (cl != 0.0) acc -= cl * gs_cg_dir(z, po, beta, c - st[a]);
             if (ch != 0.0) acc -= ch * gs_cg_dir(z, po, beta, c + st[a]);
           }
@@ -441,23 +754,28 @@ __global__ void __launch_bounds__(GS_CG_BLOCK) k_gs_cg(const DevBed *beds, const
       for (long long c = c0; c < ncells; c += stride) {
         x[c] += alpha * pn[c];
         const double rc = r[c] - alpha * Ap[c];
-        const double zc = diag[c] > 0.0 ? rc / diag[c] : 0.0;
-        r[c] = rc; z[c] = zc;
-        v2[0] += rc * rc; v2[1] += rc * zc;
+        r[c] = rc;
+        v2[0] += rc * rc;
+        if (!mg) {
+          const double zc = diag[c] > 0.0 ? rc / diag[c] : 0.0;
+          z[c] = zc;
+          v2[1] += rc * zc;
+        }
       }
       gs_block_sums<2>(v2, S.part, 1, sh);
       grid.sync();
       gs_grid_sums<2>(S.part, 1, sh, s2);
       if (sqrt(s2[0]) < GS_CG_TOL * bnorm) { ++it; break; }
-      beta = s2[1] / rz;
-      rz = s2[1];
+      const double rzn = mg ? gs_vcycle(S, lev, grid, c0, stride, sh) : s2[1];
+      beta = rzn / rz;
+      rz = rzn;
       double *t = po; po = pn; pn = t;
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *S.cg_iters = it;
 }
 
-// 5. projection: the open and outlet faces corrected by the pressure-correction gradient, the
+// 6. projection: the open and outlet faces corrected by the pressure-correction gradient, the
 // others as predicted; the pressure updated
 template <class P>
 __global__ void k_gs_correct(StepView<P> V, GasView S) {
@@ -519,35 +837,40 @@ __device__ __forceinline__ void gs_store_props(StepView<P> &V, const GasView &S,
 template <class P> __device__ __forceinline__ double gs_get(const double *G, size_t k) { return gas_d<P>(G, k); }
 template <class P> __device__ __forceinline__ void gs_put(double *G, size_t k, double v) { gas_put(G, k, v, !P::exact); }
 
-// 6. species (eq (4-9)) and energy (eq (4-6)) with the projected mass fluxes, every step:
-// on coupling steps the update, on the others a copy; the property record follows the state
+// 2. species (eq (4-9)) and energy (eq (4-6)) with the mass fluxes of the last projection
+// (the current faces, the old densities), every step: on coupling steps the update and the
+// velocity divergence continuity requires, on the others a copy of the state
 template <class P>
 __global__ void k_gs_scalars(StepView<P> V, GasView S) {
+  pdl_wait();
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= V.ncells) return;
   const size_t nc = (size_t)V.ncells;
   const bool active = gs_active(V.beds, V.step_ctr);
   const double *G = V.gas;
   double *Gn = V.gas_new;
-  double Y[3] = {gs_get<P>(G, GS_Y0 * nc + c), gs_get<P>(G, GS_Y1 * nc + c), gs_get<P>(G, GS_Y2 * nc + c)};
-  double T = gs_get<P>(G, GS_T * nc + c);
   if (!active) {   // a copy of the words (pairs stay pairs)
     for (int q = 0; q < GS_N; ++q) Gn[q * nc + c] = G[q * nc + c];
     return;
   }
+  double Y[3] = {gs_get<P>(G, GS_Y0 * nc + c), gs_get<P>(G, GS_Y1 * nc + c), gs_get<P>(G, GS_Y2 * nc + c)};
+  double T = gs_get<P>(G, GS_T * nc + c);
   const DevBed &B = V.beds[V.cell_bed[c]];
   GsGrid g{&B, V.mark};
-  const double *co = S.co;
+  double *co = S.co;
   const double eps = co[GC_EPS * nc + c];
+  const double rho = co[GC_RHO * nc + c];
+  double div = 0.0;
   if (V.mark[c] == 0) {
     int i, j, k;
     g.ijk(c, i, j, k);
     const double h[3] = {B.dx, B.dy, B.dz};
     const double Af[3] = {B.dy * B.dz, B.dx * B.dz, B.dx * B.dy};
     const double dt = B.ncouple * B.dt;
-    const double rho = co[GC_RHO * nc + c], cp = co[GC_CP * nc + c], lam = co[GC_LAM * nc + c];
+    const double rho_in = gs_rho_in(B);
+    const double cp = co[GC_CP * nc + c], lam = co[GC_LAM * nc + c];
     const double Dm = co[GC_DM * nc + c];
-    const double Y0 = Y[0], Y1 = Y[1];
+    const double Y0 = Y[0], Y1 = Y[1], Y2o = Y[2];
     double cY0 = 0.0, cY1 = 0.0, cT = 0.0, dY0 = 0.0, dY1 = 0.0, dT = 0.0;
     for (int a = 0; a < 3; ++a) {
       const int di = a == 0, dj = a == 1, dk = a == 2;
@@ -555,7 +878,9 @@ __global__ void k_gs_scalars(StepView<P> V, GasView S) {
       for (int side = 0; side < 2; ++side) {
         const int fi = i + side * di, fj = j + side * dj, fk = k + side * dk;
         const int kd = g.kind(a, fi, fj, fk);
-        const double F = gs_face_flux(co, nc, g, a, fi, fj, fk, kd, gs_face_val(S, g, a, fi, fj, fk, false), Af[a]);
+        const double F = kd == 0 ? 0.0
+                                 : gs_face_flux(co, nc, g, a, fi, fj, fk, kd, gs_face_val(S, g, a, fi, fj, fk, false),
+                                                Af[a], GC_RHO, rho_in);
         const double inflow = side == 0 ? F : -F;
         if (kd == 1) {
           const long long cn = g.cell(i + (side ? di : -di), j + (side ? dj : -dj), k + (side ? dk : -dk));
@@ -600,17 +925,40 @@ __global__ void k_gs_scalars(StepView<P> V, GasView S) {
     const double Y2f = fmax(1.0 - Y0f - Y1f, 0.0);
     const double ys = Y0f + Y1f + Y2f;
     Y[0] = Y0f / ys; Y[1] = Y1f / ys; Y[2] = Y2f / ys;
-    // M_r of eq (3-39) with the species sources, M_rm of eq (3-38)
-    const double Mr = -(h_over_R<double>(0, T) * td.RMj[0] * (-cons) + h_over_R<double>(1, T) * td.RMj[1] * (MH2O / MH2 * cons));
+    // M_r of eq (3-39) with the parcels' species sources and M_rm of eq (3-38): together the
+    // sensible enthalpy the species bring from the parcels' temperature
+    const double Mr = -(h_over_R<double>(0, T) * td.RMj[0] * d[SR_SH2] + h_over_R<double>(1, T) * td.RMj[1] * d[SR_SH2O]);
     const double Mrm = -d[SR_QRM];
     const double mc = m * cp;
-    T = (mc * T / dt + cT + dT + d[SR_HAT] + Mr + Mrm - T * cp * Mnet) / (mc / dt + d[SR_HA]);
+    const double Tn = (mc * T / dt + cT + dT + d[SR_HAT] + Mr + Mrm) / (mc / dt + d[SR_HA]);
+    // div(eps u) = -d eps/dt + M / rho - eps D ln(rho)/Dt (the material rates: the change less
+    // its convective part; the N2 carried in is -(cY0 + cY1))
+    const double DY0 = (Y[0] - Y0) / dt - cY0 / m, DY1 = (Y[1] - Y1) / dt - cY1 / m;
+    const double DY2 = (Y[2] - Y2o) / dt + (cY0 + cY1) / m;
+    const double DT = (Tn - T) / dt - cT / mc;
+    const double Mg = 1.0 / (Y0 / td.Mj[0] + Y1 / td.Mj[1] + Y2o / td.Mj[2]);
+    const double Dlnrho = -Mg * (DY0 / td.Mj[0] + DY1 / td.Mj[1] + DY2 / td.Mj[2]) - DT / T;
+    div = -(eps - co[GC_EPSO * nc + c]) / dt + Mnet / (B.vcell * rho) - eps * Dlnrho;
+    T = Tn;
   }
   gs_put<P>(Gn, GS_EPS * nc + c, eps);
   gs_put<P>(Gn, GS_Y0 * nc + c, Y[0]); gs_put<P>(Gn, GS_Y1 * nc + c, Y[1]); gs_put<P>(Gn, GS_Y2 * nc + c, Y[2]);
   gs_put<P>(Gn, GS_T * nc + c, T);
-  const double Ys[3] = {gs_get<P>(Gn, GS_Y0 * nc + c), gs_get<P>(Gn, GS_Y1 * nc + c), gs_get<P>(Gn, GS_Y2 * nc + c)};
-  gs_store_props(V, S, g, c, gs_get<P>(Gn, GS_EPS * nc + c), Ys, gs_get<P>(Gn, GS_T * nc + c));
+  co[GC_DIV * nc + c] = div;
+}
+
+// 7. on coupling steps, the cell's property record for the next steps from the updated state
+// and the projected faces
+template <class P>
+__global__ void k_gs_props(StepView<P> V, GasView S) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= V.ncells || !gs_active(V.beds, V.step_ctr)) return;
+  const size_t nc = (size_t)V.ncells;
+  const DevBed &B = V.beds[V.cell_bed[c]];
+  GsGrid g{&B, V.mark};
+  const double *Gn = V.gas_new;
+  const double Y[3] = {gs_get<P>(Gn, GS_Y0 * nc + c), gs_get<P>(Gn, GS_Y1 * nc + c), gs_get<P>(Gn, GS_Y2 * nc + c)};
+  gs_store_props(V, S, g, c, gs_get<P>(Gn, GS_EPS * nc + c), Y, gs_get<P>(Gn, GS_T * nc + c));
 }
 
 // initial flow of the solved beds: plug flow at the superficial velocity through every

@@ -148,10 +148,10 @@ int enqueue_binning(dem_ctx *c, int drift) {
 }
 
 // The gas solver's kernels of one step (beds with DEM_GAS_SOLVER), in place of k_cells: on
-// coupling steps the cell sums and coefficients, the momentum predictor, the pressure
-// equation, the cooperative conjugate-gradient solve, the projection and the species and
-// energy update; on the other steps all but the last return at once and the last copies
-// the state.
+// coupling steps the cell sums and coefficients, the species and energy update (and the new
+// densities), the momentum predictor, the pressure equation, the cooperative conjugate-
+// gradient solve, the projection and the cells' property records; on the other steps the
+// species kernel copies the state and the others return at once.
 template <class P>
 int enqueue_gas_solve(dem_ctx *c, StepView<P> &V, bool pdl) {
   cudaStream_t st = c->st;
@@ -159,6 +159,9 @@ int enqueue_gas_solve(dem_ctx *c, StepView<P> &V, bool pdl) {
   const long long nf = S.nfx + S.nfy + S.nfz;
   int ps = prof_begin(c, "k_gs_coeffs");
   launch_k(pdl, k_gs_coeffs<P>, grid_for(c->ncells, 256), 256, st, V, S);
+  prof_end(c, ps);
+  ps = prof_begin(c, "k_gs_scalars");
+  launch_k(pdl, k_gs_scalars<P>, grid_for(c->ncells, 256), 256, st, V, S);
   prof_end(c, ps);
   ps = prof_begin(c, "k_gs_predict");
   launch_k(pdl, k_gs_predict<P>, grid_for(nf, 256), 256, st, V, S);
@@ -185,10 +188,10 @@ int enqueue_gas_solve(dem_ctx *c, StepView<P> &V, bool pdl) {
   ps = prof_begin(c, "k_gs_correct");
   k_gs_correct<P><<<grid_for(nf + c->ncells, 256), 256, 0, st>>>(V, S);
   prof_end(c, ps);
-  ps = prof_begin(c, "k_gs_scalars");
-  k_gs_scalars<P><<<grid_for(c->ncells, 256), 256, 0, st>>>(V, S);
+  ps = prof_begin(c, "k_gs_props");
+  k_gs_props<P><<<grid_for(c->ncells, 256), 256, 0, st>>>(V, S);
   prof_end(c, ps);
-  c->launches += 6;
+  c->launches += 7;
   return (int)cudaPeekAtLastError();
 }
 

@@ -78,6 +78,21 @@ def test_gas_solver_fp64_against_oracle(wall):
     ctx.close()
 
 
+@pytest.mark.parametrize("sweeps", [0, 1])
+def test_gas_solver_preconditioners(sweeps):
+    # the Jacobi preconditioner and the one-sweep V-cycle reach the same solution (the default,
+    # two sweeps, runs in the other tests)
+    bed = _solved(33, synth.WALL_CONE)
+    ctx = _ctx(bed)
+    ctx.dem_set_tuning(gas_mg_sweeps=sweeps, gas_mg_weight_pct=100)
+    ref = oracle.Oracle(bed)
+    for _ in range(2):
+        ctx.dem_step(10)
+        ref.step(10)
+        _compare(ctx, ref, 1e-8, 1e-10, 1e-7)
+    ctx.close()
+
+
 def test_gas_solver_two_beds_fp64():
     bed = _two_beds(41)
     ctx = _ctx(bed)
@@ -153,4 +168,25 @@ def test_prescribed_flow_reported():
     assert it == 0
     assert np.array_equal(fg[:, :2], np.zeros((ctx.ncells, 2))) and np.all(fg[:, 3] == 0)
     assert np.allclose(fg[:, 2], bed.beds[0].U_in / eps, rtol=1e-15)
+    ctx.close()
+
+
+def test_gas_solver_reacting_column_long_run():
+    # a reacting column over 6000 steps (600 gas steps), static parcels: the H2O front passes
+    # the outlet; flow, gas and parcel state against the oracle every 1000 steps
+    from tests.helpers import bed_from_arrays
+    cfg = synth.BedConfig(D=0.004, H=0.024, nx=1, ny=1, nz=8, dt=1e-5, cg_ratio=4.0, U_in=0.2, T_in=1000.0,
+                          coupling_interval=10, Y_in=(0.9, 0.05, 0.05), kn=1e-3,
+                          flags=synth.GAS_SOLVER | synth.NO_GRAVITY | synth.NO_CONTACTS | synth.NO_DRAG)
+    rng = np.random.default_rng(3)
+    n = 40
+    bed = bed_from_arrays(cfg, rng.uniform(-0.001, 0.001, n), rng.uniform(-0.001, 0.001, n),
+                          rng.uniform(0.004, 0.012, n), d_real=100e-6, T=1000.0, comp=(1.0, 0.0, 0.0, 0.0))
+    ctx = _ctx(bed)
+    ref = oracle.Oracle(bed)
+    for _ in range(6):
+        ctx.dem_step(1000)
+        ref.step(1000)
+        _compare(ctx, ref, 1e-7, 1e-9, 1e-9)
+    assert ctx.dem_get_gas()[-1, 2] > 0.4
     ctx.close()
