@@ -66,6 +66,7 @@ def parse():
                     "e.g. neighbour_lists=1,bs_key=64,skin_permille=50 (profiler runs repeat a plain run's)")
     ap.add_argument("--no-dense-leg", action="store_true", help="skip the contact-dominated 2M bed")
     ap.add_argument("--no-batched-leg", action="store_true", help="skip the 32-bed batch")
+    ap.add_argument("--no-gas-solver-leg", action="store_true", help="skip the 2M bed with the gas phase solved")
     ap.add_argument("--coupling", default="10,1,20", help="coupling intervals n = dt_CFD/dt_DEM of the "
                     "end-to-end legs; the first one is the e2e headline (Table 3: n = 10 for Bed II)")
     return ap.parse_args()
@@ -332,16 +333,17 @@ def e2e_coupling(binding, stream, bed, ncouple, tuning, settle, steps):
 
 
 def dense_leg(binding, stream, tuning, settle, steps, precision, parcels=0, conduction=False):
-    """The 2M cone-and-plate bed as a jammed packing without gas flow (a fixed bed): the
-    contact-dominated regime of a settled bed. It starts with about 2.7 contacts per parcel;
-    the overlaps push the lattice apart and gravity packs it again over the untimed settle
-    steps; then it is timed like the headline step, and the mean number of live contacts is
-    read after the timed steps. conduction: the same with the contact heat conduction of
-    eqs (3-14)..(3-15-2) switched on in the bed."""
+    """The 2M cone-and-plate bed as a packed bed without gas flow: one parcel size, every
+    site of a square lattice filled with touching neighbours, compressed by its own weight
+    over the untimed settle steps into the contact-dominated regime (about 2.7 contacts per
+    parcel, 97 % of the parcels in contact after 100 steps). Over thousands of steps the
+    packing drains through the plate's holes (wider than the parcels), so it is timed early,
+    like the headline step, and the mean number of live contacts is read after the timed
+    steps. conduction: the same with the contact heat conduction of eqs (3-14)..(3-15-2)."""
     import torch
     from paper_2311_03908_gb300 import synth
     kw = {"n": parcels} if parcels else {}
-    bed = synth.config_ibm_2m_dense(U_in=0.0, v_scale=0.01, **kw)
+    bed = synth.config_ibm_2m_dense(**kw)
     if conduction:
         for c in bed.beds:
             c.flags |= synth.CONDUCTION
@@ -367,7 +369,7 @@ def dense_leg(binding, stream, tuning, settle, steps, precision, parcels=0, cond
     t = cx.dem_kernel_times()
     cx.dem_profile(False)
     cx.close()
-    return {"workload": f"ibm_2m_dense ({bed.n} parcels, jammed lattice, no gas flow)"
+    return {"workload": f"ibm_2m_dense ({bed.n} parcels of one size, touching square lattice under gravity, no gas flow)"
                         + (", contact conduction on" if conduction else ""),
             "ms_per_step": ms / steps, "value": bed.n * steps / (ms * 1e-3), "unit": UNIT, "steps": steps,
             "settle_steps": settle, "zbar_contacts": float(cnt.mean()), "fraction_in_contact": float((cnt > 0).mean()),
@@ -397,12 +399,68 @@ def batched_leg(binding, stream, settle, steps, precision):
     torch.cuda.synchronize()
     ms = a0.elapsed_time(a1)
     mean, _ = cx.dem_reduction_degree()
+    # launch overhead: the same steps launched kernel by kernel (no graph), and the sum of
+    # the kernels' own device times (each bracketed by events, so no overlap between them)
+    a0.record(stream)
+    cx.dem_step(steps)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms_eager = a0.elapsed_time(a1)
+    cx.dem_profile(True)
+    cx.dem_step(G)
+    t = cx.dem_kernel_times()
+    cx.dem_profile(False)
+    ksum = sum(v[1] for v in t.values()) / G
     cx.close()
     return {"workload": f"batched_32 ({bed.n} parcels in {len(bed.beds)} beds of "
                         f"{min(bed.meta['counts'])}..{max(bed.meta['counts'])})",
             "ms_per_step": ms / steps, "value": bed.n * steps / (ms * 1e-3), "unit": UNIT, "steps": steps,
             "settle_steps": settle, "tuning": tuning, "stepping": "one context, graphs of 10 steps",
+            "eager_ms_per_step": ms_eager / steps, "kernel_sum_ms_per_step": ksum,
+            "graph_over_kernel_sum": (ms / steps) / ksum if ksum > 0 else None,
             "f_ov_mean_per_bed_range": [float(mean.min()), float(mean.max())]}
+
+
+def gas_solver_leg(binding, stream, tuning, steps, precision):
+    """The 2M cone-and-plate bed with the gas phase solved on the GPU (momentum, energy and
+    species every 10 steps, the pressure by multigrid-preconditioned CG): the whole coupled
+    step, timed like the headline one, and the solver's share."""
+    import torch
+    from paper_2311_03908_gb300 import synth
+    bed = synth.config_ibm_2m()
+    for c in bed.beds:
+        c.flags |= synth.GAS_SOLVER
+        c.coupling_interval = 10
+    cx = binding.Context(bed, precision=precision, stream=stream.cuda_stream)
+    cx.dem_set_tuning(**{k: v for k, v in tuning.items() if not k.startswith("gas_")})
+    G = 10
+    steps = max(G, steps // G * G)
+    cx.dem_step_graph(G)
+    cx.dem_step_graph(G)
+    cx.dem_sync()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(steps // G):
+        cx.dem_step_graph(G)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms = a0.elapsed_time(a1)
+    fl, iters = cx.dem_get_flow()
+    cx.dem_profile(True)
+    cx.dem_step(2 * G)
+    t = cx.dem_kernel_times()
+    cx.dem_profile(False)
+    cx.close()
+    gas = {k: v[1] / 2 for k, v in t.items() if k.startswith("k_gs_")}
+    total = sum(v[1] for v in t.values()) / 2
+    return {"workload": f"ibm_2m ({bed.n} parcels, {bed.beds[0].nx}x{bed.beds[0].ny}x{bed.beds[0].nz} gas cells) "
+                        "with the gas phase solved, coupling interval 10",
+            "ms_per_step": ms / steps, "value": bed.n * steps / (ms * 1e-3), "unit": UNIT, "steps": steps,
+            "cg_iterations_last_solve": iters, "preconditioner": "multigrid V(2,2), coarse weight 1.5",
+            "ms_per_solve": {k: round(v, 4) for k, v in gas.items()},
+            "solver_share_of_10_steps": sum(gas.values()) / total if total > 0 else None,
+            "max_gas_speed_m_s": float(np.abs(fl[:, :3]).max())}
 
 
 def adjoint_cost(binding, stream):
@@ -652,14 +710,15 @@ def main():
                                       "dem_get_sources (pinned host, 14 doubles per cell) + dem_reduction_degree"}
         line["e2e_coupling"] = legs
     if not args.no_dense_leg:
-        line["dense"] = dense_leg(binding, stream, tuning, 2000, min(max(args.steps, 100), 200),
-                                  args.precision, args.parcels)
-        line["dense_conduction"] = dense_leg(binding, stream, tuning, 2000, min(max(args.steps, 100), 200),
-                                             args.precision, args.parcels, conduction=True)
+        line["dense"] = dense_leg(binding, stream, tuning, 100, 100, args.precision, args.parcels)
+        line["dense_conduction"] = dense_leg(binding, stream, tuning, 100, 100, args.precision, args.parcels,
+                                             conduction=True)
     if rank == 0 and not args.no_batched_leg and not args.parcels:
         line["batched_32"] = batched_leg(binding, stream, args.settle, min(max(args.steps, 100), 200),
                                          args.precision)
 
+    if rank == 0 and not args.no_gas_solver_leg and not args.parcels:
+        line["gas_solver"] = gas_solver_leg(binding, stream, tuning, min(max(args.steps, 40), 100), args.precision)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(bed, 1, args.cpu_sample)
     mean, _ = ctx.dem_reduction_degree()

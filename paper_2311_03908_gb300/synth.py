@@ -366,26 +366,28 @@ def config_split_200k(seed: int = 2311039082, n: int = 200_000) -> Bed:
 
 def config_ibm_2m(seed: int = 2311039083, n: int = 2_000_000, v_scale: float = 0.0,
                   solid_fraction: float = 0.4, U_in: float = 0.3, name: str = "ibm_2m",
-                  fill: float = 0.75, jitter: float = 1.0, compress: float = 0.0) -> Bed:
+                  fill: float = 0.75, jitter: float = 1.0, compress: float = 0.0, sigma: float = 0.25) -> Bed:
     cfg = BedConfig(D=0.1, H=0.6, wall_kind=WALL_CONE, cone_half_angle=math.radians(45.0),
                     cone_height=0.05, plate_z=0.05, hole_d=1e-3, hole_pitch=4e-3,
                     nx=64, ny=64, nz=384, dt=1e-5, cg_ratio=6.0, U_in=U_in, T_in=1023.0,
                     Y_in=(1.0, 0.0, 0.0), sphericity=(0.86, 0.85))
-    b = packed_bed(seed, n, cfg, 120e-6, 0.25, two_ores=True, z0=cfg.plate_z, name=name,
+    b = packed_bed(seed, n, cfg, 120e-6, sigma, two_ores=True, z0=cfg.plate_z, name=name,
                    v_scale=v_scale, solid_fraction=solid_fraction, fill=fill, jitter=jitter, compress=compress)
     b.meta["steps"] = 500
     return b
 
 
-def config_ibm_2m_dense(seed: int = 2311039086, n: int = 2_000_000, v_scale: float = 0.05,
-                        U_in: float = 0.3, compress: float = 0.005) -> Bed:
-    """The 2M bed as a jammed packing: every lattice site filled, each sphere on its site, the
-    pitch 0.5 % below the largest diameter of its stratum, so that lattice neighbours overlap
-    by up to a few micrometres (about 2.7 contacts per parcel from the first step: the
-    contact-dominated regime of a settled bed), with random velocities. U_in below about
-    0.03 m/s keeps it packed (below minimum fluidisation of 120 um ore in H2 at 1023 K)."""
+def config_ibm_2m_dense(seed: int = 2311039086, n: int = 2_000_000, v_scale: float = 0.0,
+                        U_in: float = 0.0, compress: float = 0.0, sigma: float = 0.0) -> Bed:
+    """The 2M bed as a fixed packed bed: 120 um parcels (k = 6) of one size, every site of a
+    square lattice filled, each sphere on its site and the pitch equal to the diameter, so
+    that lattice neighbours touch; resting on the plate, the packing is compressed by its own
+    weight within a few hundred steps into a static bed in which every parcel has its
+    lattice contacts (the contact-dominated regime of a settled bed). No gas flow by
+    default (U_in below about 0.03 m/s, minimum fluidisation of 120 um ore in H2 at 1023 K,
+    keeps it packed)."""
     return config_ibm_2m(seed, n, v_scale=v_scale, solid_fraction=0.6, U_in=U_in, name="ibm_2m_dense",
-                         fill=1.0, jitter=0.0, compress=compress)
+                         fill=1.0, jitter=0.0, compress=compress, sigma=sigma)
 
 
 def config_adjoint_64k(seed: int = 2311039084, n: int = 64_000) -> Bed:

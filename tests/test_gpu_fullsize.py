@@ -154,7 +154,8 @@ def test_ibm_2m_split_form_after_20_steps(bench_bed):
 
 
 def test_ibm_2m_dense_bed_fp64_and_split_after_10_steps():
-    bed = synth.config_ibm_2m_dense()
+    # the lattice jammed: neighbours overlap by up to 0.5 % of the larger diameter from the first step
+    bed = synth.config_ibm_2m_dense(v_scale=0.05, U_in=0.3, compress=0.005, sigma=0.25)
     ref = oracle.Oracle(bed)
     ref.step(10)
     r = _snap(ref, True)
