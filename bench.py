@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--no-dense-leg", action="store_true", help="skip the contact-dominated 2M bed")
     ap.add_argument("--no-batched-leg", action="store_true", help="skip the 32-bed batch")
     ap.add_argument("--no-gas-solver-leg", action="store_true", help="skip the 2M bed with the gas phase solved")
+    ap.add_argument("--gas-solver-only", action="store_true", help="run only the gas-solver leg, on --workload "
+                    "(ibm_2m or split_200k), and print its line (for profiling the solver on a small case)")
     ap.add_argument("--coupling", default="10,1,20", help="coupling intervals n = dt_CFD/dt_DEM of the "
                     "end-to-end legs; the first one is the e2e headline (Table 3: n = 10 for Bed II)")
     return ap.parse_args()
@@ -421,13 +423,13 @@ def batched_leg(binding, stream, settle, steps, precision):
             "f_ov_mean_per_bed_range": [float(mean.min()), float(mean.max())]}
 
 
-def gas_solver_leg(binding, stream, tuning, steps, precision):
-    """The 2M cone-and-plate bed with the gas phase solved on the GPU (momentum, energy and
-    species every 10 steps, the pressure by multigrid-preconditioned CG): the whole coupled
-    step, timed like the headline one, and the solver's share."""
+def gas_solver_leg(binding, stream, tuning, steps, precision, workload="ibm_2m"):
+    """A bed (by default the 2M cone-and-plate bed) with the gas phase solved on the GPU
+    (momentum, energy and species every 10 steps, the pressure by multigrid-preconditioned
+    CG): the whole coupled step, timed like the headline one, and the solver's share."""
     import torch
     from paper_2311_03908_gb300 import synth
-    bed = synth.config_ibm_2m()
+    bed = make_workload(workload)
     for c in bed.beds:
         c.flags |= synth.GAS_SOLVER
         c.coupling_interval = 10
@@ -454,7 +456,7 @@ def gas_solver_leg(binding, stream, tuning, steps, precision):
     cx.close()
     gas = {k: v[1] / 2 for k, v in t.items() if k.startswith("k_gs_")}
     total = sum(v[1] for v in t.values()) / 2
-    return {"workload": f"ibm_2m ({bed.n} parcels, {bed.beds[0].nx}x{bed.beds[0].ny}x{bed.beds[0].nz} gas cells) "
+    return {"workload": f"{workload} ({bed.n} parcels, {bed.beds[0].nx}x{bed.beds[0].ny}x{bed.beds[0].nz} gas cells) "
                         "with the gas phase solved, coupling interval 10",
             "ms_per_step": ms / steps, "value": bed.n * steps / (ms * 1e-3), "unit": UNIT, "steps": steps,
             "cg_iterations_last_solve": iters, "preconditioner": "multigrid V(2,2), coarse weight 1.5",
@@ -546,6 +548,12 @@ def main():
     torch.cuda.set_device(local)
     from paper_2311_03908_gb300 import binding
     stream = torch.cuda.current_stream()
+    if args.gas_solver_only:
+        tun = {k: int(v) for k, v in (kv.split("=") for kv in args.tuning.split(","))} if args.tuning else {}
+        leg = gas_solver_leg(binding, stream, tun, args.steps, args.precision, args.workload)
+        if rank == 0:
+            print(json.dumps({"impl": "ours", "gas_solver": leg}), flush=True)
+        return
     bed = make_workload(args.workload, rank, args.parcels, args.radiation, args.conduction)
     ctx = binding.Context(bed, precision=args.precision, stream=stream.cuda_stream)
     n = bed.n
