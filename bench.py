@@ -67,8 +67,9 @@ def parse():
     ap.add_argument("--no-dense-leg", action="store_true", help="skip the contact-dominated 2M bed")
     ap.add_argument("--no-batched-leg", action="store_true", help="skip the 32-bed batch")
     ap.add_argument("--no-gas-solver-leg", action="store_true", help="skip the 2M bed with the gas phase solved")
-    ap.add_argument("--gas-solver-only", action="store_true", help="run only the gas-solver leg, on --workload "
-                    "(ibm_2m or split_200k), and print its line (for profiling the solver on a small case)")
+    ap.add_argument("--only-leg", default="", choices=["", "gas_solver", "dense", "dense_conduction"],
+                    help="run only this leg and print its line (for profiling one regime on a small case): "
+                    "gas_solver on --workload (ibm_2m or split_200k), the dense legs with --parcels")
     ap.add_argument("--coupling", default="10,1,20", help="coupling intervals n = dt_CFD/dt_DEM of the "
                     "end-to-end legs; the first one is the e2e headline (Table 3: n = 10 for Bed II)")
     return ap.parse_args()
@@ -548,11 +549,15 @@ def main():
     torch.cuda.set_device(local)
     from paper_2311_03908_gb300 import binding
     stream = torch.cuda.current_stream()
-    if args.gas_solver_only:
+    if args.only_leg:
         tun = {k: int(v) for k, v in (kv.split("=") for kv in args.tuning.split(","))} if args.tuning else {}
-        leg = gas_solver_leg(binding, stream, tun, args.steps, args.precision, args.workload)
+        if args.only_leg == "gas_solver":
+            leg = gas_solver_leg(binding, stream, tun, args.steps, args.precision, args.workload)
+        else:
+            leg = dense_leg(binding, stream, tun, 100, args.steps, args.precision, args.parcels,
+                            conduction=args.only_leg == "dense_conduction")
         if rank == 0:
-            print(json.dumps({"impl": "ours", "gas_solver": leg}), flush=True)
+            print(json.dumps({"impl": "ours", args.only_leg: leg}), flush=True)
         return
     bed = make_workload(args.workload, rank, args.parcels, args.radiation, args.conduction)
     ctx = binding.Context(bed, precision=args.precision, stream=stream.cuda_stream)

@@ -1190,10 +1190,15 @@ __device__ __forceinline__ void store_props(StepView<P> &V, long long c, const C
 }
 
 // sums of the per-parcel sources of [jb, je): FP64 in the FP64 form, compensated FP32
-// (Kahan) in the FP32 forms
+// (Kahan) in the FP32 forms; MASK selects the rows summed (the others stay 0)
+constexpr unsigned SR_ALL = (1u << SR_CNT) - 1u;
+// the rows the prescribed gas update reads
+constexpr unsigned SR_GAS = (1u << SR_VS) | (1u << SR_SH2) | (1u << SR_SH2O) | (1u << SR_HA) | (1u << SR_HAT) |
+                            (1u << SR_QRM);
 template <class P> struct CellSum {
   using S = typename P::R;
   S s[SR_N];
+  template <unsigned MASK = SR_ALL>
   __device__ __forceinline__ void run(const S *src, size_t cp, const unsigned *vals, unsigned jb, unsigned je) {
     if constexpr (!P::exact) {
       float cc[SR_CNT];
@@ -1203,6 +1208,7 @@ template <class P> struct CellSum {
         const unsigned j = vals[jj];
 #pragma unroll
         for (int f = 0; f < SR_CNT; ++f) {
+          if (!((MASK >> f) & 1u)) continue;
           const float y = src[f * cp + j] - cc[f];
           const float t = s[f] + y;
           cc[f] = (t - s[f]) - y;
@@ -1217,7 +1223,8 @@ template <class P> struct CellSum {
       for (unsigned jj = jb; jj < je; ++jj) {
         const unsigned j = vals[jj];
 #pragma unroll
-        for (int f = 0; f < SR_CNT; ++f) s[f] += src[f * cp + j];
+        for (int f = 0; f < SR_CNT; ++f)
+          if ((MASK >> f) & 1u) s[f] += src[f * cp + j];
       }
     }
     s[SR_CNT] = (S)(je - jb);
@@ -1251,7 +1258,7 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 5) k_cells(StepView<P> V, 
       eps = solid ? B.eps_min : fmax(1.0 - vs / B.vcell, B.eps_min);
     } else if (update) {
       CellSum<P> S;
-      S.run(V.src, cp, V.vals, V.cstart[c], V.cend[c]);
+      S.run<SR_GAS>(V.src, cp, V.vals, V.cstart[c], V.cend[c]);
       const bool up = c - B.cell_off >= layer && !V.mark[c - layer];
       const double dtg = B.ncouple * B.dt;
       const double rho = (double)V.gp[(size_t)c * GP_STRIDE + GP_RHO], cpg = (double)V.gp[(size_t)c * GP_STRIDE + GP_CP];
@@ -1306,7 +1313,7 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 5) k_cells(StepView<P> V, 
       eps2 = make_float2(solid ? bp.eps_min : (e > bp.eps_min ? e : bp.eps_min), 0.f);
     } else if (update) {
       CellSum<P> S;
-      S.run(V.src, cp, V.vals, V.cstart[c], V.cend[c]);
+      S.run<SR_GAS>(V.src, cp, V.vals, V.cstart[c], V.cend[c]);
       const bool up = c - B.cell_off >= layer && !V.mark[c - layer];
       const Tab<R> &t = tab<R>();
       const R dtg = bp.dtg;
