@@ -306,9 +306,10 @@ int dem_get_diag(dem_ctx *c, double *out_host);
  *       1 = every build): between re-stores the records stay where they are and the
  *       search reads them through the sort's permutation;
  *   [9] preconditioner of the gas solver's pressure equation (DEM_GAS_SOLVER): 0 = Jacobi,
- *       1 or 2 = a multigrid V-cycle with that many damped-Jacobi sweeps before and after
- *       each coarse correction (default 2; Galerkin coarse levels of 2 x 2 x 2 aggregates,
- *       down to one cell per bed); the solve converges to the same tolerance either way;
+ *       1 or 2 = an FP32 multigrid V-cycle (under the flexible form of the FP64 conjugate
+ *       gradients) with that many damped-Jacobi sweeps before and after each coarse
+ *       correction (default 2; Galerkin coarse levels of 2 x 2 x 2 aggregates, down to one
+ *       cell per bed); the solve converges to the same FP64 tolerance either way;
  *   [10] weight of the multigrid coarse correction in percent (50..200, default 150: the
  *        piecewise-constant aggregates' correction falls short, and over-correcting it
  *        halves the iterations).

@@ -432,26 +432,24 @@ void layout(dem_ctx *c, Bump &m) {
     // multigrid levels
     const int nl = (int)c->hlev.size();
     c->dlbed.assign(nl, nullptr);
-    for (int l = 1; l < nl; ++l) {
+    for (int l = 0; l < nl; ++l) {   // FP32 operators and iterates (level 0: copies of the FP64 one)
       GsLevel &Lv = c->hlev[l];
+      if (l == 0) Lv.n = c->ncells;
       const size_t n = (size_t)Lv.n;
-      Lv.L = m.take<double>(3 * n);
-      Lv.diag = m.take<double>(n); Lv.out = m.take<double>(n); Lv.dinv = m.take<double>(n);
-      Lv.b = m.take<double>(n); Lv.xa = m.take<double>(n); Lv.xb = m.take<double>(n);
-      c->dlbed[l] = m.take<int>(n);
-      Lv.bed = c->dlbed[l];
+      Lv.L = m.take<float>(3 * n);
+      Lv.diag = m.take<float>(n); Lv.out = m.take<float>(n); Lv.dinv = m.take<float>(n);
+      Lv.b = m.take<float>(n); Lv.xa = m.take<float>(n); Lv.xb = m.take<float>(n);
+      if (l > 0) {
+        c->dlbed[l] = m.take<int>(n);
+        Lv.bed = c->dlbed[l];
+      } else {
+        Lv.bed = c->cell_bed;
+      }
     }
     c->dlpar.assign(nl, nullptr);
     for (int l = 0; l + 1 < nl; ++l) {
       c->dlpar[l] = m.take<int>((size_t)(l == 0 ? c->ncells : c->hlev[l].n));
       c->hlev[l].parent = c->dlpar[l];
-    }
-    if (nl > 0) {
-      GsLevel &L0 = c->hlev[0];
-      L0.n = c->ncells;
-      L0.L = S.co + (size_t)GC_L * C; L0.diag = S.co + (size_t)GC_DIAG * C; L0.out = S.co + (size_t)GC_OUT * C;
-      L0.dinv = S.co + (size_t)GC_DINV * C;
-      L0.b = S.r; L0.xa = S.Ap; L0.xb = S.z; L0.bed = c->cell_bed;
     }
     for (int l = 0; l < nl; ++l) {   // uniform dims per level
       const GsLevelBed *g = &c->hlb[(size_t)l * c->nbeds];

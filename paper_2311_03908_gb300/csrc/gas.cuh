@@ -34,8 +34,7 @@ enum : int {
                                 // it is open, else 0 (an upper face's is the upper neighbour's lower one)
   GC_DIAG = GC_L + 3,           // the sum over the cell's open faces plus its outlet's
   GC_OUT = GC_DIAG + 1,         // the outlet's coefficient (0 below the top)
-  GC_DINV = GC_OUT + 1,         // the smoother's GS_OMEGA / diag
-  GC_RHS = GC_DINV + 1,
+  GC_RHS = GC_OUT + 1,
   GC_DIV = GC_RHS + 1,          // div(eps u) that continuity requires of the new flow, 1/s
   GC_N
 };
@@ -48,12 +47,15 @@ constexpr double GS_CG_TOL = 1e-12;   // relative residual of the pressure corre
 // piecewise-constant prolongation): a coarse cell's lower-face coefficient is the sum of its
 // children's across that face, its diagonal the sum of its external faces' and outlets'.
 constexpr int GS_MAXLEV = 16;
+// The preconditioner runs in FP32 (level 0 holds FP32 copies of the FP64 pressure operator);
+// the CG around it stays FP64 and takes the flexible (Polak-Ribiere) beta, so the FP32
+// rounding of the V-cycle does not limit the FP64 solve.
 struct GsLevel {
   long long n;                  // cells, all beds
-  double *L;                    // [3][n] lower x-, y-, z-face coefficients
-  double *diag, *out;           // diagonal; the outlet's part of it
-  double *dinv;                 // GS_OMEGA / diag (0 for an empty cell), set with the operator
-  double *b, *xa, *xb;          // right-hand side, two iterate buffers (the result ends in xb)
+  float *L;                     // [3][n] lower x-, y-, z-face coefficients
+  float *diag, *out;            // diagonal; the outlet's part of it
+  float *dinv;                  // GS_OMEGA / diag (0 for an empty cell), set with the operator
+  float *b, *xa, *xb;           // right-hand side, two iterate buffers
   const int *bed;               // bed of each cell
   const int *parent;            // the cell of level l + 1 that holds each cell (none on the coarsest)
   int ux, uy;                   // nx, ny when every bed has the same dims at this level, else 0
@@ -71,8 +73,8 @@ struct GasView {
   double *dep;                  // cell sums of the coupling step [ncells][DEM_NDEP]
   const BedP<double> *bpd;
   long long nfx, nfy, nfz;
-  // preconditioner: mg_nu = 0 Jacobi, else a multigrid V-cycle with mg_nu damped-Jacobi
-  // sweeps before and after each coarse correction, the correction weighted by mg_alpha
+  // preconditioner: mg_nu = 0 Jacobi, else an FP32 multigrid V-cycle with mg_nu damped-
+  // Jacobi sweeps before and after each coarse correction, the correction weighted by mg_alpha
   int mg_nu, nlev, nbeds;
   double mg_alpha;
   const GsLevel *lev;           // [nlev]
@@ -380,10 +382,10 @@ __global__ void k_gs_rhs(StepView<P> V, GasView S) {
 
 // 5. preconditioned conjugate gradients on -L p'' = -rhs, from p'' = 0, to a relative
 // residual GS_CG_TOL (at most GS_CG_MAXIT iterations): one cooperative kernel whose blocks
-// meet at grid barriers. The preconditioner is Jacobi (mg_nu = 0) or one symmetric multigrid
+// meet at grid barriers. The preconditioner is Jacobi (mg_nu = 0) or one FP32 multigrid
 // V-cycle (damped Jacobi before and after the coarse correction, the coarsest level of one
-// cell per bed solved exactly); either converges to the same tolerance, so the answer
-// differs from the Jacobi-preconditioned solve by rounding only. The search direction is
+// cell per bed solved exactly) under the flexible form of CG; either converges to the same
+// FP64 tolerance, so the answer differs from the Jacobi-preconditioned solve by rounding only. The search direction is
 // double-buffered so that p_k = z_k + beta p_{k-1} is formed where -L p_k is (neighbours
 // recomputed from z and p_{k-1}). Sums are per-block partials added in block order by every
 // block: the same value in every block, reproducible run to run.
@@ -430,37 +432,36 @@ __device__ __forceinline__ void gs_grid_sums(const double *part, int slot0, doub
   __syncthreads();
 }
 
-// (A x)_i of the operator of a level (A = -L: diag x_i - sum over open faces c_f x_nb); the
-// upper neighbour along an axis is i + stride: where that steps out of the row or the plane
-// the cell reached (same bed) has the box side as its lower face, coefficient 0; out of the
-// bed there is none
-__device__ __forceinline__ double gs_apply(const GsLevel &Lv, const GsLevelBed &g, long long i, const double *x) {
-  const long long st[3] = {1, g.nx, (long long)g.nx * g.ny};
-  const long long end = g.off + st[2] * g.nz;
-  double acc = Lv.diag[i] * x[i];
+// (A x)_i of the operator of a level (A = -L: diag x_i - sum over open faces c_f x_nb), for
+// x read through XV (a plain array, or one with a coarse correction added as it is read).
+// The upper neighbour along an axis is i + stride: where that steps out of the row or the
+// plane, the cell reached (same bed) has the box side as its lower face, coefficient 0;
+// where every bed has the same dims the bed's top steps into the next bed's bottom cell,
+// whose lower z-face coefficient is 0 too (an inlet or a wall), so only the array's end
+// bounds it; otherwise the bed's end does.
+template <class XV>
+__device__ __forceinline__ float gs_apply(const GsLevel &Lv, long long sy, long long sz, long long end, long long i,
+                                          const XV &xv) {
+  const long long st[3] = {1, sy, sz};
+  float acc = Lv.diag[i] * xv(i);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const double cl = Lv.L[a * Lv.n + i];
-    const double ch = i + st[a] < end ? Lv.L[a * Lv.n + i + st[a]] : 0.0;
-    if (cl != 0.0) acc -= cl * x[i - st[a]];
-    if (ch != 0.0) acc -= ch * x[i + st[a]];
+    const float cl = Lv.L[a * Lv.n + i];
+    const float ch = i + st[a] < end ? Lv.L[a * Lv.n + i + st[a]] : 0.0f;
+    if (cl != 0.0f) acc -= cl * xv(i - st[a]);
+    if (ch != 0.0f) acc -= ch * xv(i + st[a]);
   }
   return acc;
 }
-// the same where every bed has the same dims: the upper neighbour across a bed's top is the
-// next bed's bottom cell, whose lower z-face coefficient is 0 (an inlet or a wall)
-__device__ __forceinline__ double gs_apply_u(const double *__restrict__ L, const double *__restrict__ diag, long long n,
-                                             long long sy, long long sz, long long i, const double *__restrict__ x) {
-  const long long st[3] = {1, sy, sz};
-  double acc = diag[i] * x[i];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const double cl = L[a * n + i];
-    const double ch = i + st[a] < n ? L[a * n + i + st[a]] : 0.0;
-    if (cl != 0.0) acc -= cl * x[i - st[a]];
-    if (ch != 0.0) acc -= ch * x[i + st[a]];
+// strides and end of cell i's bed at a level
+__device__ __forceinline__ void gs_strides(const GasView &S, const GsLevel &Lv, int l, long long i, long long &sy,
+                                           long long &sz, long long &end) {
+  if (Lv.ux > 0) {
+    sy = Lv.ux; sz = (long long)Lv.ux * Lv.uy; end = Lv.n;
+  } else {
+    const GsLevelBed g = S.lb[(size_t)l * S.nbeds + Lv.bed[i]];
+    sy = g.nx; sz = (long long)g.nx * g.ny; end = g.off + sz * g.nz;
   }
-  return acc;
 }
 __device__ __forceinline__ void gs_local(const GsLevelBed &g, long long i, int &x, int &y, int &z) {
   const int l = (int)(i - g.off);   // a bed has fewer than 2^30 cells
@@ -469,14 +470,28 @@ __device__ __forceinline__ void gs_local(const GsLevelBed &g, long long i, int &
   z = q / g.ny;
   y = q - z * g.ny;
 }
-// levels of at most this many cells are smoothed, restricted and prolonged by one block
-// alone (block barriers instead of grid barriers)
+// levels of at most this many cells are smoothed and restricted by one block alone (block
+// barriers instead of grid barriers)
 constexpr long long GS_SMALL = 2048;
+
+// level 0 of the preconditioner: FP32 copies of this step's pressure operator
+__device__ __forceinline__ void gs_mg_level0(const GasView &S, const GsLevel &L0, long long c0, long long stride) {
+  const size_t nc = (size_t)L0.n;
+  const double *L = S.co + GC_L * nc, *dg = S.co + GC_DIAG * nc, *ot = S.co + GC_OUT * nc;
+  for (long long c = c0; c < L0.n; c += stride) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) L0.L[a * nc + c] = (float)L[a * nc + c];
+    const double d = dg[c];
+    L0.diag[c] = (float)d;
+    L0.out[c] = (float)ot[c];
+    L0.dinv[c] = d > 0.0 ? (float)(GS_OMEGA / d) : 0.0f;
+  }
+}
 
 // Galerkin coefficients of level l + 1 from level l: per coarse cell, over its children
 static __device__ __noinline__ void gs_mg_setup(const GasView &S, const GsLevel *lev, int l, long long c0,
                                                 long long stride) {
-  const GsLevel &F = lev[l], &Cv = lev[l + 1];   // by value: the stores below cannot alias them
+  const GsLevel &F = lev[l], &Cv = lev[l + 1];
   for (long long I = c0; I < Cv.n; I += stride) {
     const int b = Cv.bed[I];
     const GsLevelBed gf = S.lb[(size_t)l * S.nbeds + b], gc = S.lb[(size_t)(l + 1) * S.nbeds + b];
@@ -484,7 +499,7 @@ static __device__ __noinline__ void gs_mg_setup(const GasView &S, const GsLevel 
     gs_local(gc, I, X, Y, Z);
     const int C[3] = {X, Y, Z}, nf[3] = {gf.nx, gf.ny, gf.nz};
     const long long st[3] = {1, gf.nx, (long long)gf.nx * gf.ny};
-    double Lc[3] = {0.0, 0.0, 0.0}, dc = 0.0, oc = 0.0;
+    float Lc[3] = {0.0f, 0.0f, 0.0f}, dc = 0.0f, oc = 0.0f;
     for (int dk = 0; dk < 2; ++dk)
       for (int dj = 0; dj < 2; ++dj)
         for (int di = 0; di < 2; ++di) {
@@ -495,7 +510,7 @@ static __device__ __noinline__ void gs_mg_setup(const GasView &S, const GsLevel 
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
             if ((f[a] - 1) >> 1 != C[a] || f[a] == 0) {   // lower face external (or the box side)
-              const double v = F.L[a * F.n + i];
+              const float v = F.L[a * F.n + i];
               Lc[a] += v;
               dc += v;
             }
@@ -506,107 +521,103 @@ static __device__ __noinline__ void gs_mg_setup(const GasView &S, const GsLevel 
     for (int a = 0; a < 3; ++a) Cv.L[a * Cv.n + I] = Lc[a];
     Cv.diag[I] = dc + oc;
     Cv.out[I] = oc;
-    Cv.dinv[I] = dc + oc > 0.0 ? GS_OMEGA / (dc + oc) : 0.0;
+    Cv.dinv[I] = dc + oc > 0.0f ? (float)GS_OMEGA / (dc + oc) : 0.0f;
   }
 }
 
-// one damped-Jacobi sweep of level l, x_dst = x_src + omega D^-1 (b - A x_src); from x = 0
-// when src is null. With rz, the r . x_dst partial of the final level-0 sweep.
-__device__ __forceinline__ void gs_mg_sweep(const GasView &S, const GsLevel *lev, int l, const double *src, double *dst,
-                                            long long c0, long long stride, double *rz) {
+// A damped-Jacobi sweep of level l, x_dst = x' + omega D^-1 (b - A x'), with x' = x_src, or
+// with CORR x' = x_src + w P x_c (the coarse correction applied as the values are read, so no
+// barrier separates it from the sweep). FINAL (level 0): the result goes to the FP64 z of the
+// CG, with the partial sums r . z and r . z_old.
+template <bool CORR, bool FINAL>
+__device__ __forceinline__ void gs_sweep(const GasView &S, const GsLevel *lev, int l, const float *src, float *dst,
+                                         long long c0, long long stride, double *rz, double *rzo) {
   const GsLevel &Lv = lev[l];
-  const double *__restrict__ L = Lv.L;
-  const double *__restrict__ dg = Lv.diag;
-  const double *__restrict__ di = Lv.dinv;
-  const double *__restrict__ b = Lv.b;
-  const long long n = Lv.n;
-  if (Lv.ux > 0) {   // uniform dims: no per-cell bed lookup
-    const long long sy = Lv.ux, sz = (long long)Lv.ux * Lv.uy;
-    for (long long i = c0; i < n; i += stride) {
-      const double w = di[i];
-      double v = 0.0;
-      if (w != 0.0) v = src ? src[i] + (b[i] - gs_apply_u(L, dg, n, sy, sz, i, src)) * w : b[i] * w;
-      dst[i] = v;
-      if (rz) *rz += b[i] * v;
+  const float *__restrict__ xc = CORR ? lev[l + 1].xb : nullptr;
+  const int *__restrict__ par = Lv.parent;
+  const float w = (float)S.mg_alpha;
+  auto xv = [&](long long k) -> float { return CORR ? src[k] + w * xc[par[k]] : src[k]; };
+  for (long long i = c0; i < Lv.n; i += stride) {
+    const float di = Lv.dinv[i];
+    float v = 0.0f;
+    if (di != 0.0f) {
+      long long sy, sz, end;
+      gs_strides(S, Lv, l, i, sy, sz, end);
+      v = xv(i) + (Lv.b[i] - gs_apply(Lv, sy, sz, end, i, xv)) * di;
     }
-    return;
-  }
-  const GsLevelBed *lb = S.lb + (size_t)l * S.nbeds;
-  for (long long i = c0; i < n; i += stride) {
-    const double w = di[i];
-    double v = 0.0;
-    if (w != 0.0) v = src ? src[i] + (b[i] - gs_apply(Lv, lb[Lv.bed[i]], i, src)) * w : b[i] * w;
-    dst[i] = v;
-    if (rz) *rz += b[i] * v;
+    if constexpr (FINAL) {
+      const double zo = S.z[i], rc = S.r[i];
+      S.z[i] = (double)v;
+      *rz += rc * (double)v;
+      *rzo += rc * zo;
+    } else {
+      dst[i] = v;
+    }
   }
 }
 
-// restriction of level l's residual b - A x (x: the iterate xf) to level l + 1's right-hand side,
-// with the first sweep there (from 0), or the exact solve of the coarsest level (one cell
-// per bed) into its xb
-__device__ __forceinline__ void gs_mg_restrict(const GasView &S, const GsLevel *lev, int l, const double *xf,
+// restriction of level l's residual b - A x (x: the iterate xf) to level l + 1's right-hand
+// side, with the first sweep there (from 0), or the exact solve of the coarsest level (one
+// cell per bed) into its xb
+__device__ __forceinline__ void gs_mg_restrict(const GasView &S, const GsLevel *lev, int l, const float *xf,
                                                long long c0, long long stride) {
   const GsLevel &F = lev[l], &Cv = lev[l + 1];
   const bool coarsest = l + 2 == S.nlev;
+  auto xv = [&](long long k) -> float { return xf[k]; };
   for (long long I = c0; I < Cv.n; I += stride) {
     const int b = Cv.bed[I];
     const GsLevelBed gf = S.lb[(size_t)l * S.nbeds + b], gc = S.lb[(size_t)(l + 1) * S.nbeds + b];
     int X, Y, Z;
     gs_local(gc, I, X, Y, Z);
-    double sum = 0.0;
+    const long long sy = gf.nx, sz = (long long)gf.nx * gf.ny;
+    const long long end = F.ux > 0 ? F.n : gf.off + sz * gf.nz;
+    float sum = 0.0f;
     for (int dk = 0; dk < 2; ++dk)
       for (int dj = 0; dj < 2; ++dj)
         for (int di = 0; di < 2; ++di) {
           const int fx = 2 * X + di, fy = 2 * Y + dj, fz = 2 * Z + dk;
           if (fx >= gf.nx || fy >= gf.ny || fz >= gf.nz) continue;
           const long long i = gf.off + ((long long)fz * gf.ny + fy) * gf.nx + fx;
-          if (F.diag[i] > 0.0)
-            sum += F.b[i] - (F.ux > 0 ? gs_apply_u(F.L, F.diag, F.n, F.ux, (long long)F.ux * F.uy, i, xf)
-                                      : gs_apply(F, gf, i, xf));
+          if (F.dinv[i] != 0.0f) sum += F.b[i] - gs_apply(F, sy, sz, end, i, xv);
         }
     Cv.b[I] = sum;
-    const double w = Cv.dinv[I];
-    if (coarsest) Cv.xb[I] = sum * (w * (1.0 / GS_OMEGA));   // one cell per bed: exact
+    const float w = Cv.dinv[I];
+    if (coarsest) Cv.xb[I] = sum * (w * (float)(1.0 / GS_OMEGA));   // one cell per bed: exact
     else Cv.xa[I] = sum * w;
   }
 }
 
-// prolongation: level l's current iterate += alpha times its parent's correction
-__device__ __forceinline__ void gs_mg_prolong(const GasView &S, const GsLevel *lev, int l, double *x, long long c0,
-                                              long long stride) {
-  const GsLevel &F = lev[l];
-  const double *__restrict__ xc = lev[l + 1].xb;
-  const int *__restrict__ par = F.parent;
-  const double w = S.mg_alpha;
-  for (long long i = c0; i < F.n; i += stride)
-    if (F.diag[i] > 0.0) x[i] += w * xc[par[i]];
-}
-
-// One V-cycle z = M r (r: level 0's b; z: level 0's xb) and the grid's r . z. The sweep
-// counts before and after each coarse correction are equal and the smoother is symmetric,
-// so M is symmetric; every sweep after the first reads its neighbours, so a grid barrier
-// separates the phases.
-static __device__ __noinline__ double gs_vcycle(const GasView &S, const GsLevel *lev,
-                                                cooperative_groups::grid_group &grid, long long c0, long long stride,
-                                                double *sh) {
+// One V-cycle z = M r (r, z: the CG's FP64 vectors) and the grid's r . z and r . z_old. The
+// sweep counts before and after each coarse correction are equal and the smoother is
+// symmetric, so M is symmetric up to the FP32 rounding; every sweep after the first reads its
+// neighbours, so a barrier separates the phases.
+static __device__ __noinline__ void gs_vcycle(const GasView &S, const GsLevel *lev,
+                                              cooperative_groups::grid_group &grid, long long c0, long long stride,
+                                              double *sh, double (&out)[2]) {
   const int nu = S.mg_nu;
-  double rz = 0.0;
+  double rz = 0.0, rzo = 0.0;
+  const GsLevel &L0 = lev[0];
   if (S.nlev == 1) {   // one cell per bed: the exact solve
-    const GsLevel &L0 = lev[0];
     for (long long i = c0; i < L0.n; i += stride) {
-      const double v = L0.b[i] * (L0.dinv[i] * (1.0 / GS_OMEGA));
-      L0.xb[i] = v;
-      rz += L0.b[i] * v;
+      const double rc = S.r[i], zo = S.z[i];
+      const double v = rc * ((double)L0.dinv[i] * (1.0 / GS_OMEGA));
+      S.z[i] = v;
+      rz += rc * v;
+      rzo += rc * zo;
     }
   } else {
     int ls = S.nlev;   // the first level that one block handles
     for (int l = 1; l < S.nlev; ++l)
       if (lev[l].n <= GS_SMALL) { ls = l; break; }
-    gs_mg_sweep(S, lev, 0, nullptr, lev[0].xa, c0, stride, nullptr);
+    for (long long i = c0; i < L0.n; i += stride) {   // level 0: b = r, first sweep from 0
+      const float b = (float)S.r[i];
+      L0.b[i] = b;
+      L0.xa[i] = b * L0.dinv[i];
+    }
     grid.sync();
     for (int l = 0; l < ls && l + 1 < S.nlev; ++l) {   // down: smooth, restrict (first sweep below fused)
       if (nu == 2) {
-        gs_mg_sweep(S, lev, l, lev[l].xa, lev[l].xb, c0, stride, nullptr);
+        gs_sweep<false, false>(S, lev, l, lev[l].xa, lev[l].xb, c0, stride, nullptr, nullptr);
         grid.sync();
       }
       gs_mg_restrict(S, lev, l, nu == 2 ? lev[l].xb : lev[l].xa, c0, stride);
@@ -617,42 +628,42 @@ static __device__ __noinline__ double gs_vcycle(const GasView &S, const GsLevel 
         const long long t0 = threadIdx.x, ts = blockDim.x;
         for (int l = ls; l + 1 < S.nlev; ++l) {
           if (nu == 2) {
-            gs_mg_sweep(S, lev, l, lev[l].xa, lev[l].xb, t0, ts, nullptr);
+            gs_sweep<false, false>(S, lev, l, lev[l].xa, lev[l].xb, t0, ts, nullptr, nullptr);
             __syncthreads();
           }
           gs_mg_restrict(S, lev, l, nu == 2 ? lev[l].xb : lev[l].xa, t0, ts);
           __syncthreads();
         }
         for (int l = S.nlev - 2; l >= ls; --l) {
-          gs_mg_prolong(S, lev, l, nu == 2 ? lev[l].xb : lev[l].xa, t0, ts);
-          __syncthreads();
           if (nu == 2) {
-            gs_mg_sweep(S, lev, l, lev[l].xb, lev[l].xa, t0, ts, nullptr);
+            gs_sweep<true, false>(S, lev, l, lev[l].xb, lev[l].xa, t0, ts, nullptr, nullptr);
             __syncthreads();
+            gs_sweep<false, false>(S, lev, l, lev[l].xa, lev[l].xb, t0, ts, nullptr, nullptr);
+          } else {
+            gs_sweep<true, false>(S, lev, l, lev[l].xa, lev[l].xb, t0, ts, nullptr, nullptr);
           }
-          gs_mg_sweep(S, lev, l, lev[l].xa, lev[l].xb, t0, ts, nullptr);
           __syncthreads();
         }
       }
       grid.sync();
     }
-    for (int l = (ls < S.nlev ? ls : S.nlev - 1) - 1; l >= 0; --l) {   // up: correct, smooth
-      gs_mg_prolong(S, lev, l, nu == 2 ? lev[l].xb : lev[l].xa, c0, stride);
-      grid.sync();
+    for (int l = (ls < S.nlev ? ls : S.nlev - 1) - 1; l >= 0; --l) {   // up: correct and smooth
       if (nu == 2) {
-        gs_mg_sweep(S, lev, l, lev[l].xb, lev[l].xa, c0, stride, nullptr);
+        gs_sweep<true, false>(S, lev, l, lev[l].xb, lev[l].xa, c0, stride, nullptr, nullptr);
         grid.sync();
+        if (l > 0) gs_sweep<false, false>(S, lev, l, lev[l].xa, lev[l].xb, c0, stride, nullptr, nullptr);
+        else gs_sweep<false, true>(S, lev, 0, lev[0].xa, nullptr, c0, stride, &rz, &rzo);
+      } else {
+        if (l > 0) gs_sweep<true, false>(S, lev, l, lev[l].xa, lev[l].xb, c0, stride, nullptr, nullptr);
+        else gs_sweep<true, true>(S, lev, 0, lev[0].xa, nullptr, c0, stride, &rz, &rzo);
       }
-      gs_mg_sweep(S, lev, l, lev[l].xa, lev[l].xb, c0, stride, l == 0 ? &rz : nullptr);
       if (l > 0) grid.sync();
     }
   }
-  double v[1] = {rz};
-  gs_block_sums<1>(v, S.part, 2, sh);
+  double v[2] = {rz, rzo};
+  gs_block_sums<2>(v, S.part, 2, sh);
   grid.sync();
-  double out[1];
-  gs_grid_sums<1>(S.part, 2, sh, out);
-  return out[0];
+  gs_grid_sums<2>(S.part, 2, sh, out);
 }
 
 template <class P>
@@ -674,8 +685,9 @@ __global__ void __launch_bounds__(GS_CG_BLOCK, 4) k_gs_cg(const DevBed *beds, co
   double *po = S.pa, *pn = S.pb;
   const bool mg = S.mg_nu > 0;
   const int uxy[2] = {lev[0].ux, lev[0].uy};
-  double *dinv0 = S.co + GC_DINV * nc;
-  if (mg) {   // the coarse levels' operators of this step's coefficients (small ones in block 0)
+  if (mg) {   // the preconditioner's operators of this step's coefficients (small levels in block 0)
+    gs_mg_level0(S, lev[0], c0, stride);
+    grid.sync();
     int l = 0;
     for (; l + 1 < S.nlev && lev[l + 1].n > GS_SMALL; ++l) {
       gs_mg_setup(S, lev, l, c0, stride);
@@ -695,13 +707,10 @@ __global__ void __launch_bounds__(GS_CG_BLOCK, 4) k_gs_cg(const DevBed *beds, co
     for (long long c = c0; c < ncells; c += stride) {
       const double rc = -rhs[c];
       r[c] = rc; x[c] = 0.0; po[c] = 0.0;
-      dinv0[c] = diag[c] > 0.0 ? GS_OMEGA / diag[c] : 0.0;
       v[0] += rc * rc;
-      if (!mg) {
-        const double zc = diag[c] > 0.0 ? rc / diag[c] : 0.0;
-        z[c] = zc;
-        v[1] += rc * zc;
-      }
+      const double zc = !mg && diag[c] > 0.0 ? rc / diag[c] : 0.0;
+      z[c] = zc;
+      v[1] += rc * zc;
     }
     gs_block_sums<2>(v, S.part, 1, sh);
   }
@@ -712,7 +721,11 @@ __global__ void __launch_bounds__(GS_CG_BLOCK, 4) k_gs_cg(const DevBed *beds, co
   double rz = s2[1], beta = 0.0;
   int it = 0;
   if (bnorm > 0.0) {
-    if (mg) rz = gs_vcycle(S, lev, grid, c0, stride, sh);
+    if (mg) {
+      double o2[2];
+      gs_vcycle(S, lev, grid, c0, stride, sh, o2);
+      rz = o2[0];
+    }
     for (; it < GS_CG_MAXIT; ++it) {
       // p_k and -L p_k
       double v1[1] = {0.0};
@@ -720,19 +733,12 @@ __global__ void __launch_bounds__(GS_CG_BLOCK, 4) k_gs_cg(const DevBed *beds, co
         const double pc = gs_cg_dir(z, po, beta, c);
         pn[c] = pc;
         double acc = diag[c] * pc;
-        if (diag[c] > 0.0 && uxy[0] > 0) {   // uniform dims: see gs_apply_u
-          const long long st[3] = {1, uxy[0], (long long)uxy[0] * uxy[1]};
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            const double cl = L[a * nc + c];
-            const double ch = c + st[a] < ncells ? L[a * nc + c + st[a]] : 0.0;
-            if (cl != 0.0) acc -= cl * gs_cg_dir(z, po, beta, c - st[a]);
-            if (ch != 0.0) acc -= ch * gs_cg_dir(z, po, beta, c + st[a]);
+        if (diag[c] > 0.0) {
+          long long st[3] = {1, uxy[0], (long long)uxy[0] * uxy[1]}, cend = ncells;   // uniform dims: see gs_apply
+          if (uxy[0] == 0) {
+            const DevBed &B = beds[cell_bed[c]];
+            st[1] = B.nx; st[2] = (long long)B.nx * B.ny; cend = B.cell_off + st[2] * B.nz;
           }
-        } else if (diag[c] > 0.0) {
-          const DevBed &B = beds[cell_bed[c]];
-          const long long st[3] = {1, B.nx, (long long)B.nx * B.ny};
-          const long long cend = B.cell_off + st[2] * B.nz;
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
             const double cl = L[a * nc + c];
@@ -766,9 +772,15 @@ __global__ void __launch_bounds__(GS_CG_BLOCK, 4) k_gs_cg(const DevBed *beds, co
       grid.sync();
       gs_grid_sums<2>(S.part, 1, sh, s2);
       if (sqrt(s2[0]) < GS_CG_TOL * bnorm) { ++it; break; }
-      const double rzn = mg ? gs_vcycle(S, lev, grid, c0, stride, sh) : s2[1];
-      beta = rzn / rz;
-      rz = rzn;
+      if (mg) {   // flexible beta: r_new . (z_new - z_old) / (r_old . z_old)
+        double o2[2];
+        gs_vcycle(S, lev, grid, c0, stride, sh, o2);
+        beta = (o2[0] - o2[1]) / rz;
+        rz = o2[0];
+      } else {
+        beta = s2[1] / rz;
+        rz = s2[1];
+      }
       double *t = po; po = pn; pn = t;
     }
   }
