@@ -301,7 +301,8 @@ def e2e_coupling(binding, stream, bed, ncouple, tuning, settle, steps):
     n = coupling_interval steps the gas field comes in from page-locked host memory
     (dem_set_gas: mass fractions and temperature of every cell), the n steps run as one
     replayed graph, and the cell sources of the coupling step go back to page-locked host
-    memory (dem_get_sources: 14 doubles per cell) with the bed reduction degrees."""
+    memory (dem_get_sources_occupied: 14 doubles and the index of every cell that holds
+    parcels, the others' sources being zero) with the bed reduction degrees."""
     import dataclasses
     import torch
     b2 = dataclasses.replace(bed, beds=[dataclasses.replace(c, coupling_interval=ncouple) for c in bed.beds])
@@ -312,27 +313,32 @@ def e2e_coupling(binding, stream, bed, ncouple, tuning, settle, steps):
     gas = cx.dem_get_gas()
     Y = torch.from_numpy(np.ascontiguousarray(gas[:, 1:4])).pin_memory()
     T = torch.from_numpy(np.ascontiguousarray(gas[:, 4])).pin_memory()
-    out = torch.empty((cx.ncells, 14), dtype=torch.float64).pin_memory()
+    cap = min(cx.n, cx.ncells)
+    out = torch.empty((cap, 14), dtype=torch.float64).pin_memory()
+    cells = torch.empty(cap, dtype=torch.int64).pin_memory()
     ncpl = max(3, steps // ncouple)
     for _ in range(2):             # warm-up couplings (graphs captured)
         cx.dem_set_gas(Y, T)
         cx.dem_step_graph(ncouple)
-        cx.dem_get_sources(out)
+        cx.dem_get_sources_occupied(cells, out)
         cx.dem_reduction_degree()
     torch.cuda.synchronize()
+    nocc = 0
     t0 = time.perf_counter()
     for _ in range(ncpl):
         cx.dem_set_gas(Y, T)
         cx.dem_step_graph(ncouple)
-        cx.dem_get_sources(out)
+        occ, _ = cx.dem_get_sources_occupied(cells, out)
+        nocc += len(occ)
         cx.dem_reduction_degree()
     torch.cuda.synchronize()
     te = time.perf_counter() - t0
     nsteps = ncpl * ncouple
     cx.close()
     return {"coupling_interval": ncouple, "steps": nsteps, "seconds": te, "ms_per_step": 1e3 * te / nsteps,
+            "occupied_cells": nocc / ncpl, "cells": int(Y.shape[0]),
             "h2d_bytes_per_step": int(Y.numel() * 8 + T.numel() * 8) / ncouple,
-            "d2h_bytes_per_step": int(out.numel() * 8 + len(bed.beds) * 16) / ncouple}
+            "d2h_bytes_per_step": (nocc / ncpl * (14 * 8 + 8) + 4 + len(bed.beds) * 16) / ncouple}
 
 
 def dense_leg(binding, stream, tuning, settle, steps, precision, parcels=0, conduction=False):
@@ -720,7 +726,8 @@ def main():
                                "d2h_bytes_per_step": int(r["d2h_bytes_per_step"]),
                                "coupling_interval": ncouple,
                                "api": "every n steps: dem_set_gas (pinned host Y, T) + dem_step_graph(n) + "
-                                      "dem_get_sources (pinned host, 14 doubles per cell) + dem_reduction_degree"}
+                                      "dem_get_sources_occupied (pinned host, 14 doubles and an index per cell "
+                                      "holding parcels) + dem_reduction_degree"}
         line["e2e_coupling"] = legs
     if not args.no_dense_leg:
         line["dense"] = dense_leg(binding, stream, tuning, 100, 100, args.precision, args.parcels)

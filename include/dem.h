@@ -271,6 +271,16 @@ int dem_get_gas(dem_ctx *c, double *out_host);
 enum { DEM_NDEP = 14 };
 int dem_get_sources(dem_ctx *c, double *out_host);
 
+/* The same sources for only the fluid cells that hold parcels (the others' are all zero), in
+ * increasing cell order: the coupling output of Sec. 4 without the empty cells, for a gas
+ * solver that takes sparse sources (no counterpart in the paper: it only changes how much
+ * crosses the link). *n_occupied (host) receives the number of such cells; cells_host (host,
+ * cap int64) their global cell indices and out_host (host, cap x DEM_NDEP doubles) their rows,
+ * identical to the rows dem_get_sources returns for them. If n_occupied exceeds cap, nothing
+ * else is written and DEM_EINVAL is returned (the count is, so the caller can size its
+ * buffers; at most min(parcels, cells)). Synchronous. */
+int dem_get_sources_occupied(dem_ctx *c, int64_t cap, int64_t *n_occupied, int64_t *cells_host, double *out_host);
+
 /* Gas flow of every cell, DEM_NFLOW doubles per cell (host): the cell-centre gas velocity
  * u_x u_y u_z (m/s; the mean of the cell's two faces on each axis where the gas is solved,
  * (0, 0, U_in / eps_g) where it is prescribed) and the pressure relative to p0 (Pa; 0 where

@@ -93,6 +93,7 @@ def lib() -> C.CDLL:
         "dem_get_gas": (C.c_int, [vp, dp]),
         "dem_get_sources": (C.c_int, [vp, dp]),
         "dem_get_flow": (C.c_int, [vp, dp, C.POINTER(C.c_int32)]),
+        "dem_get_sources_occupied": (C.c_int, [vp, C.c_int64, C.POINTER(C.c_int64), vp, vp]),
         "dem_get_contacts": (C.c_int, [vp, ip, ip, dp]),
         "dem_set_diagnostics": (C.c_int, [vp, C.c_int32]),
         "dem_get_diag": (C.c_int, [vp, dp]),
@@ -287,6 +288,21 @@ class Context:
         _check(lib().dem_get_sources(self.h, C.cast(C.c_void_p(_ptr(out)), C.POINTER(C.c_double))),
                "dem_get_sources")
         return out
+
+    def dem_get_sources_occupied(self, cells=None, out=None):
+        """Sources of the fluid cells that hold parcels: (cells int64 (k,), rows (k, DEM_NDEP)).
+        cells, out: optional host buffers of capacity >= the count (page-locked torch tensors
+        make the copies fast); views of their first k entries are returned."""
+        cap = min(self.n, self.ncells)
+        if cells is None:
+            cells = np.zeros(cap, dtype=np.int64)
+        if out is None:
+            out = np.zeros((cap, DEM_NDEP))
+        k = C.c_int64(0)
+        cap_b = min(len(cells), len(out))
+        _check(lib().dem_get_sources_occupied(self.h, cap_b, C.byref(k), C.c_void_p(_ptr(cells)),
+                                              C.c_void_p(_ptr(out))), "dem_get_sources_occupied")
+        return cells[:k.value], out[:k.value]
 
     def dem_get_flow(self):
         """Cell-centre gas velocity (3) and pressure relative to p0 of every cell,

@@ -131,6 +131,7 @@ template <class P> int enqueue_scatter_state(dem_ctx *c, double *out_dev);
 template <class P> int enqueue_scatter_diag(dem_ctx *c, double *out_dev);
 template <class P> int enqueue_scatter_hist(dem_ctx *c, int *cnt, int *partner, double *xi);
 template <class P> int enqueue_sources(dem_ctx *c);
+template <class P> int enqueue_sources_occupied(dem_ctx *c, int *cnt, long long *cells, double *out);
 template <class P> int enqueue_gas_set(dem_ctx *c, const double *Y, const double *T, cudaStream_t st);
 template <class P> int enqueue_gas_solver_init(dem_ctx *c);
 template <class P> int enqueue_flow(dem_ctx *c, double *out_dev);

@@ -1034,6 +1034,34 @@ int dem_get_sources(dem_ctx *c, double *out_host) {
   return DEM_OK;
 }
 
+int dem_get_sources_occupied(dem_ctx *c, int64_t cap, int64_t *n_occupied, int64_t *cells_host, double *out_host) {
+  if (!c || !n_occupied || cap < 0 || (cap > 0 && (!cells_host || !out_host))) return DEM_EINVAL;
+  int s = sync_all(c);
+  if (s != DEM_OK) return s;
+  const size_t nmax = (size_t)std::min<long long>(c->n, c->ncells);
+  const int nb = (c->n + OCC_CHUNK - 1) / OCC_CHUNK;
+  const size_t cells_off = ((sizeof(int) * (size_t)(nb + 1) + 255) / 256) * 256;
+  const size_t out_off = cells_off + ((sizeof(long long) * nmax + 255) / 256) * 256;
+  if ((s = ensure_scratch(c, out_off + sizeof(double) * SR_N * nmax)) != DEM_OK) return s;
+  char *base = (char *)c->scratch_out;
+  int *cnt = (int *)base;
+  long long *dcells = (long long *)(base + cells_off);
+  double *dout = (double *)(base + out_off);
+  int e = DEM_DISPATCH(c, enqueue_sources_occupied, c, cnt, dcells, dout);
+  if (e) return DEM_ECUDA;
+  int n = 0;
+  CK(cudaMemcpyAsync(&n, cnt + nb, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  *n_occupied = n;
+  if (n > cap) return DEM_EINVAL;   // the count is reported; nothing else is written
+  if (n > 0) {
+    CK(cudaMemcpyAsync(cells_host, dcells, sizeof(long long) * (size_t)n, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(out_host, dout, sizeof(double) * SR_N * (size_t)n, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+  }
+  return DEM_OK;
+}
+
 int dem_get_flow(dem_ctx *c, double *out_host, int32_t *iters) {
   if (!c || !out_host) return DEM_EINVAL;
   int s = sync_all(c);

@@ -1422,6 +1422,102 @@ __global__ void k_sources(StepView<P> V) {
   for (int f = 0; f < SR_N; ++f) V.dep[(size_t)c * SR_N + f] = solid ? 0.0 : (double)S.s[f];
 }
 
+// Cell sums of the last step's per-parcel sources for the fluid cells that hold parcels
+// (dem_get_sources_occupied), compacted in increasing cell order: the occupied cells are the
+// starts of the runs of equal keys in the sorted order. Three passes, deterministic: a count
+// per chunk of OCC_CHUNK sorted positions, an exclusive scan of the counts in one block, and
+// the writes (each chunk's block ranks its run starts with a block-wide scan).
+constexpr int OCC_BLOCK = 256;
+constexpr int OCC_PER_THREAD = 4;
+constexpr int OCC_CHUNK = OCC_BLOCK * OCC_PER_THREAD;
+template <class P>
+__device__ __forceinline__ bool occ_start(const StepView<P> &V, int s) {
+  if (s >= V.n) return false;
+  const unsigned k = V.keys[s];
+  return (s == 0 || V.keys[s - 1] != k) && V.mark[k] == 0;
+}
+template <class P>
+__global__ void __launch_bounds__(OCC_BLOCK) k_occ_count(StepView<P> V, int *cnt) {
+  const int s0 = blockIdx.x * OCC_CHUNK + threadIdx.x * OCC_PER_THREAD;
+  int m = 0;
+#pragma unroll
+  for (int q = 0; q < OCC_PER_THREAD; ++q) m += occ_start(V, s0 + q) ? 1 : 0;
+  m = __reduce_add_sync(0xffffffffu, m);
+  __shared__ int w[OCC_BLOCK / 32];
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int k = 0; k < OCC_BLOCK / 32; ++k) t += w[k];
+    cnt[blockIdx.x] = t;
+  }
+}
+// exclusive scan of nb counts in place, total in cnt[nb] (one block)
+static __global__ void __launch_bounds__(1024) k_occ_scan(int *cnt, int nb) {
+  __shared__ int carry;
+  __shared__ int ws[32];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nb; base += 1024) {
+    const int i = base + threadIdx.x;
+    const int v = i < nb ? cnt[i] : 0;
+    int x = v;   // inclusive warp scan
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if ((threadIdx.x & 31) >= o) x += y;
+    }
+    if ((threadIdx.x & 31) == 31) ws[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      int t = ws[threadIdx.x];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, t, o);
+        if (threadIdx.x >= o) t += y;
+      }
+      ws[threadIdx.x] = t;
+    }
+    __syncthreads();
+    const int incl = x + ((threadIdx.x >> 5) ? ws[(threadIdx.x >> 5) - 1] : 0);
+    if (i < nb) cnt[i] = carry + incl - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) cnt[nb] = carry;
+}
+template <class P>
+__global__ void __launch_bounds__(OCC_BLOCK) k_occ_write(StepView<P> V, const int *off, long long *cells,
+                                                         double *out /* [occupied][SR_N] */) {
+  const int s0 = blockIdx.x * OCC_CHUNK + threadIdx.x * OCC_PER_THREAD;
+  bool f[OCC_PER_THREAD];
+  int m = 0;
+#pragma unroll
+  for (int q = 0; q < OCC_PER_THREAD; ++q) { f[q] = occ_start(V, s0 + q); m += f[q] ? 1 : 0; }
+  // exclusive block scan of m
+  int x = m;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) >= o) x += y;
+  }
+  __shared__ int ws[OCC_BLOCK / 32];
+  if ((threadIdx.x & 31) == 31) ws[threadIdx.x >> 5] = x;
+  __syncthreads();
+  int before = 0;
+  for (int k = 0; k < (int)(threadIdx.x >> 5); ++k) before += ws[k];
+  int pos = off[blockIdx.x] + before + x - m;
+  const size_t cp = (size_t)V.cap;
+#pragma unroll
+  for (int q = 0; q < OCC_PER_THREAD; ++q) {
+    if (!f[q]) continue;
+    const unsigned c = V.keys[s0 + q];
+    CellSum<P> S;
+    S.run(V.src, cp, V.vals, V.cstart[c], V.cend[c]);
+    cells[pos] = (long long)c;
+    for (int g = 0; g < SR_N; ++g) out[(size_t)pos * SR_N + g] = (double)S.s[g];
+    ++pos;
+  }
+}
+
 // Initial per-parcel volume for the initial gas volume fraction.
 template <class P>
 __global__ void k_volume(StepView<P> V) {

@@ -308,6 +308,18 @@ int enqueue_sources(dem_ctx *c) {
   return (int)cudaPeekAtLastError();
 }
 
+// the occupied cells' source sums: counts per chunk into cnt[0..nb), their scan (total in
+// cnt[nb]), then the compacted cells and sums
+template <class P>
+int enqueue_sources_occupied(dem_ctx *c, int *cnt, long long *cells, double *out) {
+  StepView<P> V = make_view<P>(c, false);
+  const int nb = (c->n + OCC_CHUNK - 1) / OCC_CHUNK;
+  k_occ_count<P><<<nb, OCC_BLOCK, 0, c->st>>>(V, cnt);
+  k_occ_scan<<<1, 1024, 0, c->st>>>(cnt, nb);
+  k_occ_write<P><<<nb, OCC_BLOCK, 0, c->st>>>(V, cnt, cells, out);
+  return (int)cudaPeekAtLastError();
+}
+
 template <class P>
 int enqueue_gas_set(dem_ctx *c, const double *Y, const double *T, cudaStream_t st) {
   StepView<P> V = make_view<P>(c, false);
@@ -364,6 +376,7 @@ int kernel_limits(int *lim) {
   template int enqueue_scatter_diag<P>(dem_ctx *, double *);                            \
   template int enqueue_scatter_hist<P>(dem_ctx *, int *, int *, double *);              \
   template int enqueue_sources<P>(dem_ctx *);                                           \
+  template int enqueue_sources_occupied<P>(dem_ctx *, int *, long long *, double *);      \
   template int enqueue_gas_set<P>(dem_ctx *, const double *, const double *, cudaStream_t); \
   template int enqueue_gas_solver_init<P>(dem_ctx *);                                   \
   template int enqueue_flow<P>(dem_ctx *, double *);                                    \

@@ -113,6 +113,10 @@ def test_packed_bed_fp64_multistep(wall):
     sgs, sos = ctx.dem_get_sources(), ref.deposits()
     for col in range(binding.DEM_NDEP):
         assert _rel(sgs[:, col], sos[:, col]) < 1e-9, binding.SOURCE_ROWS[col]
+    # the occupied cells' rows: exactly the dense rows of the cells with parcels, in cell order
+    cells, rows = ctx.dem_get_sources_occupied()
+    occ = np.flatnonzero(sgs[:, binding.SOURCE_ROWS.index("count")] > 0)
+    assert np.array_equal(cells, occ) and np.array_equal(rows, sgs[occ])
     mg, _ = ctx.dem_reduction_degree()
     mo, _, _ = ref.reduction_degree()
     assert abs(mg[0] - mo[0]) < 1e-12
@@ -364,4 +368,31 @@ def test_kinetics_at_a_chemistry_time_step(prec):
     assert worst < (1e-9 if prec == "fp64" else 1e-3), worst
     if prec != "fp64":
         assert worst < 1e-4, worst
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "split_kahan"])
+def test_occupied_sources_match_the_dense_rows(prec):
+    # several beds with immersed-boundary cells (parcels never sit in solid cells), a bed with
+    # no parcels at all, many chunks of sorted positions; and the capacity check
+    beds = [synth.small_packed(seed=s, n=n, v_scale=0.3, wall_kind=w) for s, n, w in
+            ((61, 2500, synth.WALL_CONE), (62, 10, synth.WALL_FLAT), (63, 1800, synth.WALL_FLAT))]
+    beds[1] = beds[1].subset(np.arange(0))   # the middle bed without parcels
+    cat = lambda f: np.concatenate([getattr(b, f) for b in beds])
+    bed = synth.Bed([b.beds[0] for b in beds], cat("x"), cat("y"), cat("z"), cat("vx"), cat("vy"), cat("vz"),
+                    cat("d_real"), cat("T"), np.concatenate([b.m0 for b in beds], axis=1), cat("ore"),
+                    np.concatenate([np.full(b.n, k, np.int32) for k, b in enumerate(beds)]), "three-beds")
+    ctx = _ctx(bed, prec=prec)
+    for _ in range(2):
+        ctx.dem_step(7)
+        dense = ctx.dem_get_sources()
+        cells, rows = ctx.dem_get_sources_occupied()
+        occ = np.flatnonzero(dense[:, binding.SOURCE_ROWS.index("count")] > 0)
+        assert len(occ) > 100
+        assert np.array_equal(cells, occ)
+        assert np.array_equal(rows, dense[occ])
+        assert np.all(dense[np.setdiff1d(np.arange(ctx.ncells), occ)] == 0)
+    small = np.zeros(10, dtype=np.int64), np.zeros((10, binding.DEM_NDEP))
+    with pytest.raises(binding.DemError):
+        ctx.dem_get_sources_occupied(*small)
     ctx.close()
