@@ -153,12 +153,12 @@ def survey_step_bytes(n: int, ncells: int, zbar: float, rsize: int, passes: int)
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one full-size ncu
-# capture of the 2M-parcel split-precision bed between list builds, after the 300-step
-# settle; per parcel), valid only for the CUDA sources it was taken on.
-TRAFFIC_SOURCE_SHA256 = "8d6de96c4c898e16c19eb7f1288b540aa559e528b588115804f867fccba45fe2"
-TRAFFIC_WORKLOAD = ("ibm_2m", "split", 2_000_000)
-TRAFFIC_BYTES_PER_PARCEL = {"k_gas_particle": 205.5, "k_key": 177.8, "k_cells": 146.4, "k_contact_screen": 58.4,
-                            "k_contact_forces": 17.1, "k_ranges": 8.1}
+# capture of the 2M-parcel bed in the split-Kahan form between list builds, after the
+# 300-step settle; per parcel), valid only for the CUDA sources it was taken on.
+TRAFFIC_SOURCE_SHA256 = "6b3cac69955b5146be804e99b27aabec1af626d4e28af7279c80d6cede0d5c91"
+TRAFFIC_WORKLOAD = ("ibm_2m", "split_kahan", 2_000_000)
+TRAFFIC_BYTES_PER_PARCEL = {"k_gas_particle": 209.0, "k_key": 177.3, "k_cells": 146.5, "k_contact_screen": 58.5,
+                            "k_contact_forces": 17.7, "k_ranges": 8.1}
 
 
 def source_sha256() -> str:
