@@ -110,9 +110,9 @@ def algorithmic_bytes(kernel: str, n: int, ncells: int, zbar: float, L: float, r
     R = rsize
     slot = 4 + 3 * R                                  # partner id + tangential displacement
     state = 24 + 12 * R + 2 * R + 32 + 8 + 12         # x; v,w,a,al; T,d; masses; meta,orig; dsp
-    if kernel == "k_key":            # in place: half kicks, drift, displacement, key, local coordinates;
-        # the previous step's sorted keys (to empty its cell ranges)
-        return n * ((4 + 24 + 12 * R + 12 + 16 + 4 + R + 4) + (24 + 6 * R + 12 + 4 + 16))
+    if kernel == "k_key":            # in place: drift with the half-step velocity, displacement, key,
+        # local coordinates; the previous step's sorted keys (to empty its cell ranges)
+        return n * ((4 + 24 + 3 * R + 12 + 16 + 4 + R + 4) + (24 + 12 + 4 + 16))
     if kernel == "radix_sort":
         return n * passes * (8 + 8)
     if kernel == "resort":           # new keys in sorted order, re-sort, permutation and cell ranges

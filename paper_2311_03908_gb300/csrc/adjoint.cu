@@ -359,7 +359,8 @@ __device__ void load_par(const StepView<Pp> &V, const BedP<double> *bpd, int i, 
   P.a2g = 1.33 - 2.4 * P.eps + 1.2 * P.eps * P.eps;
   const double rp = 0.5 * P.d;
   for (int l = 0; l < 3; ++l) P.cB[l] = rp / (P.D * B.xi[P.ore][l] * B.inv_tau);
-  for (int q = 0; q < 3; ++q) s[q] = (double)V.A.v[q][i];
+  for (int q = 0; q < 3; ++q)   // the whole-step velocity (the state holds the half-step one)
+    s[q] = (double)half_kick_back(V.bp[meta >> 8].half_dt, B.dt, V.A.v[q][i], V.A.a[q][i]);
   s[3] = (double)V.A.T[i];
   for (int z = 0; z < 4; ++z) s[4 + z] = mass_d<Pp>(V.A.m[z], i);
 }

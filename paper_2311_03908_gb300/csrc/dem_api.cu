@@ -85,6 +85,9 @@ __global__ void k_load(int n, const double *const *src /* 8 + 4 arrays */, const
     rv[9 + q][i] = (R)0;
   }
   rv[8][i] = (B.flags & DEM_NO_GRAVITY) ? (R)0 : (R)(-kGrav);
+  // the state holds the half-step velocity: the first half kick of the first step, with the
+  // key kernel's expression and the stored acceleration (gravity)
+  rv[2][i] = half_kick<R>((R)(0.5 * B.dt), B.dt, rv[2][i], rv[8][i]);
   rv[12][i] = (R)src[7][i];
   rv[13][i] = (R)src[6][i];
   for (int q = 0; q < 4; ++q) {

@@ -112,6 +112,13 @@ __device__ __forceinline__ R half_kick(R half_dt, double dt_d, R v, R a) {
   if constexpr (sizeof(R) == 8) return __dadd_rn(v, __dmul_rn(a, 0.5 * dt_d));
   else return v + a * half_dt;
 }
+// the whole-step velocity from the half-step one the state holds (within an ulp of the
+// velocity the half kick started from)
+template <class R>
+__device__ __forceinline__ R half_kick_back(R half_dt, double dt_d, R u, R a) {
+  if constexpr (sizeof(R) == 8) return __dsub_rn(u, __dmul_rn(a, 0.5 * dt_d));
+  else return u - a * half_dt;
+}
 
 // Gas cell of a point: floor((x - x0) * (1/dx)) clamped, in FP64.
 __device__ __forceinline__ int cell_coord_d(double x, double x0, double inv, int n, bool &out) {
@@ -173,7 +180,7 @@ __device__ __forceinline__ float4 local_coords(const StepView<P> &V, const DevBe
 // one parcel's inputs of the key kernel, loaded before any of its work, so that a thread's
 // two parcels have all their loads in flight together
 template <class P> struct KeyIn {
-  typename P::R v[3], a[3], w[3], al[3], d;
+  typename P::R v[3], d;
   double x, y, z;
   float2 p2[3];
   float dsp[3];
@@ -199,7 +206,7 @@ __device__ __forceinline__ void key_load(const StepView<P> &V, int i, int drift,
   if (drift) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      in.v[q] = V.A.v[q][i]; in.a[q] = V.A.a[q][i]; in.w[q] = V.A.w[q][i]; in.al[q] = V.A.al[q][i];
+      in.v[q] = V.A.v[q][i];
       in.dsp[q] = V.A.dsp[q][i];
     }
     in.inv = V.inv[i];
@@ -209,8 +216,10 @@ __device__ __forceinline__ void key_load(const StepView<P> &V, int i, int drift,
   in.d = V.A.d[i];
 }
 
-// First half kick (velocity and spin, written back) and drift of velocity Verlet, the gas
-// cell of the new position, and the FP32 cell-local coordinates; in place, storage order.
+// Drift of velocity Verlet with the half-step velocity the state holds (the gas-particle
+// kernel of the last step applied this step's first half kick after its second one, with the
+// same expression), the gas cell of the new position, and the FP32 cell-local coordinates;
+// in place, storage order.
 // The FP32 forms take the key from the previous cell when the parcel stays more than 1e-3 of
 // an edge inside it (the local coordinates then decide it exactly, their error being
 // ~1e-10 m); otherwise, and always in the FP64 form, the key is recomputed from the
@@ -234,9 +243,7 @@ __device__ __forceinline__ void key_work(const StepView<P> &V, int i, int drift,
     R disp[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      const R vh = half_kick<R>(bp.half_dt, B.dt, in.v[q], in.a[q]);
-      V.A.v[q][i] = vh;
-      V.A.w[q][i] = in.w[q] + in.al[q] * bp.half_dt;
+      const R vh = in.v[q];
       if constexpr (sizeof(R) == 8) disp[q] = __dmul_rn(vh, B.dt);
       else disp[q] = vh * bp.dt;
     }
@@ -1099,11 +1106,18 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
   a[0] = fdiv<R>(F[0] + Fd[0], mp);
   a[1] = fdiv<R>(F[1] + Fd[1], mp);
   a[2] = fdiv<R>(F[2] + Fd[2] - Vp * bp.dpdz, mp) + bp.grav;
+  // second half kick (the whole-step velocity and spin), then the first half kick of the next
+  // step with the key kernel's expression: the state keeps the half-step velocity and spin,
+  // so the next step's drift reads neither the accelerations nor writes the velocities back
+  const double dt_d = V.beds[meta >> 8].dt;
+  R vnew[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     const R al = fdiv<R>(Tq[q], I);
-    V.A.v[q][i] = vh[q] + a[q] * bp.half_dt;
-    V.A.w[q][i] = wv[q] + al * bp.half_dt;
+    const R v1 = vh[q] + a[q] * bp.half_dt, w1 = wv[q] + al * bp.half_dt;
+    vnew[q] = half_kick<R>(bp.half_dt, dt_d, v1, a[q]);
+    V.A.v[q][i] = vnew[q];
+    V.A.w[q][i] = w1 + al * bp.half_dt;
     V.A.a[q][i] = a[q];
     V.A.al[q][i] = al;
   }
@@ -1121,7 +1135,7 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
 #pragma unroll
     for (int q = 0; q < 4; ++q) mass_add<P>(V.A.m[q], i, kn.mdot[q] * dtm);
   }
-  if (!isfinite(Tn) || !isfinite(V.A.v[0][i] + V.A.v[1][i] + V.A.v[2][i])) set_error(V.err, ERR_NONFINITE);
+  if (!isfinite(Tn) || !isfinite(vnew[0] + vnew[1] + vnew[2])) set_error(V.err, ERR_NONFINITE);
   // contributions to the cell sums
   const size_t cp = (size_t)V.cap;
   R *s = V.src;
@@ -1644,12 +1658,13 @@ __global__ void k_scatter_state(StepView<P> V, double *out /* [DEM_NSTATE][n] */
   const size_t n = (size_t)V.n;
   const int o = V.A.orig[i];
   const DevBed &B = V.beds[V.A.meta[i] >> 8];
+  const auto &bp = V.bp[V.A.meta[i] >> 8];
   out[0 * n + o] = pos_abs<P>(V.A.x, i, B.x0); out[1 * n + o] = pos_abs<P>(V.A.y, i, B.y0);
   out[2 * n + o] = pos_abs<P>(V.A.z, i, B.z0);
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    out[(3 + q) * n + o] = (double)V.A.v[q][i];
-    out[(6 + q) * n + o] = (double)V.A.w[q][i];
+  for (int q = 0; q < 3; ++q) {   // the whole-step velocity and spin (the state holds the half-step ones)
+    out[(3 + q) * n + o] = (double)half_kick_back(bp.half_dt, B.dt, V.A.v[q][i], V.A.a[q][i]);
+    out[(6 + q) * n + o] = (double)half_kick_back(bp.half_dt, B.dt, V.A.w[q][i], V.A.al[q][i]);
     out[(14 + q) * n + o] = (double)V.A.a[q][i];
     out[(17 + q) * n + o] = (double)V.A.al[q][i];
   }
