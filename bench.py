@@ -127,8 +127,9 @@ def algorithmic_bytes(kernel: str, n: int, ncells: int, zbar: float, L: float, r
         return n * ((4 + 16 + 4 + 1 + 4 * L * (1 - fbuild) + fbuild * 1) + 1)
     if kernel == "k_contact_forces":  # parcels in contact: own state, partners, history in and out, F, T
         return n * (fbuild * 5 * zbar + zbar * (2 * slot + 8 * R + 32) + fc * (8 + 6 * R + 32 + 6 * R))
-    if kernel == "k_gas_particle":
-        return n * ((4 + 4 + R + 3 * R + R + 32 + 1 + fc * 6 * R + 3 * R) + (12 * R + R + 32 + 13 * R)) + ncells * 13 * R
+    if kernel == "k_gas_particle":   # the accelerations and 7 of the 13 source rows are stored on a
+        # stepping call's last step only
+        return n * ((4 + 4 + R + 3 * R + R + 32 + 1 + fc * 6 * R + 3 * R) + (6 * R + R + 32 + 6 * R)) + ncells * 13 * R
     if kernel == "k_cells":
         return ncells * ((4 + 1 + 8 + 5 * 8 + 2 * R) + (5 * 8 + 14 * R)) + n * (6 * R + 4)
     if kernel == "k_radiation":      # own meta, local coordinates, key, d, T (+ FP64 position); the
@@ -148,7 +149,7 @@ def survey_step_bytes(n: int, ncells: int, zbar: float, rsize: int, passes: int)
         read, write, slot = 24 + 12 + 12 + 4 + 32 + 12, 24 + 12 + 12 + 4 + 32, 4 + 12
     else:
         read, write, slot = 24 + 24 + 24 + 8 + 32 + 16, 24 + 24 + 24 + 8 + 32, 4 + 24
-    staging = (13 + 6) * rsize              # per-parcel sources written, then read by the cell sums
+    staging = (6 + 6) * rsize               # per-parcel sources written, then read by the cell sums
     return n * (read + write + 4 + passes * 16 + zbar * slot * 2 + staging) + ncells * 256
 
 

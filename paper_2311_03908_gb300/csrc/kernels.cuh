@@ -1032,7 +1032,11 @@ __global__ void __launch_bounds__(128, 8) k_radiation(StepView<P> V) {
 // to L1 cost less than the latency the extra occupancy hides (ncu: 33 % -> 50 % warps).
 // RAD: some bed has radiation (the variant that adds k_radiation's Q_rad to the heat balance).
 template <class P, bool RAD>
-__global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView<P> V) {
+// full: this is the last step of a stepping call (or the gas is solved): the accelerations,
+// which only the state output and the adjoint read (to report whole-step velocities), and
+// the source rows only dem_get_sources and the gas solver read (K, K v, Q_r, E Q, E S) are
+// stored; the prescribed gas update reads the other six every step
+__global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView<P> V, int full) {
   pdl_wait();
   using R = typename P::R;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1118,8 +1122,10 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
     vnew[q] = half_kick<R>(bp.half_dt, dt_d, v1, a[q]);
     V.A.v[q][i] = vnew[q];
     V.A.w[q][i] = w1 + al * bp.half_dt;
-    V.A.a[q][i] = a[q];
-    V.A.al[q][i] = al;
+    if (full) {
+      V.A.a[q][i] = a[q];
+      V.A.al[q][i] = al;
+    }
   }
   const Tab<R> &t = tab<R>();
   R cpp = 0;
@@ -1142,16 +1148,18 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
   s[SR_VS * cp + i] = Vp;
   s[SR_SH2 * cp + i] = kn.sH2;
   s[SR_SH2O * cp + i] = kn.sH2O;
-  s[SR_K * cp + i] = Kp;
-  s[SR_KVX * cp + i] = Kp * vh[0];
-  s[SR_KVY * cp + i] = Kp * vh[1];
-  s[SR_KVZ * cp + i] = Kp * vh[2];
   s[SR_HA * cp + i] = hA;
   s[SR_HAT * cp + i] = hA * Tp;
   s[SR_QRM * cp + i] = kn.Qrm;
-  s[SR_QR * cp + i] = kn.Qr;
-  s[SR_EQ * cp + i] = kn.EQ;
-  s[SR_ES * cp + i] = kn.ES;
+  if (full) {
+    s[SR_K * cp + i] = Kp;
+    s[SR_KVX * cp + i] = Kp * vh[0];
+    s[SR_KVY * cp + i] = Kp * vh[1];
+    s[SR_KVZ * cp + i] = Kp * vh[2];
+    s[SR_QR * cp + i] = kn.Qr;
+    s[SR_EQ * cp + i] = kn.EQ;
+    s[SR_ES * cp + i] = kn.ES;
+  }
   if (V.diag) {
     double *dg = V.diag;
 #pragma unroll

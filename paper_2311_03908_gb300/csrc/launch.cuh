@@ -235,8 +235,11 @@ int enqueue_steps(dem_ctx *c, int nsteps) {
       waited = false;
     }
     ps = prof_begin(c, "k_gas_particle");
-    if (c->any_rad) launch_k(pdl && !waited, k_gas_particle<P, true>, grid_for(c->n, c->bs_gp), c->bs_gp, st, V);
-    else launch_k(pdl && !waited, k_gas_particle<P, false>, grid_for(c->n, c->bs_gp), c->bs_gp, st, V);
+    // the accelerations and the sources only dem_get_sources and the gas solver read are
+    // stored on a call's last step (every step when the gas is solved)
+    const int last = (s == nsteps - 1 || c->gas_solver) ? 1 : 0;
+    if (c->any_rad) launch_k(pdl && !waited, k_gas_particle<P, true>, grid_for(c->n, c->bs_gp), c->bs_gp, st, V, last);
+    else launch_k(pdl && !waited, k_gas_particle<P, false>, grid_for(c->n, c->bs_gp), c->bs_gp, st, V, last);
     prof_end(c, ps);
     if (c->gas_solver) {
       e = enqueue_gas_solve<P>(c, V, pdl);
