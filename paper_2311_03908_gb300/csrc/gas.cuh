@@ -163,6 +163,33 @@ __device__ inline void gs_pt(double eps, double rho, double mu, double lam, doub
   }
 }
 
+// the properties the solver's equations need (rho, mu, lam, c_p, D_m), with the same
+// expressions as gas_cell_props: the parcel-side ones (film and pore terms) are not evaluated
+struct GsProps { double rho, mu, lam, cp, Dm; };
+__device__ inline GsProps gs_props(const BedP<double> &B, const double Y[3], double T) {
+  const Tab<double> &t = tab<double>();
+  GsProps o;
+  const double p = B.p0;
+  const double inv = Y[0] / t.Mj[0] + Y[1] / t.Mj[1] + Y[2] / t.Mj[2];
+  const double Mg = 1.0 / inv;
+  const double xp0 = Y[0] * Mg / t.Mj[0], xp1 = Y[1] * Mg / t.Mj[1], xp2 = Y[2] * Mg / t.Mj[2];
+  o.rho = Mg * p / (kRgas * T);
+  double mu = 0, lam = 0, cp = 0;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    mu += Y[j] * (t.visc[j][0] + T * (t.visc[j][1] + T * t.visc[j][2]));
+    lam += Y[j] * (t.cond[j][0] + T * (t.cond[j][1] + T * (t.cond[j][2] + T * (t.cond[j][3] + T * t.cond[j][4]))));
+    cp += Y[j] * cp_over_R<double>(j, T) * t.RMj[j];
+  }
+  o.mu = mu; o.lam = lam; o.cp = cp;
+  const double sT = sqrt(T);
+  const double tf = T * sT * sqrt(sT) * (101325.0 / p) * 1e-7;
+  const double D12 = tf * B.fuller12, D13 = tf * B.fuller13;
+  const double rest = 1.0 - xp0;
+  o.Dm = rest < 1e-12 ? D12 : rest / (xp1 / D12 + xp2 / D13);
+  return o;
+}
+
 // cell-centre gas velocity: the mean of the cell's two faces on each axis
 __device__ __forceinline__ void gs_ucell(const GasView &S, const GsGrid &g, int i, int j, int k, double u[3]) {
   u[0] = 0.5 * (S.fu[g.face(0, i, j, k)] + S.fu[g.face(0, i + 1, j, k)]);
@@ -194,7 +221,7 @@ __global__ void k_gs_coeffs(StepView<P> V, GasView S) {
                        gas_d<P>(V.gas, GS_Y2 * nc + c)};
   const double T = gas_d<P>(V.gas, GS_T * nc + c);
   const double eps = fl ? fmax(1.0 - d[SR_VS] * B.inv_vcell, B.eps_min) : B.eps_min;
-  const CellProps<double> p = gas_cell_props<double>(S.bpd[b], eps, Y, T);
+  const GsProps p = gs_props(S.bpd[b], Y, T);
   double *co = S.co;
   co[GC_EPS * nc + c] = eps;
   co[GC_EPSO * nc + c] = gas_d<P>(V.gas, GS_EPS * nc + c);
@@ -878,7 +905,8 @@ __global__ void k_gs_scalars(StepView<P> V, GasView S) {
     g.ijk(c, i, j, k);
     const double h[3] = {B.dx, B.dy, B.dz};
     const double Af[3] = {B.dy * B.dz, B.dx * B.dz, B.dx * B.dy};
-    const double dt = B.ncouple * B.dt;
+    const double Afh[3] = {Af[0] / h[0], Af[1] / h[1], Af[2] / h[2]};
+    const double dt = B.ncouple * B.dt, idt = 1.0 / dt;
     const double rho_in = gs_rho_in(B);
     const double cp = co[GC_CP * nc + c], lam = co[GC_LAM * nc + c];
     const double Dm = co[GC_DM * nc + c];
@@ -907,9 +935,10 @@ __global__ void k_gs_scalars(StepView<P> V, GasView S) {
           const double ATf = 0.5 * (ATc + co[(GC_AT + a) * nc + cn]);
           const double Df = 0.5 * (Dm + co[GC_DM * nc + cn]) + ATf;
           const double lf = 0.5 * (lam + co[GC_LAM * nc + cn]) + rf * (0.5 * (cp + co[GC_CP * nc + cn])) * ATf;
-          dY0 += ef * rf * Df * Af[a] / h[a] * (yn0 - Y0);
-          dY1 += ef * rf * Df * Af[a] / h[a] * (yn1 - Y1);
-          dT += ef * lf * Af[a] / h[a] * (tn - T);
+          const double gD = ef * rf * Df * Afh[a];
+          dY0 += gD * (yn0 - Y0);
+          dY1 += gD * (yn1 - Y1);
+          dT += ef * lf * Afh[a] * (tn - T);
         } else if (kd == 2) {
           if (inflow > 0.0) {
             cY0 += inflow * (B.Y_in[0] - Y0);
@@ -917,7 +946,7 @@ __global__ void k_gs_scalars(StepView<P> V, GasView S) {
             cT += inflow * cp * (B.T_in - T);
           }
         } else if (kd == 0) {   // a wall at the inlet temperature
-          dT += eps * lam * Af[a] / (0.5 * h[a]) * (B.T_in - T);
+          dT += eps * lam * (2.0 * Afh[a]) * (B.T_in - T);
         }                       // outlet: zero gradient
       }
     }
@@ -929,28 +958,33 @@ __global__ void k_gs_scalars(StepView<P> V, GasView S) {
     const double MH2 = td.Mj[0], MH2O = td.Mj[1];
     const double C0 = MH2 * B.p0 * co[GC_AX * nc + c] * d[SR_EQ] / kRgas, C1 = MH2 * B.p0 * d[SR_ES] / kRgas;
     const double rq = MH2O / MH2 - 1.0;
-    const double Y0n = (m * Y0 / dt + cY0 + dY0 + C1 * (1.0 + Y0 * rq)) / (m / dt + C0 * (1.0 + Y0 * rq));
+    const double mdt = m * idt;
+    const double Y0n = (mdt * Y0 + cY0 + dY0 + C1 * (1.0 + Y0 * rq)) / (mdt + C0 * (1.0 + Y0 * rq));
     const double cons = C0 * Y0n - C1;
     const double Mnet = rq * cons;
     const double Y0f = fmax(Y0n, 0.0);
-    const double Y1f = fmax(Y1 + dt / m * (cY1 + dY1 + MH2O / MH2 * cons - Y1 * Mnet), 0.0);
+    const double im = 1.0 / m;
+    const double Y1f = fmax(Y1 + dt * im * (cY1 + dY1 + MH2O / MH2 * cons - Y1 * Mnet), 0.0);
     const double Y2f = fmax(1.0 - Y0f - Y1f, 0.0);
     const double ys = Y0f + Y1f + Y2f;
-    Y[0] = Y0f / ys; Y[1] = Y1f / ys; Y[2] = Y2f / ys;
+    const double iys = 1.0 / ys;
+    Y[0] = Y0f * iys; Y[1] = Y1f * iys; Y[2] = Y2f * iys;
     // M_r of eq (3-39) with the parcels' species sources and M_rm of eq (3-38): together the
     // sensible enthalpy the species bring from the parcels' temperature
     const double Mr = -(h_over_R<double>(0, T) * td.RMj[0] * d[SR_SH2] + h_over_R<double>(1, T) * td.RMj[1] * d[SR_SH2O]);
     const double Mrm = -d[SR_QRM];
     const double mc = m * cp;
-    const double Tn = (mc * T / dt + cT + dT + d[SR_HAT] + Mr + Mrm) / (mc / dt + d[SR_HA]);
+    const double mcdt = mc * idt;
+    const double Tn = (mcdt * T + cT + dT + d[SR_HAT] + Mr + Mrm) / (mcdt + d[SR_HA]);
     // div(eps u) = -d eps/dt + M / rho - eps D ln(rho)/Dt (the material rates: the change less
     // its convective part; the N2 carried in is -(cY0 + cY1))
-    const double DY0 = (Y[0] - Y0) / dt - cY0 / m, DY1 = (Y[1] - Y1) / dt - cY1 / m;
-    const double DY2 = (Y[2] - Y2o) / dt + (cY0 + cY1) / m;
-    const double DT = (Tn - T) / dt - cT / mc;
-    const double Mg = 1.0 / (Y0 / td.Mj[0] + Y1 / td.Mj[1] + Y2o / td.Mj[2]);
-    const double Dlnrho = -Mg * (DY0 / td.Mj[0] + DY1 / td.Mj[1] + DY2 / td.Mj[2]) - DT / T;
-    div = -(eps - co[GC_EPSO * nc + c]) / dt + Mnet / (B.vcell * rho) - eps * Dlnrho;
+    const double DY0 = (Y[0] - Y0) * idt - cY0 * im, DY1 = (Y[1] - Y1) * idt - cY1 * im;
+    const double DY2 = (Y[2] - Y2o) * idt + (cY0 + cY1) * im;
+    const double DT = (Tn - T) * idt - cT * im / cp;
+    const double iM[3] = {1.0 / td.Mj[0], 1.0 / td.Mj[1], 1.0 / td.Mj[2]};   // constants, folded
+    const double Mg = 1.0 / (Y0 * iM[0] + Y1 * iM[1] + Y2o * iM[2]);
+    const double Dlnrho = -Mg * (DY0 * iM[0] + DY1 * iM[1] + DY2 * iM[2]) - DT / T;
+    div = -(eps - co[GC_EPSO * nc + c]) * idt + Mnet * im * eps - eps * Dlnrho;
     T = Tn;
   }
   gs_put<P>(Gn, GS_EPS * nc + c, eps);
