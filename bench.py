@@ -156,9 +156,9 @@ def survey_step_bytes(n: int, ncells: int, zbar: float, rsize: int, passes: int)
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one full-size ncu
 # capture of the 2M-parcel bed in the split-Kahan form between list builds, after the
 # 300-step settle; per parcel), valid only for the CUDA sources it was taken on.
-TRAFFIC_SOURCE_SHA256 = "6b3cac69955b5146be804e99b27aabec1af626d4e28af7279c80d6cede0d5c91"
+TRAFFIC_SOURCE_SHA256 = "894b503217df00cce0204eb078f4154a883d4e42c9dbcad6fd630c73a605b012"
 TRAFFIC_WORKLOAD = ("ibm_2m", "split_kahan", 2_000_000)
-TRAFFIC_BYTES_PER_PARCEL = {"k_gas_particle": 209.0, "k_key": 177.3, "k_cells": 146.5, "k_contact_screen": 58.5,
+TRAFFIC_BYTES_PER_PARCEL = {"k_gas_particle": 154.5, "k_key": 117.1, "k_cells": 146.5, "k_contact_screen": 58.5,
                             "k_contact_forces": 17.7, "k_ranges": 8.1}
 
 
