@@ -117,12 +117,12 @@ def algorithmic_bytes(kernel: str, n: int, ncells: int, zbar: float, L: float, r
         return n * passes * (8 + 8)
     if kernel == "resort":           # new keys in sorted order, re-sort, permutation and cell ranges
         return n * (16 + 16 + 8)
-    if kernel == "k_restore":        # list-build steps: state, local coordinates, history out and back
-        return frestore * n * (4 * (state + 16 + 1 + zbar * slot) + 4 + 8)
+    if kernel == "k_restore":        # re-store steps: state, local coordinates, history back from the copy
+        return frestore * n * (2 * (state + 16 + 1 + zbar * slot) + 8)
     if kernel == "k_pair_search":    # list builds (the cell-list search) only
         return fbuild * n * ((4 + 16 + 4) + (4 * L + 1 + 1 + 12 + 5 * zbar))
-    if kernel == "k_ranges":
-        return n * (4 + 4 + 4)
+    if kernel == "k_ranges":         # ranges, inverse permutation; on re-store steps the records out
+        return n * (4 + 4 + 4) + frestore * n * (2 * (state + 16 + 1 + zbar * slot) + 4)
     if kernel == "k_contact_screen":  # list test (between builds), wall pre-screen; empty histories
         return n * ((4 + 16 + 4 + 1 + 4 * L * (1 - fbuild) + fbuild * 1) + 1)
     if kernel == "k_contact_forces":  # parcels in contact: own state, partners, history in and out, F, T
@@ -156,7 +156,7 @@ def survey_step_bytes(n: int, ncells: int, zbar: float, rsize: int, passes: int)
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one full-size ncu
 # capture of the 2M-parcel bed in the split-Kahan form between list builds, after the
 # 300-step settle; per parcel), valid only for the CUDA sources it was taken on.
-TRAFFIC_SOURCE_SHA256 = "894b503217df00cce0204eb078f4154a883d4e42c9dbcad6fd630c73a605b012"
+TRAFFIC_SOURCE_SHA256 = "02766230b491c695db81e4d49af4939484666b64fe133cbd434f225e037f060f"
 TRAFFIC_WORKLOAD = ("ibm_2m", "split_kahan", 2_000_000)
 TRAFFIC_BYTES_PER_PARCEL = {"k_gas_particle": 154.5, "k_key": 117.1, "k_cells": 146.5, "k_contact_screen": 58.5,
                             "k_contact_forces": 17.7, "k_ranges": 8.1}
@@ -335,8 +335,15 @@ def e2e_coupling(binding, stream, bed, ncouple, tuning, settle, steps):
     torch.cuda.synchronize()
     te = time.perf_counter() - t0
     nsteps = ncpl * ncouple
+    # the same steps without the round trip (same context, graphs replayed back to back)
+    t1 = time.perf_counter()
+    for _ in range(ncpl):
+        cx.dem_step_graph(ncouple)
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t1
     cx.close()
     return {"coupling_interval": ncouple, "steps": nsteps, "seconds": te, "ms_per_step": 1e3 * te / nsteps,
+            "steps_only_ms_per_step": 1e3 * ts / nsteps,
             "occupied_cells": nocc / ncpl, "cells": int(Y.shape[0]),
             "h2d_bytes_per_step": int(Y.numel() * 8 + T.numel() * 8) / ncouple,
             "d2h_bytes_per_step": (nocc / ncpl * (14 * 8 + 8) + 4 + len(bed.beds) * 16) / ncouple}

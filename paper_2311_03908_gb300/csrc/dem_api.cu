@@ -13,17 +13,9 @@ using dem::DevBed;
 
 namespace dem {
 
-__global__ void k_step_counter(long long *ctr, int *rebuild, int lists, int *nwork, int restore_every) {
+__global__ void k_step_counter(StepEnd se) {
   pdl_wait();
-  ctr[0] += 1;
-  *nwork = 0;   // the next step's contact work list starts empty
-  if (*rebuild) ctr[4] = ctr[4] + 1 >= restore_every ? 0 : ctr[4] + 1;   // builds since the last re-store
-  if (lists && *rebuild) {   // neighbour-list builds, and the list entries of the last one
-    ctr[1] += 1;
-    ctr[2] = ctr[3];
-    ctr[3] = 0;
-  }
-  *rebuild = 0;   // the lists built this step (if any) are current
+  step_end(se);
 }
 
 // Solid (IBM-marked) gas cells, and the cells near a wall: those whose parcels may touch a

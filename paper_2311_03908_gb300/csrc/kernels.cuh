@@ -102,10 +102,34 @@ __device__ __forceinline__ bool coupled_step(int ncouple, const long long *ctr) 
   return ncouple == 1 || (((int)(*ctr % ncouple)) + 1) % ncouple == 0;
 }
 
+// The end of a step (k_step_counter, one thread, after every other kernel of the step): the
+// step counter, the list-build and re-store counters, the next step's empty contact work
+// list. ctr[0] steps, [1] list builds, [2] list entries of the last build, [3] those of the
+// build in progress, [4] builds since the last re-store, [5] a coupling input arrived.
+struct StepEnd {
+  long long *ctr;
+  int *rebuild;
+  int *nwork;
+  int lists, restore_every;
+};
+__device__ __forceinline__ void step_end(const StepEnd &e) {
+  long long *ctr = e.ctr;
+  ctr[0] += 1;
+  *e.nwork = 0;   // the next step's contact work list starts empty
+  if (*e.rebuild) ctr[4] = ctr[4] + 1 >= e.restore_every ? 0 : ctr[4] + 1;   // builds since the last re-store
+  if (e.lists && *e.rebuild) {   // neighbour-list builds, and the list entries of the last one
+    ctr[1] += 1;
+    ctr[2] = ctr[3];
+    ctr[3] = 0;
+  }
+  *e.rebuild = 0;   // the lists built this step (if any) are current
+  ctr[5] = 0;       // the gas buffers agree after this step's k_cells (a copy step, if needed)
+}
+
 // ---------------------------------------------------------------------------------------
-// Velocity Verlet (kick-drift-kick). The key kernel applies the first half kick, writes the
-// half-step velocity back (the contact and gas-particle kernels read it) and drifts the FP64
-// positions with it; the gas-particle kernel applies the second half kick.
+// Velocity Verlet (kick-drift-kick). The state holds the half-step velocity: the key kernel
+// drifts the positions with it, the contact and gas-particle kernels read it, and the
+// gas-particle kernel applies this step's second half kick and then the next step's first.
 // ---------------------------------------------------------------------------------------
 template <class R>
 __device__ __forceinline__ R half_kick(R half_dt, double dt_d, R v, R a) {
@@ -323,15 +347,51 @@ __global__ void k_key(StepView<P> V, int drift) {
   if (two) key_work<P>(V, i1, drift, b);
 }
 
+// Re-store (list-build steps, and the first binning): copy every parcel's record, local
+// coordinates, key and history to its sorted position in the scratch buffers ...
+template <class P>
+__device__ __forceinline__ void restore_out_one(const StepView<P> &V, int i) {
+  const int j = (int)__ldg(V.vals + i);
+  const double x = __ldg(V.A.x + j), y = __ldg(V.A.y + j), z = __ldg(V.A.z + j);
+  V.S.x[i] = x; V.S.y[i] = y; V.S.z[i] = z;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    V.S.v[q][i] = __ldg(V.A.v[q] + j); V.S.w[q][i] = __ldg(V.A.w[q] + j);
+    V.S.a[q][i] = __ldg(V.A.a[q] + j); V.S.al[q][i] = __ldg(V.A.al[q] + j);
+    V.S.dsp[q][i] = __ldg(V.A.dsp[q] + j);
+  }
+  V.S.T[i] = __ldg(V.A.T + j);
+  V.S.d[i] = __ldg(V.A.d + j);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) V.S.m[q][i] = __ldg(V.A.m[q] + j);
+  V.S.meta[i] = __ldg(V.A.meta + j);
+  V.S.orig[i] = __ldg(V.A.orig + j);
+  V.xls[i] = __ldg(V.xl + j);
+  const int c = __ldg(V.H.cnt + j);
+  V.Hs.cnt[i] = (unsigned char)c;
+  for (int s = 0; s < c; ++s) {
+    V.Hs.id[(size_t)s * V.cap + i] = V.H.id[(size_t)s * V.cap + j];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) V.Hs.xi[(size_t)(s * 3 + q) * V.cap + i] = V.H.xi[(size_t)(s * 3 + q) * V.cap + j];
+  }
+}
+
 // Sorted-position range of every occupied cell, and the sorted position of every storage
 // position (the next step's key kernel scatters its keys through it). Four consecutive
-// sorted positions per thread (vector loads of keys and permutation).
+// sorted positions per thread (vector loads of keys and permutation). On a re-store step
+// (or with force, at the first binning) also the first half of the re-store: every record
+// copied to its sorted position in the scratch buffers (k_restore_in, after the whole grid,
+// copies them back).
 template <class P>
-__global__ void k_ranges(StepView<P> V) {
+__global__ void k_ranges(StepView<P> V, int force) {
   pdl_wait();
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   const int i0 = 4 * q;
   if (i0 >= V.n) return;
+  if (force || restore_now(V)) {
+    const int ce = min(i0 + 4, V.n);
+    for (int i = i0; i < ce; ++i) restore_out_one<P>(V, i);
+  }
   if (q == 0 && *V.rebuild) *V.novf = 0;   // a list build lists the overflowed parcels anew
   if (q < (V.n + 1023) / 1024) V.moved[q] = 0;   // the re-sort is done with the counts: zero for the next step
   // a search of every parcel without a re-store reads the local coordinates in sorted order
@@ -369,43 +429,6 @@ __global__ void k_ranges(StepView<P> V) {
       if constexpr (P::exact) V.tsrt[i] = t;
     }
   }
-}
-
-// Re-store (list-build steps, and the first binning): copy every parcel's record, local
-// coordinates, key and history to its sorted position in the scratch buffers ...
-template <class P>
-__device__ __forceinline__ void restore_out_one(const StepView<P> &V, int i) {
-  const int j = (int)__ldg(V.vals + i);
-  const double x = __ldg(V.A.x + j), y = __ldg(V.A.y + j), z = __ldg(V.A.z + j);
-  V.S.x[i] = x; V.S.y[i] = y; V.S.z[i] = z;
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    V.S.v[q][i] = __ldg(V.A.v[q] + j); V.S.w[q][i] = __ldg(V.A.w[q] + j);
-    V.S.a[q][i] = __ldg(V.A.a[q] + j); V.S.al[q][i] = __ldg(V.A.al[q] + j);
-    V.S.dsp[q][i] = __ldg(V.A.dsp[q] + j);
-  }
-  V.S.T[i] = __ldg(V.A.T + j);
-  V.S.d[i] = __ldg(V.A.d + j);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) V.S.m[q][i] = __ldg(V.A.m[q] + j);
-  V.S.meta[i] = __ldg(V.A.meta + j);
-  V.S.orig[i] = __ldg(V.A.orig + j);
-  V.xls[i] = __ldg(V.xl + j);
-  const int c = __ldg(V.H.cnt + j);
-  V.Hs.cnt[i] = (unsigned char)c;
-  for (int s = 0; s < c; ++s) {
-    V.Hs.id[(size_t)s * V.cap + i] = V.H.id[(size_t)s * V.cap + j];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) V.Hs.xi[(size_t)(s * 3 + q) * V.cap + i] = V.H.xi[(size_t)(s * 3 + q) * V.cap + j];
-  }
-}
-
-template <class P>
-__global__ void k_restore_out(StepView<P> V, int force) {
-  pdl_wait();
-  if (!force && !restore_now(V)) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V.n; i += gridDim.x * blockDim.x)
-    restore_out_one<P>(V, i);
 }
 
 // ... and back into the state, which is then in sorted order (storage = sorted position).
@@ -1142,15 +1165,18 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
     for (int q = 0; q < 4; ++q) mass_add<P>(V.A.m[q], i, kn.mdot[q] * dtm);
   }
   if (!isfinite(Tn) || !isfinite(vnew[0] + vnew[1] + vnew[2])) set_error(V.err, ERR_NONFINITE);
-  // contributions to the cell sums
+  // contributions to the cell sums: the rows the gas update reads at coupling steps (and on
+  // a call's last step, for dem_get_sources), the others on a call's last step
   const size_t cp = (size_t)V.cap;
   R *s = V.src;
-  s[SR_VS * cp + i] = Vp;
-  s[SR_SH2 * cp + i] = kn.sH2;
-  s[SR_SH2O * cp + i] = kn.sH2O;
-  s[SR_HA * cp + i] = hA;
-  s[SR_HAT * cp + i] = hA * Tp;
-  s[SR_QRM * cp + i] = kn.Qrm;
+  if (cpl || full) {
+    s[SR_VS * cp + i] = Vp;
+    s[SR_SH2 * cp + i] = kn.sH2;
+    s[SR_SH2O * cp + i] = kn.sH2O;
+    s[SR_HA * cp + i] = hA;
+    s[SR_HAT * cp + i] = hA * Tp;
+    s[SR_QRM * cp + i] = kn.Qrm;
+  }
   if (full) {
     s[SR_K * cp + i] = Kp;
     s[SR_KVX * cp + i] = Kp * vh[0];
@@ -1253,13 +1279,9 @@ template <class P> struct CellSum {
   }
 };
 
-// (48 registers in the FP32 forms, as the screen pass)
 template <class P>
-__global__ void __launch_bounds__(256, P::exact ? 1 : 5) k_cells(StepView<P> V, int mode /* 0 step, 1 eps init, 2 props only */) {
-  pdl_wait();
+__device__ __forceinline__ void cell_step(StepView<P> &V, long long c, int mode /* 0 step, 1 eps init */) {
   using R = typename P::R;
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= V.ncells) return;
   const int b = V.cell_bed[c];
   const DevBed &B = V.beds[b];
   const BedP<R> &bp = V.bp[b];
@@ -1269,7 +1291,13 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 5) k_cells(StepView<P> V, 
   const bool solid = V.mark[c] != 0;
   const size_t cp = (size_t)V.cap;
   const long long layer = (long long)B.nx * B.ny;
-  const bool update = mode == 0 && !solid && coupled_step(bp.ncouple, V.step_ctr) && !(bp.flags & DEM_NO_GAS_UPDATE);
+  const bool cpl = coupled_step(bp.ncouple, V.step_ctr);
+  // Between coupling steps the gas state does not change, and the other buffer already holds
+  // it, unless the last step was a coupling step (or the first after dem_init) or an input
+  // arrived since (dem_set_gas sets step_ctr[5]; the step counter clears it): then it is
+  // copied across once. The stored property records are those of the unchanged state.
+  if (mode == 0 && !cpl && V.step_ctr[0] % bp.ncouple != 0 && V.step_ctr[5] == 0) return;
+  const bool update = mode == 0 && !solid && cpl && !(bp.flags & DEM_NO_GAS_UPDATE);
   if constexpr (P::exact) {
     // the all-FP64 form: the oracle's expressions
     double eps = G[GS_EPS * nc + c], Y[3] = {G[GS_Y0 * nc + c], G[GS_Y1 * nc + c], G[GS_Y2 * nc + c]};
@@ -1394,16 +1422,25 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 5) k_cells(StepView<P> V, 
   }
 }
 
+// One thread per gas cell (48 registers in the FP32 forms, as the screen pass).
+template <class P>
+__global__ void __launch_bounds__(256, P::exact ? 1 : 5) k_cells(StepView<P> V, int mode) {
+  pdl_wait();
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < V.ncells) cell_step<P>(V, c, mode);
+}
+
 // The coupling input (dem_set_gas): the gas composition and temperature of every cell from
 // the caller (FP64; device memory, or mapped pinned host memory read directly), written to
 // the other gas-state buffer with the volume fraction kept, and the cell's property record
 // for the next step; in the FP32 forms only where the FP32 state changed (as in k_cells).
 template <class P>
 __global__ void k_gas_set_props(StepView<P> V, const double *__restrict__ Yin /* ncells*3 */,
-                                const double *__restrict__ Tin) {
+                                const double *__restrict__ Tin, long long *ctr) {
   using R = typename P::R;
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= V.ncells) return;
+  if (c == 0) ctr[5] = 1;   // the buffers differ: the next step's k_cells copies
   const BedP<R> &bp = V.bp[V.cell_bed[c]];
   const size_t nc = (size_t)V.ncells;
   const double y0 = Yin[c * 3], y1 = Yin[c * 3 + 1], y2 = Yin[c * 3 + 2], tg = Tin[c];
@@ -1707,6 +1744,6 @@ __global__ void k_scatter_hist(StepView<P> V, int *cnt, int *partner, double *xi
 
 __global__ void k_mark_cells(const DevBed *beds, const BedP<double> *bps, const int *cell_bed, unsigned char *mark,
                              unsigned char *wnear, long long ncells);
-__global__ void k_step_counter(long long *ctr, int *rebuild, int lists, int *nwork, int restore_every);
+__global__ void k_step_counter(StepEnd se);
 
 }  // namespace dem

@@ -117,7 +117,7 @@ int enqueue_binning(dem_ctx *c, int drift) {
     if (e) return e;
     prof_end(c, ps);
     ps = prof_begin(c, "k_ranges");   // the key kernel emptied the previous step's ranges
-    launch_k(pdl, k_ranges<P>, grid_for((c->n + 3) / 4, c->bs_restore), c->bs_restore, st, V);
+    launch_k(pdl, k_ranges<P>, grid_for((c->n + 3) / 4, c->bs_restore), c->bs_restore, st, V, 0);
     prof_end(c, ps);
     ++c->launches;
   } else {
@@ -135,15 +135,15 @@ int enqueue_binning(dem_ctx *c, int drift) {
     }
     cudaMemsetAsync(c->cstart, 0, sizeof(unsigned) * c->ncells, st);
     cudaMemsetAsync(c->cend, 0, sizeof(unsigned) * c->ncells, st);
-    k_ranges<P><<<grid_for((c->n + 3) / 4, 256), 256, 0, st>>>(V);
+    k_ranges<P><<<grid_for((c->n + 3) / 4, 256), 256, 0, st>>>(V, 1);
     prof_end(c, ps);
     c->launches += 2;
   }
+  // the re-store's second half (k_ranges copied the records out)
   ps = prof_begin(c, "k_restore");
-  launch_k(pdl, k_restore_out<P>, grid_wave(c, c->n, c->bs_restore), c->bs_restore, st, V, drift ? 0 : 1);
   launch_k(pdl, k_restore_in<P>, grid_wave(c, c->n, c->bs_restore), c->bs_restore, st, V, drift ? 0 : 1);
   prof_end(c, ps);
-  c->launches += 2;
+  ++c->launches;
   return (int)cudaPeekAtLastError();
 }
 
@@ -241,6 +241,12 @@ int enqueue_steps(dem_ctx *c, int nsteps) {
     if (c->any_rad) launch_k(pdl && !waited, k_gas_particle<P, true>, grid_for(c->n, c->bs_gp), c->bs_gp, st, V, last);
     else launch_k(pdl && !waited, k_gas_particle<P, false>, grid_for(c->n, c->bs_gp), c->bs_gp, st, V, last);
     prof_end(c, ps);
+    StepEnd se;   // the end of the step: its counters
+    se.ctr = c->step_ctr;
+    se.rebuild = c->rebuild;
+    se.nwork = c->nwork;
+    se.lists = c->use_lists;
+    se.restore_every = c->restore_every;
     if (c->gas_solver) {
       e = enqueue_gas_solve<P>(c, V, pdl);
       if (e) return e;
@@ -250,7 +256,7 @@ int enqueue_steps(dem_ctx *c, int nsteps) {
       prof_end(c, ps);
       ++c->launches;
     }
-    launch_k(pdl, k_step_counter, 1, 1, st, c->step_ctr, c->rebuild, c->use_lists, c->nwork, c->restore_every);
+    launch_k(pdl, k_step_counter, 1, 1, st, se);
     c->launches += 5;
     e = (int)cudaPeekAtLastError();
     if (e) return e;
@@ -328,7 +334,7 @@ int enqueue_gas_set(dem_ctx *c, const double *Y, const double *T, cudaStream_t s
   StepView<P> V = make_view<P>(c, false);
   V.gas = c->gas[c->gcur];
   V.gas_new = c->gas[1 - c->gcur];
-  k_gas_set_props<P><<<grid_for(c->ncells, 256), 256, 0, st>>>(V, Y, T);
+  k_gas_set_props<P><<<grid_for(c->ncells, 256), 256, 0, st>>>(V, Y, T, c->step_ctr);
   c->gcur = 1 - c->gcur;
   return (int)cudaPeekAtLastError();
 }
@@ -359,13 +365,16 @@ int gas_cg_occupancy(int *blocks_per_sm) {
 // largest block each tunable kernel can launch with (registers per thread decide it)
 template <class P>
 int kernel_limits(int *lim) {
-  const void *fn[6] = {(const void *)k_key<P>, (const void *)k_restore_out<P>, (const void *)k_pair_search<P>,
+  const void *fn[6] = {(const void *)k_key<P>, (const void *)k_ranges<P>, (const void *)k_pair_search<P>,
                        (const void *)k_contact_screen<P>, (const void *)k_gas_particle<P, false>, (const void *)k_cells<P>};
   for (int k = 0; k < 6; ++k) {
     cudaFuncAttributes a;
     if (cudaFuncGetAttributes(&a, fn[k]) != cudaSuccess) return -1;
     lim[k] = a.maxThreadsPerBlock;
   }
+  cudaFuncAttributes a;   // the re-store block size serves k_ranges and k_restore_in
+  if (cudaFuncGetAttributes(&a, (const void *)k_restore_in<P>) != cudaSuccess) return -1;
+  lim[1] = lim[1] < a.maxThreadsPerBlock ? lim[1] : a.maxThreadsPerBlock;
   return 0;
 }
 

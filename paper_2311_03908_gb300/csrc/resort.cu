@@ -13,6 +13,8 @@
 //   mover t:   t + (stayers before it) = t + P(clamp(idx, lb, ub)), where [lb, ub) is the run
 //              of kold equal to its new key and P(x) the number of stayers in positions < x
 //              (stayers keep their key, so kold orders them).
+// Three kernels: compaction (each block sums the counts of the blocks before it: no separate
+// scan pass), ranking (with one extra block that takes the large case), merge.
 #include <cuda_runtime.h>
 
 #include "radix.cuh"
@@ -24,42 +26,21 @@ namespace {
 constexpr int RZ_BLOCK = 1024;
 constexpr int RZ_SMEM_SORT = 4096;
 
-// exclusive scan of the per-block counts (one block); blk[nb] = total movers
-__global__ void __launch_bounds__(RZ_BLOCK) rz_scan(int *blk, int nb) {
-  pdl_wait();
-  __shared__ int part[RZ_BLOCK];
-  const int per = (nb + RZ_BLOCK - 1) / RZ_BLOCK;
-  const int b = threadIdx.x * per, e = min(b + per, nb);
-  int s = 0;
-  for (int t = b; t < e; ++t) s += blk[t];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int off = 1; off < RZ_BLOCK; off <<= 1) {
-    const int v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
-  }
-  int run = threadIdx.x ? part[threadIdx.x - 1] : 0;
-  for (int t = b; t < e; ++t) {
-    const int v = blk[t];
-    blk[t] = run;
-    run += v;
-  }
-  if (threadIdx.x == RZ_BLOCK - 1) blk[nb] = part[RZ_BLOCK - 1];
-}
-
 // movers before each position (pre[0..n], pre[n] = total) and the compacted movers; a block
 // of RZ_COMPACT threads covers RZ_BLOCK positions, four consecutive ones per thread (vector
-// loads and stores)
+// loads and stores). blk holds the movers of every block of RZ_BLOCK positions; a block adds
+// up those of the blocks before it itself (at most a few thousand counts, from L2), in a
+// fixed order, so no scan pass runs between the key kernel and this one.
 constexpr int RZ_COMPACT = RZ_BLOCK / 4;
 __global__ void __launch_bounds__(RZ_COMPACT) rz_compact(const unsigned *kold, const unsigned *knew, int n,
-                                                         const int *blk, int nb, int *pre,
-                                                         unsigned long long *comp) {
+                                                         const int *blk, int *pre, unsigned long long *comp) {
   pdl_wait();
   __shared__ int wsum[RZ_COMPACT / 32];
+  __shared__ int wbase[RZ_COMPACT / 32];
   const int i0 = blockIdx.x * RZ_BLOCK + 4 * threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int base = 0;   // this thread's share of the counts of the blocks before this one
+  for (int t = threadIdx.x; t < (int)blockIdx.x; t += RZ_COMPACT) base += blk[t];
   unsigned kn[4] = {0u, 0u, 0u, 0u};
   bool mv[4] = {false, false, false, false};
   if (i0 + 4 <= n) {
@@ -79,7 +60,10 @@ __global__ void __launch_bounds__(RZ_COMPACT) rz_compact(const unsigned *kold, c
     const int t = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += t;
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) base += __shfl_xor_sync(0xffffffffu, base, o);
   if (lane == 31) wsum[warp] = incl;
+  if (lane == 0) wbase[warp] = base;
   __syncthreads();
   if (warp == 0) {
     const int v = lane < RZ_COMPACT / 32 ? wsum[lane] : 0;
@@ -89,10 +73,13 @@ __global__ void __launch_bounds__(RZ_COMPACT) rz_compact(const unsigned *kold, c
       const int t = __shfl_up_sync(0xffffffffu, wi, o);
       if (lane >= o) wi += t;
     }
-    if (lane < RZ_COMPACT / 32) wsum[lane] = wi - v;
+    int bb = lane < RZ_COMPACT / 32 ? wbase[lane] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bb += __shfl_xor_sync(0xffffffffu, bb, o);
+    if (lane < RZ_COMPACT / 32) wsum[lane] = bb + wi - v;   // movers before the warp
   }
   __syncthreads();
-  int rank = blk[blockIdx.x] + wsum[warp] + incl - c;
+  int rank = wsum[warp] + incl - c;
   int r[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -109,23 +96,52 @@ __global__ void __launch_bounds__(RZ_COMPACT) rz_compact(const unsigned *kold, c
     for (int u = 0; u < 4; ++u)
       if (i0 + u < n) pre[i0 + u] = r[u];
   }
-  if (i0 <= n - 1 && n - 1 < i0 + 4) pre[n] = blk[nb];
+  if (i0 <= n - 1 && n - 1 < i0 + 4) pre[n] = rank;   // the last position's thread: all movers
 }
 
 __device__ __forceinline__ void cmpswap(unsigned long long &a, unsigned long long &b, bool asc) {
   if ((a > b) == asc) { const unsigned long long t = a; a = b; b = t; }
 }
 
+// more movers than fit in shared memory: one block sorts them in global memory (bitonic;
+// padded with the largest value up to a power of two)
+__device__ __noinline__ void rz_sort_big(int m, const unsigned long long *comp, unsigned long long *a, int cap) {
+  int P = 1;
+  while (P < m) P <<= 1;
+  if (P > cap) return;   // cannot happen: cap is the next power of two of n
+  for (int t = threadIdx.x; t < P; t += blockDim.x) a[t] = t < m ? comp[t] : ~0ull;
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < P; t += blockDim.x) {
+        const int u = t ^ j;
+        if (u > t) {
+          unsigned long long x = a[t], y = a[u];
+          cmpswap(x, y, (t & k) == 0);
+          a[t] = x;
+          a[u] = y;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // rank of every mover by counting the movers below it (composites are unique), written to
 // sorted[rank]; RZ_RANK_SPLIT consecutive lanes share a mover and count a share of the others
-// each; more than RZ_SMEM_SORT movers: left to rz_sort_big
+// each. More than RZ_SMEM_SORT movers: the grid's last block sorts them (rz_sort_big) and the
+// others return.
 constexpr int RZ_RANK_SPLIT = 8;
-__global__ void __launch_bounds__(256) rz_rank(const int *blk, int nb, const unsigned long long *comp,
-                                               unsigned long long *sorted) {
+constexpr int RZ_RANK_BLOCKS = RZ_SMEM_SORT * RZ_RANK_SPLIT / 256;
+__global__ void __launch_bounds__(256) rz_rank(const int *pre, int n, const unsigned long long *comp,
+                                               unsigned long long *sorted, int cap) {
   pdl_wait();
   __shared__ unsigned long long s[RZ_SMEM_SORT];
-  const int m = blk[nb];
-  if (m > RZ_SMEM_SORT) return;
+  const int m = pre[n];
+  if (m > RZ_SMEM_SORT) {
+    if (blockIdx.x == gridDim.x - 1) rz_sort_big(m, comp, sorted, cap);
+    return;
+  }
   if (blockIdx.x * blockDim.x >= m * RZ_RANK_SPLIT) return;   // whole block beyond the movers
   for (int q = threadIdx.x; q < m; q += blockDim.x) s[q] = comp[q];
   __syncthreads();
@@ -138,34 +154,6 @@ __global__ void __launch_bounds__(256) rz_rank(const int *blk, int nb, const uns
 #pragma unroll
   for (int o = RZ_RANK_SPLIT / 2; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o, RZ_RANK_SPLIT);
   if (t < m && part == 0) sorted[r] = v;
-}
-
-// more movers than fit: one block sorts them in global memory (bitonic; padded with the
-// largest value up to a power of two)
-__global__ void __launch_bounds__(RZ_BLOCK) rz_sort_big(const int *blk, int nb, const unsigned long long *comp,
-                                                        unsigned long long *a, int cap) {
-  pdl_wait();
-  const int m = blk[nb];
-  if (m <= RZ_SMEM_SORT) return;
-  int P = 1;
-  while (P < m) P <<= 1;
-  if (P > cap) return;   // cannot happen: cap is the next power of two of n
-  for (int t = threadIdx.x; t < P; t += RZ_BLOCK) a[t] = t < m ? comp[t] : ~0ull;
-  __syncthreads();
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int t = threadIdx.x; t < P; t += RZ_BLOCK) {
-        const int u = t ^ j;
-        if (u > t) {
-          unsigned long long x = a[t], y = a[u];
-          cmpswap(x, y, (t & k) == 0);
-          a[t] = x;
-          a[u] = y;
-        }
-      }
-      __syncthreads();
-    }
-  }
 }
 
 // Entries of the sorted c[lo, hi) below v (before(e, v) = e < v), or not above it
@@ -266,13 +254,12 @@ int resort_pairs(const unsigned *kold, const unsigned *knew, const unsigned *vma
   unsigned long long *sorted = comp + pow2;
   int *pre = reinterpret_cast<int *>(scratch + 4 * (size_t)pow2);
   int *blk = pre + n + 1;
-  launch_k(pdl, rz_scan, 1, RZ_BLOCK, st, blk, nb);
-  launch_k(pdl, rz_compact, nb, RZ_COMPACT, st, kold, knew, n, (const int *)blk, nb, pre, comp);
-  launch_k(pdl, rz_rank, RZ_SMEM_SORT * RZ_RANK_SPLIT / 256, 256, st, (const int *)blk, nb, (const unsigned long long *)comp, sorted);
-  launch_k(pdl, rz_sort_big, 1, RZ_BLOCK, st, (const int *)blk, nb, (const unsigned long long *)comp, sorted, pow2);
+  launch_k(pdl, rz_compact, nb, RZ_COMPACT, st, kold, knew, n, (const int *)blk, pre, comp);
+  launch_k(pdl, rz_rank, RZ_RANK_BLOCKS + 1, 256, st, (const int *)pre, n, (const unsigned long long *)comp, sorted,
+           pow2);
   launch_k(pdl, rz_merge, (n + RZ_MERGE - 1) / RZ_MERGE, RZ_MERGE, st, kold, knew, n, (const int *)pre,
            (const unsigned long long *)sorted, vmap, kout, vout);
-  if (launches) *launches += 5;
+  if (launches) *launches += 3;
   return (int)cudaPeekAtLastError();
 }
 

@@ -253,17 +253,67 @@ def test_invalid_inputs_rejected():
         _ctx(bad)
 
 
-def test_coupling_interval_parity():
+@pytest.mark.parametrize("prec", ["fp64", "split_kahan"])
+def test_coupling_interval_parity(prec):
+    # the gas is advanced every 4th step (Sec. 4); calls that end on, just after and between
+    # coupling steps, the state and the gas after each; the sources after a coupling step
     bed = synth.small_packed(seed=13, n=1500, v_scale=0.2, T0=1073.0)
     bed.beds[0].coupling_interval = 4
-    ctx = _ctx(bed)
+    ctx = _ctx(bed, prec)
     ref = oracle.Oracle(bed)
-    ctx.dem_step(10)
-    ref.step(10)
-    sg, so = ctx.dem_get_state(), ref.state()
-    for row in range(binding.DEM_NSTATE):
-        assert _rel(sg[row], so[row]) < 1e-7, binding.STATE_ROWS[row]
+    for n in (4, 1, 2, 5, 1, 3):
+        ctx.dem_step(n)
+        ref.step(n)
+        sg, so = ctx.dem_get_state(), ref.state()
+        gg, go = ctx.dem_get_gas(), ref.gas()
+        if prec == "fp64":
+            for row in range(binding.DEM_NSTATE):
+                assert _rel(sg[row], so[row]) < 1e-7, binding.STATE_ROWS[row]
+            for col in range(binding.DEM_NGAS):
+                assert _rel(gg[:, col], go[:, col]) < 1e-9
+        else:
+            for row in range(3):
+                assert _rel(sg[row], so[row]) < 1e-6
+            assert _rel(sg[9], so[9]) < 1e-5
+            assert _rel(gg[:, 0], go[:, 0]) < 1e-6 and _rel(gg[:, 4], go[:, 4]) < 1e-6
+            assert np.abs(gg[:, 1:4] - go[:, 1:4]).max() < 1e-6
+    # 16 steps: the last one is a coupling step, whose sources the oracle keeps
+    sgs, sos = ctx.dem_get_sources(), ref.deposits()
+    for col in range(binding.DEM_NDEP):
+        assert _rel(sgs[:, col], sos[:, col]) < (1e-9 if prec == "fp64" else 1e-4), binding.SOURCE_ROWS[col]
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "split"])
+def test_set_gas_between_coupling_steps(prec):
+    """A coupling input that arrives between coupling steps is the gas state until the next
+    coupling step advances it, for eager steps and replayed graphs alike (the other gas
+    buffer is brought up to date once, then left alone)."""
+    bed = synth.small_packed(seed=17, n=1500, v_scale=0.2)
+    bed.beds[0].coupling_interval = 4
+    a, b = _ctx(bed, prec), _ctx(bed, prec)
+    a.dem_step(5)
+    b.dem_step_graph(5)
+    g = a.dem_get_gas()
+    Y = np.ascontiguousarray(g[:, 1:4])
+    Y[:, 0] *= 0.8
+    Y[:, 1] = 1.0 - Y[:, 0] - Y[:, 2]
+    T = np.ascontiguousarray(g[:, 4]) + 20.0
+    for c in (a, b):
+        c.dem_set_gas(Y, T)
+    g0 = a.dem_get_gas()
+    assert np.allclose(g0[:, 4], T, rtol=1e-7) and np.array_equal(g0[:, 0], g[:, 0])
+    for k in range(2):                     # the 6th and 7th steps advance no gas
+        a.dem_step(1)
+        b.dem_step_graph(1)
+        assert np.array_equal(a.dem_get_gas(), g0) and np.array_equal(b.dem_get_gas(), g0), k
+    a.dem_step(1)                          # the 8th step is a coupling step
+    b.dem_step_graph(1)
+    g1 = a.dem_get_gas()
+    assert not np.array_equal(g1[:, 4], g0[:, 4])
+    assert np.array_equal(g1, b.dem_get_gas()) and np.array_equal(a.dem_get_state(), b.dem_get_state())
+    a.close()
+    b.close()
 
 
 @pytest.mark.parametrize("prec", ["fp64", "split"])
@@ -392,7 +442,19 @@ def test_occupied_sources_match_the_dense_rows(prec):
         assert np.array_equal(cells, occ)
         assert np.array_equal(rows, dense[occ])
         assert np.all(dense[np.setdiff1d(np.arange(ctx.ncells), occ)] == 0)
+        # page-locked buffers take the rows from the kernel itself: the same rows
+        cap = min(ctx.n, ctx.ncells)
+        pc = torch.full((cap,), -7, dtype=torch.int64).pin_memory()
+        po = torch.full((cap, binding.DEM_NDEP), -7.0, dtype=torch.float64).pin_memory()
+        c2, r2 = ctx.dem_get_sources_occupied(pc, po)
+        assert np.array_equal(c2.numpy(), occ) and np.array_equal(r2.numpy(), dense[occ])
+        assert np.all(pc[len(occ):].numpy() == -7) and np.all(po[len(occ):].numpy() == -7.0)
     small = np.zeros(10, dtype=np.int64), np.zeros((10, binding.DEM_NDEP))
     with pytest.raises(binding.DemError):
         ctx.dem_get_sources_occupied(*small)
+    # too small page-locked buffers: the count is refused and nothing is written
+    ps = torch.full((10,), -7, dtype=torch.int64).pin_memory(), torch.full((10, binding.DEM_NDEP), -7.0).pin_memory()
+    with pytest.raises(binding.DemError):
+        ctx.dem_get_sources_occupied(*ps)
+    assert np.all(ps[0].numpy() == -7) and np.all(ps[1].numpy() == -7.0)
     ctx.close()
