@@ -194,20 +194,48 @@ template <class R> __device__ __forceinline__ R frcp(R x) {
   if constexpr (sizeof(R) == 8) return 1.0 / x; else return __fdividef(1.0f, x);
 }
 
+// The NASA polynomials of Table C1 (two temperature ranges per species). In the FP32 forms
+// both ranges are evaluated and the result is selected: a range chosen before the loads would
+// make the coefficients' constant-memory address differ between the threads of a warp (whose
+// parcels straddle the range boundary) and serialise the loads, which took 15 % of the
+// gas-particle kernel; with both ranges every load is warp-uniform. The arithmetic of the
+// chosen range is the same either way, so are the results. The FP64 form, whose FP64 pipe
+// is narrow, evaluates only the chosen range.
+template <class R> __device__ __forceinline__ R h_poly(const R *a, R T) {
+  return T * (a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])))) + a[5];
+}
+template <class R> __device__ __forceinline__ R cp_poly(const R *a, R T) {
+  return a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
+}
+template <class R> __device__ __forceinline__ R dcp_poly(const R *a, R T) {
+  return a[0] + T * (a[1] + T * (a[2] + T * a[3]));
+}
 template <class R> __device__ __forceinline__ R h_over_R(int s, R T) {
   const Tab<R> &t = tab<R>();
-  const R *a = t.h[s][T <= t.nasaT[s] ? 0 : 1];
-  return T * (a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])))) + a[5];
+  if constexpr (sizeof(R) == 4) {
+    const R lo = h_poly(t.h[s][0], T), hi = h_poly(t.h[s][1], T);
+    return T <= t.nasaT[s] ? lo : hi;
+  } else {
+    return h_poly(t.h[s][T <= t.nasaT[s] ? 0 : 1], T);
+  }
 }
 template <class R> __device__ __forceinline__ R cp_over_R(int s, R T) {
   const Tab<R> &t = tab<R>();
-  const R *a = t.cp[s][T <= t.nasaT[s] ? 0 : 1];
-  return a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
+  if constexpr (sizeof(R) == 4) {
+    const R lo = cp_poly(t.cp[s][0], T), hi = cp_poly(t.cp[s][1], T);
+    return T <= t.nasaT[s] ? lo : hi;
+  } else {
+    return cp_poly(t.cp[s][T <= t.nasaT[s] ? 0 : 1], T);
+  }
 }
 template <class R> __device__ __forceinline__ R dcp_over_R(int s, R T) {
   const Tab<R> &t = tab<R>();
-  const R *a = t.dcp[s][T <= t.nasaT[s] ? 0 : 1];
-  return a[0] + T * (a[1] + T * (a[2] + T * a[3]));
+  if constexpr (sizeof(R) == 4) {
+    const R lo = dcp_poly(t.dcp[s][0], T), hi = dcp_poly(t.dcp[s][1], T);
+    return T <= t.nasaT[s] ? lo : hi;
+  } else {
+    return dcp_poly(t.dcp[s][T <= t.nasaT[s] ? 0 : 1], T);
+  }
 }
 
 // ---------------------------------------------------------------------------------------

@@ -1047,6 +1047,38 @@ __global__ void __launch_bounds__(128, 8) k_radiation(StepView<P> V) {
   if (V.diag) V.diag[(size_t)DG_TSE * V.cap + i] = (double)Tse;
 }
 
+// The diagnostics rows of parcel i (dem_set_diagnostics), as a call of its own: inlined, its
+// FP64 conversions were scheduled ahead of the branch and ran for every parcel without
+// diagnostics too, on GB300's narrow FP64 pipe.
+template <class R>
+__device__ __noinline__ void gp_write_diag(double *dg, size_t cp, int i, const R F[3], const R Tq[3], const R Fd[3],
+                                           const KinOut<R> &kn, R Kp, R Qconv, R Nu, R Re, long long cell, R Qrad,
+                                           R Qcond, bool no_tse) {
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    dg[(DG_FC + q) * cp + i] = (double)F[q];
+    dg[(DG_TC + q) * cp + i] = (double)Tq[q];
+    dg[(DG_FD + q) * cp + i] = (double)Fd[q];
+    dg[(DG_XIDOT + q) * cp + i] = (double)kn.xidot[q];
+    dg[(DG_A + q) * cp + i] = (double)kn.A[q];
+    dg[(DG_B + q) * cp + i] = (double)kn.B[q];
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) dg[(DG_MDOT + q) * cp + i] = (double)kn.mdot[q];
+  dg[DG_K * cp + i] = (double)Kp;
+  dg[DG_QCONV * cp + i] = (double)Qconv;
+  dg[DG_QR * cp + i] = (double)kn.Qr;
+  dg[DG_QRM * cp + i] = (double)kn.Qrm;
+  dg[DG_FFILM * cp + i] = (double)kn.F;
+  dg[DG_SH * cp + i] = (double)kn.Sh;
+  dg[DG_NU * cp + i] = (double)Nu;
+  dg[DG_RE * cp + i] = (double)Re;
+  dg[DG_CELL * cp + i] = (double)cell;
+  dg[DG_QRAD * cp + i] = (double)Qrad;
+  dg[DG_QCOND * cp + i] = (double)Qcond;
+  if (no_tse) dg[DG_TSE * cp + i] = 0.0;
+}
+
 // ---------------------------------------------------------------------------------------
 // Per parcel (storage order): gas-particle terms, kinetics, second half kick, temperature
 // and mass update; writes the parcel's contributions to its cell sums.
@@ -1186,32 +1218,9 @@ __global__ void __launch_bounds__(256, P::exact ? 1 : 4) k_gas_particle(StepView
     s[SR_EQ * cp + i] = kn.EQ;
     s[SR_ES * cp + i] = kn.ES;
   }
-  if (V.diag) {
-    double *dg = V.diag;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      dg[(DG_FC + q) * cp + i] = (double)F[q];
-      dg[(DG_TC + q) * cp + i] = (double)Tq[q];
-      dg[(DG_FD + q) * cp + i] = (double)Fd[q];
-      dg[(DG_XIDOT + q) * cp + i] = (double)kn.xidot[q];
-      dg[(DG_A + q) * cp + i] = (double)kn.A[q];
-      dg[(DG_B + q) * cp + i] = (double)kn.B[q];
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) dg[(DG_MDOT + q) * cp + i] = (double)kn.mdot[q];
-    dg[DG_K * cp + i] = (double)Kp;
-    dg[DG_QCONV * cp + i] = (double)Qconv;
-    dg[DG_QR * cp + i] = (double)kn.Qr;
-    dg[DG_QRM * cp + i] = (double)kn.Qrm;
-    dg[DG_FFILM * cp + i] = (double)kn.F;
-    dg[DG_SH * cp + i] = (double)kn.Sh;
-    dg[DG_NU * cp + i] = (double)Nu;
-    dg[DG_RE * cp + i] = (double)Re;
-    dg[DG_CELL * cp + i] = (double)(c - V.beds[meta >> 8].cell_off);
-    dg[DG_QRAD * cp + i] = (double)Qrad;
-    dg[DG_QCOND * cp + i] = (double)Qcond;
-    if (!RAD || !(fl & DEM_RADIATION)) dg[DG_TSE * cp + i] = 0.0;
-  }
+  if (V.diag)
+    gp_write_diag<R>(V.diag, cp, i, F, Tq, Fd, kn, Kp, Qconv, Nu, Re, (long long)c - V.beds[meta >> 8].cell_off, Qrad,
+                     Qcond, !RAD || !(fl & DEM_RADIATION));
 }
 
 // ---------------------------------------------------------------------------------------
