@@ -12,7 +12,9 @@ Parity notes per function (pins live in tests/test_oracle_*.py):
   * drag and convection: pinned by their textbook limits (Stokes drag, Nu = Sh = 2).
   * gas properties: pinned by invariants (Fuller scaling, Wilke binary limit, NASA
     dH/dT = C_p, standard enthalpies); the absolute Fuller constant is parity unpinned.
-  * gas update: parity unpinned (a prescribed field with a simple explicit update).
+  * prescribed gas update: pinned by the upwind scheme's conservation, transport speed and
+    monotonicity, the gas-parcel energy exchange and the exact mixing of the deposited
+    mass (tests/test_oracle_gas_update.py).
   * porosity-dependent D_eff values: parity unpinned (the tortuosity is not printed).
 """
 from __future__ import annotations
