@@ -65,6 +65,17 @@ def test_fuller_scaling_and_wilke_binary_limit():
     assert g1["D12"] > g1["D13"]
 
 
+def test_fuller_absolute_value_against_measured_diffusivities():
+    # eq (2-26) as a number, not only its scaling: the binary coefficients at 1 atm against
+    # measured ones (Fuller's correlation reproduces such data to a few per cent)
+    hb = handbook_values()
+    cfg = synth.BedConfig()
+    d13 = oracle.gas_props(cfg, 298.15, [0.5, 0.0, 0.5], p=101325.0)["D13"]
+    d12 = oracle.gas_props(cfg, 307.1, [0.5, 0.5, 0.0], p=101325.0)["D12"]
+    assert abs(d13 / hb["D_H2_N2_298K"] - 1.0) < 0.10, d13
+    assert abs(d12 / hb["D_H2_H2O_307K"] - 1.0) < 0.10, d12
+
+
 def test_ideal_gas_density_h2_at_stp():
     g = oracle.gas_props(synth.BedConfig(), 273.15, [1, 0, 0], p=101325.0)
     assert abs(g["rho"] - 0.08988) < 0.002 * 0.08988
