@@ -11,7 +11,8 @@ Parity notes per function (pins live in tests/test_oracle_*.py):
     against the printed closed forms, printed q values and densities, loose F_mean).
   * drag and convection: pinned by their textbook limits (Stokes drag, Nu = Sh = 2).
   * gas properties: pinned by invariants (Fuller scaling, Wilke binary limit, NASA
-    dH/dT = C_p, standard enthalpies); the absolute Fuller constant is parity unpinned.
+    dH/dT = C_p, standard enthalpies) and the absolute Fuller coefficients against measured
+    binary diffusivities.
   * prescribed gas update: pinned by the upwind scheme's conservation, transport speed and
     monotonicity, the gas-parcel energy exchange and the exact mixing of the deposited
     mass (tests/test_oracle_gas_update.py).
