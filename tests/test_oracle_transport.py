@@ -76,6 +76,16 @@ def test_fuller_absolute_value_against_measured_diffusivities():
     assert abs(d12 / hb["D_H2_H2O_307K"] - 1.0) < 0.10, d12
 
 
+@pytest.mark.parametrize("T", [600, 1000])
+def test_gas_heat_capacities_against_janaf(T):
+    # the gas ranges of Table C1 as numbers: molar C_p of the pure gases against JANAF
+    hb = handbook_values()
+    M = {"H2": 2.016e-3, "H2O": 18.015e-3, "N2": 28.014e-3}
+    for name, Y in (("H2", [1, 0, 0]), ("H2O", [0, 1, 0]), ("N2", [0, 0, 1])):
+        cp = oracle.gas_props(synth.BedConfig(), float(T), Y, p=101325.0)["cp"] * M[name]
+        assert abs(cp / hb[f"cp_{name}_{T}K"] - 1.0) < 0.01, (name, T, cp)
+
+
 def test_ideal_gas_density_h2_at_stp():
     g = oracle.gas_props(synth.BedConfig(), 273.15, [1, 0, 0], p=101325.0)
     assert abs(g["rho"] - 0.08988) < 0.002 * 0.08988
