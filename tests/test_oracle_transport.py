@@ -86,6 +86,13 @@ def test_gas_heat_capacities_against_janaf(T):
         assert abs(cp / hb[f"cp_{name}_{T}K"] - 1.0) < 0.01, (name, T, cp)
 
 
+@pytest.mark.parametrize("species", ["Fe2O3", "Fe3O4", "FeO", "Fe"])
+def test_solid_heat_capacities_at_298K_against_janaf(species):
+    # the solids' low ranges of Table C1 as numbers (J/kg/K times the molar mass)
+    cp = oracle.cp(species, 298.15) * oracle.molar_mass(species)
+    assert abs(cp / handbook_values()[f"cp_{species}_298K"] - 1.0) < 0.03, (species, cp)
+
+
 def test_ideal_gas_density_h2_at_stp():
     g = oracle.gas_props(synth.BedConfig(), 273.15, [1, 0, 0], p=101325.0)
     assert abs(g["rho"] - 0.08988) < 0.002 * 0.08988
