@@ -130,8 +130,9 @@ def algorithmic_bytes(kernel: str, n: int, ncells: int, zbar: float, L: float, r
     if kernel == "k_gas_particle":   # the accelerations and 7 of the 13 source rows are stored on a
         # stepping call's last step only
         return n * ((4 + 4 + R + 3 * R + R + 32 + 1 + fc * 6 * R + 3 * R) + (6 * R + R + 32 + 6 * R)) + ncells * 13 * R
-    if kernel == "k_cells":
-        return ncells * ((4 + 1 + 8 + 5 * 8 + 2 * R) + (5 * 8 + 14 * R)) + n * (6 * R + 4)
+    if kernel == "k_cells":          # bed, mark, range, state in (rho and c_p are recomputed in the
+        # FP32 forms, read in the FP64 form); state and properties out; the parcels' 6 source rows
+        return ncells * ((4 + 1 + 8 + 5 * 8 + (2 * R if R == 8 else 0)) + (5 * 8 + 14 * R)) + n * (6 * R + 4)
     if kernel == "k_radiation":      # own meta, local coordinates, key, d, T (+ FP64 position); the
         # cell's eps_g and T_g; Q_rad out (the neighbours' records are cache re-reads)
         return n * ((4 + 16 + 4 + 2 * R + (24 if R == 8 else 0)) + R) + ncells * 2 * R

@@ -245,24 +245,40 @@ template <class R> struct CellProps {
   R rho, mu, lam, cp, x, Dm, sc13, pr13, epow, D[2], uz, eps, T, ux, uy;
 };
 
+// mean molar mass, density (eq (3-53)) and heat capacity (eq (3-57)) of the gas: shared by the
+// property record and by the gas update, which recomputes them instead of reading the record
+template <class R> __device__ __forceinline__ R gas_molar_mass(const R Y[3]) {
+  const Tab<R> &t = tab<R>();
+  return frcp<R>(fdiv<R>(Y[0], t.Mj[0]) + fdiv<R>(Y[1], t.Mj[1]) + fdiv<R>(Y[2], t.Mj[2]));
+}
+template <class R> __device__ __forceinline__ R gas_density(const BedP<R> &B, R Mg, R T) {
+  return fdiv<R>(Mg * B.p0, (R)kRgas * T);
+}
+template <class R> __device__ __forceinline__ R gas_heat_capacity(const R Y[3], R T) {
+  const Tab<R> &t = tab<R>();
+  R cp = 0;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) cp += Y[j] * cp_over_R<R>(j, T) * t.RMj[j];
+  return cp;
+}
+
 template <class R>
 __device__ inline CellProps<R> gas_cell_props(const BedP<R> &B, R eps, const R Y[3], R T) {
   const Tab<R> &t = tab<R>();
   CellProps<R> o;
   const R p = B.p0;
-  const R inv = fdiv<R>(Y[0], t.Mj[0]) + fdiv<R>(Y[1], t.Mj[1]) + fdiv<R>(Y[2], t.Mj[2]);
-  const R Mg = frcp<R>(inv);
+  const R Mg = gas_molar_mass<R>(Y);
   const R xp0 = fdiv<R>(Y[0] * Mg, t.Mj[0]), xp1 = fdiv<R>(Y[1] * Mg, t.Mj[1]), xp2 = fdiv<R>(Y[2] * Mg, t.Mj[2]);
   const R den = xp0 + xp1;
   o.x = den > (R)0 ? fdiv<R>(xp0, den) : (R)0;
-  o.rho = fdiv<R>(Mg * p, (R)kRgas * T);
-  R mu = 0, lam = 0, cp = 0;
+  o.rho = gas_density<R>(B, Mg, T);
+  R mu = 0, lam = 0;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     mu += Y[j] * (t.visc[j][0] + T * (t.visc[j][1] + T * t.visc[j][2]));
     lam += Y[j] * (t.cond[j][0] + T * (t.cond[j][1] + T * (t.cond[j][2] + T * (t.cond[j][3] + T * t.cond[j][4]))));
-    cp += Y[j] * cp_over_R<R>(j, T) * t.RMj[j];
   }
+  const R cp = gas_heat_capacity<R>(Y, T);
   o.mu = mu; o.lam = lam; o.cp = cp;
   // Fuller binary coefficients D(H2,H2O), D(H2,N2) (T^1.75 = T sqrt(T) sqrt(sqrt(T))) and
   // Wilke's rule for H2 (its 0/0 limit in pure H2 is the binary coefficient)

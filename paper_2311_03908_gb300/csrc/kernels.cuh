@@ -1376,10 +1376,12 @@ __device__ __forceinline__ void cell_step(StepView<P> &V, long long c, int mode 
       const bool up = c - B.cell_off >= layer && !V.mark[c - layer];
       const Tab<R> &t = tab<R>();
       const R dtg = bp.dtg;
-      const R rho = V.gp[(size_t)c * GP_STRIDE + GP_RHO], cpg = V.gp[(size_t)c * GP_STRIDE + GP_CP];
       const R eps_r = eps2.x + eps2.y, T_r = T2.x + T2.y;
       const R uz = bp.U_in / eps_r;
       const R Yr[3] = {Y2[0].x + Y2[0].y, Y2[1].x + Y2[1].y, Y2[2].x + Y2[2].y};
+      // the density and heat capacity of the old state, computed as its property record holds
+      // them (the record is a function of these FP32 values), instead of read from the record
+      const R rho = gas_density<R>(bp, gas_molar_mass<R>(Yr), T_r), cpg = gas_heat_capacity<R>(Yr, T_r);
       R Yup[3] = {bp.Y_in[0], bp.Y_in[1], bp.Y_in[2]}, Tup = bp.T_in;
       if (up) {   // the old state of the cell below
         Yup[0] = gas_r<P>(G, GS_Y0 * nc + c - layer); Yup[1] = gas_r<P>(G, GS_Y1 * nc + c - layer);
