@@ -157,7 +157,7 @@ def survey_step_bytes(n: int, ncells: int, zbar: float, rsize: int, passes: int)
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one full-size ncu
 # capture of the 2M-parcel bed in the split-Kahan form between list builds, after the
 # 300-step settle; per parcel), valid only for the CUDA sources it was taken on.
-TRAFFIC_SOURCE_SHA256 = "2bb6d8ac827fd433644232a7a56571e41837c9704c8cd4acb073271fe4bbec8d"
+TRAFFIC_SOURCE_SHA256 = "0ee4708c299f9781f9e448d4fe1868d9fe41a1fe1fc1e773e628b547bef48a40"
 TRAFFIC_WORKLOAD = ("ibm_2m", "split_kahan", 2_000_000)
 TRAFFIC_BYTES_PER_PARCEL = {"k_gas_particle": 169.2, "k_key": 117.1, "k_cells": 99.6, "k_contact_screen": 58.4,
                             "k_contact_forces": 17.7, "k_ranges": 8.1}

@@ -5,8 +5,11 @@
  * One call of dem_step advances every coarse-grained parcel of every bed by one DEM time
  * step, entirely on the GPU:
  *   1. half kick and drift (velocity Verlet of eq (3-3) and eq (3-6));
- *   2. binning by an LSD radix sort of the parcels on their cell key;
- *   3. gather of the parcel state into the sorted order, occupied-cell ranges;
+ *   2. binning of the parcels on their cell key: an LSD radix sort at the first binning,
+ *      then each step an incremental re-sort of the keys and the permutation (the same
+ *      permutation bit for bit);
+ *   3. occupied-cell ranges; the parcel state re-stored in cell order at every k-th
+ *      neighbour-list build (it stays in place in between);
  *   4. soft-sphere contacts with the neighbouring parcels (linear spring-dashpot normal
  *      force, tangential spring with a contact-history table and a Coulomb cap) and with
  *      the analytic reactor wall (cylinder, flat bottom or cone, perforated plate, lid);
@@ -16,10 +19,11 @@
  *      scaling (eqs (3-41), (3-49), (3-50), (3-52));
  *   6. second half kick, particle temperature (eqs (3-8), (3-9)) and, at coupling steps
  *      (every n = coupling_interval steps, Sec. 4), the layer masses (eq (3-4));
- *   7. deposition of the cell sources by a segmented reduction over the sorted parcels
- *      (eqs (3-25), (3-27a), (3-38), (3-39), (4-4), (4-5), (4-10), (4-11));
- *   8. a simple explicit update of the prescribed gas field (volume fraction, species,
- *      temperature; semi-implicit in the convective coefficient as in eq (4-6)).
+ *   7. at coupling steps, deposition of the cell sources by a segmented reduction over the
+ *      sorted parcels (eqs (3-25), (3-27a), (3-38), (3-39), (4-4), (4-5), (4-10), (4-11));
+ *   8. at coupling steps, a simple explicit update of the prescribed gas field (volume
+ *      fraction, species, temperature; semi-implicit in the convective coefficient as in
+ *      eq (4-6)), which is otherwise left unchanged.
  *
  * Conventions (every entry point):
  *   - returns int status: DEM_OK (0) or a negative DEM_E* code; never aborts or exits;
@@ -264,7 +268,8 @@ enum { DEM_NGAS = 6 };
 int64_t dem_num_cells(dem_ctx *c);
 int dem_get_gas(dem_ctx *c, double *out_host);
 
-/* Cell sources of the last coupling step, DEM_NDEP doubles per cell (host): V_s, S_H2,
+/* Cell sources of the last step taken (the coupling output of Sec. 4 when that step is a
+ * coupling step), DEM_NDEP doubles per cell (host): V_s, S_H2,
  * S_H2O (kg/s into the gas), K, K v_x, K v_y, K v_z (eq (3-27a)), hA, hA T_p (eqs (4-4),
  * (4-5)), Q_rm, Q_r (eqs (3-38), (3-49), (3-50)), E Q, E S (eqs (4-10), (4-11)), count.
  * Recomputed from the per-parcel sources kept from the last step. Synchronous. */
