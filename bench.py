@@ -157,22 +157,29 @@ def survey_step_bytes(n: int, ncells: int, zbar: float, rsize: int, passes: int)
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one full-size ncu
 # capture of the 2M-parcel bed in the split-Kahan form between list builds, after the
 # 300-step settle; per parcel), valid only for the CUDA sources it was taken on.
-TRAFFIC_SOURCE_SHA256 = "0ee4708c299f9781f9e448d4fe1868d9fe41a1fe1fc1e773e628b547bef48a40"
+TRAFFIC_SOURCE_SHA256 = "66daeeb47eb051fdb6b1ffcd5811fd31a9fd60d4f0eb426a743c327e62aca2d8"
 TRAFFIC_WORKLOAD = ("ibm_2m", "split_kahan", 2_000_000)
 TRAFFIC_BYTES_PER_PARCEL = {"k_gas_particle": 169.2, "k_key": 117.1, "k_cells": 99.6, "k_contact_screen": 58.4,
                             "k_contact_forces": 17.7, "k_ranges": 8.1}
 
 
 def source_sha256() -> str:
+    """Hash of the CUDA sources and the C header with comments and blank lines left out: a
+    change of code invalidates the measured traffic, a change of comments does not."""
     import glob
     import hashlib
+    import re
     h = hashlib.sha256()
     files = sorted(glob.glob(os.path.join(ROOT, "paper_2311_03908_gb300", "csrc", "*.cu")) +
                    glob.glob(os.path.join(ROOT, "paper_2311_03908_gb300", "csrc", "*.cuh")) +
                    [os.path.join(ROOT, "include", "dem.h")])
     for f in files:
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        code = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+        h.update(os.path.basename(f).encode() + b"\0" + code.encode())
     return h.hexdigest()
 
 
