@@ -146,3 +146,45 @@ def test_equimolar_reduction_keeps_the_molar_flow():
         assert abs(molar_out / molar_in - 1) < 2e-3
     assert g[-1, 2] > 0.4
     assert g[:, 4].max() - cfg.T_in < 5.0
+
+
+def test_solved_flow_carries_a_band_at_the_inlet_velocity():
+    # one column of cells without parcels and a band of gas exchanged at the same mean molar
+    # mass (more H2O, less N2 and H2), so the density stays uniform: continuity (eq (3-24))
+    # makes the solved flow the plug flow U_in, and the species balance (eq (4-9)) carries the
+    # band up the column at that speed -- its excess is conserved and its centroid advances
+    # by U_in dt_CFD / dz cells per coupling step. The balance's molecular diffusion spreads
+    # the band symmetrically; with its composition-dependent coefficient it moves the centroid
+    # by ~1e-4 of that shift, so the speed is checked to 1e-3 (a wrong velocity, sign or
+    # upwind direction is off by far more)
+    nz, U, dt, n = 60, 0.2, 1e-4, 10
+    cfg = synth.BedConfig(D=0.004, H=0.003 * nz, nx=1, ny=1, nz=nz, dt=dt, cg_ratio=4.0, U_in=U, T_in=1000.0,
+                          Y_in=(0.9, 0.05, 0.05), coupling_interval=n,
+                          flags=NO_PARTICLE_PHYSICS | synth.NO_GRAVITY | synth.GAS_SOLVER)
+    M = np.array([2.016e-3, 18.015e-3, 28.014e-3])
+    # (dH2, dH2O, dN2) with sum 0 and sum d/M 0: the mean molar mass is unchanged
+    d_h2o = 0.04
+    A = np.array([[1.0, 1.0], [1.0 / M[0], 1.0 / M[2]]])
+    d_h2, d_n2 = np.linalg.solve(A, [-d_h2o, -d_h2o / M[1]])
+    band = (np.arange(nz) >= 8) & (np.arange(nz) < 12)
+    Y = np.tile([0.9, 0.05, 0.05], (nz, 1))
+    Y[band] += [d_h2, d_h2o, d_n2]
+    assert Y.min() > 0
+    o = oracle.Oracle(bed_from_arrays(cfg, np.zeros(0), 0.0, 0.0), Y, np.full(nz, 1000.0))
+    z = np.arange(nz)
+
+    def moments():
+        ex = o.gas()[:, 2] - 0.05
+        return ex.sum(), (z * ex).sum()
+
+    m0, f0 = moments()
+    solves = 100
+    o.step(solves * n)
+    m1, f1 = moments()
+    fl = o.flow()
+    assert np.allclose(fl[:, 2], U, rtol=1e-10) and np.abs(fl[:, :2]).max() == 0.0
+    assert abs(o.gas()[-3:, 2] - 0.05).max() < 1e-12           # the band has not reached the outlet
+    k = U * n * dt / (cfg.H / nz)
+    assert abs(m1 / m0 - 1.0) < 1e-10
+    assert abs((f1 / m1 - f0 / m0) / (solves * k) - 1.0) < 1e-3
+    assert o.gas()[:, 2].max() < 0.09 and o.gas()[:, 2].min() >= 0.05 - 1e-15   # spread, no new extrema
